@@ -1,0 +1,256 @@
+"""CPU oracle for the hybrid direct-iterative KKT method -- TEST INFRASTRUCTURE.
+
+Plain, slow, single-threaded FP64 restatement of what the CUDA path computes
+(symbolic analysis S1-S5, assembly of H_gamma = H~ + delta I + gamma J^T J,
+Cholesky, CG on the Schur complement S = J H_gamma^-1 J^T, residuals).
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
+leg may import this package. It shares no code with the CUDA product path.
+
+The C part (``kkt_oracle.c``) is compiled with plain gcc by ``build()``;
+``reduce4x4``/``recover4x4`` (the 4x4 <-> 2x2 reduction of Sec. 3) are
+numpy/scipy.
+
+Parity status: S2 (the AMD order) is pinned by the special cases in the
+tests (zero fill on trees, identity on cliques, hand-worked graphs, valid
+permutation, brute-force fill) and otherwise only by agreement with the
+library's independent implementation ("parity unpinned" beyond those).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "kkt_oracle.c")
+_LIB = os.path.join(_HERE, "libkkt_oracle.so")
+_lib = None
+
+# S5 relaxation parameters used unless a caller overrides them
+RELAX_SMALL, RELAX_NUM, RELAX_DEN, RELAX_WMAX = 16, 1, 10, 256
+
+
+def build(force=False):
+    """Compile the oracle with gcc (no BLAS, no OpenMP)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", _LIB, _SRC, "-lm"])
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_LIB)
+        P = C.c_void_p
+        i64p = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
+        i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+        f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+        L.orc_analyse.restype = P
+        L.orc_analyse.argtypes = [C.c_int64, C.c_int64, i64p, i32p, i64p, i32p,
+                                  C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                  C.POINTER(C.c_int32)]
+        L.orc_sym_info.argtypes = [P, i64p]
+        L.orc_sym_flops.restype = C.c_double
+        L.orc_sym_flops.argtypes = [P]
+        for nm in ("orc_sym_amd", "orc_sym_perm", "orc_sym_parent"):
+            getattr(L, nm).argtypes = [P, i32p]
+        L.orc_sym_colcount.argtypes = [P, i64p]
+        L.orc_sym_lpattern.argtypes = [P, i64p, i32p]
+        L.orc_sym_supernodes.argtypes = [P, i32p, i64p, i32p, i32p]
+        L.orc_sym_free.argtypes = [P]
+        L.orc_factor.restype = P
+        L.orc_factor.argtypes = [P, f64p, f64p, C.c_double, C.c_double, C.POINTER(C.c_int32)]
+        L.orc_fail_col.restype = C.c_int64
+        L.orc_fail_col.argtypes = [P]
+        L.orc_get_L.argtypes = [P, i64p, i32p, f64p]
+        L.orc_hsolve.argtypes = [P, f64p, f64p]
+        L.orc_solve.restype = C.c_int32
+        L.orc_solve.argtypes = [P, f64p, f64p, C.c_double, C.c_double, f64p, f64p, C.c_double,
+                                C.c_double, C.c_int32, C.c_int32, C.c_double, f64p, f64p, f64p]
+        L.orc_residual.argtypes = [P, f64p, f64p, C.c_double, f64p, f64p, f64p, f64p, f64p]
+        L.orc_num_free.argtypes = [P]
+        _lib = L
+    return _lib
+
+
+def _c(a, dt):
+    a = np.ascontiguousarray(a, dtype=dt)
+    return a if a.size else np.zeros(1, dt)
+
+
+class Symbolic:
+    """S1-S5 of the pinned symbolic analysis for one (H~, J) pattern."""
+
+    def __init__(self, n, m, H_colptr, H_rowidx, J_rowptr, J_colidx, *, relax_small=RELAX_SMALL,
+                 relax_num=RELAX_NUM, relax_den=RELAX_DEN, wmax=RELAX_WMAX, ordering="amd"):
+        L = _load()
+        self.n, self.m = int(n), int(m)
+        st = C.c_int32(0)
+        self._h = L.orc_analyse(self.n, self.m, _c(H_colptr, np.int64), _c(H_rowidx, np.int32),
+                                _c(J_rowptr, np.int64), _c(J_colidx, np.int32),
+                                relax_small, relax_num, relax_den, wmax,
+                                0 if ordering == "amd" else 1, C.byref(st))
+        if st.value != 0 or not self._h:
+            self._h = None
+            raise ValueError(f"oracle analyse: invalid input (status {st.value})")
+        info = np.zeros(5, np.int64)
+        L.orc_sym_info(self._h, info)
+        self.nsuper = int(info[1])
+        self.nnzL = int(info[2])
+        self.n_snrows = int(info[3])
+        self.panel_entries = int(info[4])
+        self.flops = float(L.orc_sym_flops(self._h))
+
+    def _get(self, fn, size, dt):
+        a = np.zeros(size, dt)
+        getattr(_load(), fn)(self._h, a)
+        return a
+
+    @property
+    def amd_order(self):
+        return self._get("orc_sym_amd", self.n, np.int32)
+
+    @property
+    def perm(self):
+        return self._get("orc_sym_perm", self.n, np.int32)
+
+    @property
+    def parent(self):
+        return self._get("orc_sym_parent", self.n, np.int32)
+
+    @property
+    def colcount(self):
+        return self._get("orc_sym_colcount", self.n, np.int64)
+
+    def l_pattern(self):
+        """Strictly-lower pattern of L by columns (final labels)."""
+        Lp = np.zeros(self.n + 1, np.int64)
+        Li = np.zeros(max(1, self.nnzL - self.n), np.int32)
+        _load().orc_sym_lpattern(self._h, Lp, Li)
+        return Lp, Li[: self.nnzL - self.n]
+
+    def supernodes(self):
+        """(start[nsuper+1], rowptr[nsuper+1], rows, parent[nsuper])."""
+        start = np.zeros(self.nsuper + 1, np.int32)
+        rowptr = np.zeros(self.nsuper + 1, np.int64)
+        rows = np.zeros(max(1, self.n_snrows), np.int32)
+        par = np.zeros(max(1, self.nsuper), np.int32)
+        _load().orc_sym_supernodes(self._h, start, rowptr, rows, par)
+        return start, rowptr, rows[: self.n_snrows], par[: self.nsuper]
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.orc_sym_free(self._h)
+            self._h = None
+
+
+class Factor:
+    """Cholesky of P(H~ + delta I + gamma J^T J)P^T on a Symbolic pattern."""
+
+    def __init__(self, sym: Symbolic, H_vals, J_vals, delta, gamma):
+        L = _load()
+        self.sym = sym
+        self.H_vals = _c(H_vals, np.float64)
+        self.J_vals = _c(J_vals, np.float64)
+        self.delta, self.gamma = float(delta), float(gamma)
+        st = C.c_int32(0)
+        self._h = L.orc_factor(sym._h, self.H_vals, self.J_vals, self.delta, self.gamma, C.byref(st))
+        self.status = int(st.value)           # 0 ok, 2 not SPD
+        self.fail_col = int(L.orc_fail_col(self._h))
+
+    @property
+    def ok(self):
+        return self.status == 0
+
+    def L_csc(self):
+        """L in CSC, final labels, diagonal first in each column."""
+        n, nnz = self.sym.n, self.sym.nnzL
+        Lp = np.zeros(n + 1, np.int64)
+        Li = np.zeros(nnz, np.int32)
+        Lx = np.zeros(nnz, np.float64)
+        _load().orc_get_L(self._h, Lp, Li, Lx)
+        return Lp, Li, Lx
+
+    def hsolve(self, b):
+        """H_delta^-1 b in the original labels."""
+        x = np.zeros(self.sym.n)
+        _load().orc_hsolve(self._h, _c(b, np.float64), x)
+        return x
+
+    def solve(self, r_x, r_y, *, delta2=1e-9, rtol=1e-12, maxit=1000, ir_maxit=0, ir_rtol=1e-8):
+        """Returns (dx, dy, info); info = dict(iters, rr, be, ir, delta2,
+        cg_status, inertia_ok, status)."""
+        n, m = self.sym.n, self.sym.m
+        dx = np.zeros(n)
+        dy = np.zeros(max(m, 1))
+        info = np.zeros(8)
+        ret = _load().orc_solve(self._h, self.H_vals, self.J_vals, self.delta, self.gamma,
+                                _c(r_x, np.float64), _c(r_y, np.float64),
+                                delta2, rtol, maxit, ir_maxit, ir_rtol, dx, dy, info)
+        return dx, dy[:m], dict(iters=int(info[0]), rr=float(info[1]), be=float(info[2]),
+                                ir=int(info[3]), delta2=float(info[4]), cg_status=int(info[5]),
+                                inertia_ok=bool(info[6]), status=int(ret))
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.orc_num_free(self._h)
+            self._h = None
+
+
+def residual(sym: Symbolic, H_vals, J_vals, delta, r_x, r_y, dx, dy):
+    """RR, BE, ||res||_2, ||K_delta||_inf of [dx;dy] for K_delta = [H~+delta I, J^T; J, 0]
+    (BE and RR as defined in Sec. 5.1, ||K||_2 estimated by ||K||_inf)."""
+    out = np.zeros(4)
+    _load().orc_residual(sym._h, _c(H_vals, np.float64), _c(J_vals, np.float64), float(delta),
+                         _c(r_x, np.float64), _c(r_y, np.float64),
+                         _c(dx, np.float64), _c(dy, np.float64), out)
+    return dict(rr=float(out[0]), be=float(out[1]), res=float(out[2]), knorm=float(out[3]))
+
+
+def solve_system(sys, *, ir_maxit=0, **kw):
+    """Analyse + factor + solve one workloads.KKTSystem; returns (sym, fac, dx, dy, info)."""
+    sym_kw = {k: v for k, v in kw.items() if k in ("relax_small", "relax_num", "relax_den", "wmax", "ordering")}
+    sol_kw = {k: v for k, v in kw.items() if k in ("delta2", "rtol", "maxit", "ir_rtol")}
+    sym = Symbolic(sys.n, sys.m, sys.H_colptr, sys.H_rowidx, sys.J_rowptr, sys.J_colidx, **sym_kw)
+    fac = Factor(sym, sys.H_vals, sys.J_vals, sys.delta, sys.gamma)
+    if not fac.ok:
+        return sym, fac, None, None, dict(status=2)
+    dx, dy, info = fac.solve(sys.r_x, sys.r_y, ir_maxit=ir_maxit, **sol_kw)
+    return sym, fac, dx, dy, info
+
+
+# --------------------------------------------------------------------------
+# 4x4 <-> 2x2 reduction (Sec. 3, eqs. linsys4x4 / linsys2x2), numpy + scipy
+# --------------------------------------------------------------------------
+def reduce4x4(p):
+    """From the parts of a 4x4 system (dict from workloads.random_4x4_parts)
+    form H~ = H + D_x + J_d^T D_s J_d (lower CSC, pattern = pat(H) U
+    pat(J_d^T J_d) U diag) and r_x = r~_x + J_d^T (D_s r_yd + r_s)."""
+    import scipy.sparse as sp
+    n = p["n_x"]
+    H = sp.csc_matrix((p["H_vals"], p["H_rowidx"], p["H_colptr"]), shape=(n, n))
+    Hfull = H + sp.tril(H, -1).T
+    Jd = sp.csr_matrix((p["Jd_vals"], p["Jd_colidx"], p["Jd_rowptr"]), shape=(p["m_d"], n))
+    Ht = Hfull + sp.diags(p["D_x"]) + (Jd.T @ sp.diags(p["D_s"]) @ Jd)
+    # structural pattern: H's entries, J_d^T J_d's entries and the diagonal
+    pat = (abs(Hfull) + abs(Jd.T) @ abs(Jd) + sp.eye(n)).tocsc()
+    low = sp.tril(pat).tocsc()
+    low.sort_indices()
+    Htd = Ht.toarray()
+    rows = low.indices.astype(np.int32)
+    cols = np.repeat(np.arange(n), np.diff(low.indptr))
+    vals = Htd[rows, cols]
+    r_x = p["r_xt"] + Jd.T @ (p["D_s"] * p["r_yd"] + p["r_s"])
+    return low.indptr.astype(np.int64), rows, vals, np.asarray(r_x)
+
+
+def recover4x4(p, dx):
+    """Delta s = J_d dx - r_yd, Delta y_d = D_s Delta s - r_s (Sec. 3)."""
+    import scipy.sparse as sp
+    Jd = sp.csr_matrix((p["Jd_vals"], p["Jd_colidx"], p["Jd_rowptr"]), shape=(p["m_d"], p["n_x"]))
+    ds = Jd @ dx - p["r_yd"]
+    dyd = p["D_s"] * ds - p["r_s"]
+    return ds, dyd

@@ -1,0 +1,942 @@
+/*
+ * kkt_oracle.c -- TEST INFRASTRUCTURE ONLY. Plain, slow, single-threaded FP64
+ * CPU restatement of the hybrid direct-iterative KKT method (Regev et al.,
+ * "A Hybrid Direct-Iterative Method for Solving KKT Linear Systems").
+ *
+ * Only tests/, the smoke check and bench.py's CPU-baseline leg may load this
+ * library. It shares no code, header, table or helper with the CUDA product
+ * path; the two are independent implementations of the same definitions, so
+ * agreement between them means something.
+ *
+ * What is here, and the passage each piece follows:
+ *   S1  pattern of H_gamma = pat(H~) U pat(J^T J) U diag          -- Sec. 4, eq. (gamma)
+ *   S2  approximate minimum degree ordering (Amestoy, Davis, Duff 1996,
+ *       SIAM J. Matrix Anal. Appl. 17(4)), with every tie pinned     -- Sec. 5.3 (AMD)
+ *   S3  elimination tree + postorder (children ascending)            -- Sec. 5.3; Sec. 2 (symbolic reuse)
+ *   S4  column counts of L (exact, from the symbolic column merge)
+ *   S5  fundamental + relaxed supernodes (pinned rule, parameters are inputs)
+ *   F   A = P (H~ + delta I + gamma J^T J) P^T and an up-looking
+ *       row-by-row sparse Cholesky L L^T = A; failure = first pivot <= 0
+ *       or non-finite                                                -- Sec. 4 eq. (gamma); Sec. 4.1; Algorithm 1
+ *   C   r^_x = r_x + gamma J^T r_y, w = H^-1 r^_x, CG on S = J H^-1 J^T
+ *       from 0 with the recurrence-residual stop, back-substitution  -- eqs. (Schur1), (Schur2); Algorithm 1
+ *       delta_2 restart on a small quadratic form                    -- Sec. 4.1; Algorithm 1
+ *   R   residual r = b - K_delta [dx;dy], RR and BE with ||K||_inf   -- Sec. 5.1 (BE, RR)
+ *
+ * Parity note: S2's exact order beyond the special cases checked by the
+ * tests (trees, cliques, hand-worked graphs, brute-force fill checks) is
+ * pinned only by agreement with the independent library implementation
+ * ("parity unpinned" for the tie-level details of S2).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------ */
+/* small dynamic int array                                              */
+/* ------------------------------------------------------------------ */
+typedef struct { int32_t *a; int64_t n, cap; } ivec;
+
+static void iv_push(ivec *v, int32_t x) {
+    if (v->n == v->cap) {
+        v->cap = v->cap ? 2 * v->cap : 4;
+        v->a = (int32_t *)realloc(v->a, (size_t)v->cap * sizeof(int32_t));
+    }
+    v->a[v->n++] = x;
+}
+static void iv_free(ivec *v) { free(v->a); v->a = NULL; v->n = v->cap = 0; }
+
+static int cmp_i32(const void *x, const void *y) {
+    int32_t a = *(const int32_t *)x, b = *(const int32_t *)y;
+    return (a > b) - (a < b);
+}
+
+/* ------------------------------------------------------------------ */
+/* S1: adjacency of pat(H~) U clique(J rows), off-diagonal, both halves  */
+/* ------------------------------------------------------------------ */
+/* CSR adjacency (sorted, de-duplicated, no diagonal). Returns 0 on success,
+ * 1 on invalid input (index out of range, entry above the diagonal in H). */
+static int build_adjacency(int64_t n, int64_t m, const int64_t *Hp, const int32_t *Hi,
+                           const int64_t *Jp, const int32_t *Ji,
+                           int64_t **adjp_out, int32_t **adji_out) {
+    ivec *nb = (ivec *)calloc((size_t)n, sizeof(ivec));
+    int bad = 0;
+    for (int64_t j = 0; j < n && !bad; j++) {
+        for (int64_t q = Hp[j]; q < Hp[j + 1]; q++) {
+            int32_t i = Hi[q];
+            if (i < j || i >= n) { bad = 1; break; }
+            if (i != j) { iv_push(&nb[i], (int32_t)j); iv_push(&nb[j], i); }
+        }
+    }
+    for (int64_t r = 0; r < m && !bad; r++) {
+        for (int64_t q1 = Jp[r]; q1 < Jp[r + 1]; q1++) {
+            int32_t a = Ji[q1];
+            if (a < 0 || a >= n) { bad = 1; break; }
+            for (int64_t q2 = Jp[r]; q2 < Jp[r + 1]; q2++)
+                if (Ji[q2] != a) iv_push(&nb[a], Ji[q2]);
+        }
+    }
+    if (bad) {
+        for (int64_t t = 0; t < n; t++) iv_free(&nb[t]);
+        free(nb);
+        return 1;
+    }
+    int64_t *adjp = (int64_t *)malloc((size_t)(n + 1) * sizeof(int64_t));
+    int64_t tot = 0;
+    for (int64_t i = 0; i < n; i++) {
+        qsort(nb[i].a, (size_t)nb[i].n, sizeof(int32_t), cmp_i32);
+        int64_t w = 0;
+        for (int64_t t = 0; t < nb[i].n; t++)
+            if (w == 0 || nb[i].a[w - 1] != nb[i].a[t]) nb[i].a[w++] = nb[i].a[t];
+        nb[i].n = w;
+        tot += w;
+    }
+    int32_t *adji = (int32_t *)malloc((size_t)(tot > 0 ? tot : 1) * sizeof(int32_t));
+    adjp[0] = 0;
+    for (int64_t i = 0; i < n; i++) {
+        if (nb[i].n) memcpy(adji + adjp[i], nb[i].a, (size_t)nb[i].n * sizeof(int32_t));
+        adjp[i + 1] = adjp[i] + nb[i].n;
+        iv_free(&nb[i]);
+    }
+    free(nb);
+    *adjp_out = adjp;
+    *adji_out = adji;
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* S2: approximate minimum degree on the quotient graph                 */
+/* ------------------------------------------------------------------ */
+/* binary min-heap of (degree, index) pairs with lazy deletion */
+typedef struct { int64_t key; int32_t idx; } hent;
+typedef struct { hent *h; int64_t n, cap; } heap;
+
+static int hless(hent a, hent b) { return a.key < b.key || (a.key == b.key && a.idx < b.idx); }
+static void hpush(heap *H, int64_t key, int32_t idx) {
+    if (H->n == H->cap) { H->cap = H->cap ? 2 * H->cap : 64; H->h = (hent *)realloc(H->h, (size_t)H->cap * sizeof(hent)); }
+    int64_t c = H->n++;
+    H->h[c].key = key; H->h[c].idx = idx;
+    while (c > 0) {
+        int64_t p = (c - 1) / 2;
+        if (!hless(H->h[c], H->h[p])) break;
+        hent t = H->h[c]; H->h[c] = H->h[p]; H->h[p] = t; c = p;
+    }
+}
+static hent hpop(heap *H) {
+    hent top = H->h[0];
+    H->h[0] = H->h[--H->n];
+    int64_t c = 0;
+    for (;;) {
+        int64_t l = 2 * c + 1, r = l + 1, s = c;
+        if (l < H->n && hless(H->h[l], H->h[s])) s = l;
+        if (r < H->n && hless(H->h[r], H->h[s])) s = r;
+        if (s == c) break;
+        hent t = H->h[c]; H->h[c] = H->h[s]; H->h[s] = t; c = s;
+    }
+    return top;
+}
+
+typedef struct { int64_t h; int32_t i; } hashent;
+static int cmp_hashent(const void *x, const void *y) {
+    const hashent *a = (const hashent *)x, *b = (const hashent *)y;
+    if (a->h != b->h) return (a->h > b->h) - (a->h < b->h);
+    return (a->i > b->i) - (a->i < b->i);
+}
+
+static int same_set(const ivec *x, const ivec *y, int32_t *t1, int32_t *t2) {
+    if (x->n != y->n) return 0;
+    if (x->n == 0) return 1;
+    memcpy(t1, x->a, (size_t)x->n * sizeof(int32_t));
+    memcpy(t2, y->a, (size_t)y->n * sizeof(int32_t));
+    qsort(t1, (size_t)x->n, sizeof(int32_t), cmp_i32);
+    qsort(t2, (size_t)y->n, sizeof(int32_t), cmp_i32);
+    return memcmp(t1, t2, (size_t)x->n * sizeof(int32_t)) == 0;
+}
+
+/*
+ * Pinned AMD (the specification both implementations follow):
+ *   state: supervariables (representative = smallest member index, weight =
+ *   member count), elements (eliminated supervariables) with variable lists
+ *   L_e, and for each variable i the variable adjacency A_i, the element
+ *   adjacency E_i and an approximate external degree d_i (initially |A_i|).
+ *   repeat while variables remain:
+ *     1. pivot p = variable minimising (d_p, p)
+ *     2. L_p = (A_p U union_{e in E_p} L_e) \ {p}
+ *     3. p's members (ascending) are appended to the order; nel += |p|
+ *     4. every e in E_p is absorbed; for i in L_p:
+ *          A_i <- A_i \ (L_p U {p});  E_i <- (E_i \ E_p) U {p}
+ *     5. p becomes element p with variable list L_p
+ *     6. for i in L_p (|X| = sum of weights of X), all with the state of 4-5:
+ *          d_i <- min( n - nel - |i|,  d_i + |L_p \ i|,
+ *                      |A_i| + |L_p \ i| + sum_{e in E_i, e != p} |L_e \ L_p| )
+ *     7. supervariables: i, j in L_p with A_i = A_j and E_i = E_j (exact
+ *        sets) merge into the smaller index r: |r| += |j|, d_r -= |j|, j is
+ *        removed everywhere
+ *   No aggressive absorption, no dense-row detection.
+ */
+static void amd_order(int64_t n, const int64_t *adjp, const int32_t *adji, int32_t *order) {
+    ivec *A = (ivec *)calloc((size_t)n, sizeof(ivec));
+    ivec *E = (ivec *)calloc((size_t)n, sizeof(ivec));
+    ivec *Le = (ivec *)calloc((size_t)n, sizeof(ivec));
+    int64_t *deg = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    int64_t *wt = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    int32_t *next_mem = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    int32_t *last_mem = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    char *alive = (char *)malloc((size_t)n);     /* uneliminated, unmerged variable */
+    char *iselem = (char *)calloc((size_t)n, 1); /* live element */
+    int64_t *mark = (int64_t *)calloc((size_t)n, sizeof(int64_t));
+    int64_t *estamp = (int64_t *)calloc((size_t)n, sizeof(int64_t));
+    int64_t *ew = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    int64_t *newdeg = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    int32_t *t1 = (int32_t *)malloc((size_t)(n + 1) * sizeof(int32_t));
+    int32_t *t2 = (int32_t *)malloc((size_t)(n + 1) * sizeof(int32_t));
+    int32_t *mem_tmp = (int32_t *)malloc((size_t)(n + 1) * sizeof(int32_t));
+    hashent *hl = (hashent *)malloc((size_t)(n + 1) * sizeof(hashent));
+    heap H = {0};
+    int64_t stamp = 0;
+
+    for (int64_t i = 0; i < n; i++) {
+        for (int64_t q = adjp[i]; q < adjp[i + 1]; q++) iv_push(&A[i], adji[q]);
+        deg[i] = A[i].n;
+        wt[i] = 1;
+        next_mem[i] = -1;
+        last_mem[i] = (int32_t)i;
+        alive[i] = 1;
+        hpush(&H, deg[i], (int32_t)i);
+    }
+    int64_t nel = 0, nout = 0;
+    while (nel < n) {
+        hent top = hpop(&H);
+        int32_t p = top.idx;
+        if (!alive[p] || deg[p] != top.key) continue;   /* stale heap entry */
+
+        /* 2. L_p */
+        ivec Lp = {0};
+        stamp++;
+        mark[p] = stamp;
+        for (int64_t t = 0; t < A[p].n; t++) {
+            int32_t v = A[p].a[t];
+            if (alive[v] && mark[v] != stamp) { mark[v] = stamp; iv_push(&Lp, v); }
+        }
+        for (int64_t t = 0; t < E[p].n; t++) {
+            int32_t e = E[p].a[t];
+            for (int64_t u = 0; u < Le[e].n; u++) {
+                int32_t v = Le[e].a[u];
+                if (alive[v] && mark[v] != stamp) { mark[v] = stamp; iv_push(&Lp, v); }
+            }
+        }
+        /* 3. output p's members ascending */
+        int64_t k = 0;
+        for (int32_t v = p; v >= 0; v = next_mem[v]) mem_tmp[k++] = v;
+        qsort(mem_tmp, (size_t)k, sizeof(int32_t), cmp_i32);
+        for (int64_t t = 0; t < k; t++) order[nout++] = mem_tmp[t];
+        nel += wt[p];
+        alive[p] = 0;
+        /* 4. absorb E_p, prune A_i, update E_i */
+        for (int64_t t = 0; t < E[p].n; t++) { int32_t e = E[p].a[t]; iselem[e] = 0; iv_free(&Le[e]); }
+        int64_t Lp_w = 0;
+        for (int64_t t = 0; t < Lp.n; t++) {
+            int32_t i = Lp.a[t];
+            Lp_w += wt[i];
+            int64_t w = 0;
+            for (int64_t u = 0; u < A[i].n; u++) {
+                int32_t v = A[i].a[u];
+                if (mark[v] != stamp) A[i].a[w++] = v;   /* drop L_p members and p */
+            }
+            A[i].n = w;
+            w = 0;
+            for (int64_t u = 0; u < E[i].n; u++) {
+                int32_t e = E[i].a[u];
+                if (iselem[e]) E[i].a[w++] = e;
+            }
+            E[i].n = w;
+            iv_push(&E[i], p);
+        }
+        iv_free(&A[p]);
+        iv_free(&E[p]);
+        /* 5. element p */
+        Le[p] = Lp;
+        iselem[p] = 1;
+        /* 6. approximate degrees */
+        for (int64_t t = 0; t < Lp.n; t++) {
+            int32_t i = Lp.a[t];
+            int64_t a = 0, c = 0;
+            for (int64_t u = 0; u < A[i].n; u++) a += wt[A[i].a[u]];
+            for (int64_t u = 0; u < E[i].n; u++) {
+                int32_t e = E[i].a[u];
+                if (e == p) continue;
+                if (estamp[e] != stamp) {
+                    /* |L_e \ L_p|, compacting merged variables away */
+                    int64_t s = 0, w = 0;
+                    for (int64_t z = 0; z < Le[e].n; z++) {
+                        int32_t v = Le[e].a[z];
+                        if (!alive[v]) continue;
+                        Le[e].a[w++] = v;
+                        if (mark[v] != stamp) s += wt[v];
+                    }
+                    Le[e].n = w;
+                    ew[e] = s;
+                    estamp[e] = stamp;
+                }
+                c += ew[e];
+            }
+            int64_t b = Lp_w - wt[i];
+            int64_t d1 = n - nel - wt[i];
+            int64_t d2 = deg[i] + b;
+            int64_t d3 = a + b + c;
+            int64_t d = d1 < d2 ? d1 : d2;
+            if (d3 < d) d = d3;
+            newdeg[i] = d;
+        }
+        for (int64_t t = 0; t < Lp.n; t++) deg[Lp.a[t]] = newdeg[Lp.a[t]];
+        /* 7. supervariable detection (the hash only filters; the exact set
+         *    comparison decides) */
+        for (int64_t t = 0; t < Lp.n; t++) {
+            int32_t i = Lp.a[t];
+            int64_t h = 0;
+            for (int64_t u = 0; u < A[i].n; u++) h += A[i].a[u];
+            for (int64_t u = 0; u < E[i].n; u++) h += (int64_t)E[i].a[u] * 7919 + 13;
+            h += 1000003LL * (A[i].n + 31 * E[i].n);
+            hl[t].h = h;
+            hl[t].i = i;
+        }
+        qsort(hl, (size_t)Lp.n, sizeof(hashent), cmp_hashent);
+        for (int64_t s0 = 0; s0 < Lp.n;) {
+            int64_t s1 = s0;
+            while (s1 < Lp.n && hl[s1].h == hl[s0].h) s1++;
+            for (int64_t x = s0; x < s1; x++) {
+                int32_t i = hl[x].i;
+                if (!alive[i]) continue;
+                for (int64_t y = x + 1; y < s1; y++) {
+                    int32_t j = hl[y].i;
+                    if (!alive[j]) continue;
+                    if (!same_set(&A[i], &A[j], t1, t2)) continue;
+                    if (!same_set(&E[i], &E[j], t1, t2)) continue;
+                    /* merge j into i (i < j: the run is sorted by index) */
+                    wt[i] += wt[j];
+                    deg[i] -= wt[j];
+                    next_mem[last_mem[i]] = j;
+                    last_mem[i] = last_mem[j];
+                    alive[j] = 0;
+                    for (int64_t u = 0; u < A[j].n; u++) {
+                        int32_t kk = A[j].a[u];
+                        int64_t w = 0;
+                        for (int64_t z = 0; z < A[kk].n; z++)
+                            if (A[kk].a[z] != j) A[kk].a[w++] = A[kk].a[z];
+                        A[kk].n = w;
+                    }
+                    iv_free(&A[j]);
+                    iv_free(&E[j]);
+                }
+            }
+            s0 = s1;
+        }
+        for (int64_t t = 0; t < Lp.n; t++) {
+            int32_t i = Lp.a[t];
+            if (alive[i]) hpush(&H, deg[i], i);
+        }
+    }
+    for (int64_t i = 0; i < n; i++) { iv_free(&A[i]); iv_free(&E[i]); iv_free(&Le[i]); }
+    free(A); free(E); free(Le); free(deg); free(wt); free(next_mem); free(last_mem);
+    free(alive); free(iselem); free(mark); free(estamp); free(ew); free(newdeg);
+    free(t1); free(t2); free(mem_tmp); free(hl); free(H.h);
+}
+
+/* ------------------------------------------------------------------ */
+/* S3/S4: symbolic column merge on a given order                        */
+/* ------------------------------------------------------------------ */
+/* For B = P A P^T (perm[k] = original index at position k): the structure of
+ * column j of L is the below-diagonal pattern of B(:,j) united with the
+ * structures of the children of j, minus j itself; parent(j) = its smallest
+ * entry (George & Liu). Outputs parent[] and the full strictly-lower pattern
+ * of L by columns (Lp/Li, rows ascending). */
+static void symbolic_merge(int64_t n, const int64_t *adjp, const int32_t *adji,
+                           const int32_t *perm, int32_t *parent,
+                           int64_t **Lp_out, int32_t **Li_out) {
+    int32_t *iperm = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    for (int64_t k = 0; k < n; k++) iperm[perm[k]] = (int32_t)k;
+    ivec *col = (ivec *)calloc((size_t)n, sizeof(ivec));
+    ivec *kids = (ivec *)calloc((size_t)n, sizeof(ivec));
+    int64_t *mark = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    for (int64_t i = 0; i < n; i++) mark[i] = -1;
+    for (int64_t j = 0; j < n; j++) {
+        int32_t orig = perm[j];
+        mark[j] = j;
+        for (int64_t q = adjp[orig]; q < adjp[orig + 1]; q++) {
+            int32_t r = iperm[adji[q]];
+            if (r > j && mark[r] != j) { mark[r] = j; iv_push(&col[j], r); }
+        }
+        for (int64_t t = 0; t < kids[j].n; t++) {
+            int32_t c = kids[j].a[t];
+            for (int64_t u = 0; u < col[c].n; u++) {
+                int32_t r = col[c].a[u];
+                if (r > j && mark[r] != j) { mark[r] = j; iv_push(&col[j], r); }
+            }
+        }
+        qsort(col[j].a, (size_t)col[j].n, sizeof(int32_t), cmp_i32);
+        parent[j] = col[j].n ? col[j].a[0] : -1;
+        if (parent[j] >= 0) iv_push(&kids[parent[j]], (int32_t)j);
+    }
+    int64_t *Lp = (int64_t *)malloc((size_t)(n + 1) * sizeof(int64_t));
+    Lp[0] = 0;
+    for (int64_t j = 0; j < n; j++) Lp[j + 1] = Lp[j] + col[j].n;
+    int32_t *Li = (int32_t *)malloc((size_t)(Lp[n] > 0 ? Lp[n] : 1) * sizeof(int32_t));
+    for (int64_t j = 0; j < n; j++) {
+        if (col[j].n) memcpy(Li + Lp[j], col[j].a, (size_t)col[j].n * sizeof(int32_t));
+        iv_free(&col[j]);
+        iv_free(&kids[j]);
+    }
+    free(col); free(kids); free(mark); free(iperm);
+    *Lp_out = Lp;
+    *Li_out = Li;
+}
+
+/* depth-first postorder; children visited in ascending index, roots ascending */
+static void postorder(int64_t n, const int32_t *parent, int32_t *post) {
+    ivec *kids = (ivec *)calloc((size_t)n, sizeof(ivec));
+    for (int64_t j = 0; j < n; j++)
+        if (parent[j] >= 0) iv_push(&kids[parent[j]], (int32_t)j);  /* ascending by construction */
+    int32_t *stk = (int32_t *)malloc((size_t)(n + 1) * sizeof(int32_t));
+    int64_t *pos = (int64_t *)calloc((size_t)n, sizeof(int64_t));
+    int64_t k = 0;
+    for (int64_t r = 0; r < n; r++) {
+        if (parent[r] >= 0) continue;
+        int64_t top = 0;
+        stk[top++] = (int32_t)r;
+        while (top) {
+            int32_t v = stk[top - 1];
+            if (pos[v] < kids[v].n) {
+                stk[top++] = kids[v].a[pos[v]++];
+            } else {
+                post[k++] = v;
+                top--;
+            }
+        }
+    }
+    for (int64_t j = 0; j < n; j++) iv_free(&kids[j]);
+    free(kids); free(stk); free(pos);
+}
+
+/* ------------------------------------------------------------------ */
+/* symbolic object                                                      */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int64_t n, m;
+    int64_t *Hp; int32_t *Hi;       /* copies of the input patterns */
+    int64_t *Jp; int32_t *Ji;
+    int32_t *amd;                   /* raw S2 order */
+    int32_t *perm, *iperm;          /* final: perm[k] = original index at k */
+    int32_t *parent;                /* etree in final labels */
+    int64_t *Lp; int32_t *Li;       /* strictly lower pattern of L, final labels */
+    int64_t *cc;                    /* column counts incl. diagonal */
+    int64_t nsuper;
+    int32_t *sn_start;              /* [nsuper+1] first column of each supernode */
+    int64_t *sn_rowptr;             /* [nsuper+1] */
+    int32_t *sn_rows;               /* rows of each supernode (its columns first), ascending */
+    int32_t *sn_parent;
+    double flops;                   /* sum_j c_j^2 */
+} orc_sym;
+
+int64_t orc_version(void) { return 1; }
+
+orc_sym *orc_analyse(int64_t n, int64_t m, const int64_t *Hp, const int32_t *Hi,
+                     const int64_t *Jp, const int32_t *Ji,
+                     int32_t relax_small, int32_t relax_num, int32_t relax_den,
+                     int32_t wmax, int32_t ordering, int32_t *status) {
+    *status = 0;
+    if (n <= 0 || m < 0) { *status = 1; return NULL; }
+    int64_t *adjp; int32_t *adji;
+    if (build_adjacency(n, m, Hp, Hi, Jp, Ji, &adjp, &adji)) { *status = 1; return NULL; }
+    orc_sym *S = (orc_sym *)calloc(1, sizeof(orc_sym));
+    S->n = n; S->m = m;
+    S->Hp = (int64_t *)malloc((size_t)(n + 1) * sizeof(int64_t));
+    S->Hi = (int32_t *)malloc((size_t)(Hp[n] > 0 ? Hp[n] : 1) * sizeof(int32_t));
+    S->Jp = (int64_t *)malloc((size_t)(m + 1) * sizeof(int64_t));
+    S->Ji = (int32_t *)malloc((size_t)(Jp[m] > 0 ? Jp[m] : 1) * sizeof(int32_t));
+    memcpy(S->Hp, Hp, (size_t)(n + 1) * sizeof(int64_t));
+    if (Hp[n]) memcpy(S->Hi, Hi, (size_t)Hp[n] * sizeof(int32_t));
+    memcpy(S->Jp, Jp, (size_t)(m + 1) * sizeof(int64_t));
+    if (Jp[m]) memcpy(S->Ji, Ji, (size_t)Jp[m] * sizeof(int32_t));
+    S->amd = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    if (ordering == 0) amd_order(n, adjp, adji, S->amd);
+    else for (int64_t i = 0; i < n; i++) S->amd[i] = (int32_t)i;   /* natural */
+
+    /* S3: etree on the AMD order, postorder, final permutation */
+    int32_t *par0 = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    int64_t *Lp0; int32_t *Li0;
+    symbolic_merge(n, adjp, adji, S->amd, par0, &Lp0, &Li0);
+    free(Lp0); free(Li0);
+    int32_t *post = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    postorder(n, par0, post);
+    S->perm = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    S->iperm = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    for (int64_t k = 0; k < n; k++) S->perm[k] = S->amd[post[k]];
+    for (int64_t k = 0; k < n; k++) S->iperm[S->perm[k]] = (int32_t)k;
+    free(par0); free(post);
+    /* S3/S4 recomputed in final labels */
+    S->parent = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    symbolic_merge(n, adjp, adji, S->perm, S->parent, &S->Lp, &S->Li);
+    S->cc = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    S->flops = 0;
+    for (int64_t j = 0; j < n; j++) {
+        S->cc[j] = S->Lp[j + 1] - S->Lp[j] + 1;
+        S->flops += (double)S->cc[j] * (double)S->cc[j];
+    }
+    free(adjp); free(adji);
+
+    /* S5: fundamental supernodes: j joins j-1's supernode iff parent(j-1)=j,
+     * j has exactly one child, and cc(j-1) = cc(j) + 1 */
+    int32_t *nkids = (int32_t *)calloc((size_t)n, sizeof(int32_t));
+    for (int64_t j = 0; j < n; j++) if (S->parent[j] >= 0) nkids[S->parent[j]]++;
+    int32_t *fstart = (int32_t *)malloc((size_t)(n + 1) * sizeof(int32_t));
+    int64_t nf = 0;
+    for (int64_t j = 0; j < n; j++) {
+        int join = j > 0 && S->parent[j - 1] == j && nkids[j] == 1 && S->cc[j - 1] == S->cc[j] + 1;
+        if (!join) fstart[nf++] = (int32_t)j;
+    }
+    fstart[nf] = (int32_t)n;
+    free(nkids);
+    /* relaxation, one pass in column order: the relaxed supernode t that
+     * ends just before fundamental supernode p merges with p when t's parent
+     * column is p's first column, the merged width W <= wmax, and either
+     * W <= relax_small or the added explicit zeros z satisfy
+     * z * relax_den <= relax_num * panel, panel = W(W+1)/2 + W * rows_below(p) */
+    int32_t *rf = (int32_t *)malloc((size_t)(nf + 1) * sizeof(int32_t));
+    int32_t *rl = (int32_t *)malloc((size_t)(nf + 1) * sizeof(int32_t));
+    int64_t *rtrue = (int64_t *)malloc((size_t)(nf + 1) * sizeof(int64_t));
+    int64_t nr = 0;
+    for (int64_t s = 0; s < nf; s++) {
+        int32_t f = fstart[s], l = fstart[s + 1] - 1;
+        int64_t tru = 0;
+        for (int32_t j = f; j <= l; j++) tru += S->cc[j];
+        int merged = 0;
+        if (nr > 0 && rl[nr - 1] == f - 1 && S->parent[rl[nr - 1]] == f) {
+            int64_t W = (int64_t)l - rf[nr - 1] + 1;
+            int64_t Rb = S->cc[l] - 1;                 /* rows strictly below the last column */
+            int64_t panel = W * (W + 1) / 2 + W * Rb;
+            int64_t ttot = rtrue[nr - 1] + tru;
+            int64_t z = panel - ttot;
+            if (W <= wmax && (W <= relax_small || z * (int64_t)relax_den <= (int64_t)relax_num * panel)) {
+                rl[nr - 1] = l;
+                rtrue[nr - 1] = ttot;
+                merged = 1;
+            }
+        }
+        if (!merged) { rf[nr] = f; rl[nr] = l; rtrue[nr] = tru; nr++; }
+    }
+    free(fstart);
+    S->nsuper = nr;
+    S->sn_start = (int32_t *)malloc((size_t)(nr + 1) * sizeof(int32_t));
+    S->sn_rowptr = (int64_t *)malloc((size_t)(nr + 1) * sizeof(int64_t));
+    S->sn_parent = (int32_t *)malloc((size_t)(nr > 0 ? nr : 1) * sizeof(int32_t));
+    int32_t *col2sn = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    S->sn_rowptr[0] = 0;
+    for (int64_t s = 0; s < nr; s++) {
+        S->sn_start[s] = rf[s];
+        for (int32_t j = rf[s]; j <= rl[s]; j++) col2sn[j] = (int32_t)s;
+        int64_t W = (int64_t)rl[s] - rf[s] + 1;
+        S->sn_rowptr[s + 1] = S->sn_rowptr[s] + W + (S->cc[rl[s]] - 1);
+    }
+    S->sn_start[nr] = (int32_t)n;
+    S->sn_rows = (int32_t *)malloc((size_t)(S->sn_rowptr[nr] > 0 ? S->sn_rowptr[nr] : 1) * sizeof(int32_t));
+    for (int64_t s = 0; s < nr; s++) {
+        int64_t q = S->sn_rowptr[s];
+        for (int32_t j = rf[s]; j <= rl[s]; j++) S->sn_rows[q++] = j;
+        int32_t l = rl[s];
+        for (int64_t u = S->Lp[l]; u < S->Lp[l + 1]; u++) S->sn_rows[q++] = S->Li[u];
+        S->sn_parent[s] = S->parent[l] >= 0 ? col2sn[S->parent[l]] : -1;
+    }
+    free(col2sn); free(rf); free(rl); free(rtrue);
+    return S;
+}
+
+void orc_sym_info(const orc_sym *S, int64_t *out) {
+    out[0] = S->n;
+    out[1] = S->nsuper;
+    out[2] = S->Lp[S->n] + S->n;          /* nnz(L) incl. diagonal */
+    out[3] = S->sn_rowptr[S->nsuper];     /* total supernode rows */
+    int64_t panel = 0;
+    for (int64_t s = 0; s < S->nsuper; s++) {
+        int64_t W = S->sn_start[s + 1] - S->sn_start[s];
+        panel += W * (S->sn_rowptr[s + 1] - S->sn_rowptr[s]);
+    }
+    out[4] = panel;                       /* rectangular panel storage entries */
+}
+double orc_sym_flops(const orc_sym *S) { return S->flops; }
+void orc_sym_amd(const orc_sym *S, int32_t *o) { memcpy(o, S->amd, (size_t)S->n * sizeof(int32_t)); }
+void orc_sym_perm(const orc_sym *S, int32_t *o) { memcpy(o, S->perm, (size_t)S->n * sizeof(int32_t)); }
+void orc_sym_parent(const orc_sym *S, int32_t *o) { memcpy(o, S->parent, (size_t)S->n * sizeof(int32_t)); }
+void orc_sym_colcount(const orc_sym *S, int64_t *o) { memcpy(o, S->cc, (size_t)S->n * sizeof(int64_t)); }
+void orc_sym_lpattern(const orc_sym *S, int64_t *Lp, int32_t *Li) {
+    memcpy(Lp, S->Lp, (size_t)(S->n + 1) * sizeof(int64_t));
+    if (S->Lp[S->n]) memcpy(Li, S->Li, (size_t)S->Lp[S->n] * sizeof(int32_t));
+}
+void orc_sym_supernodes(const orc_sym *S, int32_t *start, int64_t *rowptr, int32_t *rows, int32_t *sparent) {
+    memcpy(start, S->sn_start, (size_t)(S->nsuper + 1) * sizeof(int32_t));
+    memcpy(rowptr, S->sn_rowptr, (size_t)(S->nsuper + 1) * sizeof(int64_t));
+    memcpy(rows, S->sn_rows, (size_t)S->sn_rowptr[S->nsuper] * sizeof(int32_t));
+    memcpy(sparent, S->sn_parent, (size_t)S->nsuper * sizeof(int32_t));
+}
+
+void orc_sym_free(orc_sym *S) {
+    if (!S) return;
+    free(S->Hp); free(S->Hi); free(S->Jp); free(S->Ji);
+    free(S->amd); free(S->perm); free(S->iperm); free(S->parent); free(S->Lp); free(S->Li);
+    free(S->cc); free(S->sn_start); free(S->sn_rowptr); free(S->sn_rows); free(S->sn_parent);
+    free(S);
+}
+
+/* ------------------------------------------------------------------ */
+/* F: assembly of A = P(H~ + delta I + gamma J^T J)P^T and Cholesky     */
+/* ------------------------------------------------------------------ */
+typedef struct { int32_t r, c; double v; int64_t pos; } trip;
+/* column, then row, then generation order: duplicates are summed in the
+ * order they were generated */
+static int cmp_trip(const void *x, const void *y) {
+    const trip *a = (const trip *)x, *b = (const trip *)y;
+    if (a->c != b->c) return (a->c > b->c) - (a->c < b->c);
+    if (a->r != b->r) return (a->r > b->r) - (a->r < b->r);
+    return (a->pos > b->pos) - (a->pos < b->pos);
+}
+
+typedef struct {
+    const orc_sym *S;
+    int64_t n;
+    int64_t *Up; int32_t *Ui; double *Ux;   /* upper triangle of A by columns (row <= col) */
+    double *Lx;                              /* values on S->Lp pattern (strictly lower) */
+    double *Ld;                              /* diagonal of L */
+    int status;                              /* 0 ok, 2 not SPD */
+    int64_t fail_col;
+} orc_num;
+
+/* Upper triangle of A column by column: H~ entries in input order, then
+ * delta on the diagonal, then gamma*J_ra*J_rb for each pair of each row. */
+static void assemble(const orc_sym *S, const double *Hv, const double *Jv, double delta,
+                     double gamma, orc_num *N) {
+    int64_t n = S->n, m = S->m;
+    int64_t nt = S->Hp[n] + n;
+    for (int64_t r = 0; r < m; r++) {
+        int64_t k = S->Jp[r + 1] - S->Jp[r];
+        nt += k * (k + 1) / 2;
+    }
+    trip *T = (trip *)malloc((size_t)(nt > 0 ? nt : 1) * sizeof(trip));
+    int64_t t = 0;
+    for (int64_t j = 0; j < n; j++)
+        for (int64_t q = S->Hp[j]; q < S->Hp[j + 1]; q++) {
+            int32_t a = S->iperm[S->Hi[q]], b = S->iperm[j];
+            T[t].r = a < b ? a : b; T[t].c = a < b ? b : a; T[t].v = Hv[q]; t++;
+        }
+    for (int64_t j = 0; j < n; j++) { T[t].r = S->iperm[j]; T[t].c = S->iperm[j]; T[t].v = delta; t++; }
+    for (int64_t r = 0; r < m; r++)
+        for (int64_t q1 = S->Jp[r]; q1 < S->Jp[r + 1]; q1++)
+            for (int64_t q2 = q1; q2 < S->Jp[r + 1]; q2++) {
+                int32_t a = S->iperm[S->Ji[q1]], b = S->iperm[S->Ji[q2]];
+                T[t].r = a < b ? a : b; T[t].c = a < b ? b : a;
+                T[t].v = gamma * Jv[q1] * Jv[q2]; t++;
+            }
+    for (int64_t i = 0; i < nt; i++) T[i].pos = i;
+    qsort(T, (size_t)nt, sizeof(trip), cmp_trip);
+    N->Up = (int64_t *)calloc((size_t)(n + 1), sizeof(int64_t));
+    N->Ui = (int32_t *)malloc((size_t)(nt > 0 ? nt : 1) * sizeof(int32_t));
+    N->Ux = (double *)malloc((size_t)(nt > 0 ? nt : 1) * sizeof(double));
+    int64_t w = 0;
+    for (int64_t i = 0; i < nt; i++) {
+        if (i > 0 && T[i - 1].c == T[i].c && T[i - 1].r == T[i].r) {
+            N->Ux[w - 1] += T[i].v;
+        } else {
+            N->Ui[w] = T[i].r; N->Ux[w] = T[i].v; N->Up[T[i].c + 1]++; w++;
+        }
+    }
+    for (int64_t j = 0; j < n; j++) N->Up[j + 1] += N->Up[j];
+    free(T);
+}
+
+/* Up-looking Cholesky: row k of L solves L(0:k,0:k) l = A(0:k,k), then
+ * L_kk = sqrt(A_kk - l.l). Row patterns come from the symbolic column
+ * patterns (transposed). Columns of L fill in increasing row order. */
+orc_num *orc_factor(const orc_sym *S, const double *Hv, const double *Jv, double delta,
+                    double gamma, int32_t *status) {
+    int64_t n = S->n;
+    orc_num *N = (orc_num *)calloc(1, sizeof(orc_num));
+    N->S = S; N->n = n;
+    assemble(S, Hv, Jv, delta, gamma, N);
+    int64_t nnz = S->Lp[n];
+    N->Lx = (double *)calloc((size_t)(nnz > 0 ? nnz : 1), sizeof(double));
+    N->Ld = (double *)calloc((size_t)n, sizeof(double));
+    /* row patterns of L: row k -> columns i < k with L_ki != 0 (ascending i) */
+    int64_t *Rp = (int64_t *)calloc((size_t)(n + 1), sizeof(int64_t));
+    for (int64_t q = 0; q < nnz; q++) Rp[S->Li[q] + 1]++;
+    for (int64_t k = 0; k < n; k++) Rp[k + 1] += Rp[k];
+    int32_t *Ri = (int32_t *)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(int32_t));
+    int64_t *fill = (int64_t *)malloc((size_t)(n + 1) * sizeof(int64_t));
+    memcpy(fill, Rp, (size_t)(n + 1) * sizeof(int64_t));
+    for (int64_t j = 0; j < n; j++)
+        for (int64_t q = S->Lp[j]; q < S->Lp[j + 1]; q++) Ri[fill[S->Li[q]]++] = (int32_t)j;
+    int64_t *cpos = (int64_t *)malloc((size_t)n * sizeof(int64_t));  /* next slot per column */
+    for (int64_t j = 0; j < n; j++) cpos[j] = S->Lp[j];
+    double *x = (double *)calloc((size_t)n, sizeof(double));
+    N->status = 0; N->fail_col = -1;
+    for (int64_t k = 0; k < n; k++) {
+        double d = 0.0;
+        for (int64_t q = N->Up[k]; q < N->Up[k + 1]; q++) {
+            if (N->Ui[q] == k) d += N->Ux[q];
+            else x[N->Ui[q]] += N->Ux[q];
+        }
+        for (int64_t t = Rp[k]; t < Rp[k + 1]; t++) {
+            int32_t i = Ri[t];
+            double lki = x[i] / N->Ld[i];
+            x[i] = 0.0;
+            for (int64_t q = S->Lp[i]; q < cpos[i]; q++) x[S->Li[q]] -= N->Lx[q] * lki;
+            d -= lki * lki;
+            N->Lx[cpos[i]++] = lki;
+        }
+        if (!(d > 0.0) || !isfinite(d)) {
+            N->status = 2; N->fail_col = k;
+            break;
+        }
+        N->Ld[k] = sqrt(d);
+    }
+    free(Rp); free(Ri); free(fill); free(cpos); free(x);
+    *status = N->status;
+    return N;
+}
+
+int64_t orc_fail_col(const orc_num *N) { return N->fail_col; }
+
+/* L in CSC (diagonal first in each column), final labels */
+void orc_get_L(const orc_num *N, int64_t *Lp, int32_t *Li, double *Lx) {
+    const orc_sym *S = N->S;
+    int64_t n = S->n, w = 0;
+    for (int64_t j = 0; j < n; j++) {
+        Lp[j] = w;
+        Li[w] = (int32_t)j; Lx[w] = N->Ld[j]; w++;
+        for (int64_t q = S->Lp[j]; q < S->Lp[j + 1]; q++) { Li[w] = S->Li[q]; Lx[w] = N->Lx[q]; w++; }
+    }
+    Lp[n] = w;
+}
+
+/* x = H_delta^{-1} b in the original labels: y = P b, L z = y, L^T y = z, x = P^T y */
+static void hsolve(const orc_num *N, const double *b, double *x, double *tmp) {
+    const orc_sym *S = N->S;
+    int64_t n = S->n;
+    for (int64_t k = 0; k < n; k++) tmp[k] = b[S->perm[k]];
+    for (int64_t j = 0; j < n; j++) {
+        tmp[j] /= N->Ld[j];
+        double v = tmp[j];
+        for (int64_t q = S->Lp[j]; q < S->Lp[j + 1]; q++) tmp[S->Li[q]] -= N->Lx[q] * v;
+    }
+    for (int64_t j = n - 1; j >= 0; j--) {
+        double s = tmp[j];
+        for (int64_t q = S->Lp[j]; q < S->Lp[j + 1]; q++) s -= N->Lx[q] * tmp[S->Li[q]];
+        tmp[j] = s / N->Ld[j];
+    }
+    for (int64_t k = 0; k < n; k++) x[S->perm[k]] = tmp[k];
+}
+
+void orc_hsolve(const orc_num *N, const double *b, double *x) {
+    double *tmp = (double *)malloc((size_t)N->n * sizeof(double));
+    hsolve(N, b, x, tmp);
+    free(tmp);
+}
+
+/* J x (m) and J^T y (n) */
+static void jmul(const orc_sym *S, const double *Jv, const double *x, double *y) {
+    for (int64_t r = 0; r < S->m; r++) {
+        double s = 0.0;
+        for (int64_t q = S->Jp[r]; q < S->Jp[r + 1]; q++) s += Jv[q] * x[S->Ji[q]];
+        y[r] = s;
+    }
+}
+static void jtmul(const orc_sym *S, const double *Jv, const double *y, double *x) {
+    for (int64_t i = 0; i < S->n; i++) x[i] = 0.0;
+    for (int64_t r = 0; r < S->m; r++)
+        for (int64_t q = S->Jp[r]; q < S->Jp[r + 1]; q++) x[S->Ji[q]] += Jv[q] * y[r];
+}
+static double dot(const double *a, const double *b, int64_t k) {
+    double s = 0.0;
+    for (int64_t i = 0; i < k; i++) s += a[i] * b[i];
+    return s;
+}
+
+/*
+ * CG on (S + d2 I) y = bS, S = J H^-1 J^T: x0 = 0, stop when the recurrence
+ * residual satisfies ||r|| <= rtol ||bS||. Breakdown: p^T q <= 0, or
+ * p^T q <= 1e-12 * rho_max * p^T p with rho_max the largest Rayleigh
+ * quotient p^T q / p^T p met so far in this run (the current one included).
+ * Returns 0 converged, 3 breakdown, 4 max iterations. *iters = number of
+ * products with S.
+ */
+static int cg_schur(const orc_num *N, const double *Jv, const double *bS, double d2, double rtol,
+                    int32_t maxit, double *y, int32_t *iters, double *wn, double *wn2, double *tmp) {
+    const orc_sym *S = N->S;
+    int64_t m = S->m;
+    double *r = (double *)malloc((size_t)(m + 1) * sizeof(double));
+    double *p = (double *)malloc((size_t)(m + 1) * sizeof(double));
+    double *q = (double *)malloc((size_t)(m + 1) * sizeof(double));
+    for (int64_t i = 0; i < m; i++) { y[i] = 0.0; r[i] = bS[i]; p[i] = bS[i]; }
+    double bnorm = sqrt(dot(bS, bS, m));
+    double rho = dot(r, r, m);
+    double rq_max = 0.0;
+    int st = 4;
+    int32_t it = 0;
+    for (;;) {
+        if (sqrt(rho) <= rtol * bnorm) { st = 0; break; }
+        if (it >= maxit) { st = 4; break; }
+        jtmul(S, Jv, p, wn);
+        hsolve(N, wn, wn2, tmp);
+        jmul(S, Jv, wn2, q);
+        for (int64_t i = 0; i < m; i++) q[i] += d2 * p[i];
+        it++;
+        double pq = dot(p, q, m), pp = dot(p, p, m);
+        if (!(pq > 0.0)) { st = 3; break; }
+        double rq = pq / pp;
+        if (rq > rq_max) rq_max = rq;
+        if (rq <= 1e-12 * rq_max) { st = 3; break; }
+        double alpha = rho / pq;
+        for (int64_t i = 0; i < m; i++) { y[i] += alpha * p[i]; r[i] -= alpha * q[i]; }
+        double rho2 = dot(r, r, m);
+        double beta = rho2 / rho;
+        for (int64_t i = 0; i < m; i++) p[i] = r[i] + beta * p[i];
+        rho = rho2;
+    }
+    *iters = it;
+    free(r); free(p); free(q);
+    return st;
+}
+
+/* residual of K_delta = [H~ + delta I, J^T; J, 0]: res = b - K [dx; dy];
+ * also ||K_delta||_inf (largest absolute row sum) */
+static void kkt_residual(const orc_sym *S, const double *Hv, const double *Jv, double delta,
+                         const double *rx, const double *ry, const double *dx, const double *dy,
+                         double *res_x, double *res_y, double *knorm_inf) {
+    int64_t n = S->n, m = S->m;
+    double *rowabs = (double *)calloc((size_t)(n + m), sizeof(double));
+    for (int64_t i = 0; i < n; i++) { res_x[i] = rx[i] - delta * dx[i]; rowabs[i] += fabs(delta); }
+    for (int64_t j = 0; j < n; j++)
+        for (int64_t q = S->Hp[j]; q < S->Hp[j + 1]; q++) {
+            int32_t i = S->Hi[q];
+            res_x[i] -= Hv[q] * dx[j];
+            rowabs[i] += fabs(Hv[q]);
+            if (i != j) { res_x[j] -= Hv[q] * dx[i]; rowabs[j] += fabs(Hv[q]); }
+        }
+    for (int64_t r = 0; r < m; r++) {
+        double s = 0.0;
+        for (int64_t q = S->Jp[r]; q < S->Jp[r + 1]; q++) {
+            int32_t c = S->Ji[q];
+            s += Jv[q] * dx[c];
+            res_x[c] -= Jv[q] * dy[r];
+            rowabs[n + r] += fabs(Jv[q]);
+            rowabs[c] += fabs(Jv[q]);
+        }
+        res_y[r] = ry[r] - s;
+    }
+    double mx = 0.0;
+    for (int64_t i = 0; i < n + m; i++) if (rowabs[i] > mx) mx = rowabs[i];
+    *knorm_inf = mx;
+    free(rowabs);
+}
+
+/*
+ * Full solve (Algorithm 1 solve steps; eqs. Schur1/Schur2):
+ *   r^_x = r_x + gamma J^T r_y; w = H^-1 r^_x; bS = J w - r_y;
+ *   CG on S dy = bS (restart once with delta2 on breakdown);
+ *   dx = H^-1 (r^_x - J^T dy).
+ * Optional iterative refinement on K_delta (up to ir_maxit corrections while
+ * RR > ir_rtol): the same steps solve K c = residual, then [dx;dy] += c.
+ * info[0] CG iterations (all runs), [1] RR, [2] BE, [3] IR steps taken,
+ * [4] delta2 used, [5] CG status of the last run, [6] inertia flag.
+ * Returns 0, or the CG status (3 breakdown even after restart, 4 maxit).
+ */
+int32_t orc_solve(const orc_num *N, const double *Hv, const double *Jv, double delta,
+                  double gamma, const double *rx, const double *ry, double delta2,
+                  double rtol, int32_t maxit, int32_t ir_maxit, double ir_rtol,
+                  double *dx, double *dy, double *info) {
+    const orc_sym *S = N->S;
+    int64_t n = S->n, m = S->m;
+    double *rhx = (double *)malloc((size_t)n * sizeof(double));
+    double *w = (double *)malloc((size_t)n * sizeof(double));
+    double *wn = (double *)malloc((size_t)n * sizeof(double));
+    double *wn2 = (double *)malloc((size_t)n * sizeof(double));
+    double *tmp = (double *)malloc((size_t)n * sizeof(double));
+    double *bS = (double *)malloc((size_t)(m + 1) * sizeof(double));
+    double *cx = (double *)malloc((size_t)n * sizeof(double));
+    double *cy = (double *)malloc((size_t)(m + 1) * sizeof(double));
+    double *resx = (double *)malloc((size_t)n * sizeof(double));
+    double *resy = (double *)malloc((size_t)(m + 1) * sizeof(double));
+    int32_t total_it = 0, ir = 0, inertia_ok = 1, last_st = 0, ret = 0;
+    double d2_used = 0.0;
+    const double *bx = rx, *by = ry;
+    double *ox = dx, *oy = dy;
+    for (int64_t i = 0; i < n; i++) dx[i] = 0.0;
+    for (int64_t i = 0; i < m; i++) dy[i] = 0.0;
+    double knorm = 0.0, rr = 0.0, be = 0.0;
+    double bnorm = sqrt(dot(rx, rx, n) + dot(ry, ry, m));
+    for (int32_t pass = 0;; pass++) {
+        /* solve K c = (bx, by) into (ox, oy) */
+        jtmul(S, Jv, by, wn);
+        for (int64_t i = 0; i < n; i++) rhx[i] = bx[i] + gamma * wn[i];
+        hsolve(N, rhx, w, tmp);
+        jmul(S, Jv, w, bS);
+        for (int64_t i = 0; i < m; i++) bS[i] -= by[i];
+        int32_t it = 0;
+        int st = cg_schur(N, Jv, bS, 0.0, rtol, maxit, oy, &it, wn, wn2, tmp);
+        total_it += it;
+        if (st == 3) {
+            inertia_ok = 0;
+            d2_used = delta2;
+            st = cg_schur(N, Jv, bS, delta2, rtol, maxit, oy, &it, wn, wn2, tmp);
+            total_it += it;
+        }
+        last_st = st;
+        if (st != 0) ret = st;
+        jtmul(S, Jv, oy, wn);
+        for (int64_t i = 0; i < n; i++) wn[i] = rhx[i] - wn[i];
+        hsolve(N, wn, ox, tmp);
+        if (pass > 0) {
+            for (int64_t i = 0; i < n; i++) dx[i] += cx[i];
+            for (int64_t i = 0; i < m; i++) dy[i] += cy[i];
+        }
+        kkt_residual(S, Hv, Jv, delta, rx, ry, dx, dy, resx, resy, &knorm);
+        double resn = sqrt(dot(resx, resx, n) + dot(resy, resy, m));
+        double xn = sqrt(dot(dx, dx, n) + dot(dy, dy, m));
+        rr = bnorm > 0 ? resn / bnorm : resn;
+        be = resn / (knorm * xn + bnorm);
+        if (ret != 0 || rr <= ir_rtol || ir >= ir_maxit) break;
+        ir++;
+        /* the next pass reads resx/resy as its right-hand side before its
+         * own residual step overwrites them */
+        bx = resx; by = resy; ox = cx; oy = cy;
+    }
+    info[0] = total_it; info[1] = rr; info[2] = be; info[3] = ir;
+    info[4] = d2_used; info[5] = last_st; info[6] = inertia_ok && ret == 0;
+    free(rhx); free(w); free(wn); free(wn2); free(tmp); free(bS); free(cx); free(cy);
+    free(resx); free(resy);
+    return ret;
+}
+
+/* Residual norms of an externally computed solution against K_delta:
+ * out[0] RR, out[1] BE, out[2] ||res||_2, out[3] ||K||_inf */
+void orc_residual(const orc_sym *S, const double *Hv, const double *Jv, double delta,
+                  const double *rx, const double *ry, const double *dx, const double *dy,
+                  double *out) {
+    int64_t n = S->n, m = S->m;
+    double *resx = (double *)malloc((size_t)n * sizeof(double));
+    double *resy = (double *)malloc((size_t)(m + 1) * sizeof(double));
+    double knorm;
+    kkt_residual(S, Hv, Jv, delta, rx, ry, dx, dy, resx, resy, &knorm);
+    double resn = sqrt(dot(resx, resx, n) + dot(resy, resy, m));
+    double bnorm = sqrt(dot(rx, rx, n) + dot(ry, ry, m));
+    double xn = sqrt(dot(dx, dx, n) + dot(dy, dy, m));
+    out[0] = bnorm > 0 ? resn / bnorm : resn;
+    out[1] = resn / (knorm * xn + bnorm);
+    out[2] = resn;
+    out[3] = knorm;
+    free(resx); free(resy);
+}
+
+void orc_num_free(orc_num *N) {
+    if (!N) return;
+    free(N->Up); free(N->Ui); free(N->Ux); free(N->Lx); free(N->Ld);
+    free(N);
+}
