@@ -1,0 +1,500 @@
+"""Pins for the CPU oracle, against what the paper and the mathematics fix.
+
+None of these compare the oracle with itself: each checks it against a dense
+LU/Cholesky/eigenvalue computation (numpy), a closed form, a theorem of the
+paper, or a brute-force symbolic elimination.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------------- helpers
+def dense_H(sys):
+    n = sys.n
+    H = np.zeros((n, n))
+    for j in range(n):
+        for q in range(sys.H_colptr[j], sys.H_colptr[j + 1]):
+            i = sys.H_rowidx[q]
+            H[i, j] += sys.H_vals[q]
+            if i != j:
+                H[j, i] += sys.H_vals[q]
+    return H
+
+
+def dense_J(sys):
+    J = np.zeros((sys.m, sys.n))
+    for r in range(sys.m):
+        for q in range(sys.J_rowptr[r], sys.J_rowptr[r + 1]):
+            J[r, sys.J_colidx[q]] += sys.J_vals[q]
+    return J
+
+
+def dense_K(sys, delta=None):
+    d = sys.delta if delta is None else delta
+    H, J = dense_H(sys), dense_J(sys)
+    n, m = sys.n, sys.m
+    K = np.zeros((n + m, n + m))
+    K[:n, :n] = H + d * np.eye(n)
+    K[:n, n:] = J.T
+    K[n:, :n] = J
+    return K
+
+
+def make_sys(H, J, rx, ry, delta=0.0, gamma=1e2):
+    """KKTSystem from dense H (symmetric) and J."""
+    n, m = H.shape[0], J.shape[0]
+    rows, cols = np.nonzero(np.tril(H, -1))
+    Hp, Hi, Hv = W.lower_csc(n, rows, cols, H[rows, cols], np.diag(H))
+    Jr, Jc = np.nonzero(J)
+    Jp = np.zeros(m + 1, np.int64)
+    np.add.at(Jp, Jr + 1, 1)
+    Jp = np.cumsum(Jp)
+    return W.KKTSystem(n, m, Hp, Hi, Hv, Jp, Jc.astype(np.int32), J[Jr, Jc], rx, ry, delta, gamma)
+
+
+def brute_symbolic(n, adj_dense, perm):
+    """Dense boolean elimination of P A P^T: returns the strictly-lower
+    pattern of L as a boolean matrix (B[i, j] True for i > j)."""
+    B = adj_dense[np.ix_(perm, perm)].copy()
+    np.fill_diagonal(B, False)
+    B = B | B.T
+    L = np.zeros((n, n), bool)
+    for k in range(n):
+        nb = np.nonzero(B[k, k + 1:])[0] + k + 1
+        L[nb, k] = True
+        for a in nb:
+            B[a, nb] = True
+        B[nb, nb] = False  # no self loops
+        for a in nb:
+            for b in nb:
+                if a != b:
+                    B[a, b] = True
+    return L
+
+
+def adjacency_dense(sys):
+    A = np.zeros((sys.n, sys.n), bool)
+    for j in range(sys.n):
+        for q in range(sys.H_colptr[j], sys.H_colptr[j + 1]):
+            i = sys.H_rowidx[q]
+            A[i, j] = A[j, i] = True
+    for r in range(sys.m):
+        cols = sys.J_colidx[sys.J_rowptr[r]:sys.J_rowptr[r + 1]]
+        for a in cols:
+            for b in cols:
+                A[a, b] = True
+    np.fill_diagonal(A, False)
+    return A
+
+
+def graph_sys(n, edges):
+    """KKT system whose H~ pattern is the given graph and J is empty (m=0)."""
+    rows = [max(a, b) for a, b in edges]
+    cols = [min(a, b) for a, b in edges]
+    Hp, Hi, Hv = W.lower_csc(n, rows, cols, -np.ones(len(edges)), np.full(n, float(n)))
+    return W.KKTSystem(n, 0, Hp, Hi, Hv, np.zeros(1, np.int64), np.zeros(0, np.int32),
+                       np.zeros(0), np.zeros(n), np.zeros(0), 0.0, 0.0)
+
+
+def sym_of(sys, **kw):
+    return O.Symbolic(sys.n, sys.m, sys.H_colptr, sys.H_rowidx, sys.J_rowptr, sys.J_colidx, **kw)
+
+
+# ----------------------------------------------------------------- solution
+@pytest.mark.parametrize("seed", range(25))
+def test_solution_matches_dense_lu(seed):
+    """Solution of the 2x2 KKT system (eq. linsys2x2) equals a dense LU solve."""
+    sys = W.random_tiny_system(seed)
+    sym, fac, dx, dy, info = O.solve_system(sys)
+    assert info["status"] == 0 and info["inertia_ok"]
+    K = dense_K(sys)
+    ref = np.linalg.solve(K, np.concatenate([sys.r_x, sys.r_y]))
+    got = np.concatenate([dx, dy])
+    assert np.linalg.norm(got - ref) <= 1e-9 * np.linalg.norm(ref)
+    assert info["rr"] <= 1e-10
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_gamma_invariance(seed):
+    """H_gamma = H~ + gamma J^T J does not change the solution (Sec. 4, Q = gamma I)."""
+    sys = W.random_tiny_system(seed + 100)
+    ref = np.linalg.solve(dense_K(sys), np.concatenate([sys.r_x, sys.r_y]))
+    for gamma in (0.0, 1.0, 1e2, 1e4, 1e6):
+        s = sys.copy()
+        s.gamma = gamma
+        _, _, dx, dy, info = O.solve_system(s)
+        assert info["status"] == 0
+        err = np.linalg.norm(np.concatenate([dx, dy]) - ref) / np.linalg.norm(ref)
+        assert err <= 1e-7, (gamma, err)
+
+
+@pytest.mark.parametrize("alpha,gamma", [(1.0, 1e2), (3.0, 1e4), (0.25, 1.0), (7.0, 0.0)])
+def test_closed_form_identity_blocks(alpha, gamma):
+    """H~ = alpha I, J = [I 0]: dx1 = r_y, dy = r_x1 - alpha r_y, dx2 = r_x2/alpha,
+    and S = I/(alpha+gamma) so CG stops after exactly one product."""
+    n, m = 12, 5
+    rng = np.random.default_rng(7)
+    rx, ry = rng.standard_normal(n), rng.standard_normal(m)
+    J = np.zeros((m, n))
+    J[np.arange(m), np.arange(m)] = 1.0
+    sys = make_sys(alpha * np.eye(n), J, rx, ry, gamma=gamma)
+    _, _, dx, dy, info = O.solve_system(sys)
+    np.testing.assert_allclose(dx[:m], ry, rtol=1e-13, atol=1e-13)
+    np.testing.assert_allclose(dx[m:], rx[m:] / alpha, rtol=1e-13)
+    np.testing.assert_allclose(dy, rx[:m] - alpha * ry, rtol=1e-12, atol=1e-12)
+    assert info["iters"] == 1
+
+
+def test_zero_rhs_gives_zero_and_no_iterations():
+    sys = W.random_tiny_system(3)
+    sys.r_x[:] = 0
+    sys.r_y[:] = 0
+    _, _, dx, dy, info = O.solve_system(sys)
+    assert info["iters"] == 0 and not dx.any() and not dy.any()
+
+
+# ----------------------------------------------------------------- inertia
+@pytest.mark.parametrize("seed", range(10))
+def test_inertia_when_cholesky_succeeds(seed):
+    """Cholesky success + full-rank J  =>  inertia (n, m, 0) (Thm 1 and Thm 3)."""
+    sys = W.random_tiny_system(seed + 200, spd=False)
+    sys.gamma = 1e4
+    sym = sym_of(sys)
+    fac = O.Factor(sym, sys.H_vals, sys.J_vals, 0.0, sys.gamma)
+    ev = np.linalg.eigvalsh(dense_K(sys, 0.0))
+    J = dense_J(sys)
+    full_rank = np.linalg.matrix_rank(J) == sys.m
+    Hg = dense_H(sys) + sys.gamma * J.T @ J
+    spd = np.linalg.eigvalsh(Hg).min() > 0
+    assert fac.ok == spd
+    if fac.ok and full_rank:
+        assert (ev > 0).sum() == sys.n and (ev < 0).sum() == sys.m
+        _, _, info = fac.solve(sys.r_x, sys.r_y)
+        assert info["inertia_ok"]
+
+
+def test_thm1_gamma_threshold():
+    """H~ = diag(-1, 1, ...), J = [I_m 0]: lambda_min(H~) = -1 and
+    lambda_min*(J^T J) = 1, so H_gamma is SPD exactly when gamma > 1 (Thm 1)."""
+    n, m = 8, 3
+    H = np.eye(n)
+    H[0, 0] = -1.0
+    J = np.zeros((m, n))
+    J[np.arange(m), np.arange(m)] = 1.0
+    sys = make_sys(H, J, np.ones(n), np.ones(m))
+    sym = sym_of(sys)
+    for gamma, ok in ((0.5, False), (0.999, False), (1.001, True), (10.0, True), (1e6, True)):
+        assert O.Factor(sym, sys.H_vals, sys.J_vals, 0.0, gamma).ok == ok, gamma
+
+
+def test_indefinite_on_nullspace_fails_for_every_gamma():
+    """H~ negative on a null(J) direction: no gamma makes H_gamma SPD (Thm 1)."""
+    n, m = 8, 3
+    H = np.eye(n)
+    H[5, 5] = -0.5                 # e_5 is in null(J)
+    J = np.zeros((m, n))
+    J[np.arange(m), np.arange(m)] = 1.0
+    sys = make_sys(H, J, np.ones(n), np.ones(m))
+    sym = sym_of(sys)
+    for gamma in (0.0, 1.0, 1e4, 1e8):
+        f = O.Factor(sym, sys.H_vals, sys.J_vals, 0.0, gamma)
+        assert not f.ok
+    # a diagonal shift delta > 0.5 restores SPD (Sec. 4.1, H_delta = H_gamma + delta_1 I)
+    assert O.Factor(sym, sys.H_vals, sys.J_vals, 0.6, 1e4).ok
+
+
+def test_rank_deficient_J_triggers_delta2_and_clears_inertia():
+    """A duplicated J row makes S singular; an inconsistent r_y makes CG meet a
+    small quadratic form, restart on S + delta_2 I, and drop the inertia flag
+    (Sec. 4.1 delta_2; Thm 3 needs delta_2 = 0)."""
+    n, m = 10, 4
+    rng = np.random.default_rng(3)
+    J = np.zeros((m, n))
+    J[np.arange(3), np.arange(3)] = 1.0
+    J[:3, 3:6] = rng.standard_normal((3, 3))
+    J[3] = J[0]
+    sys = make_sys(np.eye(n) * 2.0, J, rng.standard_normal(n), rng.standard_normal(m), gamma=1e2)
+    sym = sym_of(sys)
+    fac = O.Factor(sym, sys.H_vals, sys.J_vals, 0.0, sys.gamma)
+    assert fac.ok
+    dx, dy, info = fac.solve(sys.r_x, sys.r_y, delta2=1e-6)
+    assert info["delta2"] == 1e-6 and not info["inertia_ok"]
+    # the restarted CG solved (S + delta2 I) dy = J w - r_y
+    S = J @ np.linalg.solve(2 * np.eye(n) + sys.gamma * J.T @ J, J.T)
+    rhat = sys.r_x + sys.gamma * J.T @ sys.r_y
+    w = np.linalg.solve(2 * np.eye(n) + sys.gamma * J.T @ J, rhat)
+    ref = np.linalg.solve(S + 1e-6 * np.eye(m), J @ w - sys.r_y)
+    assert np.linalg.norm(dy - ref) <= 1e-6 * np.linalg.norm(ref)
+
+
+# ----------------------------------------------------------------- convergence theory
+def test_thm4_eigenvalues_cluster_at_one():
+    """eig(gamma S) -> 1 with an error O(1/gamma) (Thm 4)."""
+    sys = W.random_tiny_system(11, n_lo=30, n_hi=30)
+    H, J = dense_H(sys), dense_J(sys)
+    errs = []
+    for gamma in (1e3, 1e4, 1e5, 1e6):
+        S = J @ np.linalg.solve(H + gamma * J.T @ J, J.T)
+        ev = np.linalg.eigvalsh(gamma * (S + S.T) / 2)
+        errs.append(np.abs(ev - 1).max())
+    for a, b in zip(errs, errs[1:]):
+        assert 5.0 <= a / b <= 20.0          # decays like 1/gamma
+
+
+@pytest.mark.parametrize("gamma", [1e2, 1e4])
+def test_cg_iterations_within_cgconv_bound(gamma):
+    """CG iterations obey eq. CGconv: ||r_k||/||r_0|| <= sqrt(k(S)) * 2((sqrt k - 1)/(sqrt k + 1))^k."""
+    sys = W.random_tiny_system(21, n_lo=40, n_hi=40, gamma=gamma)
+    H, J = dense_H(sys), dense_J(sys)
+    S = J @ np.linalg.solve(H + gamma * J.T @ J, J.T)
+    ev = np.linalg.eigvalsh((S + S.T) / 2)
+    kappa = ev.max() / ev.min()
+    q = (np.sqrt(kappa) - 1) / (np.sqrt(kappa) + 1)
+    k_bound = 1
+    while 2 * np.sqrt(kappa) * q ** k_bound > 1e-12:
+        k_bound += 1
+    _, _, _, _, info = O.solve_system(sys)
+    assert 1 <= info["iters"] <= k_bound + 1
+
+
+# ----------------------------------------------------------------- Cholesky
+@pytest.mark.parametrize("seed", range(10))
+def test_cholesky_equals_dense_cholesky(seed):
+    """L L^T = P (H~ + delta I + gamma J^T J) P^T; L equals numpy's Cholesky."""
+    sys = W.random_tiny_system(seed + 300)
+    delta, gamma = 1e-3, 50.0
+    sym = sym_of(sys)
+    fac = O.Factor(sym, sys.H_vals, sys.J_vals, delta, gamma)
+    assert fac.ok
+    Lp, Li, Lx = fac.L_csc()
+    n = sys.n
+    L = np.zeros((n, n))
+    for j in range(n):
+        L[Li[Lp[j]:Lp[j + 1]], j] = Lx[Lp[j]:Lp[j + 1]]
+    J = dense_J(sys)
+    A = dense_H(sys) + delta * np.eye(n) + gamma * J.T @ J
+    p = sym.perm
+    PA = A[np.ix_(p, p)]
+    Lref = np.linalg.cholesky(PA)
+    assert np.abs(L - Lref).max() <= 1e-12 * np.abs(Lref).max()
+    assert np.linalg.norm(L @ L.T - PA) <= 1e-14 * n * np.linalg.norm(PA)
+
+
+def test_hsolve_is_inverse():
+    sys = W.random_tiny_system(5)
+    sym = sym_of(sys)
+    fac = O.Factor(sym, sys.H_vals, sys.J_vals, 0.0, sys.gamma)
+    J = dense_J(sys)
+    A = dense_H(sys) + sys.gamma * J.T @ J
+    b = np.arange(sys.n, dtype=float)
+    np.testing.assert_allclose(fac.hsolve(b), np.linalg.solve(A, b), rtol=1e-10, atol=1e-12)
+
+
+# ----------------------------------------------------------------- symbolic
+@pytest.mark.parametrize("seed", range(40))
+def test_symbolic_equals_bruteforce_elimination(seed):
+    """Pattern of L, etree (= first off-diagonal row per column) and column
+    counts match dense boolean elimination in the oracle's permutation."""
+    sys = W.random_tiny_system(seed + 400, n_lo=5, n_hi=45, density=0.1)
+    sym = sym_of(sys)
+    p = sym.perm
+    assert sorted(p.tolist()) == list(range(sys.n))
+    Lb = brute_symbolic(sys.n, adjacency_dense(sys), p)
+    Lp, Li = sym.l_pattern()
+    got = np.zeros_like(Lb)
+    for j in range(sys.n):
+        got[Li[Lp[j]:Lp[j + 1]], j] = True
+    assert (got == Lb).all()
+    par = sym.parent
+    for j in range(sys.n):
+        rows = np.nonzero(Lb[:, j])[0]
+        assert par[j] == (rows.min() if rows.size else -1)
+    np.testing.assert_array_equal(sym.colcount, Lb.sum(0) + 1)
+
+
+@pytest.mark.parametrize("seed", range(15))
+def test_postorder_makes_subtrees_contiguous(seed):
+    sys = W.random_tiny_system(seed + 500, n_lo=20, n_hi=60, density=0.05)
+    sym = sym_of(sys)
+    par = sym.parent
+    n = sys.n
+    size = np.ones(n, int)
+    for j in range(n):          # children precede parents
+        assert par[j] == -1 or par[j] > j
+        if par[j] >= 0:
+            size[par[j]] += size[j]
+    for j in range(n):
+        # the descendants of j are exactly j-size+1 .. j
+        lo = j - size[j] + 1
+        for k in range(lo, j):
+            a = k
+            while a != -1 and a < j:
+                a = par[a]
+            assert a == j
+
+
+def _amd_case(name):
+    with open(os.path.join(GOLDEN, "amd_hand_worked.json")) as f:
+        return json.load(f)[name]
+
+
+@pytest.mark.parametrize("name", ["path5", "star5", "clique4", "two_triangles", "grid2x3"])
+def test_amd_hand_worked(name):
+    """Hand-worked orders of the pinned AMD rules (Sec. 5.3 names AMD;
+    the rules are those of Amestoy, Davis and Duff 1996 with pinned ties)."""
+    case = _amd_case(name)
+    sys = graph_sys(case["n"], [tuple(e) for e in case["edges"]])
+    assert sym_of(sys).amd_order.tolist() == case["order"]
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_amd_zero_fill_on_trees(seed):
+    """Minimum degree eliminates leaves first, so a tree gets no fill."""
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(5, 80))
+    lab = rng.permutation(n)
+    edges = [(int(lab[i]), int(lab[rng.integers(0, i)])) for i in range(1, n)]
+    sys = graph_sys(n, edges)
+    sym = sym_of(sys)
+    assert sym.nnzL == n + len(edges)
+
+
+def test_amd_clique_is_identity_and_one_supernode():
+    n = 9
+    edges = [(a, b) for a in range(n) for b in range(a)]
+    sym = sym_of(graph_sys(n, edges))
+    assert sym.amd_order.tolist() == list(range(n))
+    assert sym.nsuper == 1
+
+
+def test_amd_beats_natural_on_grid():
+    """AMD gives less fill than the natural order (Sec. 5.3 comparison)."""
+    sys = W.make_config("grid2d_n2000")
+    a = sym_of(sys)
+    b = sym_of(sys, ordering="natural")
+    assert a.nnzL < b.nnzL
+
+
+# ----------------------------------------------------------------- supernodes
+@pytest.mark.parametrize("seed", range(12))
+def test_supernodes_cover_structure(seed):
+    """Supernodes partition the columns into contiguous ranges; each row
+    list holds its columns and contains the structure of every column; the
+    supernodal parent is the supernode of the etree parent of its last column."""
+    sys = W.random_tiny_system(seed + 600, n_lo=20, n_hi=60, density=0.08)
+    for relax in ((1, 0, 1, 256), (16, 1, 10, 256), (4, 1, 2, 8)):
+        sym = sym_of(sys, relax_small=relax[0], relax_num=relax[1], relax_den=relax[2], wmax=relax[3])
+        start, rowptr, rows, spar = sym.supernodes()
+        Lp, Li = sym.l_pattern()
+        par = sym.parent
+        assert start[0] == 0 and start[-1] == sys.n and (np.diff(start) > 0).all()
+        col2sn = np.repeat(np.arange(sym.nsuper), np.diff(start))
+        zeros = 0
+        for s in range(sym.nsuper):
+            f, l = start[s], start[s + 1] - 1
+            R = rows[rowptr[s]:rowptr[s + 1]]
+            assert (np.diff(R) > 0).all()
+            assert R[:l - f + 1].tolist() == list(range(f, l + 1))
+            for j in range(f, l + 1):
+                assert set(Li[Lp[j]:Lp[j + 1]].tolist()) <= set(R.tolist())
+            W_ = l - f + 1
+            panel = W_ * (W_ + 1) // 2 + W_ * (len(R) - W_)
+            zeros_s = panel - sum(Lp[j + 1] - Lp[j] + 1 for j in range(f, l + 1))
+            zeros += zeros_s
+            if relax[0] == 1 and relax[1] == 0:
+                assert zeros_s == 0           # fundamental supernodes hold no explicit zeros
+            assert W_ <= max(relax[3], 1) or zeros_s == 0
+            assert spar[s] == (col2sn[par[l]] if par[l] >= 0 else -1)
+
+
+# ----------------------------------------------------------------- residual definitions
+def test_rr_be_definitions():
+    """RR = ||K x - b|| / ||b||, BE = ||K x - b|| / (||K||_inf ||x|| + ||b||) (Sec. 5.1)."""
+    sys = W.random_tiny_system(8)
+    K = dense_K(sys)
+    b = np.concatenate([sys.r_x, sys.r_y])
+    x = np.linalg.solve(K, b)
+    sym = sym_of(sys)
+    exact = O.residual(sym, sys.H_vals, sys.J_vals, sys.delta, sys.r_x, sys.r_y, x[:sys.n], x[sys.n:])
+    assert exact["rr"] < 1e-13 and exact["be"] <= exact["rr"]
+    assert exact["knorm"] == pytest.approx(np.abs(K).sum(1).max(), rel=1e-14)
+    e = np.zeros_like(x)
+    e[0] = 1e-3
+    pert = O.residual(sym, sys.H_vals, sys.J_vals, sys.delta, sys.r_x, sys.r_y, (x + e)[:sys.n], (x + e)[sys.n:])
+    res = np.linalg.norm(K @ (x + e) - b)
+    assert pert["rr"] == pytest.approx(res / np.linalg.norm(b), rel=1e-8)
+    assert pert["be"] == pytest.approx(res / (np.abs(K).sum(1).max() * np.linalg.norm(x + e) + np.linalg.norm(b)), rel=1e-8)
+
+
+# ----------------------------------------------------------------- 4x4 reduction
+@pytest.mark.parametrize("seed", range(5))
+def test_4x4_reduction_matches_dense(seed):
+    """Eliminating ds, dy_d (Sec. 3, eq. linsys2x2) and recovering them
+    reproduces the dense solve of the 4x4 system (eq. linsys4x4)."""
+    p = W.random_4x4_parts(seed, n_x=20, m_c=6, m_d=5)
+    Hp, Hi, Hv, r_x = O.reduce4x4(p)
+    n, mc, md = p["n_x"], p["m_c"], p["m_d"]
+    sys = W.KKTSystem(n, mc, Hp, Hi, Hv, p["J_rowptr"], p["J_colidx"], p["J_vals"], r_x,
+                      p["r_y"], 0.0, 1e2)
+    _, _, dx, dy, info = O.solve_system(sys)
+    assert info["status"] == 0
+    ds, dyd = O.recover4x4(p, dx)
+    # dense 4x4
+    H = np.zeros((n, n))
+    for j in range(n):
+        for q in range(Hp.size and p["H_colptr"][j], p["H_colptr"][j + 1]):
+            i = p["H_rowidx"][q]
+            H[i, j] += p["H_vals"][q]
+            if i != j:
+                H[j, i] += p["H_vals"][q]
+    J = np.zeros((mc, n))
+    for r in range(mc):
+        for q in range(p["J_rowptr"][r], p["J_rowptr"][r + 1]):
+            J[r, p["J_colidx"][q]] = p["J_vals"][q]
+    Jd = np.zeros((md, n))
+    for r in range(md):
+        for q in range(p["Jd_rowptr"][r], p["Jd_rowptr"][r + 1]):
+            Jd[r, p["Jd_colidx"][q]] = p["Jd_vals"][q]
+    N = n + md + mc + md
+    K = np.zeros((N, N))
+    K[:n, :n] = H + np.diag(p["D_x"])
+    K[n:n + md, n:n + md] = np.diag(p["D_s"])
+    K[:n, n + md:n + md + mc] = J.T
+    K[:n, n + md + mc:] = Jd.T
+    K[n:n + md, n + md + mc:] = -np.eye(md)
+    K[n + md:n + md + mc, :n] = J
+    K[n + md + mc:, :n] = Jd
+    K[n + md + mc:, n:n + md] = -np.eye(md)
+    rhs = np.concatenate([p["r_xt"], p["r_s"], p["r_y"], p["r_yd"]])
+    ref = np.linalg.solve(K, rhs)
+    got = np.concatenate([dx, ds, dy, dyd])
+    assert np.linalg.norm(got - ref) <= 1e-8 * np.linalg.norm(ref)
+
+
+# ----------------------------------------------------------------- the small workload
+def test_small_grid_workload_against_sparse_lu():
+    """50x40 grid workload: RR <= 1e-8 on K_delta, CG iterations O(10)
+    (Sec. 5: < 20 on average), inertia flag set, and agreement with a
+    sparse LU solve of the full KKT matrix (scipy SuperLU)."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spl
+    sys = W.make_config("grid2d_n2000")
+    sym, fac, dx, dy, info = O.solve_system(sys)
+    assert info["status"] == 0 and info["inertia_ok"]
+    assert info["rr"] <= 1e-8 and info["iters"] <= 20
+    n, m = sys.n, sys.m
+    H = sp.csc_matrix((sys.H_vals, sys.H_rowidx, sys.H_colptr), shape=(n, n))
+    H = H + sp.tril(H, -1).T + sys.delta * sp.eye(n)
+    J = sp.csr_matrix((sys.J_vals, sys.J_colidx, sys.J_rowptr), shape=(m, n))
+    K = sp.bmat([[H, J.T], [J, None]]).tocsc()
+    ref = spl.spsolve(K, np.concatenate([sys.r_x, sys.r_y]))
+    got = np.concatenate([dx, dy])
+    assert np.linalg.norm(got - ref) <= 1e-6 * np.linalg.norm(ref)
