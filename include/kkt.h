@@ -1,0 +1,192 @@
+/*
+ * kkt.h -- C ABI of the B300 hybrid direct-iterative KKT solver.
+ *
+ * Method (Regev, Chiang, Darve, Petra, Saunders, Swirydowicz, Peles,
+ * "A Hybrid Direct-Iterative Method for Solving KKT Linear Systems"):
+ * the 2x2 KKT system (Sec. 3, eq. linsys2x2)
+ *
+ *     [ H~ + delta I   J^T ] [dx]   [r_x]
+ *     [ J              0   ] [dy] = [r_y]
+ *
+ * is solved through H_gamma = H~ + delta I + gamma J^T J (Sec. 4, eqs.
+ * linsys2x2mod and gamma; delta is the delta_1 of Sec. 4.1), its sparse
+ * Cholesky factor, and CG on the Schur complement S = J H_gamma^-1 J^T
+ * (eqs. Schur1 and Schur2; Algorithm 1).
+ *
+ * Conventions for every entry point:
+ *   - Indices are 0-based. H~ is given by its LOWER triangle (diagonal
+ *     included) in CSC form with rows strictly ascending inside each column;
+ *     J (m x n) is given in CSR form with columns strictly ascending inside
+ *     each row. Entries above the diagonal, out-of-range or repeated indices
+ *     make kkt_analyse return KKT_ERR_INVALID.
+ *   - "host" pointers are read or written on the host during the call only;
+ *     "device" pointers are CUDA device memory on the handle's device and are
+ *     read/written in stream order on `stream` (a cudaStream_t passed as
+ *     void*; NULL = the legacy default stream). The caller owns every buffer
+ *     it passes; the handle owns its own copies of the pattern, the values it
+ *     needs after kkt_factor returns, the factor and all workspace.
+ *   - Every function returns a kkt_status; none aborts, traps or exits.
+ *   - A handle is not thread safe; use one handle per host thread.
+ */
+#ifndef KKT_H_
+#define KKT_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum kkt_status {
+  KKT_OK = 0,
+  KKT_ERR_INVALID = 1,       /* bad argument or pattern */
+  KKT_ERR_NOT_SPD = 2,       /* Cholesky met a pivot <= 0 or non-finite (Sec. 4.1) */
+  KKT_ERR_CG_BREAKDOWN = 3,  /* small quadratic form even after the delta_2 restart */
+  KKT_ERR_CG_MAXIT = 4,      /* CG did not reach cg_rtol in cg_maxit products */
+  KKT_ERR_OOM = 5,           /* device allocation failed */
+  KKT_ERR_CUDA = 6,          /* a CUDA call failed */
+  KKT_ERR_TIMEOUT = 7,       /* a bounded wait inside a persistent kernel gave up */
+  KKT_ERR_STATE = 8          /* call out of order (e.g. solve before a successful factor) */
+} kkt_status;
+
+typedef struct kkt_handle_s* kkt_handle;
+
+enum { KKT_FP64 = 0, KKT_MIXED = 1 };
+
+typedef struct kkt_options {
+  double gamma;        /* default gamma when kkt_factor gets gamma < 0 (Algorithm 1: 1e4) */
+  double delta2;       /* delta_2 of the CG restart on S + delta_2 I (Algorithm 1: 1e-9) */
+  double cg_rtol;      /* CG stop: ||r|| <= cg_rtol ||b_S|| (Sec. 5.1: 1e-12) */
+  int32_t cg_maxit;    /* CG product limit (1000) */
+  int32_t ir_maxit;    /* refinement steps on K_delta after the first solve */
+  double ir_rtol;      /* refine while RR(K_delta) > ir_rtol */
+  int32_t precision;   /* KKT_FP64: FP64 factor and solves; KKT_MIXED: FP32 factor and
+                          triangular solves, FP64 CG recurrences, residual and refinement */
+  int32_t ordering;    /* 0 = approximate minimum degree (Sec. 5.3), 1 = natural */
+  int32_t relax_small; /* supernode relaxation: merge when merged width <= relax_small */
+  int32_t relax_num;   /*   or explicit zeros * relax_den <= relax_num * panel entries */
+  int32_t relax_den;
+  int32_t relax_wmax;  /*   never beyond this width */
+  int32_t solve_w;     /* column width of the triangular-solve pieces (<= 256) */
+  int32_t device;      /* CUDA device ordinal */
+  int32_t debug_stall_piece; /* test hook, -1 = off: makes one triangular-solve piece wait for
+                                an arrival that never comes, so the bounded wait runs out */
+  int64_t spin_cycles; /* limit of every wait on another CTA's flag, in SM clock cycles
+                          (0 = default 4e9, about two seconds) */
+} kkt_options;
+
+/* Result of the last kkt_solve on a handle. */
+typedef struct kkt_info {
+  int32_t cg_iters;    /* products with S summed over all refinement passes */
+  int32_t ir_steps;    /* refinement passes after the first */
+  int32_t cg_status;   /* 0 converged, 3 breakdown, 4 max iterations (last pass) */
+  int32_t delta2_used; /* 1 if the delta_2 restart was taken (inertia flag then false) */
+  double rr;           /* ||b - K_delta x||_2 / ||b||_2 (Sec. 5.1, RR) */
+  double be;           /* ||b - K_delta x||_2 / (||K_delta||_inf ||x||_2 + ||b||_2) (Sec. 5.1, BE) */
+} kkt_info;
+
+typedef struct kkt_symbolic_info {
+  int64_t n, m;
+  int64_t nsuper;      /* supernodes after relaxation */
+  int64_t nnz_l;       /* nonzeros of L incl. diagonal (no explicit zeros) */
+  int64_t panel_entries;  /* stored panel entries (supernodal storage, incl. zeros) */
+  int64_t update_entries; /* multifrontal update-matrix workspace entries */
+  int64_t sn_rows_total;  /* sum of supernode row-list lengths */
+  int64_t npieces, nchunks;  /* triangular-solve work items */
+  int32_t nlevels;     /* height of the supernodal tree */
+  int32_t pad;
+  double flops;        /* sum_j colcount_j^2 (factor flop count, no explicit zeros) */
+  double device_bytes; /* device memory held by the handle */
+} kkt_symbolic_info;
+
+/* Defaults: Algorithm 1's typical parameters (gamma 1e4, delta_2 1e-9), CG
+ * tolerance 1e-12 (Sec. 5.1), AMD ordering. */
+void kkt_default_options(kkt_options* opt);
+
+/* Ordering and symbolic factorization, once per sparsity pattern (Sec. 2:
+ * both are needed only once for the whole sequence; Sec. 5.3: AMD).
+ *   n, m       dimensions of H~ (n x n) and J (m x n); n >= 1, m >= 0
+ *   H_colptr   host int64[n+1], H_rowidx host int32[H_colptr[n]]
+ *   J_rowptr   host int64[m+1], J_colidx host int32[J_rowptr[m]]
+ *   opt        host, may be NULL for the defaults
+ *   out        receives a new handle (NULL on failure)
+ * Allocates all device memory the handle will use. Errors: KKT_ERR_INVALID,
+ * KKT_ERR_OOM, KKT_ERR_CUDA. */
+kkt_status kkt_analyse(int64_t n, int64_t m, const int64_t* H_colptr, const int32_t* H_rowidx,
+                       const int64_t* J_rowptr, const int32_t* J_colidx, const kkt_options* opt,
+                       kkt_handle* out);
+
+/* Host-only variant of kkt_analyse: the same ordering, symbolic
+ * factorization and numeric plan, but no CUDA call and no device memory.
+ * The handle answers kkt_symbolic_info_get, kkt_get_symbolic and
+ * kkt_destroy; factor/solve calls on it return KKT_ERR_STATE. */
+kkt_status kkt_analyse_host(int64_t n, int64_t m, const int64_t* H_colptr, const int32_t* H_rowidx,
+                            const int64_t* J_rowptr, const int32_t* J_colidx, const kkt_options* opt,
+                            kkt_handle* out);
+
+/* Numeric factorization L L^T = P (H~ + delta I + gamma J^T J) P^T on the
+ * analysed pattern (Sec. 4 eq. gamma, Sec. 4.1 delta_1; Algorithm 1 "Try
+ * L L^T = chol(H_delta)").
+ *   H_vals  device double[nnz(H~)], in the order of H_rowidx
+ *   J_vals  device double[nnz(J)], in the order of J_colidx
+ *   delta   diagonal shift (>= 0); gamma >= 0 (gamma < 0 selects opt.gamma)
+ * Synchronizes `stream` to read the pivot status. KKT_ERR_NOT_SPD when a
+ * pivot is <= 0 or non-finite: the handle stays usable and the caller may
+ * retry with a larger delta (the delta_1 loop of Algorithm 1 is the
+ * caller's, Sec. 4.2). */
+kkt_status kkt_factor(kkt_handle h, const double* H_vals, const double* J_vals, double delta,
+                      double gamma, void* stream);
+
+/* Solve with the last successful factor (Algorithm 1 solve steps; eqs.
+ * Schur1/Schur2), then FP64 refinement on K_delta while RR > ir_rtol.
+ *   r_x, r_y  device double[n], double[m] (may alias nothing written here)
+ *   dx, dy    device double[n], double[m] outputs
+ * Synchronizes `stream`. Errors: KKT_ERR_STATE (no successful factor),
+ * KKT_ERR_CG_BREAKDOWN, KKT_ERR_CG_MAXIT, KKT_ERR_TIMEOUT, KKT_ERR_CUDA.
+ * On an error the outputs hold the last iterate. */
+kkt_status kkt_solve(kkt_handle h, const double* r_x, const double* r_y, double* dx, double* dy,
+                     void* stream);
+
+/* Factor + solve with HOST buffers (copies in and out on `stream`):
+ * H_vals/J_vals/r_x/r_y/dx/dy are host arrays of the sizes above. */
+kkt_status kkt_factor_solve_host(kkt_handle h, const double* H_vals, const double* J_vals,
+                                 double delta, double gamma, const double* r_x, const double* r_y,
+                                 double* dx, double* dy, void* stream);
+
+/* x = H_delta^-1 b with the current factor (device double[n] each; the two
+ * triangular solves of Algorithm 1). Synchronizes `stream`. */
+kkt_status kkt_hsolve(kkt_handle h, const double* b, double* x, void* stream);
+
+/* Statistics of the last kkt_solve (host struct). */
+kkt_status kkt_get_info(kkt_handle h, kkt_info* info);
+
+/* 1 when the last factor succeeded and the last solve needed no delta_2
+ * restart: then K_delta has inertia (n, m, 0) (Sec. 4.2, Thm 3; Thm 1). */
+kkt_status kkt_inertia(kkt_handle h, int32_t* inertia_ok);
+
+/* Sizes of the symbolic analysis and of the device storage (host struct). */
+kkt_status kkt_symbolic_info_get(kkt_handle h, kkt_symbolic_info* out);
+
+/* Copies of the symbolic outputs into host arrays (any pointer may be NULL):
+ *   amd[n]        ordering before the etree postorder
+ *   perm[n]       final permutation, perm[k] = original index at position k
+ *   parent[n]     elimination tree in final labels (-1 = root)
+ *   colcount[n]   nonzeros of each column of L incl. the diagonal
+ *   sn_start[nsuper+1], sn_rowptr[nsuper+1], sn_rows[sn_rows_total],
+ *   sn_parent[nsuper]  supernode partition, row lists and tree */
+kkt_status kkt_get_symbolic(kkt_handle h, int32_t* amd, int32_t* perm, int32_t* parent,
+                            int64_t* colcount, int32_t* sn_start, int64_t* sn_rowptr,
+                            int32_t* sn_rows, int32_t* sn_parent);
+
+/* The factor's supernode panels converted to FP64 into host double
+ * [panel_entries] (column-major per supernode, ld = its row count). */
+kkt_status kkt_get_factor_panels(kkt_handle h, double* panels);
+
+kkt_status kkt_destroy(kkt_handle h);
+
+const char* kkt_status_string(kkt_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KKT_H_ */

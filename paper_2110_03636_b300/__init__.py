@@ -1,0 +1,286 @@
+"""B300-native hybrid direct-iterative KKT solver (Python binding).
+
+Thin ctypes binding over the C ABI in ``include/kkt.h`` (``libkkt.so``):
+the functions here have the C names and only marshal arguments -- device
+buffers are torch CUDA tensors (``.data_ptr()``) on the current stream, host
+buffers are numpy arrays. Every step of the method runs in the library's
+CUDA kernels; there is no CPU fallback: importing this package without a
+built ``libkkt.so`` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libkkt.so")
+
+KKT_FP64, KKT_MIXED = 0, 1
+STATUS = {0: "ok", 1: "invalid", 2: "not_spd", 3: "cg_breakdown", 4: "cg_maxit",
+          5: "oom", 6: "cuda", 7: "timeout", 8: "state"}
+
+
+class KKTError(RuntimeError):
+    def __init__(self, fn, code):
+        self.code = int(code)
+        super().__init__(f"{fn}: {STATUS.get(self.code, self.code)} ({_lib.kkt_status_string(self.code).decode()})")
+
+
+class kkt_options(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("delta2", C.c_double), ("cg_rtol", C.c_double),
+                ("cg_maxit", C.c_int32), ("ir_maxit", C.c_int32), ("ir_rtol", C.c_double),
+                ("precision", C.c_int32), ("ordering", C.c_int32), ("relax_small", C.c_int32),
+                ("relax_num", C.c_int32), ("relax_den", C.c_int32), ("relax_wmax", C.c_int32),
+                ("solve_w", C.c_int32), ("device", C.c_int32), ("debug_stall_piece", C.c_int32),
+                ("spin_cycles", C.c_int64)]
+
+
+class kkt_info(C.Structure):
+    _fields_ = [("cg_iters", C.c_int32), ("ir_steps", C.c_int32), ("cg_status", C.c_int32),
+                ("delta2_used", C.c_int32), ("rr", C.c_double), ("be", C.c_double)]
+
+
+class kkt_symbolic_info(C.Structure):
+    _fields_ = [("n", C.c_int64), ("m", C.c_int64), ("nsuper", C.c_int64), ("nnz_l", C.c_int64),
+                ("panel_entries", C.c_int64), ("update_entries", C.c_int64), ("sn_rows_total", C.c_int64),
+                ("npieces", C.c_int64), ("nchunks", C.c_int64), ("nlevels", C.c_int32), ("pad", C.c_int32),
+                ("flops", C.c_double), ("device_bytes", C.c_double)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libkkt.so is not built ({LIB_PATH}); run python paper_2110_03636_b300/build.py")
+    L = C.CDLL(LIB_PATH)
+    P, I64, I32, D = C.c_void_p, C.c_int64, C.c_int32, C.c_double
+    L.kkt_default_options.argtypes = [C.POINTER(kkt_options)]
+    L.kkt_default_options.restype = None
+    L.kkt_analyse.argtypes = [I64, I64, P, P, P, P, C.POINTER(kkt_options), C.POINTER(P)]
+    L.kkt_analyse_host.argtypes = [I64, I64, P, P, P, P, C.POINTER(kkt_options), C.POINTER(P)]
+    L.kkt_factor.argtypes = [P, P, P, D, D, P]
+    L.kkt_solve.argtypes = [P, P, P, P, P, P]
+    L.kkt_factor_solve_host.argtypes = [P, P, P, D, D, P, P, P, P, P]
+    L.kkt_hsolve.argtypes = [P, P, P, P]
+    L.kkt_get_info.argtypes = [P, C.POINTER(kkt_info)]
+    L.kkt_inertia.argtypes = [P, C.POINTER(I32)]
+    L.kkt_symbolic_info_get.argtypes = [P, C.POINTER(kkt_symbolic_info)]
+    L.kkt_get_symbolic.argtypes = [P] + [P] * 8
+    L.kkt_get_factor_panels.argtypes = [P, P]
+    L.kkt_destroy.argtypes = [P]
+    L.kkt_status_string.argtypes = [I32]
+    L.kkt_status_string.restype = C.c_char_p
+    for nm in ("kkt_analyse", "kkt_analyse_host", "kkt_factor", "kkt_solve", "kkt_factor_solve_host", "kkt_hsolve", "kkt_get_info",
+               "kkt_inertia", "kkt_symbolic_info_get", "kkt_get_symbolic", "kkt_get_factor_panels", "kkt_destroy"):
+        getattr(L, nm).restype = I32
+    return L
+
+
+_lib = _load()
+EXPORTED = ("kkt_default_options", "kkt_analyse", "kkt_analyse_host", "kkt_factor", "kkt_solve", "kkt_factor_solve_host",
+            "kkt_hsolve", "kkt_get_info", "kkt_inertia", "kkt_symbolic_info_get", "kkt_get_symbolic",
+            "kkt_get_factor_panels", "kkt_destroy", "kkt_status_string")
+
+
+def _check(fn, code):
+    if code != 0:
+        raise KKTError(fn, code)
+
+
+def _np(a, dt):
+    a = np.ascontiguousarray(a, dtype=dt)
+    return a, (a.ctypes.data if a.size else None)
+
+
+def _dev(t, n):
+    """Device pointer of a contiguous float64 CUDA tensor with n elements."""
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    if t.numel() != n:
+        raise ValueError(f"expected {n} elements, got {t.numel()}")
+    return t.data_ptr() if n else None
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def kkt_default_options(**over) -> kkt_options:
+    o = kkt_options()
+    _lib.kkt_default_options(C.byref(o))
+    for k, v in over.items():
+        if k == "precision" and isinstance(v, str):
+            v = {"fp64": KKT_FP64, "mixed": KKT_MIXED}[v]
+        setattr(o, k, v)
+    return o
+
+
+def kkt_analyse(n, m, H_colptr, H_rowidx, J_rowptr, J_colidx, opt: kkt_options | None = None):
+    keep = [_np(H_colptr, np.int64), _np(H_rowidx, np.int32), _np(J_rowptr, np.int64), _np(J_colidx, np.int32)]
+    h = C.c_void_p()
+    _check("kkt_analyse", _lib.kkt_analyse(int(n), int(m), keep[0][1], keep[1][1], keep[2][1], keep[3][1],
+                                           C.byref(opt) if opt is not None else None, C.byref(h)))
+    return h
+
+
+def kkt_analyse_host(n, m, H_colptr, H_rowidx, J_rowptr, J_colidx, opt: kkt_options | None = None):
+    """Host-only symbolic analysis (no GPU needed); returns a handle for the
+    symbolic getters."""
+    keep = [_np(H_colptr, np.int64), _np(H_rowidx, np.int32), _np(J_rowptr, np.int64), _np(J_colidx, np.int32)]
+    h = C.c_void_p()
+    _check("kkt_analyse_host", _lib.kkt_analyse_host(int(n), int(m), keep[0][1], keep[1][1], keep[2][1],
+                                                     keep[3][1], C.byref(opt) if opt is not None else None,
+                                                     C.byref(h)))
+    return h
+
+
+def kkt_factor(h, H_vals, J_vals, delta, gamma, n_h, n_j, stream=None):
+    return _lib.kkt_factor(h, _dev(H_vals, n_h), _dev(J_vals, n_j), float(delta), float(gamma), _stream(stream))
+
+
+def kkt_solve(h, r_x, r_y, dx, dy, n, m, stream=None):
+    return _lib.kkt_solve(h, _dev(r_x, n), _dev(r_y, m), _dev(dx, n), _dev(dy, m), _stream(stream))
+
+
+def kkt_hsolve(h, b, x, n, stream=None):
+    return _lib.kkt_hsolve(h, _dev(b, n), _dev(x, n), _stream(stream))
+
+
+def kkt_factor_solve_host(h, H_vals, J_vals, delta, gamma, r_x, r_y, dx, dy, stream=None):
+    """All value/vector arguments are host numpy float64 arrays (dx, dy written)."""
+    for a in (H_vals, J_vals, r_x, r_y, dx, dy):
+        if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
+            raise TypeError("expected contiguous float64 numpy arrays")
+    ptr = lambda a: a.ctypes.data if a.size else None
+    return _lib.kkt_factor_solve_host(h, ptr(H_vals), ptr(J_vals), float(delta), float(gamma), ptr(r_x),
+                                      ptr(r_y), ptr(dx), ptr(dy), _stream(stream))
+
+
+def kkt_get_info(h) -> kkt_info:
+    i = kkt_info()
+    _check("kkt_get_info", _lib.kkt_get_info(h, C.byref(i)))
+    return i
+
+
+def kkt_inertia(h) -> bool:
+    v = C.c_int32()
+    _check("kkt_inertia", _lib.kkt_inertia(h, C.byref(v)))
+    return bool(v.value)
+
+
+def kkt_symbolic_info_get(h) -> kkt_symbolic_info:
+    s = kkt_symbolic_info()
+    _check("kkt_symbolic_info_get", _lib.kkt_symbolic_info_get(h, C.byref(s)))
+    return s
+
+
+def kkt_get_symbolic(h):
+    s = kkt_symbolic_info_get(h)
+    n, ns = s.n, s.nsuper
+    out = dict(amd=np.zeros(n, np.int32), perm=np.zeros(n, np.int32), parent=np.zeros(n, np.int32),
+               colcount=np.zeros(n, np.int64), sn_start=np.zeros(ns + 1, np.int32),
+               sn_rowptr=np.zeros(ns + 1, np.int64), sn_rows=np.zeros(max(1, s.sn_rows_total), np.int32),
+               sn_parent=np.zeros(max(1, ns), np.int32))
+    keys = ("amd", "perm", "parent", "colcount", "sn_start", "sn_rowptr", "sn_rows", "sn_parent")
+    _check("kkt_get_symbolic", _lib.kkt_get_symbolic(h, *[out[k].ctypes.data for k in keys]))
+    out["sn_rows"] = out["sn_rows"][: s.sn_rows_total]
+    out["sn_parent"] = out["sn_parent"][:ns]
+    return out
+
+
+def kkt_get_factor_panels(h):
+    s = kkt_symbolic_info_get(h)
+    out = np.zeros(max(1, s.panel_entries))
+    _check("kkt_get_factor_panels", _lib.kkt_get_factor_panels(h, out.ctypes.data))
+    return out[: s.panel_entries]
+
+
+def kkt_destroy(h):
+    return _lib.kkt_destroy(h)
+
+
+def kkt_status_string(code) -> str:
+    return _lib.kkt_status_string(int(code)).decode()
+
+
+class KKTSolver:
+    """One analysed pattern: factor values, solve right-hand sides.
+
+    >>> s = KKTSolver(sys.n, sys.m, sys.H_colptr, sys.H_rowidx, sys.J_rowptr, sys.J_colidx)
+    >>> s.factor(H_vals_cuda, J_vals_cuda, delta, gamma); dx, dy = s.solve(r_x_cuda, r_y_cuda)
+    """
+
+    def __init__(self, n, m, H_colptr, H_rowidx, J_rowptr, J_colidx, **options):
+        self.n, self.m = int(n), int(m)
+        self.nnz_h = int(np.asarray(H_colptr)[-1])
+        self.nnz_j = int(np.asarray(J_rowptr)[-1]) if m else 0
+        if options.get("precision") in ("mixed", KKT_MIXED):
+            # each refinement pass only needs a moderately accurate inner solve
+            # with the FP32 factor; FP64 refinement on K_delta does the rest
+            options.setdefault("cg_rtol", 1e-8)
+            options.setdefault("ir_maxit", 10)
+        self.opt = kkt_default_options(**options)
+        self.h = kkt_analyse(n, m, H_colptr, H_rowidx, J_rowptr, J_colidx, self.opt)
+
+    def factor(self, H_vals, J_vals, delta, gamma=-1.0, stream=None, check=True):
+        code = kkt_factor(self.h, H_vals, J_vals, delta, gamma, self.nnz_h, self.nnz_j, stream)
+        if check:
+            _check("kkt_factor", code)
+        return code
+
+    def solve(self, r_x, r_y, dx=None, dy=None, stream=None, check=True):
+        import torch
+        if dx is None:
+            dx = torch.empty(self.n, dtype=torch.float64, device=r_x.device)
+        if dy is None:
+            dy = torch.empty(self.m, dtype=torch.float64, device=r_x.device)
+        code = kkt_solve(self.h, r_x, r_y, dx, dy, self.n, self.m, stream)
+        if check:
+            _check("kkt_solve", code)
+        return dx, dy
+
+    def hsolve(self, b, stream=None):
+        import torch
+        x = torch.empty_like(b)
+        _check("kkt_hsolve", kkt_hsolve(self.h, b, x, self.n, stream))
+        return x
+
+    def factor_solve_host(self, H_vals, J_vals, delta, gamma, r_x, r_y, dx=None, dy=None, stream=None):
+        dx = np.zeros(self.n) if dx is None else dx
+        dy = np.zeros(self.m) if dy is None else dy
+        _check("kkt_factor_solve_host", kkt_factor_solve_host(self.h, H_vals, J_vals, delta, gamma, r_x, r_y,
+                                                               dx, dy, stream))
+        return dx, dy
+
+    @property
+    def info(self):
+        return kkt_get_info(self.h)
+
+    @property
+    def inertia_ok(self):
+        return kkt_inertia(self.h)
+
+    @property
+    def symbolic_info(self):
+        return kkt_symbolic_info_get(self.h)
+
+    def symbolic(self):
+        return kkt_get_symbolic(self.h)
+
+    def panels(self):
+        return kkt_get_factor_panels(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            kkt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,489 @@
+// C ABI of the KKT solver: handle management, device memory, and the
+// factor / solve / refinement drivers around the CUDA kernels.
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "kkt.h"
+#include "plan.hpp"
+#include "symbolic.hpp"
+
+using namespace kkt;
+
+namespace {
+
+struct DevArena {
+  std::vector<void*> ptrs;
+  size_t bytes = 0;
+  bool failed = false;
+  template <typename X>
+  X* alloc(size_t count) {
+    if (failed) return nullptr;
+    void* p = nullptr;
+    const size_t b = sizeof(X) * (count ? count : 1);
+    if (cudaMalloc(&p, b) != cudaSuccess) { cudaGetLastError(); failed = true; return nullptr; }
+    ptrs.push_back(p);
+    bytes += b;
+    return (X*)p;
+  }
+  template <typename X>
+  X* upload(const std::vector<X>& v) {
+    X* d = alloc<X>(v.size());
+    if (d && !v.empty() && cudaMemcpy(d, v.data(), sizeof(X) * v.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      failed = true;
+    }
+    return d;
+  }
+  void release() {
+    for (void* p : ptrs) cudaFree(p);
+    ptrs.clear();
+  }
+};
+
+}  // namespace
+
+struct kkt_handle_s {
+  kkt_options opt;
+  Symbolic S;
+  Plan P;
+  int device = 0;
+  int grid = 0;
+  int64_t nnzH = 0, nnzJ = 0;
+  DevArena mem;
+  // pattern / plan on the device
+  int32_t *sfirst, *sw, *snr, *sparent, *rel, *sn_rows, *perm;
+  int64_t *srow, *poff, *uoff;
+  int4 *it_trsm, *it_pupd, *it_syrk, *it_eadd;
+  int64_t *slot_pos, *src_ptr;
+  int32_t *srcA, *srcB;
+  int32_t *Jcol_perm, *JT_row, *JT_vidx, *Hs_col, *Hs_vidx, *JTo_row, *JTo_vidx, *J_colidx;
+  int64_t *JT_ptr, *Hs_ptr, *JTo_ptr, *J_rowptr;
+  int32_t *pc_first, *pc_w, *pc_ld, *pc_nchunk, *pc_need, *ch_piece, *ch_r0, *ch_nr, *ch_k, *ch_tgt;
+  int32_t *fwd_items, *bwd_items;
+  int64_t *pc_row, *pc_off, *pc_zoff, *ch_tptr;
+  // values and workspace
+  double *Hv, *Jv;
+  void *L, *U, *v, *zpart;
+  double *rhx, *p, *r, *y, *q, *bS, *red, *res_x, *res_y;
+  double *stage_rx, *stage_ry, *stage_dx, *stage_dy;
+  int* counters;   // fwd_arrive, fwd_done, bwd_arrive, bwd_done (npieces each), disp[3], bar[2]
+  DevStatus* dst;
+  DevStatus* hst = nullptr;  // pinned
+  // state
+  bool on_device = false;   // false for a host-only (symbolic) handle
+  bool factored = false;
+  double delta = 0, gamma = 0;
+  kkt_info info{};
+  int inertia_ok = 0;
+};
+
+static kkt_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return KKT_OK;
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? KKT_ERR_OOM : KKT_ERR_CUDA;
+}
+#define CK(x)                                   \
+  do {                                          \
+    cudaError_t e_ = (x);                       \
+    if (e_ != cudaSuccess) return cuda_status(e_); \
+  } while (0)
+
+extern "C" {
+
+void kkt_default_options(kkt_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->gamma = 1e4;
+  o->delta2 = 1e-9;
+  o->cg_rtol = 1e-12;
+  o->cg_maxit = 1000;
+  o->ir_maxit = 3;
+  o->ir_rtol = 1e-10;
+  o->precision = KKT_FP64;
+  o->ordering = 0;
+  o->relax_small = 16;
+  o->relax_num = 1;
+  o->relax_den = 10;
+  o->relax_wmax = 256;
+  o->solve_w = 128;
+  o->device = 0;
+  o->debug_stall_piece = -1;
+  o->spin_cycles = 0;
+}
+
+const char* kkt_status_string(kkt_status s) {
+  switch (s) {
+    case KKT_OK: return "ok";
+    case KKT_ERR_INVALID: return "invalid argument or pattern";
+    case KKT_ERR_NOT_SPD: return "H_delta is not positive definite (Cholesky pivot <= 0)";
+    case KKT_ERR_CG_BREAKDOWN: return "CG breakdown on the Schur complement";
+    case KKT_ERR_CG_MAXIT: return "CG reached its iteration limit";
+    case KKT_ERR_OOM: return "device out of memory";
+    case KKT_ERR_CUDA: return "CUDA error";
+    case KKT_ERR_TIMEOUT: return "bounded wait in a persistent kernel timed out";
+    case KKT_ERR_STATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+kkt_status kkt_destroy(kkt_handle h) {
+  if (!h) return KKT_ERR_INVALID;
+  if (!h->mem.ptrs.empty()) {
+    cudaSetDevice(h->device);
+    h->mem.release();
+  }
+  if (h->hst) cudaFreeHost(h->hst);
+  delete h;
+  return KKT_OK;
+}
+
+static kkt_status analyse_host(int64_t n, int64_t m, const int64_t* Hp, const int32_t* Hi, const int64_t* Jp,
+                               const int32_t* Ji, const kkt_options* opt, kkt_handle* out) {
+  if (!out) return KKT_ERR_INVALID;
+  *out = nullptr;
+  if (n < 1 || m < 0 || !Hp || !Hi || (m > 0 && (!Jp || !Ji))) return KKT_ERR_INVALID;
+  kkt_handle h = new (std::nothrow) kkt_handle_s();
+  if (!h) return KKT_ERR_OOM;
+  if (opt) h->opt = *opt; else kkt_default_options(&h->opt);
+  const kkt_options& o = h->opt;
+  if (o.solve_w < 32 || o.solve_w > 256 || o.relax_den <= 0 || o.precision < 0 || o.precision > 1) {
+    delete h;
+    return KKT_ERR_INVALID;
+  }
+  static const int64_t zero = 0;
+  if (m == 0) Jp = &zero;
+  RelaxParams rp;
+  rp.small = o.relax_small; rp.num = o.relax_num; rp.den = o.relax_den; rp.wmax = o.relax_wmax;
+  if (analyse_pattern(n, m, Hp, Hi, Jp, Ji, rp, o.ordering, h->S) != 0) { delete h; return KKT_ERR_INVALID; }
+  if (build_plan(h->S, Hp, Hi, Jp, Ji, o.solve_w, h->P) != 0) { delete h; return KKT_ERR_INVALID; }
+  if (o.debug_stall_piece >= 0 && o.debug_stall_piece < h->P.npieces) h->P.pc_need[o.debug_stall_piece] += 1;
+  h->nnzH = Hp[n];
+  h->nnzJ = Jp[m];
+  *out = h;
+  return KKT_OK;
+}
+
+kkt_status kkt_analyse_host(int64_t n, int64_t m, const int64_t* Hp, const int32_t* Hi, const int64_t* Jp,
+                            const int32_t* Ji, const kkt_options* opt, kkt_handle* out) {
+  return analyse_host(n, m, Hp, Hi, Jp, Ji, opt, out);
+}
+
+kkt_status kkt_analyse(int64_t n, int64_t m, const int64_t* Hp, const int32_t* Hi, const int64_t* Jp,
+                       const int32_t* Ji, const kkt_options* opt, kkt_handle* out) {
+  kkt_status s0 = analyse_host(n, m, Hp, Hi, Jp, Ji, opt, out);
+  if (s0) return s0;
+  kkt_handle h = *out;
+  *out = nullptr;
+  const kkt_options& o = h->opt;
+  static const int64_t zero = 0;
+  if (m == 0) Jp = &zero;
+  h->device = o.device;
+  if (cudaSetDevice(h->device) != cudaSuccess) { cudaGetLastError(); delete h; return KKT_ERR_CUDA; }
+  int coop = 0;
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device);
+  if (!coop) { delete h; return KKT_ERR_CUDA; }
+  const bool f64 = o.precision == KKT_FP64;
+  h->grid = f64 ? solve_grid_size<double>(h->device) : solve_grid_size<float>(h->device);
+  const Plan& P = h->P;
+  DevArena& A = h->mem;
+  auto as_int4 = [&](const std::vector<int32_t>& v) {
+    int4* d = A.alloc<int4>(v.size() / 4);
+    if (d && !v.empty() && cudaMemcpy(d, v.data(), sizeof(int32_t) * v.size(), cudaMemcpyHostToDevice)) A.failed = true;
+    return d;
+  };
+  h->sfirst = A.upload(P.sfirst); h->sw = A.upload(P.sw); h->snr = A.upload(P.snr);
+  h->sparent = A.upload(P.sparent); h->rel = A.upload(P.rel); h->sn_rows = A.upload(h->S.sn_rows);
+  h->perm = A.upload(h->S.perm);
+  h->srow = A.upload(P.srow); h->poff = A.upload(P.poff); h->uoff = A.upload(P.uoff);
+  h->it_trsm = as_int4(P.it_trsm); h->it_pupd = as_int4(P.it_pupd);
+  h->it_syrk = as_int4(P.it_syrk); h->it_eadd = as_int4(P.it_eadd);
+  h->slot_pos = A.upload(P.slot_pos); h->src_ptr = A.upload(P.src_ptr);
+  h->srcA = A.upload(P.srcA); h->srcB = A.upload(P.srcB);
+  h->Jcol_perm = A.upload(P.Jcol_perm); h->JT_ptr = A.upload(P.JT_ptr);
+  h->JT_row = A.upload(P.JT_row); h->JT_vidx = A.upload(P.JT_vidx);
+  h->Hs_ptr = A.upload(P.Hs_ptr); h->Hs_col = A.upload(P.Hs_col); h->Hs_vidx = A.upload(P.Hs_vidx);
+  h->JTo_ptr = A.upload(P.JTo_ptr); h->JTo_row = A.upload(P.JTo_row); h->JTo_vidx = A.upload(P.JTo_vidx);
+  h->J_rowptr = A.upload(std::vector<int64_t>(Jp, Jp + m + 1));
+  h->J_colidx = A.upload(std::vector<int32_t>(Ji, Ji + h->nnzJ));
+  h->pc_first = A.upload(P.pc_first); h->pc_w = A.upload(P.pc_w); h->pc_ld = A.upload(P.pc_ld);
+  h->pc_nchunk = A.upload(P.pc_nchunk); h->pc_need = A.upload(P.pc_need);
+  h->pc_row = A.upload(P.pc_row); h->pc_off = A.upload(P.pc_off); h->pc_zoff = A.upload(P.pc_zoff);
+  h->ch_piece = A.upload(P.ch_piece); h->ch_r0 = A.upload(P.ch_r0); h->ch_nr = A.upload(P.ch_nr);
+  h->ch_k = A.upload(P.ch_k); h->ch_tptr = A.upload(P.ch_tptr); h->ch_tgt = A.upload(P.ch_tgt);
+  h->fwd_items = A.upload(P.fwd_items); h->bwd_items = A.upload(P.bwd_items);
+  const size_t es = f64 ? sizeof(double) : sizeof(float);
+  h->Hv = A.alloc<double>(h->nnzH); h->Jv = A.alloc<double>(h->nnzJ);
+  h->L = A.alloc<char>(es * (size_t)P.panel_total);
+  h->U = A.alloc<char>(es * (size_t)P.u_total);
+  h->v = A.alloc<char>(es * (size_t)n);
+  h->zpart = A.alloc<char>(es * (size_t)P.z_total);
+  h->rhx = A.alloc<double>(n);
+  h->p = A.alloc<double>(m); h->r = A.alloc<double>(m); h->y = A.alloc<double>(m);
+  h->q = A.alloc<double>(m); h->bS = A.alloc<double>(m);
+  h->red = A.alloc<double>((size_t)std::max(h->grid, 296) * 4);
+  h->res_x = A.alloc<double>(n); h->res_y = A.alloc<double>(m);
+  h->stage_rx = A.alloc<double>(n); h->stage_ry = A.alloc<double>(m);
+  h->stage_dx = A.alloc<double>(n); h->stage_dy = A.alloc<double>(m);
+  h->counters = A.alloc<int>(4 * (size_t)P.npieces + 8);
+  h->dst = A.alloc<DevStatus>(1);
+  if (A.failed) { kkt_destroy(h); return KKT_ERR_OOM; }
+  if (cudaMallocHost(&h->hst, sizeof(DevStatus)) != cudaSuccess) { cudaGetLastError(); h->hst = nullptr; kkt_destroy(h); return KKT_ERR_OOM; }
+  if (cudaDeviceSynchronize() != cudaSuccess) { cudaGetLastError(); kkt_destroy(h); return KKT_ERR_CUDA; }
+  h->on_device = true;
+  *out = h;
+  return KKT_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ drivers
+static kkt_status reset_status(kkt_handle h, cudaStream_t st) {
+  std::memset(h->hst, 0, sizeof(DevStatus));
+  h->hst->fail_col = INT_MAX;
+  CK(cudaMemcpyAsync(h->dst, h->hst, sizeof(DevStatus), cudaMemcpyHostToDevice, st));
+  return KKT_OK;
+}
+
+static kkt_status read_status(kkt_handle h, cudaStream_t st) {
+  CK(cudaMemcpyAsync(h->hst, h->dst, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return KKT_OK;
+}
+
+template <typename T>
+static kkt_status factor_impl(kkt_handle h, cudaStream_t st) {
+  FacArgs<T> a;
+  a.sfirst = h->sfirst; a.sw = h->sw; a.snr = h->snr; a.sparent = h->sparent; a.rel = h->rel;
+  a.srow = h->srow; a.poff = h->poff; a.uoff = h->uoff;
+  a.Hv = h->Hv; a.Jv = h->Jv;
+  a.L = (T*)h->L; a.U = (T*)h->U; a.st = h->dst;
+  FacLists fl;
+  fl.it_trsm = h->it_trsm; fl.it_pupd = h->it_pupd; fl.it_syrk = h->it_syrk; fl.it_eadd = h->it_eadd;
+  fl.slot_pos = h->slot_pos; fl.src_ptr = h->src_ptr; fl.srcA = h->srcA; fl.srcB = h->srcB;
+  fl.nslot = (int64_t)h->P.slot_pos.size();
+  fl.panel_total = h->P.panel_total; fl.u_total = h->P.u_total;
+  fl.launches = &h->P.launches;
+  CK(launch_factor<T>(a, fl, h->delta, h->gamma, st));
+  return KKT_OK;
+}
+
+static kkt_status factor_common(kkt_handle h, double delta, double gamma, cudaStream_t st) {
+  h->factored = false;
+  h->inertia_ok = 0;
+  if (!(delta >= 0.0) || !std::isfinite(delta)) return KKT_ERR_INVALID;
+  if (gamma < 0) gamma = h->opt.gamma;
+  if (!std::isfinite(gamma)) return KKT_ERR_INVALID;
+  h->delta = delta;
+  h->gamma = gamma;
+  kkt_status s = reset_status(h, st);
+  if (s) return s;
+  s = h->opt.precision == KKT_FP64 ? factor_impl<double>(h, st) : factor_impl<float>(h, st);
+  if (s) return s;
+  if ((s = read_status(h, st))) return s;
+  if (h->hst->fail_col != INT_MAX) return KKT_ERR_NOT_SPD;
+  h->factored = true;
+  return KKT_OK;
+}
+
+template <typename T>
+static SolveArgs<T> solve_args(kkt_handle h) {
+  SolveArgs<T> a;
+  const Plan& P = h->P;
+  a.n = P.n; a.m = P.m;
+  a.sn_rows = h->sn_rows;
+  a.pc_first = h->pc_first; a.pc_w = h->pc_w; a.pc_ld = h->pc_ld; a.pc_nchunk = h->pc_nchunk;
+  a.pc_need = h->pc_need; a.pc_row = h->pc_row; a.pc_off = h->pc_off; a.pc_zoff = h->pc_zoff;
+  a.ch_piece = h->ch_piece; a.ch_r0 = h->ch_r0; a.ch_nr = h->ch_nr; a.ch_k = h->ch_k;
+  a.ch_tptr = h->ch_tptr; a.ch_tgt = h->ch_tgt;
+  a.fwd_items = h->fwd_items; a.bwd_items = h->bwd_items;
+  a.nitems = P.npieces + P.nchunks;
+  a.L = (const T*)h->L;
+  a.J_rowptr = h->J_rowptr; a.Jcol_perm = h->Jcol_perm; a.Jv = h->Jv;
+  a.JT_ptr = h->JT_ptr; a.JT_row = h->JT_row; a.JT_vidx = h->JT_vidx;
+  a.perm = h->perm;
+  a.gamma = h->gamma; a.delta2 = h->opt.delta2; a.rtol = h->opt.cg_rtol; a.maxit = h->opt.cg_maxit;
+  a.v = (T*)h->v; a.rhx = h->rhx; a.p = h->p; a.r = h->r; a.y = h->y; a.q = h->q; a.bS = h->bS;
+  a.zpart = (T*)h->zpart;
+  const int64_t np = P.npieces;
+  a.fwd_arrive = h->counters; a.fwd_done = h->counters + np;
+  a.bwd_arrive = h->counters + 2 * np; a.bwd_done = h->counters + 3 * np;
+  a.disp = h->counters + 4 * np; a.bar = h->counters + 4 * np + 4;
+  a.red = h->red; a.st = h->dst;
+  a.spin = h->opt.spin_cycles > 0 ? h->opt.spin_cycles : kSpinCycles;
+  return a;
+}
+
+template <typename T>
+static kkt_status solve_pass(kkt_handle h, const double* bx, const double* by, double* ox, double* oy,
+                             int accumulate, int mode, cudaStream_t st) {
+  CK(cudaMemsetAsync(h->counters, 0, sizeof(int) * (4 * (size_t)h->P.npieces + 8), st));
+  SolveArgs<T> a = solve_args<T>(h);
+  a.bx = bx; a.by = by; a.ox = ox; a.oy = oy; a.accumulate = accumulate; a.mode = mode;
+  CK(launch_solve<T>(a, h->grid, st));
+  return KKT_OK;
+}
+
+static kkt_status residual(kkt_handle h, const double* bx, const double* by, const double* x,
+                           const double* y, cudaStream_t st) {
+  ResArgs r;
+  r.n = h->P.n; r.m = h->P.m;
+  r.Hs_ptr = h->Hs_ptr; r.Hs_col = h->Hs_col; r.Hs_vidx = h->Hs_vidx;
+  r.J_rowptr = h->J_rowptr; r.J_colidx = h->J_colidx;
+  r.JT_ptr = h->JTo_ptr; r.JT_row = h->JTo_row; r.JT_vidx = h->JTo_vidx;
+  r.Hv = h->Hv; r.Jv = h->Jv; r.delta = h->delta;
+  r.bx = bx; r.by = by; r.x = x; r.y = y; r.res_x = h->res_x; r.res_y = h->res_y;
+  r.red = h->red; r.st = h->dst;
+  CK(launch_residual(r, st));
+  return KKT_OK;
+}
+
+static kkt_status solve_common(kkt_handle h, const double* rx, const double* ry, double* dx, double* dy,
+                               cudaStream_t st) {
+  if (!h->factored) return KKT_ERR_STATE;
+  h->inertia_ok = 0;
+  std::memset(&h->info, 0, sizeof(h->info));
+  const bool f64 = h->opt.precision == KKT_FP64;
+  kkt_status s = reset_status(h, st);
+  if (s) return s;
+  int total_it = 0, brk = 0;
+  for (int pass = 0;; pass++) {
+    const double* bx = pass == 0 ? rx : h->res_x;
+    const double* by = pass == 0 ? ry : h->res_y;
+    s = f64 ? solve_pass<double>(h, bx, by, dx, dy, pass > 0, 0, st)
+            : solve_pass<float>(h, bx, by, dx, dy, pass > 0, 0, st);
+    if (s) return s;
+    if ((s = residual(h, rx, ry, dx, dy, st))) return s;
+    if ((s = read_status(h, st))) return s;
+    const DevStatus& d = *h->hst;
+    total_it += d.cg_iters;
+    brk |= d.breakdown;
+    h->info.cg_iters = total_it;
+    h->info.ir_steps = pass;
+    h->info.cg_status = d.cg_status;
+    h->info.delta2_used = brk;
+    h->info.rr = d.rr;
+    h->info.be = d.be;
+    if (d.abort) return KKT_ERR_TIMEOUT;
+    if (d.cg_status == 3) return KKT_ERR_CG_BREAKDOWN;
+    if (d.cg_status == 4) return KKT_ERR_CG_MAXIT;
+    if (!(d.rr > h->opt.ir_rtol) || pass >= h->opt.ir_maxit) break;
+    h->hst->cg_iters = 0;
+    h->hst->breakdown = 0;
+    CK(cudaMemcpyAsync(h->dst, h->hst, sizeof(DevStatus), cudaMemcpyHostToDevice, st));
+  }
+  h->inertia_ok = brk ? 0 : 1;
+  return KKT_OK;
+}
+
+extern "C" {
+
+kkt_status kkt_factor(kkt_handle h, const double* H_vals, const double* J_vals, double delta, double gamma,
+                      void* stream) {
+  if (!h || !H_vals || (h->nnzJ > 0 && !J_vals)) return KKT_ERR_INVALID;
+  if (!h->on_device) return KKT_ERR_STATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaSetDevice(h->device));
+  CK(cudaMemcpyAsync(h->Hv, H_vals, sizeof(double) * h->nnzH, cudaMemcpyDeviceToDevice, st));
+  if (h->nnzJ) CK(cudaMemcpyAsync(h->Jv, J_vals, sizeof(double) * h->nnzJ, cudaMemcpyDeviceToDevice, st));
+  return factor_common(h, delta, gamma, st);
+}
+
+kkt_status kkt_solve(kkt_handle h, const double* r_x, const double* r_y, double* dx, double* dy, void* stream) {
+  if (!h || !r_x || !dx || (h->P.m > 0 && (!r_y || !dy))) return KKT_ERR_INVALID;
+  if (!h->on_device) return KKT_ERR_STATE;
+  CK(cudaSetDevice(h->device));
+  return solve_common(h, r_x, r_y, dx, dy, (cudaStream_t)stream);
+}
+
+kkt_status kkt_factor_solve_host(kkt_handle h, const double* H_vals, const double* J_vals, double delta,
+                                 double gamma, const double* r_x, const double* r_y, double* dx, double* dy,
+                                 void* stream) {
+  if (!h || !H_vals || !r_x || !dx || (h->P.m > 0 && (!J_vals || !r_y || !dy))) return KKT_ERR_INVALID;
+  if (!h->on_device) return KKT_ERR_STATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = h->P.n, m = h->P.m;
+  CK(cudaSetDevice(h->device));
+  CK(cudaMemcpyAsync(h->Hv, H_vals, sizeof(double) * h->nnzH, cudaMemcpyHostToDevice, st));
+  if (h->nnzJ) CK(cudaMemcpyAsync(h->Jv, J_vals, sizeof(double) * h->nnzJ, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(h->stage_rx, r_x, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+  if (m) CK(cudaMemcpyAsync(h->stage_ry, r_y, sizeof(double) * m, cudaMemcpyHostToDevice, st));
+  kkt_status s = factor_common(h, delta, gamma, st);
+  if (s) return s;
+  s = solve_common(h, h->stage_rx, h->stage_ry, h->stage_dx, h->stage_dy, st);
+  CK(cudaMemcpyAsync(dx, h->stage_dx, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+  if (m) CK(cudaMemcpyAsync(dy, h->stage_dy, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return s;
+}
+
+kkt_status kkt_hsolve(kkt_handle h, const double* b, double* x, void* stream) {
+  if (!h || !b || !x) return KKT_ERR_INVALID;
+  if (!h->factored) return KKT_ERR_STATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaSetDevice(h->device));
+  kkt_status s = reset_status(h, st);
+  if (s) return s;
+  s = h->opt.precision == KKT_FP64 ? solve_pass<double>(h, b, b, x, x, 0, 1, st)
+                                   : solve_pass<float>(h, b, b, x, x, 0, 1, st);
+  if (s) return s;
+  if ((s = read_status(h, st))) return s;
+  return h->hst->abort ? KKT_ERR_TIMEOUT : KKT_OK;
+}
+
+kkt_status kkt_get_info(kkt_handle h, kkt_info* info) {
+  if (!h || !info) return KKT_ERR_INVALID;
+  *info = h->info;
+  return KKT_OK;
+}
+
+kkt_status kkt_inertia(kkt_handle h, int32_t* ok) {
+  if (!h || !ok) return KKT_ERR_INVALID;
+  *ok = (h->factored && h->inertia_ok) ? 1 : 0;
+  return KKT_OK;
+}
+
+kkt_status kkt_symbolic_info_get(kkt_handle h, kkt_symbolic_info* o) {
+  if (!h || !o) return KKT_ERR_INVALID;
+  std::memset(o, 0, sizeof(*o));
+  o->n = h->S.n; o->m = h->S.m; o->nsuper = h->S.ns; o->nnz_l = h->S.nnzL;
+  o->panel_entries = h->P.panel_total; o->update_entries = h->P.u_total;
+  o->sn_rows_total = (int64_t)h->S.sn_rows.size();
+  o->npieces = h->P.npieces; o->nchunks = h->P.nchunks; o->nlevels = h->P.nlevels;
+  o->flops = h->S.flops;
+  o->device_bytes = (double)h->mem.bytes;
+  return KKT_OK;
+}
+
+kkt_status kkt_get_symbolic(kkt_handle h, int32_t* amd, int32_t* perm, int32_t* parent, int64_t* colcount,
+                            int32_t* sn_start, int64_t* sn_rowptr, int32_t* sn_rows, int32_t* sn_parent) {
+  if (!h) return KKT_ERR_INVALID;
+  const Symbolic& S = h->S;
+  auto cp = [](auto* dst, const auto& v) { if (dst && !v.empty()) std::memcpy(dst, v.data(), sizeof(v[0]) * v.size()); };
+  cp(amd, S.amd); cp(perm, S.perm); cp(parent, S.parent); cp(colcount, S.colcount);
+  cp(sn_start, S.sn_start); cp(sn_rowptr, S.sn_rowptr); cp(sn_rows, S.sn_rows); cp(sn_parent, S.sn_parent);
+  return KKT_OK;
+}
+
+kkt_status kkt_get_factor_panels(kkt_handle h, double* out) {
+  if (!h || !out) return KKT_ERR_INVALID;
+  if (!h->factored) return KKT_ERR_STATE;
+  CK(cudaSetDevice(h->device));
+  const size_t cnt = (size_t)h->P.panel_total;
+  if (h->opt.precision == KKT_FP64) {
+    CK(cudaMemcpy(out, h->L, sizeof(double) * cnt, cudaMemcpyDeviceToHost));
+  } else {
+    std::vector<float> tmp(cnt);
+    CK(cudaMemcpy(tmp.data(), h->L, sizeof(float) * cnt, cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < cnt; i++) out[i] = tmp[i];
+  }
+  return KKT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,262 @@
+// Numeric supernodal (multifrontal) Cholesky of
+//   A = P (H~ + delta I + gamma J^T J) P^T = L L^T
+// (Sec. 4, eq. gamma; Sec. 4.1 H_delta; Algorithm 1: "Try L L^T = chol(H_delta)").
+//
+// Layout: supernode s owns a column-major panel of snr[s] x sw[s] entries
+// (its rows = its columns followed by the rows below, ld = snr[s]) and an
+// update matrix U_s of rb x rb (rb = snr[s] - sw[s], ld = rb) that first
+// collects the children's contributions and then holds
+//   U_s = (children's updates) - L21 L21^T,
+// which is extend-added into the parent's front. Fronts of one tree level are
+// processed together; siblings add into the same parent entries with device
+// atomics, so the summation order of those contributions is not fixed.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "plan.hpp"
+
+namespace kkt {
+
+// ------------------------------------------------------------------ assembly
+// Panel slot t <- sum of its sources: H~ entries, delta on the diagonal and
+// gamma * J_ra * J_rb for each pair of entries of each row r of J.
+template <typename T>
+__global__ void k_assemble(int64_t nslot, const int64_t* __restrict__ slot_pos,
+                           const int64_t* __restrict__ src_ptr, const int32_t* __restrict__ srcA,
+                           const int32_t* __restrict__ srcB, const double* __restrict__ Hv,
+                           const double* __restrict__ Jv, double delta, double gamma, T* __restrict__ L) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nslot; t += (int64_t)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    for (int64_t q = src_ptr[t]; q < src_ptr[t + 1]; q++) {
+      const int32_t a = srcA[q], b = srcB[q];
+      v += (b == -1) ? Hv[a] : (b == -2 ? delta : gamma * Jv[a] * Jv[b]);
+    }
+    L[slot_pos[t]] = (T)v;
+  }
+}
+
+// ------------------------------------------------------------- POTRF + TRSM
+// Column block kb (kPB columns) of the fronts listed in items (s, row tile):
+// every CTA factors the kPB x kPB diagonal tile in shared memory (redundantly)
+// and solves its tile of kTR rows below it; tile 0 also stores the diagonal.
+template <typename T>
+__global__ void __launch_bounds__(kTR) k_potrf_trsm(const int4* __restrict__ items, int kb, FacArgs<T> a) {
+  __shared__ T D[kPB][kPB + 1];
+  __shared__ int bad;
+  const int4 it = items[blockIdx.x];
+  const int s = it.x, t = it.y;
+  const int w = a.sw[s], nr = a.snr[s];
+  const int c0 = kb * kPB;
+  const int bw = min(kPB, w - c0);
+  T* P = a.L + a.poff[s];
+  const int tid = threadIdx.x;
+  if (tid == 0) bad = 0;
+  for (int e = tid; e < kPB * kPB; e += blockDim.x) {
+    const int i = e % kPB, j = e / kPB;
+    D[i][j] = (i < bw && j <= i) ? P[(int64_t)(c0 + i) + (int64_t)(c0 + j) * nr] : T(0);
+  }
+  __syncthreads();
+  for (int j = 0; j < bw; j++) {
+    if (tid == 0) {
+      T d = D[j][j];
+      if (!(d > T(0)) || !isfinite((double)d)) {
+        if (t == 0) atomicMin(&a.st->fail_col, a.sfirst[s] + c0 + j);
+        bad = 1;
+        d = T(1);
+      }
+      D[j][j] = sqrt(d);
+    }
+    __syncthreads();
+    for (int i = j + 1 + tid; i < bw; i += blockDim.x) D[i][j] /= D[j][j];
+    __syncthreads();
+    const int rem = bw - j - 1;
+    for (int e = tid; e < rem * rem; e += blockDim.x) {
+      const int i = j + 1 + e % rem, k = j + 1 + e / rem;
+      if (k <= i) D[i][k] -= D[i][j] * D[k][j];
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    for (int e = tid; e < kPB * kPB; e += blockDim.x) {
+      const int i = e % kPB, j = e / kPB;
+      if (i < bw && j <= i) P[(int64_t)(c0 + i) + (int64_t)(c0 + j) * nr] = D[i][j];
+    }
+  }
+  const int r = c0 + bw + t * kTR + tid;
+  if (r < nr) {
+    T x[kPB];
+#pragma unroll
+    for (int k = 0; k < kPB; k++) x[k] = (k < bw) ? P[(int64_t)r + (int64_t)(c0 + k) * nr] : T(0);
+#pragma unroll
+    for (int j = 0; j < kPB; j++) {
+      if (j < bw) {
+        T sacc = x[j];
+#pragma unroll
+        for (int k = 0; k < j; k++) sacc -= x[k] * D[j][k];
+        x[j] = sacc / D[j][j];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kPB; k++)
+      if (k < bw) P[(int64_t)r + (int64_t)(c0 + k) * nr] = x[k];
+  }
+}
+
+// ------------------------------------------------------- in-panel update
+// Right-looking update of the panel columns after block kb:
+//   P[i, j] -= sum_k P[i, c0+k] P[j, c0+k],  j >= c0+bw, i >= j.
+// items (s, row tile of kUR rows, column tile of kPB columns).
+template <typename T>
+__global__ void __launch_bounds__(256) k_panel_update(const int4* __restrict__ items, int kb, FacArgs<T> a) {
+  __shared__ T As[kUR][kPB + 1];
+  __shared__ T Bs[kPB][kPB + 1];
+  const int4 it = items[blockIdx.x];
+  const int s = it.x, rt = it.y, ct = it.z;
+  const int w = a.sw[s], nr = a.snr[s];
+  const int c0 = kb * kPB;
+  const int bw = min(kPB, w - c0);
+  const int cstart = c0 + bw + ct * kPB;
+  const int cw = min(kPB, w - cstart);
+  const int rstart = cstart + rt * kUR;
+  const int rn = min(kUR, nr - rstart);
+  T* P = a.L + a.poff[s];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < kUR * kPB; e += blockDim.x) {
+    const int i = e % kUR, k = e / kUR;
+    As[i][k] = (i < rn && k < bw) ? P[(int64_t)(rstart + i) + (int64_t)(c0 + k) * nr] : T(0);
+  }
+  for (int e = tid; e < kPB * kPB; e += blockDim.x) {
+    const int j = e % kPB, k = e / kPB;
+    Bs[j][k] = (j < cw && k < bw) ? P[(int64_t)(cstart + j) + (int64_t)(c0 + k) * nr] : T(0);
+  }
+  __syncthreads();
+  const int i = tid % kUR;            // consecutive threads -> consecutive rows
+  const int jg = tid / kUR;           // 4 groups of 8 columns
+  T acc[8];
+#pragma unroll
+  for (int q = 0; q < 8; q++) acc[q] = T(0);
+  for (int k = 0; k < bw; k++) {
+    const T av = As[i][k];
+#pragma unroll
+    for (int q = 0; q < 8; q++) acc[q] += av * Bs[jg * 8 + q][k];
+  }
+#pragma unroll
+  for (int q = 0; q < 8; q++) {
+    const int j = jg * 8 + q;
+    if (i < rn && j < cw && rstart + i >= cstart + j)
+      P[(int64_t)(rstart + i) + (int64_t)(cstart + j) * nr] -= acc[q];
+  }
+}
+
+// ---------------------------------------------------------------- SYRK
+// U_s -= L21 L21^T on 64 x 64 tiles (ti >= tj), k = panel width.
+template <typename T>
+__global__ void __launch_bounds__(256) k_syrk(const int4* __restrict__ items, FacArgs<T> a) {
+  constexpr int KC = 16;
+  __shared__ T As[KC][kST + 1];
+  __shared__ T Bs[KC][kST + 1];
+  const int4 it = items[blockIdx.x];
+  const int s = it.x, ti = it.y, tj = it.z;
+  const int w = a.sw[s], nr = a.snr[s];
+  const int rb = nr - w;
+  const T* P = a.L + a.poff[s];
+  T* U = a.U + a.uoff[s];
+  const int i0 = ti * kST, j0 = tj * kST;
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  T acc[4][4];
+#pragma unroll
+  for (int x = 0; x < 4; x++)
+#pragma unroll
+    for (int y = 0; y < 4; y++) acc[x][y] = T(0);
+  for (int k0 = 0; k0 < w; k0 += KC) {
+    for (int e = tid; e < KC * kST; e += blockDim.x) {
+      const int r = e % kST, k = e / kST;
+      const bool kin = k0 + k < w;
+      As[k][r] = (kin && i0 + r < rb) ? P[(int64_t)(w + i0 + r) + (int64_t)(k0 + k) * nr] : T(0);
+      Bs[k][r] = (kin && j0 + r < rb) ? P[(int64_t)(w + j0 + r) + (int64_t)(k0 + k) * nr] : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < KC; k++) {
+      T av[4], bv[4];
+#pragma unroll
+      for (int x = 0; x < 4; x++) av[x] = As[k][tx + 16 * x];
+#pragma unroll
+      for (int y = 0; y < 4; y++) bv[y] = Bs[k][ty + 16 * y];
+#pragma unroll
+      for (int x = 0; x < 4; x++)
+#pragma unroll
+        for (int y = 0; y < 4; y++) acc[x][y] += av[x] * bv[y];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int y = 0; y < 4; y++)
+#pragma unroll
+    for (int x = 0; x < 4; x++) {
+      const int gi = i0 + tx + 16 * x, gj = j0 + ty + 16 * y;
+      if (gi < rb && gj < rb && gi >= gj) U[(int64_t)gi + (int64_t)gj * rb] -= acc[x][y];
+    }
+}
+
+// --------------------------------------------------------------- extend-add
+// Adds U_s into the parent's front: entry (i, j) of U_s goes to position
+// (rel[i], rel[j]) of the parent's rows, i.e. the parent's panel when rel[j]
+// is one of its columns, else its update matrix.
+template <typename T>
+__global__ void __launch_bounds__(256) k_extend_add(const int4* __restrict__ items, FacArgs<T> a) {
+  const int4 it = items[blockIdx.x];
+  const int s = it.x, ct = it.y;
+  const int p = a.sparent[s];
+  const int w = a.sw[s], rb = a.snr[s] - w;
+  const int wp = a.sw[p], nrp = a.snr[p], rbp = nrp - wp;
+  const int32_t* rel = a.rel + a.srow[s] + w;
+  const T* Us = a.U + a.uoff[s];
+  T* Pp = a.L + a.poff[p];
+  T* Up = a.U + a.uoff[p];
+  for (int jj = 0; jj < kEC; jj++) {
+    const int j = ct * kEC + jj;
+    if (j >= rb) break;
+    const int b = rel[j];
+    for (int i = j + threadIdx.x; i < rb; i += blockDim.x) {
+      const int ai = rel[i];
+      const T v = Us[(int64_t)i + (int64_t)j * rb];
+      if (b < wp) atomicAdd(&Pp[(int64_t)ai + (int64_t)b * nrp], v);
+      else atomicAdd(&Up[(int64_t)(ai - wp) + (int64_t)(b - wp) * rbp], v);
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_factor(const FacArgs<T>& a, const FacLists& fl, double delta, double gamma,
+                          cudaStream_t st) {
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(a.L, 0, sizeof(T) * (size_t)fl.panel_total, st))) return e;
+  if (fl.u_total && (e = cudaMemsetAsync(a.U, 0, sizeof(T) * (size_t)fl.u_total, st))) return e;
+  {
+    const int threads = 256;
+    int64_t blocks = (fl.nslot + threads - 1) / threads;
+    if (blocks > 148 * 64) blocks = 148 * 64;
+    if (blocks < 1) blocks = 1;
+    k_assemble<T><<<(unsigned)blocks, threads, 0, st>>>(fl.nslot, fl.slot_pos, fl.src_ptr, fl.srcA, fl.srcB,
+                                                         a.Hv, a.Jv, delta, gamma, a.L);
+  }
+  for (const Launch& L : *fl.launches) {
+    if (L.cnt <= 0) continue;
+    switch (L.kind) {
+      case 0: k_potrf_trsm<T><<<(unsigned)L.cnt, kTR, 0, st>>>(fl.it_trsm + L.off, L.kb, a); break;
+      case 1: k_panel_update<T><<<(unsigned)L.cnt, 256, 0, st>>>(fl.it_pupd + L.off, L.kb, a); break;
+      case 2: k_syrk<T><<<(unsigned)L.cnt, 256, 0, st>>>(fl.it_syrk + L.off, a); break;
+      case 3: k_extend_add<T><<<(unsigned)L.cnt, 256, 0, st>>>(fl.it_eadd + L.off, a); break;
+    }
+  }
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_factor<double>(const FacArgs<double>&, const FacLists&, double, double, cudaStream_t);
+template cudaError_t launch_factor<float>(const FacArgs<float>&, const FacLists&, double, double, cudaStream_t);
+
+}  // namespace kkt

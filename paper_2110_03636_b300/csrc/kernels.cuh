@@ -1,0 +1,98 @@
+// Argument blocks passed by value to the KKT kernels, and the host launchers.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "common.cuh"
+#include "plan.hpp"
+
+namespace kkt {
+
+template <typename T>
+struct FacArgs {
+  const int32_t *sfirst, *sw, *snr, *sparent, *rel;
+  const int64_t *srow, *poff, *uoff;
+  const double *Hv, *Jv;
+  T* L;
+  T* U;
+  DevStatus* st;
+};
+
+struct FacLists {
+  const int4 *it_trsm, *it_pupd, *it_syrk, *it_eadd;
+  const int64_t *slot_pos, *src_ptr;
+  const int32_t *srcA, *srcB;
+  int64_t nslot, panel_total, u_total;
+  const std::vector<Launch>* launches;
+};
+
+template <typename T>
+cudaError_t launch_factor(const FacArgs<T>& a, const FacLists& fl, double delta, double gamma, cudaStream_t st);
+
+// Persistent CG on the Schur complement (plus the two direct solves).
+template <typename T>
+struct SolveArgs {
+  int64_t n, m;
+  // solve DAG
+  const int32_t* sn_rows;
+  const int32_t *pc_first, *pc_w, *pc_ld, *pc_nchunk, *pc_need;
+  const int64_t *pc_row, *pc_off, *pc_zoff;
+  const int32_t *ch_piece, *ch_r0, *ch_nr, *ch_k;
+  const int64_t* ch_tptr;
+  const int32_t* ch_tgt;
+  const int32_t *fwd_items, *bwd_items;
+  int64_t nitems;
+  const T* L;
+  // J (CSR, permuted column labels) and J^T (by permuted column)
+  const int64_t* J_rowptr;
+  const int32_t* Jcol_perm;
+  const double* Jv;
+  const int64_t* JT_ptr;
+  const int32_t *JT_row, *JT_vidx;
+  const int32_t* perm;
+  // right-hand side and outputs (original labels)
+  const double *bx, *by;
+  double *ox, *oy;
+  int32_t accumulate;   // 1: ox += result, oy += result
+  int32_t mode;         // 0: full KKT solve; 1: ox = H^-1 bx only
+  double gamma, delta2, rtol;
+  int32_t maxit;
+  // workspace
+  T* v;
+  double *rhx, *p, *r, *y, *q, *bS;
+  T* zpart;
+  int *fwd_arrive, *fwd_done, *bwd_arrive, *bwd_done;
+  int* disp;   // [3]
+  int* bar;    // [2]
+  double* red; // [grid * 4]
+  DevStatus* st;
+  long long spin;  // bound of every wait, in clock cycles
+};
+
+template <typename T>
+cudaError_t launch_solve(const SolveArgs<T>& a, int grid, cudaStream_t st);
+template <typename T>
+int solve_grid_size(int device);
+
+// FP64 residual of K_delta = [H~ + delta I, J^T; J, 0] (original labels):
+// res = b - K x, and norms into DevStatus (rr, be, ...).
+struct ResArgs {
+  int64_t n, m;
+  const int64_t* Hs_ptr;
+  const int32_t *Hs_col, *Hs_vidx;
+  const int64_t* J_rowptr;
+  const int32_t* J_colidx;
+  const int64_t* JT_ptr;
+  const int32_t *JT_row, *JT_vidx;
+  const double *Hv, *Jv;
+  double delta;
+  const double *bx, *by, *x, *y;
+  double *res_x, *res_y;
+  double* red;   // scratch [blocks * 4]
+  DevStatus* st;
+};
+cudaError_t launch_residual(const ResArgs& a, cudaStream_t st);
+
+}  // namespace kkt

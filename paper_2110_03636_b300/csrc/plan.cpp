@@ -1,0 +1,268 @@
+#include "plan.hpp"
+
+#include <algorithm>
+#include <numeric>
+
+namespace kkt {
+
+static inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const int64_t* Jp,
+               const int32_t* Ji, int32_t solve_w, Plan& P) {
+  P = Plan();
+  const int64_t n = S.n, m = S.m, ns = S.ns;
+  P.n = n; P.m = m; P.ns = ns;
+  P.sfirst.resize(ns); P.sw.resize(ns); P.snr.resize(ns); P.srow.resize(ns);
+  P.poff.resize(ns); P.uoff.resize(ns); P.sparent = S.sn_parent;
+  std::vector<int32_t> col2sn(n);
+  int64_t po = 0, uo = 0;
+  for (int64_t s = 0; s < ns; s++) {
+    P.sfirst[s] = S.sn_start[s];
+    P.sw[s] = S.sn_start[s + 1] - S.sn_start[s];
+    P.snr[s] = (int32_t)(S.sn_rowptr[s + 1] - S.sn_rowptr[s]);
+    P.srow[s] = S.sn_rowptr[s];
+    P.poff[s] = po;
+    po += (int64_t)P.sw[s] * P.snr[s];
+    const int64_t rb = P.snr[s] - P.sw[s];
+    P.uoff[s] = uo;
+    uo += rb * rb;
+    for (int32_t j = S.sn_start[s]; j < S.sn_start[s + 1]; j++) col2sn[j] = (int32_t)s;
+  }
+  P.panel_total = po;
+  P.u_total = uo;
+  // relative indices of each child's below rows in its parent's row list
+  P.rel.assign(S.sn_rows.size(), -1);
+  for (int64_t s = 0; s < ns; s++) {
+    const int32_t p = P.sparent[s];
+    if (p < 0) continue;
+    const int32_t* R = S.sn_rows.data() + P.srow[p];
+    int64_t q = 0;
+    for (int64_t k = P.sw[s]; k < P.snr[s]; k++) {
+      const int32_t r = S.sn_rows[P.srow[s] + k];
+      while (q < P.snr[p] && R[q] < r) q++;
+      if (q >= P.snr[p] || R[q] != r) return 2;   // structure violated (cannot happen)
+      P.rel[P.srow[s] + k] = (int32_t)q;
+    }
+  }
+  // levels (height above the leaves)
+  std::vector<int32_t> level(ns, 0);
+  for (int64_t s = 0; s < ns; s++)
+    if (P.sparent[s] >= 0) level[P.sparent[s]] = std::max(level[P.sparent[s]], level[s] + 1);
+  P.nlevels = ns ? *std::max_element(level.begin(), level.end()) + 1 : 0;
+  std::vector<std::vector<int32_t>> bylev(P.nlevels);
+  for (int64_t s = 0; s < ns; s++) bylev[level[s]].push_back((int32_t)s);
+  for (int32_t L = 0; L < P.nlevels; L++) {
+    const auto& F = bylev[L];
+    int32_t wmax = 0;
+    for (int32_t s : F) wmax = std::max(wmax, P.sw[s]);
+    for (int32_t kb = 0; kb * kPB < wmax; kb++) {
+      const int64_t o0 = (int64_t)P.it_trsm.size() / 4;
+      for (int32_t s : F) {
+        const int32_t c0 = kb * kPB;
+        if (c0 >= P.sw[s]) continue;
+        const int32_t bw = std::min(kPB, P.sw[s] - c0);
+        const int64_t below = P.snr[s] - c0 - bw;
+        const int64_t nt = std::max<int64_t>(1, cdiv(below, kTR));
+        for (int64_t t = 0; t < nt; t++) { P.it_trsm.insert(P.it_trsm.end(), {s, (int32_t)t, 0, 0}); }
+      }
+      P.launches.push_back({0, kb, o0, (int64_t)P.it_trsm.size() / 4 - o0});
+      const int64_t o1 = (int64_t)P.it_pupd.size() / 4;
+      for (int32_t s : F) {
+        const int32_t c0 = kb * kPB;
+        if (c0 >= P.sw[s]) continue;
+        const int32_t bw = std::min(kPB, P.sw[s] - c0);
+        const int32_t jstart = c0 + bw;
+        for (int32_t ct = 0; jstart + ct * kPB < P.sw[s]; ct++) {
+          const int32_t cstart = jstart + ct * kPB;
+          const int64_t nrt = cdiv(P.snr[s] - cstart, kUR);
+          for (int64_t rt = 0; rt < nrt; rt++) P.it_pupd.insert(P.it_pupd.end(), {s, (int32_t)rt, ct, 0});
+        }
+      }
+      const int64_t c1 = (int64_t)P.it_pupd.size() / 4 - o1;
+      if (c1) P.launches.push_back({1, kb, o1, c1});
+    }
+    const int64_t o2 = (int64_t)P.it_syrk.size() / 4;
+    for (int32_t s : F) {
+      const int64_t rb = P.snr[s] - P.sw[s];
+      const int64_t nt = cdiv(rb, kST);
+      for (int64_t ti = 0; ti < nt; ti++)
+        for (int64_t tj = 0; tj <= ti; tj++) P.it_syrk.insert(P.it_syrk.end(), {s, (int32_t)ti, (int32_t)tj, 0});
+    }
+    const int64_t c2 = (int64_t)P.it_syrk.size() / 4 - o2;
+    if (c2) P.launches.push_back({2, 0, o2, c2});
+    const int64_t o3 = (int64_t)P.it_eadd.size() / 4;
+    for (int32_t s : F) {
+      if (P.sparent[s] < 0) continue;
+      const int64_t rb = P.snr[s] - P.sw[s];
+      for (int64_t ct = 0; ct < cdiv(rb, kEC); ct++) P.it_eadd.insert(P.it_eadd.end(), {s, (int32_t)ct, 0, 0});
+    }
+    const int64_t c3 = (int64_t)P.it_eadd.size() / 4 - o3;
+    if (c3) P.launches.push_back({3, 0, o3, c3});
+  }
+  // ---------------------------------------------------------- assembly map
+  // slot of (row, col) in final labels (row >= col)
+  auto slot_of = [&](int32_t r, int32_t c) -> int64_t {
+    const int32_t s = col2sn[c];
+    const int32_t* R = S.sn_rows.data() + P.srow[s];
+    const int32_t* pos = std::lower_bound(R, R + P.snr[s], r);
+    if (pos == R + P.snr[s] || *pos != r) return (int64_t)-1;   // not in the structure
+    return P.poff[s] + (int64_t)(c - P.sfirst[s]) * P.snr[s] + (pos - R);
+  };
+  struct Src { int64_t slot; int32_t a, b; };
+  std::vector<Src> src;
+  src.reserve((size_t)Hp[n] + n);
+  for (int64_t j = 0; j < n; j++)
+    for (int64_t q = Hp[j]; q < Hp[j + 1]; q++) {
+      int32_t a = S.iperm[Hi[q]], b = S.iperm[j];
+      if (a < b) std::swap(a, b);
+      src.push_back({slot_of(a, b), (int32_t)q, -1});
+    }
+  for (int64_t j = 0; j < n; j++) src.push_back({slot_of(j, j), 0, -2});
+  for (int64_t r = 0; r < m; r++)
+    for (int64_t q1 = Jp[r]; q1 < Jp[r + 1]; q1++)
+      for (int64_t q2 = q1; q2 < Jp[r + 1]; q2++) {
+        int32_t a = S.iperm[Ji[q1]], b = S.iperm[Ji[q2]];
+        if (a < b) std::swap(a, b);
+        src.push_back({slot_of(a, b), (int32_t)q1, (int32_t)q2});
+      }
+  for (const Src& x : src)
+    if (x.slot < 0) return 3;
+  std::stable_sort(src.begin(), src.end(), [](const Src& x, const Src& y) { return x.slot < y.slot; });
+  for (size_t t = 0; t < src.size(); t++) {
+    if (t == 0 || src[t].slot != src[t - 1].slot) {
+      P.slot_pos.push_back(src[t].slot);
+      P.src_ptr.push_back((int64_t)t);
+    }
+    P.srcA.push_back(src[t].a);
+    P.srcB.push_back(src[t].b);
+  }
+  P.src_ptr.push_back((int64_t)src.size());
+  // ---------------------------------------------------------- J / J^T maps
+  const int64_t nnzJ = m > 0 ? Jp[m] : 0;
+  P.Jcol_perm.resize(nnzJ);
+  for (int64_t q = 0; q < nnzJ; q++) P.Jcol_perm[q] = S.iperm[Ji[q]];
+  auto transpose = [&](bool permuted, std::vector<int64_t>& tp, std::vector<int32_t>& trow, std::vector<int32_t>& tv) {
+    tp.assign(n + 1, 0);
+    for (int64_t q = 0; q < nnzJ; q++) tp[(permuted ? P.Jcol_perm[q] : Ji[q]) + 1]++;
+    for (int64_t i = 0; i < n; i++) tp[i + 1] += tp[i];
+    std::vector<int64_t> fill(tp.begin(), tp.end() - 1);
+    trow.resize(nnzJ); tv.resize(nnzJ);
+    for (int64_t r = 0; r < m; r++)
+      for (int64_t q = Jp[r]; q < Jp[r + 1]; q++) {
+        const int64_t c = permuted ? P.Jcol_perm[q] : Ji[q];
+        trow[fill[c]] = (int32_t)r;
+        tv[fill[c]] = (int32_t)q;
+        fill[c]++;
+      }
+  };
+  transpose(true, P.JT_ptr, P.JT_row, P.JT_vidx);
+  transpose(false, P.JTo_ptr, P.JTo_row, P.JTo_vidx);
+  // symmetric H~ in original labels
+  P.Hs_ptr.assign(n + 1, 0);
+  for (int64_t j = 0; j < n; j++)
+    for (int64_t q = Hp[j]; q < Hp[j + 1]; q++) {
+      P.Hs_ptr[Hi[q] + 1]++;
+      if (Hi[q] != j) P.Hs_ptr[j + 1]++;
+    }
+  for (int64_t i = 0; i < n; i++) P.Hs_ptr[i + 1] += P.Hs_ptr[i];
+  {
+    std::vector<int64_t> fill(P.Hs_ptr.begin(), P.Hs_ptr.end() - 1);
+    P.Hs_col.resize(P.Hs_ptr[n]); P.Hs_vidx.resize(P.Hs_ptr[n]);
+    for (int64_t j = 0; j < n; j++)
+      for (int64_t q = Hp[j]; q < Hp[j + 1]; q++) {
+        const int32_t i = Hi[q];
+        P.Hs_col[fill[i]] = (int32_t)j; P.Hs_vidx[fill[i]++] = (int32_t)q;
+        if (i != j) { P.Hs_col[fill[j]] = i; P.Hs_vidx[fill[j]++] = (int32_t)q; }
+      }
+  }
+  // ---------------------------------------------------------- solve DAG
+  P.solve_w = solve_w;
+  std::vector<int32_t> col2piece(n);
+  for (int64_t s = 0; s < ns; s++) {
+    for (int32_t c = 0; c < P.sw[s]; c += solve_w) {
+      const int32_t pw = std::min(solve_w, P.sw[s] - c);
+      const int32_t pid = (int32_t)P.pc_first.size();
+      P.pc_first.push_back(P.sfirst[s] + c);
+      P.pc_w.push_back(pw);
+      P.pc_nr.push_back(P.snr[s] - c);
+      P.pc_ld.push_back(P.snr[s]);
+      P.pc_row.push_back(P.srow[s] + c);
+      P.pc_off.push_back(P.poff[s] + (int64_t)c * P.snr[s] + c);
+      P.max_pw = std::max(P.max_pw, pw);
+      for (int32_t j = 0; j < pw; j++) col2piece[P.sfirst[s] + c + j] = pid;
+    }
+  }
+  P.npieces = (int64_t)P.pc_first.size();
+  P.pc_zoff.resize(P.npieces);
+  P.pc_nchunk.resize(P.npieces);
+  P.pc_need.assign(P.npieces, 0);
+  std::vector<int32_t> tg;
+  for (int64_t p = 0; p < P.npieces; p++) {
+    const int32_t pw = P.pc_w[p];
+    int32_t rc = std::max(32, std::min(256, (int32_t)(16384 / std::max(1, pw))));
+    rc = (rc / 32) * 32;
+    const int64_t below = P.pc_nr[p] - pw;
+    const int32_t nch = (int32_t)cdiv(below, rc);
+    P.pc_nchunk[p] = nch;
+    P.pc_zoff[p] = P.z_total;
+    P.z_total += (int64_t)nch * pw;
+    for (int32_t k = 0; k < nch; k++) {
+      const int32_t r0 = pw + k * rc;
+      const int32_t nr = (int32_t)std::min<int64_t>(rc, P.pc_nr[p] - r0);
+      P.ch_piece.push_back((int32_t)p);
+      P.ch_r0.push_back(r0);
+      P.ch_nr.push_back(nr);
+      P.ch_k.push_back(k);
+      P.ch_tptr.push_back((int64_t)P.ch_tgt.size());
+      tg.clear();
+      for (int32_t i = 0; i < nr; i++) tg.push_back(col2piece[S.sn_rows[P.pc_row[p] + r0 + i]]);
+      tg.erase(std::unique(tg.begin(), tg.end()), tg.end());   // rows ascending => pieces ascending
+      for (int32_t t : tg) { P.ch_tgt.push_back(t); P.pc_need[t]++; }
+    }
+  }
+  P.nchunks = (int64_t)P.ch_piece.size();
+  P.ch_tptr.push_back((int64_t)P.ch_tgt.size());
+  // dispatch order: by depth in the dependency DAG, so that items whose inputs
+  // are ready are handed out first
+  {
+    // forward: head(p) after all chunks targeting p; chunk after its head
+    std::vector<int64_t> hd(P.npieces, 0), cd(P.nchunks, 0);
+    std::vector<int64_t> chunk_first(P.npieces + 1, 0);
+    for (int64_t c = 0; c < P.nchunks; c++) chunk_first[P.ch_piece[c] + 1]++;
+    for (int64_t p = 0; p < P.npieces; p++) chunk_first[p + 1] += chunk_first[p];
+    for (int64_t p = 0; p < P.npieces; p++) {       // pieces are in topological order
+      for (int64_t c = chunk_first[p]; c < chunk_first[p + 1]; c++) {
+        cd[c] = hd[p] + 1;
+        for (int64_t t = P.ch_tptr[c]; t < P.ch_tptr[c + 1]; t++) {
+          const int32_t q = P.ch_tgt[t];
+          hd[q] = std::max(hd[q], cd[c] + 1);
+        }
+      }
+    }
+    std::vector<std::pair<int64_t, int32_t>> ord;
+    for (int64_t p = 0; p < P.npieces; p++) ord.push_back({hd[p] * 2, (int32_t)(-1 - p)});
+    for (int64_t c = 0; c < P.nchunks; c++) ord.push_back({cd[c] * 2 + 1, (int32_t)c});
+    std::stable_sort(ord.begin(), ord.end(), [](auto& a, auto& b) { return a.first < b.first; });
+    for (auto& o : ord) P.fwd_items.push_back(o.second);
+    // backward: chunk after the heads of its targets; head after its chunks
+    std::vector<int64_t> bh(P.npieces, 0), bc(P.nchunks, 0);
+    for (int64_t p = P.npieces - 1; p >= 0; p--) {
+      int64_t d = 0;
+      for (int64_t c = chunk_first[p]; c < chunk_first[p + 1]; c++) {
+        int64_t e = 0;
+        for (int64_t t = P.ch_tptr[c]; t < P.ch_tptr[c + 1]; t++) e = std::max(e, bh[P.ch_tgt[t]] + 1);
+        bc[c] = e;
+        d = std::max(d, e + 1);
+      }
+      bh[p] = d;
+    }
+    ord.clear();
+    for (int64_t p = 0; p < P.npieces; p++) ord.push_back({bh[p] * 2 + 1, (int32_t)(-1 - p)});
+    for (int64_t c = 0; c < P.nchunks; c++) ord.push_back({bc[c] * 2, (int32_t)c});
+    std::stable_sort(ord.begin(), ord.end(), [](auto& a, auto& b) { return a.first < b.first; });
+    for (auto& o : ord) P.bwd_items.push_back(o.second);
+  }
+  return 0;
+}
+
+}  // namespace kkt

@@ -1,0 +1,77 @@
+// Numeric plan: everything the device kernels need that depends only on the
+// sparsity pattern, built once on the host after the symbolic analysis and
+// copied to the device once (Sec. 2: the pattern is fixed over the sequence).
+#pragma once
+#include <cstdint>
+#include <vector>
+
+#include "symbolic.hpp"
+
+namespace kkt {
+
+// Tile constants shared by the planner and the kernels.
+constexpr int kPB = 32;      // panel column block of the front factorization
+constexpr int kTR = 128;     // rows per TRSM item
+constexpr int kUR = 64;      // rows per in-panel update item (x kPB columns)
+constexpr int kST = 64;      // SYRK tile edge
+constexpr int kEC = 32;      // columns per extend-add item
+
+struct Launch {              // one batched kernel launch of the factorization
+  int32_t kind;              // 0 potrf+trsm, 1 in-panel update, 2 syrk, 3 extend-add
+  int32_t kb;                // column block (kinds 0,1)
+  int64_t off, cnt;          // range in the item array of that kind
+};
+
+struct Plan {
+  int64_t n = 0, m = 0, ns = 0;
+  // supernodes
+  std::vector<int32_t> sfirst, sw, snr;     // first column, width, rows
+  std::vector<int64_t> srow;                // offset of the row list in sn_rows
+  std::vector<int64_t> poff;                // panel offset (column-major, ld = snr)
+  std::vector<int64_t> uoff;                // update-matrix offset (rb x rb, ld = rb)
+  std::vector<int32_t> sparent;
+  std::vector<int32_t> rel;                 // per sn_rows slot: position of a child's below
+                                            // row inside the parent's row list
+  int64_t panel_total = 0, u_total = 0;
+  int32_t nlevels = 0;
+  // factor work lists (items are int4: s, a, b, 0)
+  std::vector<int32_t> it_trsm;             // (s, row tile) pairs
+  std::vector<int32_t> it_pupd;             // (s, row tile, col tile) triples
+  std::vector<int32_t> it_syrk;             // (s, ti, tj) triples
+  std::vector<int32_t> it_eadd;             // (s, col tile) pairs
+  std::vector<Launch> launches;
+  // assembly gather: panel slot <- sum of sources (H entry, delta, J pair)
+  std::vector<int64_t> slot_pos;            // panel position of each slot
+  std::vector<int64_t> src_ptr;             // [nslot+1]
+  std::vector<int32_t> srcA, srcB;          // srcB == -1: H entry srcA; -2: delta; else J pair
+  // J in permuted labels and its transpose (for J^T p without atomics)
+  std::vector<int32_t> Jcol_perm;           // iperm of J's column indices
+  std::vector<int64_t> JT_ptr;              // [n+1] by permuted column
+  std::vector<int32_t> JT_row, JT_vidx;     // J row and index into J values
+  // symmetric H~ (full, original labels) for the FP64 residual
+  std::vector<int64_t> Hs_ptr;
+  std::vector<int32_t> Hs_col, Hs_vidx;
+  // J^T in original labels (residual)
+  std::vector<int64_t> JTo_ptr;
+  std::vector<int32_t> JTo_row, JTo_vidx;
+  // solve DAG over column pieces of width <= solve_w
+  int32_t solve_w = 128;
+  int64_t npieces = 0, nchunks = 0;
+  std::vector<int32_t> pc_first, pc_w, pc_nr, pc_ld; // piece: first column, width, rows from its first row, ld
+  std::vector<int64_t> pc_row;              // offset in sn_rows of the piece's first row
+  std::vector<int64_t> pc_off;              // panel offset of the piece's diagonal entry
+  std::vector<int64_t> pc_zoff;             // offset of its partial-sum slots
+  std::vector<int32_t> pc_nchunk;           // row chunks below its triangle
+  std::vector<int32_t> pc_need;             // chunks targeting the piece (forward)
+  std::vector<int32_t> ch_piece, ch_r0, ch_nr, ch_k;  // chunk: piece, first row (piece-local), rows, index
+  std::vector<int64_t> ch_tptr;             // targets of each chunk (distinct pieces)
+  std::vector<int32_t> ch_tgt;
+  std::vector<int32_t> fwd_items, bwd_items; // >= 0 chunk id, < 0 head of piece (-1 - p)
+  int64_t z_total = 0;
+  int32_t max_pw = 0;
+};
+
+int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const int64_t* Jp,
+               const int32_t* Ji, int32_t solve_w, Plan& P);
+
+}  // namespace kkt

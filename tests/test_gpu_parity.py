@@ -1,0 +1,250 @@
+"""CUDA path vs the CPU oracle (needs a B300). Every call goes through the
+C ABI of libkkt.so. Tolerances: FP64 method on the workloads -- relative KKT
+residual <= 1e-8 and solution relative difference <= 1e-6 (the stated
+accuracy target); tiny well-conditioned systems -- 1e-9 on the solution."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2110_03636_b300 as K  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+def cu(a):
+    return torch.as_tensor(np.ascontiguousarray(a, np.float64), device=DEV)
+
+
+def gpu_solve(sys, precision="fp64", delta=None, gamma=None, **opt):
+    s = K.KKTSolver(sys.n, sys.m, sys.H_colptr, sys.H_rowidx, sys.J_rowptr, sys.J_colidx, precision=precision, **opt)
+    code = s.factor(cu(sys.H_vals), cu(sys.J_vals), sys.delta if delta is None else delta,
+                    sys.gamma if gamma is None else gamma, check=False)
+    if code != 0:
+        return s, code, None, None
+    dx, dy = s.solve(cu(sys.r_x), cu(sys.r_y), check=False)
+    torch.cuda.synchronize()
+    return s, 0, dx.cpu().numpy(), dy.cpu().numpy()
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.mark.parametrize("seed", range(12))
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_tiny_systems_match_oracle(seed, precision):
+    sys = W.random_tiny_system(seed, n_lo=3, n_hi=120, density=0.08)
+    _, _, odx, ody, oinfo = O.solve_system(sys)
+    s, code, dx, dy = gpu_solve(sys, precision)
+    assert code == 0
+    info = s.info
+    assert info.cg_status == 0
+    assert rel(np.concatenate([dx, dy]), np.concatenate([odx, ody])) <= 1e-9
+    assert info.rr <= 1e-10
+    r = O.residual(O.Symbolic(sys.n, sys.m, sys.H_colptr, sys.H_rowidx, sys.J_rowptr, sys.J_colidx),
+                   sys.H_vals, sys.J_vals, sys.delta, sys.r_x, sys.r_y, dx, dy)
+    assert r["rr"] <= 1e-10
+    if precision == "fp64":
+        assert abs(info.cg_iters - oinfo["iters"]) <= 1
+    assert s.inertia_ok
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_factor_panels_match_oracle_cholesky(seed):
+    """The FP64 supernodal factor holds the oracle's L entry by entry."""
+    sys = W.random_tiny_system(seed + 50, n_lo=40, n_hi=160, density=0.06)
+    delta, gamma = 1e-3, 30.0
+    s = K.KKTSolver(sys.n, sys.m, sys.H_colptr, sys.H_rowidx, sys.J_rowptr, sys.J_colidx)
+    s.factor(cu(sys.H_vals), cu(sys.J_vals), delta, gamma)
+    panels = s.panels()
+    g = s.symbolic()
+    sym = O.Symbolic(sys.n, sys.m, sys.H_colptr, sys.H_rowidx, sys.J_rowptr, sys.J_colidx)
+    fac = O.Factor(sym, sys.H_vals, sys.J_vals, delta, gamma)
+    Lp, Li, Lx = fac.L_csc()
+    start, rowptr, rows = g["sn_start"], g["sn_rowptr"], g["sn_rows"]
+    off = 0
+    worst = 0.0
+    scale = np.abs(Lx).max()
+    for sn in range(len(start) - 1):
+        w = start[sn + 1] - start[sn]
+        R = rows[rowptr[sn]:rowptr[sn + 1]]
+        nr = len(R)
+        P = panels[off:off + w * nr].reshape(w, nr).T
+        pos = {r: i for i, r in enumerate(R)}
+        for jj in range(w):
+            j = start[sn] + jj
+            col = np.zeros(nr)
+            for q in range(Lp[j], Lp[j + 1]):
+                col[pos[Li[q]]] = Lx[q]
+            col[:jj] = P[:jj, jj]          # upper part of the diagonal block is not used
+            worst = max(worst, np.abs(P[:, jj] - col).max())
+        off += w * nr
+    assert worst <= 1e-12 * scale
+
+
+def test_hsolve_matches_oracle():
+    sys = W.make_config("grid2d_n2000")
+    s = K.KKTSolver(sys.n, sys.m, sys.H_colptr, sys.H_rowidx, sys.J_rowptr, sys.J_colidx)
+    s.factor(cu(sys.H_vals), cu(sys.J_vals), sys.delta, sys.gamma)
+    b = np.random.default_rng(1).standard_normal(sys.n)
+    x = s.hsolve(cu(b)).cpu().numpy()
+    sym = O.Symbolic(sys.n, sys.m, sys.H_colptr, sys.H_rowidx, sys.J_rowptr, sys.J_colidx)
+    ref = O.Factor(sym, sys.H_vals, sys.J_vals, sys.delta, sys.gamma).hsolve(b)
+    assert rel(x, ref) <= 1e-9
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_grid_n2000_matches_oracle(precision):
+    sys = W.make_config("grid2d_n2000")
+    _, _, odx, ody, oinfo = O.solve_system(sys)
+    s, code, dx, dy = gpu_solve(sys, precision)
+    assert code == 0
+    info = s.info
+    assert info.rr <= 1e-8
+    assert rel(np.concatenate([dx, dy]), np.concatenate([odx, ody])) <= 1e-6
+    sym = O.Symbolic(sys.n, sys.m, sys.H_colptr, sys.H_rowidx, sys.J_rowptr, sys.J_colidx)
+    assert O.residual(sym, sys.H_vals, sys.J_vals, sys.delta, sys.r_x, sys.r_y, dx, dy)["rr"] <= 1e-8
+    if precision == "fp64":
+        assert abs(info.cg_iters - oinfo["iters"]) <= 1
+    assert s.inertia_ok
+
+
+def test_grid_n20k_and_value_updates():
+    """Four value refactorizations on one resident pattern (interior iterations)."""
+    base = W.make_config("grid2d_n20k")
+    s = K.KKTSolver(base.n, base.m, base.H_colptr, base.H_rowidx, base.J_rowptr, base.J_colidx)
+    sym = O.Symbolic(base.n, base.m, base.H_colptr, base.H_rowidx, base.J_rowptr, base.J_colidx)
+    sys = base
+    for t in range(4):
+        if t:
+            sys = W.rescale_barrier(sys, seed=(0, t))
+        s.factor(cu(sys.H_vals), cu(sys.J_vals), sys.delta, sys.gamma)
+        dx, dy = s.solve(cu(sys.r_x), cu(sys.r_y))
+        dx, dy = dx.cpu().numpy(), dy.cpu().numpy()
+        fac = O.Factor(sym, sys.H_vals, sys.J_vals, sys.delta, sys.gamma)
+        odx, ody, _ = fac.solve(sys.r_x, sys.r_y)
+        assert rel(np.concatenate([dx, dy]), np.concatenate([odx, ody])) <= 1e-6
+        assert s.info.rr <= 1e-8
+
+
+def test_gamma_invariance_on_gpu():
+    sys = W.make_config("grid2d_n2000")
+    sols = []
+    for gamma in (1e2, 1e4, 1e6):
+        s, code, dx, dy = gpu_solve(sys, gamma=gamma)
+        assert code == 0 and s.info.rr <= 1e-8
+        sols.append(np.concatenate([dx, dy]))
+    assert rel(sols[0], sols[2]) <= 1e-6 and rel(sols[1], sols[2]) <= 1e-6
+
+
+def test_closed_form_one_iteration():
+    from test_oracle import make_sys
+    n, m, alpha = 300, 120, 3.0
+    rng = np.random.default_rng(2)
+    J = np.zeros((m, n))
+    J[np.arange(m), np.arange(m)] = 1.0
+    sys = make_sys(alpha * np.eye(n), J, rng.standard_normal(n), rng.standard_normal(m), gamma=1e4)
+    s, code, dx, dy = gpu_solve(sys)
+    assert code == 0 and s.info.cg_iters == 1
+    np.testing.assert_allclose(dx[:m], sys.r_y, atol=1e-10)
+    np.testing.assert_allclose(dy, sys.r_x[:m] - alpha * sys.r_y, atol=1e-8)
+
+
+def test_not_spd_reported_and_handle_reusable():
+    """Thm 1: H~ negative on null(J) -> NOT_SPD; delta_1 = 0.6 restores SPD (Sec. 4.1)."""
+    from test_oracle import make_sys
+    n, m = 50, 10
+    H = np.eye(n)
+    H[30, 30] = -0.5
+    J = np.zeros((m, n))
+    J[np.arange(m), np.arange(m)] = 1.0
+    rng = np.random.default_rng(4)
+    sys = make_sys(H, J, rng.standard_normal(n), rng.standard_normal(m), gamma=1e4)
+    s, code, _, _ = gpu_solve(sys)
+    assert code == 2 and not s.inertia_ok
+    with pytest.raises(K.KKTError) as e:
+        s.solve(cu(sys.r_x), cu(sys.r_y))
+    assert e.value.code == 8
+    s.factor(cu(sys.H_vals), cu(sys.J_vals), 0.6, 1e4)
+    dx, dy = s.solve(cu(sys.r_x), cu(sys.r_y))
+    ref = np.linalg.solve(np.block([[H + 0.6 * np.eye(n), J.T], [J, np.zeros((m, m))]]),
+                          np.concatenate([sys.r_x, sys.r_y]))
+    assert rel(np.concatenate([dx.cpu().numpy(), dy.cpu().numpy()]), ref) <= 1e-9
+
+
+def test_rank_deficient_J_uses_delta2_and_clears_inertia():
+    from test_oracle import make_sys
+    n, m = 60, 8
+    rng = np.random.default_rng(3)
+    J = np.zeros((m, n))
+    J[np.arange(m - 1), np.arange(m - 1)] = 1.0
+    J[:m - 1, 20:24] = rng.standard_normal((m - 1, 4))
+    J[m - 1] = J[0]
+    sys = make_sys(2.0 * np.eye(n), J, rng.standard_normal(n), rng.standard_normal(m), gamma=1e2)
+    s, code, dx, dy = gpu_solve(sys, delta2=1e-6, ir_maxit=0)
+    assert code == 0
+    assert s.info.delta2_used == 1 and not s.inertia_ok
+    sym = O.Symbolic(sys.n, sys.m, sys.H_colptr, sys.H_rowidx, sys.J_rowptr, sys.J_colidx)
+    _, ody, oinfo = O.Factor(sym, sys.H_vals, sys.J_vals, 0.0, 1e2).solve(sys.r_x, sys.r_y, delta2=1e-6)
+    assert oinfo["delta2"] == 1e-6
+    assert rel(dy, ody) <= 1e-6
+
+
+def test_edge_sizes():
+    from test_oracle import make_sys
+    # n = 1, m = 0
+    sys = make_sys(np.array([[4.0]]), np.zeros((0, 1)), np.array([2.0]), np.zeros(0))
+    s, code, dx, dy = gpu_solve(sys)
+    assert code == 0 and abs(dx[0] - 0.5) < 1e-15 and s.info.cg_iters == 0
+    # m = 0, larger n: plain SPD solve
+    rng = np.random.default_rng(0)
+    A = rng.standard_normal((40, 40))
+    A = A @ A.T + 40 * np.eye(40)
+    sys = make_sys(A, np.zeros((0, 40)), rng.standard_normal(40), np.zeros(0))
+    s, code, dx, dy = gpu_solve(sys)
+    assert code == 0 and rel(dx, np.linalg.solve(A, sys.r_x)) <= 1e-12
+    # zero right-hand side
+    sys = W.random_tiny_system(9)
+    sys.r_x[:] = 0
+    sys.r_y[:] = 0
+    s, code, dx, dy = gpu_solve(sys)
+    assert code == 0 and not dx.any() and not dy.any() and s.info.cg_iters == 0
+
+
+def test_bounded_wait_times_out_and_context_survives():
+    """A wait that nothing satisfies (host-injected) ends with KKT_ERR_TIMEOUT;
+    the GPU context and the library stay usable."""
+    sys = W.random_tiny_system(7, n_lo=60, n_hi=60)
+    s = K.KKTSolver(sys.n, sys.m, sys.H_colptr, sys.H_rowidx, sys.J_rowptr, sys.J_colidx,
+                    debug_stall_piece=0, spin_cycles=20_000_000)
+    s.factor(cu(sys.H_vals), cu(sys.J_vals), 0.0, sys.gamma)
+    with pytest.raises(K.KKTError) as e:
+        s.solve(cu(sys.r_x), cu(sys.r_y))
+    assert e.value.code == 7
+    s2, code, dx, dy = gpu_solve(sys)
+    assert code == 0 and s2.info.rr <= 1e-10
+
+
+def test_host_buffer_entry_point():
+    sys = W.make_config("grid2d_n2000")
+    s = K.KKTSolver(sys.n, sys.m, sys.H_colptr, sys.H_rowidx, sys.J_rowptr, sys.J_colidx)
+    dx, dy = s.factor_solve_host(sys.H_vals, sys.J_vals, sys.delta, sys.gamma, sys.r_x, sys.r_y)
+    _, _, odx, ody, _ = O.solve_system(sys)
+    assert rel(np.concatenate([dx, dy]), np.concatenate([odx, ody])) <= 1e-6
+
+
+def test_repeat_solves_agree():
+    sys = W.make_config("grid2d_n2000")
+    s = K.KKTSolver(sys.n, sys.m, sys.H_colptr, sys.H_rowidx, sys.J_rowptr, sys.J_colidx)
+    s.factor(cu(sys.H_vals), cu(sys.J_vals), sys.delta, sys.gamma)
+    a = torch.cat(s.solve(cu(sys.r_x), cu(sys.r_y))).cpu().numpy()
+    b = torch.cat(s.solve(cu(sys.r_x), cu(sys.r_y))).cpu().numpy()
+    assert rel(a, b) <= 1e-12

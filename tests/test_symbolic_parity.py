@@ -1,0 +1,131 @@
+"""Host symbolic analysis of the library vs the oracle: bit-exact on the
+ordering, etree, column counts and supernodes (CPU only; the library's
+kkt_analyse_host makes no CUDA call). Also checks the C ABI surface."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2110_03636_b300 as K
+import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def lib_symbolic(sys, **opt):
+    o = K.kkt_default_options(**opt)
+    h = K.kkt_analyse_host(sys.n, sys.m, sys.H_colptr, sys.H_rowidx, sys.J_rowptr, sys.J_colidx, o)
+    try:
+        return K.kkt_get_symbolic(h), K.kkt_symbolic_info_get(h)
+    finally:
+        K.kkt_destroy(h)
+
+
+def assert_same(sys, relax=(16, 1, 10, 256), ordering=0):
+    g, info = lib_symbolic(sys, relax_small=relax[0], relax_num=relax[1], relax_den=relax[2],
+                           relax_wmax=relax[3], ordering=ordering)
+    sym = O.Symbolic(sys.n, sys.m, sys.H_colptr, sys.H_rowidx, sys.J_rowptr, sys.J_colidx,
+                     relax_small=relax[0], relax_num=relax[1], relax_den=relax[2], wmax=relax[3],
+                     ordering="amd" if ordering == 0 else "natural")
+    np.testing.assert_array_equal(g["amd"], sym.amd_order)
+    np.testing.assert_array_equal(g["perm"], sym.perm)
+    np.testing.assert_array_equal(g["parent"], sym.parent)
+    np.testing.assert_array_equal(g["colcount"], sym.colcount)
+    st, rp, rows, par = sym.supernodes()
+    np.testing.assert_array_equal(g["sn_start"], st)
+    np.testing.assert_array_equal(g["sn_rowptr"], rp)
+    np.testing.assert_array_equal(g["sn_rows"], rows)
+    np.testing.assert_array_equal(g["sn_parent"], par)
+    assert info.nnz_l == sym.nnzL and info.flops == sym.flops and info.nsuper == sym.nsuper
+    return info
+
+
+@pytest.mark.parametrize("seed", range(120))
+def test_random_tiny_patterns_bit_exact(seed):
+    rng = np.random.default_rng(seed)
+    sys = W.random_tiny_system(seed + 1000, n_lo=2, n_hi=90, density=float(rng.uniform(0.01, 0.3)))
+    assert_same(sys)
+
+
+@pytest.mark.parametrize("relax", [(1, 0, 1, 1), (1, 0, 1, 256), (4, 1, 4, 8), (32, 3, 10, 64), (16, 1, 10, 256)])
+def test_relaxation_parameters_bit_exact(relax):
+    for seed in range(6):
+        assert_same(W.random_tiny_system(seed + 2000, n_lo=30, n_hi=120, density=0.05), relax=relax)
+
+
+def test_natural_ordering_bit_exact():
+    assert_same(W.make_config("grid2d_n2000"), ordering=1)
+
+
+def test_grid_n2000_bit_exact():
+    assert_same(W.make_config("grid2d_n2000"))
+
+
+def test_grid_n20k_bit_exact():
+    assert_same(W.make_config("grid2d_n20k"))
+
+
+def test_serving_pattern_bit_exact():
+    assert_same(W.serving_pattern(100))
+
+
+@pytest.mark.slow
+def test_grid_n250k_bit_exact():
+    """The full 500 x 500 workload (oracle symbolic takes ~20 s)."""
+    info = assert_same(W.make_config("grid2d_n250k"))
+    assert info.nnz_l > 1e8
+
+
+def test_trees_and_cliques():
+    from test_oracle import graph_sys
+    for n in (1, 2, 7, 40):
+        edges = [(a, b) for a in range(n) for b in range(a)]
+        assert_same(graph_sys(n, edges))
+        path = [(i, i + 1) for i in range(n - 1)]
+        assert_same(graph_sys(n, path))
+
+
+def test_invalid_patterns_rejected():
+    sys = W.random_tiny_system(5)
+    bad = [
+        (sys.H_colptr, np.where(np.arange(sys.H_rowidx.size) == 1, 0, sys.H_rowidx)),  # an entry above the diagonal
+    ]
+    Hi = sys.H_rowidx.copy()
+    Hi[-1] = sys.n + 5                                                                  # out of range
+    bad.append((sys.H_colptr, Hi))
+    for Hp, Hi in bad:
+        with pytest.raises(K.KKTError) as e:
+            K.kkt_analyse_host(sys.n, sys.m, Hp, Hi, sys.J_rowptr, sys.J_colidx)
+        assert e.value.code == 1
+    Jc = sys.J_colidx.copy()
+    if sys.J_rowptr[1] - sys.J_rowptr[0] >= 2:
+        Jc[1] = Jc[0]                                                                   # duplicate column
+        with pytest.raises(K.KKTError):
+            K.kkt_analyse_host(sys.n, sys.m, sys.H_colptr, sys.H_rowidx, sys.J_rowptr, Jc)
+    with pytest.raises(K.KKTError):
+        K.kkt_analyse_host(0, 0, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(1, np.int64),
+                           np.zeros(0, np.int32))
+
+
+def test_library_exports_every_declared_symbol():
+    hdr = open(os.path.join(ROOT, "include", "kkt.h")).read()
+    names = set(re.findall(r"\b(kkt_[a-z0-9_]+)\s*\(", hdr))
+    lib = ctypes.CDLL(K.LIB_PATH)
+    missing = [nm for nm in sorted(names) if not hasattr(lib, nm)]
+    assert not missing, missing
+    assert set(K.EXPORTED) <= names
+
+
+def test_host_handle_refuses_device_calls():
+    sys = W.random_tiny_system(3)
+    h = K.kkt_analyse_host(sys.n, sys.m, sys.H_colptr, sys.H_rowidx, sys.J_rowptr, sys.J_colidx)
+    try:
+        code = K._lib.kkt_factor(h, None, None, 0.0, 1.0, None)
+        assert code in (1, 8)
+        code = K._lib.kkt_solve(h, None, None, None, None, None)
+        assert code in (1, 8)
+    finally:
+        K.kkt_destroy(h)
