@@ -73,7 +73,16 @@ typedef struct kkt_options {
                                 an arrival that never comes, so the bounded wait runs out */
   int64_t spin_cycles; /* limit of every wait on another CTA's flag, in SM clock cycles
                           (0 = default 4e9, about two seconds) */
+  int32_t profile;     /* 1: time every kernel launch with CUDA events (serialises the
+                          launches; for measurement runs only) */
+  int32_t pad_;
 } kkt_options;
+
+/* Kernel kinds reported by kkt_get_profile. */
+enum {
+  KKT_K_ASSEMBLE = 0, KKT_K_POTRF = 1, KKT_K_TRSM = 2, KKT_K_PANEL_UPDATE = 3, KKT_K_SYRK = 4,
+  KKT_K_EXTEND_ADD = 5, KKT_K_ZERO_U = 6, KKT_K_CG = 7, KKT_K_RESIDUAL = 8, KKT_K_COUNT = 10
+};
 
 /* Result of the last kkt_solve on a handle. */
 typedef struct kkt_info {
@@ -181,6 +190,11 @@ kkt_status kkt_get_symbolic(kkt_handle h, int32_t* amd, int32_t* perm, int32_t* 
 /* The factor's supernode panels converted to FP64 into host double
  * [panel_entries] (column-major per supernode, ld = its row count). */
 kkt_status kkt_get_factor_panels(kkt_handle h, double* panels);
+
+/* Accumulated device time (ms) and launch count per kernel kind since the
+ * last reset, for handles created with opt.profile = 1 (host arrays of
+ * KKT_K_COUNT entries). reset != 0 clears the counters after reading. */
+kkt_status kkt_get_profile(kkt_handle h, double* ms, int64_t* launches, int32_t reset);
 
 kkt_status kkt_destroy(kkt_handle h);
 

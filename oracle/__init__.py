@@ -63,6 +63,8 @@ def _load():
         L.orc_sym_free.argtypes = [P]
         L.orc_factor.restype = P
         L.orc_factor.argtypes = [P, f64p, f64p, C.c_double, C.c_double, C.POINTER(C.c_int32)]
+        L.orc_factor_sample.restype = P
+        L.orc_factor_sample.argtypes = [P, f64p, f64p, C.c_double, C.c_double, C.c_int64, f64p, f64p]
         L.orc_fail_col.restype = C.c_int64
         L.orc_fail_col.argtypes = [P]
         L.orc_get_L.argtypes = [P, i64p, i32p, f64p]
@@ -198,6 +200,27 @@ class Factor:
         if getattr(self, "_h", None) and _lib is not None:
             _lib.orc_num_free(self._h)
             self._h = None
+
+
+class FactorSample(Factor):
+    """Assembly + the first ``kmax`` rows of the oracle's factorization, timed
+    in C (for a bounded CPU-baseline sample). ``times`` = (assembly s, rows s),
+    ``work`` = inner-loop updates done; the full factorization performs
+    sum_j (c_j - 1)(c_j - 2)/2 of them (c_j = column counts)."""
+
+    def __init__(self, sym: Symbolic, H_vals, J_vals, delta, gamma, kmax):
+        L = _load()
+        self.sym = sym
+        self.H_vals = _c(H_vals, np.float64)
+        self.J_vals = _c(J_vals, np.float64)
+        self.delta, self.gamma = float(delta), float(gamma)
+        t = np.zeros(2)
+        w = np.zeros(1)
+        self._h = L.orc_factor_sample(sym._h, self.H_vals, self.J_vals, self.delta, self.gamma, int(kmax), t, w)
+        self.times = (float(t[0]), float(t[1]))
+        self.work = float(w[0])
+        self.status = 0
+        self.fail_col = -1
 
 
 def residual(sym: Symbolic, H_vals, J_vals, delta, r_x, r_y, dx, dy):

@@ -28,7 +28,9 @@
  * pinned only by agreement with the independent library implementation
  * ("parity unpinned" for the tie-level details of S2).
  */
+#define _POSIX_C_SOURCE 199309L
 #include <math.h>
+#include <time.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -654,16 +656,12 @@ static void assemble(const orc_sym *S, const double *Hv, const double *Jv, doubl
 
 /* Up-looking Cholesky: row k of L solves L(0:k,0:k) l = A(0:k,k), then
  * L_kk = sqrt(A_kk - l.l). Row patterns come from the symbolic column
- * patterns (transposed). Columns of L fill in increasing row order. */
-orc_num *orc_factor(const orc_sym *S, const double *Hv, const double *Jv, double delta,
-                    double gamma, int32_t *status) {
+ * patterns (transposed). Columns of L fill in increasing row order.
+ * Rows [0, kmax) are processed; *work counts inner-loop updates. */
+static void factor_rows(orc_num *N, int64_t kmax, double *work) {
+    const orc_sym *S = N->S;
     int64_t n = S->n;
-    orc_num *N = (orc_num *)calloc(1, sizeof(orc_num));
-    N->S = S; N->n = n;
-    assemble(S, Hv, Jv, delta, gamma, N);
     int64_t nnz = S->Lp[n];
-    N->Lx = (double *)calloc((size_t)(nnz > 0 ? nnz : 1), sizeof(double));
-    N->Ld = (double *)calloc((size_t)n, sizeof(double));
     /* row patterns of L: row k -> columns i < k with L_ki != 0 (ascending i) */
     int64_t *Rp = (int64_t *)calloc((size_t)(n + 1), sizeof(int64_t));
     for (int64_t q = 0; q < nnz; q++) Rp[S->Li[q] + 1]++;
@@ -676,8 +674,9 @@ orc_num *orc_factor(const orc_sym *S, const double *Hv, const double *Jv, double
     int64_t *cpos = (int64_t *)malloc((size_t)n * sizeof(int64_t));  /* next slot per column */
     for (int64_t j = 0; j < n; j++) cpos[j] = S->Lp[j];
     double *x = (double *)calloc((size_t)n, sizeof(double));
+    double wk = 0.0;
     N->status = 0; N->fail_col = -1;
-    for (int64_t k = 0; k < n; k++) {
+    for (int64_t k = 0; k < kmax; k++) {
         double d = 0.0;
         for (int64_t q = N->Up[k]; q < N->Up[k + 1]; q++) {
             if (N->Ui[q] == k) d += N->Ux[q];
@@ -688,6 +687,7 @@ orc_num *orc_factor(const orc_sym *S, const double *Hv, const double *Jv, double
             double lki = x[i] / N->Ld[i];
             x[i] = 0.0;
             for (int64_t q = S->Lp[i]; q < cpos[i]; q++) x[S->Li[q]] -= N->Lx[q] * lki;
+            wk += (double)(cpos[i] - S->Lp[i]);
             d -= lki * lki;
             N->Lx[cpos[i]++] = lki;
         }
@@ -697,8 +697,46 @@ orc_num *orc_factor(const orc_sym *S, const double *Hv, const double *Jv, double
         }
         N->Ld[k] = sqrt(d);
     }
+    if (work) *work = wk;
     free(Rp); free(Ri); free(fill); free(cpos); free(x);
+}
+
+orc_num *orc_factor(const orc_sym *S, const double *Hv, const double *Jv, double delta,
+                    double gamma, int32_t *status) {
+    int64_t n = S->n;
+    orc_num *N = (orc_num *)calloc(1, sizeof(orc_num));
+    N->S = S; N->n = n;
+    assemble(S, Hv, Jv, delta, gamma, N);
+    int64_t nnz = S->Lp[n];
+    N->Lx = (double *)calloc((size_t)(nnz > 0 ? nnz : 1), sizeof(double));
+    N->Ld = (double *)calloc((size_t)n, sizeof(double));
+    factor_rows(N, n, NULL);
     *status = N->status;
+    return N;
+}
+
+/* Timing sample for a CPU baseline: assembly plus rows [0, kmax) of the
+ * factorization. times[0] = assembly seconds, times[1] = row loop seconds,
+ * *work = inner-loop updates done. Diagonal entries of the rows not
+ * processed are set to 1 so that orc_hsolve can be timed on the result. */
+orc_num *orc_factor_sample(const orc_sym *S, const double *Hv, const double *Jv, double delta,
+                           double gamma, int64_t kmax, double *times, double *work) {
+    struct timespec t0, t1, t2;
+    int64_t n = S->n;
+    if (kmax > n) kmax = n;
+    orc_num *N = (orc_num *)calloc(1, sizeof(orc_num));
+    N->S = S; N->n = n;
+    clock_gettime(CLOCK_MONOTONIC, &t0);
+    assemble(S, Hv, Jv, delta, gamma, N);
+    clock_gettime(CLOCK_MONOTONIC, &t1);
+    int64_t nnz = S->Lp[n];
+    N->Lx = (double *)calloc((size_t)(nnz > 0 ? nnz : 1), sizeof(double));
+    N->Ld = (double *)calloc((size_t)n, sizeof(double));
+    factor_rows(N, kmax, work);
+    clock_gettime(CLOCK_MONOTONIC, &t2);
+    for (int64_t k = 0; k < n; k++) if (!(N->Ld[k] > 0.0)) N->Ld[k] = 1.0;
+    times[0] = (double)(t1.tv_sec - t0.tv_sec) + 1e-9 * (double)(t1.tv_nsec - t0.tv_nsec);
+    times[1] = (double)(t2.tv_sec - t1.tv_sec) + 1e-9 * (double)(t2.tv_nsec - t1.tv_nsec);
     return N;
 }
 

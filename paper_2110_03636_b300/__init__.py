@@ -34,7 +34,7 @@ class kkt_options(C.Structure):
                 ("precision", C.c_int32), ("ordering", C.c_int32), ("relax_small", C.c_int32),
                 ("relax_num", C.c_int32), ("relax_den", C.c_int32), ("relax_wmax", C.c_int32),
                 ("solve_w", C.c_int32), ("device", C.c_int32), ("debug_stall_piece", C.c_int32),
-                ("spin_cycles", C.c_int64)]
+                ("spin_cycles", C.c_int64), ("profile", C.c_int32), ("pad_", C.c_int32)]
 
 
 class kkt_info(C.Structure):
@@ -67,11 +67,12 @@ def _load():
     L.kkt_symbolic_info_get.argtypes = [P, C.POINTER(kkt_symbolic_info)]
     L.kkt_get_symbolic.argtypes = [P] + [P] * 8
     L.kkt_get_factor_panels.argtypes = [P, P]
+    L.kkt_get_profile.argtypes = [P, P, P, I32]
     L.kkt_destroy.argtypes = [P]
     L.kkt_status_string.argtypes = [I32]
     L.kkt_status_string.restype = C.c_char_p
     for nm in ("kkt_analyse", "kkt_analyse_host", "kkt_factor", "kkt_solve", "kkt_factor_solve_host", "kkt_hsolve", "kkt_get_info",
-               "kkt_inertia", "kkt_symbolic_info_get", "kkt_get_symbolic", "kkt_get_factor_panels", "kkt_destroy"):
+               "kkt_inertia", "kkt_symbolic_info_get", "kkt_get_symbolic", "kkt_get_factor_panels", "kkt_get_profile", "kkt_destroy"):
         getattr(L, nm).restype = I32
     return L
 
@@ -79,7 +80,9 @@ def _load():
 _lib = _load()
 EXPORTED = ("kkt_default_options", "kkt_analyse", "kkt_analyse_host", "kkt_factor", "kkt_solve", "kkt_factor_solve_host",
             "kkt_hsolve", "kkt_get_info", "kkt_inertia", "kkt_symbolic_info_get", "kkt_get_symbolic",
-            "kkt_get_factor_panels", "kkt_destroy", "kkt_status_string")
+            "kkt_get_factor_panels", "kkt_get_profile", "kkt_destroy", "kkt_status_string")
+KERNEL_KINDS = ("assemble", "potrf", "trsm", "panel_update", "syrk", "extend_add", "zero_u", "cg_persistent",
+                "residual")
 
 
 def _check(fn, code):
@@ -199,6 +202,14 @@ def kkt_get_factor_panels(h):
     return out[: s.panel_entries]
 
 
+def kkt_get_profile(h, reset=False):
+    """{kernel kind: (ms, launches)} accumulated by a handle made with profile=1."""
+    ms = np.zeros(10)
+    n = np.zeros(10, np.int64)
+    _check("kkt_get_profile", _lib.kkt_get_profile(h, ms.ctypes.data, n.ctypes.data, int(bool(reset))))
+    return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_KINDS)}
+
+
 def kkt_destroy(h):
     return _lib.kkt_destroy(h)
 
@@ -273,6 +284,9 @@ class KKTSolver:
 
     def panels(self):
         return kkt_get_factor_panels(self.h)
+
+    def profile(self, reset=False):
+        return kkt_get_profile(self.h, reset)
 
     def close(self):
         if getattr(self, "h", None):

@@ -60,7 +60,7 @@ struct kkt_handle_s {
   // pattern / plan on the device
   int32_t *sfirst, *sw, *snr, *sparent, *rel, *sn_rows, *perm;
   int64_t *srow, *poff, *uoff;
-  int4 *it_trsm, *it_pupd, *it_syrk, *it_eadd;
+  int4 *it_potrf, *it_trsm, *it_pupd, *it_syrk, *it_eadd, *it_zero;
   int64_t *slot_pos, *src_ptr;
   int32_t *srcA, *srcB;
   int32_t *Jcol_perm, *JT_row, *JT_vidx, *Hs_col, *Hs_vidx, *JTo_row, *JTo_vidx, *J_colidx;
@@ -82,6 +82,8 @@ struct kkt_handle_s {
   double delta = 0, gamma = 0;
   kkt_info info{};
   int inertia_ok = 0;
+  Prof prof;
+  Prof* profp = nullptr;   // non-null when opt.profile
 };
 
 static kkt_status cuda_status(cudaError_t e) {
@@ -116,6 +118,7 @@ void kkt_default_options(kkt_options* o) {
   o->device = 0;
   o->debug_stall_piece = -1;
   o->spin_cycles = 0;
+  o->profile = 0;
 }
 
 const char* kkt_status_string(kkt_status s) {
@@ -140,6 +143,8 @@ kkt_status kkt_destroy(kkt_handle h) {
     h->mem.release();
   }
   if (h->hst) cudaFreeHost(h->hst);
+  if (h->prof.a) cudaEventDestroy(h->prof.a);
+  if (h->prof.b) cudaEventDestroy(h->prof.b);
   delete h;
   return KKT_OK;
 }
@@ -202,6 +207,7 @@ kkt_status kkt_analyse(int64_t n, int64_t m, const int64_t* Hp, const int32_t* H
   h->sparent = A.upload(P.sparent); h->rel = A.upload(P.rel); h->sn_rows = A.upload(h->S.sn_rows);
   h->perm = A.upload(h->S.perm);
   h->srow = A.upload(P.srow); h->poff = A.upload(P.poff); h->uoff = A.upload(P.uoff);
+  h->it_potrf = as_int4(P.it_potrf); h->it_zero = as_int4(P.it_zero);
   h->it_trsm = as_int4(P.it_trsm); h->it_pupd = as_int4(P.it_pupd);
   h->it_syrk = as_int4(P.it_syrk); h->it_eadd = as_int4(P.it_eadd);
   h->slot_pos = A.upload(P.slot_pos); h->src_ptr = A.upload(P.src_ptr);
@@ -236,6 +242,14 @@ kkt_status kkt_analyse(int64_t n, int64_t m, const int64_t* Hp, const int32_t* H
   if (A.failed) { kkt_destroy(h); return KKT_ERR_OOM; }
   if (cudaMallocHost(&h->hst, sizeof(DevStatus)) != cudaSuccess) { cudaGetLastError(); h->hst = nullptr; kkt_destroy(h); return KKT_ERR_OOM; }
   if (cudaDeviceSynchronize() != cudaSuccess) { cudaGetLastError(); kkt_destroy(h); return KKT_ERR_CUDA; }
+  if (o.profile) {
+    if (cudaEventCreate(&h->prof.a) != cudaSuccess || cudaEventCreate(&h->prof.b) != cudaSuccess) {
+      cudaGetLastError();
+      kkt_destroy(h);
+      return KKT_ERR_CUDA;
+    }
+    h->profp = &h->prof;
+  }
   h->on_device = true;
   *out = h;
   return KKT_OK;
@@ -265,12 +279,13 @@ static kkt_status factor_impl(kkt_handle h, cudaStream_t st) {
   a.Hv = h->Hv; a.Jv = h->Jv;
   a.L = (T*)h->L; a.U = (T*)h->U; a.st = h->dst;
   FacLists fl;
-  fl.it_trsm = h->it_trsm; fl.it_pupd = h->it_pupd; fl.it_syrk = h->it_syrk; fl.it_eadd = h->it_eadd;
+  fl.it_potrf = h->it_potrf; fl.it_trsm = h->it_trsm; fl.it_pupd = h->it_pupd;
+  fl.it_syrk = h->it_syrk; fl.it_eadd = h->it_eadd; fl.it_zero = h->it_zero;
   fl.slot_pos = h->slot_pos; fl.src_ptr = h->src_ptr; fl.srcA = h->srcA; fl.srcB = h->srcB;
   fl.nslot = (int64_t)h->P.slot_pos.size();
   fl.panel_total = h->P.panel_total; fl.u_total = h->P.u_total;
   fl.launches = &h->P.launches;
-  CK(launch_factor<T>(a, fl, h->delta, h->gamma, st));
+  CK(launch_factor<T>(a, fl, h->delta, h->gamma, st, h->profp));
   return KKT_OK;
 }
 
@@ -326,7 +341,9 @@ static kkt_status solve_pass(kkt_handle h, const double* bx, const double* by, d
   CK(cudaMemsetAsync(h->counters, 0, sizeof(int) * (4 * (size_t)h->P.npieces + 8), st));
   SolveArgs<T> a = solve_args<T>(h);
   a.bx = bx; a.by = by; a.ox = ox; a.oy = oy; a.accumulate = accumulate; a.mode = mode;
+  CK(prof_begin(h->profp, st));
   CK(launch_solve<T>(a, h->grid, st));
+  CK(prof_end(h->profp, KKT_K_CG, st));
   return KKT_OK;
 }
 
@@ -340,7 +357,9 @@ static kkt_status residual(kkt_handle h, const double* bx, const double* by, con
   r.Hv = h->Hv; r.Jv = h->Jv; r.delta = h->delta;
   r.bx = bx; r.by = by; r.x = x; r.y = y; r.res_x = h->res_x; r.res_y = h->res_y;
   r.red = h->red; r.st = h->dst;
+  CK(prof_begin(h->profp, st));
   CK(launch_residual(r, st));
+  CK(prof_end(h->profp, KKT_K_RESIDUAL, st));
   return KKT_OK;
 }
 
@@ -468,6 +487,18 @@ kkt_status kkt_get_symbolic(kkt_handle h, int32_t* amd, int32_t* perm, int32_t* 
   auto cp = [](auto* dst, const auto& v) { if (dst && !v.empty()) std::memcpy(dst, v.data(), sizeof(v[0]) * v.size()); };
   cp(amd, S.amd); cp(perm, S.perm); cp(parent, S.parent); cp(colcount, S.colcount);
   cp(sn_start, S.sn_start); cp(sn_rowptr, S.sn_rowptr); cp(sn_rows, S.sn_rows); cp(sn_parent, S.sn_parent);
+  return KKT_OK;
+}
+
+kkt_status kkt_get_profile(kkt_handle h, double* ms, int64_t* launches, int32_t reset) {
+  if (!h) return KKT_ERR_INVALID;
+  for (int k = 0; k < KKT_K_COUNT; k++) {
+    if (ms) ms[k] = h->prof.ms[k];
+    if (launches) launches[k] = h->prof.n[k];
+  }
+  if (reset) {
+    for (int k = 0; k < KKT_K_COUNT; k++) { h->prof.ms[k] = 0; h->prof.n[k] = 0; }
+  }
   return KKT_OK;
 }
 

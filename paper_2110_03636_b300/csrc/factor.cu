@@ -37,22 +37,19 @@ __global__ void k_assemble(int64_t nslot, const int64_t* __restrict__ slot_pos,
   }
 }
 
-// ------------------------------------------------------------- POTRF + TRSM
-// Column block kb (kPB columns) of the fronts listed in items (s, row tile):
-// every CTA factors the kPB x kPB diagonal tile in shared memory (redundantly)
-// and solves its tile of kTR rows below it; tile 0 also stores the diagonal.
+// ------------------------------------------------------------------- POTRF
+// Column block kb (kPB columns) of each listed front: Cholesky of the
+// kPB x kPB diagonal tile in shared memory, written back to the panel. A
+// pivot <= 0 or non-finite records the column in DevStatus::fail_col.
 template <typename T>
-__global__ void __launch_bounds__(kTR) k_potrf_trsm(const int4* __restrict__ items, int kb, FacArgs<T> a) {
+__global__ void __launch_bounds__(256) k_potrf(const int4* __restrict__ items, int kb, FacArgs<T> a) {
   __shared__ T D[kPB][kPB + 1];
-  __shared__ int bad;
-  const int4 it = items[blockIdx.x];
-  const int s = it.x, t = it.y;
+  const int s = items[blockIdx.x].x;
   const int w = a.sw[s], nr = a.snr[s];
   const int c0 = kb * kPB;
   const int bw = min(kPB, w - c0);
   T* P = a.L + a.poff[s];
   const int tid = threadIdx.x;
-  if (tid == 0) bad = 0;
   for (int e = tid; e < kPB * kPB; e += blockDim.x) {
     const int i = e % kPB, j = e / kPB;
     D[i][j] = (i < bw && j <= i) ? P[(int64_t)(c0 + i) + (int64_t)(c0 + j) * nr] : T(0);
@@ -62,8 +59,7 @@ __global__ void __launch_bounds__(kTR) k_potrf_trsm(const int4* __restrict__ ite
     if (tid == 0) {
       T d = D[j][j];
       if (!(d > T(0)) || !isfinite((double)d)) {
-        if (t == 0) atomicMin(&a.st->fail_col, a.sfirst[s] + c0 + j);
-        bad = 1;
+        atomicMin(&a.st->fail_col, a.sfirst[s] + c0 + j);
         d = T(1);
       }
       D[j][j] = sqrt(d);
@@ -78,12 +74,30 @@ __global__ void __launch_bounds__(kTR) k_potrf_trsm(const int4* __restrict__ ite
     }
     __syncthreads();
   }
-  if (t == 0) {
-    for (int e = tid; e < kPB * kPB; e += blockDim.x) {
-      const int i = e % kPB, j = e / kPB;
-      if (i < bw && j <= i) P[(int64_t)(c0 + i) + (int64_t)(c0 + j) * nr] = D[i][j];
-    }
+  for (int e = tid; e < kPB * kPB; e += blockDim.x) {
+    const int i = e % kPB, j = e / kPB;
+    if (i < bw && j <= i) P[(int64_t)(c0 + i) + (int64_t)(c0 + j) * nr] = D[i][j];
   }
+}
+
+// -------------------------------------------------------------------- TRSM
+// Rows below the diagonal tile of column block kb: X = A D^-T with D the
+// factored tile (read from the panel); items (s, row tile of kTR rows).
+template <typename T>
+__global__ void __launch_bounds__(kTR) k_trsm(const int4* __restrict__ items, int kb, FacArgs<T> a) {
+  __shared__ T D[kPB][kPB + 1];
+  const int4 it = items[blockIdx.x];
+  const int s = it.x, t = it.y;
+  const int w = a.sw[s], nr = a.snr[s];
+  const int c0 = kb * kPB;
+  const int bw = min(kPB, w - c0);
+  T* P = a.L + a.poff[s];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < kPB * kPB; e += blockDim.x) {
+    const int i = e % kPB, j = e / kPB;
+    D[i][j] = (i < bw && j <= i) ? P[(int64_t)(c0 + i) + (int64_t)(c0 + j) * nr] : T(i == j ? 1 : 0);
+  }
+  __syncthreads();
   const int r = c0 + bw + t * kTR + tid;
   if (r < nr) {
     T x[kPB];
@@ -102,6 +116,17 @@ __global__ void __launch_bounds__(kTR) k_potrf_trsm(const int4* __restrict__ ite
     for (int k = 0; k < kPB; k++)
       if (k < bw) P[(int64_t)r + (int64_t)(c0 + k) * nr] = x[k];
   }
+}
+
+// ------------------------------------------------------ clear update matrices
+template <typename T>
+__global__ void __launch_bounds__(256) k_zero_u(const int4* __restrict__ items, FacArgs<T> a) {
+  const int4 it = items[blockIdx.x];
+  const int s = it.x;
+  const int64_t rb = a.snr[s] - a.sw[s];
+  const int64_t lo = (int64_t)it.y * 65536, hi = min(rb * rb, lo + 65536);
+  T* U = a.U + a.uoff[s];
+  for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) U[e] = T(0);
 }
 
 // ------------------------------------------------------- in-panel update
@@ -230,33 +255,57 @@ __global__ void __launch_bounds__(256) k_extend_add(const int4* __restrict__ ite
   }
 }
 
+cudaError_t prof_begin(Prof* pr, cudaStream_t st) {
+  if (!pr) return cudaSuccess;
+  return cudaEventRecord(pr->a, st);
+}
+
+cudaError_t prof_end(Prof* pr, int kind, cudaStream_t st) {
+  if (!pr) return cudaSuccess;
+  cudaError_t e = cudaEventRecord(pr->b, st);
+  if (e) return e;
+  if ((e = cudaEventSynchronize(pr->b))) return e;
+  float ms = 0.f;
+  if ((e = cudaEventElapsedTime(&ms, pr->a, pr->b))) return e;
+  pr->ms[kind] += ms;
+  pr->n[kind] += 1;
+  return cudaSuccess;
+}
+
 template <typename T>
 cudaError_t launch_factor(const FacArgs<T>& a, const FacLists& fl, double delta, double gamma,
-                          cudaStream_t st) {
+                          cudaStream_t st, Prof* prof) {
   cudaError_t e;
   if ((e = cudaMemsetAsync(a.L, 0, sizeof(T) * (size_t)fl.panel_total, st))) return e;
-  if (fl.u_total && (e = cudaMemsetAsync(a.U, 0, sizeof(T) * (size_t)fl.u_total, st))) return e;
   {
     const int threads = 256;
     int64_t blocks = (fl.nslot + threads - 1) / threads;
     if (blocks > 148 * 64) blocks = 148 * 64;
     if (blocks < 1) blocks = 1;
+    if ((e = prof_begin(prof, st))) return e;
     k_assemble<T><<<(unsigned)blocks, threads, 0, st>>>(fl.nslot, fl.slot_pos, fl.src_ptr, fl.srcA, fl.srcB,
                                                          a.Hv, a.Jv, delta, gamma, a.L);
+    if ((e = prof_end(prof, 0, st))) return e;
   }
   for (const Launch& L : *fl.launches) {
     if (L.cnt <= 0) continue;
+    if ((e = prof_begin(prof, st))) return e;
     switch (L.kind) {
-      case 0: k_potrf_trsm<T><<<(unsigned)L.cnt, kTR, 0, st>>>(fl.it_trsm + L.off, L.kb, a); break;
-      case 1: k_panel_update<T><<<(unsigned)L.cnt, 256, 0, st>>>(fl.it_pupd + L.off, L.kb, a); break;
-      case 2: k_syrk<T><<<(unsigned)L.cnt, 256, 0, st>>>(fl.it_syrk + L.off, a); break;
-      case 3: k_extend_add<T><<<(unsigned)L.cnt, 256, 0, st>>>(fl.it_eadd + L.off, a); break;
+      case 0: k_potrf<T><<<(unsigned)L.cnt, 256, 0, st>>>(fl.it_potrf + L.off, L.kb, a); break;
+      case 1: k_trsm<T><<<(unsigned)L.cnt, kTR, 0, st>>>(fl.it_trsm + L.off, L.kb, a); break;
+      case 2: k_panel_update<T><<<(unsigned)L.cnt, 256, 0, st>>>(fl.it_pupd + L.off, L.kb, a); break;
+      case 3: k_syrk<T><<<(unsigned)L.cnt, 256, 0, st>>>(fl.it_syrk + L.off, a); break;
+      case 4: k_extend_add<T><<<(unsigned)L.cnt, 256, 0, st>>>(fl.it_eadd + L.off, a); break;
+      case 5: k_zero_u<T><<<(unsigned)L.cnt, 256, 0, st>>>(fl.it_zero + L.off, a); break;
     }
+    if ((e = prof_end(prof, 1 + L.kind, st))) return e;
   }
   return cudaGetLastError();
 }
 
-template cudaError_t launch_factor<double>(const FacArgs<double>&, const FacLists&, double, double, cudaStream_t);
-template cudaError_t launch_factor<float>(const FacArgs<float>&, const FacLists&, double, double, cudaStream_t);
+template cudaError_t launch_factor<double>(const FacArgs<double>&, const FacLists&, double, double, cudaStream_t,
+                                           Prof*);
+template cudaError_t launch_factor<float>(const FacArgs<float>&, const FacLists&, double, double, cudaStream_t,
+                                          Prof*);
 
 }  // namespace kkt

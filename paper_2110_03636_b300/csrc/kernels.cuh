@@ -20,8 +20,18 @@ struct FacArgs {
   DevStatus* st;
 };
 
+// Optional per-launch timing (profile mode): events around each launch,
+// elapsed time accumulated per kernel kind.
+struct Prof {
+  cudaEvent_t a = nullptr, b = nullptr;
+  double ms[10] = {0};
+  long long n[10] = {0};
+};
+cudaError_t prof_begin(Prof* pr, cudaStream_t st);
+cudaError_t prof_end(Prof* pr, int kind, cudaStream_t st);
+
 struct FacLists {
-  const int4 *it_trsm, *it_pupd, *it_syrk, *it_eadd;
+  const int4 *it_potrf, *it_trsm, *it_pupd, *it_syrk, *it_eadd, *it_zero;
   const int64_t *slot_pos, *src_ptr;
   const int32_t *srcA, *srcB;
   int64_t nslot, panel_total, u_total;
@@ -29,7 +39,8 @@ struct FacLists {
 };
 
 template <typename T>
-cudaError_t launch_factor(const FacArgs<T>& a, const FacLists& fl, double delta, double gamma, cudaStream_t st);
+cudaError_t launch_factor(const FacArgs<T>& a, const FacLists& fl, double delta, double gamma, cudaStream_t st,
+                          Prof* prof = nullptr);
 
 // Persistent CG on the Schur complement (plus the two direct solves).
 template <typename T>

@@ -23,13 +23,10 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
     P.srow[s] = S.sn_rowptr[s];
     P.poff[s] = po;
     po += (int64_t)P.sw[s] * P.snr[s];
-    const int64_t rb = P.snr[s] - P.sw[s];
-    P.uoff[s] = uo;
-    uo += rb * rb;
     for (int32_t j = S.sn_start[s]; j < S.sn_start[s + 1]; j++) col2sn[j] = (int32_t)s;
   }
   P.panel_total = po;
-  P.u_total = uo;
+  (void)uo;
   // relative indices of each child's below rows in its parent's row list
   P.rel.assign(S.sn_rows.size(), -1);
   for (int64_t s = 0; s < ns; s++) {
@@ -44,28 +41,92 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
       P.rel[P.srow[s] + k] = (int32_t)q;
     }
   }
-  // levels (height above the leaves)
+  std::vector<int64_t> kid_ptr(ns + 1, 0);
+  std::vector<int32_t> kids;
+  for (int64_t s = 0; s < ns; s++) if (P.sparent[s] >= 0) kid_ptr[P.sparent[s] + 1]++;
+  for (int64_t s = 0; s < ns; s++) kid_ptr[s + 1] += kid_ptr[s];
+  kids.resize(kid_ptr[ns]);
+  {
+    std::vector<int64_t> fill(kid_ptr.begin(), kid_ptr.end() - 1);
+    for (int64_t s = 0; s < ns; s++) if (P.sparent[s] >= 0) kids[fill[P.sparent[s]]++] = (int32_t)s;
+  }
+  auto children_of = [&](int32_t p) {
+    return std::vector<int32_t>(kids.begin() + kid_ptr[p], kids.begin() + kid_ptr[p + 1]);
+  };
+  // levels: as late as possible -- every front one level below its parent
+  // (level = tree height - 1 - depth), so an update matrix lives for two
+  // levels only and side subtrees run next to the long chains
+  std::vector<int32_t> depth(ns, 0);
+  for (int64_t s = ns - 1; s >= 0; s--)            // parents have larger indices
+    depth[s] = P.sparent[s] >= 0 ? depth[P.sparent[s]] + 1 : 0;
+  const int32_t height = ns ? *std::max_element(depth.begin(), depth.end()) + 1 : 0;
   std::vector<int32_t> level(ns, 0);
-  for (int64_t s = 0; s < ns; s++)
-    if (P.sparent[s] >= 0) level[P.sparent[s]] = std::max(level[P.sparent[s]], level[s] + 1);
-  P.nlevels = ns ? *std::max_element(level.begin(), level.end()) + 1 : 0;
+  for (int64_t s = 0; s < ns; s++) level[s] = height - 1 - depth[s];
+  P.nlevels = height;
   std::vector<std::vector<int32_t>> bylev(P.nlevels);
   for (int64_t s = 0; s < ns; s++) bylev[level[s]].push_back((int32_t)s);
+  // Update matrix U_s lives from s's level (cleared, children added, SYRK)
+  // to its parent's level (extend-add). First-fit placement of these
+  // intervals in one workspace, in order of start level.
+  {
+    struct Blk { int64_t off, size; int32_t end; };
+    std::vector<Blk> live;                  // sorted by offset
+    int64_t top = 0;
+    for (int32_t L = 0; L < P.nlevels; L++) {
+      live.erase(std::remove_if(live.begin(), live.end(), [&](const Blk& b) { return b.end < L; }), live.end());
+      for (int32_t s : bylev[L]) {
+        const int64_t rb = P.snr[s] - P.sw[s];
+        const int64_t size = rb * rb;
+        if (size == 0) { P.uoff[s] = 0; continue; }
+        const int32_t end = P.sparent[s] >= 0 ? level[P.sparent[s]] : L;
+        int64_t off = 0;
+        size_t pos = 0;
+        for (; pos < live.size(); pos++) {
+          if (live[pos].off - off >= size) break;
+          off = std::max(off, live[pos].off + live[pos].size);
+        }
+        live.insert(live.begin() + pos, Blk{off, size, end});
+        P.uoff[s] = off;
+        top = std::max(top, off + size);
+      }
+    }
+    P.u_total = top;
+  }
   for (int32_t L = 0; L < P.nlevels; L++) {
     const auto& F = bylev[L];
+    // clear the update matrices of this level's fronts, then add the children's
+    const int64_t oz = (int64_t)P.it_zero.size() / 4;
+    for (int32_t s : F) {
+      const int64_t rb = P.snr[s] - P.sw[s];
+      for (int64_t c = 0; c < cdiv(rb * rb, 65536); c++) P.it_zero.insert(P.it_zero.end(), {s, (int32_t)c, 0, 0});
+    }
+    const int64_t cz = (int64_t)P.it_zero.size() / 4 - oz;
+    if (cz) P.launches.push_back({5, 0, oz, cz});
+    const int64_t o3 = (int64_t)P.it_eadd.size() / 4;
+    for (int32_t p : F)
+      for (int32_t c : children_of(p)) {
+        const int64_t rb = P.snr[c] - P.sw[c];
+        for (int64_t ct = 0; ct < cdiv(rb, kEC); ct++) P.it_eadd.insert(P.it_eadd.end(), {c, (int32_t)ct, 0, 0});
+      }
+    const int64_t c3 = (int64_t)P.it_eadd.size() / 4 - o3;
+    if (c3) P.launches.push_back({4, 0, o3, c3});
     int32_t wmax = 0;
     for (int32_t s : F) wmax = std::max(wmax, P.sw[s]);
     for (int32_t kb = 0; kb * kPB < wmax; kb++) {
+      const int64_t od = (int64_t)P.it_potrf.size() / 4;
+      for (int32_t s : F)
+        if (kb * kPB < P.sw[s]) P.it_potrf.insert(P.it_potrf.end(), {s, 0, 0, 0});
+      P.launches.push_back({0, kb, od, (int64_t)P.it_potrf.size() / 4 - od});
       const int64_t o0 = (int64_t)P.it_trsm.size() / 4;
       for (int32_t s : F) {
         const int32_t c0 = kb * kPB;
         if (c0 >= P.sw[s]) continue;
         const int32_t bw = std::min(kPB, P.sw[s] - c0);
         const int64_t below = P.snr[s] - c0 - bw;
-        const int64_t nt = std::max<int64_t>(1, cdiv(below, kTR));
-        for (int64_t t = 0; t < nt; t++) { P.it_trsm.insert(P.it_trsm.end(), {s, (int32_t)t, 0, 0}); }
+        for (int64_t t = 0; t < cdiv(below, kTR); t++) P.it_trsm.insert(P.it_trsm.end(), {s, (int32_t)t, 0, 0});
       }
-      P.launches.push_back({0, kb, o0, (int64_t)P.it_trsm.size() / 4 - o0});
+      const int64_t c0n = (int64_t)P.it_trsm.size() / 4 - o0;
+      if (c0n) P.launches.push_back({1, kb, o0, c0n});
       const int64_t o1 = (int64_t)P.it_pupd.size() / 4;
       for (int32_t s : F) {
         const int32_t c0 = kb * kPB;
@@ -79,7 +140,7 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
         }
       }
       const int64_t c1 = (int64_t)P.it_pupd.size() / 4 - o1;
-      if (c1) P.launches.push_back({1, kb, o1, c1});
+      if (c1) P.launches.push_back({2, kb, o1, c1});
     }
     const int64_t o2 = (int64_t)P.it_syrk.size() / 4;
     for (int32_t s : F) {
@@ -89,15 +150,7 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
         for (int64_t tj = 0; tj <= ti; tj++) P.it_syrk.insert(P.it_syrk.end(), {s, (int32_t)ti, (int32_t)tj, 0});
     }
     const int64_t c2 = (int64_t)P.it_syrk.size() / 4 - o2;
-    if (c2) P.launches.push_back({2, 0, o2, c2});
-    const int64_t o3 = (int64_t)P.it_eadd.size() / 4;
-    for (int32_t s : F) {
-      if (P.sparent[s] < 0) continue;
-      const int64_t rb = P.snr[s] - P.sw[s];
-      for (int64_t ct = 0; ct < cdiv(rb, kEC); ct++) P.it_eadd.insert(P.it_eadd.end(), {s, (int32_t)ct, 0, 0});
-    }
-    const int64_t c3 = (int64_t)P.it_eadd.size() / 4 - o3;
-    if (c3) P.launches.push_back({3, 0, o3, c3});
+    if (c2) P.launches.push_back({3, 0, o2, c2});
   }
   // ---------------------------------------------------------- assembly map
   // slot of (row, col) in final labels (row >= col)

@@ -17,8 +17,9 @@ constexpr int kST = 64;      // SYRK tile edge
 constexpr int kEC = 32;      // columns per extend-add item
 
 struct Launch {              // one batched kernel launch of the factorization
-  int32_t kind;              // 0 potrf+trsm, 1 in-panel update, 2 syrk, 3 extend-add
-  int32_t kb;                // column block (kinds 0,1)
+  int32_t kind;              // 0 potrf (diagonal tile), 1 trsm, 2 in-panel update, 3 syrk,
+                             // 4 extend-add, 5 zero update matrices
+  int32_t kb;                // column block (kinds 0-2)
   int64_t off, cnt;          // range in the item array of that kind
 };
 
@@ -35,10 +36,12 @@ struct Plan {
   int64_t panel_total = 0, u_total = 0;
   int32_t nlevels = 0;
   // factor work lists (items are int4: s, a, b, 0)
+  std::vector<int32_t> it_potrf;            // (s) fronts whose column block kb is factored
   std::vector<int32_t> it_trsm;             // (s, row tile) pairs
   std::vector<int32_t> it_pupd;             // (s, row tile, col tile) triples
   std::vector<int32_t> it_syrk;             // (s, ti, tj) triples
-  std::vector<int32_t> it_eadd;             // (s, col tile) pairs
+  std::vector<int32_t> it_eadd;             // (child s, col tile) pairs, at the parent's level
+  std::vector<int32_t> it_zero;             // (s, chunk) update matrices cleared at s's level
   std::vector<Launch> launches;
   // assembly gather: panel slot <- sum of sources (H entry, delta, J pair)
   std::vector<int64_t> slot_pos;            // panel position of each slot
