@@ -46,7 +46,8 @@ typedef enum kkt_status {
   KKT_ERR_OOM = 5,           /* device allocation failed */
   KKT_ERR_CUDA = 6,          /* a CUDA call failed */
   KKT_ERR_TIMEOUT = 7,       /* a bounded wait inside a persistent kernel gave up */
-  KKT_ERR_STATE = 8          /* call out of order (e.g. solve before a successful factor) */
+  KKT_ERR_STATE = 8,         /* call out of order (e.g. solve before a successful factor) */
+  KKT_ERR_TOO_LARGE = 9      /* n + m exceeds KKT_NOALLOC_MAX_ROWS (kkt_residual_noalloc) */
 } kkt_status;
 
 typedef struct kkt_handle_s* kkt_handle;
@@ -197,6 +198,40 @@ kkt_status kkt_get_factor_panels(kkt_handle h, double* panels);
 kkt_status kkt_get_profile(kkt_handle h, double* ms, int64_t* launches, int32_t reset);
 
 kkt_status kkt_destroy(kkt_handle h);
+
+/* ---------------------------------------------------------------------------
+ * Residual without any device allocation. The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc -- code whose
+ * device memory belongs to another allocator (a framework's caching pool, an
+ * application with a fixed memory budget), code running where allocating is
+ * forbidden, or code that must not risk the device synchronisation that
+ * cudaMalloc/cudaFree can cause. Every other entry point allocates in
+ * kkt_analyse; this one allocates nothing.
+ *
+ * Computes res = b - K_delta [dx; dy] for K_delta = [H~ + delta I, J^T; J, 0]
+ * and norms[0] = RR = ||res||_2/||b||_2, norms[1] = BE =
+ * ||res||_2/(||K_delta||_inf ||[dx;dy]||_2 + ||b||_2), norms[2] = ||res||_2,
+ * norms[3] = ||K_delta||_inf (the quantities of Sec. 5.1).
+ *   H_colptr/H_rowidx/H_vals  device, H~ lower triangle (CSC, as for kkt_analyse)
+ *   J_rowptr/J_colidx/J_vals  device, J (CSR); may be NULL when m == 0
+ *   r_x, r_y, dx, dy          device inputs; res_x[n], res_y[m] device outputs
+ *   norms                     device double[4] output
+ * The work is queued on `stream`; the call does not synchronise.
+ * Scratch: a fixed device array of (KKT_NOALLOC_MAX_ROWS + 1184) doubles
+ * (about 8 MiB) that every GPU loading the library holds until the process
+ * exits. n + m > KKT_NOALLOC_MAX_ROWS returns KKT_ERR_TOO_LARGE without
+ * launching anything. The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture. All calls share the array and each clears what it needs,
+ * so calls whose work overlaps on the GPU (different streams, different host
+ * threads) race: serialise them. The residual accumulates with device
+ * atomics, so its last bits may differ from run to run. */
+#define KKT_NOALLOC_MAX_ROWS (1 << 20)
+kkt_status kkt_residual_noalloc(int64_t n, int64_t m, const int64_t* H_colptr, const int32_t* H_rowidx,
+                                const double* H_vals, const int64_t* J_rowptr, const int32_t* J_colidx,
+                                const double* J_vals, double delta, const double* r_x, const double* r_y,
+                                const double* dx, const double* dy, double* res_x, double* res_y,
+                                double* norms, void* stream);
 
 const char* kkt_status_string(kkt_status s);
 

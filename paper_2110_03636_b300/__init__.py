@@ -19,7 +19,8 @@ LIB_PATH = os.path.join(_HERE, "libkkt.so")
 
 KKT_FP64, KKT_MIXED = 0, 1
 STATUS = {0: "ok", 1: "invalid", 2: "not_spd", 3: "cg_breakdown", 4: "cg_maxit",
-          5: "oom", 6: "cuda", 7: "timeout", 8: "state"}
+          5: "oom", 6: "cuda", 7: "timeout", 8: "state", 9: "too_large"}
+NOALLOC_MAX_ROWS = 1 << 20
 
 
 class KKTError(RuntimeError):
@@ -68,11 +69,12 @@ def _load():
     L.kkt_get_symbolic.argtypes = [P] + [P] * 8
     L.kkt_get_factor_panels.argtypes = [P, P]
     L.kkt_get_profile.argtypes = [P, P, P, I32]
+    L.kkt_residual_noalloc.argtypes = [I64, I64, P, P, P, P, P, P, D, P, P, P, P, P, P, P, P]
     L.kkt_destroy.argtypes = [P]
     L.kkt_status_string.argtypes = [I32]
     L.kkt_status_string.restype = C.c_char_p
     for nm in ("kkt_analyse", "kkt_analyse_host", "kkt_factor", "kkt_solve", "kkt_factor_solve_host", "kkt_hsolve", "kkt_get_info",
-               "kkt_inertia", "kkt_symbolic_info_get", "kkt_get_symbolic", "kkt_get_factor_panels", "kkt_get_profile", "kkt_destroy"):
+               "kkt_inertia", "kkt_symbolic_info_get", "kkt_get_symbolic", "kkt_get_factor_panels", "kkt_get_profile", "kkt_residual_noalloc", "kkt_destroy"):
         getattr(L, nm).restype = I32
     return L
 
@@ -80,7 +82,8 @@ def _load():
 _lib = _load()
 EXPORTED = ("kkt_default_options", "kkt_analyse", "kkt_analyse_host", "kkt_factor", "kkt_solve", "kkt_factor_solve_host",
             "kkt_hsolve", "kkt_get_info", "kkt_inertia", "kkt_symbolic_info_get", "kkt_get_symbolic",
-            "kkt_get_factor_panels", "kkt_get_profile", "kkt_destroy", "kkt_status_string")
+            "kkt_get_factor_panels", "kkt_get_profile", "kkt_residual_noalloc", "kkt_destroy",
+            "kkt_status_string")
 KERNEL_KINDS = ("assemble", "potrf", "trsm", "panel_update", "syrk", "extend_add", "zero_u", "cg_persistent",
                 "residual")
 
@@ -208,6 +211,27 @@ def kkt_get_profile(h, reset=False):
     n = np.zeros(10, np.int64)
     _check("kkt_get_profile", _lib.kkt_get_profile(h, ms.ctypes.data, n.ctypes.data, int(bool(reset))))
     return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_KINDS)}
+
+
+def kkt_residual_noalloc(n, m, H_colptr, H_rowidx, H_vals, J_rowptr, J_colidx, J_vals, delta, r_x, r_y, dx, dy,
+                         res_x, res_y, norms, stream=None):
+    """Residual of K_delta without device allocation (for callers that
+    cannot allocate device memory). Every array argument is a CUDA tensor:
+    int64/int32 patterns, float64 values; norms is float64[4] (RR, BE,
+    ||res||, ||K||_inf). Returns the status code; the work is asynchronous."""
+    import torch
+
+    def ptr(t, dt):
+        if t is None:
+            return None
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dt and t.is_contiguous()):
+            raise TypeError(f"expected a contiguous CUDA tensor of {dt}")
+        return t.data_ptr() if t.numel() else None
+    i64, i32, f64 = torch.int64, torch.int32, torch.float64
+    return _lib.kkt_residual_noalloc(int(n), int(m), ptr(H_colptr, i64), ptr(H_rowidx, i32), ptr(H_vals, f64),
+                                     ptr(J_rowptr, i64), ptr(J_colidx, i32), ptr(J_vals, f64), float(delta),
+                                     ptr(r_x, f64), ptr(r_y, f64), ptr(dx, f64), ptr(dy, f64), ptr(res_x, f64),
+                                     ptr(res_y, f64), ptr(norms, f64), _stream(stream))
 
 
 def kkt_destroy(h):

@@ -132,6 +132,7 @@ const char* kkt_status_string(kkt_status s) {
     case KKT_ERR_CUDA: return "CUDA error";
     case KKT_ERR_TIMEOUT: return "bounded wait in a persistent kernel timed out";
     case KKT_ERR_STATE: return "call out of order";
+    case KKT_ERR_TOO_LARGE: return "n + m exceeds the no-allocation scratch (KKT_NOALLOC_MAX_ROWS)";
   }
   return "unknown status";
 }
