@@ -82,7 +82,8 @@ typedef struct kkt_options {
 /* Kernel kinds reported by kkt_get_profile. */
 enum {
   KKT_K_ASSEMBLE = 0, KKT_K_POTRF = 1, KKT_K_TRSM = 2, KKT_K_PANEL_UPDATE = 3, KKT_K_SYRK = 4,
-  KKT_K_EXTEND_ADD = 5, KKT_K_ZERO_U = 6, KKT_K_CG = 7, KKT_K_RESIDUAL = 8, KKT_K_COUNT = 10
+  KKT_K_EXTEND_ADD = 5, KKT_K_ZERO_U = 6, KKT_K_CG = 7, KKT_K_RESIDUAL = 8, KKT_K_TRI_INV = 9,
+  KKT_K_COUNT = 10
 };
 
 /* Result of the last kkt_solve on a handle. */
@@ -107,6 +108,7 @@ typedef struct kkt_symbolic_info {
   int32_t pad;
   double flops;        /* sum_j colcount_j^2 (factor flop count, no explicit zeros) */
   double device_bytes; /* device memory held by the handle */
+  int64_t fwd_depth, bwd_depth;  /* longest dependency chains of the two triangular sweeps */
 } kkt_symbolic_info;
 
 /* Defaults: Algorithm 1's typical parameters (gamma 1e4, delta_2 1e-9), CG
@@ -189,7 +191,8 @@ kkt_status kkt_get_symbolic(kkt_handle h, int32_t* amd, int32_t* perm, int32_t* 
                             int32_t* sn_rows, int32_t* sn_parent);
 
 /* The factor's supernode panels converted to FP64 into host double
- * [panel_entries] (column-major per supernode, ld = its row count). */
+ * [panel_entries] (column-major per supernode, ld = its row count rounded
+ * up to a multiple of 4; the padding rows are not part of L). */
 kkt_status kkt_get_factor_panels(kkt_handle h, double* panels);
 
 /* Accumulated device time (ms) and launch count per kernel kind since the

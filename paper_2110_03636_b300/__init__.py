@@ -47,7 +47,8 @@ class kkt_symbolic_info(C.Structure):
     _fields_ = [("n", C.c_int64), ("m", C.c_int64), ("nsuper", C.c_int64), ("nnz_l", C.c_int64),
                 ("panel_entries", C.c_int64), ("update_entries", C.c_int64), ("sn_rows_total", C.c_int64),
                 ("npieces", C.c_int64), ("nchunks", C.c_int64), ("nlevels", C.c_int32), ("pad", C.c_int32),
-                ("flops", C.c_double), ("device_bytes", C.c_double)]
+                ("flops", C.c_double), ("device_bytes", C.c_double), ("fwd_depth", C.c_int64),
+                ("bwd_depth", C.c_int64)]
 
 
 def _load():
@@ -85,7 +86,7 @@ EXPORTED = ("kkt_default_options", "kkt_analyse", "kkt_analyse_host", "kkt_facto
             "kkt_get_factor_panels", "kkt_get_profile", "kkt_residual_noalloc", "kkt_destroy",
             "kkt_status_string")
 KERNEL_KINDS = ("assemble", "potrf", "trsm", "panel_update", "syrk", "extend_add", "zero_u", "cg_persistent",
-                "residual")
+                "residual", "tri_inv")
 
 
 def _check(fn, code):

@@ -58,19 +58,20 @@ struct kkt_handle_s {
   int64_t nnzH = 0, nnzJ = 0;
   DevArena mem;
   // pattern / plan on the device
-  int32_t *sfirst, *sw, *snr, *sparent, *rel, *sn_rows, *perm;
+  int32_t *sfirst, *sw, *snr, *sld, *sparent, *rel, *sn_rows, *perm;
   int64_t *srow, *poff, *uoff;
   int4 *it_potrf, *it_trsm, *it_pupd, *it_syrk, *it_eadd, *it_zero;
   int64_t *slot_pos, *src_ptr;
   int32_t *srcA, *srcB;
   int32_t *Jcol_perm, *JT_row, *JT_vidx, *Hs_col, *Hs_vidx, *JTo_row, *JTo_vidx, *J_colidx;
   int64_t *JT_ptr, *Hs_ptr, *JTo_ptr, *J_rowptr;
-  int32_t *pc_first, *pc_w, *pc_ld, *pc_nchunk, *pc_need, *ch_piece, *ch_r0, *ch_nr, *ch_k, *ch_tgt;
+  int32_t *pc_first, *pc_w, *pc_ld, *pc_c, *pc_rc0, *pc_nchunk, *pc_need, *hd_tgt;
+  int32_t *ch_piece, *ch_r0, *ch_nr, *ch_k, *ch_tgt;
   int32_t *fwd_items, *bwd_items;
-  int64_t *pc_row, *pc_off, *pc_zoff, *ch_tptr;
+  int64_t *pc_row, *pc_colbase, *pc_inv, *pc_zoff, *hd_tptr, *ch_tptr;
   // values and workspace
   double *Hv, *Jv;
-  void *L, *U, *v, *zpart;
+  void *L, *U, *v, *zpart, *Linv;
   double *rhx, *p, *r, *y, *q, *bS, *red, *res_x, *res_y;
   double *stage_rx, *stage_ry, *stage_dx, *stage_dy;
   int* counters;   // fwd_arrive, fwd_done, bwd_arrive, bwd_done (npieces each), disp[3], bar[2]
@@ -168,7 +169,10 @@ static kkt_status analyse_host(int64_t n, int64_t m, const int64_t* Hp, const in
   RelaxParams rp;
   rp.small = o.relax_small; rp.num = o.relax_num; rp.den = o.relax_den; rp.wmax = o.relax_wmax;
   if (analyse_pattern(n, m, Hp, Hi, Jp, Ji, rp, o.ordering, h->S) != 0) { delete h; return KKT_ERR_INVALID; }
-  if (build_plan(h->S, Hp, Hi, Jp, Ji, o.solve_w, h->P) != 0) { delete h; return KKT_ERR_INVALID; }
+  // tiles of the solve kernel: FP64 keeps the head's chunk 0 shorter so that
+  // its shared-memory staging fits in one SM's 227 KB
+  const int rc = 128, rc0 = o.precision == KKT_FP64 ? 64 : 128;
+  if (build_plan(h->S, Hp, Hi, Jp, Ji, o.solve_w, rc, rc0, h->P) != 0) { delete h; return KKT_ERR_INVALID; }
   if (o.debug_stall_piece >= 0 && o.debug_stall_piece < h->P.npieces) h->P.pc_need[o.debug_stall_piece] += 1;
   h->nnzH = Hp[n];
   h->nnzJ = Jp[m];
@@ -196,7 +200,9 @@ kkt_status kkt_analyse(int64_t n, int64_t m, const int64_t* Hp, const int32_t* H
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device);
   if (!coop) { delete h; return KKT_ERR_CUDA; }
   const bool f64 = o.precision == KKT_FP64;
-  h->grid = f64 ? solve_grid_size<double>(h->device) : solve_grid_size<float>(h->device);
+  h->grid = f64 ? solve_grid_size<double>(h->device, h->P.solve_w, h->P.rc, h->P.rc0)
+                : solve_grid_size<float>(h->device, h->P.solve_w, h->P.rc, h->P.rc0);
+  if (h->grid <= 0) { delete h; return KKT_ERR_INVALID; }
   const Plan& P = h->P;
   DevArena& A = h->mem;
   auto as_int4 = [&](const std::vector<int32_t>& v) {
@@ -204,7 +210,7 @@ kkt_status kkt_analyse(int64_t n, int64_t m, const int64_t* Hp, const int32_t* H
     if (d && !v.empty() && cudaMemcpy(d, v.data(), sizeof(int32_t) * v.size(), cudaMemcpyHostToDevice)) A.failed = true;
     return d;
   };
-  h->sfirst = A.upload(P.sfirst); h->sw = A.upload(P.sw); h->snr = A.upload(P.snr);
+  h->sfirst = A.upload(P.sfirst); h->sw = A.upload(P.sw); h->snr = A.upload(P.snr); h->sld = A.upload(P.sld);
   h->sparent = A.upload(P.sparent); h->rel = A.upload(P.rel); h->sn_rows = A.upload(h->S.sn_rows);
   h->perm = A.upload(h->S.perm);
   h->srow = A.upload(P.srow); h->poff = A.upload(P.poff); h->uoff = A.upload(P.uoff);
@@ -220,8 +226,10 @@ kkt_status kkt_analyse(int64_t n, int64_t m, const int64_t* Hp, const int32_t* H
   h->J_rowptr = A.upload(std::vector<int64_t>(Jp, Jp + m + 1));
   h->J_colidx = A.upload(std::vector<int32_t>(Ji, Ji + h->nnzJ));
   h->pc_first = A.upload(P.pc_first); h->pc_w = A.upload(P.pc_w); h->pc_ld = A.upload(P.pc_ld);
+  h->pc_c = A.upload(P.pc_c); h->pc_rc0 = A.upload(P.pc_rc0);
   h->pc_nchunk = A.upload(P.pc_nchunk); h->pc_need = A.upload(P.pc_need);
-  h->pc_row = A.upload(P.pc_row); h->pc_off = A.upload(P.pc_off); h->pc_zoff = A.upload(P.pc_zoff);
+  h->pc_row = A.upload(P.pc_row); h->pc_colbase = A.upload(P.pc_colbase); h->pc_inv = A.upload(P.pc_inv);
+  h->pc_zoff = A.upload(P.pc_zoff); h->hd_tptr = A.upload(P.hd_tptr); h->hd_tgt = A.upload(P.hd_tgt);
   h->ch_piece = A.upload(P.ch_piece); h->ch_r0 = A.upload(P.ch_r0); h->ch_nr = A.upload(P.ch_nr);
   h->ch_k = A.upload(P.ch_k); h->ch_tptr = A.upload(P.ch_tptr); h->ch_tgt = A.upload(P.ch_tgt);
   h->fwd_items = A.upload(P.fwd_items); h->bwd_items = A.upload(P.bwd_items);
@@ -231,6 +239,7 @@ kkt_status kkt_analyse(int64_t n, int64_t m, const int64_t* Hp, const int32_t* H
   h->U = A.alloc<char>(es * (size_t)P.u_total);
   h->v = A.alloc<char>(es * (size_t)n);
   h->zpart = A.alloc<char>(es * (size_t)P.z_total);
+  h->Linv = A.alloc<char>(es * (size_t)P.inv_total);
   h->rhx = A.alloc<double>(n);
   h->p = A.alloc<double>(m); h->r = A.alloc<double>(m); h->y = A.alloc<double>(m);
   h->q = A.alloc<double>(m); h->bS = A.alloc<double>(m);
@@ -275,7 +284,7 @@ static kkt_status read_status(kkt_handle h, cudaStream_t st) {
 template <typename T>
 static kkt_status factor_impl(kkt_handle h, cudaStream_t st) {
   FacArgs<T> a;
-  a.sfirst = h->sfirst; a.sw = h->sw; a.snr = h->snr; a.sparent = h->sparent; a.rel = h->rel;
+  a.sfirst = h->sfirst; a.sw = h->sw; a.snr = h->snr; a.sld = h->sld; a.sparent = h->sparent; a.rel = h->rel;
   a.srow = h->srow; a.poff = h->poff; a.uoff = h->uoff;
   a.Hv = h->Hv; a.Jv = h->Jv;
   a.L = (T*)h->L; a.U = (T*)h->U; a.st = h->dst;
@@ -287,6 +296,13 @@ static kkt_status factor_impl(kkt_handle h, cudaStream_t st) {
   fl.panel_total = h->P.panel_total; fl.u_total = h->P.u_total;
   fl.launches = &h->P.launches;
   CK(launch_factor<T>(a, fl, h->delta, h->gamma, st, h->profp));
+  InvArgs<T> ia;
+  ia.pc_w = h->pc_w; ia.pc_ld = h->pc_ld; ia.pc_c = h->pc_c;
+  ia.pc_colbase = h->pc_colbase; ia.pc_inv = h->pc_inv;
+  ia.L = (const T*)h->L; ia.Linv = (T*)h->Linv;
+  CK(prof_begin(h->profp, st));
+  CK(launch_tri_inv<T>(ia, h->P.npieces, h->P.solve_w, st));
+  CK(prof_end(h->profp, KKT_K_TRI_INV, st));
   return KKT_OK;
 }
 
@@ -314,8 +330,11 @@ static SolveArgs<T> solve_args(kkt_handle h) {
   const Plan& P = h->P;
   a.n = P.n; a.m = P.m;
   a.sn_rows = h->sn_rows;
-  a.pc_first = h->pc_first; a.pc_w = h->pc_w; a.pc_ld = h->pc_ld; a.pc_nchunk = h->pc_nchunk;
-  a.pc_need = h->pc_need; a.pc_row = h->pc_row; a.pc_off = h->pc_off; a.pc_zoff = h->pc_zoff;
+  a.pc_first = h->pc_first; a.pc_w = h->pc_w; a.pc_ld = h->pc_ld; a.pc_c = h->pc_c; a.pc_rc0 = h->pc_rc0;
+  a.pc_nchunk = h->pc_nchunk; a.pc_need = h->pc_need; a.pc_row = h->pc_row; a.pc_colbase = h->pc_colbase;
+  a.pc_inv = h->pc_inv; a.pc_zoff = h->pc_zoff; a.hd_tptr = h->hd_tptr; a.hd_tgt = h->hd_tgt;
+  a.sw = P.solve_w; a.rc = P.rc; a.rc0 = P.rc0;
+  a.Linv = (const T*)h->Linv;
   a.ch_piece = h->ch_piece; a.ch_r0 = h->ch_r0; a.ch_nr = h->ch_nr; a.ch_k = h->ch_k;
   a.ch_tptr = h->ch_tptr; a.ch_tgt = h->ch_tgt;
   a.fwd_items = h->fwd_items; a.bwd_items = h->bwd_items;
@@ -476,6 +495,7 @@ kkt_status kkt_symbolic_info_get(kkt_handle h, kkt_symbolic_info* o) {
   o->panel_entries = h->P.panel_total; o->update_entries = h->P.u_total;
   o->sn_rows_total = (int64_t)h->S.sn_rows.size();
   o->npieces = h->P.npieces; o->nchunks = h->P.nchunks; o->nlevels = h->P.nlevels;
+  o->fwd_depth = h->P.fwd_depth; o->bwd_depth = h->P.bwd_depth;
   o->flops = h->S.flops;
   o->device_bytes = (double)h->mem.bytes;
   return KKT_OK;

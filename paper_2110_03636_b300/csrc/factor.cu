@@ -45,14 +45,14 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_potrf(const int4* __restrict__ items, int kb, FacArgs<T> a) {
   __shared__ T D[kPB][kPB + 1];
   const int s = items[blockIdx.x].x;
-  const int w = a.sw[s], nr = a.snr[s];
+  const int w = a.sw[s], nr = a.snr[s], ld = a.sld[s];
   const int c0 = kb * kPB;
   const int bw = min(kPB, w - c0);
   T* P = a.L + a.poff[s];
   const int tid = threadIdx.x;
   for (int e = tid; e < kPB * kPB; e += blockDim.x) {
     const int i = e % kPB, j = e / kPB;
-    D[i][j] = (i < bw && j <= i) ? P[(int64_t)(c0 + i) + (int64_t)(c0 + j) * nr] : T(0);
+    D[i][j] = (i < bw && j <= i) ? P[(int64_t)(c0 + i) + (int64_t)(c0 + j) * ld] : T(0);
   }
   __syncthreads();
   for (int j = 0; j < bw; j++) {
@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(256) k_potrf(const int4* __restrict__ items, i
   }
   for (int e = tid; e < kPB * kPB; e += blockDim.x) {
     const int i = e % kPB, j = e / kPB;
-    if (i < bw && j <= i) P[(int64_t)(c0 + i) + (int64_t)(c0 + j) * nr] = D[i][j];
+    if (i < bw && j <= i) P[(int64_t)(c0 + i) + (int64_t)(c0 + j) * ld] = D[i][j];
   }
 }
 
@@ -88,21 +88,21 @@ __global__ void __launch_bounds__(kTR) k_trsm(const int4* __restrict__ items, in
   __shared__ T D[kPB][kPB + 1];
   const int4 it = items[blockIdx.x];
   const int s = it.x, t = it.y;
-  const int w = a.sw[s], nr = a.snr[s];
+  const int w = a.sw[s], nr = a.snr[s], ld = a.sld[s];
   const int c0 = kb * kPB;
   const int bw = min(kPB, w - c0);
   T* P = a.L + a.poff[s];
   const int tid = threadIdx.x;
   for (int e = tid; e < kPB * kPB; e += blockDim.x) {
     const int i = e % kPB, j = e / kPB;
-    D[i][j] = (i < bw && j <= i) ? P[(int64_t)(c0 + i) + (int64_t)(c0 + j) * nr] : T(i == j ? 1 : 0);
+    D[i][j] = (i < bw && j <= i) ? P[(int64_t)(c0 + i) + (int64_t)(c0 + j) * ld] : T(i == j ? 1 : 0);
   }
   __syncthreads();
   const int r = c0 + bw + t * kTR + tid;
   if (r < nr) {
     T x[kPB];
 #pragma unroll
-    for (int k = 0; k < kPB; k++) x[k] = (k < bw) ? P[(int64_t)r + (int64_t)(c0 + k) * nr] : T(0);
+    for (int k = 0; k < kPB; k++) x[k] = (k < bw) ? P[(int64_t)r + (int64_t)(c0 + k) * ld] : T(0);
 #pragma unroll
     for (int j = 0; j < kPB; j++) {
       if (j < bw) {
@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(kTR) k_trsm(const int4* __restrict__ items, in
     }
 #pragma unroll
     for (int k = 0; k < kPB; k++)
-      if (k < bw) P[(int64_t)r + (int64_t)(c0 + k) * nr] = x[k];
+      if (k < bw) P[(int64_t)r + (int64_t)(c0 + k) * ld] = x[k];
   }
 }
 
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(256) k_panel_update(const int4* __restrict__ i
   __shared__ T Bs[kPB][kPB + 1];
   const int4 it = items[blockIdx.x];
   const int s = it.x, rt = it.y, ct = it.z;
-  const int w = a.sw[s], nr = a.snr[s];
+  const int w = a.sw[s], nr = a.snr[s], ld = a.sld[s];
   const int c0 = kb * kPB;
   const int bw = min(kPB, w - c0);
   const int cstart = c0 + bw + ct * kPB;
@@ -150,11 +150,11 @@ __global__ void __launch_bounds__(256) k_panel_update(const int4* __restrict__ i
   const int tid = threadIdx.x;
   for (int e = tid; e < kUR * kPB; e += blockDim.x) {
     const int i = e % kUR, k = e / kUR;
-    As[i][k] = (i < rn && k < bw) ? P[(int64_t)(rstart + i) + (int64_t)(c0 + k) * nr] : T(0);
+    As[i][k] = (i < rn && k < bw) ? P[(int64_t)(rstart + i) + (int64_t)(c0 + k) * ld] : T(0);
   }
   for (int e = tid; e < kPB * kPB; e += blockDim.x) {
     const int j = e % kPB, k = e / kPB;
-    Bs[j][k] = (j < cw && k < bw) ? P[(int64_t)(cstart + j) + (int64_t)(c0 + k) * nr] : T(0);
+    Bs[j][k] = (j < cw && k < bw) ? P[(int64_t)(cstart + j) + (int64_t)(c0 + k) * ld] : T(0);
   }
   __syncthreads();
   const int i = tid % kUR;            // consecutive threads -> consecutive rows
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(256) k_panel_update(const int4* __restrict__ i
   for (int q = 0; q < 8; q++) {
     const int j = jg * 8 + q;
     if (i < rn && j < cw && rstart + i >= cstart + j)
-      P[(int64_t)(rstart + i) + (int64_t)(cstart + j) * nr] -= acc[q];
+      P[(int64_t)(rstart + i) + (int64_t)(cstart + j) * ld] -= acc[q];
   }
 }
 
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(256) k_syrk(const int4* __restrict__ items, Fa
   __shared__ T Bs[KC][kST + 1];
   const int4 it = items[blockIdx.x];
   const int s = it.x, ti = it.y, tj = it.z;
-  const int w = a.sw[s], nr = a.snr[s];
+  const int w = a.sw[s], nr = a.snr[s], ld = a.sld[s];
   const int rb = nr - w;
   const T* P = a.L + a.poff[s];
   T* U = a.U + a.uoff[s];
@@ -200,8 +200,8 @@ __global__ void __launch_bounds__(256) k_syrk(const int4* __restrict__ items, Fa
     for (int e = tid; e < KC * kST; e += blockDim.x) {
       const int r = e % kST, k = e / kST;
       const bool kin = k0 + k < w;
-      As[k][r] = (kin && i0 + r < rb) ? P[(int64_t)(w + i0 + r) + (int64_t)(k0 + k) * nr] : T(0);
-      Bs[k][r] = (kin && j0 + r < rb) ? P[(int64_t)(w + j0 + r) + (int64_t)(k0 + k) * nr] : T(0);
+      As[k][r] = (kin && i0 + r < rb) ? P[(int64_t)(w + i0 + r) + (int64_t)(k0 + k) * ld] : T(0);
+      Bs[k][r] = (kin && j0 + r < rb) ? P[(int64_t)(w + j0 + r) + (int64_t)(k0 + k) * ld] : T(0);
     }
     __syncthreads();
 #pragma unroll
@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(256) k_extend_add(const int4* __restrict__ ite
   const int s = it.x, ct = it.y;
   const int p = a.sparent[s];
   const int w = a.sw[s], rb = a.snr[s] - w;
-  const int wp = a.sw[p], nrp = a.snr[p], rbp = nrp - wp;
+  const int wp = a.sw[p], nrp = a.snr[p], rbp = nrp - wp, ldp = a.sld[p];
   const int32_t* rel = a.rel + a.srow[s] + w;
   const T* Us = a.U + a.uoff[s];
   T* Pp = a.L + a.poff[p];
@@ -249,11 +249,53 @@ __global__ void __launch_bounds__(256) k_extend_add(const int4* __restrict__ ite
     for (int i = j + threadIdx.x; i < rb; i += blockDim.x) {
       const int ai = rel[i];
       const T v = Us[(int64_t)i + (int64_t)j * rb];
-      if (b < wp) atomicAdd(&Pp[(int64_t)ai + (int64_t)b * nrp], v);
+      if (b < wp) atomicAdd(&Pp[(int64_t)ai + (int64_t)b * ldp], v);
       else atomicAdd(&Up[(int64_t)(ai - wp) + (int64_t)(b - wp) * rbp], v);
     }
   }
 }
+
+// ---------------------------------------------------------- triangle inverses
+// For every triangular-solve piece: X = T^-1 of its pw x pw diagonal
+// triangle T (lower), stored column-major with ld = round4(pw), so that the
+// solve applies T^-1 as a dense mat-vec. Thread k computes column k by
+// forward substitution; T is staged in shared memory.
+template <typename T>
+__global__ void __launch_bounds__(128) k_tri_inv(InvArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Ts = (T*)smem_raw;
+  const int p = blockIdx.x;
+  const int pw = a.pc_w[p], ld = a.pc_ld[p], c = a.pc_c[p];
+  const int ldi = (pw + 3) & ~3;
+  const T* L = a.L + a.pc_colbase[p] + c;      // (row c, col c) of the supernode panel
+  for (int e = threadIdx.x; e < pw * pw; e += blockDim.x) {
+    const int i = e % pw, j = e / pw;
+    Ts[i + j * pw] = (i >= j) ? L[(int64_t)i + (int64_t)j * ld] : T(0);
+  }
+  __syncthreads();
+  T* X = a.Linv + a.pc_inv[p];
+  for (int k = threadIdx.x; k < pw; k += blockDim.x) {
+    T* xk = X + (int64_t)k * ldi;
+    for (int i = 0; i < k; i++) xk[i] = T(0);
+    xk[k] = T(1) / Ts[k + k * pw];
+    for (int i = k + 1; i < pw; i++) {
+      T s = T(0);
+      for (int j = k; j < i; j++) s += Ts[i + j * pw] * xk[j];
+      xk[i] = -s / Ts[i + i * pw];
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_tri_inv(const InvArgs<T>& a, int64_t npieces, int max_pw, cudaStream_t st) {
+  const size_t smem = sizeof(T) * (size_t)max_pw * max_pw;
+  cudaError_t e = cudaFuncSetAttribute(k_tri_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e) return e;
+  k_tri_inv<T><<<(unsigned)npieces, 128, smem, st>>>(a);
+  return cudaGetLastError();
+}
+template cudaError_t launch_tri_inv<double>(const InvArgs<double>&, int64_t, int, cudaStream_t);
+template cudaError_t launch_tri_inv<float>(const InvArgs<float>&, int64_t, int, cudaStream_t);
 
 cudaError_t prof_begin(Prof* pr, cudaStream_t st) {
   if (!pr) return cudaSuccess;

@@ -12,7 +12,7 @@ namespace kkt {
 
 template <typename T>
 struct FacArgs {
-  const int32_t *sfirst, *sw, *snr, *sparent, *rel;
+  const int32_t *sfirst, *sw, *snr, *sld, *sparent, *rel;
   const int64_t *srow, *poff, *uoff;
   const double *Hv, *Jv;
   T* L;
@@ -39,6 +39,16 @@ struct FacLists {
 };
 
 template <typename T>
+struct InvArgs {
+  const int32_t *pc_w, *pc_ld, *pc_c;
+  const int64_t *pc_colbase, *pc_inv;
+  const T* L;
+  T* Linv;
+};
+template <typename T>
+cudaError_t launch_tri_inv(const InvArgs<T>& a, int64_t npieces, int max_pw, cudaStream_t st);
+
+template <typename T>
 cudaError_t launch_factor(const FacArgs<T>& a, const FacLists& fl, double delta, double gamma, cudaStream_t st,
                           Prof* prof = nullptr);
 
@@ -48,14 +58,17 @@ struct SolveArgs {
   int64_t n, m;
   // solve DAG
   const int32_t* sn_rows;
-  const int32_t *pc_first, *pc_w, *pc_ld, *pc_nchunk, *pc_need;
-  const int64_t *pc_row, *pc_off, *pc_zoff;
+  const int32_t *pc_first, *pc_w, *pc_ld, *pc_c, *pc_rc0, *pc_nchunk, *pc_need;
+  const int64_t *pc_row, *pc_colbase, *pc_inv, *pc_zoff, *hd_tptr;
+  const int32_t* hd_tgt;
   const int32_t *ch_piece, *ch_r0, *ch_nr, *ch_k;
   const int64_t* ch_tptr;
   const int32_t* ch_tgt;
   const int32_t *fwd_items, *bwd_items;
   int64_t nitems;
+  int32_t sw, rc, rc0;  // piece width and chunk rows the shared-memory tiles are sized for
   const T* L;
+  const T* Linv;
   // J (CSR, permuted column labels) and J^T (by permuted column)
   const int64_t* J_rowptr;
   const int32_t* Jcol_perm;
@@ -85,7 +98,8 @@ struct SolveArgs {
 template <typename T>
 cudaError_t launch_solve(const SolveArgs<T>& a, int grid, cudaStream_t st);
 template <typename T>
-int solve_grid_size(int device);
+int solve_grid_size(int device, int sw, int rc, int rc0);
+size_t solve_smem_bytes(size_t elem, int sw, int rc, int rc0);
 
 // FP64 residual of K_delta = [H~ + delta I, J^T; J, 0] (original labels):
 // res = b - K x, and norms into DevStatus (rr, be, ...).

@@ -8,11 +8,11 @@ namespace kkt {
 static inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const int64_t* Jp,
-               const int32_t* Ji, int32_t solve_w, Plan& P) {
+               const int32_t* Ji, int32_t solve_w, int32_t rc, int32_t rc0, Plan& P) {
   P = Plan();
   const int64_t n = S.n, m = S.m, ns = S.ns;
   P.n = n; P.m = m; P.ns = ns;
-  P.sfirst.resize(ns); P.sw.resize(ns); P.snr.resize(ns); P.srow.resize(ns);
+  P.sfirst.resize(ns); P.sw.resize(ns); P.snr.resize(ns); P.sld.resize(ns); P.srow.resize(ns);
   P.poff.resize(ns); P.uoff.resize(ns); P.sparent = S.sn_parent;
   std::vector<int32_t> col2sn(n);
   int64_t po = 0, uo = 0;
@@ -20,9 +20,10 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
     P.sfirst[s] = S.sn_start[s];
     P.sw[s] = S.sn_start[s + 1] - S.sn_start[s];
     P.snr[s] = (int32_t)(S.sn_rowptr[s + 1] - S.sn_rowptr[s]);
+    P.sld[s] = (P.snr[s] + 3) & ~3;
     P.srow[s] = S.sn_rowptr[s];
     P.poff[s] = po;
-    po += (int64_t)P.sw[s] * P.snr[s];
+    po += (int64_t)P.sw[s] * P.sld[s];
     for (int32_t j = S.sn_start[s]; j < S.sn_start[s + 1]; j++) col2sn[j] = (int32_t)s;
   }
   P.panel_total = po;
@@ -159,7 +160,7 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
     const int32_t* R = S.sn_rows.data() + P.srow[s];
     const int32_t* pos = std::lower_bound(R, R + P.snr[s], r);
     if (pos == R + P.snr[s] || *pos != r) return (int64_t)-1;   // not in the structure
-    return P.poff[s] + (int64_t)(c - P.sfirst[s]) * P.snr[s] + (pos - R);
+    return P.poff[s] + (int64_t)(c - P.sfirst[s]) * P.sld[s] + (pos - R);
   };
   struct Src { int64_t slot; int32_t a, b; };
   std::vector<Src> src;
@@ -230,6 +231,8 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
   }
   // ---------------------------------------------------------- solve DAG
   P.solve_w = solve_w;
+  P.rc = rc;
+  P.rc0 = rc0;
   std::vector<int32_t> col2piece(n);
   for (int64_t s = 0; s < ns; s++) {
     for (int32_t c = 0; c < P.sw[s]; c += solve_w) {
@@ -238,52 +241,67 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
       P.pc_first.push_back(P.sfirst[s] + c);
       P.pc_w.push_back(pw);
       P.pc_nr.push_back(P.snr[s] - c);
-      P.pc_ld.push_back(P.snr[s]);
+      P.pc_ld.push_back(P.sld[s]);
+      P.pc_c.push_back(c);
       P.pc_row.push_back(P.srow[s] + c);
-      P.pc_off.push_back(P.poff[s] + (int64_t)c * P.snr[s] + c);
-      P.max_pw = std::max(P.max_pw, pw);
+      P.pc_colbase.push_back(P.poff[s] + (int64_t)c * P.sld[s]);
+      P.pc_inv.push_back(P.inv_total);
+      P.inv_total += (int64_t)pw * ((pw + 3) & ~3);
       for (int32_t j = 0; j < pw; j++) col2piece[P.sfirst[s] + c + j] = pid;
     }
   }
   P.npieces = (int64_t)P.pc_first.size();
   P.pc_zoff.resize(P.npieces);
   P.pc_nchunk.resize(P.npieces);
+  P.pc_rc0.resize(P.npieces);
   P.pc_need.assign(P.npieces, 0);
   std::vector<int32_t> tg;
+  auto targets = [&](int64_t p, int32_t r0, int32_t nr, std::vector<int32_t>& out) {
+    out.clear();
+    for (int32_t i = 0; i < nr; i++) out.push_back(col2piece[S.sn_rows[P.pc_row[p] + r0 + i]]);
+    out.erase(std::unique(out.begin(), out.end()), out.end());   // rows ascending => pieces ascending
+  };
   for (int64_t p = 0; p < P.npieces; p++) {
     const int32_t pw = P.pc_w[p];
-    int32_t rc = std::max(32, std::min(256, (int32_t)(16384 / std::max(1, pw))));
-    rc = (rc / 32) * 32;
-    const int64_t below = P.pc_nr[p] - pw;
-    const int32_t nch = (int32_t)cdiv(below, rc);
+    const int32_t below = P.pc_nr[p] - pw;
+    const int32_t r0n = std::min(below, rc0);
+    P.pc_rc0[p] = r0n;
+    P.hd_tptr.push_back((int64_t)P.hd_tgt.size());
+    targets(p, pw, r0n, tg);
+    for (int32_t t : tg) { P.hd_tgt.push_back(t); P.pc_need[t]++; }
+    const int32_t rest = below - r0n;
+    const int32_t nch = (int32_t)cdiv(rest, rc);
     P.pc_nchunk[p] = nch;
     P.pc_zoff[p] = P.z_total;
     P.z_total += (int64_t)nch * pw;
     for (int32_t k = 0; k < nch; k++) {
-      const int32_t r0 = pw + k * rc;
-      const int32_t nr = (int32_t)std::min<int64_t>(rc, P.pc_nr[p] - r0);
+      const int32_t r0 = pw + r0n + k * rc;
+      const int32_t nr = std::min(rc, P.pc_nr[p] - r0);
       P.ch_piece.push_back((int32_t)p);
       P.ch_r0.push_back(r0);
       P.ch_nr.push_back(nr);
       P.ch_k.push_back(k);
       P.ch_tptr.push_back((int64_t)P.ch_tgt.size());
-      tg.clear();
-      for (int32_t i = 0; i < nr; i++) tg.push_back(col2piece[S.sn_rows[P.pc_row[p] + r0 + i]]);
-      tg.erase(std::unique(tg.begin(), tg.end()), tg.end());   // rows ascending => pieces ascending
+      targets(p, r0, nr, tg);
       for (int32_t t : tg) { P.ch_tgt.push_back(t); P.pc_need[t]++; }
     }
   }
+  P.hd_tptr.push_back((int64_t)P.hd_tgt.size());
   P.nchunks = (int64_t)P.ch_piece.size();
   P.ch_tptr.push_back((int64_t)P.ch_tgt.size());
   // dispatch order: by depth in the dependency DAG, so that items whose inputs
   // are ready are handed out first
   {
-    // forward: head(p) after all chunks targeting p; chunk after its head
-    std::vector<int64_t> hd(P.npieces, 0), cd(P.nchunks, 0);
     std::vector<int64_t> chunk_first(P.npieces + 1, 0);
     for (int64_t c = 0; c < P.nchunks; c++) chunk_first[P.ch_piece[c] + 1]++;
     for (int64_t p = 0; p < P.npieces; p++) chunk_first[p + 1] += chunk_first[p];
+    // forward: head(p) after the heads/chunks whose rows hit p; chunk after its head
+    std::vector<int64_t> hd(P.npieces, 0), cd(P.nchunks, 0);
     for (int64_t p = 0; p < P.npieces; p++) {       // pieces are in topological order
+      for (int64_t t = P.hd_tptr[p]; t < P.hd_tptr[p + 1]; t++) {
+        const int32_t q = P.hd_tgt[t];
+        hd[q] = std::max(hd[q], hd[p] + 1);
+      }
       for (int64_t c = chunk_first[p]; c < chunk_first[p + 1]; c++) {
         cd[c] = hd[p] + 1;
         for (int64_t t = P.ch_tptr[c]; t < P.ch_tptr[c + 1]; t++) {
@@ -293,14 +311,16 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
       }
     }
     std::vector<std::pair<int64_t, int32_t>> ord;
-    for (int64_t p = 0; p < P.npieces; p++) ord.push_back({hd[p] * 2, (int32_t)(-1 - p)});
+    for (int64_t p = 0; p < P.npieces; p++) { ord.push_back({hd[p] * 2, (int32_t)(-1 - p)}); P.fwd_depth = std::max(P.fwd_depth, hd[p]); }
     for (int64_t c = 0; c < P.nchunks; c++) ord.push_back({cd[c] * 2 + 1, (int32_t)c});
     std::stable_sort(ord.begin(), ord.end(), [](auto& a, auto& b) { return a.first < b.first; });
     for (auto& o : ord) P.fwd_items.push_back(o.second);
-    // backward: chunk after the heads of its targets; head after its chunks
+    // backward: chunk after the heads of its targets; head after its chunks and
+    // after the heads of its chunk-0 targets
     std::vector<int64_t> bh(P.npieces, 0), bc(P.nchunks, 0);
     for (int64_t p = P.npieces - 1; p >= 0; p--) {
       int64_t d = 0;
+      for (int64_t t = P.hd_tptr[p]; t < P.hd_tptr[p + 1]; t++) d = std::max(d, bh[P.hd_tgt[t]] + 1);
       for (int64_t c = chunk_first[p]; c < chunk_first[p + 1]; c++) {
         int64_t e = 0;
         for (int64_t t = P.ch_tptr[c]; t < P.ch_tptr[c + 1]; t++) e = std::max(e, bh[P.ch_tgt[t]] + 1);
@@ -308,6 +328,7 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
         d = std::max(d, e + 1);
       }
       bh[p] = d;
+      P.bwd_depth = std::max(P.bwd_depth, d);
     }
     ord.clear();
     for (int64_t p = 0; p < P.npieces; p++) ord.push_back({bh[p] * 2 + 1, (int32_t)(-1 - p)});

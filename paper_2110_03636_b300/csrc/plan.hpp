@@ -27,8 +27,9 @@ struct Plan {
   int64_t n = 0, m = 0, ns = 0;
   // supernodes
   std::vector<int32_t> sfirst, sw, snr;     // first column, width, rows
+  std::vector<int32_t> sld;                 // panel leading dimension = snr rounded up to 4
   std::vector<int64_t> srow;                // offset of the row list in sn_rows
-  std::vector<int64_t> poff;                // panel offset (column-major, ld = snr)
+  std::vector<int64_t> poff;                // panel offset (column-major, ld = sld; multiple of 4)
   std::vector<int64_t> uoff;                // update-matrix offset (rb x rb, ld = rb)
   std::vector<int32_t> sparent;
   std::vector<int32_t> rel;                 // per sn_rows slot: position of a child's below
@@ -57,24 +58,33 @@ struct Plan {
   // J^T in original labels (residual)
   std::vector<int64_t> JTo_ptr;
   std::vector<int32_t> JTo_row, JTo_vidx;
-  // solve DAG over column pieces of width <= solve_w
-  int32_t solve_w = 128;
+  // solve DAG over column pieces of width <= solve_w. A piece's "head" applies
+  // the inverse of its diagonal triangle and its first rc0 rows below ("chunk
+  // 0"); the remaining rows form separate chunks of at most rc rows.
+  int32_t solve_w = 128, rc = 128, rc0 = 128;
   int64_t npieces = 0, nchunks = 0;
   std::vector<int32_t> pc_first, pc_w, pc_nr, pc_ld; // piece: first column, width, rows from its first row, ld
+  std::vector<int32_t> pc_c;                // the piece's first row/column inside its supernode
+  std::vector<int32_t> pc_rc0;              // rows of the fused chunk 0
   std::vector<int64_t> pc_row;              // offset in sn_rows of the piece's first row
-  std::vector<int64_t> pc_off;              // panel offset of the piece's diagonal entry
+  std::vector<int64_t> pc_colbase;          // panel offset of (supernode row 0, piece column 0)
+  std::vector<int64_t> pc_inv;              // offset of the inverse of its triangle (ld = round4(pw))
   std::vector<int64_t> pc_zoff;             // offset of its partial-sum slots
-  std::vector<int32_t> pc_nchunk;           // row chunks below its triangle
-  std::vector<int32_t> pc_need;             // chunks targeting the piece (forward)
+  std::vector<int32_t> pc_nchunk;           // separate chunks
+  std::vector<int32_t> pc_need;             // heads + chunks whose rows hit the piece (forward)
+  std::vector<int64_t> hd_tptr;             // targets of each head's chunk 0
+  std::vector<int32_t> hd_tgt;
   std::vector<int32_t> ch_piece, ch_r0, ch_nr, ch_k;  // chunk: piece, first row (piece-local), rows, index
   std::vector<int64_t> ch_tptr;             // targets of each chunk (distinct pieces)
   std::vector<int32_t> ch_tgt;
   std::vector<int32_t> fwd_items, bwd_items; // >= 0 chunk id, < 0 head of piece (-1 - p)
+  int64_t inv_total = 0;
+  int64_t fwd_depth = 0, bwd_depth = 0;     // longest dependency chains of the sweeps
   int64_t z_total = 0;
   int32_t max_pw = 0;
 };
 
 int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const int64_t* Jp,
-               const int32_t* Ji, int32_t solve_w, Plan& P);
+               const int32_t* Ji, int32_t solve_w, int32_t rc, int32_t rc0, Plan& P);
 
 }  // namespace kkt

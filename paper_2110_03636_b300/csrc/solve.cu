@@ -21,17 +21,34 @@
 namespace kkt {
 
 constexpr int kSolveThreads = 256;
-constexpr int kSWMax = 256;
+constexpr int kAux = 512;
 
-template <typename T>
-struct SolveSmem {
-  T vec[kSWMax];
-  T aux[kSolveThreads];
-  double dred[(kSolveThreads / 32) * 2];
-  double bcast[2];
+// Static shared state; the tiles live in dynamic shared memory.
+struct SolveSmemHdr {
+  unsigned long long mbar;   // completion of the bulk copies of the current item
+  unsigned phase;
   int item;
   int flag;
+  double dred[(kSolveThreads / 32) * 2];
+  double bcast[2];
 };
+
+template <typename T>
+struct Tiles {
+  T* A;     // inverse of the piece triangle, or a chunk tile
+  T* B;     // chunk-0 tile of a head
+  T* vec;   // sw
+  T* vec2;  // sw
+  T* aux;   // kAux
+  int csA, csB;  // column strides of the chunk tiles
+};
+
+size_t solve_smem_bytes(size_t elem, int sw, int rc, int rc0) {
+  const size_t ldi = (size_t)((sw + 3) & ~3);
+  const size_t a = (size_t)sw * (ldi > (size_t)rc + 8 ? ldi : (size_t)rc + 8);
+  const size_t b = (size_t)sw * (size_t)(rc0 + 8);
+  return elem * (a + b + 2 * (size_t)sw + kAux) + 16;
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -44,8 +61,283 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
+// ------------------------------------------------------- TMA bulk copies
+__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* m) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(m)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* m, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(m)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long* m, unsigned phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(saddr(m)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, unsigned long long* m) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   saddr(dst)),
+               "l"(src), "r"(bytes), "r"(saddr(m))
+               : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// All threads: wait for the current bulk copies (bounded). On timeout the
+// abort word is set and the wait is retried once more, bounded, so that no
+// copy is left in flight into this CTA's shared memory.
 template <typename T>
-__device__ bool grid_barrier(const SolveArgs<T>& a, SolveSmem<T>& sm) {
+__device__ bool mbar_wait(const SolveArgs<T>& a, SolveSmemHdr& h) {
+  const unsigned ph = h.phase;
+  bool ok = mbar_test(&h.mbar, ph);
+  if (!ok) {
+    long long t0 = clock64();
+    while (!(ok = mbar_test(&h.mbar, ph))) {
+      if (clock64() - t0 > a.spin) {
+        atomicExch(&a.st->abort, 1);
+        t0 = clock64();
+        while (!mbar_test(&h.mbar, ph) && clock64() - t0 < a.spin) {}
+        break;
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) h.phase ^= 1u;
+  __syncthreads();
+  return ok;
+}
+
+// Warp 0 queues bulk copies of the piece columns [0, pw), piece rows
+// [r0, r0 + nrows), into `tile` (column stride cs); 16-byte aligned by
+// starting at the supernode row rounded down to 4 (offset returned).
+template <typename T>
+__device__ int stage_cols(const SolveArgs<T>& a, int p, int r0, int nrows, T* tile, int cs, uint32_t& bytes_out,
+                          unsigned long long* mbar, bool issue) {
+  const int ld = a.pc_ld[p], c = a.pc_c[p], pw = a.pc_w[p];
+  const int R0 = c + r0;
+  const int A0 = R0 & ~3;
+  const int E = (R0 + nrows + 3) & ~3;
+  const uint32_t bytes = (uint32_t)(E - A0) * (uint32_t)sizeof(T);
+  bytes_out = bytes * (uint32_t)pw;
+  if (issue) {
+    const T* base = a.L + a.pc_colbase[p] + A0;
+    for (int k = threadIdx.x; k < pw; k += 32) bulk_g2s(tile + (int64_t)k * cs, base + (int64_t)k * ld, bytes, mbar);
+  }
+  return R0 - A0;
+}
+
+// --------------------------------------------------------------- forward
+template <typename T>
+__device__ bool fwd_head(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>& t, int p, int e) {
+  const int tid = threadIdx.x;
+  const int pw = a.pc_w[p], f = a.pc_first[p], rn = a.pc_rc0[p];
+  const int ldi = (pw + 3) & ~3;
+  int d0 = 0;
+  if (tid < 32) {
+    uint32_t b1 = 0;
+    if (tid == 0) fence_proxy_async();
+    const uint32_t binv = (uint32_t)(pw * ldi * sizeof(T));
+    if (rn > 0) stage_cols(a, p, pw, rn, t.B, t.csB, b1, &h.mbar, false);
+    if (tid == 0) mbar_expect_tx(&h.mbar, binv + b1);
+    __syncwarp();
+    if (tid == 0) bulk_g2s(t.A, a.Linv + a.pc_inv[p], binv, &h.mbar);
+    if (rn > 0) d0 = stage_cols(a, p, pw, rn, t.B, t.csB, b1, &h.mbar, true);
+    if (tid == 0) h.flag = wait_geq(&a.fwd_arrive[p], e * a.pc_need[p], a.st, a.spin);
+  }
+  __syncthreads();
+  const bool dep = h.flag != 0;
+  if (dep)
+    for (int i = tid; i < pw; i += blockDim.x) t.vec[i] = ldcg(&a.v[f + i]);
+  if (!mbar_wait(a, h) || !dep) return false;
+  d0 = (a.pc_c[p] + pw) & 3;
+  // y = T^-1 b (full rows of the inverse; its upper part is zero)
+  const int pr = (pw + 31) & ~31;
+  const int G = max(1, (int)blockDim.x / pr);
+  const int i = tid % pr, g = tid / pr;
+  T acc = T(0);
+  if (g < G && i < pw)
+    for (int k = g; k <= i; k += G) acc += t.A[i + k * ldi] * t.vec[k];
+  t.aux[tid] = acc;
+  __syncthreads();
+  if (tid < pw) {
+    T y = T(0);
+    for (int gg = 0; gg < G; gg++) y += t.aux[gg * pr + tid];
+    t.vec2[tid] = y;
+    a.v[f + tid] = y;
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) st_release(&a.fwd_done[p], e);
+  if (rn > 0) {
+    // chunk 0: b[rows] -= L21(0:rn) y
+    const int rr = (rn + 31) & ~31;
+    const int G2 = max(1, (int)blockDim.x / rr);
+    const int i2 = tid % rr, g2 = tid / rr;
+    T s = T(0);
+    if (g2 < G2 && i2 < rn)
+      for (int k = g2; k < pw; k += G2) s += t.B[k * t.csB + d0 + i2] * t.vec2[k];
+    t.aux[tid] = s;
+    __syncthreads();
+    if (tid < rn) {
+      T o = T(0);
+      for (int gg = 0; gg < G2; gg++) o += t.aux[gg * rr + tid];
+      atomicAdd(&a.v[a.sn_rows[a.pc_row[p] + pw + tid]], -o);
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0)
+      for (int64_t q = a.hd_tptr[p]; q < a.hd_tptr[p + 1]; q++) atomicAdd(&a.fwd_arrive[a.hd_tgt[q]], 1);
+  }
+  return true;
+}
+
+template <typename T>
+__device__ bool fwd_chunk(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>& t, int c, int e) {
+  const int tid = threadIdx.x;
+  const int p = a.ch_piece[c];
+  const int pw = a.pc_w[p], f = a.pc_first[p];
+  const int r0 = a.ch_r0[c], nr = a.ch_nr[c];
+  if (tid < 32) {
+    uint32_t b = 0;
+    if (tid == 0) fence_proxy_async();
+    stage_cols(a, p, r0, nr, t.A, t.csA, b, &h.mbar, false);
+    if (tid == 0) mbar_expect_tx(&h.mbar, b);
+    __syncwarp();
+    stage_cols(a, p, r0, nr, t.A, t.csA, b, &h.mbar, true);
+    if (tid == 0) h.flag = wait_geq(&a.fwd_done[p], e, a.st, a.spin);
+  }
+  __syncthreads();
+  const bool dep = h.flag != 0;
+  if (dep)
+    for (int k = tid; k < pw; k += blockDim.x) t.vec[k] = ldcg(&a.v[f + k]);
+  if (!mbar_wait(a, h) || !dep) return false;
+  const int d0 = (a.pc_c[p] + r0) & 3;
+  const int rr = (nr + 31) & ~31;
+  const int G = max(1, (int)blockDim.x / rr);
+  const int i = tid % rr, g = tid / rr;
+  T acc = T(0);
+  if (g < G && i < nr)
+    for (int k = g; k < pw; k += G) acc += t.A[k * t.csA + d0 + i] * t.vec[k];
+  t.aux[tid] = acc;
+  __syncthreads();
+  if (tid < nr) {
+    T s = T(0);
+    for (int gg = 0; gg < G; gg++) s += t.aux[gg * rr + tid];
+    atomicAdd(&a.v[a.sn_rows[a.pc_row[p] + r0 + tid]], -s);
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0)
+    for (int64_t q = a.ch_tptr[c]; q < a.ch_tptr[c + 1]; q++) atomicAdd(&a.fwd_arrive[a.ch_tgt[q]], 1);
+  return true;
+}
+
+// --------------------------------------------------------------- backward
+template <typename T>
+__device__ bool bwd_chunk(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>& t, int c, int e) {
+  const int tid = threadIdx.x;
+  const int p = a.ch_piece[c];
+  const int pw = a.pc_w[p];
+  const int r0 = a.ch_r0[c], nr = a.ch_nr[c];
+  if (tid < 32) {
+    uint32_t b = 0;
+    if (tid == 0) fence_proxy_async();
+    stage_cols(a, p, r0, nr, t.A, t.csA, b, &h.mbar, false);
+    if (tid == 0) mbar_expect_tx(&h.mbar, b);
+    __syncwarp();
+    stage_cols(a, p, r0, nr, t.A, t.csA, b, &h.mbar, true);
+    if (tid == 0) {
+      int ok = 1;
+      for (int64_t q = a.ch_tptr[c]; q < a.ch_tptr[c + 1] && ok; q++)
+        ok = wait_geq(&a.bwd_done[a.ch_tgt[q]], e, a.st, a.spin);
+      h.flag = ok;
+    }
+  }
+  __syncthreads();
+  const bool dep = h.flag != 0;
+  if (dep)
+    for (int i = tid; i < nr; i += blockDim.x) t.aux[i] = ldcg(&a.v[a.sn_rows[a.pc_row[p] + r0 + i]]);
+  if (!mbar_wait(a, h) || !dep) return false;
+  const int d0 = (a.pc_c[p] + r0) & 3;
+  const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  T* z = a.zpart + a.pc_zoff[p] + (int64_t)a.ch_k[c] * pw;
+  for (int k = warp; k < pw; k += nw) {
+    T s = T(0);
+    for (int i = lane; i < nr; i += 32) s += t.A[k * t.csA + d0 + i] * t.aux[i];
+    s = warp_sum(s);
+    if (lane == 0) z[k] = s;
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) atomicAdd(&a.bwd_arrive[p], 1);
+  return true;
+}
+
+template <typename T>
+__device__ bool bwd_head(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>& t, int p, int e) {
+  const int tid = threadIdx.x;
+  const int pw = a.pc_w[p], f = a.pc_first[p], rn = a.pc_rc0[p], nch = a.pc_nchunk[p];
+  const int ldi = (pw + 3) & ~3;
+  if (tid < 32) {
+    uint32_t b1 = 0;
+    if (tid == 0) fence_proxy_async();
+    const uint32_t binv = (uint32_t)(pw * ldi * sizeof(T));
+    if (rn > 0) stage_cols(a, p, pw, rn, t.B, t.csB, b1, &h.mbar, false);
+    if (tid == 0) mbar_expect_tx(&h.mbar, binv + b1);
+    __syncwarp();
+    if (tid == 0) bulk_g2s(t.A, a.Linv + a.pc_inv[p], binv, &h.mbar);
+    if (rn > 0) stage_cols(a, p, pw, rn, t.B, t.csB, b1, &h.mbar, true);
+    if (tid == 0) {
+      int ok = wait_geq(&a.bwd_arrive[p], e * nch, a.st, a.spin);
+      for (int64_t q = a.hd_tptr[p]; q < a.hd_tptr[p + 1] && ok; q++)
+        ok = wait_geq(&a.bwd_done[a.hd_tgt[q]], e, a.st, a.spin);
+      h.flag = ok;
+    }
+  }
+  __syncthreads();
+  const bool dep = h.flag != 0;
+  if (dep) {
+    for (int i = tid; i < rn; i += blockDim.x) t.aux[i] = ldcg(&a.v[a.sn_rows[a.pc_row[p] + pw + i]]);
+    const T* z = a.zpart + a.pc_zoff[p];
+    for (int i = tid; i < pw; i += blockDim.x) {
+      T v = ldcg(&a.v[f + i]);
+      for (int k = 0; k < nch; k++) v -= ldcg(&z[(int64_t)k * pw + i]);
+      t.vec[i] = v;
+    }
+  }
+  if (!mbar_wait(a, h) || !dep) return false;
+  const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  if (rn > 0) {
+    const int d0 = (a.pc_c[p] + pw) & 3;
+    for (int k = warp; k < pw; k += nw) {
+      T s = T(0);
+      for (int i = lane; i < rn; i += 32) s += t.B[k * t.csB + d0 + i] * t.aux[i];
+      s = warp_sum(s);
+      if (lane == 0) t.vec[k] -= s;
+    }
+    __syncthreads();
+  }
+  // x = T^-T t: x_k = sum_i Tinv[i, k] t_i (Tinv lower, zero above the diagonal)
+  for (int k = warp; k < pw; k += nw) {
+    T s = T(0);
+    for (int i = k + lane; i < pw; i += 32) s += t.A[i + k * ldi] * t.vec[i];
+    s = warp_sum(s);
+    if (lane == 0) t.vec2[k] = s;
+  }
+  __syncthreads();
+  for (int i = tid; i < pw; i += blockDim.x) a.v[f + i] = t.vec2[i];
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) st_release(&a.bwd_done[p], e);
+  return true;
+}
+
+template <typename T>
+__device__ bool grid_barrier(const SolveArgs<T>& a, SolveSmemHdr& h) {
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
@@ -59,23 +351,23 @@ __device__ bool grid_barrier(const SolveArgs<T>& a, SolveSmem<T>& sm) {
       ok = wait_geq(&a.bar[1], gen + 1, a.st, a.spin) ? 1 : 0;
     }
     if (ld_acquire(&a.st->abort)) ok = 0;
-    sm.flag = ok;
+    h.flag = ok;
   }
   __syncthreads();
-  return sm.flag != 0;
+  return h.flag != 0;
 }
 
 // per-block partial sums of two values -> a.red[block*4 + {0,1}]
 template <typename T>
-__device__ void block_partial2(const SolveArgs<T>& a, SolveSmem<T>& sm, double v0, double v1) {
+__device__ void block_partial2(const SolveArgs<T>& a, SolveSmemHdr& h, double v0, double v1) {
   v0 = warp_sum(v0);
   v1 = warp_sum(v1);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) { sm.dred[warp * 2] = v0; sm.dred[warp * 2 + 1] = v1; }
+  if (lane == 0) { h.dred[warp * 2] = v0; h.dred[warp * 2 + 1] = v1; }
   __syncthreads();
   if (threadIdx.x == 0) {
     double s0 = 0, s1 = 0;
-    for (int w = 0; w < kSolveThreads / 32; w++) { s0 += sm.dred[w * 2]; s1 += sm.dred[w * 2 + 1]; }
+    for (int w = 0; w < kSolveThreads / 32; w++) { s0 += h.dred[w * 2]; s1 += h.dred[w * 2 + 1]; }
     a.red[blockIdx.x * 4] = s0;
     a.red[blockIdx.x * 4 + 1] = s1;
   }
@@ -83,7 +375,7 @@ __device__ void block_partial2(const SolveArgs<T>& a, SolveSmem<T>& sm, double v
 
 // the same grid totals in every block (fixed summation order)
 template <typename T>
-__device__ void grid_total2(const SolveArgs<T>& a, SolveSmem<T>& sm, double& t0, double& t1) {
+__device__ void grid_total2(const SolveArgs<T>& a, SolveSmemHdr& h, double& t0, double& t1) {
   if (threadIdx.x < 32) {
     double s0 = 0, s1 = 0;
     for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) {
@@ -92,212 +384,63 @@ __device__ void grid_total2(const SolveArgs<T>& a, SolveSmem<T>& sm, double& t0,
     }
     s0 = warp_sum(s0);
     s1 = warp_sum(s1);
-    if (threadIdx.x == 0) { sm.bcast[0] = s0; sm.bcast[1] = s1; }
+    if (threadIdx.x == 0) { h.bcast[0] = s0; h.bcast[1] = s1; }
   }
   __syncthreads();
-  t0 = sm.bcast[0];
-  t1 = sm.bcast[1];
+  t0 = h.bcast[0];
+  t1 = h.bcast[1];
   __syncthreads();
-}
-
-// --------------------------------------------------------------- forward
-template <typename T>
-__device__ bool fwd_head(const SolveArgs<T>& a, SolveSmem<T>& sm, int p, int e) {
-  const int tid = threadIdx.x;
-  if (tid == 0) sm.flag = wait_geq(&a.fwd_arrive[p], e * a.pc_need[p], a.st, a.spin);
-  __syncthreads();
-  if (!sm.flag) return false;
-  const int pw = a.pc_w[p], ld = a.pc_ld[p], f = a.pc_first[p];
-  const T* Lp = a.L + a.pc_off[p];
-  T* vec = sm.vec;
-  for (int i = tid; i < pw; i += blockDim.x) vec[i] = ldcg(&a.v[f + i]);
-  __syncthreads();
-  const int lane = tid & 31, warp = tid >> 5;
-  for (int jb = 0; jb < pw; jb += 32) {
-    const int bwb = min(32, pw - jb);
-    if (warp == 0) {
-      T Lr[32];
-#pragma unroll
-      for (int k = 0; k < 32; k++)
-        Lr[k] = (lane < bwb && k <= lane) ? Lp[(int64_t)(jb + lane) + (int64_t)(jb + k) * ld] : T(0);
-      T val = lane < bwb ? vec[jb + lane] : T(0);
-#pragma unroll
-      for (int j = 0; j < 32; j++) {
-        if (j < bwb) {
-          if (lane == j) val = val / Lr[j];
-          const T yj = __shfl_sync(0xffffffffu, val, j);
-          if (lane > j) val -= Lr[j] * yj;
-        }
-      }
-      if (lane < bwb) vec[jb + lane] = val;
-    }
-    __syncthreads();
-    for (int i = jb + bwb + tid; i < pw; i += blockDim.x) {
-      T acc = T(0);
-      for (int k = 0; k < bwb; k++) acc += Lp[(int64_t)i + (int64_t)(jb + k) * ld] * vec[jb + k];
-      vec[i] -= acc;
-    }
-    __syncthreads();
-  }
-  for (int i = tid; i < pw; i += blockDim.x) a.v[f + i] = vec[i];
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) st_release(&a.fwd_done[p], e);
-  return true;
-}
-
-template <typename T>
-__device__ bool fwd_chunk(const SolveArgs<T>& a, SolveSmem<T>& sm, int c, int e) {
-  const int tid = threadIdx.x;
-  const int p = a.ch_piece[c];
-  if (tid == 0) sm.flag = wait_geq(&a.fwd_done[p], e, a.st, a.spin);
-  __syncthreads();
-  if (!sm.flag) return false;
-  const int pw = a.pc_w[p], ld = a.pc_ld[p], f = a.pc_first[p];
-  const int r0 = a.ch_r0[c], nr = a.ch_nr[c];
-  const T* Lp = a.L + a.pc_off[p];
-  T* vec = sm.vec;
-  for (int k = tid; k < pw; k += blockDim.x) vec[k] = ldcg(&a.v[f + k]);
-  __syncthreads();
-  const int nrr = (nr + 31) & ~31;
-  const int G = max(1, (int)blockDim.x / nrr);
-  const int i = tid % nrr, g = tid / nrr;
-  T acc = T(0);
-  if (g < G && i < nr)
-    for (int k = g; k < pw; k += G) acc += Lp[(int64_t)(r0 + i) + (int64_t)k * ld] * vec[k];
-  sm.aux[tid] = acc;
-  __syncthreads();
-  if (tid < nr) {
-    T s = T(0);
-    for (int gg = 0; gg < G; gg++) s += sm.aux[gg * nrr + tid];
-    const int row = a.sn_rows[a.pc_row[p] + r0 + tid];
-    atomicAdd(&a.v[row], -s);
-  }
-  __threadfence();
-  __syncthreads();
-  if (tid == 0)
-    for (int64_t t = a.ch_tptr[c]; t < a.ch_tptr[c + 1]; t++) atomicAdd(&a.fwd_arrive[a.ch_tgt[t]], 1);
-  return true;
-}
-
-// --------------------------------------------------------------- backward
-template <typename T>
-__device__ bool bwd_chunk(const SolveArgs<T>& a, SolveSmem<T>& sm, int c, int e) {
-  const int tid = threadIdx.x;
-  const int p = a.ch_piece[c];
-  if (tid == 0) {
-    int ok = 1;
-    for (int64_t t = a.ch_tptr[c]; t < a.ch_tptr[c + 1] && ok; t++) ok = wait_geq(&a.bwd_done[a.ch_tgt[t]], e, a.st, a.spin);
-    sm.flag = ok;
-  }
-  __syncthreads();
-  if (!sm.flag) return false;
-  const int pw = a.pc_w[p], ld = a.pc_ld[p];
-  const int r0 = a.ch_r0[c], nr = a.ch_nr[c];
-  const T* Lp = a.L + a.pc_off[p];
-  T* xs = sm.aux;
-  for (int i = tid; i < nr; i += blockDim.x) xs[i] = ldcg(&a.v[a.sn_rows[a.pc_row[p] + r0 + i]]);
-  __syncthreads();
-  const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  T* z = a.zpart + a.pc_zoff[p] + (int64_t)a.ch_k[c] * pw;
-  for (int k = warp; k < pw; k += nw) {
-    T s = T(0);
-    for (int i = lane; i < nr; i += 32) s += Lp[(int64_t)(r0 + i) + (int64_t)k * ld] * xs[i];
-    s = warp_sum(s);
-    if (lane == 0) z[k] = s;
-  }
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) atomicAdd(&a.bwd_arrive[p], 1);
-  return true;
-}
-
-template <typename T>
-__device__ bool bwd_head(const SolveArgs<T>& a, SolveSmem<T>& sm, int p, int e) {
-  const int tid = threadIdx.x;
-  if (tid == 0) sm.flag = wait_geq(&a.bwd_arrive[p], e * a.pc_nchunk[p], a.st, a.spin);
-  __syncthreads();
-  if (!sm.flag) return false;
-  const int pw = a.pc_w[p], ld = a.pc_ld[p], f = a.pc_first[p], nch = a.pc_nchunk[p];
-  const T* Lp = a.L + a.pc_off[p];
-  const T* z = a.zpart + a.pc_zoff[p];
-  T* vec = sm.vec;
-  for (int i = tid; i < pw; i += blockDim.x) {
-    T t = ldcg(&a.v[f + i]);
-    for (int k = 0; k < nch; k++) t -= ldcg(&z[(int64_t)k * pw + i]);
-    vec[i] = t;
-  }
-  __syncthreads();
-  const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  const int nblk = (pw + 31) / 32;
-  for (int b = nblk - 1; b >= 0; b--) {
-    const int jb = b * 32, bwb = min(32, pw - jb);
-    if (jb + bwb < pw) {
-      for (int jj = warp; jj < bwb; jj += nw) {
-        const int j = jb + jj;
-        T s = T(0);
-        for (int i = jb + bwb + lane; i < pw; i += 32) s += Lp[(int64_t)i + (int64_t)j * ld] * vec[i];
-        s = warp_sum(s);
-        if (lane == 0) vec[j] -= s;
-      }
-      __syncthreads();
-    }
-    if (warp == 0) {
-      T Lc[32];
-#pragma unroll
-      for (int j = 0; j < 32; j++)
-        Lc[j] = (lane < bwb && j < bwb && j >= lane) ? Lp[(int64_t)(jb + j) + (int64_t)(jb + lane) * ld] : T(0);
-      T t = lane < bwb ? vec[jb + lane] : T(0);
-#pragma unroll
-      for (int j = 31; j >= 0; j--) {
-        if (j < bwb) {
-          if (lane == j) t = t / Lc[j];
-          const T xj = __shfl_sync(0xffffffffu, t, j);
-          if (lane < j) t -= Lc[j] * xj;
-        }
-      }
-      if (lane < bwb) vec[jb + lane] = t;
-    }
-    __syncthreads();
-  }
-  for (int i = tid; i < pw; i += blockDim.x) a.v[f + i] = vec[i];
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) st_release(&a.bwd_done[p], e);
-  return true;
 }
 
 template <typename T, bool FWD>
-__device__ bool sweep(const SolveArgs<T>& a, SolveSmem<T>& sm, int seq, int e) {
+__device__ bool sweep(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>& t, int seq, int e) {
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(&a.disp[(seq + 1) % 3], 0);
   const int32_t* items = FWD ? a.fwd_items : a.bwd_items;
   for (;;) {
-    if (threadIdx.x == 0) sm.item = atomicAdd(&a.disp[seq % 3], 1);
+    if (threadIdx.x == 0) h.item = atomicAdd(&a.disp[seq % 3], 1);
     __syncthreads();
-    const int it = sm.item;
+    const int it = h.item;
     __syncthreads();
     if (it >= a.nitems) return true;
     const int code = items[it];
     bool ok;
-    if (FWD) ok = code < 0 ? fwd_head(a, sm, -1 - code, e) : fwd_chunk(a, sm, code, e);
-    else ok = code < 0 ? bwd_head(a, sm, -1 - code, e) : bwd_chunk(a, sm, code, e);
+    if (FWD) ok = code < 0 ? fwd_head(a, h, t, -1 - code, e) : fwd_chunk(a, h, t, code, e);
+    else ok = code < 0 ? bwd_head(a, h, t, -1 - code, e) : bwd_chunk(a, h, t, code, e);
     if (!ok) return false;
   }
 }
 
 // one H^-1 application on a.v (forward then backward sweep)
 template <typename T>
-__device__ bool hsolve(const SolveArgs<T>& a, SolveSmem<T>& sm, int& seq, int& e) {
+__device__ bool hsolve(const SolveArgs<T>& a, SolveSmemHdr& sm, const Tiles<T>& t, int& seq, int& e) {
   e++;
-  if (!sweep<T, true>(a, sm, seq++, e)) return false;
+  if (!sweep<T, true>(a, sm, t, seq++, e)) return false;
   if (!grid_barrier(a, sm)) return false;
-  if (!sweep<T, false>(a, sm, seq++, e)) return false;
+  if (!sweep<T, false>(a, sm, t, seq++, e)) return false;
   return grid_barrier(a, sm);
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kSolveThreads) k_cg(SolveArgs<T> a) {
-  __shared__ SolveSmem<T> sm;
+__global__ void __launch_bounds__(kSolveThreads, 1) k_cg(SolveArgs<T> a) {
+  __shared__ SolveSmemHdr sm;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  Tiles<T> tl;
+  {
+    const int ldi = (a.sw + 3) & ~3;
+    const int csA = a.rc + 8;
+    tl.csA = csA;
+    tl.csB = a.rc0 + 8;
+    tl.A = (T*)dsm;
+    tl.B = tl.A + (size_t)a.sw * (ldi > csA ? ldi : csA);
+    tl.vec = tl.B + (size_t)a.sw * tl.csB;
+    tl.vec2 = tl.vec + a.sw;
+    tl.aux = tl.vec2 + a.sw;
+  }
+  if (threadIdx.x == 0) {
+    mbar_init(&sm.mbar);
+    sm.phase = 0;
+  }
+  __syncthreads();
   const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t gs = (int64_t)gridDim.x * blockDim.x;
   const int64_t n = a.n, m = a.m;
@@ -313,7 +456,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_cg(SolveArgs<T> a) {
     a.v[k] = (T)rh;
   }
   if (!grid_barrier(a, sm)) return;
-  if (!hsolve(a, sm, seq, e)) return;
+  if (!hsolve(a, sm, tl, seq, e)) return;
   if (a.mode == 1) {
     for (int64_t k = gt; k < n; k += gs) {
       const double val = (double)ldcg(&a.v[k]);
@@ -347,7 +490,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_cg(SolveArgs<T> a) {
       a.v[k] = (T)s;
     }
     if (!grid_barrier(a, sm)) return;
-    if (!hsolve(a, sm, seq, e)) return;
+    if (!hsolve(a, sm, tl, seq, e)) return;
     double pq = 0.0, pp = 0.0;
     for (int64_t i = gt; i < m; i += gs) {
       double s = 0.0;
@@ -406,7 +549,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_cg(SolveArgs<T> a) {
     a.v[k] = (T)(__ldcg(&a.rhx[k]) - s);
   }
   if (!grid_barrier(a, sm)) return;
-  if (!hsolve(a, sm, seq, e)) return;
+  if (!hsolve(a, sm, tl, seq, e)) return;
   for (int64_t k = gt; k < n; k += gs) {
     const double val = (double)ldcg(&a.v[k]);
     const int32_t o = a.perm[k];
@@ -424,11 +567,18 @@ __global__ void __launch_bounds__(kSolveThreads) k_cg(SolveArgs<T> a) {
 }
 
 template <typename T>
-int solve_grid_size(int device) {
-  int sms = 0, per = 0;
+int solve_grid_size(int device, int sw, int rc, int rc0) {
+  int sms = 0, per = 0, maxsm = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cg<T>, kSolveThreads, 0);
-  if (per < 1) per = 1;
+  cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  const size_t smem = solve_smem_bytes(sizeof(T), sw, rc, rc0);
+  if (smem > (size_t)maxsm) return 0;
+  if (cudaFuncSetAttribute(k_cg<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cg<T>, kSolveThreads, smem);
+  if (per < 1) return 0;
   return sms * per;
 }
 
@@ -436,11 +586,12 @@ template <typename T>
 cudaError_t launch_solve(const SolveArgs<T>& a, int grid, cudaStream_t st) {
   SolveArgs<T> args = a;
   void* params[] = {&args};
-  return cudaLaunchCooperativeKernel((const void*)k_cg<T>, dim3(grid), dim3(kSolveThreads), params, 0, st);
+  const size_t smem = solve_smem_bytes(sizeof(T), a.sw, a.rc, a.rc0);
+  return cudaLaunchCooperativeKernel((const void*)k_cg<T>, dim3(grid), dim3(kSolveThreads), params, smem, st);
 }
 
-template int solve_grid_size<double>(int);
-template int solve_grid_size<float>(int);
+template int solve_grid_size<double>(int, int, int, int);
+template int solve_grid_size<float>(int, int, int, int);
 template cudaError_t launch_solve<double>(const SolveArgs<double>&, int, cudaStream_t);
 template cudaError_t launch_solve<float>(const SolveArgs<float>&, int, cudaStream_t);
 

@@ -77,7 +77,8 @@ def test_factor_panels_match_oracle_cholesky(seed):
         w = start[sn + 1] - start[sn]
         R = rows[rowptr[sn]:rowptr[sn + 1]]
         nr = len(R)
-        P = panels[off:off + w * nr].reshape(w, nr).T
+        ld = (nr + 3) // 4 * 4
+        P = panels[off:off + w * ld].reshape(w, ld).T[:nr]
         pos = {r: i for i, r in enumerate(R)}
         for jj in range(w):
             j = start[sn] + jj
@@ -86,7 +87,7 @@ def test_factor_panels_match_oracle_cholesky(seed):
                 col[pos[Li[q]]] = Lx[q]
             col[:jj] = P[:jj, jj]          # upper part of the diagonal block is not used
             worst = max(worst, np.abs(P[:, jj] - col).max())
-        off += w * nr
+        off += w * ld
     assert worst <= 1e-12 * scale
 
 
