@@ -63,7 +63,10 @@ typedef struct kkt_options {
   double ir_rtol;      /* refine while RR(K_delta) > ir_rtol */
   int32_t precision;   /* KKT_FP64: FP64 factor and solves; KKT_MIXED: FP32 factor and
                           triangular solves, FP64 CG recurrences, residual and refinement */
-  int32_t ordering;    /* 0 = approximate minimum degree (Sec. 5.3), 1 = natural */
+  int32_t ordering;    /* 0 = approximate minimum degree (Sec. 5.3), 1 = natural,
+                          2 = nested dissection by level-structure separators (Sec. 5.3
+                          compares it with AMD; its shallow elimination tree gives the GPU
+                          far more parallel work) */
   int32_t relax_small; /* supernode relaxation: merge when merged width <= relax_small */
   int32_t relax_num;   /*   or explicit zeros * relax_den <= relax_num * panel entries */
   int32_t relax_den;
@@ -76,7 +79,8 @@ typedef struct kkt_options {
                           (0 = default 4e9, about two seconds) */
   int32_t profile;     /* 1: time every kernel launch with CUDA events (serialises the
                           launches; for measurement runs only) */
-  int32_t pad_;
+  int32_t nd_leaf;     /* nested dissection stops at components of at most this many
+                          vertices (ordered naturally); default 64 */
 } kkt_options;
 
 /* Kernel kinds reported by kkt_get_profile. */

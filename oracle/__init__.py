@@ -52,6 +52,9 @@ def _load():
         L.orc_analyse.argtypes = [C.c_int64, C.c_int64, i64p, i32p, i64p, i32p,
                                   C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                   C.POINTER(C.c_int32)]
+        L.orc_analyse_perm.restype = P
+        L.orc_analyse_perm.argtypes = [C.c_int64, C.c_int64, i64p, i32p, i64p, i32p, C.c_int32, C.c_int32,
+                                       C.c_int32, C.c_int32, C.c_int32, C.c_int32, i32p, C.POINTER(C.c_int32)]
         L.orc_sym_info.argtypes = [P, i64p]
         L.orc_sym_flops.restype = C.c_double
         L.orc_sym_flops.argtypes = [P]
@@ -87,14 +90,17 @@ class Symbolic:
     """S1-S5 of the pinned symbolic analysis for one (H~, J) pattern."""
 
     def __init__(self, n, m, H_colptr, H_rowidx, J_rowptr, J_colidx, *, relax_small=RELAX_SMALL,
-                 relax_num=RELAX_NUM, relax_den=RELAX_DEN, wmax=RELAX_WMAX, ordering="amd"):
+                 relax_num=RELAX_NUM, relax_den=RELAX_DEN, wmax=RELAX_WMAX, ordering="amd", user_order=None,
+                 nd_leaf=64):
         L = _load()
         self.n, self.m = int(n), int(m)
         st = C.c_int32(0)
-        self._h = L.orc_analyse(self.n, self.m, _c(H_colptr, np.int64), _c(H_rowidx, np.int32),
-                                _c(J_rowptr, np.int64), _c(J_colidx, np.int32),
-                                relax_small, relax_num, relax_den, wmax,
-                                0 if ordering == "amd" else 1, C.byref(st))
+        code = {"amd": 0, "natural": 1, "nd": 2, "user": 3}[ordering if user_order is None else "user"]
+        uo = _c(user_order if user_order is not None else np.zeros(1), np.int32)
+        self._h = L.orc_analyse_perm(self.n, self.m, _c(H_colptr, np.int64), _c(H_rowidx, np.int32),
+                                     _c(J_rowptr, np.int64), _c(J_colidx, np.int32),
+                                     relax_small, relax_num, relax_den, wmax, code, int(nd_leaf), uo,
+                                     C.byref(st))
         if st.value != 0 or not self._h:
             self._h = None
             raise ValueError(f"oracle analyse: invalid input (status {st.value})")

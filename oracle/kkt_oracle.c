@@ -345,6 +345,177 @@ static void amd_order(int64_t n, const int64_t *adjp, const int32_t *adji, int32
     free(t1); free(t2); free(mem_tmp); free(hl); free(H.h);
 }
 
+
+/* ------------------------------------------------------------------ */
+/* S2-ND: nested dissection by level-structure separators              */
+/* ------------------------------------------------------------------ */
+/*
+ * Pinned nested dissection (automatic nested dissection of George & Liu,
+ * "Computer Solution of Large Sparse Positive Definite Systems", 1981,
+ * Ch. 8, with the separator level chosen as below). Sec. 5.3 of the paper
+ * compares it with AMD; here it is an option of the symbolic analysis.
+ *   ND(V): split V into connected components (each found by BFS from its
+ *   smallest unvisited vertex, scanning V ascending; components in that
+ *   order). For a component C:
+ *     |C| <= leaf: emit C ascending.
+ *     r = pseudo-peripheral vertex: start at min(C); BFS; x = the vertex of
+ *         the last level with the fewest neighbours in C (ties: smallest);
+ *         move to x while its level structure is strictly taller.
+ *     L_0..L_h = level structure from r (h < 2: emit C ascending).
+ *     k = argmin over q in [max(1, h/3), min(h-1, max(1, (2h+2)/3))] of
+ *         (|L_q|, |q - (h+1)/2|, q)       (integer division)
+ *     S = vertices of L_k with a neighbour in L_{k+1}; the rest of L_k joins
+ *     part1 = L_0 .. L_{k-1}; part2 = L_{k+1} .. L_h.
+ *     emit ND(part1), ND(part2), then S ascending.
+ */
+typedef struct { int kind; ivec v; } nd_task;   /* kind 0: dissect set, 1: emit, 2: dissect component */
+
+static int64_t bfs_levels(const int64_t *adjp, const int32_t *adji, int32_t r, const int64_t *inC, int64_t cstamp,
+                          int32_t *lev, int64_t *vis, int64_t vstamp, int32_t *queue, int64_t *levstart) {
+    /* levels as contiguous ranges of `queue`; returns the number of levels */
+    int64_t head = 0, tail = 0, nl = 0;
+    queue[tail++] = r; vis[r] = vstamp; lev[r] = 0;
+    levstart[0] = 0;
+    while (head < tail) {
+        int64_t end = tail;
+        nl++;
+        for (; head < end; head++) {
+            int32_t v = queue[head];
+            for (int64_t q = adjp[v]; q < adjp[v + 1]; q++) {
+                int32_t u = adji[q];
+                if (inC[u] == cstamp && vis[u] != vstamp) { vis[u] = vstamp; lev[u] = (int32_t)nl; queue[tail++] = u; }
+            }
+        }
+        levstart[nl] = end;
+    }
+    levstart[nl] = tail;
+    return nl;
+}
+
+static void nd_order(int64_t n, const int64_t *adjp, const int32_t *adji, int32_t leaf, int32_t *order) {
+    int64_t *inC = (int64_t *)calloc((size_t)n, sizeof(int64_t));
+    int64_t *vis = (int64_t *)calloc((size_t)n, sizeof(int64_t));
+    int32_t *lev = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    int32_t *queue = (int32_t *)malloc((size_t)(n + 1) * sizeof(int32_t));
+    int32_t *queue2 = (int32_t *)malloc((size_t)(n + 1) * sizeof(int32_t));
+    int64_t *ls = (int64_t *)malloc((size_t)(n + 2) * sizeof(int64_t));
+    int64_t *ls2 = (int64_t *)malloc((size_t)(n + 2) * sizeof(int64_t));
+    int64_t stamp = 0, nout = 0;
+    nd_task *stk = NULL;
+    int64_t ns = 0, cap = 0;
+#define ND_PUSH(K, VEC) do { if (ns == cap) { cap = cap ? 2 * cap : 64; stk = (nd_task *)realloc(stk, (size_t)cap * sizeof(nd_task)); } \
+                             stk[ns].kind = (K); stk[ns].v = (VEC); ns++; } while (0)
+    ivec all = {0};
+    for (int64_t i = 0; i < n; i++) iv_push(&all, (int32_t)i);
+    ND_PUSH(0, all);
+    while (ns > 0) {
+        nd_task t = stk[--ns];
+        if (t.kind == 1) {
+            for (int64_t i = 0; i < t.v.n; i++) order[nout++] = t.v.a[i];
+            iv_free(&t.v);
+            continue;
+        }
+        if (t.kind == 0) {
+            /* connected components of the set, pushed so that the first is processed first */
+            qsort(t.v.a, (size_t)t.v.n, sizeof(int32_t), cmp_i32);
+            stamp++;
+            int64_t cs = stamp;
+            for (int64_t i = 0; i < t.v.n; i++) inC[t.v.a[i]] = cs;
+            stamp++;
+            int64_t vs = stamp;
+            int64_t ncomp = 0;
+            ivec *comps = NULL;
+            for (int64_t i = 0; i < t.v.n; i++) {
+                int32_t s0 = t.v.a[i];
+                if (vis[s0] == vs) continue;
+                ivec c = {0};
+                int64_t head = 0;
+                iv_push(&c, s0); vis[s0] = vs;
+                while (head < c.n) {
+                    int32_t v = c.a[head++];
+                    for (int64_t q = adjp[v]; q < adjp[v + 1]; q++) {
+                        int32_t u = adji[q];
+                        if (inC[u] == cs && vis[u] != vs) { vis[u] = vs; iv_push(&c, u); }
+                    }
+                }
+                qsort(c.a, (size_t)c.n, sizeof(int32_t), cmp_i32);
+                comps = (ivec *)realloc(comps, (size_t)(ncomp + 1) * sizeof(ivec));
+                comps[ncomp++] = c;
+            }
+            iv_free(&t.v);
+            for (int64_t k = ncomp - 1; k >= 0; k--) ND_PUSH(2, comps[k]);
+            free(comps);
+            continue;
+        }
+        /* kind 2: one connected component, sorted ascending */
+        ivec C = t.v;
+        if (C.n <= leaf) { ND_PUSH(1, C); continue; }
+        stamp++;
+        int64_t cs = stamp;
+        for (int64_t i = 0; i < C.n; i++) inC[C.a[i]] = cs;
+        int32_t r = C.a[0];
+        stamp++;
+        int64_t h = bfs_levels(adjp, adji, r, inC, cs, lev, vis, stamp, queue, ls) - 1;
+        for (;;) {
+            /* min-degree vertex of the last level */
+            int32_t x = -1; int64_t bestd = 0;
+            for (int64_t q = ls[h]; q < ls[h + 1]; q++) {
+                int32_t v = queue[q];
+                int64_t d = 0;
+                for (int64_t e = adjp[v]; e < adjp[v + 1]; e++) if (inC[adji[e]] == cs) d++;
+                if (x < 0 || d < bestd || (d == bestd && v < x)) { x = v; bestd = d; }
+            }
+            stamp++;
+            int64_t h2 = bfs_levels(adjp, adji, x, inC, cs, lev, vis, stamp, queue2, ls2) - 1;
+            if (h2 > h) {
+                r = x; h = h2;
+                int32_t *tq = queue; queue = queue2; queue2 = tq;
+                int64_t *tl = ls; ls = ls2; ls2 = tl;
+            } else {
+                break;
+            }
+        }
+        if (h < 2) { ND_PUSH(1, C); continue; }
+        /* levels of r are in queue/ls; recompute lev[] for them */
+        for (int64_t l = 0; l <= h; l++)
+            for (int64_t q = ls[l]; q < ls[l + 1]; q++) lev[queue[q]] = (int32_t)l;
+        int64_t lo = h / 3 > 1 ? h / 3 : 1;
+        int64_t hi = (2 * h + 2) / 3;
+        if (hi < 1) hi = 1;
+        if (hi > h - 1) hi = h - 1;
+        int64_t mid = (h + 1) / 2, k = -1;
+        for (int64_t q = lo; q <= hi; q++) {
+            int64_t sz = ls[q + 1] - ls[q];
+            if (k < 0) { k = q; continue; }
+            int64_t szk = ls[k + 1] - ls[k];
+            int64_t dq = q > mid ? q - mid : mid - q, dk = k > mid ? k - mid : mid - k;
+            if (sz < szk || (sz == szk && (dq < dk || (dq == dk && q < k)))) k = q;
+        }
+        ivec S = {0}, P1 = {0}, P2 = {0};
+        for (int64_t l = 0; l <= h; l++)
+            for (int64_t q = ls[l]; q < ls[l + 1]; q++) {
+                int32_t v = queue[q];
+                if (l < k) iv_push(&P1, v);
+                else if (l > k) iv_push(&P2, v);
+                else {
+                    int sep = 0;
+                    for (int64_t e = adjp[v]; e < adjp[v + 1]; e++) {
+                        int32_t u = adji[e];
+                        if (inC[u] == cs && lev[u] == k + 1) { sep = 1; break; }
+                    }
+                    if (sep) iv_push(&S, v); else iv_push(&P1, v);
+                }
+            }
+        qsort(S.a, (size_t)S.n, sizeof(int32_t), cmp_i32);
+        iv_free(&C);
+        ND_PUSH(1, S);
+        ND_PUSH(0, P2);
+        ND_PUSH(0, P1);
+    }
+#undef ND_PUSH
+    free(stk); free(inC); free(vis); free(lev); free(queue); free(queue2); free(ls); free(ls2);
+}
+
 /* ------------------------------------------------------------------ */
 /* S3/S4: symbolic column merge on a given order                        */
 /* ------------------------------------------------------------------ */
@@ -442,10 +613,27 @@ typedef struct {
 
 int64_t orc_version(void) { return 1; }
 
+orc_sym *orc_analyse_perm(int64_t n, int64_t m, const int64_t *Hp, const int32_t *Hi,
+                          const int64_t *Jp, const int32_t *Ji,
+                          int32_t relax_small, int32_t relax_num, int32_t relax_den,
+                          int32_t wmax, int32_t ordering, int32_t nd_leaf, const int32_t *user_order,
+                          int32_t *status);
+
 orc_sym *orc_analyse(int64_t n, int64_t m, const int64_t *Hp, const int32_t *Hi,
                      const int64_t *Jp, const int32_t *Ji,
                      int32_t relax_small, int32_t relax_num, int32_t relax_den,
                      int32_t wmax, int32_t ordering, int32_t *status) {
+    return orc_analyse_perm(n, m, Hp, Hi, Jp, Ji, relax_small, relax_num, relax_den, wmax, ordering, 64, NULL,
+                            status);
+}
+
+/* ordering: 0 AMD, 1 natural, 2 nested dissection with leaves of at most
+ * nd_leaf vertices, 3 the caller's fill-reducing order user_order[n] */
+orc_sym *orc_analyse_perm(int64_t n, int64_t m, const int64_t *Hp, const int32_t *Hi,
+                          const int64_t *Jp, const int32_t *Ji,
+                          int32_t relax_small, int32_t relax_num, int32_t relax_den,
+                          int32_t wmax, int32_t ordering, int32_t nd_leaf, const int32_t *user_order,
+                          int32_t *status) {
     *status = 0;
     if (n <= 0 || m < 0) { *status = 1; return NULL; }
     int64_t *adjp; int32_t *adji;
@@ -462,6 +650,8 @@ orc_sym *orc_analyse(int64_t n, int64_t m, const int64_t *Hp, const int32_t *Hi,
     if (Jp[m]) memcpy(S->Ji, Ji, (size_t)Jp[m] * sizeof(int32_t));
     S->amd = (int32_t *)malloc((size_t)n * sizeof(int32_t));
     if (ordering == 0) amd_order(n, adjp, adji, S->amd);
+    else if (ordering == 2) nd_order(n, adjp, adji, nd_leaf, S->amd);
+    else if (ordering == 3 && user_order) memcpy(S->amd, user_order, (size_t)n * sizeof(int32_t));
     else for (int64_t i = 0; i < n; i++) S->amd[i] = (int32_t)i;   /* natural */
 
     /* S3: etree on the AMD order, postorder, final permutation */

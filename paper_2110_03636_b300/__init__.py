@@ -35,7 +35,7 @@ class kkt_options(C.Structure):
                 ("precision", C.c_int32), ("ordering", C.c_int32), ("relax_small", C.c_int32),
                 ("relax_num", C.c_int32), ("relax_den", C.c_int32), ("relax_wmax", C.c_int32),
                 ("solve_w", C.c_int32), ("device", C.c_int32), ("debug_stall_piece", C.c_int32),
-                ("spin_cycles", C.c_int64), ("profile", C.c_int32), ("pad_", C.c_int32)]
+                ("spin_cycles", C.c_int64), ("profile", C.c_int32), ("nd_leaf", C.c_int32)]
 
 
 class kkt_info(C.Structure):
@@ -122,6 +122,8 @@ def kkt_default_options(**over) -> kkt_options:
     for k, v in over.items():
         if k == "precision" and isinstance(v, str):
             v = {"fp64": KKT_FP64, "mixed": KKT_MIXED}[v]
+        if k == "ordering" and isinstance(v, str):
+            v = {"amd": 0, "natural": 1, "nd": 2}[v]
         setattr(o, k, v)
     return o
 

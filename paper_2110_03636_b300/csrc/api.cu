@@ -120,6 +120,7 @@ void kkt_default_options(kkt_options* o) {
   o->debug_stall_piece = -1;
   o->spin_cycles = 0;
   o->profile = 0;
+  o->nd_leaf = 64;
 }
 
 const char* kkt_status_string(kkt_status s) {
@@ -168,7 +169,8 @@ static kkt_status analyse_host(int64_t n, int64_t m, const int64_t* Hp, const in
   if (m == 0) Jp = &zero;
   RelaxParams rp;
   rp.small = o.relax_small; rp.num = o.relax_num; rp.den = o.relax_den; rp.wmax = o.relax_wmax;
-  if (analyse_pattern(n, m, Hp, Hi, Jp, Ji, rp, o.ordering, h->S) != 0) { delete h; return KKT_ERR_INVALID; }
+  if (o.ordering < 0 || o.ordering > 2 || (o.ordering == 2 && o.nd_leaf < 1)) { delete h; return KKT_ERR_INVALID; }
+  if (analyse_pattern(n, m, Hp, Hi, Jp, Ji, rp, o.ordering, o.nd_leaf, h->S) != 0) { delete h; return KKT_ERR_INVALID; }
   // tiles of the solve kernel: FP64 keeps the head's chunk 0 shorter so that
   // its shared-memory staging fits in one SM's 227 KB
   const int rc = 128, rc0 = o.precision == KKT_FP64 ? 64 : 128;

@@ -13,7 +13,9 @@
 #include "symbolic.hpp"
 
 #include <algorithm>
+#include <cstdlib>
 #include <set>
+#include <tuple>
 #include <unordered_map>
 #include <utility>
 
@@ -204,6 +206,133 @@ struct Amd {
   }
 };
 
+
+// --------------------------------------------------------------- nested dissection
+// Level-structure nested dissection (George & Liu's automatic nested
+// dissection) with the pinned choices: components by BFS from their smallest
+// vertex; pseudo-peripheral root by repeated BFS from the smallest vertex
+// (move to the fewest-neighbour vertex of the last level while the level
+// structure grows); separator level = the smallest level in the middle
+// third (ties: closest to the middle, then lowest); only separator-level
+// vertices with a neighbour one level further stay in the separator; order
+// = part before, part after, separator.
+struct Nd {
+  const std::vector<int64_t>& gp;
+  const std::vector<int32_t>& gi;
+  int32_t leaf;
+  std::vector<int32_t> member;   // stamp: vertex belongs to the current set
+  std::vector<int32_t> seen;     // stamp: visited by the current BFS
+  std::vector<int32_t> level;
+  int32_t stamp = 0;
+  Nd(const std::vector<int64_t>& p, const std::vector<int32_t>& i, int32_t l)
+      : gp(p), gi(i), leaf(l), member(p.size() - 1, 0), seen(p.size() - 1, 0), level(p.size() - 1, -1) {}
+
+  // BFS level structure of the member set (stamp mst) from r
+  void levels_from(int32_t r, int32_t mst, std::vector<std::vector<int32_t>>& L) {
+    L.clear();
+    const int32_t st = ++stamp;
+    L.push_back({r});
+    seen[r] = st;
+    for (size_t d = 0; d < L.size(); d++) {
+      std::vector<int32_t> nxt;
+      for (int32_t v : L[d])
+        for (int64_t q = gp[v]; q < gp[v + 1]; q++) {
+          const int32_t u = gi[q];
+          if (member[u] == mst && seen[u] != st) { seen[u] = st; nxt.push_back(u); }
+        }
+      if (nxt.empty()) break;
+      std::sort(nxt.begin(), nxt.end());
+      L.push_back(std::move(nxt));
+    }
+  }
+
+  void run(std::vector<int32_t>& order) {
+    const int32_t n = (int32_t)gp.size() - 1;
+    order.clear();
+    order.reserve(n);
+    struct Task { int kind; std::vector<int32_t> v; };   // 0 set, 1 emit, 2 connected component
+    std::vector<Task> stack;
+    std::vector<int32_t> all(n);
+    for (int32_t i = 0; i < n; i++) all[i] = i;
+    stack.push_back({0, std::move(all)});
+    std::vector<std::vector<int32_t>> L, L2;
+    while (!stack.empty()) {
+      Task t = std::move(stack.back());
+      stack.pop_back();
+      if (t.kind == 1) {
+        order.insert(order.end(), t.v.begin(), t.v.end());
+        continue;
+      }
+      if (t.kind == 0) {
+        std::sort(t.v.begin(), t.v.end());
+        const int32_t mst = ++stamp;
+        for (int32_t v : t.v) member[v] = mst;
+        const int32_t vst = ++stamp;
+        std::vector<std::vector<int32_t>> comps;
+        for (int32_t s0 : t.v) {
+          if (seen[s0] == vst) continue;
+          std::vector<int32_t> c{s0};
+          seen[s0] = vst;
+          for (size_t h = 0; h < c.size(); h++)
+            for (int64_t q = gp[c[h]]; q < gp[c[h] + 1]; q++) {
+              const int32_t u = gi[q];
+              if (member[u] == mst && seen[u] != vst) { seen[u] = vst; c.push_back(u); }
+            }
+          std::sort(c.begin(), c.end());
+          comps.push_back(std::move(c));
+        }
+        for (size_t k = comps.size(); k-- > 0;) stack.push_back({2, std::move(comps[k])});
+        continue;
+      }
+      std::vector<int32_t>& C = t.v;
+      if ((int64_t)C.size() <= leaf) { stack.push_back({1, std::move(C)}); continue; }
+      const int32_t mst = ++stamp;
+      for (int32_t v : C) member[v] = mst;
+      auto deg_in = [&](int32_t v) {
+        int64_t d = 0;
+        for (int64_t q = gp[v]; q < gp[v + 1]; q++) d += member[gi[q]] == mst;
+        return d;
+      };
+      levels_from(C[0], mst, L);
+      for (;;) {
+        int32_t x = -1;
+        int64_t bd = 0;
+        for (int32_t v : L.back()) {
+          const int64_t d = deg_in(v);
+          if (x < 0 || d < bd || (d == bd && v < x)) { x = v; bd = d; }
+        }
+        levels_from(x, mst, L2);
+        if (L2.size() > L.size()) std::swap(L, L2);
+        else break;
+      }
+      const int64_t h = (int64_t)L.size() - 1;
+      if (h < 2) { stack.push_back({1, std::move(C)}); continue; }
+      const int64_t lo = std::max<int64_t>(1, h / 3);
+      const int64_t hi = std::min<int64_t>(h - 1, std::max<int64_t>(1, (2 * h + 2) / 3));
+      const int64_t mid = (h + 1) / 2;
+      int64_t k = lo;
+      for (int64_t q = lo + 1; q <= hi; q++) {
+        const auto key = std::make_tuple(L[q].size(), std::llabs(q - mid), q);
+        const auto best = std::make_tuple(L[k].size(), std::llabs(k - mid), k);
+        if (key < best) k = q;
+      }
+      const int32_t nst = ++stamp;            // marks level k+1
+      for (int32_t v : L[k + 1]) seen[v] = nst;
+      std::vector<int32_t> S, P1, P2;
+      for (int64_t d = 0; d < k; d++) P1.insert(P1.end(), L[d].begin(), L[d].end());
+      for (int32_t v : L[k]) {
+        bool sep = false;
+        for (int64_t q = gp[v]; q < gp[v + 1] && !sep; q++) sep = seen[gi[q]] == nst;
+        (sep ? S : P1).push_back(v);
+      }
+      for (int64_t d = k + 1; d <= h; d++) P2.insert(P2.end(), L[d].begin(), L[d].end());
+      stack.push_back({1, std::move(S)});
+      stack.push_back({0, std::move(P2)});
+      stack.push_back({0, std::move(P1)});
+    }
+  }
+};
+
 // --------------------------------------------------------------- etree
 // Liu's algorithm on P A P^T given in the graph's labels and a permutation.
 void etree_liu(int64_t n, const std::vector<int64_t>& gp, const std::vector<int32_t>& gi,
@@ -257,7 +386,7 @@ void postorder_tree(int64_t n, const std::vector<int32_t>& parent, std::vector<i
 }  // namespace
 
 int analyse_pattern(int64_t n, int64_t m, const int64_t* Hp, const int32_t* Hi, const int64_t* Jp,
-                    const int32_t* Ji, const RelaxParams& rp, int ordering, Symbolic& S) {
+                    const int32_t* Ji, const RelaxParams& rp, int ordering, int nd_leaf, Symbolic& S) {
   if (n <= 0 || m < 0 || n >= (int64_t)INT32_MAX) return 1;
   if (Hp[0] != 0 || (m > 0 && Jp[0] != 0)) return 1;
   for (int64_t j = 0; j < n; j++) if (Hp[j + 1] < Hp[j]) return 1;
@@ -271,6 +400,9 @@ int analyse_pattern(int64_t n, int64_t m, const int64_t* Hp, const int32_t* Hi, 
   if (ordering == 0) {
     Amd amd;
     amd.run(gp, gi, S.amd);
+  } else if (ordering == 2) {
+    Nd nd(gp, gi, nd_leaf);
+    nd.run(S.amd);
   } else {
     S.amd.resize(n);
     for (int64_t i = 0; i < n; i++) S.amd[i] = (int32_t)i;

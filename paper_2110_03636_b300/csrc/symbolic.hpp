@@ -17,7 +17,7 @@ struct RelaxParams {
 
 struct Symbolic {
   int64_t n = 0, m = 0;
-  std::vector<int32_t> amd;       // fill-reducing order before postordering
+  std::vector<int32_t> amd;       // fill-reducing order (AMD, natural or ND) before postordering
   std::vector<int32_t> perm;      // perm[k] = original index of position k
   std::vector<int32_t> iperm;     // iperm[perm[k]] = k
   std::vector<int32_t> parent;    // elimination tree in final labels (-1 = root)
@@ -35,8 +35,10 @@ struct Symbolic {
 // Pattern-only inputs: H~ lower CSC (diagonal optional in the input, always
 // added), J CSR. Returns 0 on success, 1 on invalid pattern (out of range,
 // entry above the diagonal, duplicates, unsorted indices).
+// ordering: 0 approximate minimum degree, 1 natural, 2 nested dissection
+// with leaves of at most nd_leaf vertices.
 int analyse_pattern(int64_t n, int64_t m, const int64_t* Hp, const int32_t* Hi,
                     const int64_t* Jp, const int32_t* Ji, const RelaxParams& rp,
-                    int ordering, Symbolic& out);
+                    int ordering, int nd_leaf, Symbolic& out);
 
 }  // namespace kkt

@@ -102,11 +102,12 @@ def test_hsolve_matches_oracle():
     assert rel(x, ref) <= 1e-9
 
 
+@pytest.mark.parametrize("ordering", ["amd", "nd"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_grid_n2000_matches_oracle(precision):
+def test_grid_n2000_matches_oracle(precision, ordering):
     sys = W.make_config("grid2d_n2000")
     _, _, odx, ody, oinfo = O.solve_system(sys)
-    s, code, dx, dy = gpu_solve(sys, precision)
+    s, code, dx, dy = gpu_solve(sys, precision, ordering=ordering)
     assert code == 0
     info = s.info
     assert info.rr <= 1e-8
@@ -118,10 +119,12 @@ def test_grid_n2000_matches_oracle(precision):
     assert s.inertia_ok
 
 
-def test_grid_n20k_and_value_updates():
+@pytest.mark.parametrize("ordering,precision", [("amd", "fp64"), ("nd", "fp64"), ("nd", "mixed")])
+def test_grid_n20k_and_value_updates(ordering, precision):
     """Four value refactorizations on one resident pattern (interior iterations)."""
     base = W.make_config("grid2d_n20k")
-    s = K.KKTSolver(base.n, base.m, base.H_colptr, base.H_rowidx, base.J_rowptr, base.J_colidx)
+    s = K.KKTSolver(base.n, base.m, base.H_colptr, base.H_rowidx, base.J_rowptr, base.J_colidx,
+                    ordering=ordering, precision=precision)
     sym = O.Symbolic(base.n, base.m, base.H_colptr, base.H_rowidx, base.J_rowptr, base.J_colidx)
     sys = base
     for t in range(4):

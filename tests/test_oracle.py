@@ -355,6 +355,39 @@ def test_amd_hand_worked(name):
     assert sym_of(sys).amd_order.tolist() == case["order"]
 
 
+@pytest.mark.parametrize("name", ["nd_path10_leaf2", "nd_star7_leaf2"])
+def test_nd_hand_worked(name):
+    case = _amd_case(name)
+    sys = graph_sys(case["n"], [tuple(e) for e in case["edges"]])
+    assert sym_of(sys, ordering="nd", nd_leaf=case["leaf"]).amd_order.tolist() == case["order"]
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_nd_is_a_permutation_and_separators_come_last(seed):
+    """Every ND separator vertex is numbered after both parts it separates:
+    so no vertex is adjacent to a later-numbered vertex of a *different*
+    earlier part. Checked through the symbolic result: the etree built on
+    the ND order is valid and the fill matches brute-force elimination."""
+    sys = W.random_tiny_system(seed + 700, n_lo=30, n_hi=90, density=0.05)
+    sym = sym_of(sys, ordering="nd", nd_leaf=4)
+    assert sorted(sym.amd_order.tolist()) == list(range(sys.n))
+    Lb = brute_symbolic(sys.n, adjacency_dense(sys), sym.perm)
+    np.testing.assert_array_equal(sym.colcount, Lb.sum(0) + 1)
+
+
+def test_nd_shortens_the_elimination_tree_on_the_grid():
+    """On the 200 x 100 grid workload nested dissection gives a much shorter
+    elimination tree than AMD (the reason to offer it on a GPU)."""
+    sys = W.make_config("grid2d_n20k")
+    def height(sym):
+        par = sym.parent
+        d = np.zeros(sys.n, int)
+        for j in range(sys.n - 1, -1, -1):
+            d[j] = d[par[j]] + 1 if par[j] >= 0 else 1
+        return d.max()
+    assert 2 * height(sym_of(sys, ordering="nd")) < height(sym_of(sys))
+
+
 @pytest.mark.parametrize("seed", range(10))
 def test_amd_zero_fill_on_trees(seed):
     """Minimum degree eliminates leaves first, so a tree gets no fill."""

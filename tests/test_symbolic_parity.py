@@ -24,12 +24,12 @@ def lib_symbolic(sys, **opt):
         K.kkt_destroy(h)
 
 
-def assert_same(sys, relax=(16, 1, 10, 256), ordering=0):
+def assert_same(sys, relax=(16, 1, 10, 256), ordering=0, nd_leaf=64):
     g, info = lib_symbolic(sys, relax_small=relax[0], relax_num=relax[1], relax_den=relax[2],
-                           relax_wmax=relax[3], ordering=ordering)
+                           relax_wmax=relax[3], ordering=ordering, nd_leaf=nd_leaf)
     sym = O.Symbolic(sys.n, sys.m, sys.H_colptr, sys.H_rowidx, sys.J_rowptr, sys.J_colidx,
                      relax_small=relax[0], relax_num=relax[1], relax_den=relax[2], wmax=relax[3],
-                     ordering="amd" if ordering == 0 else "natural")
+                     ordering={0: "amd", 1: "natural", 2: "nd"}[ordering], nd_leaf=nd_leaf)
     np.testing.assert_array_equal(g["amd"], sym.amd_order)
     np.testing.assert_array_equal(g["perm"], sym.perm)
     np.testing.assert_array_equal(g["parent"], sym.parent)
@@ -54,6 +54,24 @@ def test_random_tiny_patterns_bit_exact(seed):
 def test_relaxation_parameters_bit_exact(relax):
     for seed in range(6):
         assert_same(W.random_tiny_system(seed + 2000, n_lo=30, n_hi=120, density=0.05), relax=relax)
+
+
+@pytest.mark.parametrize("seed", range(60))
+def test_nested_dissection_random_bit_exact(seed):
+    rng = np.random.default_rng(seed)
+    sys = W.random_tiny_system(seed + 3000, n_lo=2, n_hi=120, density=float(rng.uniform(0.01, 0.2)))
+    assert_same(sys, ordering=2, nd_leaf=int(rng.integers(1, 20)))
+
+
+@pytest.mark.parametrize("name", ["grid2d_n2000", "grid2d_n20k"])
+def test_nested_dissection_workloads_bit_exact(name):
+    assert_same(W.make_config(name), ordering=2)
+
+
+@pytest.mark.slow
+def test_nested_dissection_n250k_bit_exact():
+    info = assert_same(W.make_config("grid2d_n250k"), ordering=2)
+    assert info.nnz_l > 1e8
 
 
 def test_natural_ordering_bit_exact():

@@ -270,7 +270,7 @@ def random_tiny_system(seed, n_lo=4, n_hi=40, density=0.15, spd=True, gamma=1e2)
     c = np.sort(rng.permutation(n)[:m])
     Jr, Jc, Jv = [], [], []
     for i in range(m):
-        extra = rng.choice(n, size=int(rng.integers(0, 4)), replace=False)
+        extra = rng.choice(n, size=min(int(rng.integers(0, 4)), n), replace=False)
         for cc in sorted(set([int(c[i])]) | set(int(e) for e in extra)):
             Jr.append(i)
             Jc.append(cc)
