@@ -108,10 +108,14 @@ def kernel_work(kind, prec, sym_arrays, nnz_l, iters_per_pass, nnz_j, n, m):
         return "alu", float((w * rb * (rb + 1)).sum()), "flop"         # per factorization (all launches)
     if kind == "cg_persistent":
         # one pass: (iters + 2) H^-1 applications, each reads L twice (nnz(L)
-        # entries of s bytes) and does 2 x nnz(L) FMAs; plus 2 SpMVs per iteration
+        # entries of s bytes, the algorithmic minimum; the panels also hold
+        # relaxation zeros and the unused upper part of diagonal blocks) and
+        # does 2 x nnz(L) FMAs; plus J and J^T products per iteration
         hs = iters_per_pass + 2
         byts = hs * 2 * s * nnz_l + iters_per_pass * 2 * (12 * nnz_j + 8 * (n + m))
         flops = hs * 4 * nnz_l
+        # FP64 on B300: 2 x nnz(L) DFMA per sweep at ~1/64 of the FP32 rate
+        # bounds the sweep before HBM does
         return ("alu", flops, "flop") if prec == "fp64" else ("hbm", byts, "byte")
     return None
 
@@ -152,7 +156,8 @@ def run_ours(args, rank, world):
     results = {}
     for prec in precs:
         t0 = time.time()
-        s = K.KKTSolver(n, m, base.H_colptr, base.H_rowidx, base.J_rowptr, base.J_colidx, precision=prec)
+        s = K.KKTSolver(n, m, base.H_colptr, base.H_rowidx, base.J_rowptr, base.J_colidx, precision=prec,
+                        ordering=args.ordering)
         t_analyse = time.time() - t0
         dx = torch.empty(n, dtype=torch.float64, device=dev)
         dy = torch.empty(m, dtype=torch.float64, device=dev)
@@ -203,7 +208,8 @@ def run_ours(args, rank, world):
     # steps in a profiled handle (launches serialised by the timing events)
     peaks, peak_src = load_peaks()
     prof_steps = max(1, min(args.steps, 3))
-    sp = K.KKTSolver(n, m, base.H_colptr, base.H_rowidx, base.J_rowptr, base.J_colidx, precision=head, profile=1)
+    sp = K.KKTSolver(n, m, base.H_colptr, base.H_rowidx, base.J_rowptr, base.J_colidx, precision=head, profile=1,
+                     ordering=args.ordering)
     for t in range(prof_steps):
         Hv, Jv, rx, ry, delta, gamma = dsets[t % N_VALUE_SETS]
         sp.factor(Hv, Jv, delta, gamma)
@@ -237,7 +243,8 @@ def run_ours(args, rank, world):
     e2e = None
     if not args.no_e2e:
         import torch
-        se = K.KKTSolver(n, m, base.H_colptr, base.H_rowidx, base.J_rowptr, base.J_colidx, precision=head)
+        se = K.KKTSolver(n, m, base.H_colptr, base.H_rowidx, base.J_rowptr, base.J_colidx, precision=head,
+                         ordering=args.ordering)
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
         hsets = [(pin(x.H_vals), pin(x.J_vals), pin(x.r_x), pin(x.r_y), x.delta, x.gamma) for x in sets]
         hx = pin(np.zeros(n))
@@ -269,7 +276,8 @@ def run_ours(args, rank, world):
         "dtype": "f32 factor+trisolve, f64 CG/residual/refinement" if head == "mixed" else "f64",
         "data": "synthetic (seeded grid-Laplacian + barrier + local J; paper's power-grid matrices unavailable)",
         "config": {"workload": "grid2d 500x500, n=250000, m=125000, 10 value refactorizations, gamma=1e4, delta=1e-8",
-                   "precision": head, "parallelism": "replicas" if world > 1 else "single",
+                   "precision": head, "ordering": args.ordering,
+                   "parallelism": "replicas" if world > 1 else "single",
                    "l2": "per-step working set > L2 (panels %.2f GB)" % (si.panel_entries * (4 if head == "mixed" else 8) / 1e9),
                    "nnz_L": si.nnz_l, "factor_flops": si.flops, "nsuper": si.nsuper},
         "latency_ms": {"p50": round(float(np.percentile(R["lat"], 50)), 3),
@@ -369,6 +377,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-seconds", type=float, default=10.0)
+    ap.add_argument("--ordering", default="nd", choices=["nd", "amd"])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -57,7 +57,8 @@ enum { KKT_FP64 = 0, KKT_MIXED = 1 };
 typedef struct kkt_options {
   double gamma;        /* default gamma when kkt_factor gets gamma < 0 (Algorithm 1: 1e4) */
   double delta2;       /* delta_2 of the CG restart on S + delta_2 I (Algorithm 1: 1e-9) */
-  double cg_rtol;      /* CG stop: ||r|| <= cg_rtol ||b_S|| (Sec. 5.1: 1e-12) */
+  double cg_rtol;      /* CG stop: ||r|| <= cg_rtol ||b_S|| (Sec. 5.1: 1e-12; with KKT_MIXED each
+                          refinement pass only needs ~1e-6, the FP32 factor limits it anyway) */
   int32_t cg_maxit;    /* CG product limit (1000) */
   int32_t ir_maxit;    /* refinement steps on K_delta after the first solve */
   double ir_rtol;      /* refine while RR(K_delta) > ir_rtol */
@@ -71,7 +72,8 @@ typedef struct kkt_options {
   int32_t relax_num;   /*   or explicit zeros * relax_den <= relax_num * panel entries */
   int32_t relax_den;
   int32_t relax_wmax;  /*   never beyond this width */
-  int32_t solve_w;     /* column width of the triangular-solve pieces (<= 256) */
+  int32_t solve_w;     /* column width of the triangular-solve pieces, 32..256;
+                          0 = 128 (KKT_MIXED) / 64 (KKT_FP64) */
   int32_t device;      /* CUDA device ordinal */
   int32_t debug_stall_piece; /* test hook, -1 = off: makes one triangular-solve piece wait for
                                 an arrival that never comes, so the bounded wait runs out */
@@ -113,6 +115,8 @@ typedef struct kkt_symbolic_info {
   double flops;        /* sum_j colcount_j^2 (factor flop count, no explicit zeros) */
   double device_bytes; /* device memory held by the handle */
   int64_t fwd_depth, bwd_depth;  /* longest dependency chains of the two triangular sweeps */
+  int64_t nsub;        /* small subtrees solved whole by one CTA */
+  int64_t nitems;      /* work items per triangular sweep */
 } kkt_symbolic_info;
 
 /* Defaults: Algorithm 1's typical parameters (gamma 1e4, delta_2 1e-9), CG
@@ -203,6 +207,12 @@ kkt_status kkt_get_factor_panels(kkt_handle h, double* panels);
  * last reset, for handles created with opt.profile = 1 (host arrays of
  * KKT_K_COUNT entries). reset != 0 clears the counters after reading. */
 kkt_status kkt_get_profile(kkt_handle h, double* ms, int64_t* launches, int32_t reset);
+
+/* Cycle counters of the persistent solve kernel summed over its CTAs (thread
+ * 0 of each), for handles created with opt.profile = 1; host uint64_t[8]:
+ * [0] item dispatch, [1] dependency waits, [2] bulk-copy waits, [3] whole
+ * items, [4] grid barriers, [5] items processed, [6] CTA-launches. */
+kkt_status kkt_get_solve_counters(kkt_handle h, uint64_t* out, int32_t reset);
 
 kkt_status kkt_destroy(kkt_handle h);
 

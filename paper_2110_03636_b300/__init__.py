@@ -48,7 +48,7 @@ class kkt_symbolic_info(C.Structure):
                 ("panel_entries", C.c_int64), ("update_entries", C.c_int64), ("sn_rows_total", C.c_int64),
                 ("npieces", C.c_int64), ("nchunks", C.c_int64), ("nlevels", C.c_int32), ("pad", C.c_int32),
                 ("flops", C.c_double), ("device_bytes", C.c_double), ("fwd_depth", C.c_int64),
-                ("bwd_depth", C.c_int64)]
+                ("bwd_depth", C.c_int64), ("nsub", C.c_int64), ("nitems", C.c_int64)]
 
 
 def _load():
@@ -70,12 +70,14 @@ def _load():
     L.kkt_get_symbolic.argtypes = [P] + [P] * 8
     L.kkt_get_factor_panels.argtypes = [P, P]
     L.kkt_get_profile.argtypes = [P, P, P, I32]
+    L.kkt_get_solve_counters.argtypes = [P, P, I32]
     L.kkt_residual_noalloc.argtypes = [I64, I64, P, P, P, P, P, P, D, P, P, P, P, P, P, P, P]
     L.kkt_destroy.argtypes = [P]
     L.kkt_status_string.argtypes = [I32]
     L.kkt_status_string.restype = C.c_char_p
     for nm in ("kkt_analyse", "kkt_analyse_host", "kkt_factor", "kkt_solve", "kkt_factor_solve_host", "kkt_hsolve", "kkt_get_info",
-               "kkt_inertia", "kkt_symbolic_info_get", "kkt_get_symbolic", "kkt_get_factor_panels", "kkt_get_profile", "kkt_residual_noalloc", "kkt_destroy"):
+               "kkt_inertia", "kkt_symbolic_info_get", "kkt_get_symbolic", "kkt_get_factor_panels", "kkt_get_profile", "kkt_get_solve_counters", "kkt_residual_noalloc",
+               "kkt_destroy"):
         getattr(L, nm).restype = I32
     return L
 
@@ -83,8 +85,8 @@ def _load():
 _lib = _load()
 EXPORTED = ("kkt_default_options", "kkt_analyse", "kkt_analyse_host", "kkt_factor", "kkt_solve", "kkt_factor_solve_host",
             "kkt_hsolve", "kkt_get_info", "kkt_inertia", "kkt_symbolic_info_get", "kkt_get_symbolic",
-            "kkt_get_factor_panels", "kkt_get_profile", "kkt_residual_noalloc", "kkt_destroy",
-            "kkt_status_string")
+            "kkt_get_factor_panels", "kkt_get_profile", "kkt_get_solve_counters", "kkt_residual_noalloc",
+            "kkt_destroy", "kkt_status_string")
 KERNEL_KINDS = ("assemble", "potrf", "trsm", "panel_update", "syrk", "extend_add", "zero_u", "cg_persistent",
                 "residual", "tri_inv")
 
@@ -237,6 +239,14 @@ def kkt_residual_noalloc(n, m, H_colptr, H_rowidx, H_vals, J_rowptr, J_colidx, J
                                      ptr(res_y, f64), ptr(norms, f64), _stream(stream))
 
 
+def kkt_get_solve_counters(h, reset=False):
+    """Cycle counters of the persistent solve kernel (profile=1 handles)."""
+    out = np.zeros(8, np.uint64)
+    _check("kkt_get_solve_counters", _lib.kkt_get_solve_counters(h, out.ctypes.data, int(bool(reset))))
+    keys = ("dispatch", "dep_wait", "copy_wait", "items", "barriers", "n_items", "cta_launches")
+    return {k: int(out[i]) for i, k in enumerate(keys)}
+
+
 def kkt_destroy(h):
     return _lib.kkt_destroy(h)
 
@@ -259,7 +269,7 @@ class KKTSolver:
         if options.get("precision") in ("mixed", KKT_MIXED):
             # each refinement pass only needs a moderately accurate inner solve
             # with the FP32 factor; FP64 refinement on K_delta does the rest
-            options.setdefault("cg_rtol", 1e-8)
+            options.setdefault("cg_rtol", 1e-6)
             options.setdefault("ir_maxit", 10)
         self.opt = kkt_default_options(**options)
         self.h = kkt_analyse(n, m, H_colptr, H_rowidx, J_rowptr, J_colidx, self.opt)
@@ -314,6 +324,9 @@ class KKTSolver:
 
     def profile(self, reset=False):
         return kkt_get_profile(self.h, reset)
+
+    def solve_counters(self, reset=False):
+        return kkt_get_solve_counters(self.h, reset)
 
     def close(self):
         if getattr(self, "h", None):

@@ -69,6 +69,8 @@ struct kkt_handle_s {
   int32_t *ch_piece, *ch_r0, *ch_nr, *ch_k, *ch_tgt;
   int32_t *fwd_items, *bwd_items;
   int64_t *pc_row, *pc_colbase, *pc_inv, *pc_zoff, *hd_tptr, *ch_tptr;
+  int32_t *st_first, *st_last, *st_clo, *st_chi, *st_tgt, *sn_piece;
+  int64_t* st_tptr;
   // values and workspace
   double *Hv, *Jv;
   void *L, *U, *v, *zpart, *Linv;
@@ -77,6 +79,11 @@ struct kkt_handle_s {
   int* counters;   // fwd_arrive, fwd_done, bwd_arrive, bwd_done (npieces each), disp[3], bar[2]
   DevStatus* dst;
   DevStatus* hst = nullptr;  // pinned
+  double* d_dg = nullptr;    // device [delta, gamma] read by the assembly kernel
+  unsigned long long* d_instr = nullptr;   // solve-kernel cycle counters (profile mode)
+  double* h_dg = nullptr;    // pinned staging for it
+  cudaStream_t cap_stream = nullptr;   // private stream used to capture the factor graph
+  cudaGraphExec_t fac_graph = nullptr; // the whole factorization as one CUDA graph
   // state
   bool on_device = false;   // false for a host-only (symbolic) handle
   bool factored = false;
@@ -115,7 +122,7 @@ void kkt_default_options(kkt_options* o) {
   o->relax_num = 1;
   o->relax_den = 10;
   o->relax_wmax = 256;
-  o->solve_w = 128;
+  o->solve_w = 0;
   o->device = 0;
   o->debug_stall_piece = -1;
   o->spin_cycles = 0;
@@ -146,6 +153,9 @@ kkt_status kkt_destroy(kkt_handle h) {
     h->mem.release();
   }
   if (h->hst) cudaFreeHost(h->hst);
+  if (h->h_dg) cudaFreeHost(h->h_dg);
+  if (h->fac_graph) cudaGraphExecDestroy(h->fac_graph);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->prof.a) cudaEventDestroy(h->prof.a);
   if (h->prof.b) cudaEventDestroy(h->prof.b);
   delete h;
@@ -161,7 +171,8 @@ static kkt_status analyse_host(int64_t n, int64_t m, const int64_t* Hp, const in
   if (!h) return KKT_ERR_OOM;
   if (opt) h->opt = *opt; else kkt_default_options(&h->opt);
   const kkt_options& o = h->opt;
-  if (o.solve_w < 32 || o.solve_w > 256 || o.relax_den <= 0 || o.precision < 0 || o.precision > 1) {
+  if ((o.solve_w != 0 && (o.solve_w < 32 || o.solve_w > 256)) || o.relax_den <= 0 || o.precision < 0 ||
+      o.precision > 1) {
     delete h;
     return KKT_ERR_INVALID;
   }
@@ -171,10 +182,13 @@ static kkt_status analyse_host(int64_t n, int64_t m, const int64_t* Hp, const in
   rp.small = o.relax_small; rp.num = o.relax_num; rp.den = o.relax_den; rp.wmax = o.relax_wmax;
   if (o.ordering < 0 || o.ordering > 2 || (o.ordering == 2 && o.nd_leaf < 1)) { delete h; return KKT_ERR_INVALID; }
   if (analyse_pattern(n, m, Hp, Hi, Jp, Ji, rp, o.ordering, o.nd_leaf, h->S) != 0) { delete h; return KKT_ERR_INVALID; }
-  // tiles of the solve kernel: FP64 keeps the head's chunk 0 shorter so that
-  // its shared-memory staging fits in one SM's 227 KB
-  const int rc = 128, rc0 = o.precision == KKT_FP64 ? 64 : 128;
-  if (build_plan(h->S, Hp, Hi, Jp, Ji, o.solve_w, rc, rc0, h->P) != 0) { delete h; return KKT_ERR_INVALID; }
+  // piece width and L entries per solve item: a head's first chunk covers
+  // the next piece's columns, and two CTAs of the solve kernel fit on one SM
+  // (about 107 KB (FP32) / 98 KB (FP64) of shared memory each)
+  const bool f64o = o.precision == KKT_FP64;
+  const int sw = o.solve_w > 0 ? o.solve_w : (f64o ? 64 : 128);
+  const int ent = f64o ? 8192 : 16384;
+  if (build_plan(h->S, Hp, Hi, Jp, Ji, sw, ent, ent, h->P) != 0) { delete h; return KKT_ERR_INVALID; }
   if (o.debug_stall_piece >= 0 && o.debug_stall_piece < h->P.npieces) h->P.pc_need[o.debug_stall_piece] += 1;
   h->nnzH = Hp[n];
   h->nnzJ = Jp[m];
@@ -202,8 +216,8 @@ kkt_status kkt_analyse(int64_t n, int64_t m, const int64_t* Hp, const int32_t* H
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device);
   if (!coop) { delete h; return KKT_ERR_CUDA; }
   const bool f64 = o.precision == KKT_FP64;
-  h->grid = f64 ? solve_grid_size<double>(h->device, h->P.solve_w, h->P.rc, h->P.rc0)
-                : solve_grid_size<float>(h->device, h->P.solve_w, h->P.rc, h->P.rc0);
+  h->grid = f64 ? solve_grid_size<double>(h->device, h->P.solve_w, h->P.ent, h->P.ent0, h->P.max_rows)
+                : solve_grid_size<float>(h->device, h->P.solve_w, h->P.ent, h->P.ent0, h->P.max_rows);
   if (h->grid <= 0) { delete h; return KKT_ERR_INVALID; }
   const Plan& P = h->P;
   DevArena& A = h->mem;
@@ -235,6 +249,9 @@ kkt_status kkt_analyse(int64_t n, int64_t m, const int64_t* Hp, const int32_t* H
   h->ch_piece = A.upload(P.ch_piece); h->ch_r0 = A.upload(P.ch_r0); h->ch_nr = A.upload(P.ch_nr);
   h->ch_k = A.upload(P.ch_k); h->ch_tptr = A.upload(P.ch_tptr); h->ch_tgt = A.upload(P.ch_tgt);
   h->fwd_items = A.upload(P.fwd_items); h->bwd_items = A.upload(P.bwd_items);
+  h->st_first = A.upload(P.st_first); h->st_last = A.upload(P.st_last); h->st_clo = A.upload(P.st_clo);
+  h->st_chi = A.upload(P.st_chi); h->st_tgt = A.upload(P.st_tgt); h->st_tptr = A.upload(P.st_tptr);
+  h->sn_piece = A.upload(P.sn_piece);
   const size_t es = f64 ? sizeof(double) : sizeof(float);
   h->Hv = A.alloc<double>(h->nnzH); h->Jv = A.alloc<double>(h->nnzJ);
   h->L = A.alloc<char>(es * (size_t)P.panel_total);
@@ -251,8 +268,12 @@ kkt_status kkt_analyse(int64_t n, int64_t m, const int64_t* Hp, const int32_t* H
   h->stage_dx = A.alloc<double>(n); h->stage_dy = A.alloc<double>(m);
   h->counters = A.alloc<int>(4 * (size_t)P.npieces + 8);
   h->dst = A.alloc<DevStatus>(1);
+  h->d_dg = A.alloc<double>(2);
+  h->d_instr = A.alloc<unsigned long long>(8);
   if (A.failed) { kkt_destroy(h); return KKT_ERR_OOM; }
   if (cudaMallocHost(&h->hst, sizeof(DevStatus)) != cudaSuccess) { cudaGetLastError(); h->hst = nullptr; kkt_destroy(h); return KKT_ERR_OOM; }
+  if (cudaMallocHost(&h->h_dg, 2 * sizeof(double)) != cudaSuccess) { cudaGetLastError(); h->h_dg = nullptr; kkt_destroy(h); return KKT_ERR_OOM; }
+  if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) { cudaGetLastError(); h->cap_stream = nullptr; kkt_destroy(h); return KKT_ERR_CUDA; }
   if (cudaDeviceSynchronize() != cudaSuccess) { cudaGetLastError(); kkt_destroy(h); return KKT_ERR_CUDA; }
   if (o.profile) {
     if (cudaEventCreate(&h->prof.a) != cudaSuccess || cudaEventCreate(&h->prof.b) != cudaSuccess) {
@@ -261,6 +282,7 @@ kkt_status kkt_analyse(int64_t n, int64_t m, const int64_t* Hp, const int32_t* H
       return KKT_ERR_CUDA;
     }
     h->profp = &h->prof;
+    if (cudaMemset(h->d_instr, 0, 8 * sizeof(unsigned long long)) != cudaSuccess) { cudaGetLastError(); kkt_destroy(h); return KKT_ERR_CUDA; }
   }
   h->on_device = true;
   *out = h;
@@ -284,7 +306,7 @@ static kkt_status read_status(kkt_handle h, cudaStream_t st) {
 }
 
 template <typename T>
-static kkt_status factor_impl(kkt_handle h, cudaStream_t st) {
+static cudaError_t factor_launches(kkt_handle h, cudaStream_t st, Prof* prof) {
   FacArgs<T> a;
   a.sfirst = h->sfirst; a.sw = h->sw; a.snr = h->snr; a.sld = h->sld; a.sparent = h->sparent; a.rel = h->rel;
   a.srow = h->srow; a.poff = h->poff; a.uoff = h->uoff;
@@ -297,14 +319,45 @@ static kkt_status factor_impl(kkt_handle h, cudaStream_t st) {
   fl.nslot = (int64_t)h->P.slot_pos.size();
   fl.panel_total = h->P.panel_total; fl.u_total = h->P.u_total;
   fl.launches = &h->P.launches;
-  CK(launch_factor<T>(a, fl, h->delta, h->gamma, st, h->profp));
+  cudaError_t e = launch_factor<T>(a, fl, h->d_dg, st, prof);
+  if (e) return e;
   InvArgs<T> ia;
   ia.pc_w = h->pc_w; ia.pc_ld = h->pc_ld; ia.pc_c = h->pc_c;
   ia.pc_colbase = h->pc_colbase; ia.pc_inv = h->pc_inv;
   ia.L = (const T*)h->L; ia.Linv = (T*)h->Linv;
-  CK(prof_begin(h->profp, st));
-  CK(launch_tri_inv<T>(ia, h->P.npieces, h->P.solve_w, st));
-  CK(prof_end(h->profp, KKT_K_TRI_INV, st));
+  if ((e = prof_begin(prof, st))) return e;
+  if ((e = launch_tri_inv<T>(ia, h->P.npieces, h->P.solve_w, st))) return e;
+  return prof_end(prof, KKT_K_TRI_INV, st);
+}
+
+// The factorization's launch sequence depends only on the pattern, so it is
+// captured once into a CUDA graph (on a private stream) and replayed on the
+// caller's stream for every value update; delta and gamma are read from
+// device memory. Profile mode launches kernel by kernel instead.
+template <typename T>
+static kkt_status factor_impl(kkt_handle h, cudaStream_t st) {
+  h->h_dg[0] = h->delta;
+  h->h_dg[1] = h->gamma;
+  CK(cudaMemcpyAsync(h->d_dg, h->h_dg, 2 * sizeof(double), cudaMemcpyHostToDevice, st));
+  if (h->profp) {
+    CK(factor_launches<T>(h, st, h->profp));
+    return KKT_OK;
+  }
+  if (!h->fac_graph) {
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = factor_launches<T>(h, h->cap_stream, nullptr);
+    cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &g);
+    if (e || e2) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return KKT_ERR_CUDA;
+    }
+    e = cudaGraphInstantiate(&h->fac_graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e) { h->fac_graph = nullptr; return cuda_status(e); }
+  }
+  CK(cudaGraphLaunch(h->fac_graph, st));
   return KKT_OK;
 }
 
@@ -335,12 +388,16 @@ static SolveArgs<T> solve_args(kkt_handle h) {
   a.pc_first = h->pc_first; a.pc_w = h->pc_w; a.pc_ld = h->pc_ld; a.pc_c = h->pc_c; a.pc_rc0 = h->pc_rc0;
   a.pc_nchunk = h->pc_nchunk; a.pc_need = h->pc_need; a.pc_row = h->pc_row; a.pc_colbase = h->pc_colbase;
   a.pc_inv = h->pc_inv; a.pc_zoff = h->pc_zoff; a.hd_tptr = h->hd_tptr; a.hd_tgt = h->hd_tgt;
-  a.sw = P.solve_w; a.rc = P.rc; a.rc0 = P.rc0;
+  a.sw = P.solve_w; a.ent = P.ent; a.ent0 = P.ent0; a.max_rows = P.max_rows;
   a.Linv = (const T*)h->Linv;
   a.ch_piece = h->ch_piece; a.ch_r0 = h->ch_r0; a.ch_nr = h->ch_nr; a.ch_k = h->ch_k;
   a.ch_tptr = h->ch_tptr; a.ch_tgt = h->ch_tgt;
   a.fwd_items = h->fwd_items; a.bwd_items = h->bwd_items;
-  a.nitems = P.npieces + P.nchunks;
+  a.nitems = (int64_t)P.fwd_items.size();
+  a.npieces = P.npieces;
+  a.st_first = h->st_first; a.st_last = h->st_last; a.st_clo = h->st_clo; a.st_chi = h->st_chi;
+  a.st_tgt = h->st_tgt; a.st_tptr = h->st_tptr; a.sn_piece = h->sn_piece;
+  a.sfirst = h->sfirst; a.sw_ = h->sw; a.snr = h->snr; a.sld = h->sld; a.srow = h->srow; a.poff = h->poff;
   a.L = (const T*)h->L;
   a.J_rowptr = h->J_rowptr; a.Jcol_perm = h->Jcol_perm; a.Jv = h->Jv;
   a.JT_ptr = h->JT_ptr; a.JT_row = h->JT_row; a.JT_vidx = h->JT_vidx;
@@ -354,6 +411,7 @@ static SolveArgs<T> solve_args(kkt_handle h) {
   a.disp = h->counters + 4 * np; a.bar = h->counters + 4 * np + 4;
   a.red = h->red; a.st = h->dst;
   a.spin = h->opt.spin_cycles > 0 ? h->opt.spin_cycles : kSpinCycles;
+  a.instr = h->profp ? h->d_instr : nullptr;
   return a;
 }
 
@@ -498,6 +556,7 @@ kkt_status kkt_symbolic_info_get(kkt_handle h, kkt_symbolic_info* o) {
   o->sn_rows_total = (int64_t)h->S.sn_rows.size();
   o->npieces = h->P.npieces; o->nchunks = h->P.nchunks; o->nlevels = h->P.nlevels;
   o->fwd_depth = h->P.fwd_depth; o->bwd_depth = h->P.bwd_depth;
+  o->nsub = h->P.nsub; o->nitems = (int64_t)h->P.fwd_items.size();
   o->flops = h->S.flops;
   o->device_bytes = (double)h->mem.bytes;
   return KKT_OK;
@@ -522,6 +581,15 @@ kkt_status kkt_get_profile(kkt_handle h, double* ms, int64_t* launches, int32_t 
   if (reset) {
     for (int k = 0; k < KKT_K_COUNT; k++) { h->prof.ms[k] = 0; h->prof.n[k] = 0; }
   }
+  return KKT_OK;
+}
+
+kkt_status kkt_get_solve_counters(kkt_handle h, uint64_t* out, int32_t reset) {
+  if (!h || !out) return KKT_ERR_INVALID;
+  if (!h->on_device) return KKT_ERR_STATE;
+  CK(cudaSetDevice(h->device));
+  CK(cudaMemcpy(out, h->d_instr, 8 * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+  if (reset) CK(cudaMemset(h->d_instr, 0, 8 * sizeof(uint64_t)));
   return KKT_OK;
 }
 

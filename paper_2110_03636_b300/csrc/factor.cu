@@ -26,7 +26,8 @@ template <typename T>
 __global__ void k_assemble(int64_t nslot, const int64_t* __restrict__ slot_pos,
                            const int64_t* __restrict__ src_ptr, const int32_t* __restrict__ srcA,
                            const int32_t* __restrict__ srcB, const double* __restrict__ Hv,
-                           const double* __restrict__ Jv, double delta, double gamma, T* __restrict__ L) {
+                           const double* __restrict__ Jv, const double* __restrict__ dg, T* __restrict__ L) {
+  const double delta = dg[0], gamma = dg[1];   // device scalars: a captured graph replays with new values
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nslot; t += (int64_t)gridDim.x * blockDim.x) {
     double v = 0.0;
     for (int64_t q = src_ptr[t]; q < src_ptr[t + 1]; q++) {
@@ -257,16 +258,16 @@ __global__ void __launch_bounds__(256) k_extend_add(const int4* __restrict__ ite
 
 // ---------------------------------------------------------- triangle inverses
 // For every triangular-solve piece: X = T^-1 of its pw x pw diagonal
-// triangle T (lower), stored column-major with ld = round4(pw), so that the
-// solve applies T^-1 as a dense mat-vec. Thread k computes column k by
-// forward substitution; T is staged in shared memory.
+// triangle T (lower), stored packed by columns (column k holds rows k..pw-1,
+// padded to a multiple of 4), so that the solve applies T^-1 as a dense
+// mat-vec. Thread k computes column k by forward substitution; T is staged
+// in shared memory.
 template <typename T>
 __global__ void __launch_bounds__(128) k_tri_inv(InvArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* Ts = (T*)smem_raw;
   const int p = blockIdx.x;
   const int pw = a.pc_w[p], ld = a.pc_ld[p], c = a.pc_c[p];
-  const int ldi = (pw + 3) & ~3;
   const T* L = a.L + a.pc_colbase[p] + c;      // (row c, col c) of the supernode panel
   for (int e = threadIdx.x; e < pw * pw; e += blockDim.x) {
     const int i = e % pw, j = e / pw;
@@ -275,14 +276,16 @@ __global__ void __launch_bounds__(128) k_tri_inv(InvArgs<T> a) {
   __syncthreads();
   T* X = a.Linv + a.pc_inv[p];
   for (int k = threadIdx.x; k < pw; k += blockDim.x) {
-    T* xk = X + (int64_t)k * ldi;
-    for (int i = 0; i < k; i++) xk[i] = T(0);
+    int64_t off = 0;                              // packed column offset
+    for (int j = 0; j < k; j++) off += (pw - j + 3) & ~3;
+    T* xk = X + off - k;                          // xk[i] = X(i, k), i >= k
     xk[k] = T(1) / Ts[k + k * pw];
     for (int i = k + 1; i < pw; i++) {
       T s = T(0);
       for (int j = k; j < i; j++) s += Ts[i + j * pw] * xk[j];
       xk[i] = -s / Ts[i + i * pw];
     }
+    for (int i = pw; i < k + ((pw - k + 3) & ~3); i++) xk[i] = T(0);   // padding
   }
 }
 
@@ -315,8 +318,8 @@ cudaError_t prof_end(Prof* pr, int kind, cudaStream_t st) {
 }
 
 template <typename T>
-cudaError_t launch_factor(const FacArgs<T>& a, const FacLists& fl, double delta, double gamma,
-                          cudaStream_t st, Prof* prof) {
+cudaError_t launch_factor(const FacArgs<T>& a, const FacLists& fl, const double* dg, cudaStream_t st,
+                          Prof* prof) {
   cudaError_t e;
   if ((e = cudaMemsetAsync(a.L, 0, sizeof(T) * (size_t)fl.panel_total, st))) return e;
   {
@@ -326,7 +329,7 @@ cudaError_t launch_factor(const FacArgs<T>& a, const FacLists& fl, double delta,
     if (blocks < 1) blocks = 1;
     if ((e = prof_begin(prof, st))) return e;
     k_assemble<T><<<(unsigned)blocks, threads, 0, st>>>(fl.nslot, fl.slot_pos, fl.src_ptr, fl.srcA, fl.srcB,
-                                                         a.Hv, a.Jv, delta, gamma, a.L);
+                                                         a.Hv, a.Jv, dg, a.L);
     if ((e = prof_end(prof, 0, st))) return e;
   }
   for (const Launch& L : *fl.launches) {
@@ -345,9 +348,9 @@ cudaError_t launch_factor(const FacArgs<T>& a, const FacLists& fl, double delta,
   return cudaGetLastError();
 }
 
-template cudaError_t launch_factor<double>(const FacArgs<double>&, const FacLists&, double, double, cudaStream_t,
+template cudaError_t launch_factor<double>(const FacArgs<double>&, const FacLists&, const double*, cudaStream_t,
                                            Prof*);
-template cudaError_t launch_factor<float>(const FacArgs<float>&, const FacLists&, double, double, cudaStream_t,
+template cudaError_t launch_factor<float>(const FacArgs<float>&, const FacLists&, const double*, cudaStream_t,
                                           Prof*);
 
 }  // namespace kkt

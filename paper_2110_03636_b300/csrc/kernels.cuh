@@ -49,7 +49,7 @@ template <typename T>
 cudaError_t launch_tri_inv(const InvArgs<T>& a, int64_t npieces, int max_pw, cudaStream_t st);
 
 template <typename T>
-cudaError_t launch_factor(const FacArgs<T>& a, const FacLists& fl, double delta, double gamma, cudaStream_t st,
+cudaError_t launch_factor(const FacArgs<T>& a, const FacLists& fl, const double* dg, cudaStream_t st,
                           Prof* prof = nullptr);
 
 // Persistent CG on the Schur complement (plus the two direct solves).
@@ -65,8 +65,13 @@ struct SolveArgs {
   const int64_t* ch_tptr;
   const int32_t* ch_tgt;
   const int32_t *fwd_items, *bwd_items;
-  int64_t nitems;
-  int32_t sw, rc, rc0;  // piece width and chunk rows the shared-memory tiles are sized for
+  int64_t nitems, npieces;
+  int32_t sw, ent, ent0, max_rows;  // piece width, L entries per chunk / head chunk 0, max chunk rows
+  // small subtrees solved whole by one CTA
+  const int32_t *st_first, *st_last, *st_clo, *st_chi, *st_tgt, *sn_piece;
+  const int64_t* st_tptr;
+  const int32_t *sfirst, *sw_, *snr, *sld;
+  const int64_t *srow, *poff;
   const T* L;
   const T* Linv;
   // J (CSR, permuted column labels) and J^T (by permuted column)
@@ -93,13 +98,14 @@ struct SolveArgs {
   double* red; // [grid * 4]
   DevStatus* st;
   long long spin;  // bound of every wait, in clock cycles
+  unsigned long long* instr;  // optional per-kernel cycle counters (profile mode), else null
 };
 
 template <typename T>
 cudaError_t launch_solve(const SolveArgs<T>& a, int grid, cudaStream_t st);
 template <typename T>
-int solve_grid_size(int device, int sw, int rc, int rc0);
-size_t solve_smem_bytes(size_t elem, int sw, int rc, int rc0);
+int solve_grid_size(int device, int sw, int ent, int ent0, int max_rows);
+size_t solve_smem_bytes(size_t elem, int sw, int ent, int ent0, int max_rows);
 
 // FP64 residual of K_delta = [H~ + delta I, J^T; J, 0] (original labels):
 // res = b - K x, and norms into DevStatus (rr, be, ...).

@@ -8,7 +8,7 @@ namespace kkt {
 static inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const int64_t* Jp,
-               const int32_t* Ji, int32_t solve_w, int32_t rc, int32_t rc0, Plan& P) {
+               const int32_t* Ji, int32_t solve_w, int32_t ent, int32_t ent0, Plan& P) {
   P = Plan();
   const int64_t n = S.n, m = S.m, ns = S.ns;
   P.n = n; P.m = m; P.ns = ns;
@@ -229,10 +229,63 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
         if (i != j) { P.Hs_col[fill[j]] = i; P.Hs_vidx[fill[j]++] = (int32_t)q; }
       }
   }
+  // ---------------------------------------------------------- small subtrees
+  // Maximal subtrees with at most kSubCols columns and kSubEntries panel
+  // entries; supernode indices are a postorder, so a subtree is the index
+  // range [root - size + 1, root].
+  const int64_t kSubCols = std::min<int64_t>(128, solve_w), kSubEntries = 32768;
+  std::vector<int64_t> sub_cols(ns, 0), sub_ent(ns, 0), sub_size(ns, 1);
+  for (int64_t s = 0; s < ns; s++) {
+    sub_cols[s] += P.sw[s];
+    sub_ent[s] += (int64_t)P.sw[s] * P.snr[s];
+    const int32_t p = P.sparent[s];
+    if (p >= 0) { sub_cols[p] += sub_cols[s]; sub_ent[p] += sub_ent[s]; sub_size[p] += sub_size[s]; }
+  }
+  auto small_sub = [&](int64_t s) { return sub_cols[s] <= kSubCols && sub_ent[s] <= kSubEntries; };
+  // maximal small subtrees, as supernode ranges in postorder
+  std::vector<std::pair<int64_t, int64_t>> subs;
+  for (int64_t s = 0; s < ns; s++) {
+    if (!small_sub(s)) continue;
+    const int32_t p = P.sparent[s];
+    if (p >= 0 && small_sub(p)) continue;          // not maximal: the parent's subtree covers it
+    subs.push_back({s - sub_size[s] + 1, s});
+  }
+  // bundle runs of adjacent subtrees (siblings are adjacent in postorder)
+  // into one item while it stays within the same column/entry limits; rows
+  // of a supernode inside the bundle's column range belong to its own subtree
+  std::vector<int32_t> in_sub(ns, -1);
+  for (size_t k = 0; k < subs.size();) {
+    int64_t first = subs[k].first, last = subs[k].second;
+    int64_t cols = sub_cols[last], ent = sub_ent[last];
+    size_t q = k + 1;
+    while (q < subs.size() && subs[q].first == last + 1 && cols + sub_cols[subs[q].second] <= kSubCols &&
+           ent + sub_ent[subs[q].second] <= kSubEntries) {
+      last = subs[q].second;
+      cols += sub_cols[last];
+      ent += sub_ent[last];
+      q++;
+    }
+    const int32_t t = (int32_t)P.st_first.size();
+    for (int64_t x = first; x <= last; x++) in_sub[x] = t;
+    P.st_first.push_back((int32_t)first);
+    P.st_last.push_back((int32_t)last);
+    P.st_clo.push_back(P.sfirst[first]);
+    P.st_chi.push_back(P.sfirst[last] + P.sw[last]);
+    k = q;
+  }
+  P.nsub = (int64_t)P.st_first.size();
   // ---------------------------------------------------------- solve DAG
   P.solve_w = solve_w;
-  P.rc = rc;
-  P.rc0 = rc0;
+  P.ent = ent;
+  P.ent0 = ent0;
+  // rows of an item holding at most e entries of a pw-wide piece: a multiple
+  // of 4 (so the staged column segments stay 16-byte aligned) in [4, max_rows]
+  auto rows_for = [&](int32_t e, int32_t pw) {
+    int32_t r = e / std::max(pw, 1);
+    r = std::min(r, P.max_rows);
+    r &= ~3;
+    return std::max(r, 4);
+  };
   std::vector<int32_t> col2piece(n);
   for (int64_t s = 0; s < ns; s++) {
     for (int32_t c = 0; c < P.sw[s]; c += solve_w) {
@@ -246,11 +299,13 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
       P.pc_row.push_back(P.srow[s] + c);
       P.pc_colbase.push_back(P.poff[s] + (int64_t)c * P.sld[s]);
       P.pc_inv.push_back(P.inv_total);
-      P.inv_total += (int64_t)pw * ((pw + 3) & ~3);
+      P.inv_total += packed_inv_size(pw);
       for (int32_t j = 0; j < pw; j++) col2piece[P.sfirst[s] + c + j] = pid;
+      if (c == 0) P.sn_piece.push_back(pid);
     }
   }
   P.npieces = (int64_t)P.pc_first.size();
+  P.pc_inv.push_back(P.inv_total);               // [npieces + 1]: sizes by difference
   P.pc_zoff.resize(P.npieces);
   P.pc_nchunk.resize(P.npieces);
   P.pc_rc0.resize(P.npieces);
@@ -261,9 +316,20 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
     for (int32_t i = 0; i < nr; i++) out.push_back(col2piece[S.sn_rows[P.pc_row[p] + r0 + i]]);
     out.erase(std::unique(out.begin(), out.end()), out.end());   // rows ascending => pieces ascending
   };
+  std::vector<int32_t> piece_sub(P.npieces, -1);
+  for (int64_t s = 0; s < ns; s++)
+    if (in_sub[s] >= 0) piece_sub[P.sn_piece[s]] = in_sub[s];   // subtree supernodes are single pieces
   for (int64_t p = 0; p < P.npieces; p++) {
     const int32_t pw = P.pc_w[p];
     const int32_t below = P.pc_nr[p] - pw;
+    if (piece_sub[p] >= 0) {                      // solved inside its subtree item
+      P.pc_rc0[p] = 0;
+      P.hd_tptr.push_back((int64_t)P.hd_tgt.size());
+      P.pc_nchunk[p] = 0;
+      P.pc_zoff[p] = P.z_total;
+      continue;
+    }
+    const int32_t rc0 = rows_for(ent0, pw), rc = rows_for(ent, pw);
     const int32_t r0n = std::min(below, rc0);
     P.pc_rc0[p] = r0n;
     P.hd_tptr.push_back((int64_t)P.hd_tgt.size());
@@ -289,6 +355,19 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
   P.hd_tptr.push_back((int64_t)P.hd_tgt.size());
   P.nchunks = (int64_t)P.ch_piece.size();
   P.ch_tptr.push_back((int64_t)P.ch_tgt.size());
+  for (int64_t t = 0; t < P.nsub; t++) {
+    P.st_tptr.push_back((int64_t)P.st_tgt.size());
+    tg.clear();
+    for (int64_t s = P.st_first[t]; s <= P.st_last[t]; s++)
+      for (int64_t k = P.sw[s]; k < P.snr[s]; k++) {
+        const int32_t r = S.sn_rows[P.srow[s] + k];
+        if (r >= P.st_chi[t]) tg.push_back(col2piece[r]);
+      }
+    std::sort(tg.begin(), tg.end());
+    tg.erase(std::unique(tg.begin(), tg.end()), tg.end());
+    for (int32_t q : tg) { P.st_tgt.push_back(q); P.pc_need[q]++; }
+  }
+  P.st_tptr.push_back((int64_t)P.st_tgt.size());
   // dispatch order: by depth in the dependency DAG, so that items whose inputs
   // are ready are handed out first
   {
@@ -297,7 +376,10 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
     for (int64_t p = 0; p < P.npieces; p++) chunk_first[p + 1] += chunk_first[p];
     // forward: head(p) after the heads/chunks whose rows hit p; chunk after its head
     std::vector<int64_t> hd(P.npieces, 0), cd(P.nchunks, 0);
+    for (int64_t t = 0; t < P.nsub; t++)              // subtree items depend on nothing
+      for (int64_t q = P.st_tptr[t]; q < P.st_tptr[t + 1]; q++) hd[P.st_tgt[q]] = std::max<int64_t>(hd[P.st_tgt[q]], 1);
     for (int64_t p = 0; p < P.npieces; p++) {       // pieces are in topological order
+      if (piece_sub[p] >= 0) continue;
       for (int64_t t = P.hd_tptr[p]; t < P.hd_tptr[p + 1]; t++) {
         const int32_t q = P.hd_tgt[t];
         hd[q] = std::max(hd[q], hd[p] + 1);
@@ -311,7 +393,12 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
       }
     }
     std::vector<std::pair<int64_t, int32_t>> ord;
-    for (int64_t p = 0; p < P.npieces; p++) { ord.push_back({hd[p] * 2, (int32_t)(-1 - p)}); P.fwd_depth = std::max(P.fwd_depth, hd[p]); }
+    for (int64_t t = 0; t < P.nsub; t++) ord.push_back({0, (int32_t)(-1 - P.npieces - t)});
+    for (int64_t p = 0; p < P.npieces; p++) {
+      if (piece_sub[p] >= 0) continue;
+      ord.push_back({hd[p] * 2, (int32_t)(-1 - p)});
+      P.fwd_depth = std::max(P.fwd_depth, hd[p]);
+    }
     for (int64_t c = 0; c < P.nchunks; c++) ord.push_back({cd[c] * 2 + 1, (int32_t)c});
     std::stable_sort(ord.begin(), ord.end(), [](auto& a, auto& b) { return a.first < b.first; });
     for (auto& o : ord) P.fwd_items.push_back(o.second);
@@ -319,6 +406,7 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
     // after the heads of its chunk-0 targets
     std::vector<int64_t> bh(P.npieces, 0), bc(P.nchunks, 0);
     for (int64_t p = P.npieces - 1; p >= 0; p--) {
+      if (piece_sub[p] >= 0) continue;
       int64_t d = 0;
       for (int64_t t = P.hd_tptr[p]; t < P.hd_tptr[p + 1]; t++) d = std::max(d, bh[P.hd_tgt[t]] + 1);
       for (int64_t c = chunk_first[p]; c < chunk_first[p + 1]; c++) {
@@ -331,8 +419,15 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
       P.bwd_depth = std::max(P.bwd_depth, d);
     }
     ord.clear();
-    for (int64_t p = 0; p < P.npieces; p++) ord.push_back({bh[p] * 2 + 1, (int32_t)(-1 - p)});
+    for (int64_t p = 0; p < P.npieces; p++)
+      if (piece_sub[p] < 0) ord.push_back({bh[p] * 2 + 1, (int32_t)(-1 - p)});
     for (int64_t c = 0; c < P.nchunks; c++) ord.push_back({bc[c] * 2, (int32_t)c});
+    for (int64_t t = 0; t < P.nsub; t++) {
+      int64_t d = 0;
+      for (int64_t q = P.st_tptr[t]; q < P.st_tptr[t + 1]; q++) d = std::max(d, bh[P.st_tgt[q]] + 1);
+      ord.push_back({d * 2, (int32_t)(-1 - P.npieces - t)});
+      P.bwd_depth = std::max(P.bwd_depth, d);
+    }
     std::stable_sort(ord.begin(), ord.end(), [](auto& a, auto& b) { return a.first < b.first; });
     for (auto& o : ord) P.bwd_items.push_back(o.second);
   }

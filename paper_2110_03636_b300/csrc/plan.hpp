@@ -61,14 +61,16 @@ struct Plan {
   // solve DAG over column pieces of width <= solve_w. A piece's "head" applies
   // the inverse of its diagonal triangle and its first rc0 rows below ("chunk
   // 0"); the remaining rows form separate chunks of at most rc rows.
-  int32_t solve_w = 128, rc = 128, rc0 = 128;
+  int32_t solve_w = 128;
+  int32_t ent = 16384, ent0 = 8192;         // L entries per chunk item / per head's chunk 0
+  int32_t max_rows = 1024;                  // rows of any chunk (gathered-vector limit)
   int64_t npieces = 0, nchunks = 0;
   std::vector<int32_t> pc_first, pc_w, pc_nr, pc_ld; // piece: first column, width, rows from its first row, ld
   std::vector<int32_t> pc_c;                // the piece's first row/column inside its supernode
   std::vector<int32_t> pc_rc0;              // rows of the fused chunk 0
   std::vector<int64_t> pc_row;              // offset in sn_rows of the piece's first row
   std::vector<int64_t> pc_colbase;          // panel offset of (supernode row 0, piece column 0)
-  std::vector<int64_t> pc_inv;              // offset of the inverse of its triangle (ld = round4(pw))
+  std::vector<int64_t> pc_inv;              // offset of the packed inverse of its triangle
   std::vector<int64_t> pc_zoff;             // offset of its partial-sum slots
   std::vector<int32_t> pc_nchunk;           // separate chunks
   std::vector<int32_t> pc_need;             // heads + chunks whose rows hit the piece (forward)
@@ -77,14 +79,31 @@ struct Plan {
   std::vector<int32_t> ch_piece, ch_r0, ch_nr, ch_k;  // chunk: piece, first row (piece-local), rows, index
   std::vector<int64_t> ch_tptr;             // targets of each chunk (distinct pieces)
   std::vector<int32_t> ch_tgt;
-  std::vector<int32_t> fwd_items, bwd_items; // >= 0 chunk id, < 0 head of piece (-1 - p)
+  // small subtrees solved whole by one CTA: supernodes [st_first, st_last]
+  // (postorder ranges), their column range [st_clo, st_chi), and the pieces
+  // outside the subtree that their rows hit
+  int64_t nsub = 0;
+  std::vector<int32_t> st_first, st_last, st_clo, st_chi;
+  std::vector<int64_t> st_tptr;
+  std::vector<int32_t> st_tgt;
+  std::vector<int32_t> sn_piece;            // first piece of each supernode
+  std::vector<int32_t> fwd_items, bwd_items; // >= 0 chunk id; -1-p head of piece p (p < npieces);
+                                            // -1-npieces-t subtree t
   int64_t inv_total = 0;
   int64_t fwd_depth = 0, bwd_depth = 0;     // longest dependency chains of the sweeps
   int64_t z_total = 0;
   int32_t max_pw = 0;
 };
 
+// Rows of the packed inverse of a pw-wide triangle: column k holds rows
+// k..pw-1, padded to a multiple of 4.
+inline int64_t packed_inv_size(int64_t pw) {
+  int64_t t = 0;
+  for (int64_t k = 0; k < pw; k++) t += (pw - k + 3) & ~3;
+  return t;
+}
+
 int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const int64_t* Jp,
-               const int32_t* Ji, int32_t solve_w, int32_t rc, int32_t rc0, Plan& P);
+               const int32_t* Ji, int32_t solve_w, int32_t ent, int32_t ent0, Plan& P);
 
 }  // namespace kkt

@@ -21,7 +21,6 @@
 namespace kkt {
 
 constexpr int kSolveThreads = 256;
-constexpr int kAux = 512;
 
 // Static shared state; the tiles live in dynamic shared memory.
 struct SolveSmemHdr {
@@ -29,25 +28,76 @@ struct SolveSmemHdr {
   unsigned phase;
   int item;
   int flag;
+  // cycle counters of thread 0 (kept when a.instr != nullptr): dispatch,
+  // dependency waits, bulk-copy waits, whole items, grid barriers, items
+  long long c_disp, c_dep, c_mbar, c_item, c_bar, n_items;
   double dred[(kSolveThreads / 32) * 2];
   double bcast[2];
 };
 
 template <typename T>
 struct Tiles {
-  T* A;     // inverse of the piece triangle, or a chunk tile
+  T* A;     // packed inverse of a piece triangle, or a chunk tile
   T* B;     // chunk-0 tile of a head
   T* vec;   // sw
   T* vec2;  // sw
-  T* aux;   // kAux
-  int csA, csB;  // column strides of the chunk tiles
+  T* aux;   // max_rows + kSolveThreads
 };
 
-size_t solve_smem_bytes(size_t elem, int sw, int rc, int rc0) {
-  const size_t ldi = (size_t)((sw + 3) & ~3);
-  const size_t a = (size_t)sw * (ldi > (size_t)rc + 8 ? ldi : (size_t)rc + 8);
-  const size_t b = (size_t)sw * (size_t)(rc0 + 8);
-  return elem * (a + b + 2 * (size_t)sw + kAux) + 16;
+__host__ __device__ static size_t packed_inv(size_t pw) {
+  size_t t = 0;
+  for (size_t k = 0; k < pw; k++) t += (pw - k + 3) & ~(size_t)3;
+  return t;
+}
+// Shared memory: region A holds a head's packed inverse, region B the row
+// tile of a head's chunk 0 or of a chunk (both at most ent0 = ent entries).
+__host__ __device__ static size_t tileA(int sw, int /*ent*/) { return packed_inv((size_t)sw); }
+
+size_t solve_smem_bytes(size_t elem, int sw, int ent, int ent0, int max_rows) {
+  const size_t a = tileA(sw, ent);
+  const size_t e = (size_t)(ent > ent0 ? ent : ent0);
+  const size_t b = e + 8 * (size_t)sw;
+  return elem * (a + b + 2 * (size_t)sw + (size_t)max_rows + kSolveThreads) + 16;
+}
+
+// Offset of column k in a packed pw-wide inverse: sum over j < k of
+// round4(pw - j) = S(pw) - S(pw - k), S(x) = sum_{m=1..x} round4(m)
+// = x(x+1)/2 + 6 floor(x/4) + {0,3,5,6}[x mod 4].
+__device__ __forceinline__ int packed_S(int x) {
+  const int tail = (x & 3) == 0 ? 0 : ((x & 3) == 1 ? 3 : ((x & 3) == 2 ? 5 : 6));
+  return x * (x + 1) / 2 + 6 * (x >> 2) + tail;
+}
+__device__ __forceinline__ int packed_off(int pw, int k) { return packed_S(pw) - packed_S(pw - k); }
+
+// column stride of a staged tile of nrows rows (room for the 16-byte alignment slack)
+__device__ __forceinline__ int tile_cs(int nrows) { return ((nrows + 3) & ~3) + 8; }
+
+// out_i = sum_k tile[k*cs + d0 + i] * x[k] for i < nr, handed to emit(i, out_i);
+// the k range is split among thread groups when the rows are few
+template <typename T, typename F>
+__device__ void rows_matvec(const T* tile, int cs, int d0, int nr, int pw, const T* x, T* part, F emit) {
+  const int tid = threadIdx.x;
+  if (nr <= (int)blockDim.x) {
+    const int rr = (nr + 31) & ~31;
+    const int G = max(1, (int)blockDim.x / rr);
+    const int i = tid % rr, g = tid / rr;
+    T acc = T(0);
+    if (g < G && i < nr)
+      for (int k = g; k < pw; k += G) acc += tile[k * cs + d0 + i] * x[k];
+    part[tid] = acc;
+    __syncthreads();
+    if (tid < nr) {
+      T o = T(0);
+      for (int gg = 0; gg < G; gg++) o += part[gg * rr + tid];
+      emit(tid, o);
+    }
+  } else {
+    for (int i = tid; i < nr; i += blockDim.x) {
+      T acc = T(0);
+      for (int k = 0; k < pw; k++) acc += tile[k * cs + d0 + i] * x[k];
+      emit(i, acc);
+    }
+  }
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -92,6 +142,7 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 // copy is left in flight into this CTA's shared memory.
 template <typename T>
 __device__ bool mbar_wait(const SolveArgs<T>& a, SolveSmemHdr& h) {
+  const long long tw = clock64();
   const unsigned ph = h.phase;
   bool ok = mbar_test(&h.mbar, ph);
   if (!ok) {
@@ -106,7 +157,10 @@ __device__ bool mbar_wait(const SolveArgs<T>& a, SolveSmemHdr& h) {
     }
   }
   __syncthreads();
-  if (threadIdx.x == 0) h.phase ^= 1u;
+  if (threadIdx.x == 0) {
+    h.phase ^= 1u;
+    h.c_mbar += clock64() - tw;
+  }
   __syncthreads();
   return ok;
 }
@@ -115,8 +169,9 @@ __device__ bool mbar_wait(const SolveArgs<T>& a, SolveSmemHdr& h) {
 // [r0, r0 + nrows), into `tile` (column stride cs); 16-byte aligned by
 // starting at the supernode row rounded down to 4 (offset returned).
 template <typename T>
-__device__ int stage_cols(const SolveArgs<T>& a, int p, int r0, int nrows, T* tile, int cs, uint32_t& bytes_out,
+__device__ int stage_cols(const SolveArgs<T>& a, int p, int r0, int nrows, T* tile, uint32_t& bytes_out,
                           unsigned long long* mbar, bool issue) {
+  const int cs = tile_cs(nrows);
   const int ld = a.pc_ld[p], c = a.pc_c[p], pw = a.pc_w[p];
   const int R0 = c + r0;
   const int A0 = R0 & ~3;
@@ -135,58 +190,53 @@ template <typename T>
 __device__ bool fwd_head(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>& t, int p, int e) {
   const int tid = threadIdx.x;
   const int pw = a.pc_w[p], f = a.pc_first[p], rn = a.pc_rc0[p];
-  const int ldi = (pw + 3) & ~3;
-  int d0 = 0;
   if (tid < 32) {
     uint32_t b1 = 0;
     if (tid == 0) fence_proxy_async();
-    const uint32_t binv = (uint32_t)(pw * ldi * sizeof(T));
-    if (rn > 0) stage_cols(a, p, pw, rn, t.B, t.csB, b1, &h.mbar, false);
+    const uint32_t binv = (uint32_t)((a.pc_inv[p + 1] - a.pc_inv[p]) * sizeof(T));
+    if (rn > 0) stage_cols(a, p, pw, rn, t.B, b1, &h.mbar, false);
     if (tid == 0) mbar_expect_tx(&h.mbar, binv + b1);
     __syncwarp();
     if (tid == 0) bulk_g2s(t.A, a.Linv + a.pc_inv[p], binv, &h.mbar);
-    if (rn > 0) d0 = stage_cols(a, p, pw, rn, t.B, t.csB, b1, &h.mbar, true);
-    if (tid == 0) h.flag = wait_geq(&a.fwd_arrive[p], e * a.pc_need[p], a.st, a.spin);
+    if (rn > 0) stage_cols(a, p, pw, rn, t.B, b1, &h.mbar, true);
+    if (tid == 0) {
+      const long long t0 = clock64();
+      h.flag = wait_geq(&a.fwd_arrive[p], e * a.pc_need[p], a.st, a.spin);
+      h.c_dep += clock64() - t0;
+    }
   }
   __syncthreads();
   const bool dep = h.flag != 0;
   if (dep)
     for (int i = tid; i < pw; i += blockDim.x) t.vec[i] = ldcg(&a.v[f + i]);
   if (!mbar_wait(a, h) || !dep) return false;
-  d0 = (a.pc_c[p] + pw) & 3;
-  // y = T^-1 b (full rows of the inverse; its upper part is zero)
-  const int pr = (pw + 31) & ~31;
-  const int G = max(1, (int)blockDim.x / pr);
-  const int i = tid % pr, g = tid / pr;
-  T acc = T(0);
-  if (g < G && i < pw)
-    for (int k = g; k <= i; k += G) acc += t.A[i + k * ldi] * t.vec[k];
-  t.aux[tid] = acc;
-  __syncthreads();
-  if (tid < pw) {
-    T y = T(0);
-    for (int gg = 0; gg < G; gg++) y += t.aux[gg * pr + tid];
-    t.vec2[tid] = y;
-    a.v[f + tid] = y;
+  // y = T^-1 b with the packed inverse (column k holds rows k..pw-1); the
+  // k range of each row is split among G thread groups
+  {
+    const int pr = (pw + 31) & ~31;
+    const int G = max(1, (int)blockDim.x / pr);
+    const int i = tid % pr, g = tid / pr;
+    T acc = T(0);
+    if (g < G && i < pw)
+      for (int k = g; k <= i; k += G) acc += t.A[packed_off(pw, k) + i - k] * t.vec[k];
+    t.aux[tid] = acc;
+    __syncthreads();
+    if (tid < pw) {
+      T y = T(0);
+      for (int gg = 0; gg < G; gg++) y += t.aux[gg * pr + tid];
+      t.vec2[tid] = y;
+      a.v[f + tid] = y;
+    }
   }
   __threadfence();
   __syncthreads();
   if (tid == 0) st_release(&a.fwd_done[p], e);
   if (rn > 0) {
     // chunk 0: b[rows] -= L21(0:rn) y
-    const int rr = (rn + 31) & ~31;
-    const int G2 = max(1, (int)blockDim.x / rr);
-    const int i2 = tid % rr, g2 = tid / rr;
-    T s = T(0);
-    if (g2 < G2 && i2 < rn)
-      for (int k = g2; k < pw; k += G2) s += t.B[k * t.csB + d0 + i2] * t.vec2[k];
-    t.aux[tid] = s;
-    __syncthreads();
-    if (tid < rn) {
-      T o = T(0);
-      for (int gg = 0; gg < G2; gg++) o += t.aux[gg * rr + tid];
-      atomicAdd(&a.v[a.sn_rows[a.pc_row[p] + pw + tid]], -o);
-    }
+    const int d0 = (a.pc_c[p] + pw) & 3;
+    const int32_t* rows = a.sn_rows + a.pc_row[p] + pw;
+    T* v = a.v;
+    rows_matvec(t.B, tile_cs(rn), d0, rn, pw, t.vec2, t.aux, [&](int i, T o) { atomicAdd(&v[rows[i]], -o); });
     __threadfence();
     __syncthreads();
     if (tid == 0)
@@ -204,11 +254,15 @@ __device__ bool fwd_chunk(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>
   if (tid < 32) {
     uint32_t b = 0;
     if (tid == 0) fence_proxy_async();
-    stage_cols(a, p, r0, nr, t.A, t.csA, b, &h.mbar, false);
+    stage_cols(a, p, r0, nr, t.B, b, &h.mbar, false);
     if (tid == 0) mbar_expect_tx(&h.mbar, b);
     __syncwarp();
-    stage_cols(a, p, r0, nr, t.A, t.csA, b, &h.mbar, true);
-    if (tid == 0) h.flag = wait_geq(&a.fwd_done[p], e, a.st, a.spin);
+    stage_cols(a, p, r0, nr, t.B, b, &h.mbar, true);
+    if (tid == 0) {
+      const long long t0 = clock64();
+      h.flag = wait_geq(&a.fwd_done[p], e, a.st, a.spin);
+      h.c_dep += clock64() - t0;
+    }
   }
   __syncthreads();
   const bool dep = h.flag != 0;
@@ -216,19 +270,9 @@ __device__ bool fwd_chunk(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>
     for (int k = tid; k < pw; k += blockDim.x) t.vec[k] = ldcg(&a.v[f + k]);
   if (!mbar_wait(a, h) || !dep) return false;
   const int d0 = (a.pc_c[p] + r0) & 3;
-  const int rr = (nr + 31) & ~31;
-  const int G = max(1, (int)blockDim.x / rr);
-  const int i = tid % rr, g = tid / rr;
-  T acc = T(0);
-  if (g < G && i < nr)
-    for (int k = g; k < pw; k += G) acc += t.A[k * t.csA + d0 + i] * t.vec[k];
-  t.aux[tid] = acc;
-  __syncthreads();
-  if (tid < nr) {
-    T s = T(0);
-    for (int gg = 0; gg < G; gg++) s += t.aux[gg * rr + tid];
-    atomicAdd(&a.v[a.sn_rows[a.pc_row[p] + r0 + tid]], -s);
-  }
+  const int32_t* rows = a.sn_rows + a.pc_row[p] + r0;
+  T* v = a.v;
+  rows_matvec(t.B, tile_cs(nr), d0, nr, pw, t.vec, t.aux, [&](int i, T o) { atomicAdd(&v[rows[i]], -o); });
   __threadfence();
   __syncthreads();
   if (tid == 0)
@@ -246,15 +290,17 @@ __device__ bool bwd_chunk(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>
   if (tid < 32) {
     uint32_t b = 0;
     if (tid == 0) fence_proxy_async();
-    stage_cols(a, p, r0, nr, t.A, t.csA, b, &h.mbar, false);
+    stage_cols(a, p, r0, nr, t.B, b, &h.mbar, false);
     if (tid == 0) mbar_expect_tx(&h.mbar, b);
     __syncwarp();
-    stage_cols(a, p, r0, nr, t.A, t.csA, b, &h.mbar, true);
+    stage_cols(a, p, r0, nr, t.B, b, &h.mbar, true);
     if (tid == 0) {
+      const long long t0 = clock64();
       int ok = 1;
       for (int64_t q = a.ch_tptr[c]; q < a.ch_tptr[c + 1] && ok; q++)
         ok = wait_geq(&a.bwd_done[a.ch_tgt[q]], e, a.st, a.spin);
       h.flag = ok;
+      h.c_dep += clock64() - t0;
     }
   }
   __syncthreads();
@@ -263,11 +309,12 @@ __device__ bool bwd_chunk(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>
     for (int i = tid; i < nr; i += blockDim.x) t.aux[i] = ldcg(&a.v[a.sn_rows[a.pc_row[p] + r0 + i]]);
   if (!mbar_wait(a, h) || !dep) return false;
   const int d0 = (a.pc_c[p] + r0) & 3;
+  const int cs = tile_cs(nr);
   const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   T* z = a.zpart + a.pc_zoff[p] + (int64_t)a.ch_k[c] * pw;
   for (int k = warp; k < pw; k += nw) {
     T s = T(0);
-    for (int i = lane; i < nr; i += 32) s += t.A[k * t.csA + d0 + i] * t.aux[i];
+    for (int i = lane; i < nr; i += 32) s += t.B[k * cs + d0 + i] * t.aux[i];
     s = warp_sum(s);
     if (lane == 0) z[k] = s;
   }
@@ -281,21 +328,22 @@ template <typename T>
 __device__ bool bwd_head(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>& t, int p, int e) {
   const int tid = threadIdx.x;
   const int pw = a.pc_w[p], f = a.pc_first[p], rn = a.pc_rc0[p], nch = a.pc_nchunk[p];
-  const int ldi = (pw + 3) & ~3;
   if (tid < 32) {
     uint32_t b1 = 0;
     if (tid == 0) fence_proxy_async();
-    const uint32_t binv = (uint32_t)(pw * ldi * sizeof(T));
-    if (rn > 0) stage_cols(a, p, pw, rn, t.B, t.csB, b1, &h.mbar, false);
+    const uint32_t binv = (uint32_t)((a.pc_inv[p + 1] - a.pc_inv[p]) * sizeof(T));
+    if (rn > 0) stage_cols(a, p, pw, rn, t.B, b1, &h.mbar, false);
     if (tid == 0) mbar_expect_tx(&h.mbar, binv + b1);
     __syncwarp();
     if (tid == 0) bulk_g2s(t.A, a.Linv + a.pc_inv[p], binv, &h.mbar);
-    if (rn > 0) stage_cols(a, p, pw, rn, t.B, t.csB, b1, &h.mbar, true);
+    if (rn > 0) stage_cols(a, p, pw, rn, t.B, b1, &h.mbar, true);
     if (tid == 0) {
+      const long long t0 = clock64();
       int ok = wait_geq(&a.bwd_arrive[p], e * nch, a.st, a.spin);
       for (int64_t q = a.hd_tptr[p]; q < a.hd_tptr[p + 1] && ok; q++)
         ok = wait_geq(&a.bwd_done[a.hd_tgt[q]], e, a.st, a.spin);
       h.flag = ok;
+      h.c_dep += clock64() - t0;
     }
   }
   __syncthreads();
@@ -313,18 +361,20 @@ __device__ bool bwd_head(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>&
   const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   if (rn > 0) {
     const int d0 = (a.pc_c[p] + pw) & 3;
+    const int cs = tile_cs(rn);
     for (int k = warp; k < pw; k += nw) {
       T s = T(0);
-      for (int i = lane; i < rn; i += 32) s += t.B[k * t.csB + d0 + i] * t.aux[i];
+      for (int i = lane; i < rn; i += 32) s += t.B[k * cs + d0 + i] * t.aux[i];
       s = warp_sum(s);
       if (lane == 0) t.vec[k] -= s;
     }
     __syncthreads();
   }
-  // x = T^-T t: x_k = sum_i Tinv[i, k] t_i (Tinv lower, zero above the diagonal)
+  // x = T^-T t: x_k = sum_{i >= k} Tinv[i, k] t_i (packed columns)
   for (int k = warp; k < pw; k += nw) {
+    const int off = packed_off(pw, k);
     T s = T(0);
-    for (int i = k + lane; i < pw; i += 32) s += t.A[i + k * ldi] * t.vec[i];
+    for (int i = k + lane; i < pw; i += 32) s += t.A[off + i - k] * t.vec[i];
     s = warp_sum(s);
     if (lane == 0) t.vec2[k] = s;
   }
@@ -336,10 +386,107 @@ __device__ bool bwd_head(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>&
   return true;
 }
 
+
+// ------------------------------------------------------------ small subtrees
+// A subtree whose columns [clo, chi) fit in shared memory is solved by one
+// CTA: its descendants are all inside it, so in the forward sweep it depends
+// on nothing and in the backward sweep only on the pieces owning its rows
+// outside [clo, chi).
+template <typename T>
+__device__ bool fwd_subtree(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>& t, int st) {
+  const int tid = threadIdx.x;
+  const int clo = a.st_clo[st], chi = a.st_chi[st];
+  T* xs = t.vec2;
+  for (int i = tid; i < chi - clo; i += blockDim.x) xs[i] = ldcg(&a.v[clo + i]);
+  __syncthreads();
+  for (int s = a.st_first[st]; s <= a.st_last[st]; s++) {
+    const int w = a.sw_[s], nr = a.snr[s], ld = a.sld[s], f = a.sfirst[s] - clo;
+    const T* P = a.L + a.poff[s];
+    const T* Inv = a.Linv + a.pc_inv[a.sn_piece[s]];
+    if (tid < w) {
+      T y = T(0);
+      int off = 0;
+      for (int k = 0; k <= tid; k++) {
+        y += Inv[off + tid - k] * xs[f + k];
+        off += (w - k + 3) & ~3;
+      }
+      t.vec[tid] = y;
+    }
+    __syncthreads();
+    if (tid < w) xs[f + tid] = t.vec[tid];
+    const int32_t* rows = a.sn_rows + a.srow[s];
+    for (int r = w + tid; r < nr; r += blockDim.x) {
+      T o = T(0);
+      for (int k = 0; k < w; k++) o += P[r + (int64_t)k * ld] * t.vec[k];
+      const int row = rows[r];
+      if (row < chi) xs[row - clo] -= o;
+      else atomicAdd(&a.v[row], -o);
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < chi - clo; i += blockDim.x) a.v[clo + i] = xs[i];
+  __threadfence();
+  __syncthreads();
+  if (tid == 0)
+    for (int64_t q = a.st_tptr[st]; q < a.st_tptr[st + 1]; q++) atomicAdd(&a.fwd_arrive[a.st_tgt[q]], 1);
+  return true;
+}
+
+template <typename T>
+__device__ bool bwd_subtree(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>& t, int st, int e) {
+  const int tid = threadIdx.x;
+  const int clo = a.st_clo[st], chi = a.st_chi[st];
+  if (tid == 0) {
+    const long long t0 = clock64();
+    int ok = 1;
+    for (int64_t q = a.st_tptr[st]; q < a.st_tptr[st + 1] && ok; q++)
+      ok = wait_geq(&a.bwd_done[a.st_tgt[q]], e, a.st, a.spin);
+    h.flag = ok;
+    h.c_dep += clock64() - t0;
+  }
+  __syncthreads();
+  if (!h.flag) return false;
+  T* xs = t.vec2;
+  for (int i = tid; i < chi - clo; i += blockDim.x) xs[i] = ldcg(&a.v[clo + i]);
+  __syncthreads();
+  const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (int s = a.st_last[st]; s >= a.st_first[st]; s--) {
+    const int w = a.sw_[s], nr = a.snr[s], ld = a.sld[s], f = a.sfirst[s] - clo;
+    const T* P = a.L + a.poff[s];
+    const T* Inv = a.Linv + a.pc_inv[a.sn_piece[s]];
+    const int32_t* rows = a.sn_rows + a.srow[s];
+    for (int k = warp; k < w; k += nw) {
+      T acc = T(0);
+      for (int r = w + lane; r < nr; r += 32) {
+        const int row = rows[r];
+        const T x = row < chi ? xs[row - clo] : ldcg(&a.v[row]);
+        acc += P[r + (int64_t)k * ld] * x;
+      }
+      acc = warp_sum(acc);
+      if (lane == 0) t.vec[k] = xs[f + k] - acc;
+    }
+    __syncthreads();
+    for (int k = warp; k < w; k += nw) {
+      int off = 0;
+      for (int j = 0; j < k; j++) off += (w - j + 3) & ~3;
+      T acc = T(0);
+      for (int i = k + lane; i < w; i += 32) acc += Inv[off + i - k] * t.vec[i];
+      acc = warp_sum(acc);
+      if (lane == 0) xs[f + k] = acc;
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < chi - clo; i += blockDim.x) a.v[clo + i] = xs[i];
+  __threadfence();
+  __syncthreads();
+  return true;
+}
+
 template <typename T>
 __device__ bool grid_barrier(const SolveArgs<T>& a, SolveSmemHdr& h) {
   __syncthreads();
   if (threadIdx.x == 0) {
+    const long long tb = clock64();
     int ok = 1;
     const int gen = ld_acquire(&a.bar[1]);
     __threadfence();
@@ -352,6 +499,7 @@ __device__ bool grid_barrier(const SolveArgs<T>& a, SolveSmemHdr& h) {
     }
     if (ld_acquire(&a.st->abort)) ok = 0;
     h.flag = ok;
+    h.c_bar += clock64() - tb;
   }
   __syncthreads();
   return h.flag != 0;
@@ -397,20 +545,52 @@ __device__ bool sweep(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>& t,
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(&a.disp[(seq + 1) % 3], 0);
   const int32_t* items = FWD ? a.fwd_items : a.bwd_items;
   for (;;) {
-    if (threadIdx.x == 0) h.item = atomicAdd(&a.disp[seq % 3], 1);
+    long long td = 0;
+    if (threadIdx.x == 0) {
+      td = clock64();
+      h.item = atomicAdd(&a.disp[seq % 3], 1);
+    }
     __syncthreads();
     const int it = h.item;
     __syncthreads();
+    if (threadIdx.x == 0) {
+      const long long now = clock64();
+      h.c_disp += now - td;
+      td = now;
+    }
     if (it >= a.nitems) return true;
     const int code = items[it];
     bool ok;
-    if (FWD) ok = code < 0 ? fwd_head(a, h, t, -1 - code, e) : fwd_chunk(a, h, t, code, e);
-    else ok = code < 0 ? bwd_head(a, h, t, -1 - code, e) : bwd_chunk(a, h, t, code, e);
+    if (code < -(int)a.npieces) {
+      const int st = -1 - (int)a.npieces - code;
+      ok = FWD ? fwd_subtree(a, h, t, st) : bwd_subtree(a, h, t, st, e);
+    } else if (FWD) {
+      ok = code < 0 ? fwd_head(a, h, t, -1 - code, e) : fwd_chunk(a, h, t, code, e);
+    } else {
+      ok = code < 0 ? bwd_head(a, h, t, -1 - code, e) : bwd_chunk(a, h, t, code, e);
+    }
+    if (threadIdx.x == 0) {
+      h.c_item += clock64() - td;
+      h.n_items++;
+    }
     if (!ok) return false;
   }
 }
 
 // one H^-1 application on a.v (forward then backward sweep)
+template <typename T>
+__device__ void flush_counters(const SolveArgs<T>& a, SolveSmemHdr& h) {
+  if (a.instr && threadIdx.x == 0) {
+    atomicAdd(&a.instr[0], (unsigned long long)h.c_disp);
+    atomicAdd(&a.instr[1], (unsigned long long)h.c_dep);
+    atomicAdd(&a.instr[2], (unsigned long long)h.c_mbar);
+    atomicAdd(&a.instr[3], (unsigned long long)h.c_item);
+    atomicAdd(&a.instr[4], (unsigned long long)h.c_bar);
+    atomicAdd(&a.instr[5], (unsigned long long)h.n_items);
+    atomicAdd(&a.instr[6], 1ull);
+  }
+}
+
 template <typename T>
 __device__ bool hsolve(const SolveArgs<T>& a, SolveSmemHdr& sm, const Tiles<T>& t, int& seq, int& e) {
   e++;
@@ -421,24 +601,19 @@ __device__ bool hsolve(const SolveArgs<T>& a, SolveSmemHdr& sm, const Tiles<T>& 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kSolveThreads, 1) k_cg(SolveArgs<T> a) {
+__global__ void __launch_bounds__(kSolveThreads, 2) k_cg(SolveArgs<T> a) {
   __shared__ SolveSmemHdr sm;
   extern __shared__ __align__(16) unsigned char dsm[];
   Tiles<T> tl;
-  {
-    const int ldi = (a.sw + 3) & ~3;
-    const int csA = a.rc + 8;
-    tl.csA = csA;
-    tl.csB = a.rc0 + 8;
-    tl.A = (T*)dsm;
-    tl.B = tl.A + (size_t)a.sw * (ldi > csA ? ldi : csA);
-    tl.vec = tl.B + (size_t)a.sw * tl.csB;
-    tl.vec2 = tl.vec + a.sw;
-    tl.aux = tl.vec2 + a.sw;
-  }
+  tl.A = (T*)dsm;
+  tl.B = tl.A + tileA(a.sw, a.ent);
+  tl.vec = tl.B + (size_t)(a.ent > a.ent0 ? a.ent : a.ent0) + 8 * (size_t)a.sw;
+  tl.vec2 = tl.vec + a.sw;
+  tl.aux = tl.vec2 + a.sw;
   if (threadIdx.x == 0) {
     mbar_init(&sm.mbar);
     sm.phase = 0;
+    sm.c_disp = sm.c_dep = sm.c_mbar = sm.c_item = sm.c_bar = sm.n_items = 0;
   }
   __syncthreads();
   const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -463,6 +638,7 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_cg(SolveArgs<T> a) {
       const int32_t o = a.perm[k];
       a.ox[o] = a.accumulate ? a.ox[o] + val : val;
     }
+    flush_counters(a, sm);
     return;
   }
   // b_S = J w - r_y
@@ -564,14 +740,15 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_cg(SolveArgs<T> a) {
     a.st->cg_status = status;
     a.st->breakdown = brk;
   }
+  flush_counters(a, sm);
 }
 
 template <typename T>
-int solve_grid_size(int device, int sw, int rc, int rc0) {
+int solve_grid_size(int device, int sw, int ent, int ent0, int max_rows) {
   int sms = 0, per = 0, maxsm = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
-  const size_t smem = solve_smem_bytes(sizeof(T), sw, rc, rc0);
+  const size_t smem = solve_smem_bytes(sizeof(T), sw, ent, ent0, max_rows);
   if (smem > (size_t)maxsm) return 0;
   if (cudaFuncSetAttribute(k_cg<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
     cudaGetLastError();
@@ -586,12 +763,12 @@ template <typename T>
 cudaError_t launch_solve(const SolveArgs<T>& a, int grid, cudaStream_t st) {
   SolveArgs<T> args = a;
   void* params[] = {&args};
-  const size_t smem = solve_smem_bytes(sizeof(T), a.sw, a.rc, a.rc0);
+  const size_t smem = solve_smem_bytes(sizeof(T), a.sw, a.ent, a.ent0, a.max_rows);
   return cudaLaunchCooperativeKernel((const void*)k_cg<T>, dim3(grid), dim3(kSolveThreads), params, smem, st);
 }
 
-template int solve_grid_size<double>(int, int, int, int);
-template int solve_grid_size<float>(int, int, int, int);
+template int solve_grid_size<double>(int, int, int, int, int);
+template int solve_grid_size<float>(int, int, int, int, int);
 template cudaError_t launch_solve<double>(const SolveArgs<double>&, int, cudaStream_t);
 template cudaError_t launch_solve<float>(const SolveArgs<float>&, int, cudaStream_t);
 
