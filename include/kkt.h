@@ -83,13 +83,20 @@ typedef struct kkt_options {
                           launches; for measurement runs only) */
   int32_t nd_leaf;     /* nested dissection stops at components of at most this many
                           vertices (ordered naturally); default 64 */
+  int32_t tensor_cores;/* KKT_MIXED: 1 = fronts with >= 128 update rows take the SYRK on the
+                          tcgen05 tensor cores (operands split into three TF32 parts, six
+                          partial products, FP32 accumulation in tensor memory);
+                          0 (default) = FP32 FMA units only, which is faster on the
+                          shallow fronts of a 2-D grid and more accurate (the tensor
+                          core's FP32 accumulation does not round to nearest) */
+  int32_t pad2_;
 } kkt_options;
 
 /* Kernel kinds reported by kkt_get_profile. */
 enum {
   KKT_K_ASSEMBLE = 0, KKT_K_POTRF = 1, KKT_K_TRSM = 2, KKT_K_PANEL_UPDATE = 3, KKT_K_SYRK = 4,
   KKT_K_EXTEND_ADD = 5, KKT_K_ZERO_U = 6, KKT_K_CG = 7, KKT_K_RESIDUAL = 8, KKT_K_TRI_INV = 9,
-  KKT_K_COUNT = 10
+  KKT_K_SYRK_TC = 10, KKT_K_COUNT = 12
 };
 
 /* Result of the last kkt_solve on a handle. */

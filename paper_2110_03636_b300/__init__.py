@@ -35,7 +35,8 @@ class kkt_options(C.Structure):
                 ("precision", C.c_int32), ("ordering", C.c_int32), ("relax_small", C.c_int32),
                 ("relax_num", C.c_int32), ("relax_den", C.c_int32), ("relax_wmax", C.c_int32),
                 ("solve_w", C.c_int32), ("device", C.c_int32), ("debug_stall_piece", C.c_int32),
-                ("spin_cycles", C.c_int64), ("profile", C.c_int32), ("nd_leaf", C.c_int32)]
+                ("spin_cycles", C.c_int64), ("profile", C.c_int32), ("nd_leaf", C.c_int32),
+                ("tensor_cores", C.c_int32), ("pad2_", C.c_int32)]
 
 
 class kkt_info(C.Structure):
@@ -88,7 +89,7 @@ EXPORTED = ("kkt_default_options", "kkt_analyse", "kkt_analyse_host", "kkt_facto
             "kkt_get_factor_panels", "kkt_get_profile", "kkt_get_solve_counters", "kkt_residual_noalloc",
             "kkt_destroy", "kkt_status_string")
 KERNEL_KINDS = ("assemble", "potrf", "trsm", "panel_update", "syrk", "extend_add", "zero_u", "cg_persistent",
-                "residual", "tri_inv")
+                "residual", "tri_inv", "syrk_tc")
 
 
 def _check(fn, code):
@@ -212,8 +213,8 @@ def kkt_get_factor_panels(h):
 
 def kkt_get_profile(h, reset=False):
     """{kernel kind: (ms, launches)} accumulated by a handle made with profile=1."""
-    ms = np.zeros(10)
-    n = np.zeros(10, np.int64)
+    ms = np.zeros(12)
+    n = np.zeros(12, np.int64)
     _check("kkt_get_profile", _lib.kkt_get_profile(h, ms.ctypes.data, n.ctypes.data, int(bool(reset))))
     return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_KINDS)}
 

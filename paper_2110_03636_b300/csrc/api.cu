@@ -60,7 +60,7 @@ struct kkt_handle_s {
   // pattern / plan on the device
   int32_t *sfirst, *sw, *snr, *sld, *sparent, *rel, *sn_rows, *perm;
   int64_t *srow, *poff, *uoff;
-  int4 *it_potrf, *it_trsm, *it_pupd, *it_syrk, *it_eadd, *it_zero;
+  int4 *it_potrf, *it_trsm, *it_pupd, *it_syrk, *it_eadd, *it_zero, *it_syrk_tc;
   int64_t *slot_pos, *src_ptr;
   int32_t *srcA, *srcB;
   int32_t *Jcol_perm, *JT_row, *JT_vidx, *Hs_col, *Hs_vidx, *JTo_row, *JTo_vidx, *J_colidx;
@@ -128,6 +128,7 @@ void kkt_default_options(kkt_options* o) {
   o->spin_cycles = 0;
   o->profile = 0;
   o->nd_leaf = 64;
+  o->tensor_cores = 0;
 }
 
 const char* kkt_status_string(kkt_status s) {
@@ -188,7 +189,10 @@ static kkt_status analyse_host(int64_t n, int64_t m, const int64_t* Hp, const in
   const bool f64o = o.precision == KKT_FP64;
   const int sw = o.solve_w > 0 ? o.solve_w : (f64o ? 64 : 128);
   const int ent = f64o ? 8192 : 16384;
-  if (build_plan(h->S, Hp, Hi, Jp, Ji, sw, ent, ent, h->P) != 0) { delete h; return KKT_ERR_INVALID; }
+  if (build_plan(h->S, Hp, Hi, Jp, Ji, sw, ent, ent, !f64o && o.tensor_cores, h->P) != 0) {
+    delete h;
+    return KKT_ERR_INVALID;
+  }
   if (o.debug_stall_piece >= 0 && o.debug_stall_piece < h->P.npieces) h->P.pc_need[o.debug_stall_piece] += 1;
   h->nnzH = Hp[n];
   h->nnzJ = Jp[m];
@@ -232,7 +236,7 @@ kkt_status kkt_analyse(int64_t n, int64_t m, const int64_t* Hp, const int32_t* H
   h->srow = A.upload(P.srow); h->poff = A.upload(P.poff); h->uoff = A.upload(P.uoff);
   h->it_potrf = as_int4(P.it_potrf); h->it_zero = as_int4(P.it_zero);
   h->it_trsm = as_int4(P.it_trsm); h->it_pupd = as_int4(P.it_pupd);
-  h->it_syrk = as_int4(P.it_syrk); h->it_eadd = as_int4(P.it_eadd);
+  h->it_syrk = as_int4(P.it_syrk); h->it_eadd = as_int4(P.it_eadd); h->it_syrk_tc = as_int4(P.it_syrk_tc);
   h->slot_pos = A.upload(P.slot_pos); h->src_ptr = A.upload(P.src_ptr);
   h->srcA = A.upload(P.srcA); h->srcB = A.upload(P.srcB);
   h->Jcol_perm = A.upload(P.Jcol_perm); h->JT_ptr = A.upload(P.JT_ptr);
@@ -314,7 +318,7 @@ static cudaError_t factor_launches(kkt_handle h, cudaStream_t st, Prof* prof) {
   a.L = (T*)h->L; a.U = (T*)h->U; a.st = h->dst;
   FacLists fl;
   fl.it_potrf = h->it_potrf; fl.it_trsm = h->it_trsm; fl.it_pupd = h->it_pupd;
-  fl.it_syrk = h->it_syrk; fl.it_eadd = h->it_eadd; fl.it_zero = h->it_zero;
+  fl.it_syrk = h->it_syrk; fl.it_eadd = h->it_eadd; fl.it_zero = h->it_zero; fl.it_syrk_tc = h->it_syrk_tc;
   fl.slot_pos = h->slot_pos; fl.src_ptr = h->src_ptr; fl.srcA = h->srcA; fl.srcB = h->srcB;
   fl.nslot = (int64_t)h->P.slot_pos.size();
   fl.panel_total = h->P.panel_total; fl.u_total = h->P.u_total;
@@ -374,6 +378,7 @@ static kkt_status factor_common(kkt_handle h, double delta, double gamma, cudaSt
   s = h->opt.precision == KKT_FP64 ? factor_impl<double>(h, st) : factor_impl<float>(h, st);
   if (s) return s;
   if ((s = read_status(h, st))) return s;
+  if (h->hst->abort) return KKT_ERR_TIMEOUT;
   if (h->hst->fail_col != INT_MAX) return KKT_ERR_NOT_SPD;
   h->factored = true;
   return KKT_OK;
@@ -574,6 +579,7 @@ kkt_status kkt_get_symbolic(kkt_handle h, int32_t* amd, int32_t* perm, int32_t* 
 
 kkt_status kkt_get_profile(kkt_handle h, double* ms, int64_t* launches, int32_t reset) {
   if (!h) return KKT_ERR_INVALID;
+  static_assert(KKT_K_SYRK_TC == KKT_K_SYRK_TC_PROF, "profile slots");
   for (int k = 0; k < KKT_K_COUNT; k++) {
     if (ms) ms[k] = h->prof.ms[k];
     if (launches) launches[k] = h->prof.n[k];

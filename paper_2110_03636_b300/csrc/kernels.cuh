@@ -22,16 +22,17 @@ struct FacArgs {
 
 // Optional per-launch timing (profile mode): events around each launch,
 // elapsed time accumulated per kernel kind.
+constexpr int KKT_K_SYRK_TC_PROF = 10;   // profile slot of the tensor-core SYRK
 struct Prof {
   cudaEvent_t a = nullptr, b = nullptr;
-  double ms[10] = {0};
-  long long n[10] = {0};
+  double ms[12] = {0};
+  long long n[12] = {0};
 };
 cudaError_t prof_begin(Prof* pr, cudaStream_t st);
 cudaError_t prof_end(Prof* pr, int kind, cudaStream_t st);
 
 struct FacLists {
-  const int4 *it_potrf, *it_trsm, *it_pupd, *it_syrk, *it_eadd, *it_zero;
+  const int4 *it_potrf, *it_trsm, *it_pupd, *it_syrk, *it_eadd, *it_zero, *it_syrk_tc;
   const int64_t *slot_pos, *src_ptr;
   const int32_t *srcA, *srcB;
   int64_t nslot, panel_total, u_total;

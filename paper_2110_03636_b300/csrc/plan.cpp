@@ -8,7 +8,7 @@ namespace kkt {
 static inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const int64_t* Jp,
-               const int32_t* Ji, int32_t solve_w, int32_t ent, int32_t ent0, Plan& P) {
+               const int32_t* Ji, int32_t solve_w, int32_t ent, int32_t ent0, bool tc_syrk, Plan& P) {
   P = Plan();
   const int64_t n = S.n, m = S.m, ns = S.ns;
   P.n = n; P.m = m; P.ns = ns;
@@ -143,14 +143,18 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
       const int64_t c1 = (int64_t)P.it_pupd.size() / 4 - o1;
       if (c1) P.launches.push_back({2, kb, o1, c1});
     }
-    const int64_t o2 = (int64_t)P.it_syrk.size() / 4;
+    const int64_t o2 = (int64_t)P.it_syrk.size() / 4, o6 = (int64_t)P.it_syrk_tc.size() / 4;
     for (int32_t s : F) {
       const int64_t rb = P.snr[s] - P.sw[s];
-      const int64_t nt = cdiv(rb, kST);
+      const bool tcs = tc_syrk && rb >= kTcMinRows;
+      const int64_t tile = tcs ? 128 : kST;
+      const int64_t nt = cdiv(rb, tile);
+      auto& list = tcs ? P.it_syrk_tc : P.it_syrk;
       for (int64_t ti = 0; ti < nt; ti++)
-        for (int64_t tj = 0; tj <= ti; tj++) P.it_syrk.insert(P.it_syrk.end(), {s, (int32_t)ti, (int32_t)tj, 0});
+        for (int64_t tj = 0; tj <= ti; tj++) list.insert(list.end(), {s, (int32_t)ti, (int32_t)tj, 0});
     }
-    const int64_t c2 = (int64_t)P.it_syrk.size() / 4 - o2;
+    const int64_t c2 = (int64_t)P.it_syrk.size() / 4 - o2, c6 = (int64_t)P.it_syrk_tc.size() / 4 - o6;
+    if (c6) P.launches.push_back({6, 0, o6, c6});
     if (c2) P.launches.push_back({3, 0, o2, c2});
   }
   // ---------------------------------------------------------- assembly map

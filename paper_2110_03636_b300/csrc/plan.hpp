@@ -18,7 +18,7 @@ constexpr int kEC = 32;      // columns per extend-add item
 
 struct Launch {              // one batched kernel launch of the factorization
   int32_t kind;              // 0 potrf (diagonal tile), 1 trsm, 2 in-panel update, 3 syrk,
-                             // 4 extend-add, 5 zero update matrices
+                             // 4 extend-add, 5 zero update matrices, 6 tensor-core syrk
   int32_t kb;                // column block (kinds 0-2)
   int64_t off, cnt;          // range in the item array of that kind
 };
@@ -40,7 +40,8 @@ struct Plan {
   std::vector<int32_t> it_potrf;            // (s) fronts whose column block kb is factored
   std::vector<int32_t> it_trsm;             // (s, row tile) pairs
   std::vector<int32_t> it_pupd;             // (s, row tile, col tile) triples
-  std::vector<int32_t> it_syrk;             // (s, ti, tj) triples
+  std::vector<int32_t> it_syrk;             // (s, ti, tj) triples, 64 x 64 tiles
+  std::vector<int32_t> it_syrk_tc;          // (s, ti, tj), 128 x 128 tensor-core tiles
   std::vector<int32_t> it_eadd;             // (child s, col tile) pairs, at the parent's level
   std::vector<int32_t> it_zero;             // (s, chunk) update matrices cleared at s's level
   std::vector<Launch> launches;
@@ -103,7 +104,9 @@ inline int64_t packed_inv_size(int64_t pw) {
   return t;
 }
 
+// tc_syrk: fronts with rb >= kTcMinRows get 128 x 128 tensor-core SYRK tiles
+constexpr int kTcMinRows = 128;
 int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const int64_t* Jp,
-               const int32_t* Ji, int32_t solve_w, int32_t ent, int32_t ent0, Plan& P);
+               const int32_t* Ji, int32_t solve_w, int32_t ent, int32_t ent0, bool tc_syrk, Plan& P);
 
 }  // namespace kkt

@@ -91,6 +91,23 @@ def test_factor_panels_match_oracle_cholesky(seed):
     assert worst <= 1e-12 * scale
 
 
+@pytest.mark.parametrize("name", ["grid2d_n20k", "grid2d_n2000"])
+def test_tensor_core_syrk_matches_fma_syrk(name):
+    """The FP32 factor with the tcgen05 split-TF32 SYRK equals the FP32 FMA one
+    to FP32 rounding, and both solves reach RR <= 1e-8."""
+    sys = W.make_config(name)
+    outs = []
+    for tcs in (1, 0):
+        s = K.KKTSolver(sys.n, sys.m, sys.H_colptr, sys.H_rowidx, sys.J_rowptr, sys.J_colidx,
+                        precision="mixed", ordering="nd", tensor_cores=tcs)
+        s.factor(cu(sys.H_vals), cu(sys.J_vals), sys.delta, sys.gamma)
+        outs.append(s.panels())
+        s.solve(cu(sys.r_x), cu(sys.r_y))
+        assert s.info.rr <= 1e-8
+    a, b = outs
+    assert np.abs(a - b).max() <= 1e-4 * np.abs(b).max()
+
+
 def test_hsolve_matches_oracle():
     sys = W.make_config("grid2d_n2000")
     s = K.KKTSolver(sys.n, sys.m, sys.H_colptr, sys.H_rowidx, sys.J_rowptr, sys.J_colidx)
