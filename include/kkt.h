@@ -89,7 +89,11 @@ typedef struct kkt_options {
                           0 (default) = FP32 FMA units only, which is faster on the
                           shallow fronts of a 2-D grid and more accurate (the tensor
                           core's FP32 accumulation does not round to nearest) */
-  int32_t pad2_;
+  int32_t solve_ctas;  /* resident solve-kernel CTAs per SM, 2..4 (0 = 2); the grid is this
+                          many per SM or fewer if shared memory does not allow it */
+  int32_t solve_ent;   /* L entries staged per triangular-solve work item, 2048..32768
+                          (0 = 16384 for KKT_MIXED, 8192 for KKT_FP64) */
+  int32_t pad3_;
 } kkt_options;
 
 /* Kernel kinds reported by kkt_get_profile. */
@@ -211,14 +215,18 @@ kkt_status kkt_get_symbolic(kkt_handle h, int32_t* amd, int32_t* perm, int32_t* 
 kkt_status kkt_get_factor_panels(kkt_handle h, double* panels);
 
 /* Accumulated device time (ms) and launch count per kernel kind since the
- * last reset, for handles created with opt.profile = 1 (host arrays of
- * KKT_K_COUNT entries). reset != 0 clears the counters after reading. */
+ * last reset (host arrays of KKT_K_COUNT entries). Every kind is timed for
+ * handles created with opt.profile = 1; otherwise only KKT_K_CG is (one
+ * event pair around each solve pass, at no cost to the pass). reset != 0
+ * clears the counters after reading. */
 kkt_status kkt_get_profile(kkt_handle h, double* ms, int64_t* launches, int32_t reset);
 
 /* Cycle counters of the persistent solve kernel summed over its CTAs (thread
- * 0 of each), for handles created with opt.profile = 1; host uint64_t[8]:
+ * 0 of each), for handles created with opt.profile = 1; host uint64_t[16]:
  * [0] item dispatch, [1] dependency waits, [2] bulk-copy waits, [3] whole
- * items, [4] grid barriers, [5] items processed, [6] CTA-launches. */
+ * items, [4] grid barriers, [5] items processed, [6] CTA-launches,
+ * [7]/[8] cycles/count of subtree items, [9]/[10] of piece heads,
+ * [11]/[12] of row chunks, [13..15] zero. */
 kkt_status kkt_get_solve_counters(kkt_handle h, uint64_t* out, int32_t reset);
 
 kkt_status kkt_destroy(kkt_handle h);
@@ -258,6 +266,70 @@ kkt_status kkt_residual_noalloc(int64_t n, int64_t m, const int64_t* H_colptr, c
                                 double* norms, void* stream);
 
 const char* kkt_status_string(kkt_status s);
+
+/* ------------------------------------------------------------------------
+ * The 4x4 form (Sec. 3, eq. linsys4x4):
+ *
+ *   [ H + D_x   0     J^T   J_d^T ] [dx ]   [r~_x]
+ *   [ 0         D_s   0     -I    ] [ds ]   [r_s ]
+ *   [ J         0     0     0     ] [dy ] = [r_y ]
+ *   [ J_d       -I    0     0     ] [dyd]   [r_yd]
+ *
+ * reduced to the 2x2 form by eliminating ds = J_d dx - r_yd and
+ * dy_d = D_s ds - r_s (Sec. 3, eq. linsys2x2): H~ = H + D_x + J_d^T D_s J_d,
+ * r_x = r~_x + J_d^T (D_s r_yd + r_s). The 2x2 system is then solved as
+ * above (delta and gamma act on H~) and ds, dy_d are recovered from dx.
+ * Shapes: H n_x x n_x (lower CSC, as H~ above; the diagonal may be absent),
+ * J m_c x n_x and J_d m_d x n_x (CSR, columns strictly ascending in a row).
+ * ------------------------------------------------------------------------ */
+typedef struct kkt_handle4_s* kkt_handle4;
+
+/* Pattern of H~ = pat(H) U pat(J_d^T J_d) U diag, then kkt_analyse on it.
+ *   H_colptr host int64[n_x+1], H_rowidx host int32[H_colptr[n_x]]
+ *   J_rowptr host int64[m_c+1], J_colidx host int32[J_rowptr[m_c]]
+ *   Jd_rowptr host int64[m_d+1], Jd_colidx host int32[Jd_rowptr[m_d]]
+ * Errors: KKT_ERR_INVALID (bad pattern), KKT_ERR_OOM, KKT_ERR_CUDA. */
+kkt_status kkt_analyse_4x4(int64_t n_x, int64_t m_c, int64_t m_d, const int64_t* H_colptr,
+                           const int32_t* H_rowidx, const int64_t* J_rowptr, const int32_t* J_colidx,
+                           const int64_t* Jd_rowptr, const int32_t* Jd_colidx, const kkt_options* opt,
+                           kkt_handle4* out);
+
+/* Host-only variant (no CUDA call; the inner handle is a kkt_analyse_host
+ * handle): for the pattern and the symbolic analysis. */
+kkt_status kkt_analyse_4x4_host(int64_t n_x, int64_t m_c, int64_t m_d, const int64_t* H_colptr,
+                                const int32_t* H_rowidx, const int64_t* J_rowptr, const int32_t* J_colidx,
+                                const int64_t* Jd_rowptr, const int32_t* Jd_colidx, const kkt_options* opt,
+                                kkt_handle4* out);
+
+/* The 2x2 handle inside (owned by h): for kkt_get_info, kkt_inertia,
+ * kkt_symbolic_info_get, kkt_get_symbolic. NULL for a NULL h. */
+kkt_handle kkt_4x4_inner(kkt_handle4 h);
+
+/* The lower CSC pattern of H~ into host arrays (any pointer may be NULL):
+ * *nnz, colptr[n_x+1], rowidx[*nnz]. */
+kkt_status kkt_get_4x4_pattern(kkt_handle4 h, int64_t* nnz, int64_t* colptr, int32_t* rowidx);
+
+/* Forms H~ on the device and factors H~ + delta I + gamma J^T J.
+ *   H_vals device double[nnz(H)], D_x device double[n_x],
+ *   Jd_vals device double[nnz(J_d)], D_s device double[m_d] (D_s > 0),
+ *   J_vals device double[nnz(J)]
+ * J_d and D_s are copied into the handle for kkt_solve_4x4. Errors as
+ * kkt_factor. */
+kkt_status kkt_factor_4x4(kkt_handle4 h, const double* H_vals, const double* D_x, const double* Jd_vals,
+                          const double* D_s, const double* J_vals, double delta, double gamma,
+                          void* stream);
+
+/* Solves eq. linsys4x4 with the last factor: device inputs r~_x[n_x],
+ * r_s[m_d], r_y[m_c], r_yd[m_d]; device outputs dx[n_x], ds[m_d], dy[m_c],
+ * dyd[m_d]. kkt_get_info(kkt_4x4_inner(h)) then reports the 2x2 solve
+ * (its RR and BE are those of the reduced system). Errors as kkt_solve; on
+ * KKT_ERR_CG_MAXIT / KKT_ERR_CG_BREAKDOWN ds and dyd are still recovered
+ * from the last iterate. */
+kkt_status kkt_solve_4x4(kkt_handle4 h, const double* r_xt, const double* r_s, const double* r_y,
+                         const double* r_yd, double* dx, double* ds, double* dy, double* dyd, void* stream);
+
+/* Releases the 4x4 handle and its inner 2x2 handle. */
+kkt_status kkt_destroy_4x4(kkt_handle4 h);
 
 #ifdef __cplusplus
 }

@@ -10,10 +10,11 @@ The C part (``kkt_oracle.c``) is compiled with plain gcc by ``build()``;
 ``reduce4x4``/``recover4x4`` (the 4x4 <-> 2x2 reduction of Sec. 3) are
 numpy/scipy.
 
-Parity status: S2 (the AMD order) is pinned by the special cases in the
-tests (zero fill on trees, identity on cliques, hand-worked graphs, valid
-permutation, brute-force fill) and otherwise only by agreement with the
-library's independent implementation ("parity unpinned" beyond those).
+Parity status: S2 (the AMD order) and S2' (nested dissection) are pinned by
+the special cases in the tests (zero fill on trees, identity on cliques,
+hand-worked graphs, separator properties, valid permutation, brute-force
+fill) and otherwise only by agreement with the library's independent
+implementation ("parity unpinned" beyond those).
 """
 from __future__ import annotations
 

@@ -12,6 +12,8 @@
  *   S1  pattern of H_gamma = pat(H~) U pat(J^T J) U diag          -- Sec. 4, eq. (gamma)
  *   S2  approximate minimum degree ordering (Amestoy, Davis, Duff 1996,
  *       SIAM J. Matrix Anal. Appl. 17(4)), with every tie pinned     -- Sec. 5.3 (AMD)
+ *   S2' nested dissection by level-structure separators (George & Liu),
+ *       the other ordering Sec. 5.3 compares with AMD, every choice pinned
  *   S3  elimination tree + postorder (children ascending)            -- Sec. 5.3; Sec. 2 (symbolic reuse)
  *   S4  column counts of L (exact, from the symbolic column merge)
  *   S5  fundamental + relaxed supernodes (pinned rule, parameters are inputs)
@@ -23,10 +25,11 @@
  *       delta_2 restart on a small quadratic form                    -- Sec. 4.1; Algorithm 1
  *   R   residual r = b - K_delta [dx;dy], RR and BE with ||K||_inf   -- Sec. 5.1 (BE, RR)
  *
- * Parity note: S2's exact order beyond the special cases checked by the
- * tests (trees, cliques, hand-worked graphs, brute-force fill checks) is
- * pinned only by agreement with the independent library implementation
- * ("parity unpinned" for the tie-level details of S2).
+ * Parity note: S2's and S2''s exact orders beyond the special cases checked
+ * by the tests (trees, cliques, paths, stars, hand-worked graphs, separator
+ * properties, brute-force fill checks) are pinned only by agreement with the
+ * independent library implementation ("parity unpinned" for the tie-level
+ * details of S2 and S2').
  */
 #define _POSIX_C_SOURCE 199309L
 #include <math.h>

@@ -36,7 +36,8 @@ class kkt_options(C.Structure):
                 ("relax_num", C.c_int32), ("relax_den", C.c_int32), ("relax_wmax", C.c_int32),
                 ("solve_w", C.c_int32), ("device", C.c_int32), ("debug_stall_piece", C.c_int32),
                 ("spin_cycles", C.c_int64), ("profile", C.c_int32), ("nd_leaf", C.c_int32),
-                ("tensor_cores", C.c_int32), ("pad2_", C.c_int32)]
+                ("tensor_cores", C.c_int32), ("solve_ctas", C.c_int32), ("solve_ent", C.c_int32),
+                ("pad3_", C.c_int32)]
 
 
 class kkt_info(C.Structure):
@@ -74,11 +75,20 @@ def _load():
     L.kkt_get_solve_counters.argtypes = [P, P, I32]
     L.kkt_residual_noalloc.argtypes = [I64, I64, P, P, P, P, P, P, D, P, P, P, P, P, P, P, P]
     L.kkt_destroy.argtypes = [P]
+    L.kkt_analyse_4x4.argtypes = [I64, I64, I64, P, P, P, P, P, P, C.POINTER(kkt_options), C.POINTER(P)]
+    L.kkt_analyse_4x4_host.argtypes = [I64, I64, I64, P, P, P, P, P, P, C.POINTER(kkt_options), C.POINTER(P)]
+    L.kkt_4x4_inner.argtypes = [P]
+    L.kkt_4x4_inner.restype = P
+    L.kkt_get_4x4_pattern.argtypes = [P, P, P, P]
+    L.kkt_factor_4x4.argtypes = [P, P, P, P, P, P, D, D, P]
+    L.kkt_solve_4x4.argtypes = [P, P, P, P, P, P, P, P, P, P]
+    L.kkt_destroy_4x4.argtypes = [P]
     L.kkt_status_string.argtypes = [I32]
     L.kkt_status_string.restype = C.c_char_p
     for nm in ("kkt_analyse", "kkt_analyse_host", "kkt_factor", "kkt_solve", "kkt_factor_solve_host", "kkt_hsolve", "kkt_get_info",
                "kkt_inertia", "kkt_symbolic_info_get", "kkt_get_symbolic", "kkt_get_factor_panels", "kkt_get_profile", "kkt_get_solve_counters", "kkt_residual_noalloc",
-               "kkt_destroy"):
+               "kkt_destroy", "kkt_analyse_4x4", "kkt_analyse_4x4_host", "kkt_get_4x4_pattern", "kkt_factor_4x4",
+               "kkt_solve_4x4", "kkt_destroy_4x4"):
         getattr(L, nm).restype = I32
     return L
 
@@ -87,7 +97,8 @@ _lib = _load()
 EXPORTED = ("kkt_default_options", "kkt_analyse", "kkt_analyse_host", "kkt_factor", "kkt_solve", "kkt_factor_solve_host",
             "kkt_hsolve", "kkt_get_info", "kkt_inertia", "kkt_symbolic_info_get", "kkt_get_symbolic",
             "kkt_get_factor_panels", "kkt_get_profile", "kkt_get_solve_counters", "kkt_residual_noalloc",
-            "kkt_destroy", "kkt_status_string")
+            "kkt_destroy", "kkt_status_string", "kkt_analyse_4x4", "kkt_analyse_4x4_host", "kkt_4x4_inner",
+            "kkt_get_4x4_pattern", "kkt_factor_4x4", "kkt_solve_4x4", "kkt_destroy_4x4")
 KERNEL_KINDS = ("assemble", "potrf", "trsm", "panel_update", "syrk", "extend_add", "zero_u", "cg_persistent",
                 "residual", "tri_inv", "syrk_tc")
 
@@ -242,14 +253,55 @@ def kkt_residual_noalloc(n, m, H_colptr, H_rowidx, H_vals, J_rowptr, J_colidx, J
 
 def kkt_get_solve_counters(h, reset=False):
     """Cycle counters of the persistent solve kernel (profile=1 handles)."""
-    out = np.zeros(8, np.uint64)
+    out = np.zeros(16, np.uint64)
     _check("kkt_get_solve_counters", _lib.kkt_get_solve_counters(h, out.ctypes.data, int(bool(reset))))
-    keys = ("dispatch", "dep_wait", "copy_wait", "items", "barriers", "n_items", "cta_launches")
+    keys = ("dispatch", "dep_wait", "copy_wait", "items", "barriers", "n_items", "cta_launches",
+            "subtree_cycles", "n_subtree", "head_cycles", "n_head", "chunk_cycles", "n_chunk")
     return {k: int(out[i]) for i, k in enumerate(keys)}
 
 
 def kkt_destroy(h):
     return _lib.kkt_destroy(h)
+
+
+def kkt_analyse_4x4(n_x, m_c, m_d, H_colptr, H_rowidx, J_rowptr, J_colidx, Jd_rowptr, Jd_colidx,
+                    opt: kkt_options | None = None, host=False):
+    keep = [_np(H_colptr, np.int64), _np(H_rowidx, np.int32), _np(J_rowptr, np.int64), _np(J_colidx, np.int32),
+            _np(Jd_rowptr, np.int64), _np(Jd_colidx, np.int32)]
+    h = C.c_void_p()
+    fn = "kkt_analyse_4x4_host" if host else "kkt_analyse_4x4"
+    _check(fn, getattr(_lib, fn)(int(n_x), int(m_c), int(m_d), *[k[1] for k in keep],
+                                 C.byref(opt) if opt is not None else None, C.byref(h)))
+    return h
+
+
+def kkt_4x4_inner(h4):
+    return C.c_void_p(_lib.kkt_4x4_inner(h4))
+
+
+def kkt_get_4x4_pattern(h4, n_x):
+    nnz = C.c_int64()
+    _check("kkt_get_4x4_pattern", _lib.kkt_get_4x4_pattern(h4, C.byref(nnz), None, None))
+    ptr = np.zeros(n_x + 1, np.int64)
+    row = np.zeros(max(1, nnz.value), np.int32)
+    _check("kkt_get_4x4_pattern", _lib.kkt_get_4x4_pattern(h4, None, ptr.ctypes.data, row.ctypes.data))
+    return ptr, row[: nnz.value]
+
+
+def kkt_factor_4x4(h4, H_vals, D_x, Jd_vals, D_s, J_vals, delta, gamma, sizes, stream=None):
+    nh, nx, njd, md, nj = sizes
+    return _lib.kkt_factor_4x4(h4, _dev(H_vals, nh), _dev(D_x, nx), _dev(Jd_vals, njd), _dev(D_s, md),
+                               _dev(J_vals, nj), float(delta), float(gamma), _stream(stream))
+
+
+def kkt_solve_4x4(h4, r_xt, r_s, r_y, r_yd, dx, ds, dy, dyd, sizes, stream=None):
+    nx, mc, md = sizes
+    return _lib.kkt_solve_4x4(h4, _dev(r_xt, nx), _dev(r_s, md), _dev(r_y, mc), _dev(r_yd, md), _dev(dx, nx),
+                              _dev(ds, md), _dev(dy, mc), _dev(dyd, md), _stream(stream))
+
+
+def kkt_destroy_4x4(h4):
+    return _lib.kkt_destroy_4x4(h4)
 
 
 def kkt_status_string(code) -> str:
@@ -332,6 +384,67 @@ class KKTSolver:
     def close(self):
         if getattr(self, "h", None):
             kkt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class KKTSolver4x4:
+    """The 4x4 form (Sec. 3, eq. linsys4x4): H, D_x, D_s, J, J_d values per
+    factorization; (r~_x, r_s, r_y, r_yd) -> (dx, ds, dy, dy_d) per solve.
+    Reduction to the 2x2 form, the solve, and the recovery of ds and dy_d all
+    run on the device."""
+
+    def __init__(self, n_x, m_c, m_d, H_colptr, H_rowidx, J_rowptr, J_colidx, Jd_rowptr, Jd_colidx, **options):
+        self.n, self.m, self.md = int(n_x), int(m_c), int(m_d)
+        self.nnz_h = int(np.asarray(H_colptr)[-1])
+        self.nnz_j = int(np.asarray(J_rowptr)[-1]) if m_c else 0
+        self.nnz_jd = int(np.asarray(Jd_rowptr)[-1]) if m_d else 0
+        if options.get("precision") in ("mixed", KKT_MIXED):
+            options.setdefault("cg_rtol", 1e-6)
+            options.setdefault("ir_maxit", 10)
+        self.opt = kkt_default_options(**options)
+        self.h = kkt_analyse_4x4(n_x, m_c, m_d, H_colptr, H_rowidx, J_rowptr, J_colidx, Jd_rowptr, Jd_colidx,
+                                 self.opt)
+
+    def factor(self, H_vals, D_x, Jd_vals, D_s, J_vals, delta, gamma=-1.0, stream=None, check=True):
+        code = kkt_factor_4x4(self.h, H_vals, D_x, Jd_vals, D_s, J_vals, delta, gamma,
+                              (self.nnz_h, self.n, self.nnz_jd, self.md, self.nnz_j), stream)
+        if check:
+            _check("kkt_factor_4x4", code)
+        return code
+
+    def solve(self, r_xt, r_s, r_y, r_yd, stream=None, check=True):
+        import torch
+        f = lambda k: torch.empty(k, dtype=torch.float64, device=r_xt.device)
+        dx, ds, dy, dyd = f(self.n), f(self.md), f(self.m), f(self.md)
+        code = kkt_solve_4x4(self.h, r_xt, r_s, r_y, r_yd, dx, ds, dy, dyd, (self.n, self.m, self.md), stream)
+        if check:
+            _check("kkt_solve_4x4", code)
+        return dx, ds, dy, dyd
+
+    @property
+    def inner(self):
+        return kkt_4x4_inner(self.h)
+
+    @property
+    def info(self):
+        return kkt_get_info(self.inner)
+
+    @property
+    def inertia_ok(self):
+        return kkt_inertia(self.inner)
+
+    def pattern(self):
+        return kkt_get_4x4_pattern(self.h, self.n)
+
+    def close(self):
+        if getattr(self, "h", None):
+            kkt_destroy_4x4(self.h)
             self.h = None
 
     def __del__(self):

@@ -55,6 +55,7 @@ struct kkt_handle_s {
   Plan P;
   int device = 0;
   int grid = 0;
+  int ctas = 2;   // solve-kernel CTAs per SM
   int64_t nnzH = 0, nnzJ = 0;
   DevArena mem;
   // pattern / plan on the device
@@ -92,6 +93,9 @@ struct kkt_handle_s {
   int inertia_ok = 0;
   Prof prof;
   Prof* profp = nullptr;   // non-null when opt.profile
+  // the solve kernel is timed in every mode: one event pair per pass, read
+  // after the pass's status read has synchronised the stream anyway
+  cudaEvent_t cg_a = nullptr, cg_b = nullptr;
 };
 
 static kkt_status cuda_status(cudaError_t e) {
@@ -159,6 +163,8 @@ kkt_status kkt_destroy(kkt_handle h) {
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->prof.a) cudaEventDestroy(h->prof.a);
   if (h->prof.b) cudaEventDestroy(h->prof.b);
+  if (h->cg_a) cudaEventDestroy(h->cg_a);
+  if (h->cg_b) cudaEventDestroy(h->cg_b);
   delete h;
   return KKT_OK;
 }
@@ -173,7 +179,8 @@ static kkt_status analyse_host(int64_t n, int64_t m, const int64_t* Hp, const in
   if (opt) h->opt = *opt; else kkt_default_options(&h->opt);
   const kkt_options& o = h->opt;
   if ((o.solve_w != 0 && (o.solve_w < 32 || o.solve_w > 256)) || o.relax_den <= 0 || o.precision < 0 ||
-      o.precision > 1) {
+      o.precision > 1 || o.solve_ctas < 0 || o.solve_ctas == 1 || o.solve_ctas > 4 ||
+      (o.solve_ent != 0 && (o.solve_ent < 2048 || o.solve_ent > 32768))) {
     delete h;
     return KKT_ERR_INVALID;
   }
@@ -188,7 +195,7 @@ static kkt_status analyse_host(int64_t n, int64_t m, const int64_t* Hp, const in
   // (about 107 KB (FP32) / 98 KB (FP64) of shared memory each)
   const bool f64o = o.precision == KKT_FP64;
   const int sw = o.solve_w > 0 ? o.solve_w : (f64o ? 64 : 128);
-  const int ent = f64o ? 8192 : 16384;
+  const int ent = o.solve_ent > 0 ? o.solve_ent : (f64o ? 8192 : 16384);
   if (build_plan(h->S, Hp, Hi, Jp, Ji, sw, ent, ent, !f64o && o.tensor_cores, h->P) != 0) {
     delete h;
     return KKT_ERR_INVALID;
@@ -220,8 +227,9 @@ kkt_status kkt_analyse(int64_t n, int64_t m, const int64_t* Hp, const int32_t* H
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device);
   if (!coop) { delete h; return KKT_ERR_CUDA; }
   const bool f64 = o.precision == KKT_FP64;
-  h->grid = f64 ? solve_grid_size<double>(h->device, h->P.solve_w, h->P.ent, h->P.ent0, h->P.max_rows)
-                : solve_grid_size<float>(h->device, h->P.solve_w, h->P.ent, h->P.ent0, h->P.max_rows);
+  h->ctas = o.solve_ctas > 0 ? o.solve_ctas : 2;
+  h->grid = f64 ? solve_grid_size<double>(h->device, h->P.solve_w, h->P.ent, h->P.ent0, h->P.max_rows, h->ctas)
+                : solve_grid_size<float>(h->device, h->P.solve_w, h->P.ent, h->P.ent0, h->P.max_rows, h->ctas);
   if (h->grid <= 0) { delete h; return KKT_ERR_INVALID; }
   const Plan& P = h->P;
   DevArena& A = h->mem;
@@ -273,12 +281,17 @@ kkt_status kkt_analyse(int64_t n, int64_t m, const int64_t* Hp, const int32_t* H
   h->counters = A.alloc<int>(4 * (size_t)P.npieces + 8);
   h->dst = A.alloc<DevStatus>(1);
   h->d_dg = A.alloc<double>(2);
-  h->d_instr = A.alloc<unsigned long long>(8);
+  h->d_instr = A.alloc<unsigned long long>(16);
   if (A.failed) { kkt_destroy(h); return KKT_ERR_OOM; }
   if (cudaMallocHost(&h->hst, sizeof(DevStatus)) != cudaSuccess) { cudaGetLastError(); h->hst = nullptr; kkt_destroy(h); return KKT_ERR_OOM; }
   if (cudaMallocHost(&h->h_dg, 2 * sizeof(double)) != cudaSuccess) { cudaGetLastError(); h->h_dg = nullptr; kkt_destroy(h); return KKT_ERR_OOM; }
   if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) { cudaGetLastError(); h->cap_stream = nullptr; kkt_destroy(h); return KKT_ERR_CUDA; }
   if (cudaDeviceSynchronize() != cudaSuccess) { cudaGetLastError(); kkt_destroy(h); return KKT_ERR_CUDA; }
+  if (cudaEventCreate(&h->cg_a) != cudaSuccess || cudaEventCreate(&h->cg_b) != cudaSuccess) {
+    cudaGetLastError();
+    kkt_destroy(h);
+    return KKT_ERR_CUDA;
+  }
   if (o.profile) {
     if (cudaEventCreate(&h->prof.a) != cudaSuccess || cudaEventCreate(&h->prof.b) != cudaSuccess) {
       cudaGetLastError();
@@ -286,7 +299,7 @@ kkt_status kkt_analyse(int64_t n, int64_t m, const int64_t* Hp, const int32_t* H
       return KKT_ERR_CUDA;
     }
     h->profp = &h->prof;
-    if (cudaMemset(h->d_instr, 0, 8 * sizeof(unsigned long long)) != cudaSuccess) { cudaGetLastError(); kkt_destroy(h); return KKT_ERR_CUDA; }
+    if (cudaMemset(h->d_instr, 0, 16 * sizeof(unsigned long long)) != cudaSuccess) { cudaGetLastError(); kkt_destroy(h); return KKT_ERR_CUDA; }
   }
   h->on_device = true;
   *out = h;
@@ -426,9 +439,15 @@ static kkt_status solve_pass(kkt_handle h, const double* bx, const double* by, d
   CK(cudaMemsetAsync(h->counters, 0, sizeof(int) * (4 * (size_t)h->P.npieces + 8), st));
   SolveArgs<T> a = solve_args<T>(h);
   a.bx = bx; a.by = by; a.ox = ox; a.oy = oy; a.accumulate = accumulate; a.mode = mode;
-  CK(prof_begin(h->profp, st));
-  CK(launch_solve<T>(a, h->grid, st));
-  CK(prof_end(h->profp, KKT_K_CG, st));
+  if (h->profp) {
+    CK(prof_begin(h->profp, st));
+    CK(launch_solve<T>(a, h->grid, h->ctas, st));
+    CK(prof_end(h->profp, KKT_K_CG, st));
+  } else {
+    CK(cudaEventRecord(h->cg_a, st));
+    CK(launch_solve<T>(a, h->grid, h->ctas, st));
+    CK(cudaEventRecord(h->cg_b, st));
+  }
   return KKT_OK;
 }
 
@@ -465,6 +484,12 @@ static kkt_status solve_common(kkt_handle h, const double* rx, const double* ry,
     if (s) return s;
     if ((s = residual(h, rx, ry, dx, dy, st))) return s;
     if ((s = read_status(h, st))) return s;
+    if (!h->profp) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, h->cg_a, h->cg_b));
+      h->prof.ms[KKT_K_CG] += ms;
+      h->prof.n[KKT_K_CG] += 1;
+    }
     const DevStatus& d = *h->hst;
     total_it += d.cg_iters;
     brk |= d.breakdown;
@@ -594,8 +619,8 @@ kkt_status kkt_get_solve_counters(kkt_handle h, uint64_t* out, int32_t reset) {
   if (!h || !out) return KKT_ERR_INVALID;
   if (!h->on_device) return KKT_ERR_STATE;
   CK(cudaSetDevice(h->device));
-  CK(cudaMemcpy(out, h->d_instr, 8 * sizeof(uint64_t), cudaMemcpyDeviceToHost));
-  if (reset) CK(cudaMemset(h->d_instr, 0, 8 * sizeof(uint64_t)));
+  CK(cudaMemcpy(out, h->d_instr, 16 * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+  if (reset) CK(cudaMemset(h->d_instr, 0, 16 * sizeof(uint64_t)));
   return KKT_OK;
 }
 

@@ -103,9 +103,9 @@ struct SolveArgs {
 };
 
 template <typename T>
-cudaError_t launch_solve(const SolveArgs<T>& a, int grid, cudaStream_t st);
+cudaError_t launch_solve(const SolveArgs<T>& a, int grid, int ctas, cudaStream_t st);
 template <typename T>
-int solve_grid_size(int device, int sw, int ent, int ent0, int max_rows);
+int solve_grid_size(int device, int sw, int ent, int ent0, int max_rows, int ctas);
 size_t solve_smem_bytes(size_t elem, int sw, int ent, int ent0, int max_rows);
 
 // FP64 residual of K_delta = [H~ + delta I, J^T; J, 0] (original labels):

@@ -237,11 +237,15 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
   // Maximal subtrees with at most kSubCols columns and kSubEntries panel
   // entries; supernode indices are a postorder, so a subtree is the index
   // range [root - size + 1, root].
-  const int64_t kSubCols = std::min<int64_t>(128, solve_w), kSubEntries = 32768;
+  // The solve kernel stages a subtree's panels (stored entries, ld
+  // included) into its row-tile region of ent entries and the inverses of
+  // its triangles into the inverse region of one solve_w-wide piece (their
+  // sum over <= solve_w columns never exceeds that piece's).
+  const int64_t kSubCols = std::min<int64_t>(128, solve_w), kSubEntries = ent;
   std::vector<int64_t> sub_cols(ns, 0), sub_ent(ns, 0), sub_size(ns, 1);
   for (int64_t s = 0; s < ns; s++) {
     sub_cols[s] += P.sw[s];
-    sub_ent[s] += (int64_t)P.sw[s] * P.snr[s];
+    sub_ent[s] += (int64_t)P.sw[s] * P.sld[s];
     const int32_t p = P.sparent[s];
     if (p >= 0) { sub_cols[p] += sub_cols[s]; sub_ent[p] += sub_ent[s]; sub_size[p] += sub_size[s]; }
   }
@@ -310,6 +314,13 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
   }
   P.npieces = (int64_t)P.pc_first.size();
   P.pc_inv.push_back(P.inv_total);               // [npieces + 1]: sizes by difference
+  // each subtree's staged ranges fit the solve kernel's tile regions
+  for (int64_t t = 0; t < P.nsub; t++) {
+    const int32_t s0 = P.st_first[t], s1 = P.st_last[t];
+    const int64_t pe = P.poff[s1] + (int64_t)P.sw[s1] * P.sld[s1] - P.poff[s0];
+    const int64_t ie = P.pc_inv[P.sn_piece[s1] + 1] - P.pc_inv[P.sn_piece[s0]];
+    if (pe > ent || ie > packed_inv_size(solve_w) || P.sn_piece[s1] - P.sn_piece[s0] != s1 - s0) return 2;
+  }
   P.pc_zoff.resize(P.npieces);
   P.pc_nchunk.resize(P.npieces);
   P.pc_rc0.resize(P.npieces);

@@ -15,6 +15,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -31,6 +33,7 @@ struct SolveSmemHdr {
   // cycle counters of thread 0 (kept when a.instr != nullptr): dispatch,
   // dependency waits, bulk-copy waits, whole items, grid barriers, items
   long long c_disp, c_dep, c_mbar, c_item, c_bar, n_items;
+  long long c_kind[3], n_kind[3];   // whole-item cycles and counts: subtrees, heads, chunks
   double dred[(kSolveThreads / 32) * 2];
   double bcast[2];
 };
@@ -391,18 +394,39 @@ __device__ bool bwd_head(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>&
 // A subtree whose columns [clo, chi) fit in shared memory is solved by one
 // CTA: its descendants are all inside it, so in the forward sweep it depends
 // on nothing and in the backward sweep only on the pieces owning its rows
-// outside [clo, chi).
+// outside [clo, chi). Its supernodes are consecutive, so their panels and
+// the inverses of their triangles are two contiguous ranges, each staged
+// into shared memory with one bulk copy (the plan keeps both within the
+// tile regions).
+template <typename T>
+__device__ void stage_subtree(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>& t, int st, int64_t& pbase,
+                              int64_t& ibase) {
+  const int s0 = a.st_first[st], s1 = a.st_last[st];
+  pbase = a.poff[s0];
+  ibase = a.pc_inv[a.sn_piece[s0]];
+  if (threadIdx.x == 0) {
+    const uint32_t bp = (uint32_t)((a.poff[s1] + (int64_t)a.sld[s1] * a.sw_[s1] - pbase) * sizeof(T));
+    const uint32_t bi = (uint32_t)((a.pc_inv[a.sn_piece[s1] + 1] - ibase) * sizeof(T));
+    fence_proxy_async();
+    mbar_expect_tx(&h.mbar, bp + bi);
+    bulk_g2s(t.B, a.L + pbase, bp, &h.mbar);
+    bulk_g2s(t.A, a.Linv + ibase, bi, &h.mbar);
+  }
+}
+
 template <typename T>
 __device__ bool fwd_subtree(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>& t, int st) {
   const int tid = threadIdx.x;
   const int clo = a.st_clo[st], chi = a.st_chi[st];
+  int64_t pbase, ibase;
+  stage_subtree(a, h, t, st, pbase, ibase);
   T* xs = t.vec2;
   for (int i = tid; i < chi - clo; i += blockDim.x) xs[i] = ldcg(&a.v[clo + i]);
-  __syncthreads();
+  if (!mbar_wait(a, h)) return false;
   for (int s = a.st_first[st]; s <= a.st_last[st]; s++) {
     const int w = a.sw_[s], nr = a.snr[s], ld = a.sld[s], f = a.sfirst[s] - clo;
-    const T* P = a.L + a.poff[s];
-    const T* Inv = a.Linv + a.pc_inv[a.sn_piece[s]];
+    const T* P = t.B + (a.poff[s] - pbase);
+    const T* Inv = t.A + (a.pc_inv[a.sn_piece[s]] - ibase);
     if (tid < w) {
       T y = T(0);
       int off = 0;
@@ -417,7 +441,7 @@ __device__ bool fwd_subtree(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<
     const int32_t* rows = a.sn_rows + a.srow[s];
     for (int r = w + tid; r < nr; r += blockDim.x) {
       T o = T(0);
-      for (int k = 0; k < w; k++) o += P[r + (int64_t)k * ld] * t.vec[k];
+      for (int k = 0; k < w; k++) o += P[r + k * ld] * t.vec[k];
       const int row = rows[r];
       if (row < chi) xs[row - clo] -= o;
       else atomicAdd(&a.v[row], -o);
@@ -436,6 +460,8 @@ template <typename T>
 __device__ bool bwd_subtree(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>& t, int st, int e) {
   const int tid = threadIdx.x;
   const int clo = a.st_clo[st], chi = a.st_chi[st];
+  int64_t pbase, ibase;
+  stage_subtree(a, h, t, st, pbase, ibase);
   if (tid == 0) {
     const long long t0 = clock64();
     int ok = 1;
@@ -445,22 +471,23 @@ __device__ bool bwd_subtree(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<
     h.c_dep += clock64() - t0;
   }
   __syncthreads();
-  if (!h.flag) return false;
+  const bool dep = h.flag != 0;
   T* xs = t.vec2;
-  for (int i = tid; i < chi - clo; i += blockDim.x) xs[i] = ldcg(&a.v[clo + i]);
-  __syncthreads();
+  if (dep)
+    for (int i = tid; i < chi - clo; i += blockDim.x) xs[i] = ldcg(&a.v[clo + i]);
+  if (!mbar_wait(a, h) || !dep) return false;
   const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   for (int s = a.st_last[st]; s >= a.st_first[st]; s--) {
     const int w = a.sw_[s], nr = a.snr[s], ld = a.sld[s], f = a.sfirst[s] - clo;
-    const T* P = a.L + a.poff[s];
-    const T* Inv = a.Linv + a.pc_inv[a.sn_piece[s]];
+    const T* P = t.B + (a.poff[s] - pbase);
+    const T* Inv = t.A + (a.pc_inv[a.sn_piece[s]] - ibase);
     const int32_t* rows = a.sn_rows + a.srow[s];
     for (int k = warp; k < w; k += nw) {
       T acc = T(0);
       for (int r = w + lane; r < nr; r += 32) {
         const int row = rows[r];
         const T x = row < chi ? xs[row - clo] : ldcg(&a.v[row]);
-        acc += P[r + (int64_t)k * ld] * x;
+        acc += P[r + k * ld] * x;
       }
       acc = warp_sum(acc);
       if (lane == 0) t.vec[k] = xs[f + k] - acc;
@@ -560,6 +587,7 @@ __device__ bool sweep(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>& t,
     }
     if (it >= a.nitems) return true;
     const int code = items[it];
+    const int kind = code < -(int)a.npieces ? 0 : (code < 0 ? 1 : 2);
     bool ok;
     if (code < -(int)a.npieces) {
       const int st = -1 - (int)a.npieces - code;
@@ -570,8 +598,11 @@ __device__ bool sweep(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>& t,
       ok = code < 0 ? bwd_head(a, h, t, -1 - code, e) : bwd_chunk(a, h, t, code, e);
     }
     if (threadIdx.x == 0) {
-      h.c_item += clock64() - td;
+      const long long dt = clock64() - td;
+      h.c_item += dt;
       h.n_items++;
+      h.c_kind[kind] += dt;
+      h.n_kind[kind]++;
     }
     if (!ok) return false;
   }
@@ -588,6 +619,10 @@ __device__ void flush_counters(const SolveArgs<T>& a, SolveSmemHdr& h) {
     atomicAdd(&a.instr[4], (unsigned long long)h.c_bar);
     atomicAdd(&a.instr[5], (unsigned long long)h.n_items);
     atomicAdd(&a.instr[6], 1ull);
+    for (int k = 0; k < 3; k++) {
+      atomicAdd(&a.instr[7 + 2 * k], (unsigned long long)h.c_kind[k]);
+      atomicAdd(&a.instr[8 + 2 * k], (unsigned long long)h.n_kind[k]);
+    }
   }
 }
 
@@ -600,8 +635,9 @@ __device__ bool hsolve(const SolveArgs<T>& a, SolveSmemHdr& sm, const Tiles<T>& 
   return grid_barrier(a, sm);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kSolveThreads, 2) k_cg(SolveArgs<T> a) {
+// MB = resident CTAs per SM the register allocation is bounded for
+template <typename T, int MB>
+__global__ void __launch_bounds__(kSolveThreads, MB) k_cg(SolveArgs<T> a) {
   __shared__ SolveSmemHdr sm;
   extern __shared__ __align__(16) unsigned char dsm[];
   Tiles<T> tl;
@@ -614,6 +650,7 @@ __global__ void __launch_bounds__(kSolveThreads, 2) k_cg(SolveArgs<T> a) {
     mbar_init(&sm.mbar);
     sm.phase = 0;
     sm.c_disp = sm.c_dep = sm.c_mbar = sm.c_item = sm.c_bar = sm.n_items = 0;
+    for (int k = 0; k < 3; k++) sm.c_kind[k] = sm.n_kind[k] = 0;
   }
   __syncthreads();
   const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -744,33 +781,43 @@ __global__ void __launch_bounds__(kSolveThreads, 2) k_cg(SolveArgs<T> a) {
 }
 
 template <typename T>
-int solve_grid_size(int device, int sw, int ent, int ent0, int max_rows) {
+using CgKernel = void (*)(SolveArgs<T>);
+
+template <typename T>
+static CgKernel<T> cg_kernel(int ctas) {
+  return ctas >= 4 ? k_cg<T, 4> : (ctas == 3 ? k_cg<T, 3> : k_cg<T, 2>);
+}
+
+template <typename T>
+int solve_grid_size(int device, int sw, int ent, int ent0, int max_rows, int ctas) {
   int sms = 0, per = 0, maxsm = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
   const size_t smem = solve_smem_bytes(sizeof(T), sw, ent, ent0, max_rows);
   if (smem > (size_t)maxsm) return 0;
-  if (cudaFuncSetAttribute(k_cg<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+  auto k = cg_kernel<T>(ctas);
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cg<T>, kSolveThreads, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, kSolveThreads, smem);
   if (per < 1) return 0;
-  return sms * per;
+  return sms * std::min(per, std::max(ctas, 2));
 }
 
 template <typename T>
-cudaError_t launch_solve(const SolveArgs<T>& a, int grid, cudaStream_t st) {
+cudaError_t launch_solve(const SolveArgs<T>& a, int grid, int ctas, cudaStream_t st) {
   SolveArgs<T> args = a;
   void* params[] = {&args};
   const size_t smem = solve_smem_bytes(sizeof(T), a.sw, a.ent, a.ent0, a.max_rows);
-  return cudaLaunchCooperativeKernel((const void*)k_cg<T>, dim3(grid), dim3(kSolveThreads), params, smem, st);
+  return cudaLaunchCooperativeKernel((const void*)cg_kernel<T>(ctas), dim3(grid), dim3(kSolveThreads), params, smem,
+                                     st);
 }
 
-template int solve_grid_size<double>(int, int, int, int, int);
-template int solve_grid_size<float>(int, int, int, int, int);
-template cudaError_t launch_solve<double>(const SolveArgs<double>&, int, cudaStream_t);
-template cudaError_t launch_solve<float>(const SolveArgs<float>&, int, cudaStream_t);
+template int solve_grid_size<double>(int, int, int, int, int, int);
+template int solve_grid_size<float>(int, int, int, int, int, int);
+template cudaError_t launch_solve<double>(const SolveArgs<double>&, int, int, cudaStream_t);
+template cudaError_t launch_solve<float>(const SolveArgs<float>&, int, int, cudaStream_t);
 
 // --------------------------------------------------------------- residual
 __global__ void __launch_bounds__(256) k_residual(ResArgs a) {

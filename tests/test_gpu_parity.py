@@ -273,3 +273,58 @@ def test_repeat_solves_agree():
     a = torch.cat(s.solve(cu(sys.r_x), cu(sys.r_y))).cpu().numpy()
     b = torch.cat(s.solve(cu(sys.r_x), cu(sys.r_y))).cpu().numpy()
     assert rel(a, b) <= 1e-12
+
+
+# ----------------------------------------------------------------- 4x4 form (Sec. 3)
+def _oracle_4x4(p):
+    """Oracle 4x4 solve (reduction, 2x2 solve, recovery); None when the
+    oracle's Cholesky of H~ + gamma J^T J fails."""
+    Hp, Hi, Hv, r_x = O.reduce4x4(p)
+    s = W.KKTSystem(p["n_x"], p["m_c"], Hp, Hi, Hv, p["J_rowptr"], p["J_colidx"], p["J_vals"], r_x, p["r_y"],
+                    p.get("delta", 0.0), p.get("gamma", 1e2))
+    _, _, dx, dy, info = O.solve_system(s, ir_maxit=2)
+    if info["status"] == 2:
+        return None
+    assert info["status"] == 0
+    ds, dyd = O.recover4x4(p, dx)
+    return np.concatenate([dx, ds, dy, dyd])
+
+
+def _gpu_4x4(p, precision):
+    s = K.KKTSolver4x4(p["n_x"], p["m_c"], p["m_d"], p["H_colptr"], p["H_rowidx"], p["J_rowptr"], p["J_colidx"],
+                       p["Jd_rowptr"], p["Jd_colidx"], precision=precision)
+    try:
+        code = s.factor(cu(p["H_vals"]), cu(p["D_x"]), cu(p["Jd_vals"]), cu(p["D_s"]), cu(p["J_vals"]),
+                        p.get("delta", 0.0), p.get("gamma", 1e2), check=False)
+        if code == 2:
+            return None
+        assert code == 0
+        out = s.solve(cu(p["r_xt"]), cu(p["r_s"]), cu(p["r_y"]), cu(p["r_yd"]))
+        assert s.info.rr <= 1e-8
+        return np.concatenate([o.cpu().numpy() for o in out])
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("seed", range(6))
+def test_4x4_tiny_matches_oracle(seed, precision):
+    """Random 4x4 parts as drawn (H often indefinite on null(J): then both
+    sides must report the failed Cholesky, Thm 1) and with D_x shifted by 10
+    (H~ SPD: solutions agree)."""
+    p = W.random_4x4_parts(seed, n_x=20 + 9 * seed, m_c=5 + seed, m_d=4 + 3 * seed)
+    ref, got = _oracle_4x4(p), _gpu_4x4(p, precision)
+    assert (ref is None) == (got is None)
+    if ref is not None:
+        assert rel(got, ref) <= 1e-6
+    p["D_x"] = p["D_x"] + 10.0
+    ref, got = _oracle_4x4(p), _gpu_4x4(p, precision)
+    assert ref is not None and got is not None
+    assert rel(got, ref) <= 1e-6
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_4x4_grid_matches_oracle(precision):
+    """50x40 grid, J_d with 500 local rows, D_s over eight decades."""
+    p = W.grid_4x4_parts("grid2d_n2000")
+    assert rel(_gpu_4x4(p, precision), _oracle_4x4(p)) <= 1e-6

@@ -531,3 +531,32 @@ def test_small_grid_workload_against_sparse_lu():
     ref = spl.spsolve(K, np.concatenate([sys.r_x, sys.r_y]))
     got = np.concatenate([dx, dy])
     assert np.linalg.norm(got - ref) <= 1e-6 * np.linalg.norm(ref)
+
+
+def test_grid_4x4_reduction_matches_sparse_lu():
+    """The 4x4 form on the 50x40 grid (J_d with n/4 local rows, D_s over
+    eight decades): reduction + 2x2 solve + recovery (Sec. 3) equals a
+    sparse LU solve of the full eq. linsys4x4 matrix with delta on the
+    H + D_x block."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spl
+    p = W.grid_4x4_parts("grid2d_n2000")
+    Hp, Hi, Hv, r_x = O.reduce4x4(p)
+    n, mc, md = p["n_x"], p["m_c"], p["m_d"]
+    s = W.KKTSystem(n, mc, Hp, Hi, Hv, p["J_rowptr"], p["J_colidx"], p["J_vals"], r_x, p["r_y"], p["delta"],
+                    p["gamma"])
+    _, _, dx, dy, info = O.solve_system(s)
+    assert info["status"] == 0
+    ds, dyd = O.recover4x4(p, dx)
+    H = sp.csc_matrix((p["H_vals"], p["H_rowidx"], p["H_colptr"]), shape=(n, n))
+    H = H + sp.tril(H, -1).T
+    J = sp.csr_matrix((p["J_vals"], p["J_colidx"], p["J_rowptr"]), shape=(mc, n))
+    Jd = sp.csr_matrix((p["Jd_vals"], p["Jd_colidx"], p["Jd_rowptr"]), shape=(md, n))
+    I = sp.eye(md)
+    K4 = sp.bmat([[H + sp.diags(p["D_x"]) + p["delta"] * sp.eye(n), None, J.T, Jd.T],
+                  [None, sp.diags(p["D_s"]), None, -I], [J, None, None, None], [Jd, -I, None, None]]).tocsc()
+    b = np.concatenate([p["r_xt"], p["r_s"], p["r_y"], p["r_yd"]])
+    ref = spl.splu(K4).solve(b)
+    got = np.concatenate([dx, ds, dy, dyd])
+    assert np.linalg.norm(got - ref) <= 1e-9 * np.linalg.norm(ref)
+    assert np.linalg.norm(b - K4 @ got) <= 1e-10 * np.linalg.norm(b)

@@ -147,3 +147,53 @@ def test_host_handle_refuses_device_calls():
         assert code in (1, 8)
     finally:
         K.kkt_destroy(h)
+
+
+# ----------------------------------------------------------------- 4x4 form (Sec. 3)
+@pytest.mark.parametrize("seed", range(8))
+def test_4x4_pattern_and_symbolic_match_oracle_reduction(seed):
+    """The library's H~ pattern of the 4x4 form (pat(H) U pat(J_d^T J_d) U
+    diag) equals the oracle's reduction, and the symbolic analysis of the
+    inner 2x2 system is bit-exact."""
+    p = W.random_4x4_parts(seed, n_x=25 + 7 * seed, m_c=6 + seed, m_d=4 + 2 * seed)
+    h = K.kkt_analyse_4x4(p["n_x"], p["m_c"], p["m_d"], p["H_colptr"], p["H_rowidx"], p["J_rowptr"],
+                          p["J_colidx"], p["Jd_rowptr"], p["Jd_colidx"], host=True)
+    try:
+        ptr, row = K.kkt_get_4x4_pattern(h, p["n_x"])
+        Hp, Hi, _, _ = O.reduce4x4(p)
+        np.testing.assert_array_equal(ptr, Hp)
+        np.testing.assert_array_equal(row, Hi)
+        g = K.kkt_get_symbolic(K.kkt_4x4_inner(h))
+        sym = O.Symbolic(p["n_x"], p["m_c"], Hp, Hi, p["J_rowptr"], p["J_colidx"])
+        np.testing.assert_array_equal(g["perm"], sym.perm)
+        np.testing.assert_array_equal(g["colcount"], sym.colcount)
+    finally:
+        K.kkt_destroy_4x4(h)
+
+
+def test_4x4_grid_pattern_matches_oracle_reduction():
+    p = W.grid_4x4_parts("grid2d_n2000")
+    h = K.kkt_analyse_4x4(p["n_x"], p["m_c"], p["m_d"], p["H_colptr"], p["H_rowidx"], p["J_rowptr"],
+                          p["J_colidx"], p["Jd_rowptr"], p["Jd_colidx"], host=True)
+    try:
+        ptr, row = K.kkt_get_4x4_pattern(h, p["n_x"])
+        Hp, Hi, _, _ = O.reduce4x4(p)
+        np.testing.assert_array_equal(ptr, Hp)
+        np.testing.assert_array_equal(row, Hi)
+    finally:
+        K.kkt_destroy_4x4(h)
+
+
+def test_4x4_invalid_jd_rejected():
+    p = W.random_4x4_parts(1, n_x=20, m_c=5, m_d=4)
+    for bad in ("range", "dup"):
+        Jc = p["Jd_colidx"].copy()
+        if bad == "range":
+            Jc[0] = p["n_x"]
+        else:
+            r = int(np.argmax(np.diff(p["Jd_rowptr"]) >= 2))
+            Jc[p["Jd_rowptr"][r] + 1] = Jc[p["Jd_rowptr"][r]]
+        with pytest.raises(K.KKTError) as e:
+            K.kkt_analyse_4x4(p["n_x"], p["m_c"], p["m_d"], p["H_colptr"], p["H_rowidx"], p["J_rowptr"],
+                              p["J_colidx"], p["Jd_rowptr"], Jc, host=True)
+        assert e.value.code == 1

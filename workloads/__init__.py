@@ -314,3 +314,36 @@ def random_4x4_parts(seed, n_x, m_c, m_d):
                 Jd_rowptr=Jdp, Jd_colidx=Jdc, Jd_vals=Jdv,
                 r_xt=rng.standard_normal(n_x), r_s=rng.standard_normal(m_d),
                 r_y=rng.standard_normal(m_c), r_yd=rng.standard_normal(m_d))
+
+
+def grid_4x4_parts(name, m_d_frac=0.25, seed=7):
+    """A 4x4 system (eq. linsys4x4) on a grid workload: H = the workload's
+    H~ (Laplacian + barrier), D_x = 10^U(-2,2), J = the workload's J, and
+    J_d with round(m_d_frac * n) rows of 2-4 N(0,1) entries at distinct
+    columns within +-w of a uniform centre (w = the workload's window),
+    D_s = 10^U(-4,4) (slack barriers spread over eight decades); right-hand
+    sides N(0,1). Draw order: D_x, then per J_d row (centre, count, columns,
+    values), then D_s, then r~_x, r_s, r_yd; r_y is the workload's."""
+    base = make_config(name)
+    rng = np.random.default_rng(seed)
+    n = base.n
+    w = CONFIGS[name]["window"]
+    D_x = 10.0 ** rng.uniform(-2, 2, n)
+    md = int(round(m_d_frac * n))
+    R, Cc, V = [], [], []
+    for r in range(md):
+        c = int(rng.integers(0, n))
+        k = int(rng.integers(2, 5))
+        lo, hi = max(0, c - w), min(n, c + w + 1)
+        cols = np.sort(lo + rng.choice(hi - lo, size=min(k, hi - lo), replace=False))
+        vals = rng.standard_normal(cols.size)
+        R += [r] * cols.size
+        Cc += cols.tolist()
+        V += vals.tolist()
+    Jdp, Jdc, Jdv = _csr(md, R, Cc, V)
+    D_s = 10.0 ** rng.uniform(-4, 4, md)
+    return dict(n_x=n, m_c=base.m, m_d=md, H_colptr=base.H_colptr, H_rowidx=base.H_rowidx, H_vals=base.H_vals,
+                D_x=D_x, D_s=D_s, J_rowptr=base.J_rowptr, J_colidx=base.J_colidx, J_vals=base.J_vals,
+                Jd_rowptr=Jdp, Jd_colidx=Jdc, Jd_vals=Jdv,
+                r_xt=rng.standard_normal(n), r_s=rng.standard_normal(md), r_y=base.r_y,
+                r_yd=rng.standard_normal(md), delta=base.delta, gamma=base.gamma)
