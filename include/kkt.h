@@ -57,10 +57,12 @@ enum { KKT_FP64 = 0, KKT_MIXED = 1 };
 typedef struct kkt_options {
   double gamma;        /* default gamma when kkt_factor gets gamma < 0 (Algorithm 1: 1e4) */
   double delta2;       /* delta_2 of the CG restart on S + delta_2 I (Algorithm 1: 1e-9) */
-  double cg_rtol;      /* CG stop: ||r|| <= cg_rtol ||b_S|| (Sec. 5.1: 1e-12; with KKT_MIXED each
-                          refinement pass only needs ~1e-6, the FP32 factor limits it anyway) */
+  double cg_rtol;      /* CG stop: ||r|| <= cg_rtol ||b_S||; <= 0 selects by precision:
+                          1e-12 for KKT_FP64 (Sec. 5.1), 3e-3 per refinement pass for
+                          KKT_MIXED (the FP32 factor bounds what one pass can reach) */
   int32_t cg_maxit;    /* CG product limit (1000) */
-  int32_t ir_maxit;    /* refinement steps on K_delta after the first solve */
+  int32_t ir_maxit;    /* refinement passes on K_delta after the first solve; < 0 selects
+                          by precision: 3 (KKT_FP64), 10 (KKT_MIXED) */
   double ir_rtol;      /* refine while RR(K_delta) > ir_rtol */
   int32_t precision;   /* KKT_FP64: FP64 factor and solves; KKT_MIXED: FP32 factor and
                           triangular solves, FP64 CG recurrences, residual and refinement */

@@ -319,11 +319,6 @@ class KKTSolver:
         self.n, self.m = int(n), int(m)
         self.nnz_h = int(np.asarray(H_colptr)[-1])
         self.nnz_j = int(np.asarray(J_rowptr)[-1]) if m else 0
-        if options.get("precision") in ("mixed", KKT_MIXED):
-            # each refinement pass only needs a moderately accurate inner solve
-            # with the FP32 factor; FP64 refinement on K_delta does the rest
-            options.setdefault("cg_rtol", 1e-6)
-            options.setdefault("ir_maxit", 10)
         self.opt = kkt_default_options(**options)
         self.h = kkt_analyse(n, m, H_colptr, H_rowidx, J_rowptr, J_colidx, self.opt)
 
@@ -404,9 +399,6 @@ class KKTSolver4x4:
         self.nnz_h = int(np.asarray(H_colptr)[-1])
         self.nnz_j = int(np.asarray(J_rowptr)[-1]) if m_c else 0
         self.nnz_jd = int(np.asarray(Jd_rowptr)[-1]) if m_d else 0
-        if options.get("precision") in ("mixed", KKT_MIXED):
-            options.setdefault("cg_rtol", 1e-6)
-            options.setdefault("ir_maxit", 10)
         self.opt = kkt_default_options(**options)
         self.h = kkt_analyse_4x4(n_x, m_c, m_d, H_colptr, H_rowidx, J_rowptr, J_colidx, Jd_rowptr, Jd_colidx,
                                  self.opt)

@@ -116,9 +116,9 @@ void kkt_default_options(kkt_options* o) {
   std::memset(o, 0, sizeof(*o));
   o->gamma = 1e4;
   o->delta2 = 1e-9;
-  o->cg_rtol = 1e-12;
+  o->cg_rtol = 0;      // by precision, resolved in the analysis
   o->cg_maxit = 1000;
-  o->ir_maxit = 3;
+  o->ir_maxit = -1;     // by precision, resolved in the analysis
   o->ir_rtol = 1e-10;
   o->precision = KKT_FP64;
   o->ordering = 0;
@@ -184,6 +184,12 @@ static kkt_status analyse_host(int64_t n, int64_t m, const int64_t* Hp, const in
     delete h;
     return KKT_ERR_INVALID;
   }
+  // precision-dependent defaults: FP64 solves S to Sec. 5.1's 1e-12 in one
+  // pass (refinement is a safety net); the FP32 factor bounds what one pass
+  // can reach, so a mixed pass stops early and FP64 refinement does the rest
+  const bool f64d = o.precision == KKT_FP64;
+  if (!(h->opt.cg_rtol > 0)) h->opt.cg_rtol = f64d ? 1e-12 : 3e-3;
+  if (h->opt.ir_maxit < 0) h->opt.ir_maxit = f64d ? 3 : 10;
   static const int64_t zero = 0;
   if (m == 0) Jp = &zero;
   RelaxParams rp;

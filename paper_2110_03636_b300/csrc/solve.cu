@@ -10,6 +10,10 @@
 // solve_w columns of one supernode) and "chunks" (row ranges of a piece's
 // off-diagonal block), handed out in a fixed topological order through an
 // atomic ticket. Every wait is bounded (DevStatus::abort on timeout).
+// Signalling: a CTA barrier, then thread 0 alone publishes with a release
+// store or a fence + atomic (the fence is cumulative over the writes the
+// barrier ordered before it); a waiter polls with an acquire load, then
+// barriers its CTA.
 // The CG recurrences, dot products and scalars are FP64 in both precisions;
 // T is the storage/arithmetic type of L and of the triangular-solve vector.
 #include <cuda_runtime.h>
@@ -231,7 +235,6 @@ __device__ bool fwd_head(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>&
       a.v[f + tid] = y;
     }
   }
-  __threadfence();
   __syncthreads();
   if (tid == 0) st_release(&a.fwd_done[p], e);
   if (rn > 0) {
@@ -240,10 +243,11 @@ __device__ bool fwd_head(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>&
     const int32_t* rows = a.sn_rows + a.pc_row[p] + pw;
     T* v = a.v;
     rows_matvec(t.B, tile_cs(rn), d0, rn, pw, t.vec2, t.aux, [&](int i, T o) { atomicAdd(&v[rows[i]], -o); });
-    __threadfence();
     __syncthreads();
-    if (tid == 0)
+    if (tid == 0) {
+      __threadfence();
       for (int64_t q = a.hd_tptr[p]; q < a.hd_tptr[p + 1]; q++) atomicAdd(&a.fwd_arrive[a.hd_tgt[q]], 1);
+    }
   }
   return true;
 }
@@ -276,10 +280,11 @@ __device__ bool fwd_chunk(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>
   const int32_t* rows = a.sn_rows + a.pc_row[p] + r0;
   T* v = a.v;
   rows_matvec(t.B, tile_cs(nr), d0, nr, pw, t.vec, t.aux, [&](int i, T o) { atomicAdd(&v[rows[i]], -o); });
-  __threadfence();
   __syncthreads();
-  if (tid == 0)
+  if (tid == 0) {
+    __threadfence();
     for (int64_t q = a.ch_tptr[c]; q < a.ch_tptr[c + 1]; q++) atomicAdd(&a.fwd_arrive[a.ch_tgt[q]], 1);
+  }
   return true;
 }
 
@@ -321,9 +326,11 @@ __device__ bool bwd_chunk(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>
     s = warp_sum(s);
     if (lane == 0) z[k] = s;
   }
-  __threadfence();
   __syncthreads();
-  if (tid == 0) atomicAdd(&a.bwd_arrive[p], 1);
+  if (tid == 0) {
+    __threadfence();
+    atomicAdd(&a.bwd_arrive[p], 1);
+  }
   return true;
 }
 
@@ -383,7 +390,6 @@ __device__ bool bwd_head(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>&
   }
   __syncthreads();
   for (int i = tid; i < pw; i += blockDim.x) a.v[f + i] = t.vec2[i];
-  __threadfence();
   __syncthreads();
   if (tid == 0) st_release(&a.bwd_done[p], e);
   return true;
@@ -449,10 +455,11 @@ __device__ bool fwd_subtree(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<
     __syncthreads();
   }
   for (int i = tid; i < chi - clo; i += blockDim.x) a.v[clo + i] = xs[i];
-  __threadfence();
   __syncthreads();
-  if (tid == 0)
+  if (tid == 0) {
+    __threadfence();
     for (int64_t q = a.st_tptr[st]; q < a.st_tptr[st + 1]; q++) atomicAdd(&a.fwd_arrive[a.st_tgt[q]], 1);
+  }
   return true;
 }
 
@@ -504,8 +511,7 @@ __device__ bool bwd_subtree(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<
     __syncthreads();
   }
   for (int i = tid; i < chi - clo; i += blockDim.x) a.v[clo + i] = xs[i];
-  __threadfence();
-  __syncthreads();
+  __syncthreads();   // the results are read after the next grid barrier
   return true;
 }
 
