@@ -63,7 +63,9 @@ typedef struct kkt_options {
   int32_t cg_maxit;    /* CG product limit (1000) */
   int32_t ir_maxit;    /* refinement passes on K_delta after the first solve; < 0 selects
                           by precision: 3 (KKT_FP64), 10 (KKT_MIXED) */
-  double ir_rtol;      /* refine while RR(K_delta) > ir_rtol */
+  double ir_rtol;      /* refine while RR(K_delta) > ir_rtol; <= 0 selects by precision:
+                          1e-10 (KKT_FP64), 1e-9 (KKT_MIXED: a tenth of the 1e-8 target, so
+                          the pass count does not hinge on rounding noise) */
   int32_t precision;   /* KKT_FP64: FP64 factor and solves; KKT_MIXED: FP32 factor and
                           triangular solves, FP64 CG recurrences, residual and refinement */
   int32_t ordering;    /* 0 = approximate minimum degree (Sec. 5.3), 1 = natural,
@@ -74,8 +76,9 @@ typedef struct kkt_options {
   int32_t relax_num;   /*   or explicit zeros * relax_den <= relax_num * panel entries */
   int32_t relax_den;
   int32_t relax_wmax;  /*   never beyond this width */
-  int32_t solve_w;     /* column width of the triangular-solve pieces, 32..256;
-                          0 = 128 (KKT_MIXED) / 64 (KKT_FP64) */
+  int32_t solve_w;     /* column width of the triangular-solve pieces, 32..224 (KKT_MIXED) or
+                          32..160 (KKT_FP64): a piece's triangle must fit in 200 KB of shared
+                          memory; 0 = 128 (KKT_MIXED) / 64 (KKT_FP64) */
   int32_t device;      /* CUDA device ordinal */
   int32_t debug_stall_piece; /* test hook, -1 = off: makes one triangular-solve piece wait for
                                 an arrival that never comes, so the bounded wait runs out */
@@ -102,7 +105,7 @@ typedef struct kkt_options {
 enum {
   KKT_K_ASSEMBLE = 0, KKT_K_POTRF = 1, KKT_K_TRSM = 2, KKT_K_PANEL_UPDATE = 3, KKT_K_SYRK = 4,
   KKT_K_EXTEND_ADD = 5, KKT_K_ZERO_U = 6, KKT_K_CG = 7, KKT_K_RESIDUAL = 8, KKT_K_TRI_INV = 9,
-  KKT_K_SYRK_TC = 10, KKT_K_COUNT = 12
+  KKT_K_SYRK_TC = 10, KKT_K_BLOCK = 11, KKT_K_COUNT = 12
 };
 
 /* Result of the last kkt_solve on a handle. */
@@ -224,11 +227,15 @@ kkt_status kkt_get_factor_panels(kkt_handle h, double* panels);
 kkt_status kkt_get_profile(kkt_handle h, double* ms, int64_t* launches, int32_t reset);
 
 /* Cycle counters of the persistent solve kernel summed over its CTAs (thread
- * 0 of each), for handles created with opt.profile = 1; host uint64_t[16]:
+ * 0 of each), for handles created with opt.profile = 1; host uint64_t[32]:
  * [0] item dispatch, [1] dependency waits, [2] bulk-copy waits, [3] whole
  * items, [4] grid barriers, [5] items processed, [6] CTA-launches,
  * [7]/[8] cycles/count of subtree items, [9]/[10] of piece heads,
- * [11]/[12] of row chunks, [13..15] zero. */
+ * [11]/[12] of row chunks, [13]/[14] cycles in / number of the level
+ * loops of subtree items, [15] zero, [16..18] forward subtree items:
+ * staging, levels, publishing; [19..23] forward chunks: metadata and copy
+ * issue, dependency wait, vector load and copy wait, mat-vec, publishing;
+ * [24..31] zero. */
 kkt_status kkt_get_solve_counters(kkt_handle h, uint64_t* out, int32_t reset);
 
 kkt_status kkt_destroy(kkt_handle h);

@@ -100,7 +100,7 @@ EXPORTED = ("kkt_default_options", "kkt_analyse", "kkt_analyse_host", "kkt_facto
             "kkt_destroy", "kkt_status_string", "kkt_analyse_4x4", "kkt_analyse_4x4_host", "kkt_4x4_inner",
             "kkt_get_4x4_pattern", "kkt_factor_4x4", "kkt_solve_4x4", "kkt_destroy_4x4")
 KERNEL_KINDS = ("assemble", "potrf", "trsm", "panel_update", "syrk", "extend_add", "zero_u", "cg_persistent",
-                "residual", "tri_inv", "syrk_tc")
+                "residual", "tri_inv", "syrk_tc", "block")
 
 
 def _check(fn, code):
@@ -253,10 +253,12 @@ def kkt_residual_noalloc(n, m, H_colptr, H_rowidx, H_vals, J_rowptr, J_colidx, J
 
 def kkt_get_solve_counters(h, reset=False):
     """Cycle counters of the persistent solve kernel (profile=1 handles)."""
-    out = np.zeros(16, np.uint64)
+    out = np.zeros(32, np.uint64)
     _check("kkt_get_solve_counters", _lib.kkt_get_solve_counters(h, out.ctypes.data, int(bool(reset))))
     keys = ("dispatch", "dep_wait", "copy_wait", "items", "barriers", "n_items", "cta_launches",
-            "subtree_cycles", "n_subtree", "head_cycles", "n_head", "chunk_cycles", "n_chunk")
+            "subtree_cycles", "n_subtree", "head_cycles", "n_head", "chunk_cycles", "n_chunk",
+            "subtree_level_cycles", "n_subtree_levels", "zero15",
+            "fsub_stage", "fsub_levels", "fsub_publish", "fch_issue", "fch_dep", "fch_load", "fch_matvec", "fch_publish")
     return {k: int(out[i]) for i, k in enumerate(keys)}
 
 

@@ -1,5 +1,7 @@
 // C ABI of the KKT solver: handle management, device memory, and the
 // factor / solve / refinement drivers around the CUDA kernels.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <climits>
@@ -61,7 +63,8 @@ struct kkt_handle_s {
   // pattern / plan on the device
   int32_t *sfirst, *sw, *snr, *sld, *sparent, *rel, *sn_rows, *perm;
   int64_t *srow, *poff, *uoff;
-  int4 *it_potrf, *it_trsm, *it_pupd, *it_syrk, *it_eadd, *it_zero, *it_syrk_tc;
+  int4 *it_potrf, *it_trsm, *it_pupd, *it_syrk, *it_eadd, *it_zero, *it_syrk_tc, *it_block, *it_syrk128, *it_dstore;
+  void* Dsc;
   int64_t *slot_pos, *src_ptr;
   int32_t *srcA, *srcB;
   int32_t *Jcol_perm, *JT_row, *JT_vidx, *Hs_col, *Hs_vidx, *JTo_row, *JTo_vidx, *J_colidx;
@@ -72,6 +75,10 @@ struct kkt_handle_s {
   int64_t *pc_row, *pc_colbase, *pc_inv, *pc_zoff, *hd_tptr, *ch_tptr;
   int32_t *st_first, *st_last, *st_clo, *st_chi, *st_tgt, *sn_piece;
   int64_t* st_tptr;
+  int32_t *st_lptr, *st_lev, *st_sn;
+  ChunkDesc* cdesc;
+  HeadDesc* hdesc;
+  uint8_t* tmaps;
   // values and workspace
   double *Hv, *Jv;
   void *L, *U, *v, *zpart, *Linv;
@@ -98,6 +105,43 @@ struct kkt_handle_s {
   cudaEvent_t cg_a = nullptr, cg_b = nullptr;
 };
 
+// Tensor maps of the pieces whose row tiles are staged as 2-D TMA boxes:
+// the piece's pw columns of its supernode panel (ld rows each, rows past
+// the panel read as zeros), box = pc_box rows x pw columns. The encoder is
+// the driver's, fetched through the runtime (no link against libcuda).
+static bool build_tensor_maps(const Plan& P, void* L, size_t es, std::vector<uint8_t>& out) {
+  static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
+  out.assign((size_t)P.npieces * 128, 0);
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      return false;
+    }
+    encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }
+  for (int64_t p = 0; p < P.npieces; p++) {
+    if (P.pc_box[p] <= 0) continue;
+    const int32_t pw = P.pc_w[p], ld = P.pc_ld[p], box = P.pc_box[p];
+    if (box > 256 || pw > 256 || (box * es) % 16 || ((size_t)ld * es) % 16 || (P.pc_colbase[p] * es) % 16) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)pw};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * es};
+    const cuuint32_t boxd[2] = {(cuuint32_t)box, (cuuint32_t)pw};
+    const cuuint32_t estr[2] = {1, 1};
+    CUtensorMap* m = (CUtensorMap*)(out.data() + (size_t)p * 128);
+    void* g = (char*)L + (size_t)P.pc_colbase[p] * es;
+    if (encode(m, es == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, g, dims, strides,
+               boxd, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  return true;
+}
+
 static kkt_status cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return KKT_OK;
   cudaGetLastError();
@@ -119,7 +163,7 @@ void kkt_default_options(kkt_options* o) {
   o->cg_rtol = 0;      // by precision, resolved in the analysis
   o->cg_maxit = 1000;
   o->ir_maxit = -1;     // by precision, resolved in the analysis
-  o->ir_rtol = 1e-10;
+  o->ir_rtol = 0;       // by precision, resolved in the analysis
   o->precision = KKT_FP64;
   o->ordering = 0;
   o->relax_small = 16;
@@ -190,6 +234,7 @@ static kkt_status analyse_host(int64_t n, int64_t m, const int64_t* Hp, const in
   const bool f64d = o.precision == KKT_FP64;
   if (!(h->opt.cg_rtol > 0)) h->opt.cg_rtol = f64d ? 1e-12 : 3e-3;
   if (h->opt.ir_maxit < 0) h->opt.ir_maxit = f64d ? 3 : 10;
+  if (!(h->opt.ir_rtol > 0)) h->opt.ir_rtol = f64d ? 1e-10 : 1e-9;
   static const int64_t zero = 0;
   if (m == 0) Jp = &zero;
   RelaxParams rp;
@@ -202,7 +247,9 @@ static kkt_status analyse_host(int64_t n, int64_t m, const int64_t* Hp, const in
   const bool f64o = o.precision == KKT_FP64;
   const int sw = o.solve_w > 0 ? o.solve_w : (f64o ? 64 : 128);
   const int ent = o.solve_ent > 0 ? o.solve_ent : (f64o ? 8192 : 16384);
-  if (build_plan(h->S, Hp, Hi, Jp, Ji, sw, ent, ent, !f64o && o.tensor_cores, h->P) != 0) {
+  // the triangle inversion holds a piece's sw x sw triangle in shared memory
+  if ((size_t)sw * sw * (f64o ? 8 : 4) > (size_t)200 * 1024) { delete h; return KKT_ERR_INVALID; }
+  if (build_plan(h->S, Hp, Hi, Jp, Ji, sw, ent, ent, !f64o && o.tensor_cores, !f64o, h->P) != 0) {
     delete h;
     return KKT_ERR_INVALID;
   }
@@ -251,6 +298,7 @@ kkt_status kkt_analyse(int64_t n, int64_t m, const int64_t* Hp, const int32_t* H
   h->it_potrf = as_int4(P.it_potrf); h->it_zero = as_int4(P.it_zero);
   h->it_trsm = as_int4(P.it_trsm); h->it_pupd = as_int4(P.it_pupd);
   h->it_syrk = as_int4(P.it_syrk); h->it_eadd = as_int4(P.it_eadd); h->it_syrk_tc = as_int4(P.it_syrk_tc);
+  h->it_block = as_int4(P.it_block); h->it_syrk128 = as_int4(P.it_syrk128); h->it_dstore = as_int4(P.it_dstore);
   h->slot_pos = A.upload(P.slot_pos); h->src_ptr = A.upload(P.src_ptr);
   h->srcA = A.upload(P.srcA); h->srcB = A.upload(P.srcB);
   h->Jcol_perm = A.upload(P.Jcol_perm); h->JT_ptr = A.upload(P.JT_ptr);
@@ -269,14 +317,29 @@ kkt_status kkt_analyse(int64_t n, int64_t m, const int64_t* Hp, const int32_t* H
   h->fwd_items = A.upload(P.fwd_items); h->bwd_items = A.upload(P.bwd_items);
   h->st_first = A.upload(P.st_first); h->st_last = A.upload(P.st_last); h->st_clo = A.upload(P.st_clo);
   h->st_chi = A.upload(P.st_chi); h->st_tgt = A.upload(P.st_tgt); h->st_tptr = A.upload(P.st_tptr);
+  h->st_lptr = A.upload(P.st_lptr); h->st_lev = A.upload(P.st_lev); h->st_sn = A.upload(P.st_sn);
+  {
+    std::vector<HeadDesc> hd = P.hdesc;
+    for (size_t p = 0; p < hd.size(); p++) hd[p].need = P.pc_need[p];
+    h->hdesc = A.upload(hd);
+    h->cdesc = A.upload(P.cdesc);
+  }
   h->sn_piece = A.upload(P.sn_piece);
   const size_t es = f64 ? sizeof(double) : sizeof(float);
   h->Hv = A.alloc<double>(h->nnzH); h->Jv = A.alloc<double>(h->nnzJ);
   h->L = A.alloc<char>(es * (size_t)P.panel_total);
   h->U = A.alloc<char>(es * (size_t)P.u_total);
+  h->Dsc = A.alloc<char>(es * (size_t)P.dsc_total);
   h->v = A.alloc<char>(es * (size_t)n);
   h->zpart = A.alloc<char>(es * (size_t)P.z_total);
   h->Linv = A.alloc<char>(es * (size_t)P.inv_total);
+  {
+    std::vector<uint8_t> maps;
+    if (!A.failed) {
+      if (!build_tensor_maps(P, h->L, es, maps)) { kkt_destroy(h); return KKT_ERR_CUDA; }
+      h->tmaps = A.upload(maps);
+    }
+  }
   h->rhx = A.alloc<double>(n);
   h->p = A.alloc<double>(m); h->r = A.alloc<double>(m); h->y = A.alloc<double>(m);
   h->q = A.alloc<double>(m); h->bS = A.alloc<double>(m);
@@ -287,7 +350,7 @@ kkt_status kkt_analyse(int64_t n, int64_t m, const int64_t* Hp, const int32_t* H
   h->counters = A.alloc<int>(4 * (size_t)P.npieces + 8);
   h->dst = A.alloc<DevStatus>(1);
   h->d_dg = A.alloc<double>(2);
-  h->d_instr = A.alloc<unsigned long long>(16);
+  h->d_instr = A.alloc<unsigned long long>(32);
   if (A.failed) { kkt_destroy(h); return KKT_ERR_OOM; }
   if (cudaMallocHost(&h->hst, sizeof(DevStatus)) != cudaSuccess) { cudaGetLastError(); h->hst = nullptr; kkt_destroy(h); return KKT_ERR_OOM; }
   if (cudaMallocHost(&h->h_dg, 2 * sizeof(double)) != cudaSuccess) { cudaGetLastError(); h->h_dg = nullptr; kkt_destroy(h); return KKT_ERR_OOM; }
@@ -305,7 +368,7 @@ kkt_status kkt_analyse(int64_t n, int64_t m, const int64_t* Hp, const int32_t* H
       return KKT_ERR_CUDA;
     }
     h->profp = &h->prof;
-    if (cudaMemset(h->d_instr, 0, 16 * sizeof(unsigned long long)) != cudaSuccess) { cudaGetLastError(); kkt_destroy(h); return KKT_ERR_CUDA; }
+    if (cudaMemset(h->d_instr, 0, 32 * sizeof(unsigned long long)) != cudaSuccess) { cudaGetLastError(); kkt_destroy(h); return KKT_ERR_CUDA; }
   }
   h->on_device = true;
   *out = h;
@@ -334,10 +397,11 @@ static cudaError_t factor_launches(kkt_handle h, cudaStream_t st, Prof* prof) {
   a.sfirst = h->sfirst; a.sw = h->sw; a.snr = h->snr; a.sld = h->sld; a.sparent = h->sparent; a.rel = h->rel;
   a.srow = h->srow; a.poff = h->poff; a.uoff = h->uoff;
   a.Hv = h->Hv; a.Jv = h->Jv;
-  a.L = (T*)h->L; a.U = (T*)h->U; a.st = h->dst;
+  a.L = (T*)h->L; a.U = (T*)h->U; a.Dsc = (T*)h->Dsc; a.st = h->dst;
   FacLists fl;
   fl.it_potrf = h->it_potrf; fl.it_trsm = h->it_trsm; fl.it_pupd = h->it_pupd;
   fl.it_syrk = h->it_syrk; fl.it_eadd = h->it_eadd; fl.it_zero = h->it_zero; fl.it_syrk_tc = h->it_syrk_tc;
+  fl.it_block = h->it_block; fl.it_syrk128 = h->it_syrk128; fl.it_dstore = h->it_dstore;
   fl.slot_pos = h->slot_pos; fl.src_ptr = h->src_ptr; fl.srcA = h->srcA; fl.srcB = h->srcB;
   fl.nslot = (int64_t)h->P.slot_pos.size();
   fl.panel_total = h->P.panel_total; fl.u_total = h->P.u_total;
@@ -421,6 +485,8 @@ static SolveArgs<T> solve_args(kkt_handle h) {
   a.npieces = P.npieces;
   a.st_first = h->st_first; a.st_last = h->st_last; a.st_clo = h->st_clo; a.st_chi = h->st_chi;
   a.st_tgt = h->st_tgt; a.st_tptr = h->st_tptr; a.sn_piece = h->sn_piece;
+  a.st_lptr = h->st_lptr; a.st_lev = h->st_lev; a.st_sn = h->st_sn;
+  a.cdesc = h->cdesc; a.hdesc = h->hdesc; a.tmaps = h->tmaps;
   a.sfirst = h->sfirst; a.sw_ = h->sw; a.snr = h->snr; a.sld = h->sld; a.srow = h->srow; a.poff = h->poff;
   a.L = (const T*)h->L;
   a.J_rowptr = h->J_rowptr; a.Jcol_perm = h->Jcol_perm; a.Jv = h->Jv;
@@ -610,7 +676,7 @@ kkt_status kkt_get_symbolic(kkt_handle h, int32_t* amd, int32_t* perm, int32_t* 
 
 kkt_status kkt_get_profile(kkt_handle h, double* ms, int64_t* launches, int32_t reset) {
   if (!h) return KKT_ERR_INVALID;
-  static_assert(KKT_K_SYRK_TC == KKT_K_SYRK_TC_PROF, "profile slots");
+  static_assert(KKT_K_SYRK_TC == KKT_K_SYRK_TC_PROF && KKT_K_BLOCK == KKT_K_BLOCK_PROF, "profile slots");
   for (int k = 0; k < KKT_K_COUNT; k++) {
     if (ms) ms[k] = h->prof.ms[k];
     if (launches) launches[k] = h->prof.n[k];
@@ -625,8 +691,8 @@ kkt_status kkt_get_solve_counters(kkt_handle h, uint64_t* out, int32_t reset) {
   if (!h || !out) return KKT_ERR_INVALID;
   if (!h->on_device) return KKT_ERR_STATE;
   CK(cudaSetDevice(h->device));
-  CK(cudaMemcpy(out, h->d_instr, 16 * sizeof(uint64_t), cudaMemcpyDeviceToHost));
-  if (reset) CK(cudaMemset(h->d_instr, 0, 16 * sizeof(uint64_t)));
+  CK(cudaMemcpy(out, h->d_instr, 32 * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+  if (reset) CK(cudaMemset(h->d_instr, 0, 32 * sizeof(uint64_t)));
   return KKT_OK;
 }
 

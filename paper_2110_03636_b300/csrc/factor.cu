@@ -119,6 +119,103 @@ __global__ void __launch_bounds__(kTR) k_trsm(const int4* __restrict__ items, in
   }
 }
 
+// ------------------------------------------------- fused block step
+// Right-looking step for column block kb of each listed front, one CTA per
+// (front, tile of kTR rows below the block), after the in-panel updates of
+// the earlier blocks:
+//   D = chol(A[blk, blk]),   L[r, blk] = A[r, blk] D^-T   for the tile's rows r.
+// Every CTA of a front factors the same D (same inputs, same operation
+// order, so the same bits); tile 0 keeps it in the level's scratch slot
+// (k_dstore moves it into the panel after the level's last step, so no
+// CTA reads a half-written diagonal tile). Replaces the separate POTRF and
+// TRSM launches.
+template <typename T>
+__device__ __forceinline__ void warp_potrf32(T (&D)[kPB][kPB + 1], int bw, int fail_base, DevStatus* st) {
+  // lane i holds row i of the tile
+  const int lane = threadIdx.x & 31;
+  T d[kPB];
+#pragma unroll
+  for (int k = 0; k < kPB; k++) d[k] = (lane < bw && k <= lane) ? D[lane][k] : T(lane == k ? 1 : 0);
+#pragma unroll
+  for (int j = 0; j < kPB; j++) {
+    if (j < bw) {
+      T djj = __shfl_sync(0xffffffffu, d[j], j);
+      if (!(djj > T(0)) || !isfinite((double)djj)) {
+        if (lane == 0) atomicMin(&st->fail_col, fail_base + j);
+        djj = T(1);
+      }
+      const T s = sqrt(djj);
+      if (lane == j) d[j] = s;
+      if (lane > j) d[j] = d[j] / s;
+#pragma unroll
+      for (int k = j + 1; k < kPB; k++) {
+        const T lkj = __shfl_sync(0xffffffffu, d[j], k);
+        if (lane >= k) d[k] -= d[j] * lkj;
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kPB; k++)
+    if (lane < bw && k <= lane) D[lane][k] = d[k];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTR) k_block(const int4* __restrict__ items, int kb, FacArgs<T> a) {
+  __shared__ T D[kPB][kPB + 1];
+  const int4 it = items[blockIdx.x];
+  const int s = it.x, t = it.y;
+  const int w = a.sw[s], nr = a.snr[s], ld = a.sld[s];
+  const int c0 = kb * kPB;
+  const int bw = min(kPB, w - c0);
+  T* P = a.L + a.poff[s];
+  const int tid = threadIdx.x;
+  const int r = c0 + bw + t * kTR + tid;
+  const bool row = r < nr;
+  T x[kPB];
+#pragma unroll
+  for (int j = 0; j < kPB; j++) x[j] = (row && j < bw) ? P[(int64_t)r + (int64_t)(c0 + j) * ld] : T(0);
+  for (int e = tid; e < kPB * kPB; e += kTR) {
+    const int i = e % kPB, j = e / kPB;
+    D[i][j] = (i < bw && j <= i) ? P[(int64_t)(c0 + i) + (int64_t)(c0 + j) * ld] : T(0);
+  }
+  __syncthreads();
+  if (tid < 32) warp_potrf32(D, bw, a.sfirst[s] + c0, a.st);
+  __syncthreads();
+  if (t == 0) {
+    T* dst = a.Dsc + (int64_t)it.z * (kPB * kPB);
+    for (int e = tid; e < kPB * kPB; e += kTR) dst[e] = D[e % kPB][e / kPB];
+  }
+  if (row) {
+#pragma unroll
+    for (int j = 0; j < kPB; j++) {
+      if (j < bw) {
+        T sacc = x[j];
+#pragma unroll
+        for (int k = 0; k < j; k++) sacc -= x[k] * D[j][k];
+        x[j] = sacc / D[j][j];
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kPB; j++)
+      if (j < bw) P[(int64_t)r + (int64_t)(c0 + j) * ld] = x[j];
+  }
+}
+
+// The level's factored diagonal tiles from the scratch into the panels.
+template <typename T>
+__global__ void __launch_bounds__(256) k_dstore(const int4* __restrict__ items, FacArgs<T> a) {
+  const int4 it = items[blockIdx.x];
+  const int s = it.x, c0 = it.y * kPB;
+  const int w = a.sw[s], ld = a.sld[s];
+  const int bw = min(kPB, w - c0);
+  T* P = a.L + a.poff[s];
+  const T* src = a.Dsc + (int64_t)it.z * (kPB * kPB);
+  for (int e = threadIdx.x; e < kPB * kPB; e += blockDim.x) {
+    const int i = e % kPB, j = e / kPB;
+    if (i < bw && j <= i) P[(int64_t)(c0 + i) + (int64_t)(c0 + j) * ld] = src[e];
+  }
+}
+
 // ------------------------------------------------------ clear update matrices
 template <typename T>
 __global__ void __launch_bounds__(256) k_zero_u(const int4* __restrict__ items, FacArgs<T> a) {
@@ -226,6 +323,85 @@ __global__ void __launch_bounds__(256) k_syrk(const int4* __restrict__ items, Fa
       const int gi = i0 + tx + 16 * x, gj = j0 + ty + 16 * y;
       if (gi < rb && gj < rb && gi >= gj) U[(int64_t)gi + (int64_t)gj * rb] -= acc[x][y];
     }
+}
+
+// ----------------------------------------------------- SYRK, 128 x 128 tiles
+// FP32 fronts with rb >= kBigRows: U_s -= L21 L21^T on 128 x 128 tiles
+// (ti >= tj), 256 threads with 8 x 8 register tiles (rows tx*4 + {0..3, 64..67},
+// columns ty*4 + {0..3, 64..67}, tx = tid % 16, ty = tid / 16), K staged 16
+// columns at a time through two shared-memory buffers.
+__global__ void __launch_bounds__(256) k_syrk128(const int4* __restrict__ items, FacArgs<float> a) {
+  constexpr int KC = 16, TS = 128;
+  __shared__ __align__(16) float As[2][KC][TS];
+  __shared__ __align__(16) float Bs[2][KC][TS];
+  const int4 it = items[blockIdx.x];
+  const int s = it.x, ti = it.y, tj = it.z;
+  const int w = a.sw[s], nr = a.snr[s], ld = a.sld[s];
+  const int rb = nr - w;
+  const float* P = a.L + a.poff[s];
+  float* U = a.U + a.uoff[s];
+  const int i0 = ti * TS, j0 = tj * TS;
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  float acc[8][8];
+#pragma unroll
+  for (int x = 0; x < 8; x++)
+#pragma unroll
+    for (int y = 0; y < 8; y++) acc[x][y] = 0.f;
+  // each thread stages 8 entries of A and 8 of B per chunk: row tid % 128,
+  // columns (tid / 128) * 8 + {0..7}
+  const int lr = tid % TS, lk = (tid / TS) * 8;
+  const bool ra = i0 + lr < rb, rbv = j0 + lr < rb;
+  const float* pa = P + (w + i0 + lr);
+  const float* pb = P + (w + j0 + lr);
+  float va[8], vb[8];
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+      const int k = k0 + lk + q;
+      va[q] = (ra && k < w) ? pa[(int64_t)k * ld] : 0.f;
+      vb[q] = (rbv && k < w) ? pb[(int64_t)k * ld] : 0.f;
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+      As[buf][lk + q][lr] = va[q];
+      Bs[buf][lk + q][lr] = vb[q];
+    }
+  };
+  load(0);
+  store(0);
+  __syncthreads();
+  int buf = 0;
+  for (int k0 = 0; k0 < w; k0 += KC) {
+    const bool more = k0 + KC < w;
+    if (more) load(k0 + KC);
+#pragma unroll
+    for (int k = 0; k < KC; k++) {
+      const float4 a0 = *(const float4*)&As[buf][k][tx * 4];
+      const float4 a1 = *(const float4*)&As[buf][k][tx * 4 + 64];
+      const float4 b0 = *(const float4*)&Bs[buf][k][ty * 4];
+      const float4 b1 = *(const float4*)&Bs[buf][k][ty * 4 + 64];
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int x = 0; x < 8; x++)
+#pragma unroll
+        for (int y = 0; y < 8; y++) acc[x][y] += av[x] * bv[y];
+    }
+    if (more) store(buf ^ 1);
+    __syncthreads();
+    buf ^= 1;
+  }
+#pragma unroll
+  for (int y = 0; y < 8; y++) {
+    const int gj = j0 + ty * 4 + (y & 3) + (y >> 2) * 64;
+#pragma unroll
+    for (int x = 0; x < 8; x++) {
+      const int gi = i0 + tx * 4 + (x & 3) + (x >> 2) * 64;
+      if (gi < rb && gj < rb && gi >= gj) U[(int64_t)gi + (int64_t)gj * rb] -= acc[x][y];
+    }
+  }
 }
 
 // --------------------------------------------------------------- extend-add
@@ -442,6 +618,15 @@ __global__ void __launch_bounds__(128) k_syrk_tc(const int4* __restrict__ items,
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
 }
 
+static cudaError_t launch_syrk128(const int4* items, int64_t cnt, const FacArgs<float>& a, cudaStream_t st) {
+  k_syrk128<<<(unsigned)cnt, 256, 0, st>>>(items, a);
+  return cudaGetLastError();
+}
+template <typename T>
+static cudaError_t launch_syrk128(const int4*, int64_t, const FacArgs<T>&, cudaStream_t) {
+  return cudaErrorNotSupported;   // FP64 fronts keep the 64 x 64 tiles
+}
+
 static cudaError_t launch_syrk_tc(const int4* items, int64_t cnt, const FacArgs<float>& a, cudaStream_t st) {
   const int smem = 6 * (int)tc::TILE;   // 96 KB: two CTAs (2 x 128 tensor-memory columns) per SM
   cudaError_t e = cudaFuncSetAttribute(k_syrk_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -543,8 +728,16 @@ cudaError_t launch_factor(const FacArgs<T>& a, const FacLists& fl, const double*
       case 6:
         if ((e = launch_syrk_tc(fl.it_syrk_tc + L.off, L.cnt, a, st))) return e;
         break;
+      case 7: k_block<T><<<(unsigned)L.cnt, kTR, 0, st>>>(fl.it_block + L.off, L.kb, a); break;
+      case 8:
+        if ((e = launch_syrk128(fl.it_syrk128 + L.off, L.cnt, a, st))) return e;
+        break;
+      case 9: k_dstore<T><<<(unsigned)L.cnt, 256, 0, st>>>(fl.it_dstore + L.off, a); break;
     }
-    if ((e = prof_end(prof, L.kind == 6 ? KKT_K_SYRK_TC_PROF : 1 + L.kind, st))) return e;
+    // kinds 0..5 -> profile slots 1..6; 8 (128-tile SYRK) shares the SYRK slot
+    const int slot = L.kind == 6 ? KKT_K_SYRK_TC_PROF
+                                 : ((L.kind == 7 || L.kind == 9) ? KKT_K_BLOCK_PROF : (L.kind == 8 ? 4 : 1 + L.kind));
+    if ((e = prof_end(prof, slot, st))) return e;
   }
   return cudaGetLastError();
 }

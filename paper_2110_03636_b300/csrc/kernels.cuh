@@ -17,12 +17,14 @@ struct FacArgs {
   const double *Hv, *Jv;
   T* L;
   T* U;
+  T* Dsc;    // factored diagonal tiles of the current level's block steps (kPB x kPB each)
   DevStatus* st;
 };
 
 // Optional per-launch timing (profile mode): events around each launch,
 // elapsed time accumulated per kernel kind.
 constexpr int KKT_K_SYRK_TC_PROF = 10;   // profile slot of the tensor-core SYRK
+constexpr int KKT_K_BLOCK_PROF = 11;     // profile slot of the fused block step
 struct Prof {
   cudaEvent_t a = nullptr, b = nullptr;
   double ms[12] = {0};
@@ -32,7 +34,8 @@ cudaError_t prof_begin(Prof* pr, cudaStream_t st);
 cudaError_t prof_end(Prof* pr, int kind, cudaStream_t st);
 
 struct FacLists {
-  const int4 *it_potrf, *it_trsm, *it_pupd, *it_syrk, *it_eadd, *it_zero, *it_syrk_tc;
+  const int4 *it_potrf, *it_trsm, *it_pupd, *it_syrk, *it_eadd, *it_zero, *it_syrk_tc, *it_block, *it_syrk128,
+      *it_dstore;
   const int64_t *slot_pos, *src_ptr;
   const int32_t *srcA, *srcB;
   int64_t nslot, panel_total, u_total;
@@ -71,6 +74,10 @@ struct SolveArgs {
   // small subtrees solved whole by one CTA
   const int32_t *st_first, *st_last, *st_clo, *st_chi, *st_tgt, *sn_piece;
   const int64_t* st_tptr;
+  const int32_t *st_lptr, *st_lev, *st_sn;
+  const ChunkDesc* cdesc;
+  const HeadDesc* hdesc;
+  const uint8_t* tmaps;     // one 128-byte tensor map per piece (TMA pieces only)
   const int32_t *sfirst, *sw_, *snr, *sld;
   const int64_t *srow, *poff;
   const T* L;

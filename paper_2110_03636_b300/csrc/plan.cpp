@@ -8,7 +8,7 @@ namespace kkt {
 static inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const int64_t* Jp,
-               const int32_t* Ji, int32_t solve_w, int32_t ent, int32_t ent0, bool tc_syrk, Plan& P) {
+               const int32_t* Ji, int32_t solve_w, int32_t ent, int32_t ent0, bool tc_syrk, bool f32, Plan& P) {
   P = Plan();
   const int64_t n = S.n, m = S.m, ns = S.ns;
   P.n = n; P.m = m; P.ns = ns;
@@ -113,21 +113,41 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
     if (c3) P.launches.push_back({4, 0, o3, c3});
     int32_t wmax = 0;
     for (int32_t s : F) wmax = std::max(wmax, P.sw[s]);
+    // per 32-column block step: one fused POTRF + TRSM launch (every front
+    // with columns left gets its row tiles below the block, at least one
+    // item; every item factors the block's diagonal tile itself, tile 0
+    // keeps the result in a per-level scratch slot, and one launch after the
+    // level's last step stores the tiles into the panels, since a panel
+    // write during the step would race with the other tiles' reads of A),
+    // then the right-looking update of the later panel columns. FP64
+    // fronts (f32 off) keep separate POTRF and TRSM launches: the
+    // fused kernel's register footprint costs more than the launch it saves.
+    int32_t slot = 0;
+    const int64_t od = (int64_t)P.it_dstore.size() / 4;
     for (int32_t kb = 0; kb * kPB < wmax; kb++) {
-      const int64_t od = (int64_t)P.it_potrf.size() / 4;
-      for (int32_t s : F)
-        if (kb * kPB < P.sw[s]) P.it_potrf.insert(P.it_potrf.end(), {s, 0, 0, 0});
-      P.launches.push_back({0, kb, od, (int64_t)P.it_potrf.size() / 4 - od});
-      const int64_t o0 = (int64_t)P.it_trsm.size() / 4;
+      const int64_t ob = (int64_t)P.it_block.size() / 4;
+      const int64_t opo = (int64_t)P.it_potrf.size() / 4, otr = (int64_t)P.it_trsm.size() / 4;
       for (int32_t s : F) {
         const int32_t c0 = kb * kPB;
         if (c0 >= P.sw[s]) continue;
         const int32_t bw = std::min(kPB, P.sw[s] - c0);
         const int64_t below = P.snr[s] - c0 - bw;
-        for (int64_t t = 0; t < cdiv(below, kTR); t++) P.it_trsm.insert(P.it_trsm.end(), {s, (int32_t)t, 0, 0});
+        const int64_t nt = std::max<int64_t>(1, cdiv(below, kTR));
+        if (f32) {
+          for (int64_t t = 0; t < nt; t++) P.it_block.insert(P.it_block.end(), {s, (int32_t)t, slot, 0});
+          P.it_dstore.insert(P.it_dstore.end(), {s, kb, slot, 0});
+          slot++;
+        } else {
+          P.it_potrf.insert(P.it_potrf.end(), {s, 0, 0, 0});
+          for (int64_t t = 0; t < cdiv(below, kTR); t++) P.it_trsm.insert(P.it_trsm.end(), {s, (int32_t)t, 0, 0});
+        }
       }
-      const int64_t c0n = (int64_t)P.it_trsm.size() / 4 - o0;
-      if (c0n) P.launches.push_back({1, kb, o0, c0n});
+      const int64_t cb = (int64_t)P.it_block.size() / 4 - ob;
+      if (cb) P.launches.push_back({7, kb, ob, cb});
+      const int64_t cpo = (int64_t)P.it_potrf.size() / 4 - opo, ctr = (int64_t)P.it_trsm.size() / 4 - otr;
+      if (cpo) P.launches.push_back({0, kb, opo, cpo});
+      if (ctr) P.launches.push_back({1, kb, otr, ctr});
+      // right-looking update of the panel columns after the block
       const int64_t o1 = (int64_t)P.it_pupd.size() / 4;
       for (int32_t s : F) {
         const int32_t c0 = kb * kPB;
@@ -143,18 +163,25 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
       const int64_t c1 = (int64_t)P.it_pupd.size() / 4 - o1;
       if (c1) P.launches.push_back({2, kb, o1, c1});
     }
-    const int64_t o2 = (int64_t)P.it_syrk.size() / 4, o6 = (int64_t)P.it_syrk_tc.size() / 4;
+    P.dsc_total = std::max(P.dsc_total, (int64_t)slot * kPB * kPB);
+    const int64_t cd = (int64_t)P.it_dstore.size() / 4 - od;
+    if (cd) P.launches.push_back({9, 0, od, cd});
+    const int64_t o2 = (int64_t)P.it_syrk.size() / 4, o6 = (int64_t)P.it_syrk_tc.size() / 4,
+                  o8 = (int64_t)P.it_syrk128.size() / 4;
     for (int32_t s : F) {
       const int64_t rb = P.snr[s] - P.sw[s];
       const bool tcs = tc_syrk && rb >= kTcMinRows;
-      const int64_t tile = tcs ? 128 : kST;
+      const bool big = !tcs && f32 && rb >= kBigRows;
+      const int64_t tile = (tcs || big) ? 128 : kST;
       const int64_t nt = cdiv(rb, tile);
-      auto& list = tcs ? P.it_syrk_tc : P.it_syrk;
+      auto& list = tcs ? P.it_syrk_tc : (big ? P.it_syrk128 : P.it_syrk);
       for (int64_t ti = 0; ti < nt; ti++)
         for (int64_t tj = 0; tj <= ti; tj++) list.insert(list.end(), {s, (int32_t)ti, (int32_t)tj, 0});
     }
-    const int64_t c2 = (int64_t)P.it_syrk.size() / 4 - o2, c6 = (int64_t)P.it_syrk_tc.size() / 4 - o6;
+    const int64_t c2 = (int64_t)P.it_syrk.size() / 4 - o2, c6 = (int64_t)P.it_syrk_tc.size() / 4 - o6,
+                  c8 = (int64_t)P.it_syrk128.size() / 4 - o8;
     if (c6) P.launches.push_back({6, 0, o6, c6});
+    if (c8) P.launches.push_back({8, 0, o8, c8});
     if (c2) P.launches.push_back({3, 0, o2, c2});
   }
   // ---------------------------------------------------------- assembly map
@@ -282,6 +309,27 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
     k = q;
   }
   P.nsub = (int64_t)P.st_first.size();
+  {
+    std::vector<int32_t> lvl(ns, 0);
+    P.st_lptr.assign(1, 0);
+    for (int64_t t = 0; t < P.nsub; t++) {
+      const int32_t first = P.st_first[t], last = P.st_last[t];
+      int32_t top = 0;
+      for (int32_t s = first; s <= last; s++) lvl[s] = 0;
+      for (int32_t s = first; s <= last; s++) {       // postorder: children before parents
+        const int32_t p = P.sparent[s];
+        if (p >= first && p <= last) lvl[p] = std::max(lvl[p], lvl[s] + 1);
+        top = std::max(top, lvl[s]);
+      }
+      for (int32_t L = 0; L <= top; L++) {
+        P.st_lev.push_back((int32_t)P.st_sn.size());
+        for (int32_t s = first; s <= last; s++)
+          if (lvl[s] == L) P.st_sn.push_back(s);
+      }
+      P.st_lev.push_back((int32_t)P.st_sn.size());
+      P.st_lptr.push_back((int32_t)P.st_lev.size());
+    }
+  }
   // ---------------------------------------------------------- solve DAG
   P.solve_w = solve_w;
   P.ent = ent;
@@ -314,6 +362,9 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
   }
   P.npieces = (int64_t)P.pc_first.size();
   P.pc_inv.push_back(P.inv_total);               // [npieces + 1]: sizes by difference
+  // the solve kernel's per-warp subtree scratch (8 x 160 entries) lives in
+  // its gathered-vector region of max_rows + 256 entries
+  if (P.max_rows + 256 < 8 * 160) return 2;
   // each subtree's staged ranges fit the solve kernel's tile regions
   for (int64_t t = 0; t < P.nsub; t++) {
     const int32_t s0 = P.st_first[t], s1 = P.st_last[t];
@@ -325,6 +376,7 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
   P.pc_nchunk.resize(P.npieces);
   P.pc_rc0.resize(P.npieces);
   P.pc_need.assign(P.npieces, 0);
+  P.pc_box.assign(P.npieces, 0);
   std::vector<int32_t> tg;
   auto targets = [&](int64_t p, int32_t r0, int32_t nr, std::vector<int32_t>& out) {
     out.clear();
@@ -344,7 +396,10 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
       P.pc_zoff[p] = P.z_total;
       continue;
     }
-    const int32_t rc0 = rows_for(ent0, pw), rc = rows_for(ent, pw);
+    const bool tma = pw >= kTmaMinWidth;
+    const int32_t rc0 = tma ? std::min(rows_for(ent0, pw), kTmaRows) : rows_for(ent0, pw);
+    const int32_t rc = tma ? std::min(rows_for(ent, pw), kTmaRows) : rows_for(ent, pw);
+    P.pc_box[p] = tma ? std::max(rc0, rc) + 4 : 0;
     const int32_t r0n = std::min(below, rc0);
     P.pc_rc0[p] = r0n;
     P.hd_tptr.push_back((int64_t)P.hd_tgt.size());
@@ -370,6 +425,30 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
   P.hd_tptr.push_back((int64_t)P.hd_tgt.size());
   P.nchunks = (int64_t)P.ch_piece.size();
   P.ch_tptr.push_back((int64_t)P.ch_tgt.size());
+  P.cdesc.resize(P.nchunks);
+  for (int64_t c = 0; c < P.nchunks; c++) {
+    ChunkDesc& d = P.cdesc[c];
+    const int32_t p = P.ch_piece[c];
+    d.p = p; d.r0 = P.ch_r0[c]; d.nr = P.ch_nr[c]; d.pw = P.pc_w[p];
+    d.f = P.pc_first[p]; d.ld = P.pc_ld[p]; d.c = P.pc_c[p]; d.k = P.ch_k[c];
+    d.colbase = P.pc_colbase[p]; d.rowbase = P.pc_row[p] + d.r0;
+    d.tp0 = P.ch_tptr[c]; d.tp1 = P.ch_tptr[c + 1];
+    d.zoff = P.pc_zoff[p] + (int64_t)d.k * d.pw;
+    d.tma = P.pc_box[p] > 0 ? 1 : 0;
+    d.cs = d.tma ? P.pc_box[p] : ((d.nr + 3) & ~3) + 8;
+  }
+  P.hdesc.resize(P.npieces);
+  for (int64_t p = 0; p < P.npieces; p++) {
+    HeadDesc& d = P.hdesc[p];
+    d.pw = P.pc_w[p]; d.f = P.pc_first[p]; d.rn = P.pc_rc0[p]; d.need = 0;   // need: set below
+    d.c = P.pc_c[p]; d.ld = P.pc_ld[p]; d.nch = P.pc_nchunk[p];
+    d.tma = P.pc_box[p] > 0 ? 1 : 0; d.pad = 0;
+    d.cs = d.tma ? P.pc_box[p] : ((d.rn + 3) & ~3) + 8;
+    d.colbase = P.pc_colbase[p]; d.rowbase = P.pc_row[p];
+    d.inv0 = P.pc_inv[p]; d.inv1 = P.pc_inv[p + 1];
+    d.tp0 = P.hd_tptr[p]; d.tp1 = P.hd_tptr[p + 1];
+    d.zoff = P.pc_zoff[p];
+  }
   for (int64_t t = 0; t < P.nsub; t++) {
     P.st_tptr.push_back((int64_t)P.st_tgt.size());
     tg.clear();

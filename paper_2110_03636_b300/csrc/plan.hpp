@@ -9,6 +9,37 @@
 
 namespace kkt {
 
+// Everything a triangular-solve work item needs about its piece, packed so
+// the solve kernel fetches it in one round trip (16-byte aligned vectors).
+struct alignas(16) ChunkDesc {
+  int32_t p, r0, nr, pw;        // piece, first row (piece-local), rows, piece width
+  int32_t f, ld, c, k;          // piece's first column, panel ld, column offset in the supernode, chunk index
+  int64_t colbase, rowbase;     // piece's first L entry; sn_rows index of the chunk's first row
+  int64_t tp0, tp1;             // target pieces [tp0, tp1) in ch_tgt
+  int64_t zoff;                 // backward partial sums of this chunk
+  int32_t cs, tma;              // tile column stride in shared memory; 1 = one 2-D TMA box (else per column)
+};
+struct alignas(16) HeadDesc {
+  int32_t pw, f, rn, need;      // width, first column, rows of chunk 0, arrivals expected per sweep
+  int32_t c, ld, nch, cs;       // column offset in the supernode, panel ld, row chunks after chunk 0,
+                                // chunk-0 tile column stride in shared memory
+  int64_t colbase, rowbase;     // first L entry; sn_rows index of the piece's first row
+  int64_t inv0, inv1;           // packed inverse [inv0, inv1) in Linv
+  int64_t tp0, tp1;             // chunk-0 target pieces [tp0, tp1) in hd_tgt
+  int64_t zoff;                 // backward partial sums of the piece's chunks
+  int32_t tma, pad;             // 1 = chunk 0 is one 2-D TMA box
+};
+
+// Pieces at least this wide stage their row tiles with one 2-D TMA box
+// (rows x piece width, at most kTmaRows rows + 4 for the 16-byte start
+// alignment); narrower pieces copy column by column.
+constexpr int kTmaMinWidth = 32;
+constexpr int kTmaRows = 252;
+
+}  // namespace kkt
+
+namespace kkt {
+
 // Tile constants shared by the planner and the kernels.
 constexpr int kPB = 32;      // panel column block of the front factorization
 constexpr int kTR = 128;     // rows per TRSM item
@@ -34,7 +65,7 @@ struct Plan {
   std::vector<int32_t> sparent;
   std::vector<int32_t> rel;                 // per sn_rows slot: position of a child's below
                                             // row inside the parent's row list
-  int64_t panel_total = 0, u_total = 0;
+  int64_t panel_total = 0, u_total = 0;   // (dsc_total below)
   int32_t nlevels = 0;
   // factor work lists (items are int4: s, a, b, 0)
   std::vector<int32_t> it_potrf;            // (s) fronts whose column block kb is factored
@@ -42,6 +73,10 @@ struct Plan {
   std::vector<int32_t> it_pupd;             // (s, row tile, col tile) triples
   std::vector<int32_t> it_syrk;             // (s, ti, tj) triples, 64 x 64 tiles
   std::vector<int32_t> it_syrk_tc;          // (s, ti, tj), 128 x 128 tensor-core tiles
+  std::vector<int32_t> it_block;            // (s, row tile) per fused left-looking block step
+  std::vector<int32_t> it_syrk128;          // (s, ti, tj), 128 x 128 FP32 register-tiled SYRK
+  std::vector<int32_t> it_dstore;           // (s, kb, slot): factored diagonal tile -> panel, per level
+  int64_t dsc_total = 0;                    // entries of the diagonal-tile scratch (largest level)
   std::vector<int32_t> it_eadd;             // (child s, col tile) pairs, at the parent's level
   std::vector<int32_t> it_zero;             // (s, chunk) update matrices cleared at s's level
   std::vector<Launch> launches;
@@ -87,6 +122,13 @@ struct Plan {
   std::vector<int32_t> st_first, st_last, st_clo, st_chi;
   std::vector<int64_t> st_tptr;
   std::vector<int32_t> st_tgt;
+  // supernodes of each subtree item grouped by height above its leaves:
+  // item t's level boundaries are st_lev[st_lptr[t] .. st_lptr[t+1]) (offsets
+  // into st_sn); supernodes of one level are independent of each other
+  std::vector<int32_t> st_lptr, st_lev, st_sn;
+  std::vector<ChunkDesc> cdesc;             // per chunk
+  std::vector<HeadDesc> hdesc;              // per piece
+  std::vector<int32_t> pc_box;              // per piece: TMA box rows (0 = per-column copies)
   std::vector<int32_t> sn_piece;            // first piece of each supernode
   std::vector<int32_t> fwd_items, bwd_items; // >= 0 chunk id; -1-p head of piece p (p < npieces);
                                             // -1-npieces-t subtree t
@@ -106,7 +148,10 @@ inline int64_t packed_inv_size(int64_t pw) {
 
 // tc_syrk: fronts with rb >= kTcMinRows get 128 x 128 tensor-core SYRK tiles
 constexpr int kTcMinRows = 128;
+// f32 (FP32 factor): fronts with rb >= kBigRows get 128 x 128 register-tiled SYRK
+// tiles, and each block step fuses POTRF into the TRSM launch
+constexpr int kBigRows = 128;
 int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const int64_t* Jp,
-               const int32_t* Ji, int32_t solve_w, int32_t ent, int32_t ent0, bool tc_syrk, Plan& P);
+               const int32_t* Ji, int32_t solve_w, int32_t ent, int32_t ent0, bool tc_syrk, bool f32, Plan& P);
 
 }  // namespace kkt

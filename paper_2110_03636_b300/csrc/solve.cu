@@ -38,6 +38,8 @@ struct SolveSmemHdr {
   // dependency waits, bulk-copy waits, whole items, grid barriers, items
   long long c_disp, c_dep, c_mbar, c_item, c_bar, n_items;
   long long c_kind[3], n_kind[3];   // whole-item cycles and counts: subtrees, heads, chunks
+  long long c_lvl, n_lvl;           // subtree items: cycles in the level loops, levels
+  long long c_ph[8], t_mark;        // phases of forward subtree and chunk items (thread 0)
   double dred[(kSolveThreads / 32) * 2];
   double bcast[2];
 };
@@ -64,7 +66,7 @@ size_t solve_smem_bytes(size_t elem, int sw, int ent, int ent0, int max_rows) {
   const size_t a = tileA(sw, ent);
   const size_t e = (size_t)(ent > ent0 ? ent : ent0);
   const size_t b = e + 8 * (size_t)sw;
-  return elem * (a + b + 2 * (size_t)sw + (size_t)max_rows + kSolveThreads) + 16;
+  return elem * (a + b + 2 * (size_t)sw + (size_t)max_rows + kSolveThreads) + 256;   // + alignment of A and B
 }
 
 // Offset of column k in a packed pw-wide inverse: sum over j < k of
@@ -76,8 +78,6 @@ __device__ __forceinline__ int packed_S(int x) {
 }
 __device__ __forceinline__ int packed_off(int pw, int k) { return packed_S(pw) - packed_S(pw - k); }
 
-// column stride of a staged tile of nrows rows (room for the 16-byte alignment slack)
-__device__ __forceinline__ int tile_cs(int nrows) { return ((nrows + 3) & ~3) + 8; }
 
 // out_i = sum_k tile[k*cs + d0 + i] * x[k] for i < nr, handed to emit(i, out_i);
 // the k range is split among thread groups when the rows are few
@@ -118,6 +118,16 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
+// thread 0: charge the cycles since the last mark to phase i (profile runs)
+template <typename T>
+__device__ __forceinline__ void mark(const SolveArgs<T>& a, SolveSmemHdr& h, int i) {
+  if (a.instr && threadIdx.x == 0) {
+    const long long now = clock64();
+    if (i >= 0) h.c_ph[i] += now - h.t_mark;
+    h.t_mark = now;
+  }
+}
+
 // ------------------------------------------------------- TMA bulk copies
 __device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(unsigned long long* m) {
@@ -143,6 +153,15 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                : "memory");
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// 2-D tiled TMA load of the box at (x = row, y = column) of a tensor map held
+// in global memory; x * element size is a multiple of 16 bytes
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int x, int y, unsigned long long* m) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          saddr(dst)),
+      "l"(tmap), "r"(x), "r"(y), "r"(saddr(m))
+      : "memory");
+}
 
 // All threads: wait for the current bulk copies (bounded). On timeout the
 // abort word is set and the wait is retried once more, bounded, so that no
@@ -172,43 +191,57 @@ __device__ bool mbar_wait(const SolveArgs<T>& a, SolveSmemHdr& h) {
   return ok;
 }
 
-// Warp 0 queues bulk copies of the piece columns [0, pw), piece rows
-// [r0, r0 + nrows), into `tile` (column stride cs); 16-byte aligned by
-// starting at the supernode row rounded down to 4 (offset returned).
+// Warp 0 stages rows [r0, r0 + nrows) (piece-local) of the piece's pw
+// columns into `tile` (column stride cs), starting at the supernode row
+// rounded down to 4 so every copy starts on 16 bytes (offset returned):
+// one 2-D TMA box through the piece's tensor map when tma is set (cs = the
+// box rows; rows past the panel read as zeros), else one bulk copy per column.
 template <typename T>
-__device__ int stage_cols(const SolveArgs<T>& a, int p, int r0, int nrows, T* tile, uint32_t& bytes_out,
-                          unsigned long long* mbar, bool issue) {
-  const int cs = tile_cs(nrows);
-  const int ld = a.pc_ld[p], c = a.pc_c[p], pw = a.pc_w[p];
+__device__ int stage_tile(const SolveArgs<T>& a, int p, int64_t colbase, int ld, int c, int pw, int r0, int nrows,
+                          int cs, int tma, T* tile, uint32_t& bytes_out, unsigned long long* mbar, bool issue) {
   const int R0 = c + r0;
   const int A0 = R0 & ~3;
-  const int E = (R0 + nrows + 3) & ~3;
-  const uint32_t bytes = (uint32_t)(E - A0) * (uint32_t)sizeof(T);
-  bytes_out = bytes * (uint32_t)pw;
-  if (issue) {
-    const T* base = a.L + a.pc_colbase[p] + A0;
-    for (int k = threadIdx.x; k < pw; k += 32) bulk_g2s(tile + (int64_t)k * cs, base + (int64_t)k * ld, bytes, mbar);
+  if (tma) {
+    bytes_out = (uint32_t)cs * (uint32_t)pw * (uint32_t)sizeof(T);
+    if (issue && threadIdx.x == 0) tma_load_2d(tile, a.tmaps + (int64_t)p * 128, A0, 0, mbar);
+  } else {
+    const int E = (R0 + nrows + 3) & ~3;
+    const uint32_t bytes = (uint32_t)(E - A0) * (uint32_t)sizeof(T);
+    bytes_out = bytes * (uint32_t)pw;
+    if (issue) {
+      const T* base = a.L + colbase + A0;
+      for (int k = threadIdx.x; k < pw; k += 32) bulk_g2s(tile + (int64_t)k * cs, base + (int64_t)k * ld, bytes, mbar);
+    }
   }
   return R0 - A0;
+}
+
+// The sn_rows entry of row i of an item (i < nr), fetched before the item
+// waits on its inputs when the item has at most one row per thread.
+__device__ __forceinline__ int prefetch_row(const int32_t* rows, int nr) {
+  return (int)threadIdx.x < nr ? __ldg(&rows[threadIdx.x]) : 0;
 }
 
 // --------------------------------------------------------------- forward
 template <typename T>
 __device__ bool fwd_head(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>& t, int p, int e) {
   const int tid = threadIdx.x;
-  const int pw = a.pc_w[p], f = a.pc_first[p], rn = a.pc_rc0[p];
+  const HeadDesc d = a.hdesc[p];
+  const int pw = d.pw, f = d.f, rn = d.rn;
+  const int32_t* rows = a.sn_rows + d.rowbase + pw;
+  const int myrow = prefetch_row(rows, rn);
   if (tid < 32) {
     uint32_t b1 = 0;
     if (tid == 0) fence_proxy_async();
-    const uint32_t binv = (uint32_t)((a.pc_inv[p + 1] - a.pc_inv[p]) * sizeof(T));
-    if (rn > 0) stage_cols(a, p, pw, rn, t.B, b1, &h.mbar, false);
+    const uint32_t binv = (uint32_t)((d.inv1 - d.inv0) * sizeof(T));
+    if (rn > 0) stage_tile(a, p, d.colbase, d.ld, d.c, pw, pw, rn, d.cs, d.tma, t.B, b1, &h.mbar, false);
     if (tid == 0) mbar_expect_tx(&h.mbar, binv + b1);
     __syncwarp();
-    if (tid == 0) bulk_g2s(t.A, a.Linv + a.pc_inv[p], binv, &h.mbar);
-    if (rn > 0) stage_cols(a, p, pw, rn, t.B, b1, &h.mbar, true);
+    if (tid == 0) bulk_g2s(t.A, a.Linv + d.inv0, binv, &h.mbar);
+    if (rn > 0) stage_tile(a, p, d.colbase, d.ld, d.c, pw, pw, rn, d.cs, d.tma, t.B, b1, &h.mbar, true);
     if (tid == 0) {
       const long long t0 = clock64();
-      h.flag = wait_geq(&a.fwd_arrive[p], e * a.pc_need[p], a.st, a.spin);
+      h.flag = wait_geq(&a.fwd_arrive[p], e * d.need, a.st, a.spin);
       h.c_dep += clock64() - t0;
     }
   }
@@ -239,14 +272,15 @@ __device__ bool fwd_head(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>&
   if (tid == 0) st_release(&a.fwd_done[p], e);
   if (rn > 0) {
     // chunk 0: b[rows] -= L21(0:rn) y
-    const int d0 = (a.pc_c[p] + pw) & 3;
-    const int32_t* rows = a.sn_rows + a.pc_row[p] + pw;
+    const int d0 = (d.c + pw) & 3;
     T* v = a.v;
-    rows_matvec(t.B, tile_cs(rn), d0, rn, pw, t.vec2, t.aux, [&](int i, T o) { atomicAdd(&v[rows[i]], -o); });
+    rows_matvec(t.B, d.cs, d0, rn, pw, t.vec2, t.aux, [&](int i, T o) {
+      atomicAdd(&v[rn <= (int)blockDim.x ? myrow : rows[i]], -o);
+    });
     __syncthreads();
     if (tid == 0) {
       __threadfence();
-      for (int64_t q = a.hd_tptr[p]; q < a.hd_tptr[p + 1]; q++) atomicAdd(&a.fwd_arrive[a.hd_tgt[q]], 1);
+      for (int64_t q = d.tp0; q < d.tp1; q++) atomicAdd(&a.fwd_arrive[a.hd_tgt[q]], 1);
     }
   }
   return true;
@@ -255,36 +289,44 @@ __device__ bool fwd_head(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>&
 template <typename T>
 __device__ bool fwd_chunk(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>& t, int c, int e) {
   const int tid = threadIdx.x;
-  const int p = a.ch_piece[c];
-  const int pw = a.pc_w[p], f = a.pc_first[p];
-  const int r0 = a.ch_r0[c], nr = a.ch_nr[c];
+  mark(a, h, -1);
+  const ChunkDesc d = a.cdesc[c];
+  const int p = d.p, pw = d.pw, f = d.f, nr = d.nr;
+  const int32_t* rows = a.sn_rows + d.rowbase;
+  const int myrow = prefetch_row(rows, nr);
   if (tid < 32) {
     uint32_t b = 0;
     if (tid == 0) fence_proxy_async();
-    stage_cols(a, p, r0, nr, t.B, b, &h.mbar, false);
+    stage_tile(a, p, d.colbase, d.ld, d.c, pw, d.r0, nr, d.cs, d.tma, t.B, b, &h.mbar, false);
     if (tid == 0) mbar_expect_tx(&h.mbar, b);
     __syncwarp();
-    stage_cols(a, p, r0, nr, t.B, b, &h.mbar, true);
+    stage_tile(a, p, d.colbase, d.ld, d.c, pw, d.r0, nr, d.cs, d.tma, t.B, b, &h.mbar, true);
+    mark(a, h, 3);
     if (tid == 0) {
       const long long t0 = clock64();
       h.flag = wait_geq(&a.fwd_done[p], e, a.st, a.spin);
       h.c_dep += clock64() - t0;
     }
+    mark(a, h, 4);
   }
   __syncthreads();
   const bool dep = h.flag != 0;
   if (dep)
     for (int k = tid; k < pw; k += blockDim.x) t.vec[k] = ldcg(&a.v[f + k]);
   if (!mbar_wait(a, h) || !dep) return false;
-  const int d0 = (a.pc_c[p] + r0) & 3;
-  const int32_t* rows = a.sn_rows + a.pc_row[p] + r0;
+  mark(a, h, 5);
+  const int d0 = (d.c + d.r0) & 3;
   T* v = a.v;
-  rows_matvec(t.B, tile_cs(nr), d0, nr, pw, t.vec, t.aux, [&](int i, T o) { atomicAdd(&v[rows[i]], -o); });
+  rows_matvec(t.B, d.cs, d0, nr, pw, t.vec, t.aux, [&](int i, T o) {
+    atomicAdd(&v[nr <= (int)blockDim.x ? myrow : rows[i]], -o);
+  });
   __syncthreads();
+  mark(a, h, 6);
   if (tid == 0) {
     __threadfence();
-    for (int64_t q = a.ch_tptr[c]; q < a.ch_tptr[c + 1]; q++) atomicAdd(&a.fwd_arrive[a.ch_tgt[q]], 1);
+    for (int64_t q = d.tp0; q < d.tp1; q++) atomicAdd(&a.fwd_arrive[a.ch_tgt[q]], 1);
   }
+  mark(a, h, 7);
   return true;
 }
 
@@ -292,34 +334,39 @@ __device__ bool fwd_chunk(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>
 template <typename T>
 __device__ bool bwd_chunk(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>& t, int c, int e) {
   const int tid = threadIdx.x;
-  const int p = a.ch_piece[c];
-  const int pw = a.pc_w[p];
-  const int r0 = a.ch_r0[c], nr = a.ch_nr[c];
+  const ChunkDesc d = a.cdesc[c];
+  const int p = d.p, pw = d.pw, nr = d.nr;
+  const int32_t* rows = a.sn_rows + d.rowbase;
+  const int myrow = prefetch_row(rows, nr);
   if (tid < 32) {
     uint32_t b = 0;
     if (tid == 0) fence_proxy_async();
-    stage_cols(a, p, r0, nr, t.B, b, &h.mbar, false);
+    stage_tile(a, p, d.colbase, d.ld, d.c, pw, d.r0, nr, d.cs, d.tma, t.B, b, &h.mbar, false);
     if (tid == 0) mbar_expect_tx(&h.mbar, b);
     __syncwarp();
-    stage_cols(a, p, r0, nr, t.B, b, &h.mbar, true);
+    stage_tile(a, p, d.colbase, d.ld, d.c, pw, d.r0, nr, d.cs, d.tma, t.B, b, &h.mbar, true);
     if (tid == 0) {
       const long long t0 = clock64();
       int ok = 1;
-      for (int64_t q = a.ch_tptr[c]; q < a.ch_tptr[c + 1] && ok; q++)
-        ok = wait_geq(&a.bwd_done[a.ch_tgt[q]], e, a.st, a.spin);
+      for (int64_t q = d.tp0; q < d.tp1 && ok; q++) ok = wait_geq(&a.bwd_done[a.ch_tgt[q]], e, a.st, a.spin);
       h.flag = ok;
       h.c_dep += clock64() - t0;
     }
   }
   __syncthreads();
   const bool dep = h.flag != 0;
-  if (dep)
-    for (int i = tid; i < nr; i += blockDim.x) t.aux[i] = ldcg(&a.v[a.sn_rows[a.pc_row[p] + r0 + i]]);
+  if (dep) {
+    if (nr <= (int)blockDim.x) {
+      if (tid < nr) t.aux[tid] = ldcg(&a.v[myrow]);
+    } else {
+      for (int i = tid; i < nr; i += blockDim.x) t.aux[i] = ldcg(&a.v[rows[i]]);
+    }
+  }
   if (!mbar_wait(a, h) || !dep) return false;
-  const int d0 = (a.pc_c[p] + r0) & 3;
-  const int cs = tile_cs(nr);
+  const int d0 = (d.c + d.r0) & 3;
+  const int cs = d.cs;
   const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  T* z = a.zpart + a.pc_zoff[p] + (int64_t)a.ch_k[c] * pw;
+  T* z = a.zpart + d.zoff;
   for (int k = warp; k < pw; k += nw) {
     T s = T(0);
     for (int i = lane; i < nr; i += 32) s += t.B[k * cs + d0 + i] * t.aux[i];
@@ -337,21 +384,23 @@ __device__ bool bwd_chunk(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>
 template <typename T>
 __device__ bool bwd_head(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>& t, int p, int e) {
   const int tid = threadIdx.x;
-  const int pw = a.pc_w[p], f = a.pc_first[p], rn = a.pc_rc0[p], nch = a.pc_nchunk[p];
+  const HeadDesc d = a.hdesc[p];
+  const int pw = d.pw, f = d.f, rn = d.rn, nch = d.nch;
+  const int32_t* rows = a.sn_rows + d.rowbase + pw;
+  const int myrow = prefetch_row(rows, rn);
   if (tid < 32) {
     uint32_t b1 = 0;
     if (tid == 0) fence_proxy_async();
-    const uint32_t binv = (uint32_t)((a.pc_inv[p + 1] - a.pc_inv[p]) * sizeof(T));
-    if (rn > 0) stage_cols(a, p, pw, rn, t.B, b1, &h.mbar, false);
+    const uint32_t binv = (uint32_t)((d.inv1 - d.inv0) * sizeof(T));
+    if (rn > 0) stage_tile(a, p, d.colbase, d.ld, d.c, pw, pw, rn, d.cs, d.tma, t.B, b1, &h.mbar, false);
     if (tid == 0) mbar_expect_tx(&h.mbar, binv + b1);
     __syncwarp();
-    if (tid == 0) bulk_g2s(t.A, a.Linv + a.pc_inv[p], binv, &h.mbar);
-    if (rn > 0) stage_cols(a, p, pw, rn, t.B, b1, &h.mbar, true);
+    if (tid == 0) bulk_g2s(t.A, a.Linv + d.inv0, binv, &h.mbar);
+    if (rn > 0) stage_tile(a, p, d.colbase, d.ld, d.c, pw, pw, rn, d.cs, d.tma, t.B, b1, &h.mbar, true);
     if (tid == 0) {
       const long long t0 = clock64();
       int ok = wait_geq(&a.bwd_arrive[p], e * nch, a.st, a.spin);
-      for (int64_t q = a.hd_tptr[p]; q < a.hd_tptr[p + 1] && ok; q++)
-        ok = wait_geq(&a.bwd_done[a.hd_tgt[q]], e, a.st, a.spin);
+      for (int64_t q = d.tp0; q < d.tp1 && ok; q++) ok = wait_geq(&a.bwd_done[a.hd_tgt[q]], e, a.st, a.spin);
       h.flag = ok;
       h.c_dep += clock64() - t0;
     }
@@ -359,8 +408,12 @@ __device__ bool bwd_head(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>&
   __syncthreads();
   const bool dep = h.flag != 0;
   if (dep) {
-    for (int i = tid; i < rn; i += blockDim.x) t.aux[i] = ldcg(&a.v[a.sn_rows[a.pc_row[p] + pw + i]]);
-    const T* z = a.zpart + a.pc_zoff[p];
+    if (rn <= (int)blockDim.x) {
+      if (tid < rn) t.aux[tid] = ldcg(&a.v[myrow]);
+    } else {
+      for (int i = tid; i < rn; i += blockDim.x) t.aux[i] = ldcg(&a.v[rows[i]]);
+    }
+    const T* z = a.zpart + d.zoff;
     for (int i = tid; i < pw; i += blockDim.x) {
       T v = ldcg(&a.v[f + i]);
       for (int k = 0; k < nch; k++) v -= ldcg(&z[(int64_t)k * pw + i]);
@@ -370,8 +423,8 @@ __device__ bool bwd_head(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>&
   if (!mbar_wait(a, h) || !dep) return false;
   const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   if (rn > 0) {
-    const int d0 = (a.pc_c[p] + pw) & 3;
-    const int cs = tile_cs(rn);
+    const int d0 = (d.c + pw) & 3;
+    const int cs = d.cs;
     for (int k = warp; k < pw; k += nw) {
       T s = T(0);
       for (int i = lane; i < rn; i += 32) s += t.B[k * cs + d0 + i] * t.aux[i];
@@ -420,52 +473,143 @@ __device__ void stage_subtree(const SolveArgs<T>& a, SolveSmemHdr& h, const Tile
   }
 }
 
+// Forward step of one subtree supernode by one warp: y = T^-1 x on its
+// columns (packed inverse), then x[row] -= L21 y for its rows below, into
+// shared memory inside the subtree's column range and into v outside it.
+template <typename T>
+__device__ void warp_fwd_supernode(const SolveArgs<T>& a, const Tiles<T>& t, int s, int clo, int chi,
+                                   int64_t pbase, int64_t ibase, T* xs) {
+  const int lane = threadIdx.x & 31;
+  const int w = __ldg(&a.sw_[s]), nr = __ldg(&a.snr[s]), ld = __ldg(&a.sld[s]), f = __ldg(&a.sfirst[s]) - clo;
+  const T* P = t.B + (__ldg(&a.poff[s]) - pbase);
+  const T* Inv = t.A + (__ldg(&a.pc_inv[__ldg(&a.sn_piece[s])]) - ibase);
+  const int32_t* rows = a.sn_rows + __ldg(&a.srow[s]);
+  T y[4];
+#pragma unroll
+  for (int c = 0; c < 4; c++) {
+    const int i = lane + 32 * c;
+    T acc = T(0);
+    if (i < w) {
+      int off = 0;
+      for (int k = 0; k <= i; k++) {
+        acc += Inv[off + i - k] * xs[f + k];
+        off += (w - k + 3) & ~3;
+      }
+    }
+    y[c] = acc;
+  }
+  __syncwarp();
+#pragma unroll
+  for (int c = 0; c < 4; c++)
+    if (lane + 32 * c < w) xs[f + lane + 32 * c] = y[c];
+  __syncwarp();
+  for (int r = w + lane; r < nr; r += 128) {
+    int rr[4];
+    T o[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) rr[u] = r + 32 * u < nr ? __ldg(&rows[r + 32 * u]) : -1;
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      o[u] = T(0);
+      if (rr[u] >= 0)
+        for (int k = 0; k < w; k++) o[u] += P[r + 32 * u + k * ld] * xs[f + k];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      if (rr[u] < 0) continue;
+      if (rr[u] < chi) atomicAdd(&xs[rr[u] - clo], -o[u]);
+      else atomicAdd(&a.v[rr[u]], -o[u]);
+    }
+  }
+}
+
+// Backward step of one subtree supernode by one warp: t = x - L21^T x[rows]
+// on its columns, then x = T^-T t. Scratch of this warp (kSubScratch
+// entries): t (w <= 128 entries), then x at the first rows below.
+constexpr int kSubScratch = 160;
+template <typename T>
+__device__ void warp_bwd_supernode(const SolveArgs<T>& a, const Tiles<T>& t, int s, int clo, int chi,
+                                   int64_t pbase, int64_t ibase, T* xs, T* scratch) {
+  const int lane = threadIdx.x & 31;
+  const int w = __ldg(&a.sw_[s]), nr = __ldg(&a.snr[s]), ld = __ldg(&a.sld[s]), f = __ldg(&a.sfirst[s]) - clo;
+  const T* P = t.B + (__ldg(&a.poff[s]) - pbase);
+  const T* Inv = t.A + (__ldg(&a.pc_inv[__ldg(&a.sn_piece[s])]) - ibase);
+  const int32_t* rows = a.sn_rows + __ldg(&a.srow[s]);
+  // gather x at the rows below into the scratch after t (w entries) once;
+  // rows beyond the scratch are read where they are
+  T* xr = scratch + w;
+  const int cache = kSubScratch - w;
+  const int nb = nr - w;
+  for (int r = lane; r < nb && r < cache; r += 32) {
+    const int row = __ldg(&rows[w + r]);
+    xr[r] = row < chi ? xs[row - clo] : ldcg(&a.v[row]);
+  }
+  __syncwarp();
+  for (int k = 0; k < w; k++) {
+    T acc = T(0);
+    for (int r = lane; r < nb; r += 32) {
+      T x;
+      if (r < cache) {
+        x = xr[r];
+      } else {
+        const int row = __ldg(&rows[w + r]);
+        x = row < chi ? xs[row - clo] : ldcg(&a.v[row]);
+      }
+      acc += P[w + r + k * ld] * x;
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) scratch[k] = xs[f + k] - acc;
+  }
+  __syncwarp();
+  int off = 0;
+  for (int k = 0; k < w; k++) {
+    T acc = T(0);
+    for (int i = k + lane; i < w; i += 32) acc += Inv[off + i - k] * scratch[i];
+    acc = warp_sum(acc);
+    if (lane == 0) xs[f + k] = acc;
+    off += (w - k + 3) & ~3;
+  }
+  __syncwarp();
+}
+
+// Small subtrees: the supernodes of one item are processed level by level
+// (height above the item's leaves), one warp per supernode; supernodes of
+// one level are independent, so one CTA barrier per level suffices.
 template <typename T>
 __device__ bool fwd_subtree(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>& t, int st) {
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, nw = blockDim.x >> 5;
   const int clo = a.st_clo[st], chi = a.st_chi[st];
+  mark(a, h, -1);
   int64_t pbase, ibase;
   stage_subtree(a, h, t, st, pbase, ibase);
   T* xs = t.vec2;
   for (int i = tid; i < chi - clo; i += blockDim.x) xs[i] = ldcg(&a.v[clo + i]);
   if (!mbar_wait(a, h)) return false;
-  for (int s = a.st_first[st]; s <= a.st_last[st]; s++) {
-    const int w = a.sw_[s], nr = a.snr[s], ld = a.sld[s], f = a.sfirst[s] - clo;
-    const T* P = t.B + (a.poff[s] - pbase);
-    const T* Inv = t.A + (a.pc_inv[a.sn_piece[s]] - ibase);
-    if (tid < w) {
-      T y = T(0);
-      int off = 0;
-      for (int k = 0; k <= tid; k++) {
-        y += Inv[off + tid - k] * xs[f + k];
-        off += (w - k + 3) & ~3;
-      }
-      t.vec[tid] = y;
-    }
-    __syncthreads();
-    if (tid < w) xs[f + tid] = t.vec[tid];
-    const int32_t* rows = a.sn_rows + a.srow[s];
-    for (int r = w + tid; r < nr; r += blockDim.x) {
-      T o = T(0);
-      for (int k = 0; k < w; k++) o += P[r + k * ld] * t.vec[k];
-      const int row = rows[r];
-      if (row < chi) xs[row - clo] -= o;
-      else atomicAdd(&a.v[row], -o);
-    }
+  mark(a, h, 0);
+  const long long tl0 = clock64();
+  for (int L = a.st_lptr[st]; L + 1 < a.st_lptr[st + 1]; L++) {
+    for (int q = a.st_lev[L] + warp; q < a.st_lev[L + 1]; q += nw)
+      warp_fwd_supernode(a, t, a.st_sn[q], clo, chi, pbase, ibase, xs);
     __syncthreads();
   }
+  if (tid == 0) {
+    h.c_lvl += clock64() - tl0;
+    h.n_lvl += a.st_lptr[st + 1] - a.st_lptr[st] - 1;
+  }
+  mark(a, h, 1);
   for (int i = tid; i < chi - clo; i += blockDim.x) a.v[clo + i] = xs[i];
   __syncthreads();
   if (tid == 0) {
     __threadfence();
     for (int64_t q = a.st_tptr[st]; q < a.st_tptr[st + 1]; q++) atomicAdd(&a.fwd_arrive[a.st_tgt[q]], 1);
   }
+  mark(a, h, 2);
   return true;
 }
 
 template <typename T>
 __device__ bool bwd_subtree(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>& t, int st, int e) {
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, nw = blockDim.x >> 5;
   const int clo = a.st_clo[st], chi = a.st_chi[st];
   int64_t pbase, ibase;
   stage_subtree(a, h, t, st, pbase, ibase);
@@ -483,32 +627,16 @@ __device__ bool bwd_subtree(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<
   if (dep)
     for (int i = tid; i < chi - clo; i += blockDim.x) xs[i] = ldcg(&a.v[clo + i]);
   if (!mbar_wait(a, h) || !dep) return false;
-  const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  for (int s = a.st_last[st]; s >= a.st_first[st]; s--) {
-    const int w = a.sw_[s], nr = a.snr[s], ld = a.sld[s], f = a.sfirst[s] - clo;
-    const T* P = t.B + (a.poff[s] - pbase);
-    const T* Inv = t.A + (a.pc_inv[a.sn_piece[s]] - ibase);
-    const int32_t* rows = a.sn_rows + a.srow[s];
-    for (int k = warp; k < w; k += nw) {
-      T acc = T(0);
-      for (int r = w + lane; r < nr; r += 32) {
-        const int row = rows[r];
-        const T x = row < chi ? xs[row - clo] : ldcg(&a.v[row]);
-        acc += P[r + k * ld] * x;
-      }
-      acc = warp_sum(acc);
-      if (lane == 0) t.vec[k] = xs[f + k] - acc;
-    }
+  T* scratch = t.aux + kSubScratch * warp;   // 8 warps x 160 <= max_rows + kSolveThreads
+  const long long tl0 = clock64();
+  for (int L = a.st_lptr[st + 1] - 2; L >= a.st_lptr[st]; L--) {
+    for (int q = a.st_lev[L] + warp; q < a.st_lev[L + 1]; q += nw)
+      warp_bwd_supernode(a, t, a.st_sn[q], clo, chi, pbase, ibase, xs, scratch);
     __syncthreads();
-    for (int k = warp; k < w; k += nw) {
-      int off = 0;
-      for (int j = 0; j < k; j++) off += (w - j + 3) & ~3;
-      T acc = T(0);
-      for (int i = k + lane; i < w; i += 32) acc += Inv[off + i - k] * t.vec[i];
-      acc = warp_sum(acc);
-      if (lane == 0) xs[f + k] = acc;
-    }
-    __syncthreads();
+  }
+  if (tid == 0) {
+    h.c_lvl += clock64() - tl0;
+    h.n_lvl += a.st_lptr[st + 1] - a.st_lptr[st] - 1;
   }
   for (int i = tid; i < chi - clo; i += blockDim.x) a.v[clo + i] = xs[i];
   __syncthreads();   // the results are read after the next grid barrier
@@ -629,6 +757,9 @@ __device__ void flush_counters(const SolveArgs<T>& a, SolveSmemHdr& h) {
       atomicAdd(&a.instr[7 + 2 * k], (unsigned long long)h.c_kind[k]);
       atomicAdd(&a.instr[8 + 2 * k], (unsigned long long)h.n_kind[k]);
     }
+    atomicAdd(&a.instr[13], (unsigned long long)h.c_lvl);
+    atomicAdd(&a.instr[14], (unsigned long long)h.n_lvl);
+    for (int k = 0; k < 8; k++) atomicAdd(&a.instr[16 + k], (unsigned long long)h.c_ph[k]);
   }
 }
 
@@ -647,8 +778,14 @@ __global__ void __launch_bounds__(kSolveThreads, MB) k_cg(SolveArgs<T> a) {
   __shared__ SolveSmemHdr sm;
   extern __shared__ __align__(16) unsigned char dsm[];
   Tiles<T> tl;
-  tl.A = (T*)dsm;
-  tl.B = tl.A + tileA(a.sw, a.ent);
+  {
+    // region A at a 128-byte aligned shared address, region B (TMA boxes) too
+    const uint32_t sa = saddr(dsm);
+    unsigned char* pa = dsm + ((128u - (sa & 127u)) & 127u);
+    tl.A = (T*)pa;
+    const size_t abytes = (tileA(a.sw, a.ent) * sizeof(T) + 127) & ~(size_t)127;
+    tl.B = (T*)(pa + abytes);
+  }
   tl.vec = tl.B + (size_t)(a.ent > a.ent0 ? a.ent : a.ent0) + 8 * (size_t)a.sw;
   tl.vec2 = tl.vec + a.sw;
   tl.aux = tl.vec2 + a.sw;
@@ -657,6 +794,9 @@ __global__ void __launch_bounds__(kSolveThreads, MB) k_cg(SolveArgs<T> a) {
     sm.phase = 0;
     sm.c_disp = sm.c_dep = sm.c_mbar = sm.c_item = sm.c_bar = sm.n_items = 0;
     for (int k = 0; k < 3; k++) sm.c_kind[k] = sm.n_kind[k] = 0;
+    sm.c_lvl = sm.n_lvl = 0;
+    for (int k = 0; k < 8; k++) sm.c_ph[k] = 0;
+    sm.t_mark = 0;
   }
   __syncthreads();
   const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;

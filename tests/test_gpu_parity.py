@@ -47,11 +47,13 @@ def test_tiny_systems_match_oracle(seed, precision):
     assert code == 0
     info = s.info
     assert info.cg_status == 0
-    assert rel(np.concatenate([dx, dy]), np.concatenate([odx, ody])) <= 1e-9
-    assert info.rr <= 1e-10
+    # FP64 solves to 1e-12; the mixed form refines until RR <= 1e-9 (its default stop)
+    rr_max, sol = (1e-10, 1e-9) if precision == "fp64" else (1e-9, 1e-7)
+    assert rel(np.concatenate([dx, dy]), np.concatenate([odx, ody])) <= sol
+    assert info.rr <= rr_max
     r = O.residual(O.Symbolic(sys.n, sys.m, sys.H_colptr, sys.H_rowidx, sys.J_rowptr, sys.J_colidx),
                    sys.H_vals, sys.J_vals, sys.delta, sys.r_x, sys.r_y, dx, dy)
-    assert r["rr"] <= 1e-10
+    assert r["rr"] <= rr_max
     if precision == "fp64":
         assert abs(info.cg_iters - oinfo["iters"]) <= 1
     assert s.inertia_ok
@@ -106,6 +108,60 @@ def test_tensor_core_syrk_matches_fma_syrk(name):
         assert s.info.rr <= 1e-8
     a, b = outs
     assert np.abs(a - b).max() <= 1e-4 * np.abs(b).max()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("wide,hubs_last", [(40, False), (100, False), (40, True), (300, True)])
+def test_wide_front_with_many_row_tiles(precision, wide, hubs_last):
+    """Natural ordering of an arrowhead: `wide` hub variables couple to all
+    1200 others. Hubs first: one dense supernode of all 1200 + wide columns,
+    so every 32-column block step has many row tiles below it. Hubs last:
+    1200 one-column fronts whose `wide` x `wide` update matrices (128-tile
+    SYRK when wide >= 128) are all extend-added into the hub front. FP64
+    panels equal the oracle's L; both precisions reach the oracle's solution."""
+    from test_oracle import make_sys
+    rng = np.random.default_rng(wide)
+    n, m = wide + 1200, 60
+    H = np.zeros((n, n))
+    H[:wide, wide:] = rng.uniform(-1, 1, (wide, n - wide)) / np.sqrt(n)
+    H = H + H.T
+    H[np.arange(n), np.arange(n)] = np.abs(H).sum(1) + rng.uniform(0.5, 2.0, n)
+    H[:wide, :wide] += rng.uniform(-0.1, 0.1, (wide, wide)) * (rng.random((wide, wide)) < 0.3)
+    H[:wide, :wide] = (H[:wide, :wide] + H[:wide, :wide].T) / 2
+    H[np.arange(wide), np.arange(wide)] += wide * 0.1
+    if hubs_last:
+        order = np.r_[wide:n, 0:wide]
+        H = H[np.ix_(order, order)]
+    J = np.zeros((m, n))
+    J[np.arange(m), rng.choice(n, m, replace=False)] = 1.0
+    J[np.arange(m), rng.integers(0, n, m)] += rng.standard_normal(m)
+    sys = make_sys(H, J, rng.standard_normal(n), rng.standard_normal(m), gamma=1e2)
+    _, _, odx, ody, oinfo = O.solve_system(sys, ordering="natural")
+    assert oinfo["status"] == 0
+    s, code, dx, dy = gpu_solve(sys, precision, ordering="natural")
+    assert code == 0
+    assert s.info.rr <= (1e-10 if precision == "fp64" else 1e-9)
+    assert rel(np.concatenate([dx, dy]), np.concatenate([odx, ody])) <= (1e-8 if precision == "fp64" else 1e-6)
+    if precision == "fp64":
+        sym = O.Symbolic(sys.n, sys.m, sys.H_colptr, sys.H_rowidx, sys.J_rowptr, sys.J_colidx, ordering="natural")
+        f = O.Factor(sym, sys.H_vals, sys.J_vals, sys.delta, sys.gamma)
+        Lp, Li, Lx = f.L_csc()
+        pan = s.panels()
+        st, rp, rows, _ = sym.supernodes()
+        off, worst = 0, 0.0
+        for k in range(len(st) - 1):
+            w, nr = st[k + 1] - st[k], rp[k + 1] - rp[k]
+            ld = (nr + 3) // 4 * 4
+            R = rows[rp[k]:rp[k + 1]]
+            for c in range(w):
+                col = st[k] + c
+                q0, q1 = Lp[col], Lp[col + 1]
+                ref = dict(zip(Li[q0:q1], Lx[q0:q1]))
+                for r_i in range(c, nr):
+                    v = pan[off + c * ld + r_i]
+                    worst = max(worst, abs(v - ref.get(R[r_i], 0.0)))
+            off += w * ld
+        assert worst <= 1e-12 * np.abs(Lx).max()
 
 
 def test_hsolve_matches_oracle():
