@@ -318,10 +318,68 @@ def run_ours(args, rank, world):
                        "cg_iters_mean": float(np.mean(results[p]["iters"])),
                        "latency_ms": {"p50": round(float(np.percentile(results[p]["lat"], 50)), 3),
                                       "p99": round(float(np.percentile(results[p]["lat"], 99)), 3)}}
+    if not args.no_batch:
+        line["batching"] = run_batching(args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sets, iters=float(np.mean(results.get("fp64", R)["iters"])),
                                             seconds=args.cpu_sample_seconds)
     return line
+
+
+# ------------------------------------------------------------------ batching forms
+def run_batching(args, dev):
+    """The batching workload (200 x 100 grid, n = 20000, m = 10000): nsys
+    systems sharing one analysed pattern with per-system edge weights and
+    barriers (independent seeds), factored and solved through the batched
+    entry points; and one of them with 64 right-hand sides solved together
+    (the triangular sweeps shared) against 64 separate solves. Mixed
+    precision (FP32 factor, FP64 CG and refinement)."""
+    import torch
+    import paper_2110_03636_b300 as K
+    import workloads as W
+    base = W.make_config("grid2d_n20k")
+    systems = [W.reweight(base, seed=(1, b)) for b in range(args.batch_systems)]
+    cu = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
+    Hs = cu(np.stack([x.H_vals for x in systems]))
+    Js = cu(np.stack([x.J_vals for x in systems]))
+    rng = np.random.default_rng(11)
+    RX = cu(rng.standard_normal((args.batch_systems, base.n)))
+    RY = cu(rng.standard_normal((args.batch_systems, base.m)))
+    s = K.KKTSolver(base.n, base.m, base.H_colptr, base.H_rowidx, base.J_rowptr, base.J_colidx,
+                    precision="mixed", ordering=args.ordering)
+    out = {"workload": "grid2d 200x100, n=20000, m=10000, per-system weights and barriers (seeds (1, b))",
+           "precision": "mixed"}
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            r = fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / reps, r
+
+    def batch_step():
+        code, st = s.factor_batch(Hs, Js, base.delta, base.gamma)
+        dx, dy, infos, sst, code2 = s.solve_batch(RX, RY)
+        return st, sst, infos
+    sec, (st, sst, infos) = timed(batch_step, 2)
+    out["batch"] = {"systems": args.batch_systems, "solves_per_s": round(args.batch_systems / sec, 2),
+                    "ms_per_system": round(1e3 * sec / args.batch_systems, 3),
+                    "failed": int((np.asarray(st) != 0).sum() + (np.asarray(sst) != 0).sum()),
+                    "rr_max": max(i.rr for i in infos),
+                    "form": "factor_batch + solve_batch, one system after another on the shared analysis"}
+    # one factor, 64 right-hand sides
+    s.factor(Hs[0], Js[0], base.delta, base.gamma)
+    R64 = cu(rng.standard_normal((64, base.n)))
+    Y64 = cu(rng.standard_normal((64, base.m)))
+    sec_m, (dx, dy, infos) = timed(lambda: s.solve_multi(R64, Y64), 2)
+    sec_1, _ = timed(lambda: [s.solve(R64[j], Y64[j]) for j in range(64)], 1)
+    out["multi_rhs"] = {"nrhs": 64, "rhs_per_s": round(64 / sec_m, 2), "separate_rhs_per_s": round(64 / sec_1, 2),
+                        "rr_max": max(i.rr for i in infos),
+                        "form": "solve_multi: 8 right-hand sides per persistent launch sharing each sweep"}
+    s.close()
+    return out
 
 
 # ------------------------------------------------------------------ oracle arm
@@ -410,6 +468,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-seconds", type=float, default=10.0)
     ap.add_argument("--ordering", default="nd", choices=["nd", "amd"])
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched / multi-RHS measurements")
+    ap.add_argument("--batch-systems", type=int, default=256)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -183,6 +183,43 @@ kkt_status kkt_factor(kkt_handle h, const double* H_vals, const double* J_vals, 
 kkt_status kkt_solve(kkt_handle h, const double* r_x, const double* r_y, double* dx, double* dy,
                      void* stream);
 
+/* Several right-hand sides with the last successful factor (one factor
+ * with many RHS): right-hand side j is r_x + j n, r_y + j m (device, RHS
+ * after RHS), its solution dx + j n, dy + j m. Up to 8 right-hand sides
+ * share each persistent solve launch: every triangular sweep stages each L
+ * tile once and applies it to all of them, while CG runs independently per
+ * right-hand side (own scalars, stop test and delta_2 restart; Algorithm 1
+ * per right-hand side); refinement passes continue while any RR > ir_rtol.
+ *   nrhs  >= 1
+ *   info  host kkt_info[nrhs] (may be NULL): statistics per right-hand side;
+ *         kkt_get_info then reports the worst of them
+ * The first call allocates the multiple-RHS workspace (8 vectors of each
+ * solve vector). Errors as kkt_solve. */
+kkt_status kkt_solve_multi(kkt_handle h, int32_t nrhs, const double* r_x, const double* r_y, double* dx,
+                           double* dy, kkt_info* info, void* stream);
+
+/* Batched form: nsys systems with the analysed pattern (the symbolic
+ * analysis is shared), e.g. the same network at several operating points.
+ *   H_vals  device double[nsys * nnz(H~)], system after system
+ *   J_vals  device double[nsys * nnz(J)]
+ *   status  host int32[nsys] (may be NULL): KKT_OK or KKT_ERR_NOT_SPD per system
+ * Each system is factored by the handle's own factorization and kept in a
+ * per-system slot (the handle allocates nsys slots of panels, inverses and
+ * values; a larger nsys later reallocates them). Returns KKT_ERR_NOT_SPD if
+ * any system failed (the others are usable), else the first other error.
+ * The single-system factor is not kept: kkt_solve needs a new kkt_factor. */
+kkt_status kkt_factor_batch(kkt_handle h, int32_t nsys, const double* H_vals, const double* J_vals,
+                            double delta, double gamma, int32_t* status, void* stream);
+
+/* Solves system b of the last kkt_factor_batch with right-hand side
+ * r_x + b n, r_y + b m (device) into dx + b n, dy + b m, for b < nsys.
+ *   info    host kkt_info[nsys] (may be NULL)
+ *   status  host int32[nsys] (may be NULL): per-system status (a system whose
+ *           factorization failed reports KKT_ERR_NOT_SPD and is skipped)
+ * Returns the first per-system error, KKT_OK if none. */
+kkt_status kkt_solve_batch(kkt_handle h, int32_t nsys, const double* r_x, const double* r_y, double* dx,
+                           double* dy, kkt_info* info, int32_t* status, void* stream);
+
 /* Factor + solve with HOST buffers (copies in and out on `stream`):
  * H_vals/J_vals/r_x/r_y/dx/dy are host arrays of the sizes above. */
 kkt_status kkt_factor_solve_host(kkt_handle h, const double* H_vals, const double* J_vals,

@@ -64,6 +64,9 @@ def _load():
     L.kkt_analyse_host.argtypes = [I64, I64, P, P, P, P, C.POINTER(kkt_options), C.POINTER(P)]
     L.kkt_factor.argtypes = [P, P, P, D, D, P]
     L.kkt_solve.argtypes = [P, P, P, P, P, P]
+    L.kkt_solve_multi.argtypes = [P, I32, P, P, P, P, P, P]
+    L.kkt_factor_batch.argtypes = [P, I32, P, P, D, D, P, P]
+    L.kkt_solve_batch.argtypes = [P, I32, P, P, P, P, P, P, P]
     L.kkt_factor_solve_host.argtypes = [P, P, P, D, D, P, P, P, P, P]
     L.kkt_hsolve.argtypes = [P, P, P, P]
     L.kkt_get_info.argtypes = [P, C.POINTER(kkt_info)]
@@ -85,7 +88,7 @@ def _load():
     L.kkt_destroy_4x4.argtypes = [P]
     L.kkt_status_string.argtypes = [I32]
     L.kkt_status_string.restype = C.c_char_p
-    for nm in ("kkt_analyse", "kkt_analyse_host", "kkt_factor", "kkt_solve", "kkt_factor_solve_host", "kkt_hsolve", "kkt_get_info",
+    for nm in ("kkt_analyse", "kkt_analyse_host", "kkt_factor", "kkt_solve", "kkt_solve_multi", "kkt_factor_batch", "kkt_solve_batch", "kkt_factor_solve_host", "kkt_hsolve", "kkt_get_info",
                "kkt_inertia", "kkt_symbolic_info_get", "kkt_get_symbolic", "kkt_get_factor_panels", "kkt_get_profile", "kkt_get_solve_counters", "kkt_residual_noalloc",
                "kkt_destroy", "kkt_analyse_4x4", "kkt_analyse_4x4_host", "kkt_get_4x4_pattern", "kkt_factor_4x4",
                "kkt_solve_4x4", "kkt_destroy_4x4"):
@@ -94,7 +97,7 @@ def _load():
 
 
 _lib = _load()
-EXPORTED = ("kkt_default_options", "kkt_analyse", "kkt_analyse_host", "kkt_factor", "kkt_solve", "kkt_factor_solve_host",
+EXPORTED = ("kkt_default_options", "kkt_analyse", "kkt_analyse_host", "kkt_factor", "kkt_solve", "kkt_solve_multi", "kkt_factor_batch", "kkt_solve_batch", "kkt_factor_solve_host",
             "kkt_hsolve", "kkt_get_info", "kkt_inertia", "kkt_symbolic_info_get", "kkt_get_symbolic",
             "kkt_get_factor_panels", "kkt_get_profile", "kkt_get_solve_counters", "kkt_residual_noalloc",
             "kkt_destroy", "kkt_status_string", "kkt_analyse_4x4", "kkt_analyse_4x4_host", "kkt_4x4_inner",
@@ -167,6 +170,15 @@ def kkt_factor(h, H_vals, J_vals, delta, gamma, n_h, n_j, stream=None):
 
 def kkt_solve(h, r_x, r_y, dx, dy, n, m, stream=None):
     return _lib.kkt_solve(h, _dev(r_x, n), _dev(r_y, m), _dev(dx, n), _dev(dy, m), _stream(stream))
+
+
+def kkt_solve_multi(h, nrhs, r_x, r_y, dx, dy, n, m, stream=None):
+    """nrhs right-hand sides, RHS after RHS: r_x, dx CUDA float64 (nrhs*n),
+    r_y, dy (nrhs*m). Returns (status, [kkt_info per RHS])."""
+    infos = (kkt_info * max(int(nrhs), 1))()
+    code = _lib.kkt_solve_multi(h, int(nrhs), _dev(r_x, nrhs * n), _dev(r_y, nrhs * m), _dev(dx, nrhs * n),
+                                _dev(dy, nrhs * m), C.cast(infos, C.c_void_p), _stream(stream))
+    return code, [infos[j] for j in range(int(nrhs))]
 
 
 def kkt_hsolve(h, b, x, n, stream=None):
@@ -340,6 +352,43 @@ class KKTSolver:
         if check:
             _check("kkt_solve", code)
         return dx, dy
+
+    def solve_multi(self, r_x, r_y, stream=None, check=True):
+        """r_x: CUDA float64 (nrhs, n), r_y: (nrhs, m), contiguous; returns
+        (dx, dy) of the same shapes and the per-RHS kkt_info list."""
+        import torch
+        k = int(r_x.shape[0])
+        dx = torch.empty_like(r_x)
+        dy = torch.empty((k, self.m), dtype=torch.float64, device=r_x.device)
+        code, infos = kkt_solve_multi(self.h, k, r_x.reshape(-1), r_y.reshape(-1), dx.view(-1), dy.view(-1),
+                                      self.n, self.m, stream)
+        if check:
+            _check("kkt_solve_multi", code)
+        return dx, dy, infos
+
+    def factor_batch(self, H_vals, J_vals, delta, gamma=-1.0, stream=None):
+        """H_vals: CUDA float64 (nsys, nnz(H~)), J_vals: (nsys, nnz(J)). Returns
+        (status code, per-system status array)."""
+        k = int(H_vals.shape[0])
+        st = np.zeros(k, np.int32)
+        code = _lib.kkt_factor_batch(self.h, k, _dev(H_vals.reshape(-1), k * self.nnz_h),
+                                     _dev(J_vals.reshape(-1), k * self.nnz_j), float(delta), float(gamma),
+                                     st.ctypes.data, _stream(stream))
+        return code, st
+
+    def solve_batch(self, r_x, r_y, stream=None):
+        """r_x: CUDA float64 (nsys, n), r_y: (nsys, m). Returns (dx, dy, infos,
+        per-system status, code)."""
+        import torch
+        k = int(r_x.shape[0])
+        dx = torch.empty_like(r_x)
+        dy = torch.empty((k, self.m), dtype=torch.float64, device=r_x.device)
+        infos = (kkt_info * k)()
+        st = np.zeros(k, np.int32)
+        code = _lib.kkt_solve_batch(self.h, k, _dev(r_x.reshape(-1), k * self.n), _dev(r_y.reshape(-1), k * self.m),
+                                    _dev(dx.view(-1), k * self.n), _dev(dy.view(-1), k * self.m),
+                                    C.cast(infos, C.c_void_p), st.ctypes.data, _stream(stream))
+        return dx, dy, [infos[j] for j in range(k)], st, code
 
     def hsolve(self, b, stream=None):
         import torch

@@ -87,6 +87,18 @@ struct kkt_handle_s {
   int* counters;   // fwd_arrive, fwd_done, bwd_arrive, bwd_done (npieces each), disp[3], bar[2]
   DevStatus* dst;
   DevStatus* hst = nullptr;  // pinned
+  int32_t* rhs_stat = nullptr;   // per right-hand side: CG products, status, delta_2 restart
+  // workspace of the multiple-right-hand-side solve (kMaxRhs vectors each),
+  // allocated by the first kkt_solve_multi
+  // saved factors of a batch of systems on this pattern (kkt_factor_batch):
+  // slot b holds system b's panels, triangle inverses and values
+  int64_t batch_cap = 0;
+  void *bL = nullptr, *bLinv = nullptr;
+  double *bHv = nullptr, *bJv = nullptr;
+  std::vector<int32_t> bstatus;
+  bool multi = false;
+  void *mv, *mzpart;
+  double *mrhx, *mp, *mr, *my, *mq, *mbS, *mres_x, *mres_y;
   double* d_dg = nullptr;    // device [delta, gamma] read by the assembly kernel
   unsigned long long* d_instr = nullptr;   // solve-kernel cycle counters (profile mode)
   double* h_dg = nullptr;    // pinned staging for it
@@ -207,6 +219,7 @@ kkt_status kkt_destroy(kkt_handle h) {
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->prof.a) cudaEventDestroy(h->prof.a);
   if (h->prof.b) cudaEventDestroy(h->prof.b);
+  if (h->bL) { cudaFree(h->bL); cudaFree(h->bLinv); cudaFree(h->bHv); cudaFree(h->bJv); }
   if (h->cg_a) cudaEventDestroy(h->cg_a);
   if (h->cg_b) cudaEventDestroy(h->cg_b);
   delete h;
@@ -343,7 +356,8 @@ kkt_status kkt_analyse(int64_t n, int64_t m, const int64_t* Hp, const int32_t* H
   h->rhx = A.alloc<double>(n);
   h->p = A.alloc<double>(m); h->r = A.alloc<double>(m); h->y = A.alloc<double>(m);
   h->q = A.alloc<double>(m); h->bS = A.alloc<double>(m);
-  h->red = A.alloc<double>((size_t)std::max(h->grid, 296) * 4);
+  h->red = A.alloc<double>((size_t)std::max(h->grid, 296) * kRedStride);
+  h->rhs_stat = A.alloc<int32_t>(3 * kMaxRhs);
   h->res_x = A.alloc<double>(n); h->res_y = A.alloc<double>(m);
   h->stage_rx = A.alloc<double>(n); h->stage_ry = A.alloc<double>(m);
   h->stage_dx = A.alloc<double>(n); h->stage_dy = A.alloc<double>(m);
@@ -500,6 +514,7 @@ static SolveArgs<T> solve_args(kkt_handle h) {
   a.bwd_arrive = h->counters + 2 * np; a.bwd_done = h->counters + 3 * np;
   a.disp = h->counters + 4 * np; a.bar = h->counters + 4 * np + 4;
   a.red = h->red; a.st = h->dst;
+  a.nrhs = 1; a.z_total = P.z_total; a.rhs_stat = h->rhs_stat;
   a.spin = h->opt.spin_cycles > 0 ? h->opt.spin_cycles : kSpinCycles;
   a.instr = h->profp ? h->d_instr : nullptr;
   return a;
@@ -507,10 +522,15 @@ static SolveArgs<T> solve_args(kkt_handle h) {
 
 template <typename T>
 static kkt_status solve_pass(kkt_handle h, const double* bx, const double* by, double* ox, double* oy,
-                             int accumulate, int mode, cudaStream_t st) {
+                             int accumulate, int mode, cudaStream_t st, int nrhs = 1) {
   CK(cudaMemsetAsync(h->counters, 0, sizeof(int) * (4 * (size_t)h->P.npieces + 8), st));
   SolveArgs<T> a = solve_args<T>(h);
   a.bx = bx; a.by = by; a.ox = ox; a.oy = oy; a.accumulate = accumulate; a.mode = mode;
+  if (nrhs > 1) {
+    a.nrhs = nrhs;
+    a.v = (T*)h->mv; a.zpart = (T*)h->mzpart; a.rhx = h->mrhx;
+    a.p = h->mp; a.r = h->mr; a.y = h->my; a.q = h->mq; a.bS = h->mbS;
+  }
   if (h->profp) {
     CK(prof_begin(h->profp, st));
     CK(launch_solve<T>(a, h->grid, h->ctas, st));
@@ -524,14 +544,15 @@ static kkt_status solve_pass(kkt_handle h, const double* bx, const double* by, d
 }
 
 static kkt_status residual(kkt_handle h, const double* bx, const double* by, const double* x,
-                           const double* y, cudaStream_t st) {
+                           const double* y, cudaStream_t st, double* res_x = nullptr, double* res_y = nullptr) {
   ResArgs r;
   r.n = h->P.n; r.m = h->P.m;
   r.Hs_ptr = h->Hs_ptr; r.Hs_col = h->Hs_col; r.Hs_vidx = h->Hs_vidx;
   r.J_rowptr = h->J_rowptr; r.J_colidx = h->J_colidx;
   r.JT_ptr = h->JTo_ptr; r.JT_row = h->JTo_row; r.JT_vidx = h->JTo_vidx;
   r.Hv = h->Hv; r.Jv = h->Jv; r.delta = h->delta;
-  r.bx = bx; r.by = by; r.x = x; r.y = y; r.res_x = h->res_x; r.res_y = h->res_y;
+  r.bx = bx; r.by = by; r.x = x; r.y = y;
+  r.res_x = res_x ? res_x : h->res_x; r.res_y = res_y ? res_y : h->res_y;
   r.red = h->red; r.st = h->dst;
   CK(prof_begin(h->profp, st));
   CK(launch_residual(r, st));
@@ -583,7 +604,197 @@ static kkt_status solve_common(kkt_handle h, const double* rx, const double* ry,
   return KKT_OK;
 }
 
+// Up to kMaxRhs right-hand sides in one persistent launch per refinement
+// pass: the triangular sweeps stage each L tile once for all of them; CG
+// runs independently per right-hand side (its own scalars and stop test).
+// Refinement passes continue while any RR(K_delta) > ir_rtol.
+static kkt_status solve_group(kkt_handle h, int R, const double* rx, const double* ry, double* dx, double* dy,
+                              kkt_info* info, cudaStream_t st) {
+  const bool f64 = h->opt.precision == KKT_FP64;
+  const int64_t n = h->P.n, m = h->P.m;
+  kkt_status s = reset_status(h, st);
+  if (s) return s;
+  int it_sum[kMaxRhs] = {0}, brk[kMaxRhs] = {0}, cst[kMaxRhs] = {0};
+  double rr[kMaxRhs] = {0}, be[kMaxRhs] = {0};
+  int32_t stat[3 * kMaxRhs];
+  for (int pass = 0;; pass++) {
+    const double* bx = pass == 0 ? rx : h->mres_x;
+    const double* by = pass == 0 ? ry : h->mres_y;
+    s = f64 ? solve_pass<double>(h, bx, by, dx, dy, pass > 0, 0, st, R)
+            : solve_pass<float>(h, bx, by, dx, dy, pass > 0, 0, st, R);
+    if (s) return s;
+    CK(cudaMemcpyAsync(stat, h->rhs_stat, sizeof(int32_t) * 3 * R, cudaMemcpyDeviceToHost, st));
+    if ((s = read_status(h, st))) return s;
+    if (h->hst->abort) return KKT_ERR_TIMEOUT;
+    if (!h->profp) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, h->cg_a, h->cg_b));
+      h->prof.ms[KKT_K_CG] += ms;
+      h->prof.n[KKT_K_CG] += 1;
+    }
+    double worst = 0.0;
+    for (int j = 0; j < R; j++) {
+      it_sum[j] += stat[3 * j];
+      cst[j] = stat[3 * j + 1];
+      brk[j] |= stat[3 * j + 2];
+      if ((s = residual(h, rx + j * n, ry + j * m, dx + j * n, dy + j * m, st, h->mres_x + j * n,
+                        h->mres_y + j * m)))
+        return s;
+      if ((s = read_status(h, st))) return s;
+      rr[j] = h->hst->rr;
+      be[j] = h->hst->be;
+      worst = std::max(worst, rr[j]);
+    }
+    for (int j = 0; j < R; j++) {
+      info[j].cg_iters = it_sum[j];
+      info[j].ir_steps = pass;
+      info[j].cg_status = cst[j];
+      info[j].delta2_used = brk[j];
+      info[j].rr = rr[j];
+      info[j].be = be[j];
+    }
+    for (int j = 0; j < R; j++) {
+      if (cst[j] == 3) return KKT_ERR_CG_BREAKDOWN;
+      if (cst[j] == 4) return KKT_ERR_CG_MAXIT;
+    }
+    if (!(worst > h->opt.ir_rtol) || pass >= h->opt.ir_maxit) break;
+  }
+  return KKT_OK;
+}
+
 extern "C" {
+
+// Batched form: nsys systems on the analysed pattern, factored one after
+// another with the handle's factorization (its captured graph) and kept in
+// per-system slots; each solve copies its system's factor back into the
+// working buffers (a few microseconds of device copies) and runs the solve.
+kkt_status kkt_factor_batch(kkt_handle h, int32_t nsys, const double* H_vals, const double* J_vals,
+                            double delta, double gamma, int32_t* status, void* stream) {
+  if (!h || nsys < 1 || !H_vals || (h->nnzJ > 0 && !J_vals)) return KKT_ERR_INVALID;
+  if (!h->on_device) return KKT_ERR_STATE;
+  CK(cudaSetDevice(h->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t es = h->opt.precision == KKT_FP64 ? sizeof(double) : sizeof(float);
+  const size_t pb = es * (size_t)h->P.panel_total, ib = es * (size_t)h->P.inv_total;
+  if (nsys > h->batch_cap) {
+    if (h->bL) { cudaFree(h->bL); cudaFree(h->bLinv); cudaFree(h->bHv); cudaFree(h->bJv); }
+    h->bL = h->bLinv = nullptr; h->bHv = h->bJv = nullptr; h->batch_cap = 0;
+    if (cudaMalloc(&h->bL, pb * nsys) || cudaMalloc(&h->bLinv, std::max<size_t>(ib, 16) * nsys) ||
+        cudaMalloc((void**)&h->bHv, sizeof(double) * std::max<int64_t>(h->nnzH, 1) * nsys) ||
+        cudaMalloc((void**)&h->bJv, sizeof(double) * std::max<int64_t>(h->nnzJ, 1) * nsys)) {
+      cudaGetLastError();
+      return KKT_ERR_OOM;
+    }
+    h->batch_cap = nsys;
+  }
+  h->bstatus.assign((size_t)nsys, KKT_ERR_STATE);
+  kkt_status worst = KKT_OK;
+  for (int b = 0; b < nsys; b++) {
+    CK(cudaMemcpyAsync(h->Hv, H_vals + (int64_t)b * h->nnzH, sizeof(double) * h->nnzH, cudaMemcpyDeviceToDevice,
+                       st));
+    if (h->nnzJ)
+      CK(cudaMemcpyAsync(h->Jv, J_vals + (int64_t)b * h->nnzJ, sizeof(double) * h->nnzJ,
+                         cudaMemcpyDeviceToDevice, st));
+    const kkt_status s = factor_common(h, delta, gamma, st);
+    h->bstatus[b] = s;
+    if (status) status[b] = s;
+    if (s == KKT_OK) {
+      CK(cudaMemcpyAsync((char*)h->bL + pb * b, h->L, pb, cudaMemcpyDeviceToDevice, st));
+      if (ib) CK(cudaMemcpyAsync((char*)h->bLinv + ib * b, h->Linv, ib, cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(h->bHv + (int64_t)b * h->nnzH, h->Hv, sizeof(double) * h->nnzH, cudaMemcpyDeviceToDevice,
+                         st));
+      if (h->nnzJ)
+        CK(cudaMemcpyAsync(h->bJv + (int64_t)b * h->nnzJ, h->Jv, sizeof(double) * h->nnzJ,
+                           cudaMemcpyDeviceToDevice, st));
+    } else if (s != KKT_ERR_NOT_SPD) {
+      return s;
+    } else {
+      worst = KKT_ERR_NOT_SPD;
+    }
+  }
+  CK(cudaStreamSynchronize(st));
+  h->factored = false;   // the working buffers hold a slot's copy only during kkt_solve_batch
+  return worst;
+}
+
+kkt_status kkt_solve_batch(kkt_handle h, int32_t nsys, const double* r_x, const double* r_y, double* dx,
+                           double* dy, kkt_info* info, int32_t* status, void* stream) {
+  if (!h || nsys < 1 || !r_x || !dx || (h->P.m > 0 && (!r_y || !dy))) return KKT_ERR_INVALID;
+  if (!h->on_device) return KKT_ERR_STATE;
+  if (nsys > (int32_t)h->bstatus.size()) return KKT_ERR_STATE;
+  CK(cudaSetDevice(h->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = h->P.n, m = h->P.m;
+  const size_t es = h->opt.precision == KKT_FP64 ? sizeof(double) : sizeof(float);
+  const size_t pb = es * (size_t)h->P.panel_total, ib = es * (size_t)h->P.inv_total;
+  kkt_status worst = KKT_OK;
+  for (int b = 0; b < nsys; b++) {
+    kkt_status s = (kkt_status)h->bstatus[b];
+    if (s == KKT_OK) {
+      CK(cudaMemcpyAsync(h->L, (char*)h->bL + pb * b, pb, cudaMemcpyDeviceToDevice, st));
+      if (ib) CK(cudaMemcpyAsync(h->Linv, (char*)h->bLinv + ib * b, ib, cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(h->Hv, h->bHv + (int64_t)b * h->nnzH, sizeof(double) * h->nnzH, cudaMemcpyDeviceToDevice,
+                         st));
+      if (h->nnzJ)
+        CK(cudaMemcpyAsync(h->Jv, h->bJv + (int64_t)b * h->nnzJ, sizeof(double) * h->nnzJ,
+                           cudaMemcpyDeviceToDevice, st));
+      h->factored = true;
+      s = solve_common(h, r_x + b * n, r_y + b * m, dx + b * n, dy + b * m, st);
+      h->factored = false;
+      if (info) info[b] = h->info;
+    } else if (info) {
+      std::memset(&info[b], 0, sizeof(kkt_info));
+    }
+    if (status) status[b] = s;
+    if (s == KKT_ERR_CUDA || s == KKT_ERR_TIMEOUT || s == KKT_ERR_OOM) return s;
+    if (s != KKT_OK && worst == KKT_OK) worst = s;
+  }
+  return worst;
+}
+
+kkt_status kkt_solve_multi(kkt_handle h, int32_t nrhs, const double* r_x, const double* r_y, double* dx,
+                           double* dy, kkt_info* info, void* stream) {
+  if (!h || nrhs < 1 || !r_x || !dx || (h->P.m > 0 && (!r_y || !dy))) return KKT_ERR_INVALID;
+  if (!h->on_device) return KKT_ERR_STATE;
+  if (!h->factored) return KKT_ERR_STATE;
+  CK(cudaSetDevice(h->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = h->P.n, m = h->P.m;
+  if (!h->multi) {
+    const size_t es = h->opt.precision == KKT_FP64 ? sizeof(double) : sizeof(float);
+    DevArena& A = h->mem;
+    h->mv = A.alloc<char>(es * (size_t)n * kMaxRhs);
+    h->mzpart = A.alloc<char>(es * (size_t)std::max<int64_t>(h->P.z_total, 1) * kMaxRhs);
+    h->mrhx = A.alloc<double>((size_t)n * kMaxRhs);
+    h->mp = A.alloc<double>((size_t)m * kMaxRhs); h->mr = A.alloc<double>((size_t)m * kMaxRhs);
+    h->my = A.alloc<double>((size_t)m * kMaxRhs); h->mq = A.alloc<double>((size_t)m * kMaxRhs);
+    h->mbS = A.alloc<double>((size_t)m * kMaxRhs);
+    h->mres_x = A.alloc<double>((size_t)n * kMaxRhs); h->mres_y = A.alloc<double>((size_t)m * kMaxRhs);
+    if (A.failed) return KKT_ERR_OOM;
+    h->multi = true;
+  }
+  h->inertia_ok = 0;
+  std::memset(&h->info, 0, sizeof(h->info));
+  std::vector<kkt_info> all((size_t)nrhs);
+  int brk = 0;
+  kkt_status s = KKT_OK;
+  for (int g0 = 0; g0 < nrhs && s == KKT_OK; g0 += kMaxRhs) {
+    const int R = std::min(kMaxRhs, nrhs - g0);
+    s = solve_group(h, R, r_x + g0 * n, r_y + g0 * m, dx + g0 * n, dy + g0 * m, all.data() + g0, st);
+  }
+  for (int j = 0; j < nrhs; j++) {
+    h->info.cg_iters = std::max(h->info.cg_iters, all[j].cg_iters);
+    h->info.ir_steps = std::max(h->info.ir_steps, all[j].ir_steps);
+    h->info.cg_status = std::max(h->info.cg_status, all[j].cg_status);
+    h->info.rr = std::max(h->info.rr, all[j].rr);
+    h->info.be = std::max(h->info.be, all[j].be);
+    brk |= all[j].delta2_used;
+  }
+  h->info.delta2_used = brk;
+  if (info) std::memcpy(info, all.data(), sizeof(kkt_info) * (size_t)nrhs);
+  if (s == KKT_OK) h->inertia_ok = brk ? 0 : 1;
+  return s;
+}
 
 kkt_status kkt_factor(kkt_handle h, const double* H_vals, const double* J_vals, double delta, double gamma,
                       void* stream) {

@@ -97,17 +97,27 @@ struct SolveArgs {
   double gamma, delta2, rtol;
   int32_t maxit;
   // workspace
+  // nrhs right-hand sides share every triangular sweep (each staged L tile
+  // serves all of them); vector j of each workspace array starts at j times
+  // its length (n for v, rhx, bx, ox; m for the CG vectors, by, oy; z_total
+  // for zpart)
+  int32_t nrhs;
+  int64_t z_total;
+  int32_t* rhs_stat;   // [kMaxRhs * 3]: CG products, status, delta_2 restart per right-hand side
   T* v;
   double *rhx, *p, *r, *y, *q, *bS;
   T* zpart;
   int *fwd_arrive, *fwd_done, *bwd_arrive, *bwd_done;
   int* disp;   // [3]
   int* bar;    // [2]
-  double* red; // [grid * 4]
+  double* red; // [grid * kRedStride]
   DevStatus* st;
   long long spin;  // bound of every wait, in clock cycles
   unsigned long long* instr;  // optional per-kernel cycle counters (profile mode), else null
 };
+
+constexpr int kMaxRhs = 8;                // right-hand sides per solve-kernel launch
+constexpr int kRedStride = 2 * kMaxRhs;   // doubles per CTA in the reduction buffer
 
 template <typename T>
 cudaError_t launch_solve(const SolveArgs<T>& a, int grid, int ctas, cudaStream_t st);

@@ -252,32 +252,43 @@ __device__ bool fwd_head(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>&
   if (!mbar_wait(a, h) || !dep) return false;
   // y = T^-1 b with the packed inverse (column k holds rows k..pw-1); the
   // k range of each row is split among G thread groups
-  {
-    const int pr = (pw + 31) & ~31;
-    const int G = max(1, (int)blockDim.x / pr);
-    const int i = tid % pr, g = tid / pr;
+  const int pr = (pw + 31) & ~31;
+  const int G = max(1, (int)blockDim.x / pr);
+  const int gi = tid % pr, gg0 = tid / pr;
+  for (int j = 0; j < a.nrhs; j++) {
+    T* vj = a.v + (int64_t)j * a.n;
+    if (j > 0) {
+      for (int i = tid; i < pw; i += blockDim.x) t.vec[i] = ldcg(&vj[f + i]);
+      __syncthreads();
+    }
     T acc = T(0);
-    if (g < G && i < pw)
-      for (int k = g; k <= i; k += G) acc += t.A[packed_off(pw, k) + i - k] * t.vec[k];
+    if (gg0 < G && gi < pw)
+      for (int k = gg0; k <= gi; k += G) acc += t.A[packed_off(pw, k) + gi - k] * t.vec[k];
     t.aux[tid] = acc;
     __syncthreads();
     if (tid < pw) {
       T y = T(0);
-      for (int gg = 0; gg < G; gg++) y += t.aux[gg * pr + tid];
+      for (int g = 0; g < G; g++) y += t.aux[g * pr + tid];
       t.vec2[tid] = y;
-      a.v[f + tid] = y;
+      vj[f + tid] = y;
     }
+    __syncthreads();
   }
-  __syncthreads();
   if (tid == 0) st_release(&a.fwd_done[p], e);
   if (rn > 0) {
     // chunk 0: b[rows] -= L21(0:rn) y
     const int d0 = (d.c + pw) & 3;
-    T* v = a.v;
-    rows_matvec(t.B, d.cs, d0, rn, pw, t.vec2, t.aux, [&](int i, T o) {
-      atomicAdd(&v[rn <= (int)blockDim.x ? myrow : rows[i]], -o);
-    });
-    __syncthreads();
+    for (int j = 0; j < a.nrhs; j++) {
+      T* vj = a.v + (int64_t)j * a.n;
+      if (a.nrhs > 1) {
+        for (int i = tid; i < pw; i += blockDim.x) t.vec2[i] = ldcg(&vj[f + i]);
+        __syncthreads();
+      }
+      rows_matvec(t.B, d.cs, d0, rn, pw, t.vec2, t.aux, [&](int i, T o) {
+        atomicAdd(&vj[rn <= (int)blockDim.x ? myrow : rows[i]], -o);
+      });
+      __syncthreads();
+    }
     if (tid == 0) {
       __threadfence();
       for (int64_t q = d.tp0; q < d.tp1; q++) atomicAdd(&a.fwd_arrive[a.hd_tgt[q]], 1);
@@ -316,11 +327,17 @@ __device__ bool fwd_chunk(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>
   if (!mbar_wait(a, h) || !dep) return false;
   mark(a, h, 5);
   const int d0 = (d.c + d.r0) & 3;
-  T* v = a.v;
-  rows_matvec(t.B, d.cs, d0, nr, pw, t.vec, t.aux, [&](int i, T o) {
-    atomicAdd(&v[nr <= (int)blockDim.x ? myrow : rows[i]], -o);
-  });
-  __syncthreads();
+  for (int j = 0; j < a.nrhs; j++) {
+    T* vj = a.v + (int64_t)j * a.n;
+    if (j > 0) {
+      for (int k = tid; k < pw; k += blockDim.x) t.vec[k] = ldcg(&vj[f + k]);
+      __syncthreads();
+    }
+    rows_matvec(t.B, d.cs, d0, nr, pw, t.vec, t.aux, [&](int i, T o) {
+      atomicAdd(&vj[nr <= (int)blockDim.x ? myrow : rows[i]], -o);
+    });
+    __syncthreads();
+  }
   mark(a, h, 6);
   if (tid == 0) {
     __threadfence();
@@ -355,25 +372,32 @@ __device__ bool bwd_chunk(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>
   }
   __syncthreads();
   const bool dep = h.flag != 0;
-  if (dep) {
+  auto gather = [&](const T* vj) {
     if (nr <= (int)blockDim.x) {
-      if (tid < nr) t.aux[tid] = ldcg(&a.v[myrow]);
+      if (tid < nr) t.aux[tid] = ldcg(&vj[myrow]);
     } else {
-      for (int i = tid; i < nr; i += blockDim.x) t.aux[i] = ldcg(&a.v[rows[i]]);
+      for (int i = tid; i < nr; i += blockDim.x) t.aux[i] = ldcg(&vj[rows[i]]);
     }
-  }
+  };
+  if (dep) gather(a.v);
   if (!mbar_wait(a, h) || !dep) return false;
   const int d0 = (d.c + d.r0) & 3;
   const int cs = d.cs;
   const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  T* z = a.zpart + d.zoff;
-  for (int k = warp; k < pw; k += nw) {
-    T s = T(0);
-    for (int i = lane; i < nr; i += 32) s += t.B[k * cs + d0 + i] * t.aux[i];
-    s = warp_sum(s);
-    if (lane == 0) z[k] = s;
+  for (int j = 0; j < a.nrhs; j++) {
+    if (j > 0) {
+      gather(a.v + (int64_t)j * a.n);
+      __syncthreads();
+    }
+    T* z = a.zpart + (int64_t)j * a.z_total + d.zoff;
+    for (int k = warp; k < pw; k += nw) {
+      T s = T(0);
+      for (int i = lane; i < nr; i += 32) s += t.B[k * cs + d0 + i] * t.aux[i];
+      s = warp_sum(s);
+      if (lane == 0) z[k] = s;
+    }
+    __syncthreads();
   }
-  __syncthreads();
   if (tid == 0) {
     __threadfence();
     atomicAdd(&a.bwd_arrive[p], 1);
@@ -407,43 +431,53 @@ __device__ bool bwd_head(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>&
   }
   __syncthreads();
   const bool dep = h.flag != 0;
-  if (dep) {
+  // t = v[cols] - (the chunks' partial sums), and v at the chunk-0 rows
+  auto gather = [&](int j) {
+    const T* vj = a.v + (int64_t)j * a.n;
     if (rn <= (int)blockDim.x) {
-      if (tid < rn) t.aux[tid] = ldcg(&a.v[myrow]);
+      if (tid < rn) t.aux[tid] = ldcg(&vj[myrow]);
     } else {
-      for (int i = tid; i < rn; i += blockDim.x) t.aux[i] = ldcg(&a.v[rows[i]]);
+      for (int i = tid; i < rn; i += blockDim.x) t.aux[i] = ldcg(&vj[rows[i]]);
     }
-    const T* z = a.zpart + d.zoff;
+    const T* z = a.zpart + (int64_t)j * a.z_total + d.zoff;
     for (int i = tid; i < pw; i += blockDim.x) {
-      T v = ldcg(&a.v[f + i]);
+      T v = ldcg(&vj[f + i]);
       for (int k = 0; k < nch; k++) v -= ldcg(&z[(int64_t)k * pw + i]);
       t.vec[i] = v;
     }
-  }
+  };
+  if (dep) gather(0);
   if (!mbar_wait(a, h) || !dep) return false;
   const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  if (rn > 0) {
-    const int d0 = (d.c + pw) & 3;
-    const int cs = d.cs;
+  for (int j = 0; j < a.nrhs; j++) {
+    if (j > 0) {
+      gather(j);
+      __syncthreads();
+    }
+    if (rn > 0) {
+      const int d0 = (d.c + pw) & 3;
+      const int cs = d.cs;
+      for (int k = warp; k < pw; k += nw) {
+        T s = T(0);
+        for (int i = lane; i < rn; i += 32) s += t.B[k * cs + d0 + i] * t.aux[i];
+        s = warp_sum(s);
+        if (lane == 0) t.vec[k] -= s;
+      }
+      __syncthreads();
+    }
+    // x = T^-T t: x_k = sum_{i >= k} Tinv[i, k] t_i (packed columns)
     for (int k = warp; k < pw; k += nw) {
+      const int off = packed_off(pw, k);
       T s = T(0);
-      for (int i = lane; i < rn; i += 32) s += t.B[k * cs + d0 + i] * t.aux[i];
+      for (int i = k + lane; i < pw; i += 32) s += t.A[off + i - k] * t.vec[i];
       s = warp_sum(s);
-      if (lane == 0) t.vec[k] -= s;
+      if (lane == 0) t.vec2[k] = s;
     }
     __syncthreads();
+    T* vj = a.v + (int64_t)j * a.n;
+    for (int i = tid; i < pw; i += blockDim.x) vj[f + i] = t.vec2[i];
+    __syncthreads();
   }
-  // x = T^-T t: x_k = sum_{i >= k} Tinv[i, k] t_i (packed columns)
-  for (int k = warp; k < pw; k += nw) {
-    const int off = packed_off(pw, k);
-    T s = T(0);
-    for (int i = k + lane; i < pw; i += 32) s += t.A[off + i - k] * t.vec[i];
-    s = warp_sum(s);
-    if (lane == 0) t.vec2[k] = s;
-  }
-  __syncthreads();
-  for (int i = tid; i < pw; i += blockDim.x) a.v[f + i] = t.vec2[i];
-  __syncthreads();
   if (tid == 0) st_release(&a.bwd_done[p], e);
   return true;
 }
@@ -478,7 +512,7 @@ __device__ void stage_subtree(const SolveArgs<T>& a, SolveSmemHdr& h, const Tile
 // shared memory inside the subtree's column range and into v outside it.
 template <typename T>
 __device__ void warp_fwd_supernode(const SolveArgs<T>& a, const Tiles<T>& t, int s, int clo, int chi,
-                                   int64_t pbase, int64_t ibase, T* xs) {
+                                   int64_t pbase, int64_t ibase, T* xs, T* vj) {
   const int lane = threadIdx.x & 31;
   const int w = __ldg(&a.sw_[s]), nr = __ldg(&a.snr[s]), ld = __ldg(&a.sld[s]), f = __ldg(&a.sfirst[s]) - clo;
   const T* P = t.B + (__ldg(&a.poff[s]) - pbase);
@@ -518,7 +552,7 @@ __device__ void warp_fwd_supernode(const SolveArgs<T>& a, const Tiles<T>& t, int
     for (int u = 0; u < 4; u++) {
       if (rr[u] < 0) continue;
       if (rr[u] < chi) atomicAdd(&xs[rr[u] - clo], -o[u]);
-      else atomicAdd(&a.v[rr[u]], -o[u]);
+      else atomicAdd(&vj[rr[u]], -o[u]);
     }
   }
 }
@@ -529,7 +563,7 @@ __device__ void warp_fwd_supernode(const SolveArgs<T>& a, const Tiles<T>& t, int
 constexpr int kSubScratch = 160;
 template <typename T>
 __device__ void warp_bwd_supernode(const SolveArgs<T>& a, const Tiles<T>& t, int s, int clo, int chi,
-                                   int64_t pbase, int64_t ibase, T* xs, T* scratch) {
+                                   int64_t pbase, int64_t ibase, T* xs, T* scratch, const T* vj) {
   const int lane = threadIdx.x & 31;
   const int w = __ldg(&a.sw_[s]), nr = __ldg(&a.snr[s]), ld = __ldg(&a.sld[s]), f = __ldg(&a.sfirst[s]) - clo;
   const T* P = t.B + (__ldg(&a.poff[s]) - pbase);
@@ -542,7 +576,7 @@ __device__ void warp_bwd_supernode(const SolveArgs<T>& a, const Tiles<T>& t, int
   const int nb = nr - w;
   for (int r = lane; r < nb && r < cache; r += 32) {
     const int row = __ldg(&rows[w + r]);
-    xr[r] = row < chi ? xs[row - clo] : ldcg(&a.v[row]);
+    xr[r] = row < chi ? xs[row - clo] : ldcg(&vj[row]);
   }
   __syncwarp();
   for (int k = 0; k < w; k++) {
@@ -553,7 +587,7 @@ __device__ void warp_bwd_supernode(const SolveArgs<T>& a, const Tiles<T>& t, int
         x = xr[r];
       } else {
         const int row = __ldg(&rows[w + r]);
-        x = row < chi ? xs[row - clo] : ldcg(&a.v[row]);
+        x = row < chi ? xs[row - clo] : ldcg(&vj[row]);
       }
       acc += P[w + r + k * ld] * x;
     }
@@ -587,9 +621,18 @@ __device__ bool fwd_subtree(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<
   if (!mbar_wait(a, h)) return false;
   mark(a, h, 0);
   const long long tl0 = clock64();
-  for (int L = a.st_lptr[st]; L + 1 < a.st_lptr[st + 1]; L++) {
-    for (int q = a.st_lev[L] + warp; q < a.st_lev[L + 1]; q += nw)
-      warp_fwd_supernode(a, t, a.st_sn[q], clo, chi, pbase, ibase, xs);
+  for (int j = 0; j < a.nrhs; j++) {
+    T* vj = a.v + (int64_t)j * a.n;
+    if (j > 0) {
+      for (int i = tid; i < chi - clo; i += blockDim.x) xs[i] = ldcg(&vj[clo + i]);
+      __syncthreads();
+    }
+    for (int L = a.st_lptr[st]; L + 1 < a.st_lptr[st + 1]; L++) {
+      for (int q = a.st_lev[L] + warp; q < a.st_lev[L + 1]; q += nw)
+        warp_fwd_supernode(a, t, a.st_sn[q], clo, chi, pbase, ibase, xs, vj);
+      __syncthreads();
+    }
+    for (int i = tid; i < chi - clo; i += blockDim.x) vj[clo + i] = xs[i];
     __syncthreads();
   }
   if (tid == 0) {
@@ -597,8 +640,6 @@ __device__ bool fwd_subtree(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<
     h.n_lvl += a.st_lptr[st + 1] - a.st_lptr[st] - 1;
   }
   mark(a, h, 1);
-  for (int i = tid; i < chi - clo; i += blockDim.x) a.v[clo + i] = xs[i];
-  __syncthreads();
   if (tid == 0) {
     __threadfence();
     for (int64_t q = a.st_tptr[st]; q < a.st_tptr[st + 1]; q++) atomicAdd(&a.fwd_arrive[a.st_tgt[q]], 1);
@@ -629,17 +670,24 @@ __device__ bool bwd_subtree(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<
   if (!mbar_wait(a, h) || !dep) return false;
   T* scratch = t.aux + kSubScratch * warp;   // 8 warps x 160 <= max_rows + kSolveThreads
   const long long tl0 = clock64();
-  for (int L = a.st_lptr[st + 1] - 2; L >= a.st_lptr[st]; L--) {
-    for (int q = a.st_lev[L] + warp; q < a.st_lev[L + 1]; q += nw)
-      warp_bwd_supernode(a, t, a.st_sn[q], clo, chi, pbase, ibase, xs, scratch);
-    __syncthreads();
+  for (int j = 0; j < a.nrhs; j++) {
+    T* vj = a.v + (int64_t)j * a.n;
+    if (j > 0) {
+      for (int i = tid; i < chi - clo; i += blockDim.x) xs[i] = ldcg(&vj[clo + i]);
+      __syncthreads();
+    }
+    for (int L = a.st_lptr[st + 1] - 2; L >= a.st_lptr[st]; L--) {
+      for (int q = a.st_lev[L] + warp; q < a.st_lev[L + 1]; q += nw)
+        warp_bwd_supernode(a, t, a.st_sn[q], clo, chi, pbase, ibase, xs, scratch, vj);
+      __syncthreads();
+    }
+    for (int i = tid; i < chi - clo; i += blockDim.x) vj[clo + i] = xs[i];
+    __syncthreads();   // the results are read after the next grid barrier
   }
   if (tid == 0) {
     h.c_lvl += clock64() - tl0;
     h.n_lvl += a.st_lptr[st + 1] - a.st_lptr[st] - 1;
   }
-  for (int i = tid; i < chi - clo; i += blockDim.x) a.v[clo + i] = xs[i];
-  __syncthreads();   // the results are read after the next grid barrier
   return true;
 }
 
@@ -666,30 +714,31 @@ __device__ bool grid_barrier(const SolveArgs<T>& a, SolveSmemHdr& h) {
   return h.flag != 0;
 }
 
-// per-block partial sums of two values -> a.red[block*4 + {0,1}]
+// per-block partial sums of two values -> a.red[block * kRedStride + 2 slot + {0,1}]
 template <typename T>
-__device__ void block_partial2(const SolveArgs<T>& a, SolveSmemHdr& h, double v0, double v1) {
+__device__ void block_partial2(const SolveArgs<T>& a, SolveSmemHdr& h, double v0, double v1, int slot = 0) {
   v0 = warp_sum(v0);
   v1 = warp_sum(v1);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();   // the previous call's reader of dred is done
   if (lane == 0) { h.dred[warp * 2] = v0; h.dred[warp * 2 + 1] = v1; }
   __syncthreads();
   if (threadIdx.x == 0) {
     double s0 = 0, s1 = 0;
     for (int w = 0; w < kSolveThreads / 32; w++) { s0 += h.dred[w * 2]; s1 += h.dred[w * 2 + 1]; }
-    a.red[blockIdx.x * 4] = s0;
-    a.red[blockIdx.x * 4 + 1] = s1;
+    a.red[blockIdx.x * kRedStride + 2 * slot] = s0;
+    a.red[blockIdx.x * kRedStride + 2 * slot + 1] = s1;
   }
 }
 
 // the same grid totals in every block (fixed summation order)
 template <typename T>
-__device__ void grid_total2(const SolveArgs<T>& a, SolveSmemHdr& h, double& t0, double& t1) {
+__device__ void grid_total2(const SolveArgs<T>& a, SolveSmemHdr& h, double& t0, double& t1, int slot = 0) {
   if (threadIdx.x < 32) {
     double s0 = 0, s1 = 0;
     for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) {
-      s0 += __ldcg(&a.red[b * 4]);
-      s1 += __ldcg(&a.red[b * 4 + 1]);
+      s0 += __ldcg(&a.red[b * kRedStride + 2 * slot]);
+      s1 += __ldcg(&a.red[b * kRedStride + 2 * slot + 1]);
     }
     s0 = warp_sum(s0);
     s1 = warp_sum(s1);
@@ -803,122 +852,209 @@ __global__ void __launch_bounds__(kSolveThreads, MB) k_cg(SolveArgs<T> a) {
   const int64_t gs = (int64_t)gridDim.x * blockDim.x;
   const int64_t n = a.n, m = a.m;
   int seq = 0, e = 0;
+  const int R = a.nrhs;
   // phase 0: r^_x = r_x + gamma J^T r_y in permuted labels; v = r^_x
-  for (int64_t k = gt; k < n; k += gs) {
-    const int32_t o = a.perm[k];
-    double s = 0.0;
-    if (a.mode == 0)
-      for (int64_t q = a.JT_ptr[k]; q < a.JT_ptr[k + 1]; q++) s += a.Jv[a.JT_vidx[q]] * a.by[a.JT_row[q]];
-    const double rh = a.bx[o] + a.gamma * s;
-    a.rhx[k] = rh;
-    a.v[k] = (T)rh;
+  for (int j = 0; j < R; j++) {
+    const double* bx = a.bx + (int64_t)j * n;
+    const double* by = a.by + (int64_t)j * m;
+    double* rhx = a.rhx + (int64_t)j * n;
+    T* v = a.v + (int64_t)j * n;
+    for (int64_t k = gt; k < n; k += gs) {
+      const int32_t o = a.perm[k];
+      double s = 0.0;
+      if (a.mode == 0)
+        for (int64_t q = a.JT_ptr[k]; q < a.JT_ptr[k + 1]; q++) s += a.Jv[a.JT_vidx[q]] * by[a.JT_row[q]];
+      const double rh = bx[o] + a.gamma * s;
+      rhx[k] = rh;
+      v[k] = (T)rh;
+    }
   }
   if (!grid_barrier(a, sm)) return;
   if (!hsolve(a, sm, tl, seq, e)) return;
   if (a.mode == 1) {
-    for (int64_t k = gt; k < n; k += gs) {
-      const double val = (double)ldcg(&a.v[k]);
-      const int32_t o = a.perm[k];
-      a.ox[o] = a.accumulate ? a.ox[o] + val : val;
+    for (int j = 0; j < R; j++) {
+      const T* v = a.v + (int64_t)j * n;
+      double* ox = a.ox + (int64_t)j * n;
+      for (int64_t k = gt; k < n; k += gs) {
+        const double val = (double)ldcg(&v[k]);
+        const int32_t o = a.perm[k];
+        ox[o] = a.accumulate ? ox[o] + val : val;
+      }
     }
     flush_counters(a, sm);
     return;
   }
+  // per-right-hand-side CG state: identical in every CTA (grid totals are
+  // summed in a fixed order), kept in shared memory
+  __shared__ double s_rho[kMaxRhs], s_rqmax[kMaxRhs], s_d2[kMaxRhs], s_bn2[kMaxRhs], s_alpha[kMaxRhs];
+  __shared__ int s_it[kMaxRhs], s_status[kMaxRhs], s_brk[kMaxRhs], s_step[kMaxRhs];
   // b_S = J w - r_y
-  double part = 0.0;
-  for (int64_t i = gt; i < m; i += gs) {
-    double s = 0.0;
-    for (int64_t q = a.J_rowptr[i]; q < a.J_rowptr[i + 1]; q++) s += a.Jv[q] * (double)ldcg(&a.v[a.Jcol_perm[q]]);
-    const double b = s - a.by[i];
-    a.bS[i] = b; a.r[i] = b; a.p[i] = b; a.y[i] = 0.0;
-    part += b * b;
-  }
-  block_partial2(a, sm, part, 0.0);
-  if (!grid_barrier(a, sm)) return;
-  double bn2, dummy;
-  grid_total2(a, sm, bn2, dummy);
-  double rho = bn2, rqmax = 0.0, d2 = 0.0;
-  int it = 0, status = 4, brk = 0;
-  const double stop = a.rtol * sqrt(bn2);
-  for (;;) {
-    if (sqrt(rho) <= stop) { status = 0; break; }
-    if (it >= a.maxit) { status = 4; break; }
-    for (int64_t k = gt; k < n; k += gs) {
+  for (int j = 0; j < R; j++) {
+    const T* v = a.v + (int64_t)j * n;
+    const double* by = a.by + (int64_t)j * m;
+    double *bS = a.bS + j * m, *r = a.r + j * m, *p = a.p + j * m, *y = a.y + j * m;
+    double part = 0.0;
+    for (int64_t i = gt; i < m; i += gs) {
       double s = 0.0;
-      for (int64_t q = a.JT_ptr[k]; q < a.JT_ptr[k + 1]; q++) s += a.Jv[a.JT_vidx[q]] * __ldcg(&a.p[a.JT_row[q]]);
-      a.v[k] = (T)s;
+      for (int64_t q = a.J_rowptr[i]; q < a.J_rowptr[i + 1]; q++) s += a.Jv[q] * (double)ldcg(&v[a.Jcol_perm[q]]);
+      const double b = s - by[i];
+      bS[i] = b; r[i] = b; p[i] = b; y[i] = 0.0;
+      part += b * b;
+    }
+    block_partial2(a, sm, part, 0.0, j);
+  }
+  if (!grid_barrier(a, sm)) return;
+  for (int j = 0; j < R; j++) {
+    double bn2, dummy;
+    grid_total2(a, sm, bn2, dummy, j);
+    if (threadIdx.x == 0) {
+      s_bn2[j] = bn2; s_rho[j] = bn2; s_rqmax[j] = 0.0; s_d2[j] = 0.0;
+      s_it[j] = 0; s_status[j] = -1; s_brk[j] = 0;
+    }
+  }
+  __syncthreads();
+  for (;;) {
+    // status -1 = running; 0 converged, 3 breakdown, 4 iteration limit
+    if (threadIdx.x == 0)
+      for (int j = 0; j < R; j++) {
+        if (s_status[j] != -1) continue;
+        if (sqrt(s_rho[j]) <= a.rtol * sqrt(s_bn2[j])) s_status[j] = 0;
+        else if (s_it[j] >= a.maxit) s_status[j] = 4;
+      }
+    __syncthreads();
+    bool any = false;
+    for (int j = 0; j < R; j++) any |= s_status[j] == -1;
+    if (!any) break;
+    // v = J^T p (finished right-hand sides ride along unchanged)
+    for (int j = 0; j < R; j++) {
+      const double* p = a.p + j * m;
+      T* v = a.v + (int64_t)j * n;
+      for (int64_t k = gt; k < n; k += gs) {
+        double s = 0.0;
+        for (int64_t q = a.JT_ptr[k]; q < a.JT_ptr[k + 1]; q++) s += a.Jv[a.JT_vidx[q]] * __ldcg(&p[a.JT_row[q]]);
+        v[k] = (T)s;
+      }
     }
     if (!grid_barrier(a, sm)) return;
     if (!hsolve(a, sm, tl, seq, e)) return;
-    double pq = 0.0, pp = 0.0;
-    for (int64_t i = gt; i < m; i += gs) {
-      double s = 0.0;
-      for (int64_t q = a.J_rowptr[i]; q < a.J_rowptr[i + 1]; q++) s += a.Jv[q] * (double)ldcg(&a.v[a.Jcol_perm[q]]);
-      const double pi = __ldcg(&a.p[i]);
-      const double qi = s + d2 * pi;
-      a.q[i] = qi;
-      pq += pi * qi;
-      pp += pi * pi;
+    for (int j = 0; j < R; j++) {
+      if (s_status[j] != -1) continue;
+      const T* v = a.v + (int64_t)j * n;
+      const double* p = a.p + j * m;
+      double* q_ = a.q + j * m;
+      const double d2 = s_d2[j];
+      double pq = 0.0, pp = 0.0;
+      for (int64_t i = gt; i < m; i += gs) {
+        double s = 0.0;
+        for (int64_t q = a.J_rowptr[i]; q < a.J_rowptr[i + 1]; q++) s += a.Jv[q] * (double)ldcg(&v[a.Jcol_perm[q]]);
+        const double pi = __ldcg(&p[i]);
+        const double qi = s + d2 * pi;
+        q_[i] = qi;
+        pq += pi * qi;
+        pp += pi * pi;
+      }
+      block_partial2(a, sm, pq, pp, j);
     }
-    block_partial2(a, sm, pq, pp);
     if (!grid_barrier(a, sm)) return;
-    double PQ, PP;
-    grid_total2(a, sm, PQ, PP);
-    it++;
-    const double rq = PQ / PP;
-    if (rq > rqmax) rqmax = rq;
-    if (!(PQ > 0.0) || rq <= 1e-12 * rqmax) {
-      if (d2 == 0.0 && a.delta2 > 0.0) {        // restart once on S + delta_2 I
-        brk = 1;
-        d2 = a.delta2;
-        rqmax = 0.0;
-        rho = bn2;
-        for (int64_t i = gt; i < m; i += gs) {
-          const double b = __ldcg(&a.bS[i]);
-          a.y[i] = 0.0; a.r[i] = b; a.p[i] = b;
+    // step kind per right-hand side: 1 = CG step, 2 = delta_2 restart
+    for (int j = 0; j < R; j++) {
+      if (s_status[j] != -1) continue;
+      double PQ, PP;
+      grid_total2(a, sm, PQ, PP, j);
+      if (threadIdx.x == 0) {
+        s_it[j]++;
+        const double rq = PQ / PP;
+        if (rq > s_rqmax[j]) s_rqmax[j] = rq;
+        if (!(PQ > 0.0) || rq <= 1e-12 * s_rqmax[j]) {
+          if (s_d2[j] == 0.0 && a.delta2 > 0.0) {   // restart once on S + delta_2 I
+            s_brk[j] = 1; s_d2[j] = a.delta2; s_rqmax[j] = 0.0; s_rho[j] = s_bn2[j];
+            s_step[j] = 2;
+          } else {
+            s_status[j] = 3;
+            s_step[j] = 0;
+          }
+        } else {
+          s_alpha[j] = s_rho[j] / PQ;
+          s_step[j] = 1;
         }
-        if (!grid_barrier(a, sm)) return;
+      }
+    }
+    __syncthreads();
+    for (int j = 0; j < R; j++) {
+      if (s_status[j] != -1) continue;
+      double *p = a.p + j * m, *r = a.r + j * m, *y = a.y + j * m;
+      const double* q_ = a.q + j * m;
+      if (s_step[j] == 2) {
+        const double* bS = a.bS + j * m;
+        for (int64_t i = gt; i < m; i += gs) {
+          const double b = __ldcg(&bS[i]);
+          y[i] = 0.0; r[i] = b; p[i] = b;
+        }
         continue;
       }
-      status = 3;
-      break;
+      const double alpha = s_alpha[j];
+      double rr = 0.0;
+      for (int64_t i = gt; i < m; i += gs) {
+        const double pi = __ldcg(&p[i]), qi = __ldcg(&q_[i]);
+        y[i] += alpha * pi;
+        const double ri = __ldcg(&r[i]) - alpha * qi;
+        r[i] = ri;
+        rr += ri * ri;
+      }
+      block_partial2(a, sm, rr, 0.0, j);
     }
-    const double alpha = rho / PQ;
-    double rr = 0.0;
-    for (int64_t i = gt; i < m; i += gs) {
-      const double pi = __ldcg(&a.p[i]), qi = __ldcg(&a.q[i]);
-      a.y[i] += alpha * pi;
-      const double ri = __ldcg(&a.r[i]) - alpha * qi;
-      a.r[i] = ri;
-      rr += ri * ri;
-    }
-    block_partial2(a, sm, rr, 0.0);
     if (!grid_barrier(a, sm)) return;
-    double rho2;
-    grid_total2(a, sm, rho2, dummy);
-    const double beta = rho2 / rho;
-    rho = rho2;
-    for (int64_t i = gt; i < m; i += gs) a.p[i] = __ldcg(&a.r[i]) + beta * __ldcg(&a.p[i]);
+    for (int j = 0; j < R; j++) {
+      if (s_status[j] != -1 || s_step[j] != 1) continue;
+      double rho2, dummy;
+      grid_total2(a, sm, rho2, dummy, j);
+      const double beta = rho2 / s_rho[j];
+      double* p = a.p + j * m;
+      const double* r = a.r + j * m;
+      for (int64_t i = gt; i < m; i += gs) p[i] = __ldcg(&r[i]) + beta * __ldcg(&p[i]);
+      __syncthreads();
+      if (threadIdx.x == 0) s_rho[j] = rho2;
+    }
     if (!grid_barrier(a, sm)) return;
   }
   // dx = H^-1 (r^_x - J^T dy)
-  for (int64_t k = gt; k < n; k += gs) {
-    double s = 0.0;
-    for (int64_t q = a.JT_ptr[k]; q < a.JT_ptr[k + 1]; q++) s += a.Jv[a.JT_vidx[q]] * __ldcg(&a.y[a.JT_row[q]]);
-    a.v[k] = (T)(__ldcg(&a.rhx[k]) - s);
+  for (int j = 0; j < R; j++) {
+    const double* y = a.y + j * m;
+    const double* rhx = a.rhx + (int64_t)j * n;
+    T* v = a.v + (int64_t)j * n;
+    for (int64_t k = gt; k < n; k += gs) {
+      double s = 0.0;
+      for (int64_t q = a.JT_ptr[k]; q < a.JT_ptr[k + 1]; q++) s += a.Jv[a.JT_vidx[q]] * __ldcg(&y[a.JT_row[q]]);
+      v[k] = (T)(__ldcg(&rhx[k]) - s);
+    }
   }
   if (!grid_barrier(a, sm)) return;
   if (!hsolve(a, sm, tl, seq, e)) return;
-  for (int64_t k = gt; k < n; k += gs) {
-    const double val = (double)ldcg(&a.v[k]);
-    const int32_t o = a.perm[k];
-    a.ox[o] = a.accumulate ? a.ox[o] + val : val;
-  }
-  for (int64_t i = gt; i < m; i += gs) {
-    const double yi = __ldcg(&a.y[i]);
-    a.oy[i] = a.accumulate ? a.oy[i] + yi : yi;
+  for (int j = 0; j < R; j++) {
+    const T* v = a.v + (int64_t)j * n;
+    const double* y = a.y + j * m;
+    double* ox = a.ox + (int64_t)j * n;
+    double* oy = a.oy + j * m;
+    for (int64_t k = gt; k < n; k += gs) {
+      const double val = (double)ldcg(&v[k]);
+      const int32_t o = a.perm[k];
+      ox[o] = a.accumulate ? ox[o] + val : val;
+    }
+    for (int64_t i = gt; i < m; i += gs) {
+      const double yi = __ldcg(&y[i]);
+      oy[i] = a.accumulate ? oy[i] + yi : yi;
+    }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
+    int it = 0, status = 0, brk = 0;
+    for (int j = 0; j < R; j++) {
+      a.rhs_stat[3 * j] = s_it[j];
+      a.rhs_stat[3 * j + 1] = s_status[j];
+      a.rhs_stat[3 * j + 2] = s_brk[j];
+      it = max(it, s_it[j]);
+      status = max(status, s_status[j]);
+      brk |= s_brk[j];
+    }
     a.st->cg_iters = it;
     a.st->cg_status = status;
     a.st->breakdown = brk;

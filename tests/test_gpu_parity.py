@@ -384,3 +384,79 @@ def test_4x4_grid_matches_oracle(precision):
     """50x40 grid, J_d with 500 local rows, D_s over eight decades."""
     p = W.grid_4x4_parts("grid2d_n2000")
     assert rel(_gpu_4x4(p, precision), _oracle_4x4(p)) <= 1e-6
+
+
+# ----------------------------------------------------------------- several right-hand sides (a12)
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("nrhs", [1, 3, 8, 11])
+def test_multi_rhs_matches_oracle(precision, nrhs):
+    """One factor, nrhs right-hand sides sharing the triangular sweeps (groups
+    of up to 8 per launch): every solution equals the oracle's solve of that
+    right-hand side, and each reaches the RR target."""
+    sys = W.make_config("grid2d_n2000")
+    rng = np.random.default_rng(nrhs)
+    RX = rng.standard_normal((nrhs, sys.n))
+    RY = rng.standard_normal((nrhs, sys.m))
+    s = K.KKTSolver(sys.n, sys.m, sys.H_colptr, sys.H_rowidx, sys.J_rowptr, sys.J_colidx, precision=precision,
+                    ordering="nd")
+    s.factor(cu(sys.H_vals), cu(sys.J_vals), sys.delta, sys.gamma)
+    dx, dy, infos = s.solve_multi(cu(RX), cu(RY))
+    dx, dy = dx.cpu().numpy(), dy.cpu().numpy()
+    sym = O.Symbolic(sys.n, sys.m, sys.H_colptr, sys.H_rowidx, sys.J_rowptr, sys.J_colidx)
+    fac = O.Factor(sym, sys.H_vals, sys.J_vals, sys.delta, sys.gamma)
+    for j in range(nrhs):
+        odx, ody, oinfo = fac.solve(RX[j], RY[j])
+        assert rel(np.concatenate([dx[j], dy[j]]), np.concatenate([odx, ody])) <= 1e-6
+        assert infos[j].rr <= 1e-8 and infos[j].cg_status == 0
+        if precision == "fp64":
+            assert abs(infos[j].cg_iters - oinfo["iters"]) <= 1
+    assert s.info.rr == max(i.rr for i in infos)
+    assert s.inertia_ok
+
+
+def test_multi_rhs_equals_single_solves():
+    """The same right-hand sides solved together and one at a time agree to
+    rounding (FP64)."""
+    sys = W.make_config("grid2d_n20k")
+    rng = np.random.default_rng(5)
+    RX = rng.standard_normal((5, sys.n))
+    RY = rng.standard_normal((5, sys.m))
+    s = K.KKTSolver(sys.n, sys.m, sys.H_colptr, sys.H_rowidx, sys.J_rowptr, sys.J_colidx, ordering="nd")
+    s.factor(cu(sys.H_vals), cu(sys.J_vals), sys.delta, sys.gamma)
+    dx, dy, _ = s.solve_multi(cu(RX), cu(RY))
+    for j in range(5):
+        sx, sy = s.solve(cu(RX[j]), cu(RY[j]))
+        a = torch.cat([dx[j], dy[j]]).cpu().numpy()
+        b = torch.cat([sx, sy]).cpu().numpy()
+        assert rel(a, b) <= 1e-10
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batched_systems_match_oracle(precision):
+    """Five systems on one analysed pattern (the 50x40 grid with per-entry
+    rescaled barriers, one of them shifted to be indefinite): each solution
+    equals the oracle's; the indefinite one reports NOT_SPD and is skipped."""
+    base = W.make_config("grid2d_n2000")
+    systems = [base]
+    for t in range(1, 5):
+        systems.append(W.rescale_barrier(systems[-1], seed=(7, t)))
+    bad = 3
+    Hbad = systems[bad].H_vals.copy()
+    diag = systems[bad].H_colptr[:-1]           # the diagonal entry leads each lower column
+    Hbad[diag] -= 1e3
+    systems[bad] = W.KKTSystem(base.n, base.m, base.H_colptr, base.H_rowidx, Hbad, base.J_rowptr,
+                               base.J_colidx, base.J_vals, systems[bad].r_x, systems[bad].r_y, base.delta, base.gamma)
+    s = K.KKTSolver(base.n, base.m, base.H_colptr, base.H_rowidx, base.J_rowptr, base.J_colidx,
+                    precision=precision, ordering="nd")
+    code, st = s.factor_batch(cu(np.stack([x.H_vals for x in systems])), cu(np.stack([x.J_vals for x in systems])),
+                              base.delta, base.gamma)
+    assert code == 2 and list(st) == [0, 0, 0, 2, 0]
+    dx, dy, infos, sst, code = s.solve_batch(cu(np.stack([x.r_x for x in systems])),
+                                             cu(np.stack([x.r_y for x in systems])))
+    assert code == 2 and list(sst) == [0, 0, 0, 2, 0]
+    for b, x in enumerate(systems):
+        if b == bad:
+            continue
+        _, _, odx, ody, oinfo = O.solve_system(x)
+        assert infos[b].rr <= 1e-8
+        assert rel(np.concatenate([dx[b].cpu().numpy(), dy[b].cpu().numpy()]), np.concatenate([odx, ody])) <= 1e-6
