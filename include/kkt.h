@@ -173,6 +173,20 @@ kkt_status kkt_analyse_host(int64_t n, int64_t m, const int64_t* H_colptr, const
 kkt_status kkt_factor(kkt_handle h, const double* H_vals, const double* J_vals, double delta,
                       double gamma, void* stream);
 
+/* Algorithm 1's delta_1 loop around kkt_factor: delta_1 = 0 first; while
+ * the Cholesky fails (a pivot <= 0, Thm 1: H~ not positive definite on
+ * null(J)) and delta_1 <= delta_max / 2, delta_1 becomes delta_min on the
+ * first retry and doubles on each later one (delta_min itself unchanged).
+ *   H_vals, J_vals  device, as kkt_factor
+ *   gamma           as kkt_factor
+ *   delta_min, delta_max  <= 0 selects Algorithm 1's typical 1e-9, 1e-6
+ *   delta_used      host double* (may be NULL): the delta_1 of the last trial
+ * Returns KKT_OK with the handle factored at delta_used, or KKT_ERR_NOT_SPD
+ * when even the largest shift failed (Algorithm 1 then hands the system to
+ * an LDL^T solver or back to the optimizer; that is the caller's). */
+kkt_status kkt_factor_regularized(kkt_handle h, const double* H_vals, const double* J_vals, double gamma,
+                                  double delta_min, double delta_max, double* delta_used, void* stream);
+
 /* Solve with the last successful factor (Algorithm 1 solve steps; eqs.
  * Schur1/Schur2), then FP64 refinement on K_delta while RR > ir_rtol.
  *   r_x, r_y  device double[n], double[m] (may alias nothing written here)

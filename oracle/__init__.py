@@ -230,6 +230,20 @@ class FactorSample(Factor):
         self.fail_col = -1
 
 
+def factor_regularized(sym: Symbolic, H_vals, J_vals, gamma, delta_min=1e-9, delta_max=1e-6):
+    """Algorithm 1's delta_1 loop (its lines from "delta_1 <- 0" to the end of
+    the while loop): try the Cholesky with delta_1 = 0; while it fails and
+    delta_1 <= delta_max / 2, set delta_1 to delta_min on the first retry and
+    double it afterwards (the garbled update is read as "double delta_1").
+    Returns (Factor of the last trial, delta_1)."""
+    d1 = 0.0
+    fac = Factor(sym, H_vals, J_vals, d1, gamma)
+    while not fac.ok and d1 <= delta_max / 2:
+        d1 = delta_min if d1 == 0.0 else 2.0 * d1
+        fac = Factor(sym, H_vals, J_vals, d1, gamma)
+    return fac, d1
+
+
 def residual(sym: Symbolic, H_vals, J_vals, delta, r_x, r_y, dx, dy):
     """RR, BE, ||res||_2, ||K_delta||_inf of [dx;dy] for K_delta = [H~+delta I, J^T; J, 0]
     (BE and RR as defined in Sec. 5.1, ||K||_2 estimated by ||K||_inf)."""

@@ -65,6 +65,7 @@ def _load():
     L.kkt_factor.argtypes = [P, P, P, D, D, P]
     L.kkt_solve.argtypes = [P, P, P, P, P, P]
     L.kkt_solve_multi.argtypes = [P, I32, P, P, P, P, P, P]
+    L.kkt_factor_regularized.argtypes = [P, P, P, D, D, D, P, P]
     L.kkt_factor_batch.argtypes = [P, I32, P, P, D, D, P, P]
     L.kkt_solve_batch.argtypes = [P, I32, P, P, P, P, P, P, P]
     L.kkt_factor_solve_host.argtypes = [P, P, P, D, D, P, P, P, P, P]
@@ -88,7 +89,7 @@ def _load():
     L.kkt_destroy_4x4.argtypes = [P]
     L.kkt_status_string.argtypes = [I32]
     L.kkt_status_string.restype = C.c_char_p
-    for nm in ("kkt_analyse", "kkt_analyse_host", "kkt_factor", "kkt_solve", "kkt_solve_multi", "kkt_factor_batch", "kkt_solve_batch", "kkt_factor_solve_host", "kkt_hsolve", "kkt_get_info",
+    for nm in ("kkt_analyse", "kkt_analyse_host", "kkt_factor", "kkt_solve", "kkt_solve_multi", "kkt_factor_batch", "kkt_solve_batch", "kkt_factor_regularized", "kkt_factor_solve_host", "kkt_hsolve", "kkt_get_info",
                "kkt_inertia", "kkt_symbolic_info_get", "kkt_get_symbolic", "kkt_get_factor_panels", "kkt_get_profile", "kkt_get_solve_counters", "kkt_residual_noalloc",
                "kkt_destroy", "kkt_analyse_4x4", "kkt_analyse_4x4_host", "kkt_get_4x4_pattern", "kkt_factor_4x4",
                "kkt_solve_4x4", "kkt_destroy_4x4"):
@@ -97,7 +98,7 @@ def _load():
 
 
 _lib = _load()
-EXPORTED = ("kkt_default_options", "kkt_analyse", "kkt_analyse_host", "kkt_factor", "kkt_solve", "kkt_solve_multi", "kkt_factor_batch", "kkt_solve_batch", "kkt_factor_solve_host",
+EXPORTED = ("kkt_default_options", "kkt_analyse", "kkt_analyse_host", "kkt_factor", "kkt_solve", "kkt_solve_multi", "kkt_factor_batch", "kkt_solve_batch", "kkt_factor_regularized", "kkt_factor_solve_host",
             "kkt_hsolve", "kkt_get_info", "kkt_inertia", "kkt_symbolic_info_get", "kkt_get_symbolic",
             "kkt_get_factor_panels", "kkt_get_profile", "kkt_get_solve_counters", "kkt_residual_noalloc",
             "kkt_destroy", "kkt_status_string", "kkt_analyse_4x4", "kkt_analyse_4x4_host", "kkt_4x4_inner",
@@ -365,6 +366,16 @@ class KKTSolver:
         if check:
             _check("kkt_solve_multi", code)
         return dx, dy, infos
+
+    def factor_regularized(self, H_vals, J_vals, gamma=-1.0, delta_min=1e-9, delta_max=1e-6, stream=None,
+                           check=True):
+        """Algorithm 1's delta_1 loop; returns (status code, delta_1 used)."""
+        d = C.c_double(0.0)
+        code = _lib.kkt_factor_regularized(self.h, _dev(H_vals, self.nnz_h), _dev(J_vals, self.nnz_j), float(gamma),
+                                           float(delta_min), float(delta_max), C.byref(d), _stream(stream))
+        if check and code not in (0, 2):
+            _check("kkt_factor_regularized", code)
+        return code, d.value
 
     def factor_batch(self, H_vals, J_vals, delta, gamma=-1.0, stream=None):
         """H_vals: CUDA float64 (nsys, nnz(H~)), J_vals: (nsys, nnz(J)). Returns

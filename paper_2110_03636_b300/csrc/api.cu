@@ -807,6 +807,31 @@ kkt_status kkt_factor(kkt_handle h, const double* H_vals, const double* J_vals, 
   return factor_common(h, delta, gamma, st);
 }
 
+// Algorithm 1's regularization loop: delta_1 = 0; while the Cholesky fails
+// and delta_1 <= delta_max / 2, delta_1 becomes delta_min, then doubles.
+// Each trial replays the factorization with the new shift (the assembly
+// reads delta from device memory).
+kkt_status kkt_factor_regularized(kkt_handle h, const double* H_vals, const double* J_vals, double gamma,
+                                  double delta_min, double delta_max, double* delta_used, void* stream) {
+  if (!h || !H_vals || (h->nnzJ > 0 && !J_vals)) return KKT_ERR_INVALID;
+  if (!h->on_device) return KKT_ERR_STATE;
+  if (!(delta_min > 0)) delta_min = 1e-9;
+  if (!(delta_max > 0)) delta_max = 1e-6;
+  if (!std::isfinite(delta_min) || !std::isfinite(delta_max) || delta_max < delta_min) return KKT_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaSetDevice(h->device));
+  CK(cudaMemcpyAsync(h->Hv, H_vals, sizeof(double) * h->nnzH, cudaMemcpyDeviceToDevice, st));
+  if (h->nnzJ) CK(cudaMemcpyAsync(h->Jv, J_vals, sizeof(double) * h->nnzJ, cudaMemcpyDeviceToDevice, st));
+  double d1 = 0.0;
+  kkt_status s = factor_common(h, d1, gamma, st);
+  while (s == KKT_ERR_NOT_SPD && d1 <= delta_max / 2) {
+    d1 = d1 == 0.0 ? delta_min : 2.0 * d1;
+    s = factor_common(h, d1, gamma, st);
+  }
+  if (delta_used) *delta_used = d1;
+  return s;
+}
+
 kkt_status kkt_solve(kkt_handle h, const double* r_x, const double* r_y, double* dx, double* dy, void* stream) {
   if (!h || !r_x || !dx || (h->P.m > 0 && (!r_y || !dy))) return KKT_ERR_INVALID;
   if (!h->on_device) return KKT_ERR_STATE;

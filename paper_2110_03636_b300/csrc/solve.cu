@@ -107,6 +107,53 @@ __device__ void rows_matvec(const T* tile, int cs, int d0, int nr, int pw, const
   }
 }
 
+// rows_matvec for R right-hand sides at once: out_ij = sum_k tile[k*cs + d0 + i]
+// * X[j*pw + k], handed to emit(i, j, out_ij); each tile entry is read once
+// for all of them (part: R * blockDim entries)
+template <typename T, typename F>
+__device__ void rows_matvec_multi(const T* tile, int cs, int d0, int nr, int pw, const T* X, int R, T* part, F emit) {
+  const int tid = threadIdx.x;
+  T acc[kMaxRhs];
+#pragma unroll
+  for (int j = 0; j < kMaxRhs; j++) acc[j] = T(0);
+  if (nr <= (int)blockDim.x) {
+    const int rr = (nr + 31) & ~31;
+    const int G = max(1, (int)blockDim.x / rr);
+    const int i = tid % rr, g = tid / rr;
+    if (g < G && i < nr)
+      for (int k = g; k < pw; k += G) {
+        const T tv = tile[k * cs + d0 + i];
+#pragma unroll
+        for (int j = 0; j < kMaxRhs; j++)
+          if (j < R) acc[j] += tv * X[j * pw + k];
+      }
+#pragma unroll
+    for (int j = 0; j < kMaxRhs; j++)
+      if (j < R) part[j * blockDim.x + tid] = acc[j];
+    __syncthreads();
+    if (tid < nr)
+      for (int j = 0; j < R; j++) {
+        T o = T(0);
+        for (int gg = 0; gg < G; gg++) o += part[j * blockDim.x + gg * rr + tid];
+        emit(tid, j, o);
+      }
+  } else {
+    for (int i = tid; i < nr; i += blockDim.x) {
+#pragma unroll
+      for (int j = 0; j < kMaxRhs; j++) acc[j] = T(0);
+      for (int k = 0; k < pw; k++) {
+        const T tv = tile[k * cs + d0 + i];
+#pragma unroll
+        for (int j = 0; j < kMaxRhs; j++)
+          if (j < R) acc[j] += tv * X[j * pw + k];
+      }
+#pragma unroll
+      for (int j = 0; j < kMaxRhs; j++)
+        if (j < R) emit(i, j, acc[j]);
+    }
+  }
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -322,6 +369,26 @@ __device__ bool fwd_chunk(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>
   }
   __syncthreads();
   const bool dep = h.flag != 0;
+  const int R = a.nrhs;
+  if (R > 1 && R * pw <= a.max_rows + kSolveThreads && (size_t)R * blockDim.x <= packed_inv((size_t)a.sw)) {
+    // all right-hand sides' piece vectors at once (into the gathered-vector
+    // region; chunks leave the inverse region free for the partial sums)
+    T* X = t.aux;
+    if (dep)
+      for (int idx = tid; idx < R * pw; idx += blockDim.x)
+        X[idx] = ldcg(&a.v[(int64_t)(idx / pw) * a.n + f + idx % pw]);
+    if (!mbar_wait(a, h) || !dep) return false;
+    const int d0 = (d.c + d.r0) & 3;
+    rows_matvec_multi(t.B, d.cs, d0, nr, pw, X, R, t.A, [&](int i, int j, T o) {
+      atomicAdd(&a.v[(int64_t)j * a.n + (nr <= (int)blockDim.x ? myrow : rows[i])], -o);
+    });
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      for (int64_t q = d.tp0; q < d.tp1; q++) atomicAdd(&a.fwd_arrive[a.ch_tgt[q]], 1);
+    }
+    return true;
+  }
   if (dep)
     for (int k = tid; k < pw; k += blockDim.x) t.vec[k] = ldcg(&a.v[f + k]);
   if (!mbar_wait(a, h) || !dep) return false;
@@ -379,11 +446,45 @@ __device__ bool bwd_chunk(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>
       for (int i = tid; i < nr; i += blockDim.x) t.aux[i] = ldcg(&vj[rows[i]]);
     }
   };
-  if (dep) gather(a.v);
-  if (!mbar_wait(a, h) || !dep) return false;
+  const int R = a.nrhs;
   const int d0 = (d.c + d.r0) & 3;
   const int cs = d.cs;
   const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  if (R > 1 && (size_t)R * nr <= packed_inv((size_t)a.sw)) {
+    // every right-hand side's values at the chunk rows at once (inverse region)
+    T* Gx = t.A;
+    if (dep)
+      for (int idx = tid; idx < R * nr; idx += blockDim.x) {
+        const int j = idx / nr, i = idx % nr;
+        Gx[idx] = ldcg(&a.v[(int64_t)j * a.n + (i == tid && nr <= (int)blockDim.x ? myrow : rows[i])]);
+      }
+    if (!mbar_wait(a, h) || !dep) return false;
+    for (int k = warp; k < pw; k += nw) {
+      T acc[kMaxRhs];
+#pragma unroll
+      for (int j = 0; j < kMaxRhs; j++) acc[j] = T(0);
+      for (int i = lane; i < nr; i += 32) {
+        const T tv = t.B[k * cs + d0 + i];
+#pragma unroll
+        for (int j = 0; j < kMaxRhs; j++)
+          if (j < R) acc[j] += tv * Gx[j * nr + i];
+      }
+#pragma unroll
+      for (int j = 0; j < kMaxRhs; j++)
+        if (j < R) {
+          const T sj = warp_sum(acc[j]);
+          if (lane == 0) a.zpart[(int64_t)j * a.z_total + d.zoff + k] = sj;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      atomicAdd(&a.bwd_arrive[p], 1);
+    }
+    return true;
+  }
+  if (dep) gather(a.v);
+  if (!mbar_wait(a, h) || !dep) return false;
   for (int j = 0; j < a.nrhs; j++) {
     if (j > 0) {
       gather(a.v + (int64_t)j * a.n);

@@ -460,3 +460,21 @@ def test_batched_systems_match_oracle(precision):
         _, _, odx, ody, oinfo = O.solve_system(x)
         assert infos[b].rr <= 1e-8
         assert rel(np.concatenate([dx[b].cpu().numpy(), dy[b].cpu().numpy()]), np.concatenate([odx, ody])) <= 1e-6
+
+
+@pytest.mark.parametrize("lam", [0.5, -2.5e-8, -1e-5])
+def test_factor_regularized_matches_oracle(lam):
+    """Algorithm 1's delta_1 loop on the device takes the same delta_1 as the
+    oracle's (FP64), and the solve at that shift matches."""
+    from test_oracle import nullspace_indefinite_system
+    sys, _, _ = nullspace_indefinite_system(lam)
+    sym = O.Symbolic(sys.n, sys.m, sys.H_colptr, sys.H_rowidx, sys.J_rowptr, sys.J_colidx)
+    fac, d_ref = O.factor_regularized(sym, sys.H_vals, sys.J_vals, sys.gamma)
+    s = K.KKTSolver(sys.n, sys.m, sys.H_colptr, sys.H_rowidx, sys.J_rowptr, sys.J_colidx)
+    code, d = s.factor_regularized(cu(sys.H_vals), cu(sys.J_vals), sys.gamma)
+    assert d == d_ref
+    assert (code == 0) == fac.ok
+    if fac.ok:
+        dx, dy = s.solve(cu(sys.r_x), cu(sys.r_y))
+        odx, ody, _ = fac.solve(sys.r_x, sys.r_y)
+        assert rel(np.concatenate([dx.cpu().numpy(), dy.cpu().numpy()]), np.concatenate([odx, ody])) <= 1e-6

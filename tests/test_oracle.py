@@ -560,3 +560,34 @@ def test_grid_4x4_reduction_matches_sparse_lu():
     got = np.concatenate([dx, ds, dy, dyd])
     assert np.linalg.norm(got - ref) <= 1e-9 * np.linalg.norm(ref)
     assert np.linalg.norm(b - K4 @ got) <= 1e-10 * np.linalg.norm(b)
+
+
+# ----------------------------------------------------------------- Algorithm 1's delta_1 loop
+def nullspace_indefinite_system(lam, n=30, m=10, seed=3):
+    """H~ with eigenvalue lam along a unit v in null(J) (all other eigenvalues
+    >= 1), so H_gamma has lam as its smallest eigenvalue for every gamma."""
+    rng = np.random.default_rng(seed)
+    J = rng.standard_normal((m, n))
+    _, _, Vt = np.linalg.svd(J)
+    v = Vt[m]                                   # in null(J)
+    P = np.eye(n) - np.outer(v, v)
+    A = rng.standard_normal((n, n))
+    A = A @ A.T + n * np.eye(n)
+    H = P @ A @ P + lam * np.outer(v, v)
+    H = (H + H.T) / 2
+    return make_sys(H, J, rng.standard_normal(n), rng.standard_normal(m), gamma=1e2), H, J
+
+
+@pytest.mark.parametrize("lam,expect_delta,expect_ok", [(0.5, 0.0, True), (-2.5e-8, 3.2e-8, True),
+                                                        (-1e-5, 5.12e-7, False)])
+def test_factor_regularized_loop(lam, expect_delta, expect_ok):
+    """delta_1 = 0, then delta_min = 1e-9 doubling while the Cholesky fails and
+    delta_1 <= delta_max / 2 = 5e-7: the first trial value above -lam."""
+    sys, H, J = nullspace_indefinite_system(lam)
+    sym = O.Symbolic(sys.n, sys.m, sys.H_colptr, sys.H_rowidx, sys.J_rowptr, sys.J_colidx)
+    fac, d1 = O.factor_regularized(sym, sys.H_vals, sys.J_vals, sys.gamma)
+    assert fac.ok == expect_ok
+    assert d1 == pytest.approx(expect_delta, rel=1e-12, abs=0)
+    # Thm 1: the smallest eigenvalue of H_gamma + delta_1 I decides
+    lmin = np.linalg.eigvalsh(H + sys.gamma * J.T @ J + d1 * np.eye(sys.n)).min()
+    assert (lmin > 0) == expect_ok
