@@ -29,6 +29,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "grid2d_n250k"
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum under ncu) of one
+# H^-1 application of the solve kernel on the 500x500 workload: kkt_hsolve
+# launches the kernel for exactly one application (profiles/
+# k_cg_grid2d_n250k_mixed_nd.md); a CG launch does (iterations + 2) of them.
+# Valid only for the kernel source it was measured on.
+NCU_BYTES_PER_H_APPLICATION = {("grid2d_n250k", "mixed", "nd"): 2.4835e9 + 0.0146e9}
 N_VALUE_SETS = 10
 RR_TARGET = 1e-8
 
@@ -258,8 +264,13 @@ def run_ours(args, rank, world):
             per_ms = ms_dom / max(n_dom, 1)
         achieved = amount / (per_ms / 1e3) / 1e9
         peak, peak_unit, peak_note = peak_for(bound, head, peaks, unit)
+        traffic = None
+        key = (args.workload, head, args.ordering)
+        if dom == "cg_persistent" and key in NCU_BYTES_PER_H_APPLICATION:
+            traffic = round(NCU_BYTES_PER_H_APPLICATION[key] * (iters_pass + 2))
         roof = {"kernel": dom, "bound": bound, "achieved": round(achieved, 2), "peak": round(peak, 1),
-                "unit": peak_unit, "frac": round(achieved / peak, 4), "traffic": None,
+                "unit": peak_unit, "frac": round(achieved / peak, 4), "traffic": traffic,
+                "traffic_note": "ncu DRAM bytes of one H^-1 application x (iterations per launch + 2)",
                 "peak_source": f"{peak_src if bound == 'hbm' else 'derived'}: {peak_note}",
                 "share_of_step": round(ms_dom / total_prof, 3), "timing": timing,
                 "ms_per_launch": round(per_ms, 3),
