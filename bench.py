@@ -32,7 +32,8 @@ WORKLOAD = "grid2d_n250k"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum under ncu) of one
 # H^-1 application of the solve kernel on the 500x500 workload: kkt_hsolve
 # launches the kernel for exactly one application (profiles/
-# k_cg_grid2d_n250k_mixed_nd.md); a CG launch does (iterations + 2) of them.
+# k_cg_grid2d_n250k_mixed_nd.md); a mixed-precision CG launch does
+# (iterations + 1) of them.
 # Valid only for the kernel source it was measured on.
 NCU_BYTES_PER_H_APPLICATION = {("grid2d_n250k", "mixed", "nd"): 2.4835e9 + 0.0146e9}
 N_VALUE_SETS = 10
@@ -133,11 +134,13 @@ def kernel_work(kind, prec, sym_arrays, nnz_l, iters_per_pass, nnz_j, n, m):
     if kind == "syrk":
         return "alu", float((w * rb * (rb + 1)).sum()), "flop"         # per factorization (all launches)
     if kind == "cg_persistent":
-        # one pass: (iters + 2) H^-1 applications, each reads L twice (nnz(L)
+        # one pass: w = H^-1 r^_x, one H^-1 application per CG product, and
+        # (FP64 only) the back-substitution; the mixed form accumulates dx
+        # along the recurrence instead. Each application reads L twice (nnz(L)
         # entries of s bytes, the algorithmic minimum; the panels also hold
         # relaxation zeros and the unused upper part of diagonal blocks) and
         # does 2 x nnz(L) FMAs; plus J and J^T products per iteration
-        hs = iters_per_pass + 2
+        hs = iters_per_pass + (1 if prec == "mixed" else 2)
         byts = hs * 2 * s * nnz_l + iters_per_pass * 2 * (12 * nnz_j + 8 * (n + m))
         flops = hs * 4 * nnz_l
         # FP64 on B300: 2 x nnz(L) DFMA per sweep at ~1/64 of the FP32 rate
@@ -267,10 +270,10 @@ def run_ours(args, rank, world):
         traffic = None
         key = (args.workload, head, args.ordering)
         if dom == "cg_persistent" and key in NCU_BYTES_PER_H_APPLICATION:
-            traffic = round(NCU_BYTES_PER_H_APPLICATION[key] * (iters_pass + 2))
+            traffic = round(NCU_BYTES_PER_H_APPLICATION[key] * (iters_pass + 1))
         roof = {"kernel": dom, "bound": bound, "achieved": round(achieved, 2), "peak": round(peak, 1),
                 "unit": peak_unit, "frac": round(achieved / peak, 4), "traffic": traffic,
-                "traffic_note": "ncu DRAM bytes of one H^-1 application x (iterations per launch + 2)",
+                "traffic_note": "ncu DRAM bytes of one H^-1 application x (iterations per launch + 1)",
                 "peak_source": f"{peak_src if bound == 'hbm' else 'derived'}: {peak_note}",
                 "share_of_step": round(ms_dom / total_prof, 3), "timing": timing,
                 "ms_per_launch": round(per_ms, 3),

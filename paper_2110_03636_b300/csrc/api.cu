@@ -82,7 +82,7 @@ struct kkt_handle_s {
   // values and workspace
   double *Hv, *Jv;
   void *L, *U, *v, *zpart, *Linv;
-  double *rhx, *p, *r, *y, *q, *bS, *red, *res_x, *res_y;
+  double *rhx, *p, *r, *y, *q, *bS, *red, *res_x, *res_y, *wv, *xa;
   double *stage_rx, *stage_ry, *stage_dx, *stage_dy;
   int* counters;   // fwd_arrive, fwd_done, bwd_arrive, bwd_done (npieces each), disp[3], bar[2]
   DevStatus* dst;
@@ -98,7 +98,7 @@ struct kkt_handle_s {
   std::vector<int32_t> bstatus;
   bool multi = false;
   void *mv, *mzpart;
-  double *mrhx, *mp, *mr, *my, *mq, *mbS, *mres_x, *mres_y;
+  double *mrhx, *mp, *mr, *my, *mq, *mbS, *mres_x, *mres_y, *mwv, *mxa;
   double* d_dg = nullptr;    // device [delta, gamma] read by the assembly kernel
   unsigned long long* d_instr = nullptr;   // solve-kernel cycle counters (profile mode)
   double* h_dg = nullptr;    // pinned staging for it
@@ -354,6 +354,7 @@ kkt_status kkt_analyse(int64_t n, int64_t m, const int64_t* Hp, const int32_t* H
     }
   }
   h->rhx = A.alloc<double>(n);
+  h->wv = A.alloc<double>(n); h->xa = A.alloc<double>(n);
   h->p = A.alloc<double>(m); h->r = A.alloc<double>(m); h->y = A.alloc<double>(m);
   h->q = A.alloc<double>(m); h->bS = A.alloc<double>(m);
   h->red = A.alloc<double>((size_t)std::max(h->grid, 296) * kRedStride);
@@ -508,6 +509,8 @@ static SolveArgs<T> solve_args(kkt_handle h) {
   a.perm = h->perm;
   a.gamma = h->gamma; a.delta2 = h->opt.delta2; a.rtol = h->opt.cg_rtol; a.maxit = h->opt.cg_maxit;
   a.v = (T*)h->v; a.rhx = h->rhx; a.p = h->p; a.r = h->r; a.y = h->y; a.q = h->q; a.bS = h->bS;
+  a.wv = h->wv; a.xa = h->xa;
+  a.xacc = h->opt.precision == KKT_MIXED ? 1 : 0;
   a.zpart = (T*)h->zpart;
   const int64_t np = P.npieces;
   a.fwd_arrive = h->counters; a.fwd_done = h->counters + np;
@@ -530,6 +533,7 @@ static kkt_status solve_pass(kkt_handle h, const double* bx, const double* by, d
     a.nrhs = nrhs;
     a.v = (T*)h->mv; a.zpart = (T*)h->mzpart; a.rhx = h->mrhx;
     a.p = h->mp; a.r = h->mr; a.y = h->my; a.q = h->mq; a.bS = h->mbS;
+    a.wv = h->mwv; a.xa = h->mxa;
   }
   if (h->profp) {
     CK(prof_begin(h->profp, st));
@@ -766,6 +770,7 @@ kkt_status kkt_solve_multi(kkt_handle h, int32_t nrhs, const double* r_x, const 
     h->mv = A.alloc<char>(es * (size_t)n * kMaxRhs);
     h->mzpart = A.alloc<char>(es * (size_t)std::max<int64_t>(h->P.z_total, 1) * kMaxRhs);
     h->mrhx = A.alloc<double>((size_t)n * kMaxRhs);
+    h->mwv = A.alloc<double>((size_t)n * kMaxRhs); h->mxa = A.alloc<double>((size_t)n * kMaxRhs);
     h->mp = A.alloc<double>((size_t)m * kMaxRhs); h->mr = A.alloc<double>((size_t)m * kMaxRhs);
     h->my = A.alloc<double>((size_t)m * kMaxRhs); h->mq = A.alloc<double>((size_t)m * kMaxRhs);
     h->mbS = A.alloc<double>((size_t)m * kMaxRhs);

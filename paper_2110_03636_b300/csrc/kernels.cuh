@@ -106,6 +106,8 @@ struct SolveArgs {
   int32_t* rhs_stat;   // [kMaxRhs * 3]: CG products, status, delta_2 restart per right-hand side
   T* v;
   double *rhx, *p, *r, *y, *q, *bS;
+  double *wv, *xa;     // w = H^-1 r^_x and the accumulated dx (n each)
+  int32_t xacc;        // 1: accumulate dx along CG (mixed form); 0: direct solve for dx
   T* zpart;
   int *fwd_arrive, *fwd_done, *bwd_arrive, *bwd_done;
   int* disp;   // [3]

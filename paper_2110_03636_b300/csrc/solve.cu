@@ -1,6 +1,12 @@
 // Persistent, cooperative CG on the Schur complement (eqs. Schur1/Schur2 and
 // Algorithm 1's solve steps):
 //   r^_x = r_x + gamma J^T r_y;  w = H^-1 r^_x;  b_S = J w - r_y;
+// With a.xacc set (the mixed-precision form), eq. Schur2's back-substitution
+// dx = H^-1 (r^_x - J^T dy) is not a third solve: every CG product already
+// forms t_i = H^-1 J^T p_i, and with dy = sum alpha_i p_i, dx = w - sum
+// alpha_i t_i is accumulated (FP64) along the CG recurrence, saving one H^-1
+// application per refinement pass. The sum cancels when H_delta is nearly
+// singular along null(J), so the FP64 form keeps Algorithm 1's direct solve.
 //   CG on (S + d2 I) dy = b_S with S = J H^-1 J^T, one product per iteration
 //   = J^T p, forward and backward triangular solves with L, J (Sec. 4.1);
 //   dx = H^-1 (r^_x - J^T dy).
@@ -989,6 +995,17 @@ __global__ void __launch_bounds__(kSolveThreads, MB) k_cg(SolveArgs<T> a) {
   // summed in a fixed order), kept in shared memory
   __shared__ double s_rho[kMaxRhs], s_rqmax[kMaxRhs], s_d2[kMaxRhs], s_bn2[kMaxRhs], s_alpha[kMaxRhs];
   __shared__ int s_it[kMaxRhs], s_status[kMaxRhs], s_brk[kMaxRhs], s_step[kMaxRhs];
+  // keep w = H^-1 r^_x (FP64) and start dx = w
+  for (int j = 0; j < R && a.xacc; j++) {
+    const T* v = a.v + (int64_t)j * n;
+    double* wv = a.wv + (int64_t)j * n;
+    double* xa = a.xa + (int64_t)j * n;
+    for (int64_t k = gt; k < n; k += gs) {
+      const double wk = (double)ldcg(&v[k]);
+      wv[k] = wk;
+      xa[k] = wk;
+    }
+  }
   // b_S = J w - r_y
   for (int j = 0; j < R; j++) {
     const T* v = a.v + (int64_t)j * n;
@@ -1091,9 +1108,20 @@ __global__ void __launch_bounds__(kSolveThreads, MB) k_cg(SolveArgs<T> a) {
           const double b = __ldcg(&bS[i]);
           y[i] = 0.0; r[i] = b; p[i] = b;
         }
+        if (a.xacc) {
+          const double* wv = a.wv + (int64_t)j * n;
+          double* xa = a.xa + (int64_t)j * n;
+          for (int64_t k = gt; k < n; k += gs) xa[k] = __ldcg(&wv[k]);
+        }
         continue;
       }
       const double alpha = s_alpha[j];
+      if (a.xacc) {
+        // dx -= alpha t, t = H^-1 J^T p of this product (still in v)
+        const T* v = a.v + (int64_t)j * n;
+        double* xa = a.xa + (int64_t)j * n;
+        for (int64_t k = gt; k < n; k += gs) xa[k] -= alpha * (double)ldcg(&v[k]);
+      }
       double rr = 0.0;
       for (int64_t i = gt; i < m; i += gs) {
         const double pi = __ldcg(&p[i]), qi = __ldcg(&q_[i]);
@@ -1118,26 +1146,29 @@ __global__ void __launch_bounds__(kSolveThreads, MB) k_cg(SolveArgs<T> a) {
     }
     if (!grid_barrier(a, sm)) return;
   }
-  // dx = H^-1 (r^_x - J^T dy)
-  for (int j = 0; j < R; j++) {
-    const double* y = a.y + j * m;
-    const double* rhx = a.rhx + (int64_t)j * n;
-    T* v = a.v + (int64_t)j * n;
-    for (int64_t k = gt; k < n; k += gs) {
-      double s = 0.0;
-      for (int64_t q = a.JT_ptr[k]; q < a.JT_ptr[k + 1]; q++) s += a.Jv[a.JT_vidx[q]] * __ldcg(&y[a.JT_row[q]]);
-      v[k] = (T)(__ldcg(&rhx[k]) - s);
+  // dx = H^-1 (r^_x - J^T dy) (eq. Schur2): accumulated, or a direct solve
+  if (!a.xacc) {
+    for (int j = 0; j < R; j++) {
+      const double* y = a.y + j * m;
+      const double* rhx = a.rhx + (int64_t)j * n;
+      T* v = a.v + (int64_t)j * n;
+      for (int64_t k = gt; k < n; k += gs) {
+        double s = 0.0;
+        for (int64_t q = a.JT_ptr[k]; q < a.JT_ptr[k + 1]; q++) s += a.Jv[a.JT_vidx[q]] * __ldcg(&y[a.JT_row[q]]);
+        v[k] = (T)(__ldcg(&rhx[k]) - s);
+      }
     }
+    if (!grid_barrier(a, sm)) return;
+    if (!hsolve(a, sm, tl, seq, e)) return;
   }
-  if (!grid_barrier(a, sm)) return;
-  if (!hsolve(a, sm, tl, seq, e)) return;
   for (int j = 0; j < R; j++) {
+    const double* xa = a.xa + (int64_t)j * n;
     const T* v = a.v + (int64_t)j * n;
     const double* y = a.y + j * m;
     double* ox = a.ox + (int64_t)j * n;
     double* oy = a.oy + j * m;
     for (int64_t k = gt; k < n; k += gs) {
-      const double val = (double)ldcg(&v[k]);
+      const double val = a.xacc ? __ldcg(&xa[k]) : (double)ldcg(&v[k]);
       const int32_t o = a.perm[k];
       ox[o] = a.accumulate ? ox[o] + val : val;
     }

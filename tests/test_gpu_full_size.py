@@ -1,0 +1,75 @@
+"""Full-size workloads on the GPU, checked through properties that hold at
+any size: the relative residual of the returned solution on K_delta (Sec. 5.1,
+RR), computed here on the host in FP64 from its definition with scipy, the
+inertia flag, and agreement between the two precisions. The 100^3 workload
+(about 100 GB of device memory and minutes of host analysis) runs only with
+KKT_BIG=1."""
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+import paper_2110_03636_b300 as K
+
+pytestmark = pytest.mark.gpu
+
+
+def cu(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def host_rr(x, dx, dy):
+    """||b - K_delta [dx; dy]|| / ||b|| with K_delta = [H~ + delta I, J^T; J, 0]."""
+    import scipy.sparse as sp
+    H = sp.csc_matrix((x.H_vals, x.H_rowidx, x.H_colptr), shape=(x.n, x.n))
+    J = sp.csr_matrix((x.J_vals, x.J_colidx, x.J_rowptr), shape=(x.m, x.n))
+    Hx = H @ dx + H.T @ dx - H.diagonal() * dx + x.delta * dx
+    rx = x.r_x - Hx - J.T @ dy
+    ry = x.r_y - J @ dx
+    return np.sqrt(np.dot(rx, rx) + np.dot(ry, ry)) / np.sqrt(np.dot(x.r_x, x.r_x) + np.dot(x.r_y, x.r_y))
+
+
+@pytest.mark.slow
+def test_grid2d_n250k_both_precisions():
+    """500x500 grid, ND ordering, two value sets of the interior sequence:
+    both precisions reach RR <= 1e-8 by the oracle's residual and agree with
+    each other to 1e-6."""
+    base = W.make_config("grid2d_n250k")
+    sets = [base, W.rescale_barrier(base, seed=(0, 1))]
+    sols = {}
+    for prec in ("mixed", "fp64"):
+        s = K.KKTSolver(base.n, base.m, base.H_colptr, base.H_rowidx, base.J_rowptr, base.J_colidx,
+                        precision=prec, ordering="nd")
+        for t, x in enumerate(sets):
+            s.factor(cu(x.H_vals), cu(x.J_vals), x.delta, x.gamma)
+            dx, dy = s.solve(cu(x.r_x), cu(x.r_y))
+            dx, dy = dx.cpu().numpy(), dy.cpu().numpy()
+            rr = host_rr(x, dx, dy)
+            assert rr <= 1e-8, (prec, t, rr)
+            assert abs(rr - s.info.rr) <= 0.1 * rr + 1e-15
+            assert s.inertia_ok
+            sols[(prec, t)] = np.concatenate([dx, dy])
+        s.close()
+    for t in range(2):
+        a, b = sols[("mixed", t)], sols[("fp64", t)]
+        assert np.linalg.norm(a - b) <= 1e-6 * np.linalg.norm(b)
+
+
+@pytest.mark.slow
+@pytest.mark.skipif(os.environ.get("KKT_BIG") != "1", reason="100^3 workload: set KKT_BIG=1")
+def test_grid3d_n1m_mixed():
+    """The 100^3 precision-form workload (n = 1e6, m = 5e5, gamma = 1e6):
+    FP32 factor, FP64 CG and refinement; RR <= 1e-8 by the oracle's residual."""
+    x = W.make_config("grid3d_n1m")
+    s = K.KKTSolver(x.n, x.m, x.H_colptr, x.H_rowidx, x.J_rowptr, x.J_colidx, precision="mixed", ordering="nd")
+    info = s.symbolic_info
+    print("nnzL", info.nnz_l, "flops", info.flops, "device GB", info.device_bytes / 1e9)
+    s.factor(cu(x.H_vals), cu(x.J_vals), x.delta, x.gamma)
+    dx, dy = s.solve(cu(x.r_x), cu(x.r_y))
+    print("cg", s.info.cg_iters, "ir", s.info.ir_steps, "rr", s.info.rr)
+    assert host_rr(x, dx.cpu().numpy(), dy.cpu().numpy()) <= 1e-8
