@@ -101,7 +101,10 @@ typedef struct kkt_options {
   int32_t pad3_;
 } kkt_options;
 
-/* Kernel kinds reported by kkt_get_profile. */
+/* Kernel kinds reported by kkt_get_profile. Kinds a plan does not launch
+ * stay zero: KKT_MIXED factors with KKT_K_BLOCK (fused POTRF + TRSM) instead
+ * of KKT_K_POTRF and KKT_K_TRSM; no plan clears update matrices any more
+ * (KKT_K_ZERO_U): the SYRK stores them. */
 enum {
   KKT_K_ASSEMBLE = 0, KKT_K_POTRF = 1, KKT_K_TRSM = 2, KKT_K_PANEL_UPDATE = 3, KKT_K_SYRK = 4,
   KKT_K_EXTEND_ADD = 5, KKT_K_ZERO_U = 6, KKT_K_CG = 7, KKT_K_RESIDUAL = 8, KKT_K_TRI_INV = 9,

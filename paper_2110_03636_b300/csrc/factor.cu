@@ -4,9 +4,9 @@
 //
 // Layout: supernode s owns a column-major panel of snr[s] x sw[s] entries
 // (its rows = its columns followed by the rows below, ld = snr[s]) and an
-// update matrix U_s of rb x rb (rb = snr[s] - sw[s], ld = rb) that first
-// collects the children's contributions and then holds
-//   U_s = (children's updates) - L21 L21^T,
+// update matrix U_s of rb x rb (rb = snr[s] - sw[s], ld = rb) holding
+//   U_s = - L21 L21^T + (children's updates)
+// (the SYRK stores it, then the children's update-matrix entries are added),
 // which is extend-added into the parent's front. Fronts of one tree level are
 // processed together; siblings add into the same parent entries with device
 // atomics, so the summation order of those contributions is not fixed.
@@ -216,17 +216,6 @@ __global__ void __launch_bounds__(256) k_dstore(const int4* __restrict__ items, 
   }
 }
 
-// ------------------------------------------------------ clear update matrices
-template <typename T>
-__global__ void __launch_bounds__(256) k_zero_u(const int4* __restrict__ items, FacArgs<T> a) {
-  const int4 it = items[blockIdx.x];
-  const int s = it.x;
-  const int64_t rb = a.snr[s] - a.sw[s];
-  const int64_t lo = (int64_t)it.y * 65536, hi = min(rb * rb, lo + 65536);
-  T* U = a.U + a.uoff[s];
-  for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) U[e] = T(0);
-}
-
 // ------------------------------------------------------- in-panel update
 // Right-looking update of the panel columns after block kb:
 //   P[i, j] -= sum_k P[i, c0+k] P[j, c0+k],  j >= c0+bw, i >= j.
@@ -274,7 +263,7 @@ __global__ void __launch_bounds__(256) k_panel_update(const int4* __restrict__ i
 }
 
 // ---------------------------------------------------------------- SYRK
-// U_s -= L21 L21^T on 64 x 64 tiles (ti >= tj), k = panel width.
+// U_s = -L21 L21^T on 64 x 64 tiles (ti >= tj), k = panel width.
 template <typename T>
 __global__ void __launch_bounds__(256) k_syrk(const int4* __restrict__ items, FacArgs<T> a) {
   constexpr int KC = 16;
@@ -321,12 +310,12 @@ __global__ void __launch_bounds__(256) k_syrk(const int4* __restrict__ items, Fa
 #pragma unroll
     for (int x = 0; x < 4; x++) {
       const int gi = i0 + tx + 16 * x, gj = j0 + ty + 16 * y;
-      if (gi < rb && gj < rb && gi >= gj) U[(int64_t)gi + (int64_t)gj * rb] -= acc[x][y];
+      if (gi < rb && gj < rb && gi >= gj) U[(int64_t)gi + (int64_t)gj * rb] = -acc[x][y];
     }
 }
 
 // ----------------------------------------------------- SYRK, 128 x 128 tiles
-// FP32 fronts with rb >= kBigRows: U_s -= L21 L21^T on 128 x 128 tiles
+// FP32 fronts with rb >= kBigRows: U_s = -L21 L21^T on 128 x 128 tiles
 // (ti >= tj), 256 threads with 8 x 8 register tiles (rows tx*4 + {0..3, 64..67},
 // columns ty*4 + {0..3, 64..67}, tx = tid % 16, ty = tid / 16), K staged 16
 // columns at a time through two shared-memory buffers.
@@ -399,7 +388,7 @@ __global__ void __launch_bounds__(256) k_syrk128(const int4* __restrict__ items,
 #pragma unroll
     for (int x = 0; x < 8; x++) {
       const int gi = i0 + tx * 4 + (x & 3) + (x >> 2) * 64;
-      if (gi < rb && gj < rb && gi >= gj) U[(int64_t)gi + (int64_t)gj * rb] -= acc[x][y];
+      if (gi < rb && gj < rb && gi >= gj) U[(int64_t)gi + (int64_t)gj * rb] = -acc[x][y];
     }
   }
 }
@@ -411,7 +400,7 @@ __global__ void __launch_bounds__(256) k_syrk128(const int4* __restrict__ items,
 template <typename T>
 __global__ void __launch_bounds__(256) k_extend_add(const int4* __restrict__ items, FacArgs<T> a) {
   const int4 it = items[blockIdx.x];
-  const int s = it.x, ct = it.y;
+  const int s = it.x, j0 = it.y, j1 = it.z;   // child columns [j0, min(j0 + kEC, j1))
   const int p = a.sparent[s];
   const int w = a.sw[s], rb = a.snr[s] - w;
   const int wp = a.sw[p], nrp = a.snr[p], rbp = nrp - wp, ldp = a.sld[p];
@@ -420,8 +409,8 @@ __global__ void __launch_bounds__(256) k_extend_add(const int4* __restrict__ ite
   T* Pp = a.L + a.poff[p];
   T* Up = a.U + a.uoff[p];
   for (int jj = 0; jj < kEC; jj++) {
-    const int j = ct * kEC + jj;
-    if (j >= rb) break;
+    const int j = j0 + jj;
+    if (j >= j1) break;
     const int b = rel[j];
     for (int i = j + threadIdx.x; i < rb; i += blockDim.x) {
       const int ai = rel[i];
@@ -434,7 +423,7 @@ __global__ void __launch_bounds__(256) k_extend_add(const int4* __restrict__ ite
 
 
 // ------------------------------------------------------- SYRK on tcgen05
-// FP32 fronts with rb >= 128: U_s -= L21 L21^T on 128 x 128 tiles with the
+// FP32 fronts with rb >= 128: U_s = -L21 L21^T on 128 x 128 tiles with the
 // 5th-generation tensor cores. Each operand element x is split into three
 // TF32 parts, hi = tf32(x), mid = tf32(x - hi), lo = tf32(x - hi - mid), and
 // the product is taken as hi*hi + hi*mid + mid*hi + hi*lo + lo*hi + mid*mid
@@ -608,7 +597,7 @@ __global__ void __launch_bounds__(128) k_syrk_tc(const int4* __restrict__ items,
 #pragma unroll
         for (int j = 0; j < 32; j++) {
           const int gj = j0 + c0 + j;
-          if (gj < rb && gi >= gj) U[(int64_t)gi + (int64_t)gj * rb] -= __uint_as_float(r[j]);
+          if (gj < rb && gi >= gj) U[(int64_t)gi + (int64_t)gj * rb] = -__uint_as_float(r[j]);
         }
       }
     }
@@ -724,7 +713,6 @@ cudaError_t launch_factor(const FacArgs<T>& a, const FacLists& fl, const double*
       case 2: k_panel_update<T><<<(unsigned)L.cnt, 256, 0, st>>>(fl.it_pupd + L.off, L.kb, a); break;
       case 3: k_syrk<T><<<(unsigned)L.cnt, 256, 0, st>>>(fl.it_syrk + L.off, a); break;
       case 4: k_extend_add<T><<<(unsigned)L.cnt, 256, 0, st>>>(fl.it_eadd + L.off, a); break;
-      case 5: k_zero_u<T><<<(unsigned)L.cnt, 256, 0, st>>>(fl.it_zero + L.off, a); break;
       case 6:
         if ((e = launch_syrk_tc(fl.it_syrk_tc + L.off, L.cnt, a, st))) return e;
         break;

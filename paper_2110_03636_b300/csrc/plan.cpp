@@ -1,6 +1,7 @@
 #include "plan.hpp"
 
 #include <algorithm>
+#include <array>
 #include <numeric>
 
 namespace kkt {
@@ -95,19 +96,20 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
   }
   for (int32_t L = 0; L < P.nlevels; L++) {
     const auto& F = bylev[L];
-    // clear the update matrices of this level's fronts, then add the children's
-    const int64_t oz = (int64_t)P.it_zero.size() / 4;
-    for (int32_t s : F) {
-      const int64_t rb = P.snr[s] - P.sw[s];
-      for (int64_t c = 0; c < cdiv(rb * rb, 65536); c++) P.it_zero.insert(P.it_zero.end(), {s, (int32_t)c, 0, 0});
-    }
-    const int64_t cz = (int64_t)P.it_zero.size() / 4 - oz;
-    if (cz) P.launches.push_back({5, 0, oz, cz});
+    // the children's update matrices split by column: columns landing in a
+    // parent's panel are added before its block steps, columns landing in
+    // its update matrix after its SYRK (which stores U = -L21 L21^T, so no
+    // clearing pass is needed)
+    std::vector<std::array<int32_t, 3>> ecols_u;   // (child, first column, end) of the U part
     const int64_t o3 = (int64_t)P.it_eadd.size() / 4;
     for (int32_t p : F)
       for (int32_t c : children_of(p)) {
-        const int64_t rb = P.snr[c] - P.sw[c];
-        for (int64_t ct = 0; ct < cdiv(rb, kEC); ct++) P.it_eadd.insert(P.it_eadd.end(), {c, (int32_t)ct, 0, 0});
+        const int32_t rb = P.snr[c] - P.sw[c];
+        const int32_t* relc = P.rel.data() + P.srow[c] + P.sw[c];
+        int32_t split = 0;
+        while (split < rb && relc[split] < P.sw[p]) split++;
+        for (int32_t j = 0; j < split; j += kEC) P.it_eadd.insert(P.it_eadd.end(), {c, j, split, 0});
+        if (split < rb) ecols_u.push_back({c, split, rb});
       }
     const int64_t c3 = (int64_t)P.it_eadd.size() / 4 - o3;
     if (c3) P.launches.push_back({4, 0, o3, c3});
@@ -183,6 +185,11 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
     if (c6) P.launches.push_back({6, 0, o6, c6});
     if (c8) P.launches.push_back({8, 0, o8, c8});
     if (c2) P.launches.push_back({3, 0, o2, c2});
+    const int64_t o4 = (int64_t)P.it_eadd.size() / 4;
+    for (const auto& e : ecols_u)
+      for (int32_t j = e[1]; j < e[2]; j += kEC) P.it_eadd.insert(P.it_eadd.end(), {e[0], j, e[2], 0});
+    const int64_t c4 = (int64_t)P.it_eadd.size() / 4 - o4;
+    if (c4) P.launches.push_back({4, 0, o4, c4});
   }
   // ---------------------------------------------------------- assembly map
   // slot of (row, col) in final labels (row >= col)
