@@ -63,16 +63,15 @@ struct kkt_handle_s {
   // pattern / plan on the device
   int32_t *sfirst, *sw, *snr, *sld, *sparent, *rel, *sn_rows, *perm;
   int64_t *srow, *poff, *uoff;
-  int4 *it_potrf, *it_trsm, *it_pupd, *it_syrk, *it_eadd, *it_zero, *it_syrk_tc, *it_block, *it_syrk128, *it_dstore;
+  int4 *it_potrf, *it_trsm, *it_pupd, *it_syrk, *it_eadd, *it_syrk_tc, *it_block, *it_syrk128, *it_dstore;
   void* Dsc;
   int64_t *slot_pos, *src_ptr;
   int32_t *srcA, *srcB;
   int32_t *Jcol_perm, *JT_row, *JT_vidx, *Hs_col, *Hs_vidx, *JTo_row, *JTo_vidx, *J_colidx;
   int64_t *JT_ptr, *Hs_ptr, *JTo_ptr, *J_rowptr;
-  int32_t *pc_first, *pc_w, *pc_ld, *pc_c, *pc_rc0, *pc_nchunk, *pc_need, *hd_tgt;
-  int32_t *ch_piece, *ch_r0, *ch_nr, *ch_k, *ch_tgt;
+  int32_t *pc_w, *pc_ld, *pc_c, *hd_tgt, *ch_tgt;
   int32_t *fwd_items, *bwd_items;
-  int64_t *pc_row, *pc_colbase, *pc_inv, *pc_zoff, *hd_tptr, *ch_tptr;
+  int64_t *pc_colbase, *pc_inv;
   int32_t *st_first, *st_last, *st_clo, *st_chi, *st_tgt, *sn_piece;
   int64_t* st_tptr;
   int32_t *st_lptr, *st_lev, *st_sn;
@@ -308,7 +307,7 @@ kkt_status kkt_analyse(int64_t n, int64_t m, const int64_t* Hp, const int32_t* H
   h->sparent = A.upload(P.sparent); h->rel = A.upload(P.rel); h->sn_rows = A.upload(h->S.sn_rows);
   h->perm = A.upload(h->S.perm);
   h->srow = A.upload(P.srow); h->poff = A.upload(P.poff); h->uoff = A.upload(P.uoff);
-  h->it_potrf = as_int4(P.it_potrf); h->it_zero = as_int4(P.it_zero);
+  h->it_potrf = as_int4(P.it_potrf);
   h->it_trsm = as_int4(P.it_trsm); h->it_pupd = as_int4(P.it_pupd);
   h->it_syrk = as_int4(P.it_syrk); h->it_eadd = as_int4(P.it_eadd); h->it_syrk_tc = as_int4(P.it_syrk_tc);
   h->it_block = as_int4(P.it_block); h->it_syrk128 = as_int4(P.it_syrk128); h->it_dstore = as_int4(P.it_dstore);
@@ -320,13 +319,11 @@ kkt_status kkt_analyse(int64_t n, int64_t m, const int64_t* Hp, const int32_t* H
   h->JTo_ptr = A.upload(P.JTo_ptr); h->JTo_row = A.upload(P.JTo_row); h->JTo_vidx = A.upload(P.JTo_vidx);
   h->J_rowptr = A.upload(std::vector<int64_t>(Jp, Jp + m + 1));
   h->J_colidx = A.upload(std::vector<int32_t>(Ji, Ji + h->nnzJ));
-  h->pc_first = A.upload(P.pc_first); h->pc_w = A.upload(P.pc_w); h->pc_ld = A.upload(P.pc_ld);
-  h->pc_c = A.upload(P.pc_c); h->pc_rc0 = A.upload(P.pc_rc0);
-  h->pc_nchunk = A.upload(P.pc_nchunk); h->pc_need = A.upload(P.pc_need);
-  h->pc_row = A.upload(P.pc_row); h->pc_colbase = A.upload(P.pc_colbase); h->pc_inv = A.upload(P.pc_inv);
-  h->pc_zoff = A.upload(P.pc_zoff); h->hd_tptr = A.upload(P.hd_tptr); h->hd_tgt = A.upload(P.hd_tgt);
-  h->ch_piece = A.upload(P.ch_piece); h->ch_r0 = A.upload(P.ch_r0); h->ch_nr = A.upload(P.ch_nr);
-  h->ch_k = A.upload(P.ch_k); h->ch_tptr = A.upload(P.ch_tptr); h->ch_tgt = A.upload(P.ch_tgt);
+  // pieces: the triangle inversion's inputs, the inverses' offsets and the
+  // target lists (the rest of each work item's description is in its descriptor)
+  h->pc_w = A.upload(P.pc_w); h->pc_ld = A.upload(P.pc_ld); h->pc_c = A.upload(P.pc_c);
+  h->pc_colbase = A.upload(P.pc_colbase); h->pc_inv = A.upload(P.pc_inv);
+  h->hd_tgt = A.upload(P.hd_tgt); h->ch_tgt = A.upload(P.ch_tgt);
   h->fwd_items = A.upload(P.fwd_items); h->bwd_items = A.upload(P.bwd_items);
   h->st_first = A.upload(P.st_first); h->st_last = A.upload(P.st_last); h->st_clo = A.upload(P.st_clo);
   h->st_chi = A.upload(P.st_chi); h->st_tgt = A.upload(P.st_tgt); h->st_tptr = A.upload(P.st_tptr);
@@ -415,7 +412,7 @@ static cudaError_t factor_launches(kkt_handle h, cudaStream_t st, Prof* prof) {
   a.L = (T*)h->L; a.U = (T*)h->U; a.Dsc = (T*)h->Dsc; a.st = h->dst;
   FacLists fl;
   fl.it_potrf = h->it_potrf; fl.it_trsm = h->it_trsm; fl.it_pupd = h->it_pupd;
-  fl.it_syrk = h->it_syrk; fl.it_eadd = h->it_eadd; fl.it_zero = h->it_zero; fl.it_syrk_tc = h->it_syrk_tc;
+  fl.it_syrk = h->it_syrk; fl.it_eadd = h->it_eadd; fl.it_syrk_tc = h->it_syrk_tc;
   fl.it_block = h->it_block; fl.it_syrk128 = h->it_syrk128; fl.it_dstore = h->it_dstore;
   fl.slot_pos = h->slot_pos; fl.src_ptr = h->src_ptr; fl.srcA = h->srcA; fl.srcB = h->srcB;
   fl.nslot = (int64_t)h->P.slot_pos.size();
@@ -488,13 +485,10 @@ static SolveArgs<T> solve_args(kkt_handle h) {
   const Plan& P = h->P;
   a.n = P.n; a.m = P.m;
   a.sn_rows = h->sn_rows;
-  a.pc_first = h->pc_first; a.pc_w = h->pc_w; a.pc_ld = h->pc_ld; a.pc_c = h->pc_c; a.pc_rc0 = h->pc_rc0;
-  a.pc_nchunk = h->pc_nchunk; a.pc_need = h->pc_need; a.pc_row = h->pc_row; a.pc_colbase = h->pc_colbase;
-  a.pc_inv = h->pc_inv; a.pc_zoff = h->pc_zoff; a.hd_tptr = h->hd_tptr; a.hd_tgt = h->hd_tgt;
+  a.pc_inv = h->pc_inv; a.hd_tgt = h->hd_tgt;
   a.sw = P.solve_w; a.ent = P.ent; a.ent0 = P.ent0; a.max_rows = P.max_rows;
   a.Linv = (const T*)h->Linv;
-  a.ch_piece = h->ch_piece; a.ch_r0 = h->ch_r0; a.ch_nr = h->ch_nr; a.ch_k = h->ch_k;
-  a.ch_tptr = h->ch_tptr; a.ch_tgt = h->ch_tgt;
+  a.ch_tgt = h->ch_tgt;
   a.fwd_items = h->fwd_items; a.bwd_items = h->bwd_items;
   a.nitems = (int64_t)P.fwd_items.size();
   a.npieces = P.npieces;

@@ -34,8 +34,7 @@ cudaError_t prof_begin(Prof* pr, cudaStream_t st);
 cudaError_t prof_end(Prof* pr, int kind, cudaStream_t st);
 
 struct FacLists {
-  const int4 *it_potrf, *it_trsm, *it_pupd, *it_syrk, *it_eadd, *it_zero, *it_syrk_tc, *it_block, *it_syrk128,
-      *it_dstore;
+  const int4 *it_potrf, *it_trsm, *it_pupd, *it_syrk, *it_eadd, *it_syrk_tc, *it_block, *it_syrk128, *it_dstore;
   const int64_t *slot_pos, *src_ptr;
   const int32_t *srcA, *srcB;
   int64_t nslot, panel_total, u_total;
@@ -62,12 +61,8 @@ struct SolveArgs {
   int64_t n, m;
   // solve DAG
   const int32_t* sn_rows;
-  const int32_t *pc_first, *pc_w, *pc_ld, *pc_c, *pc_rc0, *pc_nchunk, *pc_need;
-  const int64_t *pc_row, *pc_colbase, *pc_inv, *pc_zoff, *hd_tptr;
-  const int32_t* hd_tgt;
-  const int32_t *ch_piece, *ch_r0, *ch_nr, *ch_k;
-  const int64_t* ch_tptr;
-  const int32_t* ch_tgt;
+  const int64_t* pc_inv;                 // packed triangle inverses of the pieces
+  const int32_t *hd_tgt, *ch_tgt;        // target pieces of heads' chunk 0 and of chunks
   const int32_t *fwd_items, *bwd_items;
   int64_t nitems, npieces;
   int32_t sw, ent, ent0, max_rows;  // piece width, L entries per chunk / head chunk 0, max chunk rows

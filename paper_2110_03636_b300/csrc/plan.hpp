@@ -78,7 +78,6 @@ struct Plan {
   std::vector<int32_t> it_dstore;           // (s, kb, slot): factored diagonal tile -> panel, per level
   int64_t dsc_total = 0;                    // entries of the diagonal-tile scratch (largest level)
   std::vector<int32_t> it_eadd;             // (child s, col tile) pairs, at the parent's level
-  std::vector<int32_t> it_zero;             // (s, chunk) update matrices cleared at s's level
   std::vector<Launch> launches;
   // assembly gather: panel slot <- sum of sources (H entry, delta, J pair)
   std::vector<int64_t> slot_pos;            // panel position of each slot
