@@ -17,9 +17,9 @@
 // off-diagonal block), handed out in a fixed topological order through an
 // atomic ticket. Every wait is bounded (DevStatus::abort on timeout).
 // Signalling: a CTA barrier, then thread 0 alone publishes with a release
-// store or a fence + atomic (the fence is cumulative over the writes the
-// barrier ordered before it); a waiter polls with an acquire load, then
-// barriers its CTA.
+// store or a release reduction (cumulative over the writes the barrier
+// ordered before it); a waiter polls with an acquire load, then barriers
+// its CTA.
 // The CG recurrences, dot products and scalars are FP64 in both precisions;
 // T is the storage/arithmetic type of L and of the triangular-solve vector.
 #include <cuda_runtime.h>
@@ -94,10 +94,21 @@ __device__ void rows_matvec(const T* tile, int cs, int d0, int nr, int pw, const
     const int rr = (nr + 31) & ~31;
     const int G = max(1, (int)blockDim.x / rr);
     const int i = tid % rr, g = tid / rr;
-    T acc = T(0);
-    if (g < G && i < nr)
-      for (int k = g; k < pw; k += G) acc += tile[k * cs + d0 + i] * x[k];
-    part[tid] = acc;
+    // four independent partial sums (the FMA chain, not the shared-memory
+    // loads, would otherwise set the pace)
+    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+    if (g < G && i < nr) {
+      const T* tc = tile + d0 + i;
+      int k = g;
+      for (; k + 3 * G < pw; k += 4 * G) {
+        a0 += tc[k * cs] * x[k];
+        a1 += tc[(k + G) * cs] * x[k + G];
+        a2 += tc[(k + 2 * G) * cs] * x[k + 2 * G];
+        a3 += tc[(k + 3 * G) * cs] * x[k + 3 * G];
+      }
+      for (; k < pw; k += G) a0 += tc[k * cs] * x[k];
+    }
+    part[tid] = (a0 + a1) + (a2 + a3);
     __syncthreads();
     if (tid < nr) {
       T o = T(0);
@@ -169,6 +180,12 @@ __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
+}
+
+// Arrival on a dependency counter with release semantics: the CTA's writes
+// that a preceding CTA barrier ordered before it become visible first.
+__device__ __forceinline__ void red_release(int* p, int v) {
+  asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 // thread 0: charge the cycles since the last mark to phase i (profile runs)
@@ -343,8 +360,7 @@ __device__ bool fwd_head(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>&
       __syncthreads();
     }
     if (tid == 0) {
-      __threadfence();
-      for (int64_t q = d.tp0; q < d.tp1; q++) atomicAdd(&a.fwd_arrive[a.hd_tgt[q]], 1);
+      for (int64_t q = d.tp0; q < d.tp1; q++) red_release(&a.fwd_arrive[a.hd_tgt[q]], 1);
     }
   }
   return true;
@@ -390,8 +406,7 @@ __device__ bool fwd_chunk(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>
     });
     __syncthreads();
     if (tid == 0) {
-      __threadfence();
-      for (int64_t q = d.tp0; q < d.tp1; q++) atomicAdd(&a.fwd_arrive[a.ch_tgt[q]], 1);
+      for (int64_t q = d.tp0; q < d.tp1; q++) red_release(&a.fwd_arrive[a.ch_tgt[q]], 1);
     }
     return true;
   }
@@ -413,8 +428,7 @@ __device__ bool fwd_chunk(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>
   }
   mark(a, h, 6);
   if (tid == 0) {
-    __threadfence();
-    for (int64_t q = d.tp0; q < d.tp1; q++) atomicAdd(&a.fwd_arrive[a.ch_tgt[q]], 1);
+    for (int64_t q = d.tp0; q < d.tp1; q++) red_release(&a.fwd_arrive[a.ch_tgt[q]], 1);
   }
   mark(a, h, 7);
   return true;
@@ -484,8 +498,7 @@ __device__ bool bwd_chunk(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>
     }
     __syncthreads();
     if (tid == 0) {
-      __threadfence();
-      atomicAdd(&a.bwd_arrive[p], 1);
+      red_release(&a.bwd_arrive[p], 1);
     }
     return true;
   }
@@ -506,8 +519,7 @@ __device__ bool bwd_chunk(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>
     __syncthreads();
   }
   if (tid == 0) {
-    __threadfence();
-    atomicAdd(&a.bwd_arrive[p], 1);
+    red_release(&a.bwd_arrive[p], 1);
   }
   return true;
 }
@@ -748,8 +760,7 @@ __device__ bool fwd_subtree(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<
   }
   mark(a, h, 1);
   if (tid == 0) {
-    __threadfence();
-    for (int64_t q = a.st_tptr[st]; q < a.st_tptr[st + 1]; q++) atomicAdd(&a.fwd_arrive[a.st_tgt[q]], 1);
+    for (int64_t q = a.st_tptr[st]; q < a.st_tptr[st + 1]; q++) red_release(&a.fwd_arrive[a.st_tgt[q]], 1);
   }
   mark(a, h, 2);
   return true;

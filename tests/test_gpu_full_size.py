@@ -86,6 +86,10 @@ def test_grid3d_n1m(precision):
     rr = host_rr(x, dx.cpu().numpy(), dy.cpu().numpy())
     print(precision, "factor s", round(t1 - t0, 2), "solve s", round(t2 - t1, 2), "cg", i.cg_iters, "ir", i.ir_steps,
           "rr(device)", i.rr, "rr(host)", rr, flush=True)
-    assert abs(rr - i.rr) <= 0.1 * rr + 1e-15
+    # residuals near 1e-13 differ in their own rounding: absolute slack
+    assert abs(rr - i.rr) <= 0.1 * rr + 1e-12
+    s.close()
+    del s, dx, dy
+    torch.cuda.empty_cache()
     if precision == "fp64":
         assert rr <= 1e-8
