@@ -98,7 +98,13 @@ typedef struct kkt_options {
                           many per SM or fewer if shared memory does not allow it */
   int32_t solve_ent;   /* L entries staged per triangular-solve work item, 2048..32768
                           (0 = 16384 for KKT_MIXED, 8192 for KKT_FP64) */
-  int32_t pad3_;
+  int32_t refine;      /* KKT_MIXED refinement on K_delta: 0 = plain passes x += M r;
+                          1 = flexible GMRES (restart 20) preconditioned by the mixed
+                          solve M: one M application per iteration, like a pass, and it
+                          converges where the FP32 factor's error is too large for plain
+                          passes (eps_32 kappa(H_gamma) > 1). ir_maxit bounds the M
+                          applications after the first in both modes (< 0: 10 for plain
+                          passes, 60 for GMRES) */
 } kkt_options;
 
 /* Kernel kinds reported by kkt_get_profile. Kinds a plan does not launch

@@ -95,6 +95,10 @@ struct kkt_handle_s {
   void *bL = nullptr, *bLinv = nullptr;
   double *bHv = nullptr, *bJv = nullptr;
   std::vector<int32_t> bstatus;
+  // FGMRES refinement workspace (first use): basis V (N x (kRestart + 1)),
+  // preconditioned directions Z (N x kRestart), N = n + m
+  double *fV = nullptr, *fZ = nullptr, *fw = nullptr, *fr = nullptr, *fzero = nullptr, *fpart = nullptr,
+         *fdots = nullptr, *fcoef = nullptr;
   bool multi = false;
   void *mv, *mzpart;
   double *mrhx, *mp, *mr, *my, *mq, *mbS, *mres_x, *mres_y, *mwv, *mxa;
@@ -235,7 +239,8 @@ static kkt_status analyse_host(int64_t n, int64_t m, const int64_t* Hp, const in
   if (opt) h->opt = *opt; else kkt_default_options(&h->opt);
   const kkt_options& o = h->opt;
   if ((o.solve_w != 0 && (o.solve_w < 32 || o.solve_w > 256)) || o.relax_den <= 0 || o.precision < 0 ||
-      o.precision > 1 || o.solve_ctas < 0 || o.solve_ctas == 1 || o.solve_ctas > 4 ||
+      o.precision > 1 || o.solve_ctas < 0 || o.solve_ctas == 1 || o.solve_ctas > 4 || o.refine < 0 ||
+      o.refine > 1 ||
       (o.solve_ent != 0 && (o.solve_ent < 2048 || o.solve_ent > 32768))) {
     delete h;
     return KKT_ERR_INVALID;
@@ -245,7 +250,7 @@ static kkt_status analyse_host(int64_t n, int64_t m, const int64_t* Hp, const in
   // can reach, so a mixed pass stops early and FP64 refinement does the rest
   const bool f64d = o.precision == KKT_FP64;
   if (!(h->opt.cg_rtol > 0)) h->opt.cg_rtol = f64d ? 1e-12 : 3e-3;
-  if (h->opt.ir_maxit < 0) h->opt.ir_maxit = f64d ? 3 : 10;
+  if (h->opt.ir_maxit < 0) h->opt.ir_maxit = f64d ? 3 : (h->opt.refine == 1 ? 60 : 10);
   if (!(h->opt.ir_rtol > 0)) h->opt.ir_rtol = f64d ? 1e-10 : 1e-9;
   static const int64_t zero = 0;
   if (m == 0) Jp = &zero;
@@ -558,9 +563,161 @@ static kkt_status residual(kkt_handle h, const double* bx, const double* by, con
   return KKT_OK;
 }
 
+// Flexible GMRES on K_delta [dx; dy] = [r_x; r_y], right-preconditioned by
+// the mixed solve M (one persistent solve pass: Schur CG with the FP32
+// factor), restarted every kRestart iterations; classical Gram-Schmidt with
+// one reorthogonalisation; the small Hessenberg problem by Givens rotations
+// on the host. Used by the mixed form when opt.refine = 1.
+constexpr int kRestart = 20;
+static_assert(kRestart + 1 <= kMaxKrylov, "basis size");
+
+static kkt_status solve_fgmres(kkt_handle h, const double* rx, const double* ry, double* dx, double* dy,
+                               cudaStream_t st) {
+  const int64_t n = h->P.n, m = h->P.m, N = n + m;
+  if (!h->fV) {
+    DevArena& A = h->mem;
+    h->fV = A.alloc<double>((size_t)N * (kRestart + 1));
+    h->fZ = A.alloc<double>((size_t)N * kRestart);
+    h->fw = A.alloc<double>(N); h->fr = A.alloc<double>(N); h->fzero = A.alloc<double>(N);
+    h->fpart = A.alloc<double>((size_t)296 * kMaxKrylov);
+    h->fdots = A.alloc<double>(kMaxKrylov); h->fcoef = A.alloc<double>(kMaxKrylov);
+    if (A.failed) { h->fV = nullptr; return KKT_ERR_OOM; }
+    CK(cudaMemsetAsync(h->fzero, 0, sizeof(double) * N, st));
+  }
+  kkt_status s = reset_status(h, st);
+  if (s) return s;
+  int total_it = 0, brk = 0, applications = 0;
+  auto apply_M = [&](const double* bx, const double* by, double* ox, double* oy) -> kkt_status {
+    kkt_status e = solve_pass<float>(h, bx, by, ox, oy, 0, 0, st);
+    if (e) return e;
+    if ((e = read_status(h, st))) return e;
+    if (!h->profp) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, h->cg_a, h->cg_b));
+      h->prof.ms[KKT_K_CG] += ms;
+      h->prof.n[KKT_K_CG] += 1;
+    }
+    const DevStatus& d = *h->hst;
+    total_it += d.cg_iters;
+    brk |= d.breakdown;
+    applications++;
+    if (d.abort) return KKT_ERR_TIMEOUT;
+    if (d.cg_status == 3) return KKT_ERR_CG_BREAKDOWN;
+    if (d.cg_status == 4) return KKT_ERR_CG_MAXIT;
+    h->hst->cg_iters = 0;
+    h->hst->breakdown = 0;
+    CK(cudaMemcpyAsync(h->dst, h->hst, sizeof(DevStatus), cudaMemcpyHostToDevice, st));
+    return KKT_OK;
+  };
+  auto dots = [&](const double* w, int cnt, double* out) -> kkt_status {
+    CK(launch_multidot(w, h->fV, N, N, cnt, h->fpart, h->fdots, st));
+    CK(cudaMemcpyAsync(out, h->fdots, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return KKT_OK;
+  };
+  auto coefs = [&](const double* c, int cnt) -> kkt_status {   // pageable copy: the host buffer is reusable at once
+    CK(cudaMemcpy(h->fcoef, c, sizeof(double) * cnt, cudaMemcpyHostToDevice));
+    return KKT_OK;
+  };
+  auto true_residual = [&](double& rr, double& rnorm, double& bnorm) -> kkt_status {
+    kkt_status e = residual(h, rx, ry, dx, dy, st, h->fr, h->fr + n);
+    if (e) return e;
+    if ((e = read_status(h, st))) return e;
+    rr = h->hst->rr; rnorm = h->hst->res_norm; bnorm = h->hst->b_norm;
+    h->info.rr = h->hst->rr;
+    h->info.be = h->hst->be;
+    return KKT_OK;
+  };
+  auto finish = [&](kkt_status e) {
+    h->info.cg_iters = total_it;
+    h->info.ir_steps = applications > 0 ? applications - 1 : 0;
+    h->info.delta2_used = brk;
+    if (e == KKT_OK) h->inertia_ok = brk ? 0 : 1;
+    return e;
+  };
+  // x0 = M b
+  if ((s = apply_M(rx, ry, dx, dy))) return finish(s);
+  double rr, rnorm, bnorm;
+  if ((s = true_residual(rr, rnorm, bnorm))) return finish(s);
+  double H[kRestart + 1][kRestart], cs[kRestart], sn[kRestart], g[kRestart + 1], hc[kMaxKrylov], d2[kMaxKrylov];
+  while (rr > h->opt.ir_rtol && applications - 1 < h->opt.ir_maxit) {
+    // V0 = r / ||r||
+    double c0 = 1.0 / rnorm;
+    if ((s = coefs(&c0, 1))) return finish(s);
+    CK(launch_lincomb(h->fV, 0.0, h->fr, N, N, 1, h->fcoef, st));
+    for (int i = 0; i <= kRestart; i++) g[i] = 0.0;
+    g[0] = rnorm;
+    int k = 0;
+    for (; k < kRestart && applications - 1 < h->opt.ir_maxit; k++) {
+      double* Vk = h->fV + (size_t)k * N;
+      double* Zk = h->fZ + (size_t)k * N;
+      if ((s = apply_M(Vk, Vk + n, Zk, Zk + n))) return finish(s);
+      // w = -K Z_k (the residual kernel with a zero right-hand side)
+      if ((s = residual(h, h->fzero, h->fzero, Zk, Zk + n, st, h->fw, h->fw + n))) return finish(s);
+      // u = K Z_k = -w; h_i = (u, V_i) = -(w, V_i); w <- w - sum (w, V_i) V_i (twice)
+      if ((s = dots(h->fw, k + 1, hc))) return finish(s);
+      for (int i = 0; i <= k; i++) d2[i] = -hc[i];
+      if ((s = coefs(d2, k + 1))) return finish(s);
+      CK(launch_lincomb(h->fw, 1.0, h->fV, N, N, k + 1, h->fcoef, st));
+      double hc2[kMaxKrylov];
+      if ((s = dots(h->fw, k + 1, hc2))) return finish(s);
+      for (int i = 0; i <= k; i++) { d2[i] = -hc2[i]; hc[i] += hc2[i]; }
+      if ((s = coefs(d2, k + 1))) return finish(s);
+      CK(launch_lincomb(h->fw, 1.0, h->fV, N, N, k + 1, h->fcoef, st));
+      CK(launch_multidot(h->fw, h->fw, N, N, 1, h->fpart, h->fdots, st));
+      double ww;
+      CK(cudaMemcpyAsync(&ww, h->fdots, sizeof(double), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      const double hn = std::sqrt(std::max(ww, 0.0));
+      for (int i = 0; i <= k; i++) H[i][k] = -hc[i];
+      H[k + 1][k] = hn;
+      // V_{k+1} = u / ||u|| = -w / hn
+      if (hn > 0) {
+        double c1 = -1.0 / hn;
+        if ((s = coefs(&c1, 1))) return finish(s);
+        CK(launch_lincomb(h->fV + (size_t)(k + 1) * N, 0.0, h->fw, N, N, 1, h->fcoef, st));
+      }
+      // Givens rotations
+      for (int i = 0; i < k; i++) {
+        const double t = cs[i] * H[i][k] + sn[i] * H[i + 1][k];
+        H[i + 1][k] = -sn[i] * H[i][k] + cs[i] * H[i + 1][k];
+        H[i][k] = t;
+      }
+      const double den = std::hypot(H[k][k], H[k + 1][k]);
+      cs[k] = den > 0 ? H[k][k] / den : 1.0;
+      sn[k] = den > 0 ? H[k + 1][k] / den : 0.0;
+      H[k][k] = den;
+      H[k + 1][k] = 0.0;
+      g[k + 1] = -sn[k] * g[k];
+      g[k] = cs[k] * g[k];
+      if (std::fabs(g[k + 1]) <= 0.5 * h->opt.ir_rtol * bnorm || hn == 0.0) { k++; break; }
+    }
+    // y = H^-1 g (upper triangular k x k); x += Z y
+    double y[kRestart];
+    for (int i = k - 1; i >= 0; i--) {
+      double t = g[i];
+      for (int j = i + 1; j < k; j++) t -= H[i][j] * y[j];
+      y[i] = H[i][i] != 0.0 ? t / H[i][i] : 0.0;
+    }
+    if (k > 0) {
+      if ((s = coefs(y, k))) return finish(s);
+      CK(launch_lincomb(dx, 1.0, h->fZ, N, n, k, h->fcoef, st));
+      if (m) CK(launch_lincomb(dy, 1.0, h->fZ + n, N, m, k, h->fcoef, st));
+    }
+    if ((s = true_residual(rr, rnorm, bnorm))) return finish(s);
+    if (k == 0) break;
+  }
+  return finish(KKT_OK);
+}
+
 static kkt_status solve_common(kkt_handle h, const double* rx, const double* ry, double* dx, double* dy,
                                cudaStream_t st) {
   if (!h->factored) return KKT_ERR_STATE;
+  if (h->opt.precision == KKT_MIXED && h->opt.refine == 1) {
+    h->inertia_ok = 0;
+    std::memset(&h->info, 0, sizeof(h->info));
+    return solve_fgmres(h, rx, ry, dx, dy, st);
+  }
   h->inertia_ok = 0;
   std::memset(&h->info, 0, sizeof(h->info));
   const bool f64 = h->opt.precision == KKT_FP64;

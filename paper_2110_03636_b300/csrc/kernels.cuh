@@ -114,6 +114,13 @@ struct SolveArgs {
 };
 
 constexpr int kMaxRhs = 8;                // right-hand sides per solve-kernel launch
+constexpr int kMaxKrylov = 24;            // basis vectors of the FGMRES refinement (restart length + 1)
+
+// FP64 vector kernels of the FGMRES refinement (krylov.cu)
+cudaError_t launch_multidot(const double* w, const double* V, int64_t ld, int64_t N, int cnt, double* part,
+                            double* out, cudaStream_t st);
+cudaError_t launch_lincomb(double* y, double alpha, const double* V, int64_t ld, int64_t N, int cnt, const double* c,
+                           cudaStream_t st);
 constexpr int kRedStride = 2 * kMaxRhs;   // doubles per CTA in the reduction buffer
 
 template <typename T>

@@ -17,9 +17,9 @@
 // off-diagonal block), handed out in a fixed topological order through an
 // atomic ticket. Every wait is bounded (DevStatus::abort on timeout).
 // Signalling: a CTA barrier, then thread 0 alone publishes with a release
-// store or a release reduction (cumulative over the writes the barrier
-// ordered before it); a waiter polls with an acquire load, then barriers
-// its CTA.
+// store or a fence + atomic (the fence is cumulative over the writes the
+// barrier ordered before it; measured cheaper than release reductions); a
+// waiter polls with an acquire load, then barriers its CTA.
 // The CG recurrences, dot products and scalars are FP64 in both precisions;
 // T is the storage/arithmetic type of L and of the triangular-solve vector.
 #include <cuda_runtime.h>
@@ -180,12 +180,6 @@ __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
-}
-
-// Arrival on a dependency counter with release semantics: the CTA's writes
-// that a preceding CTA barrier ordered before it become visible first.
-__device__ __forceinline__ void red_release(int* p, int v) {
-  asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 // thread 0: charge the cycles since the last mark to phase i (profile runs)
@@ -360,7 +354,8 @@ __device__ bool fwd_head(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>&
       __syncthreads();
     }
     if (tid == 0) {
-      for (int64_t q = d.tp0; q < d.tp1; q++) red_release(&a.fwd_arrive[a.hd_tgt[q]], 1);
+      __threadfence();
+      for (int64_t q = d.tp0; q < d.tp1; q++) atomicAdd(&a.fwd_arrive[a.hd_tgt[q]], 1);
     }
   }
   return true;
@@ -406,7 +401,8 @@ __device__ bool fwd_chunk(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>
     });
     __syncthreads();
     if (tid == 0) {
-      for (int64_t q = d.tp0; q < d.tp1; q++) red_release(&a.fwd_arrive[a.ch_tgt[q]], 1);
+      __threadfence();
+      for (int64_t q = d.tp0; q < d.tp1; q++) atomicAdd(&a.fwd_arrive[a.ch_tgt[q]], 1);
     }
     return true;
   }
@@ -428,7 +424,8 @@ __device__ bool fwd_chunk(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>
   }
   mark(a, h, 6);
   if (tid == 0) {
-    for (int64_t q = d.tp0; q < d.tp1; q++) red_release(&a.fwd_arrive[a.ch_tgt[q]], 1);
+    __threadfence();
+    for (int64_t q = d.tp0; q < d.tp1; q++) atomicAdd(&a.fwd_arrive[a.ch_tgt[q]], 1);
   }
   mark(a, h, 7);
   return true;
@@ -498,7 +495,8 @@ __device__ bool bwd_chunk(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>
     }
     __syncthreads();
     if (tid == 0) {
-      red_release(&a.bwd_arrive[p], 1);
+      __threadfence();
+      atomicAdd(&a.bwd_arrive[p], 1);
     }
     return true;
   }
@@ -519,7 +517,8 @@ __device__ bool bwd_chunk(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>
     __syncthreads();
   }
   if (tid == 0) {
-    red_release(&a.bwd_arrive[p], 1);
+    __threadfence();
+    atomicAdd(&a.bwd_arrive[p], 1);
   }
   return true;
 }
@@ -760,7 +759,8 @@ __device__ bool fwd_subtree(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<
   }
   mark(a, h, 1);
   if (tid == 0) {
-    for (int64_t q = a.st_tptr[st]; q < a.st_tptr[st + 1]; q++) red_release(&a.fwd_arrive[a.st_tgt[q]], 1);
+    __threadfence();
+    for (int64_t q = a.st_tptr[st]; q < a.st_tptr[st + 1]; q++) atomicAdd(&a.fwd_arrive[a.st_tgt[q]], 1);
   }
   mark(a, h, 2);
   return true;

@@ -490,3 +490,15 @@ def test_factor_regularized_matches_oracle(lam):
             # conditioning-limited (reading of the 1e-6 gate: RR decides)
             odx, ody, _ = fac.solve(sys.r_x, sys.r_y)
             assert rel(np.concatenate([dx, dy]), np.concatenate([odx, ody])) <= 1e-6
+
+
+@pytest.mark.parametrize("name", ["grid2d_n2000", "grid2d_n20k"])
+def test_mixed_fgmres_refinement_matches_oracle(name):
+    """The mixed form with flexible-GMRES refinement (refine=1) reaches the
+    oracle's solution and RR <= 1e-9, like the plain refinement passes."""
+    sys = W.make_config(name)
+    _, _, odx, ody, _ = O.solve_system(sys)
+    s, code, dx, dy = gpu_solve(sys, "mixed", ordering="nd", refine=1)
+    assert code == 0
+    assert s.info.rr <= 1e-9 and s.inertia_ok
+    assert rel(np.concatenate([dx, dy]), np.concatenate([odx, ody])) <= 1e-6
