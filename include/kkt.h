@@ -197,12 +197,15 @@ kkt_status kkt_factor_regularized(kkt_handle h, const double* H_vals, const doub
                                   double delta_min, double delta_max, double* delta_used, void* stream);
 
 /* Solve with the last successful factor (Algorithm 1 solve steps; eqs.
- * Schur1/Schur2), then FP64 refinement on K_delta while RR > ir_rtol.
+ * Schur1/Schur2), then FP64 refinement on K_delta while RR > ir_rtol
+ * (plain passes, or flexible GMRES for KKT_MIXED with opt.refine = 1).
  *   r_x, r_y  device double[n], double[m] (may alias nothing written here)
  *   dx, dy    device double[n], double[m] outputs
  * Synchronizes `stream`. Errors: KKT_ERR_STATE (no successful factor),
  * KKT_ERR_CG_BREAKDOWN, KKT_ERR_CG_MAXIT, KKT_ERR_TIMEOUT, KKT_ERR_CUDA.
- * On an error the outputs hold the last iterate. */
+ * On an error the outputs hold the last iterate. KKT_OK with
+ * kkt_info.rr > ir_rtol means the refinement budget (ir_maxit) ran out
+ * first: the caller decides whether that residual is acceptable. */
 kkt_status kkt_solve(kkt_handle h, const double* r_x, const double* r_y, double* dx, double* dy,
                      void* stream);
 
