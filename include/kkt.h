@@ -98,13 +98,13 @@ typedef struct kkt_options {
                           many per SM or fewer if shared memory does not allow it */
   int32_t solve_ent;   /* L entries staged per triangular-solve work item, 2048..32768
                           (0 = 16384 for KKT_MIXED, 8192 for KKT_FP64) */
-  int32_t refine;      /* KKT_MIXED refinement on K_delta: 0 = plain passes x += M r;
-                          1 = flexible GMRES (restart 20) preconditioned by the mixed
+  int32_t refine;      /* KKT_MIXED refinement on K_delta: 1 = plain passes x += M r;
+                          2 = flexible GMRES (restart 20) preconditioned by the mixed
                           solve M: one M application per iteration, like a pass, and it
                           converges where the FP32 factor's error is too large for plain
-                          passes (eps_32 kappa(H_gamma) > 1). ir_maxit bounds the M
-                          applications after the first in both modes (< 0: 10 for plain
-                          passes, 60 for GMRES) */
+                          passes (eps_32 kappa(H_gamma) > 1); 0 (default) = 2. ir_maxit
+                          bounds the M applications after the first in both modes
+                          (< 0: 10 for plain passes, 60 for GMRES) */
 } kkt_options;
 
 /* Kernel kinds reported by kkt_get_profile. Kinds a plan does not launch
@@ -198,7 +198,7 @@ kkt_status kkt_factor_regularized(kkt_handle h, const double* H_vals, const doub
 
 /* Solve with the last successful factor (Algorithm 1 solve steps; eqs.
  * Schur1/Schur2), then FP64 refinement on K_delta while RR > ir_rtol
- * (plain passes, or flexible GMRES for KKT_MIXED with opt.refine = 1).
+ * (flexible GMRES for KKT_MIXED unless opt.refine = 1 selects plain passes).
  *   r_x, r_y  device double[n], double[m] (may alias nothing written here)
  *   dx, dy    device double[n], double[m] outputs
  * Synchronizes `stream`. Errors: KKT_ERR_STATE (no successful factor),

@@ -240,7 +240,7 @@ static kkt_status analyse_host(int64_t n, int64_t m, const int64_t* Hp, const in
   const kkt_options& o = h->opt;
   if ((o.solve_w != 0 && (o.solve_w < 32 || o.solve_w > 256)) || o.relax_den <= 0 || o.precision < 0 ||
       o.precision > 1 || o.solve_ctas < 0 || o.solve_ctas == 1 || o.solve_ctas > 4 || o.refine < 0 ||
-      o.refine > 1 ||
+      o.refine > 2 ||
       (o.solve_ent != 0 && (o.solve_ent < 2048 || o.solve_ent > 32768))) {
     delete h;
     return KKT_ERR_INVALID;
@@ -250,7 +250,8 @@ static kkt_status analyse_host(int64_t n, int64_t m, const int64_t* Hp, const in
   // can reach, so a mixed pass stops early and FP64 refinement does the rest
   const bool f64d = o.precision == KKT_FP64;
   if (!(h->opt.cg_rtol > 0)) h->opt.cg_rtol = f64d ? 1e-12 : 3e-3;
-  if (h->opt.ir_maxit < 0) h->opt.ir_maxit = f64d ? 3 : (h->opt.refine == 1 ? 60 : 10);
+  if (h->opt.refine == 0) h->opt.refine = 2;
+  if (h->opt.ir_maxit < 0) h->opt.ir_maxit = f64d ? 3 : (h->opt.refine == 2 ? 60 : 10);
   if (!(h->opt.ir_rtol > 0)) h->opt.ir_rtol = f64d ? 1e-10 : 1e-9;
   static const int64_t zero = 0;
   if (m == 0) Jp = &zero;
@@ -567,7 +568,7 @@ static kkt_status residual(kkt_handle h, const double* bx, const double* by, con
 // the mixed solve M (one persistent solve pass: Schur CG with the FP32
 // factor), restarted every kRestart iterations; classical Gram-Schmidt with
 // one reorthogonalisation; the small Hessenberg problem by Givens rotations
-// on the host. Used by the mixed form when opt.refine = 1.
+// on the host. The mixed form's default refinement (opt.refine = 2).
 constexpr int kRestart = 20;
 static_assert(kRestart + 1 <= kMaxKrylov, "basis size");
 
@@ -713,7 +714,7 @@ static kkt_status solve_fgmres(kkt_handle h, const double* rx, const double* ry,
 static kkt_status solve_common(kkt_handle h, const double* rx, const double* ry, double* dx, double* dy,
                                cudaStream_t st) {
   if (!h->factored) return KKT_ERR_STATE;
-  if (h->opt.precision == KKT_MIXED && h->opt.refine == 1) {
+  if (h->opt.precision == KKT_MIXED && h->opt.refine == 2) {
     h->inertia_ok = 0;
     std::memset(&h->info, 0, sizeof(h->info));
     return solve_fgmres(h, rx, ry, dx, dy, st);

@@ -492,13 +492,15 @@ def test_factor_regularized_matches_oracle(lam):
             assert rel(np.concatenate([dx, dy]), np.concatenate([odx, ody])) <= 1e-6
 
 
+@pytest.mark.parametrize("refine", [1, 2])
 @pytest.mark.parametrize("name", ["grid2d_n2000", "grid2d_n20k"])
-def test_mixed_fgmres_refinement_matches_oracle(name):
-    """The mixed form with flexible-GMRES refinement (refine=1) reaches the
-    oracle's solution and RR <= 1e-9, like the plain refinement passes."""
+def test_mixed_refinement_modes_match_oracle(name, refine):
+    """The mixed form with plain refinement passes (refine=1) and with
+    flexible GMRES (refine=2, the default) reaches the oracle's solution and
+    RR <= 1e-9."""
     sys = W.make_config(name)
     _, _, odx, ody, _ = O.solve_system(sys)
-    s, code, dx, dy = gpu_solve(sys, "mixed", ordering="nd", refine=1)
+    s, code, dx, dy = gpu_solve(sys, "mixed", ordering="nd", refine=refine)
     assert code == 0
     assert s.info.rr <= 1e-9 and s.inertia_ok
     assert rel(np.concatenate([dx, dy]), np.concatenate([odx, ody])) <= 1e-6
