@@ -298,8 +298,27 @@ kkt_status kkt_get_profile(kkt_handle h, double* ms, int64_t* launches, int32_t 
  * loops of subtree items, [15] zero, [16..18] forward subtree items:
  * staging, levels, publishing; [19..23] forward chunks: metadata and copy
  * issue, dependency wait, vector load and copy wait, mat-vec, publishing;
- * [24..31] zero. */
+ * [24..29] backward piece heads: metadata and copy issue, dependency wait,
+ * vector loads and copy wait, chunk-0 product, inverse product, storing
+ * and publishing; [30..31] zero. */
 kkt_status kkt_get_solve_counters(kkt_handle h, uint64_t* out, int32_t reset);
+
+/* Item timeline of the persistent solve kernel, for handles created with
+ * opt.profile = 1 (KKT_ERR_STATE otherwise): the forward and the backward
+ * sweep of the first H_gamma^-1 application of the last solve-kernel launch.
+ * Host uint64_t[6 * nitems] (nitems from kkt_symbolic_info.nitems; cap is
+ * the array length, KKT_ERR_INVALID when smaller), laid out
+ * [sweep 0 forward / 1 backward][dispatch ticket][3]: the device global
+ * timer (ns) when the item was handed out and when it finished, and the CTA
+ * that ran it. Entries of an item not run since the handle was created are
+ * zero. */
+kkt_status kkt_get_solve_trace(kkt_handle h, uint64_t* out, int64_t cap);
+
+/* The two sweeps' dispatch orders (host int32_t[nitems] each, cap their
+ * length): entry t is the item handed out at ticket t, coded as a row chunk
+ * c >= 0, a piece head -1 - p (p < npieces), or a subtree item
+ * -1 - npieces - s. Available after kkt_analyse_host; no device access. */
+kkt_status kkt_get_solve_item_order(kkt_handle h, int32_t* fwd, int32_t* bwd, int64_t cap);
 
 kkt_status kkt_destroy(kkt_handle h);
 

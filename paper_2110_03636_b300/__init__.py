@@ -77,6 +77,8 @@ def _load():
     L.kkt_get_factor_panels.argtypes = [P, P]
     L.kkt_get_profile.argtypes = [P, P, P, I32]
     L.kkt_get_solve_counters.argtypes = [P, P, I32]
+    L.kkt_get_solve_trace.argtypes = [P, P, I64]
+    L.kkt_get_solve_item_order.argtypes = [P, P, P, I64]
     L.kkt_residual_noalloc.argtypes = [I64, I64, P, P, P, P, P, P, D, P, P, P, P, P, P, P, P]
     L.kkt_destroy.argtypes = [P]
     L.kkt_analyse_4x4.argtypes = [I64, I64, I64, P, P, P, P, P, P, C.POINTER(kkt_options), C.POINTER(P)]
@@ -91,7 +93,7 @@ def _load():
     L.kkt_status_string.restype = C.c_char_p
     for nm in ("kkt_analyse", "kkt_analyse_host", "kkt_factor", "kkt_solve", "kkt_solve_multi", "kkt_factor_batch", "kkt_solve_batch", "kkt_factor_regularized", "kkt_factor_solve_host", "kkt_hsolve", "kkt_get_info",
                "kkt_inertia", "kkt_symbolic_info_get", "kkt_get_symbolic", "kkt_get_factor_panels", "kkt_get_profile", "kkt_get_solve_counters", "kkt_residual_noalloc",
-               "kkt_destroy", "kkt_analyse_4x4", "kkt_analyse_4x4_host", "kkt_get_4x4_pattern", "kkt_factor_4x4",
+               "kkt_get_solve_trace", "kkt_get_solve_item_order", "kkt_destroy", "kkt_analyse_4x4", "kkt_analyse_4x4_host", "kkt_get_4x4_pattern", "kkt_factor_4x4",
                "kkt_solve_4x4", "kkt_destroy_4x4"):
         getattr(L, nm).restype = I32
     return L
@@ -101,7 +103,7 @@ _lib = _load()
 EXPORTED = ("kkt_default_options", "kkt_analyse", "kkt_analyse_host", "kkt_factor", "kkt_solve", "kkt_solve_multi", "kkt_factor_batch", "kkt_solve_batch", "kkt_factor_regularized", "kkt_factor_solve_host",
             "kkt_hsolve", "kkt_get_info", "kkt_inertia", "kkt_symbolic_info_get", "kkt_get_symbolic",
             "kkt_get_factor_panels", "kkt_get_profile", "kkt_get_solve_counters", "kkt_residual_noalloc",
-            "kkt_destroy", "kkt_status_string", "kkt_analyse_4x4", "kkt_analyse_4x4_host", "kkt_4x4_inner",
+            "kkt_get_solve_trace", "kkt_get_solve_item_order", "kkt_destroy", "kkt_status_string", "kkt_analyse_4x4", "kkt_analyse_4x4_host", "kkt_4x4_inner",
             "kkt_get_4x4_pattern", "kkt_factor_4x4", "kkt_solve_4x4", "kkt_destroy_4x4")
 KERNEL_KINDS = ("assemble", "potrf", "trsm", "panel_update", "syrk", "extend_add", "zero_u", "cg_persistent",
                 "residual", "tri_inv", "syrk_tc", "block")
@@ -271,8 +273,26 @@ def kkt_get_solve_counters(h, reset=False):
     keys = ("dispatch", "dep_wait", "copy_wait", "items", "barriers", "n_items", "cta_launches",
             "subtree_cycles", "n_subtree", "head_cycles", "n_head", "chunk_cycles", "n_chunk",
             "subtree_level_cycles", "n_subtree_levels", "zero15",
-            "fsub_stage", "fsub_levels", "fsub_publish", "fch_issue", "fch_dep", "fch_load", "fch_matvec", "fch_publish")
+            "fsub_stage", "fsub_levels", "fsub_publish", "fch_issue", "fch_dep", "fch_load", "fch_matvec", "fch_publish",
+            "bhd_issue", "bhd_dep", "bhd_load", "bhd_chunk0", "bhd_inverse", "bhd_publish")
     return {k: int(out[i]) for i, k in enumerate(keys)}
+
+
+def kkt_get_solve_trace(h):
+    """Item timeline of the first H^-1 application of the last solve launch
+    (profile=1 handles): uint64 array [2 sweeps, nitems, (start ns, end ns, CTA)]."""
+    ni = kkt_symbolic_info_get(h).nitems
+    out = np.zeros((2, ni, 3), np.uint64)
+    _check("kkt_get_solve_trace", _lib.kkt_get_solve_trace(h, out.ctypes.data, out.size))
+    return out
+
+
+def kkt_get_solve_item_order(h):
+    """Dispatch orders of the forward and backward sweeps (int32 item codes)."""
+    ni = kkt_symbolic_info_get(h).nitems
+    f, b = np.zeros(ni, np.int32), np.zeros(ni, np.int32)
+    _check("kkt_get_solve_item_order", _lib.kkt_get_solve_item_order(h, f.ctypes.data, b.ctypes.data, ni))
+    return f, b
 
 
 def kkt_destroy(h):
@@ -437,6 +457,12 @@ class KKTSolver:
 
     def solve_counters(self, reset=False):
         return kkt_get_solve_counters(self.h, reset)
+
+    def solve_trace(self):
+        return kkt_get_solve_trace(self.h)
+
+    def solve_item_order(self):
+        return kkt_get_solve_item_order(self.h)
 
     def close(self):
         if getattr(self, "h", None):

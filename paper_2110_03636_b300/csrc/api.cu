@@ -80,7 +80,7 @@ struct kkt_handle_s {
   uint8_t* tmaps;
   // values and workspace
   double *Hv, *Jv;
-  void *L, *U, *v, *zpart, *Linv;
+  void *L, *U, *v, *Linv;
   double *rhx, *p, *r, *y, *q, *bS, *red, *res_x, *res_y, *wv, *xa;
   double *stage_rx, *stage_ry, *stage_dx, *stage_dy;
   int* counters;   // fwd_arrive, fwd_done, bwd_arrive, bwd_done (npieces each), disp[3], bar[2]
@@ -100,10 +100,11 @@ struct kkt_handle_s {
   double *fV = nullptr, *fZ = nullptr, *fw = nullptr, *fr = nullptr, *fzero = nullptr, *fpart = nullptr,
          *fdots = nullptr, *fcoef = nullptr;
   bool multi = false;
-  void *mv, *mzpart;
+  void *mv;
   double *mrhx, *mp, *mr, *my, *mq, *mbS, *mres_x, *mres_y, *mwv, *mxa;
   double* d_dg = nullptr;    // device [delta, gamma] read by the assembly kernel
   unsigned long long* d_instr = nullptr;   // solve-kernel cycle counters (profile mode)
+  unsigned long long* d_trace = nullptr;   // solve-kernel item timeline (profile mode)
   double* h_dg = nullptr;    // pinned staging for it
   cudaStream_t cap_stream = nullptr;   // private stream used to capture the factor graph
   cudaGraphExec_t fac_graph = nullptr; // the whole factorization as one CUDA graph
@@ -347,7 +348,6 @@ kkt_status kkt_analyse(int64_t n, int64_t m, const int64_t* Hp, const int32_t* H
   h->U = A.alloc<char>(es * (size_t)P.u_total);
   h->Dsc = A.alloc<char>(es * (size_t)P.dsc_total);
   h->v = A.alloc<char>(es * (size_t)n);
-  h->zpart = A.alloc<char>(es * (size_t)P.z_total);
   h->Linv = A.alloc<char>(es * (size_t)P.inv_total);
   {
     std::vector<uint8_t> maps;
@@ -369,6 +369,7 @@ kkt_status kkt_analyse(int64_t n, int64_t m, const int64_t* Hp, const int32_t* H
   h->dst = A.alloc<DevStatus>(1);
   h->d_dg = A.alloc<double>(2);
   h->d_instr = A.alloc<unsigned long long>(32);
+  if (o.profile) h->d_trace = A.alloc<unsigned long long>(6 * P.fwd_items.size() + 6);
   if (A.failed) { kkt_destroy(h); return KKT_ERR_OOM; }
   if (cudaMallocHost(&h->hst, sizeof(DevStatus)) != cudaSuccess) { cudaGetLastError(); h->hst = nullptr; kkt_destroy(h); return KKT_ERR_OOM; }
   if (cudaMallocHost(&h->h_dg, 2 * sizeof(double)) != cudaSuccess) { cudaGetLastError(); h->h_dg = nullptr; kkt_destroy(h); return KKT_ERR_OOM; }
@@ -511,15 +512,15 @@ static SolveArgs<T> solve_args(kkt_handle h) {
   a.v = (T*)h->v; a.rhx = h->rhx; a.p = h->p; a.r = h->r; a.y = h->y; a.q = h->q; a.bS = h->bS;
   a.wv = h->wv; a.xa = h->xa;
   a.xacc = h->opt.precision == KKT_MIXED ? 1 : 0;
-  a.zpart = (T*)h->zpart;
   const int64_t np = P.npieces;
   a.fwd_arrive = h->counters; a.fwd_done = h->counters + np;
   a.bwd_arrive = h->counters + 2 * np; a.bwd_done = h->counters + 3 * np;
   a.disp = h->counters + 4 * np; a.bar = h->counters + 4 * np + 4;
   a.red = h->red; a.st = h->dst;
-  a.nrhs = 1; a.z_total = P.z_total; a.rhs_stat = h->rhs_stat;
+  a.nrhs = 1; a.rhs_stat = h->rhs_stat;
   a.spin = h->opt.spin_cycles > 0 ? h->opt.spin_cycles : kSpinCycles;
   a.instr = h->profp ? h->d_instr : nullptr;
+  a.trace = h->profp ? h->d_trace : nullptr;
   return a;
 }
 
@@ -531,7 +532,7 @@ static kkt_status solve_pass(kkt_handle h, const double* bx, const double* by, d
   a.bx = bx; a.by = by; a.ox = ox; a.oy = oy; a.accumulate = accumulate; a.mode = mode;
   if (nrhs > 1) {
     a.nrhs = nrhs;
-    a.v = (T*)h->mv; a.zpart = (T*)h->mzpart; a.rhx = h->mrhx;
+    a.v = (T*)h->mv; a.rhx = h->mrhx;
     a.p = h->mp; a.r = h->mr; a.y = h->my; a.q = h->mq; a.bS = h->mbS;
     a.wv = h->mwv; a.xa = h->mxa;
   }
@@ -920,7 +921,6 @@ kkt_status kkt_solve_multi(kkt_handle h, int32_t nrhs, const double* r_x, const 
     const size_t es = h->opt.precision == KKT_FP64 ? sizeof(double) : sizeof(float);
     DevArena& A = h->mem;
     h->mv = A.alloc<char>(es * (size_t)n * kMaxRhs);
-    h->mzpart = A.alloc<char>(es * (size_t)std::max<int64_t>(h->P.z_total, 1) * kMaxRhs);
     h->mrhx = A.alloc<double>((size_t)n * kMaxRhs);
     h->mwv = A.alloc<double>((size_t)n * kMaxRhs); h->mxa = A.alloc<double>((size_t)n * kMaxRhs);
     h->mp = A.alloc<double>((size_t)m * kMaxRhs); h->mr = A.alloc<double>((size_t)m * kMaxRhs);
@@ -1086,6 +1086,25 @@ kkt_status kkt_get_solve_counters(kkt_handle h, uint64_t* out, int32_t reset) {
   CK(cudaSetDevice(h->device));
   CK(cudaMemcpy(out, h->d_instr, 32 * sizeof(uint64_t), cudaMemcpyDeviceToHost));
   if (reset) CK(cudaMemset(h->d_instr, 0, 32 * sizeof(uint64_t)));
+  return KKT_OK;
+}
+
+kkt_status kkt_get_solve_trace(kkt_handle h, uint64_t* out, int64_t cap) {
+  if (!h || !out) return KKT_ERR_INVALID;
+  if (!h->on_device || !h->d_trace) return KKT_ERR_STATE;
+  const int64_t total = 6 * (int64_t)h->P.fwd_items.size();
+  if (cap < total) return KKT_ERR_INVALID;
+  CK(cudaSetDevice(h->device));
+  CK(cudaMemcpy(out, h->d_trace, (size_t)total * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+  return KKT_OK;
+}
+
+kkt_status kkt_get_solve_item_order(kkt_handle h, int32_t* fwd, int32_t* bwd, int64_t cap) {
+  if (!h || !fwd || !bwd) return KKT_ERR_INVALID;
+  const int64_t n = (int64_t)h->P.fwd_items.size();
+  if (cap < n) return KKT_ERR_INVALID;
+  std::copy(h->P.fwd_items.begin(), h->P.fwd_items.end(), fwd);
+  std::copy(h->P.bwd_items.begin(), h->P.bwd_items.end(), bwd);
   return KKT_OK;
 }
 

@@ -94,16 +94,13 @@ struct SolveArgs {
   // workspace
   // nrhs right-hand sides share every triangular sweep (each staged L tile
   // serves all of them); vector j of each workspace array starts at j times
-  // its length (n for v, rhx, bx, ox; m for the CG vectors, by, oy; z_total
-  // for zpart)
+  // its length (n for v, rhx, bx, ox; m for the CG vectors, by, oy)
   int32_t nrhs;
-  int64_t z_total;
   int32_t* rhs_stat;   // [kMaxRhs * 3]: CG products, status, delta_2 restart per right-hand side
   T* v;
   double *rhx, *p, *r, *y, *q, *bS;
   double *wv, *xa;     // w = H^-1 r^_x and the accumulated dx (n each)
   int32_t xacc;        // 1: accumulate dx along CG (mixed form); 0: direct solve for dx
-  T* zpart;
   int *fwd_arrive, *fwd_done, *bwd_arrive, *bwd_done;
   int* disp;   // [3]
   int* bar;    // [2]
@@ -111,6 +108,8 @@ struct SolveArgs {
   DevStatus* st;
   long long spin;  // bound of every wait, in clock cycles
   unsigned long long* instr;  // optional per-kernel cycle counters (profile mode), else null
+  unsigned long long* trace;  // optional item timeline of the first H^-1 application of each
+                              // launch (profile mode): [sweep][item][start ns, end ns, CTA]
 };
 
 constexpr int kMaxRhs = 8;                // right-hand sides per solve-kernel launch

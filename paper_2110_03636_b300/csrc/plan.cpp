@@ -379,7 +379,6 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
     const int64_t ie = P.pc_inv[P.sn_piece[s1] + 1] - P.pc_inv[P.sn_piece[s0]];
     if (pe > ent || ie > packed_inv_size(solve_w) || P.sn_piece[s1] - P.sn_piece[s0] != s1 - s0) return 2;
   }
-  P.pc_zoff.resize(P.npieces);
   P.pc_nchunk.resize(P.npieces);
   P.pc_rc0.resize(P.npieces);
   P.pc_need.assign(P.npieces, 0);
@@ -400,7 +399,6 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
       P.pc_rc0[p] = 0;
       P.hd_tptr.push_back((int64_t)P.hd_tgt.size());
       P.pc_nchunk[p] = 0;
-      P.pc_zoff[p] = P.z_total;
       continue;
     }
     const bool tma = pw >= kTmaMinWidth;
@@ -415,8 +413,6 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
     const int32_t rest = below - r0n;
     const int32_t nch = (int32_t)cdiv(rest, rc);
     P.pc_nchunk[p] = nch;
-    P.pc_zoff[p] = P.z_total;
-    P.z_total += (int64_t)nch * pw;
     for (int32_t k = 0; k < nch; k++) {
       const int32_t r0 = pw + r0n + k * rc;
       const int32_t nr = std::min(rc, P.pc_nr[p] - r0);
@@ -440,7 +436,6 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
     d.f = P.pc_first[p]; d.ld = P.pc_ld[p]; d.c = P.pc_c[p]; d.k = P.ch_k[c];
     d.colbase = P.pc_colbase[p]; d.rowbase = P.pc_row[p] + d.r0;
     d.tp0 = P.ch_tptr[c]; d.tp1 = P.ch_tptr[c + 1];
-    d.zoff = P.pc_zoff[p] + (int64_t)d.k * d.pw;
     d.tma = P.pc_box[p] > 0 ? 1 : 0;
     d.cs = d.tma ? P.pc_box[p] : ((d.nr + 3) & ~3) + 8;
   }
@@ -454,7 +449,6 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
     d.colbase = P.pc_colbase[p]; d.rowbase = P.pc_row[p];
     d.inv0 = P.pc_inv[p]; d.inv1 = P.pc_inv[p + 1];
     d.tp0 = P.hd_tptr[p]; d.tp1 = P.hd_tptr[p + 1];
-    d.zoff = P.pc_zoff[p];
   }
   for (int64_t t = 0; t < P.nsub; t++) {
     P.st_tptr.push_back((int64_t)P.st_tgt.size());
@@ -469,8 +463,11 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
     for (int32_t q : tg) { P.st_tgt.push_back(q); P.pc_need[q]++; }
   }
   P.st_tptr.push_back((int64_t)P.st_tgt.size());
-  // dispatch order: by depth in the dependency DAG, so that items whose inputs
-  // are ready are handed out first
+  // dispatch order: by the longest dependency chain that still follows an
+  // item (most first), ties by depth from the sweep's start. Every item then
+  // comes after all of its inputs (the order is topological, so CTAs that
+  // hold items waiting on inputs never hold up the items those inputs need),
+  // and the items of the critical path are handed out as early as possible.
   {
     std::vector<int64_t> chunk_first(P.npieces + 1, 0);
     for (int64_t c = 0; c < P.nchunks; c++) chunk_first[P.ch_piece[c] + 1]++;
@@ -493,16 +490,38 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
         }
       }
     }
-    std::vector<std::pair<int64_t, int32_t>> ord;
-    for (int64_t t = 0; t < P.nsub; t++) ord.push_back({0, (int32_t)(-1 - P.npieces - t)});
+    // forward chains still to come: pieces in reverse topological order
+    std::vector<int64_t> rh(P.npieces, 0), rc(P.nchunks, 0);
+    for (int64_t p = P.npieces - 1; p >= 0; p--) {
+      if (piece_sub[p] >= 0) continue;
+      int64_t r = 0;
+      for (int64_t t = P.hd_tptr[p]; t < P.hd_tptr[p + 1]; t++) r = std::max(r, rh[P.hd_tgt[t]] + 1);
+      for (int64_t c = chunk_first[p]; c < chunk_first[p + 1]; c++) {
+        int64_t q = 0;
+        for (int64_t t = P.ch_tptr[c]; t < P.ch_tptr[c + 1]; t++) q = std::max(q, rh[P.ch_tgt[t]] + 1);
+        rc[c] = q;
+        r = std::max(r, q + 1);
+      }
+      rh[p] = r;
+    }
+    // (key: longest chain after the item, descending; then depth, ascending)
+    std::vector<std::array<int64_t, 3>> ord;
+    for (int64_t t = 0; t < P.nsub; t++) {
+      int64_t r = 0;
+      for (int64_t q = P.st_tptr[t]; q < P.st_tptr[t + 1]; q++) r = std::max(r, rh[P.st_tgt[q]] + 1);
+      ord.push_back({-r, 0, -1 - P.npieces - t});
+    }
     for (int64_t p = 0; p < P.npieces; p++) {
       if (piece_sub[p] >= 0) continue;
-      ord.push_back({hd[p] * 2, (int32_t)(-1 - p)});
+      ord.push_back({-rh[p], hd[p] * 2, -1 - p});
       P.fwd_depth = std::max(P.fwd_depth, hd[p]);
     }
-    for (int64_t c = 0; c < P.nchunks; c++) ord.push_back({cd[c] * 2 + 1, (int32_t)c});
-    std::stable_sort(ord.begin(), ord.end(), [](auto& a, auto& b) { return a.first < b.first; });
-    for (auto& o : ord) P.fwd_items.push_back(o.second);
+    for (int64_t c = 0; c < P.nchunks; c++) ord.push_back({-rc[c], cd[c] * 2 + 1, c});
+    auto by_key = [](const std::array<int64_t, 3>& a, const std::array<int64_t, 3>& b) {
+      return a[0] != b[0] ? a[0] < b[0] : a[1] < b[1];
+    };
+    std::stable_sort(ord.begin(), ord.end(), by_key);
+    for (auto& o : ord) P.fwd_items.push_back((int32_t)o[2]);
     // backward: chunk after the heads of its targets; head after its chunks and
     // after the heads of its chunk-0 targets
     std::vector<int64_t> bh(P.npieces, 0), bc(P.nchunks, 0);
@@ -519,18 +538,32 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
       bh[p] = d;
       P.bwd_depth = std::max(P.bwd_depth, d);
     }
+    // backward chains still to come: subtrees and lower pieces are the
+    // later items, so pieces ascending give each head's final value before
+    // it is passed on to its inputs (its chunks and chunk-0 targets)
+    std::vector<int64_t> gh(P.npieces, 0), gc(P.nchunks, 0);
+    for (int64_t t = 0; t < P.nsub; t++)
+      for (int64_t q = P.st_tptr[t]; q < P.st_tptr[t + 1]; q++) gh[P.st_tgt[q]] = std::max<int64_t>(gh[P.st_tgt[q]], 1);
+    for (int64_t p = 0; p < P.npieces; p++) {
+      if (piece_sub[p] >= 0) continue;
+      for (int64_t t = P.hd_tptr[p]; t < P.hd_tptr[p + 1]; t++) gh[P.hd_tgt[t]] = std::max(gh[P.hd_tgt[t]], gh[p] + 1);
+      for (int64_t c = chunk_first[p]; c < chunk_first[p + 1]; c++) {
+        gc[c] = gh[p] + 1;
+        for (int64_t t = P.ch_tptr[c]; t < P.ch_tptr[c + 1]; t++) gh[P.ch_tgt[t]] = std::max(gh[P.ch_tgt[t]], gc[c] + 1);
+      }
+    }
     ord.clear();
     for (int64_t p = 0; p < P.npieces; p++)
-      if (piece_sub[p] < 0) ord.push_back({bh[p] * 2 + 1, (int32_t)(-1 - p)});
-    for (int64_t c = 0; c < P.nchunks; c++) ord.push_back({bc[c] * 2, (int32_t)c});
+      if (piece_sub[p] < 0) ord.push_back({-gh[p], bh[p] * 2 + 1, -1 - p});
+    for (int64_t c = 0; c < P.nchunks; c++) ord.push_back({-gc[c], bc[c] * 2, c});
     for (int64_t t = 0; t < P.nsub; t++) {
       int64_t d = 0;
       for (int64_t q = P.st_tptr[t]; q < P.st_tptr[t + 1]; q++) d = std::max(d, bh[P.st_tgt[q]] + 1);
-      ord.push_back({d * 2, (int32_t)(-1 - P.npieces - t)});
+      ord.push_back({0, d * 2, -1 - P.npieces - t});
       P.bwd_depth = std::max(P.bwd_depth, d);
     }
-    std::stable_sort(ord.begin(), ord.end(), [](auto& a, auto& b) { return a.first < b.first; });
-    for (auto& o : ord) P.bwd_items.push_back(o.second);
+    std::stable_sort(ord.begin(), ord.end(), by_key);
+    for (auto& o : ord) P.bwd_items.push_back((int32_t)o[2]);
   }
   return 0;
 }

@@ -16,7 +16,6 @@ struct alignas(16) ChunkDesc {
   int32_t f, ld, c, k;          // piece's first column, panel ld, column offset in the supernode, chunk index
   int64_t colbase, rowbase;     // piece's first L entry; sn_rows index of the chunk's first row
   int64_t tp0, tp1;             // target pieces [tp0, tp1) in ch_tgt
-  int64_t zoff;                 // backward partial sums of this chunk
   int32_t cs, tma;              // tile column stride in shared memory; 1 = one 2-D TMA box (else per column)
 };
 struct alignas(16) HeadDesc {
@@ -26,7 +25,6 @@ struct alignas(16) HeadDesc {
   int64_t colbase, rowbase;     // first L entry; sn_rows index of the piece's first row
   int64_t inv0, inv1;           // packed inverse [inv0, inv1) in Linv
   int64_t tp0, tp1;             // chunk-0 target pieces [tp0, tp1) in hd_tgt
-  int64_t zoff;                 // backward partial sums of the piece's chunks
   int32_t tma, pad;             // 1 = chunk 0 is one 2-D TMA box
 };
 
@@ -106,7 +104,6 @@ struct Plan {
   std::vector<int64_t> pc_row;              // offset in sn_rows of the piece's first row
   std::vector<int64_t> pc_colbase;          // panel offset of (supernode row 0, piece column 0)
   std::vector<int64_t> pc_inv;              // offset of the packed inverse of its triangle
-  std::vector<int64_t> pc_zoff;             // offset of its partial-sum slots
   std::vector<int32_t> pc_nchunk;           // separate chunks
   std::vector<int32_t> pc_need;             // heads + chunks whose rows hit the piece (forward)
   std::vector<int64_t> hd_tptr;             // targets of each head's chunk 0
@@ -133,7 +130,6 @@ struct Plan {
                                             // -1-npieces-t subtree t
   int64_t inv_total = 0;
   int64_t fwd_depth = 0, bwd_depth = 0;     // longest dependency chains of the sweeps
-  int64_t z_total = 0;
   int32_t max_pw = 0;
 };
 

@@ -15,7 +15,11 @@
 // solves are dependency-driven sweeps over "pieces" (column ranges of at most
 // solve_w columns of one supernode) and "chunks" (row ranges of a piece's
 // off-diagonal block), handed out in a fixed topological order through an
-// atomic ticket. Every wait is bounded (DevStatus::abort on timeout).
+// atomic ticket. Every wait is bounded (DevStatus::abort on timeout). In the
+// forward sweep a chunk subtracts L21 y from the vector at its rows; in the
+// backward sweep it subtracts L21^T x from the vector at its piece's columns
+// (atomic adds in both, so the head of a piece finds its right-hand side
+// complete once the arrival count says so).
 // Signalling: a CTA barrier, then thread 0 alone publishes with a release
 // store or a fence + atomic (the fence is cumulative over the writes the
 // barrier ordered before it; measured cheaper than release reductions); a
@@ -45,7 +49,7 @@ struct SolveSmemHdr {
   long long c_disp, c_dep, c_mbar, c_item, c_bar, n_items;
   long long c_kind[3], n_kind[3];   // whole-item cycles and counts: subtrees, heads, chunks
   long long c_lvl, n_lvl;           // subtree items: cycles in the level loops, levels
-  long long c_ph[8], t_mark;        // phases of forward subtree and chunk items (thread 0)
+  long long c_ph[16], t_mark;       // phases of forward subtree and chunk items, backward heads (thread 0)
   double dred[(kSolveThreads / 32) * 2];
   double bcast[2];
 };
@@ -182,6 +186,36 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
+// Sums eight per-lane values over the warp at once: each halving step trades
+// half of a lane's columns with the partner lane, so the eight totals take
+// 4 + 2 + 1 + 1 + 1 shuffles instead of 8 x 5. On return lanes 4c..4c+3
+// hold the total of column c in v[0].
+template <typename T>
+__device__ __forceinline__ T warp_sum8(T (&v)[8]) {
+  const int lane = threadIdx.x & 31;
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+#pragma unroll
+  for (int j = 0; j < 4; j++) {
+    const T send = b4 ? v[j] : v[j + 4];
+    const T keep = b4 ? v[j + 4] : v[j];
+    v[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int j = 0; j < 2; j++) {
+    const T send = b3 ? v[j] : v[j + 2];
+    const T keep = b3 ? v[j + 2] : v[j];
+    v[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  {
+    const T send = b2 ? v[0] : v[1];
+    const T keep = b2 ? v[1] : v[0];
+    v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+  return v[0];
+}
+
 // thread 0: charge the cycles since the last mark to phase i (profile runs)
 template <typename T>
 __device__ __forceinline__ void mark(const SolveArgs<T>& a, SolveSmemHdr& h, int i) {
@@ -193,6 +227,11 @@ __device__ __forceinline__ void mark(const SolveArgs<T>& a, SolveSmemHdr& h, int
 }
 
 // ------------------------------------------------------- TMA bulk copies
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 __device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(unsigned long long* m) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(m)) : "memory");
@@ -490,7 +529,7 @@ __device__ bool bwd_chunk(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>
       for (int j = 0; j < kMaxRhs; j++)
         if (j < R) {
           const T sj = warp_sum(acc[j]);
-          if (lane == 0) a.zpart[(int64_t)j * a.z_total + d.zoff + k] = sj;
+          if (lane == 0) atomicAdd(&a.v[(int64_t)j * a.n + d.f + k], -sj);
         }
     }
     __syncthreads();
@@ -507,12 +546,20 @@ __device__ bool bwd_chunk(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>
       gather(a.v + (int64_t)j * a.n);
       __syncthreads();
     }
-    T* z = a.zpart + (int64_t)j * a.z_total + d.zoff;
-    for (int k = warp; k < pw; k += nw) {
-      T s = T(0);
-      for (int i = lane; i < nr; i += 32) s += t.B[k * cs + d0 + i] * t.aux[i];
-      s = warp_sum(s);
-      if (lane == 0) z[k] = s;
+    T* vj = a.v + (int64_t)j * a.n + d.f;
+    for (int k0 = 8 * warp; k0 < pw; k0 += 8 * nw) {
+      T acc[8];
+#pragma unroll
+      for (int q = 0; q < 8; q++) acc[q] = T(0);
+      for (int i = lane; i < nr; i += 32) {
+        const T xv = t.aux[i];
+#pragma unroll
+        for (int q = 0; q < 8; q++)
+          if (k0 + q < pw) acc[q] += t.B[(k0 + q) * cs + d0 + i] * xv;
+      }
+      const T sum = warp_sum8(acc);
+      const int k = k0 + (lane >> 2);
+      if ((lane & 3) == 0 && k < pw) atomicAdd(&vj[k], -sum);
     }
     __syncthreads();
   }
@@ -526,6 +573,7 @@ __device__ bool bwd_chunk(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>
 template <typename T>
 __device__ bool bwd_head(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>& t, int p, int e) {
   const int tid = threadIdx.x;
+  mark(a, h, -1);
   const HeadDesc d = a.hdesc[p];
   const int pw = d.pw, f = d.f, rn = d.rn, nch = d.nch;
   const int32_t* rows = a.sn_rows + d.rowbase + pw;
@@ -539,6 +587,7 @@ __device__ bool bwd_head(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>&
     __syncwarp();
     if (tid == 0) bulk_g2s(t.A, a.Linv + d.inv0, binv, &h.mbar);
     if (rn > 0) stage_tile(a, p, d.colbase, d.ld, d.c, pw, pw, rn, d.cs, d.tma, t.B, b1, &h.mbar, true);
+    mark(a, h, 8);
     if (tid == 0) {
       const long long t0 = clock64();
       int ok = wait_geq(&a.bwd_arrive[p], e * nch, a.st, a.spin);
@@ -546,10 +595,12 @@ __device__ bool bwd_head(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>&
       h.flag = ok;
       h.c_dep += clock64() - t0;
     }
+    mark(a, h, 9);
   }
   __syncthreads();
   const bool dep = h.flag != 0;
-  // t = v[cols] - (the chunks' partial sums), and v at the chunk-0 rows
+  // t = v[cols] (the piece's chunks have already subtracted their products
+  // from it) and v at the chunk-0 rows
   auto gather = [&](int j) {
     const T* vj = a.v + (int64_t)j * a.n;
     if (rn <= (int)blockDim.x) {
@@ -557,46 +608,65 @@ __device__ bool bwd_head(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>&
     } else {
       for (int i = tid; i < rn; i += blockDim.x) t.aux[i] = ldcg(&vj[rows[i]]);
     }
-    const T* z = a.zpart + (int64_t)j * a.z_total + d.zoff;
-    for (int i = tid; i < pw; i += blockDim.x) {
-      T v = ldcg(&vj[f + i]);
-      for (int k = 0; k < nch; k++) v -= ldcg(&z[(int64_t)k * pw + i]);
-      t.vec[i] = v;
-    }
+    for (int i = tid; i < pw; i += blockDim.x) t.vec[i] = ldcg(&vj[f + i]);
   };
   if (dep) gather(0);
   if (!mbar_wait(a, h) || !dep) return false;
+  mark(a, h, 10);
   const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   for (int j = 0; j < a.nrhs; j++) {
     if (j > 0) {
       gather(j);
       __syncthreads();
     }
+    // each warp takes eight columns at a time and sums them together
     if (rn > 0) {
       const int d0 = (d.c + pw) & 3;
       const int cs = d.cs;
-      for (int k = warp; k < pw; k += nw) {
-        T s = T(0);
-        for (int i = lane; i < rn; i += 32) s += t.B[k * cs + d0 + i] * t.aux[i];
-        s = warp_sum(s);
-        if (lane == 0) t.vec[k] -= s;
+      for (int k0 = 8 * warp; k0 < pw; k0 += 8 * nw) {
+        T acc[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) acc[q] = T(0);
+        for (int i = lane; i < rn; i += 32) {
+          const T xv = t.aux[i];
+#pragma unroll
+          for (int q = 0; q < 8; q++)
+            if (k0 + q < pw) acc[q] += t.B[(k0 + q) * cs + d0 + i] * xv;
+        }
+        const T sum = warp_sum8(acc);
+        const int k = k0 + (lane >> 2);
+        if ((lane & 3) == 0 && k < pw) t.vec[k] -= sum;
       }
       __syncthreads();
     }
+    mark(a, h, 11);
     // x = T^-T t: x_k = sum_{i >= k} Tinv[i, k] t_i (packed columns)
-    for (int k = warp; k < pw; k += nw) {
-      const int off = packed_off(pw, k);
-      T s = T(0);
-      for (int i = k + lane; i < pw; i += 32) s += t.A[off + i - k] * t.vec[i];
-      s = warp_sum(s);
-      if (lane == 0) t.vec2[k] = s;
+    for (int k0 = 8 * warp; k0 < pw; k0 += 8 * nw) {
+      T acc[8];
+      int off[8];
+#pragma unroll
+      for (int q = 0; q < 8; q++) {
+        acc[q] = T(0);
+        off[q] = packed_off(pw, min(k0 + q, pw - 1)) - (k0 + q);
+      }
+      for (int i = k0 + lane; i < pw; i += 32) {
+        const T tv = t.vec[i];
+#pragma unroll
+        for (int q = 0; q < 8; q++)
+          if (i >= k0 + q) acc[q] += t.A[off[q] + i] * tv;
+      }
+      const T sum = warp_sum8(acc);
+      const int k = k0 + (lane >> 2);
+      if ((lane & 3) == 0 && k < pw) t.vec2[k] = sum;
     }
     __syncthreads();
+    mark(a, h, 12);
     T* vj = a.v + (int64_t)j * a.n;
     for (int i = tid; i < pw; i += blockDim.x) vj[f + i] = t.vec2[i];
     __syncthreads();
   }
   if (tid == 0) st_release(&a.bwd_done[p], e);
+  mark(a, h, 13);
   return true;
 }
 
@@ -881,10 +951,12 @@ __device__ bool sweep(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>& t,
     __syncthreads();
     const int it = h.item;
     __syncthreads();
+    unsigned long long tg0 = 0;
     if (threadIdx.x == 0) {
       const long long now = clock64();
       h.c_disp += now - td;
       td = now;
+      if (a.trace) tg0 = globaltimer();
     }
     if (it >= a.nitems) return true;
     const int code = items[it];
@@ -899,6 +971,12 @@ __device__ bool sweep(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>& t,
       ok = code < 0 ? bwd_head(a, h, t, -1 - code, e) : bwd_chunk(a, h, t, code, e);
     }
     if (threadIdx.x == 0) {
+      if (a.trace && seq < 2) {
+        unsigned long long* q = a.trace + 3 * ((int64_t)seq * a.nitems + it);
+        q[0] = tg0;
+        q[1] = globaltimer();
+        q[2] = blockIdx.x;
+      }
       const long long dt = clock64() - td;
       h.c_item += dt;
       h.n_items++;
@@ -926,7 +1004,7 @@ __device__ void flush_counters(const SolveArgs<T>& a, SolveSmemHdr& h) {
     }
     atomicAdd(&a.instr[13], (unsigned long long)h.c_lvl);
     atomicAdd(&a.instr[14], (unsigned long long)h.n_lvl);
-    for (int k = 0; k < 8; k++) atomicAdd(&a.instr[16 + k], (unsigned long long)h.c_ph[k]);
+    for (int k = 0; k < 14; k++) atomicAdd(&a.instr[16 + k], (unsigned long long)h.c_ph[k]);
   }
 }
 
@@ -962,7 +1040,7 @@ __global__ void __launch_bounds__(kSolveThreads, MB) k_cg(SolveArgs<T> a) {
     sm.c_disp = sm.c_dep = sm.c_mbar = sm.c_item = sm.c_bar = sm.n_items = 0;
     for (int k = 0; k < 3; k++) sm.c_kind[k] = sm.n_kind[k] = 0;
     sm.c_lvl = sm.n_lvl = 0;
-    for (int k = 0; k < 8; k++) sm.c_ph[k] = 0;
+    for (int k = 0; k < 16; k++) sm.c_ph[k] = 0;
     sm.t_mark = 0;
   }
   __syncthreads();
