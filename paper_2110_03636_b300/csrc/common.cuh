@@ -49,4 +49,31 @@ __device__ __forceinline__ bool wait_geq(const int* flag, int target, DevStatus*
   }
 }
 
+// Wait (all 32 lanes of one warp) until flags[tg[q]] >= target for every q
+// in [q0, q1): the lanes poll different flags at once, so a list of k
+// satisfied flags costs one round trip per 32 instead of k. Flags only grow
+// within a sweep, so a lane moves on as soon as its current flag is met.
+// Returns false (in every lane) when the wait gave up or the abort word is set.
+__device__ __forceinline__ bool warp_wait_all(const int* flags, const int32_t* tg, int64_t q0, int64_t q1,
+                                              int target, DevStatus* st, long long limit = kSpinCycles) {
+  bool ok = true;
+  const long long t0 = clock64();
+  int spins = 0;
+  for (int64_t q = q0 + (threadIdx.x & 31); q < q1;) {
+    if (ld_acquire(&flags[__ldg(&tg[q])]) >= target) {
+      q += 32;
+      continue;
+    }
+    if ((++spins & 15) == 0) {
+      if (ld_acquire(&st->abort)) { ok = false; break; }
+      if (clock64() - t0 > limit) {
+        atomicExch(&st->abort, 1);
+        ok = false;
+        break;
+      }
+    }
+  }
+  return __all_sync(0xffffffffu, ok);
+}
+
 }  // namespace kkt

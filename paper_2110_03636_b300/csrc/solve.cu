@@ -319,6 +319,34 @@ __device__ int stage_tile(const SolveArgs<T>& a, int p, int64_t colbase, int ld,
   return R0 - A0;
 }
 
+// Publish (the 32 lanes of one warp, after a CTA barrier that follows the
+// CTA's writes): one arrival on counters[tg[q]] for every q in [q0, q1). Each
+// lane fences before its increments, and the fence is cumulative over the
+// writes the barrier ordered before it; the lanes spread the index loads and
+// increments of a long target list.
+__device__ __forceinline__ void signal_all(int* counters, const int32_t* tg, int64_t q0, int64_t q1) {
+  __threadfence();
+  for (int64_t q = q0 + (threadIdx.x & 31); q < q1; q += 32) atomicAdd(&counters[__ldg(&tg[q])], 1);
+}
+
+// out[i] = v[rows[i]] for i < nr <= 4 * blockDim: every row index is loaded
+// before any value, so the block waits two memory round trips, not 2 per
+// blockDim rows.
+template <typename T>
+__device__ __forceinline__ void gather_rows(const T* v, const int32_t* rows, int nr, T* out) {
+  const int tid = threadIdx.x, bd = blockDim.x;
+  int r[4];
+#pragma unroll
+  for (int u = 0; u < 4; u++) r[u] = tid + u * bd < nr ? __ldg(&rows[tid + u * bd]) : -1;
+  T x[4];
+#pragma unroll
+  for (int u = 0; u < 4; u++) x[u] = r[u] >= 0 ? ldcg(&v[r[u]]) : T(0);
+#pragma unroll
+  for (int u = 0; u < 4; u++)
+    if (r[u] >= 0) out[tid + u * bd] = x[u];
+  for (int i = tid + 4 * bd; i < nr; i += bd) out[i] = ldcg(&v[rows[i]]);
+}
+
 // The sn_rows entry of row i of an item (i < nr), fetched before the item
 // waits on its inputs when the item has at most one row per thread.
 __device__ __forceinline__ int prefetch_row(const int32_t* rows, int nr) {
@@ -392,10 +420,7 @@ __device__ bool fwd_head(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>&
       });
       __syncthreads();
     }
-    if (tid == 0) {
-      __threadfence();
-      for (int64_t q = d.tp0; q < d.tp1; q++) atomicAdd(&a.fwd_arrive[a.hd_tgt[q]], 1);
-    }
+    if (tid < 32) signal_all(a.fwd_arrive, a.hd_tgt, d.tp0, d.tp1);
   }
   return true;
 }
@@ -439,10 +464,7 @@ __device__ bool fwd_chunk(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>
       atomicAdd(&a.v[(int64_t)j * a.n + (nr <= (int)blockDim.x ? myrow : rows[i])], -o);
     });
     __syncthreads();
-    if (tid == 0) {
-      __threadfence();
-      for (int64_t q = d.tp0; q < d.tp1; q++) atomicAdd(&a.fwd_arrive[a.ch_tgt[q]], 1);
-    }
+    if (tid < 32) signal_all(a.fwd_arrive, a.ch_tgt, d.tp0, d.tp1);
     return true;
   }
   if (dep)
@@ -462,10 +484,7 @@ __device__ bool fwd_chunk(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>
     __syncthreads();
   }
   mark(a, h, 6);
-  if (tid == 0) {
-    __threadfence();
-    for (int64_t q = d.tp0; q < d.tp1; q++) atomicAdd(&a.fwd_arrive[a.ch_tgt[q]], 1);
-  }
+  if (tid < 32) signal_all(a.fwd_arrive, a.ch_tgt, d.tp0, d.tp1);
   mark(a, h, 7);
   return true;
 }
@@ -485,11 +504,10 @@ __device__ bool bwd_chunk(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>
     if (tid == 0) mbar_expect_tx(&h.mbar, b);
     __syncwarp();
     stage_tile(a, p, d.colbase, d.ld, d.c, pw, d.r0, nr, d.cs, d.tma, t.B, b, &h.mbar, true);
+    const long long t0 = clock64();
+    const bool ok = warp_wait_all(a.bwd_done, a.ch_tgt, d.tp0, d.tp1, e, a.st, a.spin);
     if (tid == 0) {
-      const long long t0 = clock64();
-      int ok = 1;
-      for (int64_t q = d.tp0; q < d.tp1 && ok; q++) ok = wait_geq(&a.bwd_done[a.ch_tgt[q]], e, a.st, a.spin);
-      h.flag = ok;
+      h.flag = ok ? 1 : 0;
       h.c_dep += clock64() - t0;
     }
   }
@@ -499,7 +517,7 @@ __device__ bool bwd_chunk(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>
     if (nr <= (int)blockDim.x) {
       if (tid < nr) t.aux[tid] = ldcg(&vj[myrow]);
     } else {
-      for (int i = tid; i < nr; i += blockDim.x) t.aux[i] = ldcg(&vj[rows[i]]);
+      gather_rows(vj, rows, nr, t.aux);
     }
   };
   const int R = a.nrhs;
@@ -588,11 +606,11 @@ __device__ bool bwd_head(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>&
     if (tid == 0) bulk_g2s(t.A, a.Linv + d.inv0, binv, &h.mbar);
     if (rn > 0) stage_tile(a, p, d.colbase, d.ld, d.c, pw, pw, rn, d.cs, d.tma, t.B, b1, &h.mbar, true);
     mark(a, h, 8);
+    const long long t0 = clock64();
+    bool ok = warp_wait_all(a.bwd_done, a.hd_tgt, d.tp0, d.tp1, e, a.st, a.spin);
     if (tid == 0) {
-      const long long t0 = clock64();
-      int ok = wait_geq(&a.bwd_arrive[p], e * nch, a.st, a.spin);
-      for (int64_t q = d.tp0; q < d.tp1 && ok; q++) ok = wait_geq(&a.bwd_done[a.hd_tgt[q]], e, a.st, a.spin);
-      h.flag = ok;
+      ok = ok && wait_geq(&a.bwd_arrive[p], e * nch, a.st, a.spin);
+      h.flag = ok ? 1 : 0;
       h.c_dep += clock64() - t0;
     }
     mark(a, h, 9);
@@ -606,7 +624,7 @@ __device__ bool bwd_head(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>&
     if (rn <= (int)blockDim.x) {
       if (tid < rn) t.aux[tid] = ldcg(&vj[myrow]);
     } else {
-      for (int i = tid; i < rn; i += blockDim.x) t.aux[i] = ldcg(&vj[rows[i]]);
+      gather_rows(vj, rows, rn, t.aux);
     }
     for (int i = tid; i < pw; i += blockDim.x) t.vec[i] = ldcg(&vj[f + i]);
   };
@@ -706,19 +724,19 @@ __device__ void warp_fwd_supernode(const SolveArgs<T>& a, const Tiles<T>& t, int
   const T* P = t.B + (__ldg(&a.poff[s]) - pbase);
   const T* Inv = t.A + (__ldg(&a.pc_inv[__ldg(&a.sn_piece[s])]) - ibase);
   const int32_t* rows = a.sn_rows + __ldg(&a.srow[s]);
-  T y[4];
+  // lane owns rows lane + 32c; the k loop runs once for all four of them
+  T y[4] = {T(0), T(0), T(0), T(0)};
+  {
+    int off = 0;
+    for (int k = 0; k < w; k++) {
+      const T xk = xs[f + k];
 #pragma unroll
-  for (int c = 0; c < 4; c++) {
-    const int i = lane + 32 * c;
-    T acc = T(0);
-    if (i < w) {
-      int off = 0;
-      for (int k = 0; k <= i; k++) {
-        acc += Inv[off + i - k] * xs[f + k];
-        off += (w - k + 3) & ~3;
+      for (int c = 0; c < 4; c++) {
+        const int i = lane + 32 * c;
+        if (i >= k && i < w) y[c] += Inv[off + i - k] * xk;
       }
+      off += (w - k + 3) & ~3;
     }
-    y[c] = acc;
   }
   __syncwarp();
 #pragma unroll
@@ -767,8 +785,11 @@ __device__ void warp_bwd_supernode(const SolveArgs<T>& a, const Tiles<T>& t, int
     xr[r] = row < chi ? xs[row - clo] : ldcg(&vj[row]);
   }
   __syncwarp();
-  for (int k = 0; k < w; k++) {
-    T acc = T(0);
+  // eight columns at a time: a row past the cache is fetched once per eight
+  for (int k0 = 0; k0 < w; k0 += 8) {
+    T acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; q++) acc[q] = T(0);
     for (int r = lane; r < nb; r += 32) {
       T x;
       if (r < cache) {
@@ -777,19 +798,33 @@ __device__ void warp_bwd_supernode(const SolveArgs<T>& a, const Tiles<T>& t, int
         const int row = __ldg(&rows[w + r]);
         x = row < chi ? xs[row - clo] : ldcg(&vj[row]);
       }
-      acc += P[w + r + k * ld] * x;
+#pragma unroll
+      for (int q = 0; q < 8; q++)
+        if (k0 + q < w) acc[q] += P[w + r + (k0 + q) * ld] * x;
     }
-    acc = warp_sum(acc);
-    if (lane == 0) scratch[k] = xs[f + k] - acc;
+    const T sum = warp_sum8(acc);
+    const int k = k0 + (lane >> 2);
+    if ((lane & 3) == 0 && k < w) scratch[k] = xs[f + k] - sum;
   }
   __syncwarp();
-  int off = 0;
-  for (int k = 0; k < w; k++) {
-    T acc = T(0);
-    for (int i = k + lane; i < w; i += 32) acc += Inv[off + i - k] * scratch[i];
-    acc = warp_sum(acc);
-    if (lane == 0) xs[f + k] = acc;
-    off += (w - k + 3) & ~3;
+  // x = T^-T t (packed columns: column k holds rows k..w-1)
+  for (int k0 = 0; k0 < w; k0 += 8) {
+    T acc[8];
+    int off[8];
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+      acc[q] = T(0);
+      off[q] = packed_off(w, min(k0 + q, w - 1)) - (k0 + q);
+    }
+    for (int i = k0 + lane; i < w; i += 32) {
+      const T tv = scratch[i];
+#pragma unroll
+      for (int q = 0; q < 8; q++)
+        if (i >= k0 + q) acc[q] += Inv[off[q] + i] * tv;
+    }
+    const T sum = warp_sum8(acc);
+    const int k = k0 + (lane >> 2);
+    if ((lane & 3) == 0 && k < w) xs[f + k] = sum;
   }
   __syncwarp();
 }
@@ -828,10 +863,7 @@ __device__ bool fwd_subtree(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<
     h.n_lvl += a.st_lptr[st + 1] - a.st_lptr[st] - 1;
   }
   mark(a, h, 1);
-  if (tid == 0) {
-    __threadfence();
-    for (int64_t q = a.st_tptr[st]; q < a.st_tptr[st + 1]; q++) atomicAdd(&a.fwd_arrive[a.st_tgt[q]], 1);
-  }
+  if (tid < 32) signal_all(a.fwd_arrive, a.st_tgt, a.st_tptr[st], a.st_tptr[st + 1]);
   mark(a, h, 2);
   return true;
 }
@@ -842,13 +874,13 @@ __device__ bool bwd_subtree(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<
   const int clo = a.st_clo[st], chi = a.st_chi[st];
   int64_t pbase, ibase;
   stage_subtree(a, h, t, st, pbase, ibase);
-  if (tid == 0) {
+  if (tid < 32) {
     const long long t0 = clock64();
-    int ok = 1;
-    for (int64_t q = a.st_tptr[st]; q < a.st_tptr[st + 1] && ok; q++)
-      ok = wait_geq(&a.bwd_done[a.st_tgt[q]], e, a.st, a.spin);
-    h.flag = ok;
-    h.c_dep += clock64() - t0;
+    const bool ok = warp_wait_all(a.bwd_done, a.st_tgt, a.st_tptr[st], a.st_tptr[st + 1], e, a.st, a.spin);
+    if (tid == 0) {
+      h.flag = ok ? 1 : 0;
+      h.c_dep += clock64() - t0;
+    }
   }
   __syncthreads();
   const bool dep = h.flag != 0;
