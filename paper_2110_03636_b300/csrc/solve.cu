@@ -382,20 +382,32 @@ __device__ bool fwd_head(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>&
     for (int i = tid; i < pw; i += blockDim.x) t.vec[i] = ldcg(&a.v[f + i]);
   if (!mbar_wait(a, h) || !dep) return false;
   // y = T^-1 b with the packed inverse (column k holds rows k..pw-1); the
-  // k range of each row is split among G thread groups
+  // k range of each row is split into G contiguous parts, one per thread
+  // group, walked with a running column offset and two partial sums
   const int pr = (pw + 31) & ~31;
   const int G = max(1, (int)blockDim.x / pr);
   const int gi = tid % pr, gg0 = tid / pr;
+  const int kspan = (pw + G - 1) / G;
+  const int kb = gg0 * kspan, ke = min(gi + 1, kb + kspan);
+  const int off0 = gg0 < G && kb < pw ? packed_off(pw, kb) : 0;
   for (int j = 0; j < a.nrhs; j++) {
     T* vj = a.v + (int64_t)j * a.n;
     if (j > 0) {
       for (int i = tid; i < pw; i += blockDim.x) t.vec[i] = ldcg(&vj[f + i]);
       __syncthreads();
     }
-    T acc = T(0);
-    if (gg0 < G && gi < pw)
-      for (int k = gg0; k <= gi; k += G) acc += t.A[packed_off(pw, k) + gi - k] * t.vec[k];
-    t.aux[tid] = acc;
+    T acc = T(0), acc2 = T(0);
+    if (gg0 < G && gi < pw) {
+      int off = off0, k = kb;
+      for (; k + 1 < ke; k += 2) {
+        acc += t.A[off + gi - k] * t.vec[k];
+        off += (pw - k + 3) & ~3;
+        acc2 += t.A[off + gi - k - 1] * t.vec[k + 1];
+        off += (pw - k + 2) & ~3;
+      }
+      if (k < ke) acc += t.A[off + gi - k] * t.vec[k];
+    }
+    t.aux[tid] = acc + acc2;
     __syncthreads();
     if (tid < pw) {
       T y = T(0);
@@ -405,7 +417,10 @@ __device__ bool fwd_head(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>&
     }
     __syncthreads();
   }
-  if (tid == 0) st_release(&a.fwd_done[p], e);
+  // the piece's done flag (its chunks wait on it) goes out after chunk 0, so
+  // the fence of chunk 0's arrivals serves both and the next piece's head,
+  // usually on the critical path, does not wait for a second one
+  if (rn == 0 && tid == 0) st_release(&a.fwd_done[p], e);
   if (rn > 0) {
     // chunk 0: b[rows] -= L21(0:rn) y
     const int d0 = (d.c + pw) & 3;
@@ -420,7 +435,10 @@ __device__ bool fwd_head(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>&
       });
       __syncthreads();
     }
-    if (tid < 32) signal_all(a.fwd_arrive, a.hd_tgt, d.tp0, d.tp1);
+    if (tid < 32) {
+      signal_all(a.fwd_arrive, a.hd_tgt, d.tp0, d.tp1);
+      if (tid == 0) st_relaxed(&a.fwd_done[p], e);   // ordered by signal_all's fence
+    }
   }
   return true;
 }
