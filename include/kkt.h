@@ -295,12 +295,14 @@ kkt_status kkt_get_profile(kkt_handle h, double* ms, int64_t* launches, int32_t 
  * items, [4] grid barriers, [5] items processed, [6] CTA-launches,
  * [7]/[8] cycles/count of subtree items, [9]/[10] of piece heads,
  * [11]/[12] of row chunks, [13]/[14] cycles in / number of the level
- * loops of subtree items, [15] zero, [16..18] forward subtree items:
- * staging, levels, publishing; [19..23] forward chunks: metadata and copy
- * issue, dependency wait, vector load and copy wait, mat-vec, publishing;
- * [24..29] backward piece heads: metadata and copy issue, dependency wait,
- * vector loads and copy wait, chunk-0 product, inverse product, storing
- * and publishing; [30..31] zero. */
+ * loops of subtree items, [15] zero, [16..18] forward piece heads:
+ * metadata and copy issue, dependency wait, vector load and copy wait;
+ * [19..23] forward chunks: metadata and copy issue, dependency wait, vector
+ * load and copy wait, mat-vec, publishing; [24..29] backward piece heads:
+ * metadata and copy issue, dependency wait, vector loads and copy wait,
+ * chunk-0 product, inverse product, storing and publishing; [30..31]
+ * forward piece heads: inverse product and store, chunk-0 product and
+ * publishing. */
 kkt_status kkt_get_solve_counters(kkt_handle h, uint64_t* out, int32_t reset);
 
 /* Item timeline of the persistent solve kernel, for handles created with

@@ -273,8 +273,8 @@ def kkt_get_solve_counters(h, reset=False):
     keys = ("dispatch", "dep_wait", "copy_wait", "items", "barriers", "n_items", "cta_launches",
             "subtree_cycles", "n_subtree", "head_cycles", "n_head", "chunk_cycles", "n_chunk",
             "subtree_level_cycles", "n_subtree_levels", "zero15",
-            "fsub_stage", "fsub_levels", "fsub_publish", "fch_issue", "fch_dep", "fch_load", "fch_matvec", "fch_publish",
-            "bhd_issue", "bhd_dep", "bhd_load", "bhd_chunk0", "bhd_inverse", "bhd_publish")
+            "fhd_issue", "fhd_dep", "fhd_load", "fch_issue", "fch_dep", "fch_load", "fch_matvec", "fch_publish",
+            "bhd_issue", "bhd_dep", "bhd_load", "bhd_chunk0", "bhd_inverse", "bhd_publish", "fhd_inverse", "fhd_chunk0")
     return {k: int(out[i]) for i, k in enumerate(keys)}
 
 

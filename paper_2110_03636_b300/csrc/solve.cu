@@ -49,7 +49,7 @@ struct SolveSmemHdr {
   long long c_disp, c_dep, c_mbar, c_item, c_bar, n_items;
   long long c_kind[3], n_kind[3];   // whole-item cycles and counts: subtrees, heads, chunks
   long long c_lvl, n_lvl;           // subtree items: cycles in the level loops, levels
-  long long c_ph[16], t_mark;       // phases of forward subtree and chunk items, backward heads (thread 0)
+  long long c_ph[16], t_mark;       // phases of heads and forward chunks (thread 0)
   double dred[(kSolveThreads / 32) * 2];
   double bcast[2];
 };
@@ -357,6 +357,7 @@ __device__ __forceinline__ int prefetch_row(const int32_t* rows, int nr) {
 template <typename T>
 __device__ bool fwd_head(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>& t, int p, int e) {
   const int tid = threadIdx.x;
+  mark(a, h, -1);
   const HeadDesc d = a.hdesc[p];
   const int pw = d.pw, f = d.f, rn = d.rn;
   const int32_t* rows = a.sn_rows + d.rowbase + pw;
@@ -370,17 +371,20 @@ __device__ bool fwd_head(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>&
     __syncwarp();
     if (tid == 0) bulk_g2s(t.A, a.Linv + d.inv0, binv, &h.mbar);
     if (rn > 0) stage_tile(a, p, d.colbase, d.ld, d.c, pw, pw, rn, d.cs, d.tma, t.B, b1, &h.mbar, true);
+    mark(a, h, 0);
     if (tid == 0) {
       const long long t0 = clock64();
       h.flag = wait_geq(&a.fwd_arrive[p], e * d.need, a.st, a.spin);
       h.c_dep += clock64() - t0;
     }
+    mark(a, h, 1);
   }
   __syncthreads();
   const bool dep = h.flag != 0;
   if (dep)
     for (int i = tid; i < pw; i += blockDim.x) t.vec[i] = ldcg(&a.v[f + i]);
   if (!mbar_wait(a, h) || !dep) return false;
+  mark(a, h, 2);
   // y = T^-1 b with the packed inverse (column k holds rows k..pw-1); the
   // k range of each row is split into G contiguous parts, one per thread
   // group, walked with a running column offset and two partial sums
@@ -417,6 +421,7 @@ __device__ bool fwd_head(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>&
     }
     __syncthreads();
   }
+  mark(a, h, 14);
   // the piece's done flag (its chunks wait on it) goes out after chunk 0, so
   // the fence of chunk 0's arrivals serves both and the next piece's head,
   // usually on the critical path, does not wait for a second one
@@ -440,6 +445,7 @@ __device__ bool fwd_head(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>&
       if (tid == 0) st_relaxed(&a.fwd_done[p], e);   // ordered by signal_all's fence
     }
   }
+  mark(a, h, 15);
   return true;
 }
 
@@ -860,7 +866,6 @@ __device__ bool fwd_subtree(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<
   T* xs = t.vec2;
   for (int i = tid; i < chi - clo; i += blockDim.x) xs[i] = ldcg(&a.v[clo + i]);
   if (!mbar_wait(a, h)) return false;
-  mark(a, h, 0);
   const long long tl0 = clock64();
   for (int j = 0; j < a.nrhs; j++) {
     T* vj = a.v + (int64_t)j * a.n;
@@ -880,9 +885,7 @@ __device__ bool fwd_subtree(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<
     h.c_lvl += clock64() - tl0;
     h.n_lvl += a.st_lptr[st + 1] - a.st_lptr[st] - 1;
   }
-  mark(a, h, 1);
   if (tid < 32) signal_all(a.fwd_arrive, a.st_tgt, a.st_tptr[st], a.st_tptr[st + 1]);
-  mark(a, h, 2);
   return true;
 }
 
@@ -1054,7 +1057,7 @@ __device__ void flush_counters(const SolveArgs<T>& a, SolveSmemHdr& h) {
     }
     atomicAdd(&a.instr[13], (unsigned long long)h.c_lvl);
     atomicAdd(&a.instr[14], (unsigned long long)h.n_lvl);
-    for (int k = 0; k < 14; k++) atomicAdd(&a.instr[16 + k], (unsigned long long)h.c_ph[k]);
+    for (int k = 0; k < 16; k++) atomicAdd(&a.instr[16 + k], (unsigned long long)h.c_ph[k]);
   }
 }
 
