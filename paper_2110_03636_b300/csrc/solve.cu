@@ -285,7 +285,7 @@ __device__ bool mbar_wait(const SolveArgs<T>& a, SolveSmemHdr& h) {
       }
     }
   }
-  __syncthreads();
+  ok = __syncthreads_and(ok);   // every thread takes the same exit
   if (threadIdx.x == 0) {
     h.phase ^= 1u;
     h.c_mbar += clock64() - tw;
