@@ -35,7 +35,7 @@ WORKLOAD = "grid2d_n250k"
 # k_cg_grid2d_n250k_mixed_nd.md); a mixed-precision CG launch does
 # (iterations + 1) of them.
 # Valid only for the kernel source it was measured on.
-NCU_BYTES_PER_H_APPLICATION = {("grid2d_n250k", "mixed", "nd"): 2.4833e9 + 0.0143e9}
+NCU_BYTES_PER_H_APPLICATION = {("grid2d_n250k", "mixed", "nd"): 2.4732e9 + 0.0074e9}
 N_VALUE_SETS = 10
 RR_TARGET = 1e-8
 
