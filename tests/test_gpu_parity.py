@@ -504,3 +504,35 @@ def test_mixed_refinement_modes_match_oracle(name, refine):
     assert code == 0
     assert s.info.rr <= 1e-9 and s.inertia_ok
     assert rel(np.concatenate([dx, dy]), np.concatenate([odx, ody])) <= 1e-6
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_solve_trace_records_every_item(precision):
+    """A profile handle records the item timeline of one H^-1 application:
+    every item of both sweeps ran (dispatch and finish stamps set, finish
+    not before dispatch, a CTA index inside the grid), the backward sweep
+    starts after the forward one ends, and a handle without profiling
+    refuses the call."""
+    sys = W.make_config("grid2d_n2000")
+    s = K.KKTSolver(sys.n, sys.m, sys.H_colptr, sys.H_rowidx, sys.J_rowptr, sys.J_colidx,
+                    precision=precision, ordering="nd", profile=1)
+    try:
+        s.factor(cu(sys.H_vals), cu(sys.J_vals), sys.delta, sys.gamma)
+        s.solve(cu(sys.r_x), cu(sys.r_y))
+        torch.cuda.synchronize()
+        tr = s.solve_trace().astype(np.int64)
+        f, b = s.solve_item_order()
+        assert tr.shape == (2, len(f), 3)
+        start, end, cta = tr[..., 0], tr[..., 1], tr[..., 2]
+        assert (start > 0).all() and (end >= start).all()
+        assert (cta >= 0).all() and (cta < 148 * 4).all()
+        assert start[1].min() >= end[0].max()
+    finally:
+        s.close()
+    s2 = K.KKTSolver(sys.n, sys.m, sys.H_colptr, sys.H_rowidx, sys.J_rowptr, sys.J_colidx,
+                     precision=precision, ordering="nd")
+    try:
+        with pytest.raises(K.KKTError):
+            s2.solve_trace()
+    finally:
+        s2.close()

@@ -149,6 +149,34 @@ def test_host_handle_refuses_device_calls():
         K.kkt_destroy(h)
 
 
+@pytest.mark.parametrize("name,precision", [("grid2d_n2000", 1), ("grid2d_n20k", 1), ("grid2d_n20k", 0)])
+def test_solve_item_orders_cover_every_item_once(name, precision):
+    """Both sweeps hand out every work item exactly once: each row chunk, each
+    subtree item and the same set of piece heads, nitems in all; the forward
+    sweep starts with an item that has no inputs (a subtree or a head)."""
+    sys = W.make_config(name)
+    o = K.kkt_default_options(precision=precision, ordering=2)
+    h = K.kkt_analyse_host(sys.n, sys.m, sys.H_colptr, sys.H_rowidx, sys.J_rowptr, sys.J_colidx, o)
+    try:
+        info = K.kkt_symbolic_info_get(h)
+        f, b = K.kkt_get_solve_item_order(h)
+    finally:
+        K.kkt_destroy(h)
+    npc = info.npieces
+    assert len(f) == len(b) == info.nitems
+    for order in (f, b):
+        assert len(set(order.tolist())) == len(order)
+        chunks = np.sort(order[order >= 0])
+        np.testing.assert_array_equal(chunks, np.arange(info.nchunks))
+        subs = order[order < -npc]
+        assert len(subs) == info.nsub and set((-1 - npc - subs).tolist()) == set(range(info.nsub))
+        heads = order[(order < 0) & (order >= -npc)]
+        assert len(heads) == info.nitems - info.nchunks - info.nsub
+    assert set(f.tolist()) == set(b.tolist())
+    # forward: subtree items depend on nothing; some of them come first
+    assert f[0] < 0
+
+
 # ----------------------------------------------------------------- 4x4 form (Sec. 3)
 @pytest.mark.parametrize("seed", range(8))
 def test_4x4_pattern_and_symbolic_match_oracle_reduction(seed):
