@@ -404,19 +404,34 @@ __global__ void __launch_bounds__(256) k_extend_add(const int4* __restrict__ ite
   const int p = a.sparent[s];
   const int w = a.sw[s], rb = a.snr[s] - w;
   const int wp = a.sw[p], nrp = a.snr[p], rbp = nrp - wp, ldp = a.sld[p];
-  const int32_t* rel = a.rel + a.srow[s] + w;
-  const T* Us = a.U + a.uoff[s];
-  T* Pp = a.L + a.poff[p];
-  T* Up = a.U + a.uoff[p];
+  const int32_t* __restrict__ rel = a.rel + a.srow[s] + w;
+  const T* __restrict__ Us = a.U + a.uoff[s];
+  // an item's columns all land in the parent's panel or all in its update
+  // matrix (the plan splits the children's columns there)
+  const bool panel = rel[j0] < wp;
+  T* __restrict__ dst = panel ? a.L + a.poff[p] : a.U + a.uoff[p] - wp;   // + row + col * ld
+  const int64_t ldd = panel ? ldp : rbp;
+  const int cofs = panel ? 0 : wp;
+  const int bd = blockDim.x;
   for (int jj = 0; jj < kEC; jj++) {
     const int j = j0 + jj;
     if (j >= j1) break;
-    const int b = rel[j];
-    for (int i = j + threadIdx.x; i < rb; i += blockDim.x) {
-      const int ai = rel[i];
-      const T v = Us[(int64_t)i + (int64_t)j * rb];
-      if (b < wp) atomicAdd(&Pp[(int64_t)ai + (int64_t)b * ldp], v);
-      else atomicAdd(&Up[(int64_t)(ai - wp) + (int64_t)(b - wp) * rbp], v);
+    T* __restrict__ col = dst + (int64_t)(rel[j] - cofs) * ldd;
+    const T* __restrict__ uc = Us + (int64_t)j * rb;
+    // four rows per thread at a time: every load is issued before the adds,
+    // so a thread waits one memory round trip per four entries
+    for (int i0 = j + threadIdx.x; i0 < rb; i0 += 4 * bd) {
+      int ai[4];
+      T v[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        const int i = i0 + u * bd;
+        ai[u] = i < rb ? __ldg(&rel[i]) : -1;
+        v[u] = i < rb ? uc[i] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; u++)
+        if (ai[u] >= 0) atomicAdd(&col[ai[u]], v[u]);
     }
   }
 }
