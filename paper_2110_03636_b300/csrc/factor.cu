@@ -261,6 +261,7 @@ __global__ void __launch_bounds__(256) k_panel_update(const int4* __restrict__ i
       P[(int64_t)(rstart + i) + (int64_t)(cstart + j) * ld] -= acc[q];
   }
 }
+}
 
 // ---------------------------------------------------------------- SYRK
 // U_s = -L21 L21^T on 64 x 64 tiles (ti >= tj), k = panel width.
@@ -405,7 +406,7 @@ __global__ void __launch_bounds__(256) k_extend_add(const int4* __restrict__ ite
   const int w = a.sw[s], rb = a.snr[s] - w;
   const int wp = a.sw[p], nrp = a.snr[p], rbp = nrp - wp, ldp = a.sld[p];
   const int32_t* __restrict__ rel = a.rel + a.srow[s] + w;
-  const T* __restrict__ Us = a.U + a.uoff[s];
+  const T* __restrict__ Us = a.U + a.uoff[s];   // column j at Us + j * rb, rows j..rb-1 used
   // an item's columns all land in the parent's panel or all in its update
   // matrix (the plan splits the children's columns there)
   const bool panel = rel[j0] < wp;
@@ -413,25 +414,35 @@ __global__ void __launch_bounds__(256) k_extend_add(const int4* __restrict__ ite
   const int64_t ldd = panel ? ldp : rbp;
   const int cofs = panel ? 0 : wp;
   const int bd = blockDim.x;
-  for (int jj = 0; jj < kEC; jj++) {
-    const int j = j0 + jj;
-    if (j >= j1) break;
-    T* __restrict__ col = dst + (int64_t)(rel[j] - cofs) * ldd;
-    const T* __restrict__ uc = Us + (int64_t)j * rb;
-    // four rows per thread at a time: every load is issued before the adds,
-    // so a thread waits one memory round trip per four entries
-    for (int i0 = j + threadIdx.x; i0 < rb; i0 += 4 * bd) {
-      int ai[4];
-      T v[4];
+  // four columns x four rows per thread at a time: every index and value
+  // load is issued before the adds, so a thread waits one memory round trip
+  // per sixteen entries
+  for (int jj = 0; jj < kEC; jj += 4) {
+    const int jb = j0 + jj;
+    if (jb >= j1) break;
+    T* __restrict__ col[4];
+    int jc[4];
 #pragma unroll
-      for (int u = 0; u < 4; u++) {
-        const int i = i0 + u * bd;
-        ai[u] = i < rb ? __ldg(&rel[i]) : -1;
-        v[u] = i < rb ? uc[i] : T(0);
-      }
+    for (int c = 0; c < 4; c++) {
+      jc[c] = jb + c < min(j1, j0 + kEC) ? jb + c : rb;   // rb: no rows
+      col[c] = jc[c] < rb ? dst + (int64_t)(rel[jc[c]] - cofs) * ldd : dst;
+    }
+    for (int ib = threadIdx.x; jb + ib < rb; ib += 4 * bd) {
+      int ai[4][4];
+      T v[4][4];
 #pragma unroll
-      for (int u = 0; u < 4; u++)
-        if (ai[u] >= 0) atomicAdd(&col[ai[u]], v[u]);
+      for (int c = 0; c < 4; c++)
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          const int i = jc[c] + ib + u * bd;
+          ai[c][u] = i < rb ? __ldg(&rel[i]) : -1;
+          v[c][u] = i < rb ? Us[i + (int64_t)jc[c] * rb] : T(0);
+        }
+#pragma unroll
+      for (int c = 0; c < 4; c++)
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+          if (ai[c][u] >= 0) atomicAdd(&col[c][ai[c][u]], v[c][u]);
     }
   }
 }
