@@ -261,7 +261,6 @@ __global__ void __launch_bounds__(256) k_panel_update(const int4* __restrict__ i
       P[(int64_t)(rstart + i) + (int64_t)(cstart + j) * ld] -= acc[q];
   }
 }
-}
 
 // ---------------------------------------------------------------- SYRK
 // U_s = -L21 L21^T on 64 x 64 tiles (ti >= tj), k = panel width.
