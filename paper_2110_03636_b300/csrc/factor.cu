@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(kTR) k_trsm(const int4* __restrict__ items, in
 // CTA reads a half-written diagonal tile). Replaces the separate POTRF and
 // TRSM launches.
 template <typename T>
-__device__ __forceinline__ void warp_potrf32(T (&D)[kPB][kPB + 1], int bw, int fail_base, DevStatus* st) {
+__device__ __forceinline__ void warp_potrf32(T (&D)[kPB][kPB + 1], T* dinv, int bw, int fail_base, DevStatus* st) {
   // lane i holds row i of the tile
   const int lane = threadIdx.x & 31;
   T d[kPB];
@@ -140,13 +140,19 @@ __device__ __forceinline__ void warp_potrf32(T (&D)[kPB][kPB + 1], int bw, int f
   for (int j = 0; j < kPB; j++) {
     if (j < bw) {
       T djj = __shfl_sync(0xffffffffu, d[j], j);
-      if (!(djj > T(0)) || !isfinite((double)djj)) {
+      if (!(djj > T(0)) || !isfinite(djj)) {
         if (lane == 0) atomicMin(&st->fail_col, fail_base + j);
         djj = T(1);
       }
-      const T s = sqrt(djj);
-      if (lane == j) d[j] = s;
-      if (lane > j) d[j] = d[j] / s;
+      // one reciprocal square root and multiplies: the IEEE square root and
+      // a division per column made up most of this warp's time (each
+      // column waits on the previous one)
+      const T rs = rsqrt(djj);
+      if (lane == j) {
+        d[j] = djj * rs;
+        dinv[j] = rs;
+      }
+      if (lane > j) d[j] = d[j] * rs;
 #pragma unroll
       for (int k = j + 1; k < kPB; k++) {
         const T lkj = __shfl_sync(0xffffffffu, d[j], k);
@@ -162,6 +168,7 @@ __device__ __forceinline__ void warp_potrf32(T (&D)[kPB][kPB + 1], int bw, int f
 template <typename T>
 __global__ void __launch_bounds__(kTR) k_block(const int4* __restrict__ items, int kb, FacArgs<T> a) {
   __shared__ T D[kPB][kPB + 1];
+  __shared__ T Dinv[kPB];   // reciprocals of the factored tile's diagonal
   const int4 it = items[blockIdx.x];
   const int s = it.x, t = it.y;
   const int w = a.sw[s], nr = a.snr[s], ld = a.sld[s];
@@ -179,7 +186,7 @@ __global__ void __launch_bounds__(kTR) k_block(const int4* __restrict__ items, i
     D[i][j] = (i < bw && j <= i) ? P[(int64_t)(c0 + i) + (int64_t)(c0 + j) * ld] : T(0);
   }
   __syncthreads();
-  if (tid < 32) warp_potrf32(D, bw, a.sfirst[s] + c0, a.st);
+  if (tid < 32) warp_potrf32(D, Dinv, bw, a.sfirst[s] + c0, a.st);
   __syncthreads();
   if (t == 0) {
     T* dst = a.Dsc + (int64_t)it.z * (kPB * kPB);
@@ -189,10 +196,15 @@ __global__ void __launch_bounds__(kTR) k_block(const int4* __restrict__ items, i
 #pragma unroll
     for (int j = 0; j < kPB; j++) {
       if (j < bw) {
-        T sacc = x[j];
+        // two partial sums halve the dependent FMA chain
+        T s0 = x[j], s1 = T(0);
 #pragma unroll
-        for (int k = 0; k < j; k++) sacc -= x[k] * D[j][k];
-        x[j] = sacc / D[j][j];
+        for (int k = 0; k + 1 < j; k += 2) {
+          s0 -= x[k] * D[j][k];
+          s1 -= x[k + 1] * D[j][k + 1];
+        }
+        if (j & 1) s0 -= x[j - 1] * D[j][j - 1];
+        x[j] = (s0 + s1) * Dinv[j];
       }
     }
 #pragma unroll
