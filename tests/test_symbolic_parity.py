@@ -145,6 +145,8 @@ def test_host_handle_refuses_device_calls():
         assert code in (1, 8)
         code = K._lib.kkt_solve(h, None, None, None, None, None)
         assert code in (1, 8)
+        buf = np.zeros(6 * max(K.kkt_symbolic_info_get(h).nitems, 1), np.uint64)
+        assert K._lib.kkt_get_solve_trace(h, buf.ctypes.data, buf.size) == 8   # no device state
     finally:
         K.kkt_destroy(h)
 
