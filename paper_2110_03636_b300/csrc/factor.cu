@@ -165,16 +165,18 @@ __device__ __forceinline__ void warp_potrf32(T (&D)[kPB][kPB + 1], T* dinv, int 
     if (lane < bw && k <= lane) D[lane][k] = d[k];
 }
 
+static_assert(kFItem == 3 * 4, "block-step and update items are three int4");
+
 template <typename T>
 __global__ void __launch_bounds__(kTR) k_block(const int4* __restrict__ items, int kb, FacArgs<T> a) {
   __shared__ T D[kPB][kPB + 1];
   __shared__ T Dinv[kPB];   // reciprocals of the factored tile's diagonal
-  const int4 it = items[blockIdx.x];
-  const int s = it.x, t = it.y;
-  const int w = a.sw[s], nr = a.snr[s], ld = a.sld[s];
+  const int4 it = items[3 * blockIdx.x], fm = items[3 * blockIdx.x + 1], fo = items[3 * blockIdx.x + 2];
+  const int t = it.y;
+  const int w = fm.x, nr = fm.y, ld = fm.z, sfirst = fm.w;
   const int c0 = kb * kPB;
   const int bw = min(kPB, w - c0);
-  T* P = a.L + a.poff[s];
+  T* P = a.L + (int64_t)(((uint64_t)(uint32_t)fo.y << 32) | (uint32_t)fo.x);
   const int tid = threadIdx.x;
   const int r = c0 + bw + t * kTR + tid;
   const bool row = r < nr;
@@ -186,7 +188,7 @@ __global__ void __launch_bounds__(kTR) k_block(const int4* __restrict__ items, i
     D[i][j] = (i < bw && j <= i) ? P[(int64_t)(c0 + i) + (int64_t)(c0 + j) * ld] : T(0);
   }
   __syncthreads();
-  if (tid < 32) warp_potrf32(D, Dinv, bw, a.sfirst[s] + c0, a.st);
+  if (tid < 32) warp_potrf32(D, Dinv, bw, sfirst + c0, a.st);
   __syncthreads();
   if (t == 0) {
     T* dst = a.Dsc + (int64_t)it.z * (kPB * kPB);
@@ -236,16 +238,16 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_panel_update(const int4* __restrict__ items, int kb, FacArgs<T> a) {
   __shared__ T As[kUR][kPB + 1];
   __shared__ T Bs[kPB][kPB + 1];
-  const int4 it = items[blockIdx.x];
-  const int s = it.x, rt = it.y, ct = it.z;
-  const int w = a.sw[s], nr = a.snr[s], ld = a.sld[s];
+  const int4 it = items[3 * blockIdx.x], fm = items[3 * blockIdx.x + 1], fo = items[3 * blockIdx.x + 2];
+  const int rt = it.y, ct = it.z;
+  const int w = fm.x, nr = fm.y, ld = fm.z;
   const int c0 = kb * kPB;
   const int bw = min(kPB, w - c0);
   const int cstart = c0 + bw + ct * kPB;
   const int cw = min(kPB, w - cstart);
   const int rstart = cstart + rt * kUR;
   const int rn = min(kUR, nr - rstart);
-  T* P = a.L + a.poff[s];
+  T* P = a.L + (int64_t)(((uint64_t)(uint32_t)fo.y << 32) | (uint32_t)fo.x);
   const int tid = threadIdx.x;
   for (int e = tid; e < kUR * kPB; e += blockDim.x) {
     const int i = e % kUR, k = e / kUR;
@@ -747,13 +749,13 @@ cudaError_t launch_factor(const FacArgs<T>& a, const FacLists& fl, const double*
     switch (L.kind) {
       case 0: k_potrf<T><<<(unsigned)L.cnt, 256, 0, st>>>(fl.it_potrf + L.off, L.kb, a); break;
       case 1: k_trsm<T><<<(unsigned)L.cnt, kTR, 0, st>>>(fl.it_trsm + L.off, L.kb, a); break;
-      case 2: k_panel_update<T><<<(unsigned)L.cnt, 256, 0, st>>>(fl.it_pupd + L.off, L.kb, a); break;
+      case 2: k_panel_update<T><<<(unsigned)L.cnt, 256, 0, st>>>(fl.it_pupd + 3 * L.off, L.kb, a); break;
       case 3: k_syrk<T><<<(unsigned)L.cnt, 256, 0, st>>>(fl.it_syrk + L.off, a); break;
       case 4: k_extend_add<T><<<(unsigned)L.cnt, 256, 0, st>>>(fl.it_eadd + L.off, a); break;
       case 6:
         if ((e = launch_syrk_tc(fl.it_syrk_tc + L.off, L.cnt, a, st))) return e;
         break;
-      case 7: k_block<T><<<(unsigned)L.cnt, kTR, 0, st>>>(fl.it_block + L.off, L.kb, a); break;
+      case 7: k_block<T><<<(unsigned)L.cnt, kTR, 0, st>>>(fl.it_block + 3 * L.off, L.kb, a); break;
       case 8:
         if ((e = launch_syrk128(fl.it_syrk128 + L.off, L.cnt, a, st))) return e;
         break;

@@ -94,6 +94,14 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
     }
     P.u_total = top;
   }
+  // block-step and in-panel-update items carry their front's width, rows,
+  // leading dimension, first column and panel offset, so their kernels reach
+  // the panel after one load instead of two dependent ones
+  auto push_fitem = [&](std::vector<int32_t>& v, int32_t sn, int32_t x, int32_t y) {
+    const int64_t po = P.poff[sn];
+    v.insert(v.end(), {sn, x, y, 0, P.sw[sn], P.snr[sn], P.sld[sn], P.sfirst[sn],
+                       (int32_t)(uint32_t)(po & 0xffffffff), (int32_t)(po >> 32), 0, 0});
+  };
   for (int32_t L = 0; L < P.nlevels; L++) {
     const auto& F = bylev[L];
     // the children's update matrices split by column: columns landing in a
@@ -127,7 +135,7 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
     int32_t slot = 0;
     const int64_t od = (int64_t)P.it_dstore.size() / 4;
     for (int32_t kb = 0; kb * kPB < wmax; kb++) {
-      const int64_t ob = (int64_t)P.it_block.size() / 4;
+      const int64_t ob = (int64_t)P.it_block.size() / kFItem;
       const int64_t opo = (int64_t)P.it_potrf.size() / 4, otr = (int64_t)P.it_trsm.size() / 4;
       for (int32_t s : F) {
         const int32_t c0 = kb * kPB;
@@ -136,7 +144,7 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
         const int64_t below = P.snr[s] - c0 - bw;
         const int64_t nt = std::max<int64_t>(1, cdiv(below, kTR));
         if (f32) {
-          for (int64_t t = 0; t < nt; t++) P.it_block.insert(P.it_block.end(), {s, (int32_t)t, slot, 0});
+          for (int64_t t = 0; t < nt; t++) push_fitem(P.it_block, s, (int32_t)t, slot);
           P.it_dstore.insert(P.it_dstore.end(), {s, kb, slot, 0});
           slot++;
         } else {
@@ -144,13 +152,13 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
           for (int64_t t = 0; t < cdiv(below, kTR); t++) P.it_trsm.insert(P.it_trsm.end(), {s, (int32_t)t, 0, 0});
         }
       }
-      const int64_t cb = (int64_t)P.it_block.size() / 4 - ob;
+      const int64_t cb = (int64_t)P.it_block.size() / kFItem - ob;
       if (cb) P.launches.push_back({7, kb, ob, cb});
       const int64_t cpo = (int64_t)P.it_potrf.size() / 4 - opo, ctr = (int64_t)P.it_trsm.size() / 4 - otr;
       if (cpo) P.launches.push_back({0, kb, opo, cpo});
       if (ctr) P.launches.push_back({1, kb, otr, ctr});
       // right-looking update of the panel columns after the block
-      const int64_t o1 = (int64_t)P.it_pupd.size() / 4;
+      const int64_t o1 = (int64_t)P.it_pupd.size() / kFItem;
       for (int32_t s : F) {
         const int32_t c0 = kb * kPB;
         if (c0 >= P.sw[s]) continue;
@@ -159,10 +167,10 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
         for (int32_t ct = 0; jstart + ct * kPB < P.sw[s]; ct++) {
           const int32_t cstart = jstart + ct * kPB;
           const int64_t nrt = cdiv(P.snr[s] - cstart, kUR);
-          for (int64_t rt = 0; rt < nrt; rt++) P.it_pupd.insert(P.it_pupd.end(), {s, (int32_t)rt, ct, 0});
+          for (int64_t rt = 0; rt < nrt; rt++) push_fitem(P.it_pupd, s, (int32_t)rt, ct);
         }
       }
-      const int64_t c1 = (int64_t)P.it_pupd.size() / 4 - o1;
+      const int64_t c1 = (int64_t)P.it_pupd.size() / kFItem - o1;
       if (c1) P.launches.push_back({2, kb, o1, c1});
     }
     P.dsc_total = std::max(P.dsc_total, (int64_t)slot * kPB * kPB);

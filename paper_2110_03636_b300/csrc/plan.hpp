@@ -44,6 +44,10 @@ constexpr int kTR = 128;     // rows per TRSM item
 constexpr int kUR = 64;      // rows per in-panel update item (x kPB columns)
 constexpr int kST = 64;      // SYRK tile edge
 constexpr int kEC = 32;      // columns per extend-add item
+// Ints per block-step / in-panel-update item: (s, a, b, 0), (w, nr, ld,
+// first column), (panel offset low, high, 0, 0) -- three int4 loads that
+// do not depend on one another.
+constexpr int kFItem = 12;
 
 struct Launch {              // one batched kernel launch of the factorization
   int32_t kind;              // 0 potrf (diagonal tile), 1 trsm, 2 in-panel update, 3 syrk,
@@ -68,10 +72,10 @@ struct Plan {
   // factor work lists (items are int4: s, a, b, 0)
   std::vector<int32_t> it_potrf;            // (s) fronts whose column block kb is factored
   std::vector<int32_t> it_trsm;             // (s, row tile) pairs
-  std::vector<int32_t> it_pupd;             // (s, row tile, col tile) triples
+  std::vector<int32_t> it_pupd;             // (s, row tile, col tile) triples (kFItem ints each)
   std::vector<int32_t> it_syrk;             // (s, ti, tj) triples, 64 x 64 tiles
   std::vector<int32_t> it_syrk_tc;          // (s, ti, tj), 128 x 128 tensor-core tiles
-  std::vector<int32_t> it_block;            // (s, row tile) per fused left-looking block step
+  std::vector<int32_t> it_block;            // (s, row tile, slot) per fused block step (kFItem ints each)
   std::vector<int32_t> it_syrk128;          // (s, ti, tj), 128 x 128 FP32 register-tiled SYRK
   std::vector<int32_t> it_dstore;           // (s, kb, slot): factored diagonal tile -> panel, per level
   int64_t dsc_total = 0;                    // entries of the diagonal-tile scratch (largest level)
