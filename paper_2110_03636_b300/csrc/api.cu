@@ -387,7 +387,12 @@ kkt_status kkt_analyse(int64_t n, int64_t m, const int64_t* Hp, const int32_t* H
       return KKT_ERR_CUDA;
     }
     h->profp = &h->prof;
-    if (cudaMemset(h->d_instr, 0, 32 * sizeof(unsigned long long)) != cudaSuccess) { cudaGetLastError(); kkt_destroy(h); return KKT_ERR_CUDA; }
+    if (cudaMemset(h->d_instr, 0, 32 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMemset(h->d_trace, 0, (6 * h->P.fwd_items.size() + 6) * sizeof(unsigned long long)) != cudaSuccess) {
+      cudaGetLastError();
+      kkt_destroy(h);
+      return KKT_ERR_CUDA;
+    }
   }
   h->on_device = true;
   *out = h;
