@@ -89,8 +89,11 @@ __device__ __forceinline__ int packed_S(int x) {
 __device__ __forceinline__ int packed_off(int pw, int k) { return packed_S(pw) - packed_S(pw - k); }
 
 
-// out_i = sum_k tile[k*cs + d0 + i] * x[k] for i < nr, handed to emit(i, out_i);
-// the k range is split among thread groups when the rows are few
+// out_i = sum_k tile[k*cs + d0 + i] * x[k] for i < nr, handed to
+// emit(i, u, out_i) with u the thread's row slot (i = tid + u * blockDim for
+// u < 4, u = -1 beyond); the k range is split among thread groups when the
+// rows are few, and with more rows than threads every sum is formed before
+// the first is handed over
 template <typename T, typename F>
 __device__ void rows_matvec(const T* tile, int cs, int d0, int nr, int pw, const T* x, T* part, F emit) {
   const int tid = threadIdx.x;
@@ -117,13 +120,27 @@ __device__ void rows_matvec(const T* tile, int cs, int d0, int nr, int pw, const
     if (tid < nr) {
       T o = T(0);
       for (int gg = 0; gg < G; gg++) o += part[gg * rr + tid];
-      emit(tid, o);
+      emit(tid, 0, o);
     }
   } else {
-    for (int i = tid; i < nr; i += blockDim.x) {
+    T acc4[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const int i = tid + u * (int)blockDim.x;
+      T acc = T(0);
+      if (i < nr)
+        for (int k = 0; k < pw; k++) acc += tile[k * cs + d0 + i] * x[k];
+      acc4[u] = acc;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const int i = tid + u * (int)blockDim.x;
+      if (i < nr) emit(i, u, acc4[u]);
+    }
+    for (int i = tid + 4 * (int)blockDim.x; i < nr; i += blockDim.x) {
       T acc = T(0);
       for (int k = 0; k < pw; k++) acc += tile[k * cs + d0 + i] * x[k];
-      emit(i, acc);
+      emit(i, -1, acc);
     }
   }
 }
@@ -347,6 +364,16 @@ __device__ __forceinline__ void gather_rows(const T* v, const int32_t* rows, int
   for (int i = tid + 4 * bd; i < nr; i += bd) out[i] = ldcg(&v[rows[i]]);
 }
 
+// The sn_rows entries of rows tid + u * blockDim (u < 4) of an item, fetched
+// before the item waits on its inputs (0 past nr).
+__device__ __forceinline__ void prefetch_rows4(const int32_t* rows, int nr, int (&r)[4]) {
+#pragma unroll
+  for (int u = 0; u < 4; u++) {
+    const int i = (int)threadIdx.x + u * (int)blockDim.x;
+    r[u] = i < nr ? __ldg(&rows[i]) : 0;
+  }
+}
+
 // The sn_rows entry of row i of an item (i < nr), fetched before the item
 // waits on its inputs when the item has at most one row per thread.
 __device__ __forceinline__ int prefetch_row(const int32_t* rows, int nr) {
@@ -361,7 +388,8 @@ __device__ bool fwd_head(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>&
   const HeadDesc d = a.hdesc[p];
   const int pw = d.pw, f = d.f, rn = d.rn;
   const int32_t* rows = a.sn_rows + d.rowbase + pw;
-  const int myrow = prefetch_row(rows, rn);
+  int myrows[4];
+  prefetch_rows4(rows, rn, myrows);
   if (tid < 32) {
     uint32_t b1 = 0;
     if (tid == 0) fence_proxy_async();
@@ -435,8 +463,8 @@ __device__ bool fwd_head(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>&
         for (int i = tid; i < pw; i += blockDim.x) t.vec2[i] = ldcg(&vj[f + i]);
         __syncthreads();
       }
-      rows_matvec(t.B, d.cs, d0, rn, pw, t.vec2, t.aux, [&](int i, T o) {
-        atomicAdd(&vj[rn <= (int)blockDim.x ? myrow : rows[i]], -o);
+      rows_matvec(t.B, d.cs, d0, rn, pw, t.vec2, t.aux, [&](int i, int u, T o) {
+        atomicAdd(&vj[u >= 0 ? myrows[u] : rows[i]], -o);
       });
       __syncthreads();
     }
@@ -456,7 +484,9 @@ __device__ bool fwd_chunk(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>
   const ChunkDesc d = a.cdesc[c];
   const int p = d.p, pw = d.pw, f = d.f, nr = d.nr;
   const int32_t* rows = a.sn_rows + d.rowbase;
-  const int myrow = prefetch_row(rows, nr);
+  int myrows[4];
+  prefetch_rows4(rows, nr, myrows);
+  const int myrow = myrows[0];
   if (tid < 32) {
     uint32_t b = 0;
     if (tid == 0) fence_proxy_async();
@@ -502,8 +532,8 @@ __device__ bool fwd_chunk(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>
       for (int k = tid; k < pw; k += blockDim.x) t.vec[k] = ldcg(&vj[f + k]);
       __syncthreads();
     }
-    rows_matvec(t.B, d.cs, d0, nr, pw, t.vec, t.aux, [&](int i, T o) {
-      atomicAdd(&vj[nr <= (int)blockDim.x ? myrow : rows[i]], -o);
+    rows_matvec(t.B, d.cs, d0, nr, pw, t.vec, t.aux, [&](int i, int u, T o) {
+      atomicAdd(&vj[u >= 0 ? myrows[u] : rows[i]], -o);
     });
     __syncthreads();
   }
