@@ -182,10 +182,17 @@ kkt_status kkt_analyse_host(int64_t n, int64_t m, const int64_t* H_colptr, const
 kkt_status kkt_factor(kkt_handle h, const double* H_vals, const double* J_vals, double delta,
                       double gamma, void* stream);
 
-/* Algorithm 1's delta_1 loop around kkt_factor: delta_1 = 0 first; while
- * the Cholesky fails (a pivot <= 0, Thm 1: H~ not positive definite on
- * null(J)) and delta_1 <= delta_max / 2, delta_1 becomes delta_min on the
- * first retry and doubles on each later one (delta_min itself unchanged).
+/* Algorithm 1's delta_1 loop around kkt_factor, with the sequence rule of
+ * Sec. 4.1: delta_1 = 0 first; while the Cholesky fails (a pivot <= 0,
+ * Thm 1: H~ not positive definite on null(J)) and delta_1 <= delta_max / 2,
+ * delta_1 becomes, on the first retry, the value this handle accepted for
+ * the previous matrix (delta_min if that was 0 or if there was none), and
+ * doubles on each later retry (delta_min itself unchanged). A successful
+ * call stores its delta_1 as the previous value for the next call; a failed
+ * one leaves it. The loop runs on the device as one CUDA graph (a
+ * conditional WHILE node around the captured factorization): one launch and
+ * one status read per call, whatever the number of trials (profile handles
+ * loop on the host instead).
  *   H_vals, J_vals  device, as kkt_factor
  *   gamma           as kkt_factor
  *   delta_min, delta_max  <= 0 selects Algorithm 1's typical 1e-9, 1e-6
@@ -195,6 +202,11 @@ kkt_status kkt_factor(kkt_handle h, const double* H_vals, const double* J_vals, 
  * an LDL^T solver or back to the optimizer; that is the caller's). */
 kkt_status kkt_factor_regularized(kkt_handle h, const double* H_vals, const double* J_vals, double gamma,
                                   double delta_min, double delta_max, double* delta_used, void* stream);
+
+/* Sets the previous matrix's delta_1 that kkt_factor_regularized goes back
+ * to (Sec. 4.1); 0 starts a new sequence (a new handle starts at 0).
+ * Errors: KKT_ERR_INVALID for a negative or non-finite value. */
+kkt_status kkt_set_delta_prev(kkt_handle h, double delta_prev);
 
 /* Solve with the last successful factor (Algorithm 1 solve steps; eqs.
  * Schur1/Schur2), then FP64 refinement on K_delta while RR > ir_rtol
@@ -347,7 +359,11 @@ kkt_status kkt_destroy(kkt_handle h);
  * exits. n + m > KKT_NOALLOC_MAX_ROWS returns KKT_ERR_TOO_LARGE without
  * launching anything. The first call on a device looks up the array's
  * device address (cudaGetSymbolAddress); make that first call before any
- * stream capture. All calls share the array and each clears what it needs,
+ * stream capture. Later calls look the address up again unless `stream` is
+ * capturing, so a device reset between calls (which may reload the library's
+ * module at another address) is picked up. The caller checks the arrays'
+ * lengths and that they live on the current device: the kernels trust them.
+ * All calls share the array and each clears what it needs,
  * so calls whose work overlaps on the GPU (different streams, different host
  * threads) race: serialise them. The residual accumulates with device
  * atomics, so its last bits may differ from run to run. */

@@ -77,6 +77,7 @@ def _load():
         L.orc_solve.argtypes = [P, f64p, f64p, C.c_double, C.c_double, f64p, f64p, C.c_double,
                                 C.c_double, C.c_int32, C.c_int32, C.c_double, f64p, f64p, f64p]
         L.orc_residual.argtypes = [P, f64p, f64p, C.c_double, f64p, f64p, f64p, f64p, f64p]
+        L.orc_residual_vec.argtypes = [P, f64p, f64p, C.c_double, f64p, f64p, f64p, f64p, f64p, f64p]
         L.orc_num_free.argtypes = [P]
         _lib = L
     return _lib
@@ -230,28 +231,41 @@ class FactorSample(Factor):
         self.fail_col = -1
 
 
-def factor_regularized(sym: Symbolic, H_vals, J_vals, gamma, delta_min=1e-9, delta_max=1e-6):
+def factor_regularized(sym: Symbolic, H_vals, J_vals, gamma, delta_min=1e-9, delta_max=1e-6, delta_prev=0.0):
     """Algorithm 1's delta_1 loop (its lines from "delta_1 <- 0" to the end of
-    the while loop): try the Cholesky with delta_1 = 0; while it fails and
-    delta_1 <= delta_max / 2, set delta_1 to delta_min on the first retry and
-    double it afterwards (the garbled update is read as "double delta_1").
-    Returns (Factor of the last trial, delta_1)."""
+    the while loop) with the sequence rule of Sec. 4.1: try the Cholesky with
+    delta_1 = 0; while it fails and delta_1 <= delta_max / 2, set delta_1 on
+    the first retry back to the previous matrix's accepted value
+    ``delta_prev`` (delta_min when that was 0) and double it afterwards (the
+    garbled update is read as "double delta_1"). Returns (Factor of the last
+    trial, delta_1); the caller carries delta_1 to the next matrix when the
+    factorization succeeded."""
     d1 = 0.0
     fac = Factor(sym, H_vals, J_vals, d1, gamma)
     while not fac.ok and d1 <= delta_max / 2:
-        d1 = delta_min if d1 == 0.0 else 2.0 * d1
+        if d1 == 0.0:
+            d1 = delta_prev if delta_prev > 0 else delta_min
+        else:
+            d1 = 2.0 * d1
         fac = Factor(sym, H_vals, J_vals, d1, gamma)
     return fac, d1
 
 
-def residual(sym: Symbolic, H_vals, J_vals, delta, r_x, r_y, dx, dy):
+def residual(sym: Symbolic, H_vals, J_vals, delta, r_x, r_y, dx, dy, *, vector=False):
     """RR, BE, ||res||_2, ||K_delta||_inf of [dx;dy] for K_delta = [H~+delta I, J^T; J, 0]
-    (BE and RR as defined in Sec. 5.1, ||K||_2 estimated by ||K||_inf)."""
+    (BE and RR as defined in Sec. 5.1, ||K||_2 estimated by ||K||_inf).
+    With ``vector=True`` the dict also holds ``res`` = b - K_delta [dx; dy]
+    as ``res_x`` (n) and ``res_y`` (m)."""
     out = np.zeros(4)
-    _load().orc_residual(sym._h, _c(H_vals, np.float64), _c(J_vals, np.float64), float(delta),
-                         _c(r_x, np.float64), _c(r_y, np.float64),
-                         _c(dx, np.float64), _c(dy, np.float64), out)
-    return dict(rr=float(out[0]), be=float(out[1]), res=float(out[2]), knorm=float(out[3]))
+    n, m = sym.n, sym.m
+    rv = np.zeros(n + max(m, 1))
+    _load().orc_residual_vec(sym._h, _c(H_vals, np.float64), _c(J_vals, np.float64), float(delta),
+                             _c(r_x, np.float64), _c(r_y, np.float64),
+                             _c(dx, np.float64), _c(dy, np.float64), out, rv)
+    d = dict(rr=float(out[0]), be=float(out[1]), res=float(out[2]), knorm=float(out[3]))
+    if vector:
+        d["res_x"], d["res_y"] = rv[:n].copy(), rv[n:n + m].copy()
+    return d
 
 
 def solve_system(sys, *, ir_maxit=0, **kw):

@@ -1148,9 +1148,11 @@ int32_t orc_solve(const orc_num *N, const double *Hv, const double *Jv, double d
 
 /* Residual norms of an externally computed solution against K_delta:
  * out[0] RR, out[1] BE, out[2] ||res||_2, out[3] ||K||_inf */
-void orc_residual(const orc_sym *S, const double *Hv, const double *Jv, double delta,
-                  const double *rx, const double *ry, const double *dx, const double *dy,
-                  double *out) {
+/* Residual res = b - K_delta [dx; dy] and its norms (Sec. 5.1). res_out,
+ * when not NULL, receives [res_x (n); res_y (m)]. */
+void orc_residual_vec(const orc_sym *S, const double *Hv, const double *Jv, double delta,
+                      const double *rx, const double *ry, const double *dx, const double *dy,
+                      double *out, double *res_out) {
     int64_t n = S->n, m = S->m;
     double *resx = (double *)malloc((size_t)n * sizeof(double));
     double *resy = (double *)malloc((size_t)(m + 1) * sizeof(double));
@@ -1163,7 +1165,17 @@ void orc_residual(const orc_sym *S, const double *Hv, const double *Jv, double d
     out[1] = resn / (knorm * xn + bnorm);
     out[2] = resn;
     out[3] = knorm;
+    if (res_out) {
+        memcpy(res_out, resx, (size_t)n * sizeof(double));
+        if (m > 0) memcpy(res_out + n, resy, (size_t)m * sizeof(double));
+    }
     free(resx); free(resy);
+}
+
+void orc_residual(const orc_sym *S, const double *Hv, const double *Jv, double delta,
+                  const double *rx, const double *ry, const double *dx, const double *dy,
+                  double *out) {
+    orc_residual_vec(S, Hv, Jv, delta, rx, ry, dx, dy, out, NULL);
 }
 
 void orc_num_free(orc_num *N) {

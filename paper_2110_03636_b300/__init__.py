@@ -66,6 +66,7 @@ def _load():
     L.kkt_solve.argtypes = [P, P, P, P, P, P]
     L.kkt_solve_multi.argtypes = [P, I32, P, P, P, P, P, P]
     L.kkt_factor_regularized.argtypes = [P, P, P, D, D, D, P, P]
+    L.kkt_set_delta_prev.argtypes = [P, D]
     L.kkt_factor_batch.argtypes = [P, I32, P, P, D, D, P, P]
     L.kkt_solve_batch.argtypes = [P, I32, P, P, P, P, P, P, P]
     L.kkt_factor_solve_host.argtypes = [P, P, P, D, D, P, P, P, P, P]
@@ -91,7 +92,7 @@ def _load():
     L.kkt_destroy_4x4.argtypes = [P]
     L.kkt_status_string.argtypes = [I32]
     L.kkt_status_string.restype = C.c_char_p
-    for nm in ("kkt_analyse", "kkt_analyse_host", "kkt_factor", "kkt_solve", "kkt_solve_multi", "kkt_factor_batch", "kkt_solve_batch", "kkt_factor_regularized", "kkt_factor_solve_host", "kkt_hsolve", "kkt_get_info",
+    for nm in ("kkt_analyse", "kkt_analyse_host", "kkt_factor", "kkt_solve", "kkt_solve_multi", "kkt_factor_batch", "kkt_solve_batch", "kkt_factor_regularized", "kkt_set_delta_prev", "kkt_factor_solve_host", "kkt_hsolve", "kkt_get_info",
                "kkt_inertia", "kkt_symbolic_info_get", "kkt_get_symbolic", "kkt_get_factor_panels", "kkt_get_profile", "kkt_get_solve_counters", "kkt_residual_noalloc",
                "kkt_get_solve_trace", "kkt_get_solve_item_order", "kkt_destroy", "kkt_analyse_4x4", "kkt_analyse_4x4_host", "kkt_get_4x4_pattern", "kkt_factor_4x4",
                "kkt_solve_4x4", "kkt_destroy_4x4"):
@@ -100,7 +101,7 @@ def _load():
 
 
 _lib = _load()
-EXPORTED = ("kkt_default_options", "kkt_analyse", "kkt_analyse_host", "kkt_factor", "kkt_solve", "kkt_solve_multi", "kkt_factor_batch", "kkt_solve_batch", "kkt_factor_regularized", "kkt_factor_solve_host",
+EXPORTED = ("kkt_default_options", "kkt_analyse", "kkt_analyse_host", "kkt_factor", "kkt_solve", "kkt_solve_multi", "kkt_factor_batch", "kkt_solve_batch", "kkt_factor_regularized", "kkt_set_delta_prev", "kkt_factor_solve_host",
             "kkt_hsolve", "kkt_get_info", "kkt_inertia", "kkt_symbolic_info_get", "kkt_get_symbolic",
             "kkt_get_factor_panels", "kkt_get_profile", "kkt_get_solve_counters", "kkt_residual_noalloc",
             "kkt_get_solve_trace", "kkt_get_solve_item_order", "kkt_destroy", "kkt_status_string", "kkt_analyse_4x4", "kkt_analyse_4x4_host", "kkt_4x4_inner",
@@ -248,22 +249,42 @@ def kkt_get_profile(h, reset=False):
 def kkt_residual_noalloc(n, m, H_colptr, H_rowidx, H_vals, J_rowptr, J_colidx, J_vals, delta, r_x, r_y, dx, dy,
                          res_x, res_y, norms, stream=None):
     """Residual of K_delta without device allocation (for callers that
-    cannot allocate device memory). Every array argument is a CUDA tensor:
-    int64/int32 patterns, float64 values; norms is float64[4] (RR, BE,
-    ||res||, ||K||_inf). Returns the status code; the work is asynchronous."""
+    cannot allocate device memory). Every array argument is a CUDA tensor on
+    the current device: int64/int32 patterns, float64 values; norms is
+    float64[4] (RR, BE, ||res||, ||K||_inf). The J arrays, r_y, dy and res_y
+    may be None when m == 0. Sizes are checked here (ValueError) because the
+    kernels trust them; the pattern's contents (H_colptr[n] equal to the
+    entry count, indices in range) are the caller's to guarantee. Returns the
+    status code; the work is asynchronous."""
     import torch
 
-    def ptr(t, dt):
+    n, m = int(n), int(m)
+    cur = torch.cuda.current_device()
+
+    def ptr(name, t, dt, size):
         if t is None:
+            if size > 0:
+                raise ValueError(f"{name}: a tensor of {size} elements is required")
             return None
         if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dt and t.is_contiguous()):
-            raise TypeError(f"expected a contiguous CUDA tensor of {dt}")
+            raise TypeError(f"{name}: expected a contiguous CUDA tensor of {dt}")
+        if t.device.index != cur:
+            raise ValueError(f"{name}: on cuda:{t.device.index}, the current device is cuda:{cur}")
+        if size >= 0 and t.numel() != size:
+            raise ValueError(f"{name}: {t.numel()} elements, expected {size}")
         return t.data_ptr() if t.numel() else None
     i64, i32, f64 = torch.int64, torch.int32, torch.float64
-    return _lib.kkt_residual_noalloc(int(n), int(m), ptr(H_colptr, i64), ptr(H_rowidx, i32), ptr(H_vals, f64),
-                                     ptr(J_rowptr, i64), ptr(J_colidx, i32), ptr(J_vals, f64), float(delta),
-                                     ptr(r_x, f64), ptr(r_y, f64), ptr(dx, f64), ptr(dy, f64), ptr(res_x, f64),
-                                     ptr(res_y, f64), ptr(norms, f64), _stream(stream))
+    nh = -1 if H_rowidx is None else H_rowidx.numel()
+    nj = (-1 if J_colidx is None else J_colidx.numel()) if m > 0 else 0
+    if nj < 0:
+        raise ValueError("J_colidx: required when m > 0")
+    args = (ptr("H_colptr", H_colptr, i64, n + 1), ptr("H_rowidx", H_rowidx, i32, nh),
+            ptr("H_vals", H_vals, f64, nh), ptr("J_rowptr", J_rowptr, i64, m + 1 if m > 0 else 0),
+            ptr("J_colidx", J_colidx, i32, nj), ptr("J_vals", J_vals, f64, nj))
+    return _lib.kkt_residual_noalloc(n, m, *args, float(delta),
+                                     ptr("r_x", r_x, f64, n), ptr("r_y", r_y, f64, m), ptr("dx", dx, f64, n),
+                                     ptr("dy", dy, f64, m), ptr("res_x", res_x, f64, n),
+                                     ptr("res_y", res_y, f64, m), ptr("norms", norms, f64, 4), _stream(stream))
 
 
 def kkt_get_solve_counters(h, reset=False):
@@ -389,13 +410,20 @@ class KKTSolver:
 
     def factor_regularized(self, H_vals, J_vals, gamma=-1.0, delta_min=1e-9, delta_max=1e-6, stream=None,
                            check=True):
-        """Algorithm 1's delta_1 loop; returns (status code, delta_1 used)."""
+        """Algorithm 1's delta_1 loop with the sequence rule of Sec. 4.1 (the
+        first retry goes back to the delta_1 the handle accepted for the
+        previous matrix); returns (status code, delta_1 used)."""
         d = C.c_double(0.0)
         code = _lib.kkt_factor_regularized(self.h, _dev(H_vals, self.nnz_h), _dev(J_vals, self.nnz_j), float(gamma),
                                            float(delta_min), float(delta_max), C.byref(d), _stream(stream))
         if check and code not in (0, 2):
             _check("kkt_factor_regularized", code)
         return code, d.value
+
+    def set_delta_prev(self, delta_prev=0.0):
+        """The delta_1 the next factor_regularized call goes back to after a
+        failed unshifted trial (0 starts a new sequence)."""
+        _check("kkt_set_delta_prev", _lib.kkt_set_delta_prev(self.h, float(delta_prev)))
 
     def factor_batch(self, H_vals, J_vals, delta, gamma=-1.0, stream=None):
         """H_vals: CUDA float64 (nsys, nnz(H~)), J_vals: (nsys, nnz(J)). Returns

@@ -102,12 +102,15 @@ struct kkt_handle_s {
   bool multi = false;
   void *mv;
   double *mrhx, *mp, *mr, *my, *mq, *mbS, *mres_x, *mres_y, *mwv, *mxa;
-  double* d_dg = nullptr;    // device [delta, gamma] read by the assembly kernel
+  double* d_dg = nullptr;    // device [delta, gamma, delta_min, delta_max, delta_prev, 0]: the
+                             // assembly reads the first two, the delta_1 loop the rest
   unsigned long long* d_instr = nullptr;   // solve-kernel cycle counters (profile mode)
   unsigned long long* d_trace = nullptr;   // solve-kernel item timeline (profile mode)
   double* h_dg = nullptr;    // pinned staging for it
   cudaStream_t cap_stream = nullptr;   // private stream used to capture the factor graph
   cudaGraphExec_t fac_graph = nullptr; // the whole factorization as one CUDA graph
+  cudaGraphExec_t reg_graph = nullptr; // Algorithm 1's delta_1 loop around it (conditional node)
+  double delta_prev = 0;     // delta_1 accepted for the previous matrix of the sequence (Sec. 4.1)
   // state
   bool on_device = false;   // false for a host-only (symbolic) handle
   bool factored = false;
@@ -220,6 +223,7 @@ kkt_status kkt_destroy(kkt_handle h) {
   if (h->hst) cudaFreeHost(h->hst);
   if (h->h_dg) cudaFreeHost(h->h_dg);
   if (h->fac_graph) cudaGraphExecDestroy(h->fac_graph);
+  if (h->reg_graph) cudaGraphExecDestroy(h->reg_graph);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->prof.a) cudaEventDestroy(h->prof.a);
   if (h->prof.b) cudaEventDestroy(h->prof.b);
@@ -367,12 +371,12 @@ kkt_status kkt_analyse(int64_t n, int64_t m, const int64_t* Hp, const int32_t* H
   h->stage_dx = A.alloc<double>(n); h->stage_dy = A.alloc<double>(m);
   h->counters = A.alloc<int>(4 * (size_t)P.npieces + 8);
   h->dst = A.alloc<DevStatus>(1);
-  h->d_dg = A.alloc<double>(2);
+  h->d_dg = A.alloc<double>(6);
   h->d_instr = A.alloc<unsigned long long>(32);
   if (o.profile) h->d_trace = A.alloc<unsigned long long>(6 * P.fwd_items.size() + 6);
   if (A.failed) { kkt_destroy(h); return KKT_ERR_OOM; }
   if (cudaMallocHost(&h->hst, sizeof(DevStatus)) != cudaSuccess) { cudaGetLastError(); h->hst = nullptr; kkt_destroy(h); return KKT_ERR_OOM; }
-  if (cudaMallocHost(&h->h_dg, 2 * sizeof(double)) != cudaSuccess) { cudaGetLastError(); h->h_dg = nullptr; kkt_destroy(h); return KKT_ERR_OOM; }
+  if (cudaMallocHost(&h->h_dg, 6 * sizeof(double)) != cudaSuccess) { cudaGetLastError(); h->h_dg = nullptr; kkt_destroy(h); return KKT_ERR_OOM; }
   if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) { cudaGetLastError(); h->cap_stream = nullptr; kkt_destroy(h); return KKT_ERR_CUDA; }
   if (cudaDeviceSynchronize() != cudaSuccess) { cudaGetLastError(); kkt_destroy(h); return KKT_ERR_CUDA; }
   if (cudaEventCreate(&h->cg_a) != cudaSuccess || cudaEventCreate(&h->cg_b) != cudaSuccess) {
@@ -488,6 +492,66 @@ static kkt_status factor_common(kkt_handle h, double delta, double gamma, cudaSt
   if (h->hst->abort) return KKT_ERR_TIMEOUT;
   if (h->hst->fail_col != INT_MAX) return KKT_ERR_NOT_SPD;
   h->factored = true;
+  return KKT_OK;
+}
+
+// Algorithm 1's regularization loop with the sequence rule of Sec. 4.1:
+// delta_1 = 0; while the Cholesky fails and delta_1 <= delta_max / 2,
+// delta_1 becomes the previous matrix's accepted value (delta_min when that
+// was 0) on the first retry, then doubles. The loop runs on the device as
+// one CUDA graph: a conditional WHILE node whose body is the captured
+// factorization followed by k_reg_next, which reads the pivot status and
+// either ends the loop or writes the next shift to device memory (the
+// assembly reads it there) and clears the status for the next trial. One
+// launch and one status read per call, whatever the number of trials.
+__global__ void k_reg_next(cudaGraphConditionalHandle loop, double* dg, DevStatus* st) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double d1 = dg[0], dmin = dg[2], dmax = dg[3], prev = dg[4];
+  unsigned go = 0;
+  if (st->fail_col != INT_MAX && st->abort == 0 && d1 <= dmax / 2) {
+    dg[0] = d1 == 0.0 ? (prev > 0.0 ? prev : dmin) : 2.0 * d1;
+    st->fail_col = INT_MAX;
+    go = 1;
+  }
+  cudaGraphSetConditional(loop, go);
+}
+
+template <typename T>
+static kkt_status build_reg_graph(kkt_handle h) {
+  cudaGraph_t g = nullptr;
+  CK(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle loop;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&loop, g, 1, cudaGraphCondAssignDefault);
+  // the parameter union has no default constructor: zero raw storage
+  alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
+  std::memset(cp_raw, 0, sizeof(cp_raw));
+  cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_raw);
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = loop;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (!e) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp);
+  if (!e) {
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (!e) {
+      cudaError_t e1 = factor_launches<T>(h, h->cap_stream, nullptr);
+      if (!e1) {
+        k_reg_next<<<1, 32, 0, h->cap_stream>>>(loop, h->d_dg, h->dst);
+        e1 = cudaGetLastError();
+      }
+      e = cudaStreamEndCapture(h->cap_stream, &body);
+      if (!e) e = e1;
+    }
+  }
+  if (!e) e = cudaGraphInstantiate(&h->reg_graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e) {
+    h->reg_graph = nullptr;
+    cudaGetLastError();
+    return cuda_status(e);
+  }
   return KKT_OK;
 }
 
@@ -969,10 +1033,6 @@ kkt_status kkt_factor(kkt_handle h, const double* H_vals, const double* J_vals, 
   return factor_common(h, delta, gamma, st);
 }
 
-// Algorithm 1's regularization loop: delta_1 = 0; while the Cholesky fails
-// and delta_1 <= delta_max / 2, delta_1 becomes delta_min, then doubles.
-// Each trial replays the factorization with the new shift (the assembly
-// reads delta from device memory).
 kkt_status kkt_factor_regularized(kkt_handle h, const double* H_vals, const double* J_vals, double gamma,
                                   double delta_min, double delta_max, double* delta_used, void* stream) {
   if (!h || !H_vals || (h->nnzJ > 0 && !J_vals)) return KKT_ERR_INVALID;
@@ -980,18 +1040,54 @@ kkt_status kkt_factor_regularized(kkt_handle h, const double* H_vals, const doub
   if (!(delta_min > 0)) delta_min = 1e-9;
   if (!(delta_max > 0)) delta_max = 1e-6;
   if (!std::isfinite(delta_min) || !std::isfinite(delta_max) || delta_max < delta_min) return KKT_ERR_INVALID;
+  if (gamma < 0) gamma = h->opt.gamma;
+  if (!std::isfinite(gamma)) return KKT_ERR_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
   CK(cudaSetDevice(h->device));
   CK(cudaMemcpyAsync(h->Hv, H_vals, sizeof(double) * h->nnzH, cudaMemcpyDeviceToDevice, st));
   if (h->nnzJ) CK(cudaMemcpyAsync(h->Jv, J_vals, sizeof(double) * h->nnzJ, cudaMemcpyDeviceToDevice, st));
   double d1 = 0.0;
-  kkt_status s = factor_common(h, d1, gamma, st);
-  while (s == KKT_ERR_NOT_SPD && d1 <= delta_max / 2) {
-    d1 = d1 == 0.0 ? delta_min : 2.0 * d1;
+  kkt_status s;
+  if (h->profp) {
+    // profile mode times kernel by kernel, so the loop stays on the host
     s = factor_common(h, d1, gamma, st);
+    while (s == KKT_ERR_NOT_SPD && d1 <= delta_max / 2) {
+      d1 = d1 == 0.0 ? (h->delta_prev > 0.0 ? h->delta_prev : delta_min) : 2.0 * d1;
+      s = factor_common(h, d1, gamma, st);
+    }
+  } else {
+    h->factored = false;
+    h->inertia_ok = 0;
+    if (!h->reg_graph) {
+      s = h->opt.precision == KKT_FP64 ? build_reg_graph<double>(h) : build_reg_graph<float>(h);
+      if (s) return s;
+    }
+    if ((s = reset_status(h, st))) return s;
+    double* dg = h->h_dg;
+    dg[0] = 0.0; dg[1] = gamma; dg[2] = delta_min; dg[3] = delta_max; dg[4] = h->delta_prev; dg[5] = 0.0;
+    CK(cudaMemcpyAsync(h->d_dg, dg, 6 * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaGraphLaunch(h->reg_graph, st));
+    CK(cudaMemcpyAsync(dg, h->d_dg, sizeof(double), cudaMemcpyDeviceToHost, st));
+    if ((s = read_status(h, st))) return s;   // synchronises the stream
+    d1 = dg[0];
+    h->delta = d1;
+    h->gamma = gamma;
+    if (h->hst->abort) s = KKT_ERR_TIMEOUT;
+    else if (h->hst->fail_col != INT_MAX) s = KKT_ERR_NOT_SPD;
+    else {
+      h->factored = true;
+      s = KKT_OK;
+    }
   }
+  if (s == KKT_OK) h->delta_prev = d1;
   if (delta_used) *delta_used = d1;
   return s;
+}
+
+kkt_status kkt_set_delta_prev(kkt_handle h, double delta_prev) {
+  if (!h || !(delta_prev >= 0.0) || !std::isfinite(delta_prev)) return KKT_ERR_INVALID;
+  h->delta_prev = delta_prev;
+  return KKT_OK;
 }
 
 kkt_status kkt_solve(kkt_handle h, const double* r_x, const double* r_y, double* dx, double* dy, void* stream) {

@@ -30,15 +30,22 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 double* g_scratch_addr[kMaxDevices] = {nullptr};
 
-// Device address of the scratch array on the current device (looked up once
-// per device; the host-side name is only a stand-in for the symbol).
-cudaError_t scratch_on_current_device(double** out) {
+// Device address of the scratch array on the current device. The
+// host-side name is only a stand-in for the symbol, so the address is
+// looked up with cudaGetSymbolAddress: on the first call on each device,
+// and again on every call whose stream is not capturing (a device reset
+// between calls reloads the module, possibly at another address). A call
+// made during stream capture uses the address cached by an earlier call.
+cudaError_t scratch_on_current_device(cudaStream_t st, double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(st, &cs);
+  if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_scratch_addr[dev]) {
+  if (cs == cudaStreamCaptureStatusNone || !g_scratch_addr[dev]) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
@@ -161,12 +168,12 @@ extern "C" kkt_status kkt_residual_noalloc(int64_t n, int64_t m, const int64_t* 
   if (m > 0 && (!J_rowptr || !J_colidx || !J_vals || !r_y || !dy || !res_y)) return KKT_ERR_INVALID;
   if (n + m > kNoAllocMaxRows) return KKT_ERR_TOO_LARGE;
   if (!std::isfinite(delta)) return KKT_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
   double* scratch = nullptr;
-  cudaError_t e = scratch_on_current_device(&scratch);
+  cudaError_t e = scratch_on_current_device(st, &scratch);
   if (e != cudaSuccess) { cudaGetLastError(); return KKT_ERR_CUDA; }
   double* rowsum = scratch;
   double* part = scratch + kNoAllocMaxRows;
-  cudaStream_t st = (cudaStream_t)stream;
   k_na_init<<<kNaBlocks, kNaThreads, 0, st>>>(n, m, delta, r_x, r_y, dx, res_x, res_y, rowsum);
   k_na_h<<<kNaBlocks, kNaThreads, 0, st>>>(n, H_colptr, H_rowidx, H_vals, dx, res_x, rowsum);
   if (m > 0) k_na_j<<<kNaBlocks, kNaThreads, 0, st>>>(n, m, J_rowptr, J_colidx, J_vals, dx, dy, res_x, res_y, rowsum);

@@ -492,6 +492,37 @@ def test_factor_regularized_matches_oracle(lam):
             assert rel(np.concatenate([dx, dy]), np.concatenate([odx, ody])) <= 1e-6
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_factor_regularized_sequence_matches_oracle(precision):
+    """A sequence of matrices on one handle: the device loop (one graph
+    launch per matrix) carries delta_1 as Sec. 4.1 says, back to the
+    previous matrix's value after a failed unshifted trial, and accepts the
+    same delta_1 as the oracle at every step; kkt_set_delta_prev(0) starts a
+    new sequence. Each accepted factor then solves to the oracle's RR."""
+    from test_oracle import nullspace_indefinite_system
+    lams = [-2.5e-8, -1e-8, 0.5, -5e-9, -5e-8]
+    base, _, _ = nullspace_indefinite_system(lams[0])
+    s = K.KKTSolver(base.n, base.m, base.H_colptr, base.H_rowidx, base.J_rowptr, base.J_colidx, precision=precision)
+    sym = O.Symbolic(base.n, base.m, base.H_colptr, base.H_rowidx, base.J_rowptr, base.J_colidx)
+    prev = 0.0
+    for t, lam in enumerate(lams + [lams[1]]):
+        if t == len(lams):
+            s.set_delta_prev(0.0)                  # new sequence: the second matrix again, from scratch
+            prev = 0.0
+        sys, _, _ = nullspace_indefinite_system(lam)
+        fac, d_ref = O.factor_regularized(sym, sys.H_vals, sys.J_vals, sys.gamma, delta_prev=prev)
+        code, d = s.factor_regularized(cu(sys.H_vals), cu(sys.J_vals), sys.gamma)
+        assert (code == 0) == fac.ok and fac.ok
+        assert d == d_ref, (lam, d, d_ref)
+        dx, dy = s.solve(cu(sys.r_x), cu(sys.r_y))
+        rr = O.residual(sym, sys.H_vals, sys.J_vals, d, sys.r_x, sys.r_y, dx.cpu().numpy(), dy.cpu().numpy())["rr"]
+        _, _, oinfo = fac.solve(sys.r_x, sys.r_y, ir_maxit=3)
+        assert rr <= max(1e-8, 10 * oinfo["rr"])
+        prev = d
+    assert d == pytest.approx(1.6e-8, rel=1e-12)   # -1e-8 from scratch: 1e-9 * 2^4
+    s.close()
+
+
 @pytest.mark.parametrize("refine", [1, 2])
 @pytest.mark.parametrize("name", ["grid2d_n2000", "grid2d_n20k"])
 def test_mixed_refinement_modes_match_oracle(name, refine):

@@ -591,3 +591,25 @@ def test_factor_regularized_loop(lam, expect_delta, expect_ok):
     # Thm 1: the smallest eigenvalue of H_gamma + delta_1 I decides
     lmin = np.linalg.eigvalsh(H + sys.gamma * J.T @ J + d1 * np.eye(sys.n)).min()
     assert (lmin > 0) == expect_ok
+
+
+def test_factor_regularized_sequence_carries_delta():
+    """Sec. 4.1: for each next matrix delta_1 starts at 0 and, if that
+    Cholesky fails, is set back to the previous matrix's value (then doubled
+    while it still fails); after a matrix that needed no shift the first
+    retry is delta_min, as in Algorithm 1. The smallest eigenvalue of H_gamma
+    is lam along a null(J) direction, so the accepted shifts follow by hand:
+    -2.5e-8 -> 1e-9 * 2^5 = 3.2e-8; -1e-8 -> back to 3.2e-8 (from scratch it
+    would be 1.6e-8); 0.5 -> 0; -5e-9 -> 1e-9 * 2^3 = 8e-9; -5e-8 -> 8e-9 *
+    2^3 = 6.4e-8."""
+    lams = [-2.5e-8, -1e-8, 0.5, -5e-9, -5e-8]
+    want = [3.2e-8, 3.2e-8, 0.0, 8e-9, 6.4e-8]
+    prev = 0.0
+    for lam, w in zip(lams, want):
+        sys, H, J = nullspace_indefinite_system(lam)
+        sym = O.Symbolic(sys.n, sys.m, sys.H_colptr, sys.H_rowidx, sys.J_rowptr, sys.J_colidx)
+        fac, d1 = O.factor_regularized(sym, sys.H_vals, sys.J_vals, sys.gamma, delta_prev=prev)
+        assert fac.ok
+        assert d1 == pytest.approx(w, rel=1e-12, abs=0)
+        assert np.linalg.eigvalsh(H + sys.gamma * J.T @ J + d1 * np.eye(sys.n)).min() > 0
+        prev = d1
