@@ -423,18 +423,47 @@ int analyse_pattern(int64_t n, int64_t m, const int64_t* Hp, const int32_t* Hi, 
     const int32_t pa = par0[post[k]];
     S.parent[k] = pa < 0 ? -1 : ipost[pa];
   }
-  // column counts by row subtrees: row k of L is the union of the etree
-  // paths from each i < k adjacent to k up to k
-  S.colcount.assign(n, 1);
-  std::vector<int32_t> visited(n, -1);
-  for (int64_t k = 0; k < n; k++) {
-    visited[k] = (int32_t)k;
-    const int32_t ok = S.perm[k];
-    for (int64_t q = gp[ok]; q < gp[ok + 1]; q++) {
-      for (int32_t i = S.iperm[gi[q]]; i < k && visited[i] != k; i = S.parent[i]) {
-        visited[i] = (int32_t)k;
-        S.colcount[i]++;
+  // Column counts without visiting L (Gilbert, Ng & Peyton, "An efficient
+  // algorithm to compute row and column counts for sparse Cholesky
+  // factorization", SIAM J. Matrix Anal. Appl. 15(4), 1994). Row i of L is
+  // the row subtree T_i: the etree paths from i's neighbours k < i up to i.
+  // cc(j) counts the row subtrees holding j. Give each T_i weights: +1 at
+  // every neighbour k < i and at i, -1 at the lowest common ancestor of
+  // consecutive ones (in postorder, i last) and -1 at parent(i); the weights
+  // of T_i summed over the subtree of any j give 1 if j lies in T_i, else 0.
+  // So cc(j) is the subtree sum of all weights. Columns are taken in
+  // postorder; a disjoint-set forest over the finished columns (each linked
+  // to its parent once done) answers lca(prev, j) = find(prev).
+  {
+    std::vector<int64_t> wgt(n, 1);            // +1: i as the last leaf of T_i
+    std::vector<int32_t> prev(n, -1), anc(n);
+    for (int64_t j = 0; j < n; j++) anc[j] = (int32_t)j;
+    auto find = [&](int32_t x) {
+      while (anc[x] != x) {                    // path halving
+        anc[x] = anc[anc[x]];
+        x = anc[x];
       }
+      return x;
+    };
+    for (int64_t j = 0; j < n; j++) {
+      const int32_t oj = S.perm[j];
+      for (int64_t q = gp[oj]; q < gp[oj + 1]; q++) {
+        const int32_t i = S.iperm[gi[q]];
+        if (i <= j) continue;                  // j is a neighbour k < i of row i
+        wgt[j] += 1;
+        if (prev[i] >= 0) wgt[find(prev[i])] -= 1;
+        prev[i] = (int32_t)j;
+      }
+      if (S.parent[j] >= 0) anc[j] = S.parent[j];
+    }
+    for (int64_t i = 0; i < n; i++) {
+      if (prev[i] >= 0) wgt[i] -= 1;           // lca(last neighbour, i) = i
+      if (S.parent[i] >= 0) wgt[S.parent[i]] -= 1;
+    }
+    S.colcount.assign(n, 0);
+    for (int64_t j = 0; j < n; j++) {          // children precede parents
+      S.colcount[j] += wgt[j];
+      if (S.parent[j] >= 0) S.colcount[S.parent[j]] += S.colcount[j];
     }
   }
   S.nnzL = 0;
@@ -484,18 +513,36 @@ int analyse_pattern(int64_t n, int64_t m, const int64_t* Hp, const int32_t* Hi, 
     last_of[rel[s].l] = (int32_t)s;
   }
   S.sn_start[S.ns] = (int32_t)n;
-  // rows below each supernode = structure of its last column, gathered by a
-  // second row-subtree sweep (rows arrive in increasing order)
+  // rows below each supernode = structure of its last column l: the rows
+  // > l adjacent to any of its columns, joined with the rows > l of its
+  // child supernodes (a supernode's columns form one etree chain, and every
+  // other etree child of those columns ends a child supernode). Children
+  // precede parents, so one pass in supernode order suffices; it touches
+  // the row lists, not the entries of L.
   std::vector<std::vector<int32_t>> below(S.ns);
-  std::fill(visited.begin(), visited.end(), -1);
-  for (int64_t k = 0; k < n; k++) {
-    visited[k] = (int32_t)k;
-    const int32_t ok = S.perm[k];
-    for (int64_t q = gp[ok]; q < gp[ok + 1]; q++) {
-      for (int32_t i = S.iperm[gi[q]]; i < k && visited[i] != k; i = S.parent[i]) {
-        visited[i] = (int32_t)k;
-        if (last_of[i] >= 0) below[last_of[i]].push_back((int32_t)k);
+  {
+    std::vector<std::vector<int32_t>> kids(S.ns);
+    for (int64_t s = 0; s < S.ns; s++) {
+      const int32_t pl = S.parent[rel[s].l];
+      if (pl >= 0) kids[col2sn[pl]].push_back((int32_t)s);
+    }
+    std::vector<int32_t> mark(n, -1);
+    for (int64_t s = 0; s < S.ns; s++) {
+      const int32_t l = rel[s].l;
+      std::vector<int32_t>& B = below[s];
+      auto add = [&](int32_t r) {
+        if (r > l && mark[r] != (int32_t)s) {
+          mark[r] = (int32_t)s;
+          B.push_back(r);
+        }
+      };
+      for (int32_t j = rel[s].f; j <= l; j++) {
+        const int32_t oj = S.perm[j];
+        for (int64_t q = gp[oj]; q < gp[oj + 1]; q++) add(S.iperm[gi[q]]);
       }
+      for (int32_t c : kids[s])
+        for (int32_t r : below[c]) add(r);
+      std::sort(B.begin(), B.end());
     }
   }
   S.sn_rowptr.assign(S.ns + 1, 0);

@@ -492,13 +492,14 @@ def test_factor_regularized_matches_oracle(lam):
             assert rel(np.concatenate([dx, dy]), np.concatenate([odx, ody])) <= 1e-6
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_factor_regularized_sequence_matches_oracle(precision):
+def test_factor_regularized_sequence_matches_oracle(precision="fp64"):
     """A sequence of matrices on one handle: the device loop (one graph
     launch per matrix) carries delta_1 as Sec. 4.1 says, back to the
     previous matrix's value after a failed unshifted trial, and accepts the
     same delta_1 as the oracle at every step; kkt_set_delta_prev(0) starts a
-    new sequence. Each accepted factor then solves to the oracle's RR."""
+    new sequence. Each accepted factor then solves to the oracle's RR. FP64
+    only: the shifts here (~1e-8 against ||H_gamma|| ~ 1e3) lie below the
+    FP32 factor's rounding, so its pivots decide at another threshold."""
     from test_oracle import nullspace_indefinite_system
     lams = [-2.5e-8, -1e-8, 0.5, -5e-9, -5e-8]
     base, _, _ = nullspace_indefinite_system(lams[0])
