@@ -88,12 +88,12 @@ typedef struct kkt_options {
                           launches; for measurement runs only) */
   int32_t nd_leaf;     /* nested dissection stops at components of at most this many
                           vertices (ordered naturally); default 64 */
-  int32_t tensor_cores;/* KKT_MIXED: 1 = fronts with >= 128 update rows take the SYRK on the
-                          tcgen05 tensor cores (operands split into three TF32 parts, six
-                          partial products, FP32 accumulation in tensor memory);
-                          0 (default) = FP32 FMA units only, which is faster on the
-                          shallow fronts of a 2-D grid and more accurate (the tensor
-                          core's FP32 accumulation does not round to nearest) */
+  int32_t tensor_cores;/* KKT_MIXED: 1 (default) = fronts with >= 128 update rows and >= 32
+                          columns take their update-matrix product (SYRK) on the tcgen05
+                          tensor cores: operands split into two TF32 parts, three partial
+                          products, FP32 accumulation in tensor memory drained into FP32
+                          registers every 64 K and summed there with round-to-nearest;
+                          0 = FP32 FMA units only */
   int32_t solve_ctas;  /* resident solve-kernel CTAs per SM, 2..4 (0 = 2); the grid is this
                           many per SM or fewer if shared memory does not allow it */
   int32_t solve_ent;   /* L entries staged per triangular-solve work item, 2048..32768

@@ -78,6 +78,7 @@ struct kkt_handle_s {
   ChunkDesc* cdesc;
   HeadDesc* hdesc;
   uint8_t* tmaps;
+  uint8_t* tc_maps = nullptr;   // tensor maps of the tensor-core fronts' panels (FP32)
   // values and workspace
   double *Hv, *Jv;
   void *L, *U, *v, *Linv;
@@ -161,6 +162,38 @@ static bool build_tensor_maps(const Plan& P, void* L, size_t es, std::vector<uin
   return true;
 }
 
+// Tensor maps of the fronts whose updates run on the tensor cores: the
+// whole FP32 panel (ld rows x w columns; rows past ld and columns past w
+// read as zeros), boxes of kTcBoxRows rows x 32 columns.
+static bool build_tc_maps(const Plan& P, void* L, std::vector<uint8_t>& out) {
+  out.assign(P.tc_front.size() * 128, 0);
+  if (P.tc_front.empty()) return true;
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn) {
+    cudaGetLastError();
+    return false;
+  }
+  PFN_cuTensorMapEncodeTiled_v12000 encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  for (size_t k = 0; k < P.tc_front.size(); k++) {
+    const int32_t s = P.tc_front[k];
+    const int32_t ld = P.sld[s], w = P.sw[s];
+    if (ld < kTcBoxRows || w < kTcMinWidth || (ld * 4) % 16 || (P.poff[s] * 4) % 16) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)w};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+    const cuuint32_t boxd[2] = {(cuuint32_t)kTcBoxRows, 32};
+    const cuuint32_t estr[2] = {1, 1};
+    CUtensorMap* m = (CUtensorMap*)(out.data() + k * 128);
+    void* g = (char*)L + (size_t)P.poff[s] * 4;
+    if (encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, g, dims, strides, boxd, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  return true;
+}
+
 static kkt_status cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return KKT_OK;
   cudaGetLastError();
@@ -195,7 +228,7 @@ void kkt_default_options(kkt_options* o) {
   o->spin_cycles = 0;
   o->profile = 0;
   o->nd_leaf = 64;
-  o->tensor_cores = 0;
+  o->tensor_cores = 1;
 }
 
 const char* kkt_status_string(kkt_status s) {
@@ -358,6 +391,10 @@ kkt_status kkt_analyse(int64_t n, int64_t m, const int64_t* Hp, const int32_t* H
     if (!A.failed) {
       if (!build_tensor_maps(P, h->L, es, maps)) { kkt_destroy(h); return KKT_ERR_CUDA; }
       h->tmaps = A.upload(maps);
+      if (!f64) {
+        if (!build_tc_maps(P, h->L, maps)) { kkt_destroy(h); return KKT_ERR_CUDA; }
+        h->tc_maps = A.upload(maps);
+      }
     }
   }
   h->rhx = A.alloc<double>(n);
@@ -429,6 +466,7 @@ static cudaError_t factor_launches(kkt_handle h, cudaStream_t st, Prof* prof) {
   FacLists fl;
   fl.it_potrf = h->it_potrf; fl.it_trsm = h->it_trsm; fl.it_pupd = h->it_pupd;
   fl.it_syrk = h->it_syrk; fl.it_eadd = h->it_eadd; fl.it_syrk_tc = h->it_syrk_tc;
+  fl.tc_maps = h->tc_maps;
   fl.it_block = h->it_block; fl.it_syrk128 = h->it_syrk128; fl.it_dstore = h->it_dstore;
   fl.slot_pos = h->slot_pos; fl.src_ptr = h->src_ptr; fl.srcA = h->srcA; fl.srcB = h->srcB;
   fl.nslot = (int64_t)h->P.slot_pos.size();

@@ -461,191 +461,6 @@ __global__ void __launch_bounds__(256) k_extend_add(const int4* __restrict__ ite
 }
 
 
-// ------------------------------------------------------- SYRK on tcgen05
-// FP32 fronts with rb >= 128: U_s = -L21 L21^T on 128 x 128 tiles with the
-// 5th-generation tensor cores. Each operand element x is split into three
-// TF32 parts, hi = tf32(x), mid = tf32(x - hi), lo = tf32(x - hi - mid), and
-// the product is taken as hi*hi + hi*mid + mid*hi + hi*lo + lo*hi + mid*mid
-// with FP32 accumulation in tensor memory (split-precision products after
-// Ootomo & Yokota, "Recovering single precision accuracy from Tensor Cores
-// while surpassing the FP32 theoretical peak performance", 2022; the two-part
-// hi/lo form carries ~21 bits, which cost the refinement an extra pass).
-// Operands are staged K-major in shared memory in 8-row x 16-byte core
-// matrices (no swizzle): element (i, k) at (i/8)*SBO + (k/4)*LBO + (i%8)*16 + (k%4)*4.
-namespace tc {
-constexpr int KC = 32;                       // K elements staged per step
-constexpr uint32_t LBO = 128;                // bytes between core matrices along K
-constexpr uint32_t SBO = (KC / 4) * 128;     // bytes between 8-row groups
-constexpr uint32_t TILE = 128 * KC * 4;      // one 128 x KC operand tile (16 KB)
-
-__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ uint64_t desc(uint32_t addr) {
-  uint64_t d = (uint64_t)((addr & 0x3FFFF) >> 4);
-  d |= (uint64_t)((LBO >> 4) & 0x3FFF) << 16;
-  d |= (uint64_t)((SBO >> 4) & 0x3FFF) << 32;
-  d |= (uint64_t)1 << 46;                    // descriptor version of this architecture
-  return d;
-}
-__device__ __forceinline__ float tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
-__device__ __forceinline__ uint32_t koff(int i, int k) {
-  return (uint32_t)((i >> 3) * SBO + (k >> 2) * LBO + (i & 7) * 16 + (k & 3) * 4);
-}
-__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-}  // namespace tc
-
-__global__ void __launch_bounds__(128) k_syrk_tc(const int4* __restrict__ items, FacArgs<float> a) {
-  extern __shared__ __align__(1024) unsigned char smem_tc[];
-  __shared__ __align__(8) unsigned long long mbar;
-  __shared__ uint32_t tmem_base;
-  const int4 it = items[blockIdx.x];
-  const int s = it.x, ti = it.y, tj = it.z;
-  const int w = a.sw[s], nr = a.snr[s], ld = a.sld[s];
-  const int rb = nr - w;
-  const bool diag = ti == tj;
-  const float* P = a.L + a.poff[s];
-  float* U = a.U + a.uoff[s];
-  const int i0 = ti * 128, j0 = tj * 128;
-  // three TF32 parts (hi, mid, lo) of each operand
-  unsigned char* Ap[3] = {smem_tc, smem_tc + tc::TILE, smem_tc + 2 * tc::TILE};
-  unsigned char* Bp[3];
-  for (int q = 0; q < 3; q++) Bp[q] = diag ? Ap[q] : smem_tc + (3 + q) * tc::TILE;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(tc::saddr(&tmem_base)));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::saddr(&mbar)));
-    asm volatile("fence.mbarrier_init.release.cluster;");
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  const uint32_t tmem = tmem_base;
-  // D = F32, A = B = TF32, K-major, N = 128, M = 128
-  const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | (16u << 17) | (8u << 24);
-  // thread tid owns row tid of both operand tiles and loads its KC columns
-  const bool ra = i0 + tid < rb, rbv = !diag && (j0 + tid < rb);
-  const float* pa = P + (w + i0 + tid);
-  const float* pb = P + (w + j0 + tid);
-  float xa[tc::KC], xb[tc::KC];
-  auto load = [&](int k0) {
-#pragma unroll
-    for (int k = 0; k < tc::KC; k++) {
-      const bool kin = k0 + k < w;
-      xa[k] = (kin && ra) ? pa[(int64_t)(k0 + k) * ld] : 0.f;
-      xb[k] = (kin && rbv) ? pb[(int64_t)(k0 + k) * ld] : 0.f;
-    }
-  };
-  auto store = [&](const float* x, unsigned char* const* dst) {
-#pragma unroll
-    for (int q = 0; q < tc::KC / 4; q++) {
-      float4 h, m, l;
-      float* hp = &h.x; float* mp = &m.x; float* lp = &l.x;
-#pragma unroll
-      for (int r = 0; r < 4; r++) {
-        const float v = x[4 * q + r];
-        const float vh = tc::tf32(v);
-        const float r1 = v - vh;
-        const float vm = tc::tf32(r1);
-        hp[r] = vh;
-        mp[r] = vm;
-        lp[r] = tc::tf32(r1 - vm);
-      }
-      const uint32_t o = tc::koff(tid, 4 * q);
-      *(float4*)(dst[0] + o) = h;
-      *(float4*)(dst[1] + o) = m;
-      *(float4*)(dst[2] + o) = l;
-    }
-  };
-  unsigned phase = 0;
-  bool ok = true;
-  load(0);
-  for (int k0 = 0; k0 < w && ok; k0 += tc::KC) {
-    store(xa, Ap);
-    if (!diag) store(xb, Bp);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      for (int kk = 0; kk < tc::KC / 8; kk++) {
-        const uint32_t off = kk * 2 * tc::LBO;
-        uint64_t da[3], db[3];
-        for (int q = 0; q < 3; q++) {
-          da[q] = tc::desc(tc::saddr(Ap[q]) + off);
-          db[q] = tc::desc(tc::saddr(Bp[q]) + off);
-        }
-        // hi*hi + hi*mid + mid*hi + hi*lo + lo*hi + mid*mid
-        tc::mma(tmem, da[0], db[0], idesc, (k0 > 0 || kk > 0) ? 1u : 0u);
-        tc::mma(tmem, da[0], db[1], idesc, 1u);
-        tc::mma(tmem, da[1], db[0], idesc, 1u);
-        tc::mma(tmem, da[0], db[2], idesc, 1u);
-        tc::mma(tmem, da[2], db[0], idesc, 1u);
-        tc::mma(tmem, da[1], db[1], idesc, 1u);
-      }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       tc::saddr(&mbar))
-                   : "memory");
-    }
-    // next chunk's loads overlap this chunk's MMAs
-    if (k0 + tc::KC < w) load(k0 + tc::KC);
-    // the MMAs read the staged tiles: wait (bounded) before refilling them
-    const long long t0 = clock64();
-    uint32_t done = 0;
-    while (!done) {
-      asm volatile(
-          "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-          : "=r"(done)
-          : "r"(tc::saddr(&mbar)), "r"(phase)
-          : "memory");
-      if (!done && clock64() - t0 > kSpinCycles) {
-        ok = false;
-        break;
-      }
-    }
-    phase ^= 1;
-    ok = __syncthreads_and(ok);   // every thread takes the same exit
-  }
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  if (!ok) {
-    if (tid == 0) atomicExch(&a.st->abort, 2);
-  } else {
-    // warp w owns accumulator rows 32w..32w+31 (tensor-memory lanes)
-    const int gi = i0 + 32 * warp + lane;
-    for (int c0 = 0; c0 < 128; c0 += 32) {
-      uint32_t r[32];
-      const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-            "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-            "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-          : "r"(ta));
-      asm volatile("tcgen05.wait::ld.sync.aligned;");
-      if (gi < rb) {
-#pragma unroll
-        for (int j = 0; j < 32; j++) {
-          const int gj = j0 + c0 + j;
-          if (gj < rb && gi >= gj) U[(int64_t)gi + (int64_t)gj * rb] = -__uint_as_float(r[j]);
-        }
-      }
-    }
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;");
-  __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
-}
-
 static cudaError_t launch_syrk128(const int4* items, int64_t cnt, const FacArgs<float>& a, cudaStream_t st) {
   k_syrk128<<<(unsigned)cnt, 256, 0, st>>>(items, a);
   return cudaGetLastError();
@@ -655,16 +470,13 @@ static cudaError_t launch_syrk128(const int4*, int64_t, const FacArgs<T>&, cudaS
   return cudaErrorNotSupported;   // FP64 fronts keep the 64 x 64 tiles
 }
 
-static cudaError_t launch_syrk_tc(const int4* items, int64_t cnt, const FacArgs<float>& a, cudaStream_t st) {
-  const int smem = 6 * (int)tc::TILE;   // 96 KB: two CTAs (2 x 128 tensor-memory columns) per SM
-  cudaError_t e = cudaFuncSetAttribute(k_syrk_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e) return e;
-  k_syrk_tc<<<(unsigned)cnt, 128, smem, st>>>(items, a);
-  return cudaGetLastError();
+static cudaError_t launch_syrk_tc(const int4* items, int64_t cnt, const uint8_t* maps, const FacArgs<float>& a,
+                                  cudaStream_t st) {
+  return launch_tc_update(items, cnt, maps, a, st);
 }
 template <typename T>
-static cudaError_t launch_syrk_tc(const int4*, int64_t, const FacArgs<T>&, cudaStream_t) {
-  return cudaErrorNotSupported;   // tensor-core SYRK is the FP32 factor's
+static cudaError_t launch_syrk_tc(const int4*, int64_t, const uint8_t*, const FacArgs<T>&, cudaStream_t) {
+  return cudaErrorNotSupported;   // the tensor-core updates are the FP32 factor's
 }
 
 // ---------------------------------------------------------- triangle inverses
@@ -753,7 +565,7 @@ cudaError_t launch_factor(const FacArgs<T>& a, const FacLists& fl, const double*
       case 3: k_syrk<T><<<(unsigned)L.cnt, 256, 0, st>>>(fl.it_syrk + L.off, a); break;
       case 4: k_extend_add<T><<<(unsigned)L.cnt, 256, 0, st>>>(fl.it_eadd + L.off, a); break;
       case 6:
-        if ((e = launch_syrk_tc(fl.it_syrk_tc + L.off, L.cnt, a, st))) return e;
+        if ((e = launch_syrk_tc(fl.it_syrk_tc + 2 * L.off, L.cnt, fl.tc_maps, a, st))) return e;
         break;
       case 7: k_block<T><<<(unsigned)L.cnt, kTR, 0, st>>>(fl.it_block + 3 * L.off, L.kb, a); break;
       case 8:

@@ -35,6 +35,7 @@ cudaError_t prof_end(Prof* pr, int kind, cudaStream_t st);
 
 struct FacLists {
   const int4 *it_potrf, *it_trsm, *it_pupd, *it_syrk, *it_eadd, *it_syrk_tc, *it_block, *it_syrk128, *it_dstore;
+  const uint8_t* tc_maps;   // one 128-byte tensor map per tensor-core front (Plan::tc_front)
   const int64_t *slot_pos, *src_ptr;
   const int32_t *srcA, *srcB;
   int64_t nslot, panel_total, u_total;
@@ -50,6 +51,10 @@ struct InvArgs {
 };
 template <typename T>
 cudaError_t launch_tri_inv(const InvArgs<T>& a, int64_t npieces, int max_pw, cudaStream_t st);
+
+// Tensor-core update tiles (tc_update.cu): items of 8 ints (Plan::it_syrk_tc).
+cudaError_t launch_tc_update(const int4* items, int64_t cnt, const uint8_t* maps, const FacArgs<float>& a,
+                             cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_factor(const FacArgs<T>& a, const FacLists& fl, const double* dg, cudaStream_t st,

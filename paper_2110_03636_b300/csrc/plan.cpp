@@ -176,19 +176,34 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
     P.dsc_total = std::max(P.dsc_total, (int64_t)slot * kPB * kPB);
     const int64_t cd = (int64_t)P.it_dstore.size() / 4 - od;
     if (cd) P.launches.push_back({9, 0, od, cd});
-    const int64_t o2 = (int64_t)P.it_syrk.size() / 4, o6 = (int64_t)P.it_syrk_tc.size() / 4,
+    const int64_t o2 = (int64_t)P.it_syrk.size() / 4, o6 = (int64_t)P.it_syrk_tc.size() / 8,
                   o8 = (int64_t)P.it_syrk128.size() / 4;
+    // tensor-core tiles of the level's fronts, widest (longest K) first, so
+    // the persistent kernel's round-robin hands every CTA a similar share
+    std::vector<int32_t> tcf;
     for (int32_t s : F) {
       const int64_t rb = P.snr[s] - P.sw[s];
-      const bool tcs = tc_syrk && rb >= kTcMinRows;
-      const bool big = !tcs && f32 && rb >= kBigRows;
-      const int64_t tile = (tcs || big) ? 128 : kST;
+      const bool tcs = tc_syrk && rb >= kTcMinRows && P.sw[s] >= kTcMinWidth;
+      if (tcs) { tcf.push_back(s); continue; }
+      const bool big = f32 && rb >= kBigRows;
+      const int64_t tile = big ? 128 : kST;
       const int64_t nt = cdiv(rb, tile);
-      auto& list = tcs ? P.it_syrk_tc : (big ? P.it_syrk128 : P.it_syrk);
+      auto& list = big ? P.it_syrk128 : P.it_syrk;
       for (int64_t ti = 0; ti < nt; ti++)
         for (int64_t tj = 0; tj <= ti; tj++) list.insert(list.end(), {s, (int32_t)ti, (int32_t)tj, 0});
     }
-    const int64_t c2 = (int64_t)P.it_syrk.size() / 4 - o2, c6 = (int64_t)P.it_syrk_tc.size() / 4 - o6,
+    std::stable_sort(tcf.begin(), tcf.end(), [&](int32_t x, int32_t y) { return P.sw[x] > P.sw[y]; });
+    for (int32_t s : tcf) {
+      const int32_t mi = (int32_t)P.tc_front.size();
+      P.tc_front.push_back(s);
+      const int32_t w = P.sw[s];
+      const int64_t nt = cdiv(P.snr[s] - w, 128);
+      for (int64_t ti = 0; ti < nt; ti++)
+        for (int64_t tj = 0; tj <= ti; tj++)
+          P.it_syrk_tc.insert(P.it_syrk_tc.end(),
+                              {s, w + (int32_t)ti * 128, w + (int32_t)tj * 128, mi, 0, w, 0, 0});
+    }
+    const int64_t c2 = (int64_t)P.it_syrk.size() / 4 - o2, c6 = (int64_t)P.it_syrk_tc.size() / 8 - o6,
                   c8 = (int64_t)P.it_syrk128.size() / 4 - o8;
     if (c6) P.launches.push_back({6, 0, o6, c6});
     if (c8) P.launches.push_back({8, 0, o8, c8});

@@ -74,7 +74,9 @@ struct Plan {
   std::vector<int32_t> it_trsm;             // (s, row tile) pairs
   std::vector<int32_t> it_pupd;             // (s, row tile, col tile) triples (kFItem ints each)
   std::vector<int32_t> it_syrk;             // (s, ti, tj) triples, 64 x 64 tiles
-  std::vector<int32_t> it_syrk_tc;          // (s, ti, tj), 128 x 128 tensor-core tiles
+  std::vector<int32_t> it_syrk_tc;          // tensor-core update tiles, 8 ints each: (s, panel row of A,
+                                            // panel row of B, tensor map), (K begin, K end, mode, 0)
+  std::vector<int32_t> tc_front;            // fronts with a tensor map (index = map number)
   std::vector<int32_t> it_block;            // (s, row tile, slot) per fused block step (kFItem ints each)
   std::vector<int32_t> it_syrk128;          // (s, ti, tj), 128 x 128 FP32 register-tiled SYRK
   std::vector<int32_t> it_dstore;           // (s, kb, slot): factored diagonal tile -> panel, per level
@@ -145,8 +147,14 @@ inline int64_t packed_inv_size(int64_t pw) {
   return t;
 }
 
-// tc_syrk: fronts with rb >= kTcMinRows get 128 x 128 tensor-core SYRK tiles
+// tc_syrk: fronts with rb >= kTcMinRows and at least kTcMinWidth columns get
+// 128 x 128 tensor-core SYRK tiles; their panels are read through tensor maps
+// with boxes of kTcBoxRows rows x 32 columns; the persistent kernel runs at
+// most kTcGrid CTAs (one per SM)
 constexpr int kTcMinRows = 128;
+constexpr int kTcMinWidth = 32;
+constexpr int kTcBoxRows = 132;
+constexpr int kTcGrid = 148;
 // f32 (FP32 factor): fronts with rb >= kBigRows get 128 x 128 register-tiled SYRK
 // tiles, and each block step fuses POTRF into the TRSM launch
 constexpr int kBigRows = 128;
