@@ -97,6 +97,19 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
   // block-step and in-panel-update items carry their front's width, rows,
   // leading dimension, first column and panel offset, so their kernels reach
   // the panel after one load instead of two dependent ones
+  // tensor-core fronts: a tensor map per front (index in P.tc_front)
+  std::vector<int32_t> map_idx(ns, -1);
+  auto map_of = [&](int32_t sn) {
+    if (map_idx[sn] < 0) {
+      map_idx[sn] = (int32_t)P.tc_front.size();
+      P.tc_front.push_back(sn);
+    }
+    return map_idx[sn];
+  };
+  // fronts at least kTcPanelMinWidth wide take the in-panel update beyond
+  // each outer block on the tensor cores (narrower fronts give launches too
+  // small to pay for the persistent kernel's start)
+  auto tc_panel = [&](int32_t sn) { return tc_syrk && P.sw[sn] >= kTcPanelMinWidth; };
   auto push_fitem = [&](std::vector<int32_t>& v, int32_t sn, int32_t x, int32_t y) {
     const int64_t po = P.poff[sn];
     v.insert(v.end(), {sn, x, y, 0, P.sw[sn], P.snr[sn], P.sld[sn], P.sfirst[sn],
@@ -157,14 +170,18 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
       const int64_t cpo = (int64_t)P.it_potrf.size() / 4 - opo, ctr = (int64_t)P.it_trsm.size() / 4 - otr;
       if (cpo) P.launches.push_back({0, kb, opo, cpo});
       if (ctr) P.launches.push_back({1, kb, otr, ctr});
-      // right-looking update of the panel columns after the block
+      // right-looking update of the panel columns after the block; fronts
+      // on the tensor-core path update only the columns of their current
+      // kTcPB-column outer block here, and the columns beyond it once per
+      // outer block (below)
       const int64_t o1 = (int64_t)P.it_pupd.size() / kFItem;
       for (int32_t s : F) {
         const int32_t c0 = kb * kPB;
         if (c0 >= P.sw[s]) continue;
         const int32_t bw = std::min(kPB, P.sw[s] - c0);
         const int32_t jstart = c0 + bw;
-        for (int32_t ct = 0; jstart + ct * kPB < P.sw[s]; ct++) {
+        const int32_t jend = tc_panel(s) ? std::min(P.sw[s], (c0 / kTcPB + 1) * kTcPB) : P.sw[s];
+        for (int32_t ct = 0; jstart + ct * kPB < jend; ct++) {
           const int32_t cstart = jstart + ct * kPB;
           const int64_t nrt = cdiv(P.snr[s] - cstart, kUR);
           for (int64_t rt = 0; rt < nrt; rt++) push_fitem(P.it_pupd, s, (int32_t)rt, ct);
@@ -172,6 +189,21 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
       }
       const int64_t c1 = (int64_t)P.it_pupd.size() / kFItem - o1;
       if (c1) P.launches.push_back({2, kb, o1, c1});
+      // end of an outer block: the columns beyond it -= L[rows, block] L[cols, block]^T,
+      // K = the block's kTcPB columns, on the tensor cores (mode 1)
+      if ((kb + 1) * kPB % kTcPB == 0) {
+        const int64_t o6 = (int64_t)P.it_syrk_tc.size() / 8;
+        const int32_t oe = (kb + 1) * kPB;          // first column after the outer block
+        for (int32_t s : F) {
+          if (!tc_panel(s) || oe >= P.sw[s]) continue;
+          const int32_t mi = map_of(s);
+          for (int32_t cs = oe; cs < P.sw[s]; cs += 128)
+            for (int32_t rs = cs; rs < P.snr[s]; rs += 128)
+              P.it_syrk_tc.insert(P.it_syrk_tc.end(), {s, rs, cs, mi, oe - kTcPB, oe, 1, 0});
+        }
+        const int64_t c6 = (int64_t)P.it_syrk_tc.size() / 8 - o6;
+        if (c6) P.launches.push_back({6, kb, o6, c6});
+      }
     }
     P.dsc_total = std::max(P.dsc_total, (int64_t)slot * kPB * kPB);
     const int64_t cd = (int64_t)P.it_dstore.size() / 4 - od;
@@ -194,8 +226,7 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
     }
     std::stable_sort(tcf.begin(), tcf.end(), [&](int32_t x, int32_t y) { return P.sw[x] > P.sw[y]; });
     for (int32_t s : tcf) {
-      const int32_t mi = (int32_t)P.tc_front.size();
-      P.tc_front.push_back(s);
+      const int32_t mi = map_of(s);
       const int32_t w = P.sw[s];
       const int64_t nt = cdiv(P.snr[s] - w, 128);
       for (int64_t ti = 0; ti < nt; ti++)

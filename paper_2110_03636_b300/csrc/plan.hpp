@@ -152,6 +152,8 @@ inline int64_t packed_inv_size(int64_t pw) {
 // with boxes of kTcBoxRows rows x 32 columns; the persistent kernel runs at
 // most kTcGrid CTAs (one per SM)
 constexpr int kTcMinRows = 128;
+constexpr int kTcPB = 128;        // outer column block of the tensor-core in-panel update
+constexpr int kTcPanelMinWidth = 1024;   // narrowest front that takes it
 constexpr int kTcMinWidth = 32;
 constexpr int kTcBoxRows = 132;
 constexpr int kTcGrid = 148;

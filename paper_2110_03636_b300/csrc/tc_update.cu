@@ -317,6 +317,17 @@ __global__ void __launch_bounds__(tcu::kThreads, 1)
     for (int64_t t = blockIdx.x; t < nitems && ok; t += gridDim.x) {
       const int4 i0 = items[2 * t], i1 = items[2 * t + 1];
       const int nk = (i1.y - i1.x + KC - 1) / KC;
+      if (i1.z != 0) {
+        // in-panel tile: pull this row's 128 outputs into L2 while the MMAs
+        // run, so the read-modify-write below waits on L2, not on HBM
+        const int s = i0.x;
+        const int ld = a.sld[s], nr = a.snr[s], w = a.sw[s];
+        const int row = i0.y + i;
+        const float* P = a.L + a.poff[s] + row;
+        if (row < nr)
+          for (int j = 0; j < 128 && i0.z + j < w; j++)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(P + (int64_t)(i0.z + j) * ld));
+      }
       float acc[128];
 #pragma unroll
       for (int j = 0; j < 128; j++) acc[j] = 0.f;
@@ -364,14 +375,24 @@ __global__ void __launch_bounds__(tcu::kThreads, 1)
           }
         }
       } else {
+        // read-modify-write in batches of 32 independent loads
         const int ld = a.sld[s];
         const int row = i0.y + i, col0 = i0.z;
-        float* P = a.L + a.poff[s];
+        float* __restrict__ P = a.L + a.poff[s] + row;
         if (row < nr) {
 #pragma unroll
-          for (int j = 0; j < 128; j++) {
-            const int col = col0 + j;
-            if (col < w && row >= col) P[(int64_t)row + (int64_t)col * ld] -= acc[j];
+          for (int c4 = 0; c4 < 4; c4++) {
+            float v[32];
+#pragma unroll
+            for (int j = 0; j < 32; j++) {
+              const int col = col0 + c4 * 32 + j;
+              v[j] = (col < w && row >= col) ? P[(int64_t)col * ld] : 0.f;
+            }
+#pragma unroll
+            for (int j = 0; j < 32; j++) {
+              const int col = col0 + c4 * 32 + j;
+              if (col < w && row >= col) P[(int64_t)col * ld] = v[j] - acc[c4 * 32 + j];
+            }
           }
         }
       }

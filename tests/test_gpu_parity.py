@@ -120,22 +120,22 @@ def panel_error_vs_oracle(s, sys, ordering="natural"):
     return worst, float(np.abs(Lx).max())
 
 
-def block_front_system(seed=5):
-    """n = 1000, natural order: block A (columns 0..599) and block B
-    (600..699) are dense and both couple densely to block C (700..999), A
-    and B do not couple. The etree gives fundamental supernodes A (600
-    columns, 300 rows below), B (100 columns, 300 below) and C; B + C is
+def block_front_system(wa=600, seed=5):
+    """n = wa + 400, natural order: block A (columns 0..wa-1) and block B
+    (the next 100) are dense and both couple densely to block C (the last
+    300), A and B do not couple. The etree gives fundamental supernodes A
+    (wa columns, 300 rows below), B (100 columns, 300 below) and C; B + C is
     wider than the relaxation limit and A is not C's last child, so A stays
-    a 600-column front: its update matrix is a K = 600 product of 300 rows
+    a wa-column front: its update matrix is a K = wa product of 300 rows
     (ragged 128-row tiles). J rows stay inside one block."""
     from test_oracle import make_sys
     rng = np.random.default_rng(seed)
-    n, m = 1000, 60
-    blocks = [(0, 600), (600, 700), (700, 1000)]
+    n, m = wa + 400, 60
+    blocks = [(0, wa), (wa, wa + 100), (wa + 100, n)]
     mask = np.zeros((n, n), bool)
     for lo, hi in blocks:
         mask[lo:hi, lo:hi] = True
-    mask[0:700, 700:1000] = True
+    mask[0:wa + 100, wa + 100:n] = True
     mask = mask | mask.T
     H = np.where(mask, rng.uniform(-1, 1, (n, n)), 0.0) / np.sqrt(n)
     H = np.triu(H, 1)
@@ -150,14 +150,16 @@ def block_front_system(seed=5):
     return make_sys(H, J, rng.standard_normal(n), rng.standard_normal(m), gamma=1e2)
 
 
-def test_tensor_core_updates_match_oracle_on_a_wide_front():
+@pytest.mark.parametrize("wa", [600, 1100])
+def test_tensor_core_updates_match_oracle_on_a_wide_front(wa):
     """The FP32 factor with the tcgen05 split-TF32 updates (three products,
     tensor-memory accumulation drained to FP32 registers per 64 K) against
-    the FP64 oracle's L, entry by entry, on a front with K = 600 and 300
-    update rows: within FP32 rounding of the largest entry, and no worse
-    than 4x the FP32 FMA factor's own error. Both solve to the oracle's
-    solution."""
-    sys = block_front_system()
+    the FP64 oracle's L, entry by entry, on a front with K = wa and 300
+    update rows (wa = 1100 also takes the in-panel update beyond each
+    128-column outer block on the tensor cores): within FP32 rounding of the
+    largest entry, and no worse than 4x the FP32 FMA factor's own error.
+    Both solve to the oracle's solution."""
+    sys = block_front_system(wa)
     _, _, odx, ody, oinfo = O.solve_system(sys, ordering="natural")
     assert oinfo["status"] == 0
     errs = {}
@@ -166,7 +168,7 @@ def test_tensor_core_updates_match_oracle_on_a_wide_front():
         assert code == 0
         g = K.kkt_get_symbolic(s.h)
         st = g["sn_start"]
-        assert 600 in np.diff(st)                     # the wide front exists
+        assert wa in np.diff(st)                      # the wide front exists
         err, lmax = panel_error_vs_oracle(s, sys)
         errs[tcs] = err
         assert err <= 2e-5 * lmax, (tcs, err, lmax)
