@@ -142,6 +142,9 @@ typedef struct kkt_symbolic_info {
   int64_t fwd_depth, bwd_depth;  /* longest dependency chains of the two triangular sweeps */
   int64_t nsub;        /* small subtrees solved whole by one CTA */
   int64_t nitems;      /* work items per triangular sweep */
+  double tc_flops;     /* flops the factorization runs on the tensor cores (update-matrix
+                          products and in-panel updates of the tensor-core fronts, counted
+                          as 2 per multiply-add of the FP32 product they stand for) */
 } kkt_symbolic_info;
 
 /* Defaults: Algorithm 1's typical parameters (gamma 1e4, delta_2 1e-9), CG
@@ -300,6 +303,21 @@ kkt_status kkt_get_factor_panels(kkt_handle h, double* panels);
  * event pair around each solve pass, at no cost to the pass). reset != 0
  * clears the counters after reading. */
 kkt_status kkt_get_profile(kkt_handle h, double* ms, int64_t* launches, int32_t reset);
+
+/* Switches the per-kernel timing of kkt_get_profile on (1) or off (0) on an
+ * existing handle, as opt.profile = 1 does at analysis: every launch is
+ * bracketed by CUDA events and the factorization runs launch by launch
+ * instead of as one graph (for measurement runs only). The item timeline of
+ * kkt_get_solve_trace still needs opt.profile = 1 at analysis. */
+kkt_status kkt_set_profile(kkt_handle h, int32_t on);
+
+/* A new handle for the same pattern with other options (e.g. the other
+ * precision), reusing src's ordering and symbolic factorization (Sec. 2:
+ * they depend on the pattern only); only the numeric plan is rebuilt and
+ * the device memory allocated. opt.ordering, opt.nd_leaf and the relaxation
+ * parameters must equal src's (KKT_ERR_INVALID otherwise). src stays valid.
+ * Errors as kkt_analyse. */
+kkt_status kkt_analyse_like(kkt_handle src, const kkt_options* opt, kkt_handle* out);
 
 /* Cycle counters of the persistent solve kernel summed over its CTAs (thread
  * 0 of each), for handles created with opt.profile = 1; host uint64_t[32]:

@@ -50,7 +50,7 @@ class kkt_symbolic_info(C.Structure):
                 ("panel_entries", C.c_int64), ("update_entries", C.c_int64), ("sn_rows_total", C.c_int64),
                 ("npieces", C.c_int64), ("nchunks", C.c_int64), ("nlevels", C.c_int32), ("pad", C.c_int32),
                 ("flops", C.c_double), ("device_bytes", C.c_double), ("fwd_depth", C.c_int64),
-                ("bwd_depth", C.c_int64), ("nsub", C.c_int64), ("nitems", C.c_int64)]
+                ("bwd_depth", C.c_int64), ("nsub", C.c_int64), ("nitems", C.c_int64), ("tc_flops", C.c_double)]
 
 
 def _load():
@@ -67,6 +67,8 @@ def _load():
     L.kkt_solve_multi.argtypes = [P, I32, P, P, P, P, P, P]
     L.kkt_factor_regularized.argtypes = [P, P, P, D, D, D, P, P]
     L.kkt_set_delta_prev.argtypes = [P, D]
+    L.kkt_set_profile.argtypes = [P, I32]
+    L.kkt_analyse_like.argtypes = [P, C.POINTER(kkt_options), C.POINTER(P)]
     L.kkt_factor_batch.argtypes = [P, I32, P, P, D, D, P, P]
     L.kkt_solve_batch.argtypes = [P, I32, P, P, P, P, P, P, P]
     L.kkt_factor_solve_host.argtypes = [P, P, P, D, D, P, P, P, P, P]
@@ -92,7 +94,7 @@ def _load():
     L.kkt_destroy_4x4.argtypes = [P]
     L.kkt_status_string.argtypes = [I32]
     L.kkt_status_string.restype = C.c_char_p
-    for nm in ("kkt_analyse", "kkt_analyse_host", "kkt_factor", "kkt_solve", "kkt_solve_multi", "kkt_factor_batch", "kkt_solve_batch", "kkt_factor_regularized", "kkt_set_delta_prev", "kkt_factor_solve_host", "kkt_hsolve", "kkt_get_info",
+    for nm in ("kkt_analyse", "kkt_analyse_host", "kkt_factor", "kkt_solve", "kkt_solve_multi", "kkt_factor_batch", "kkt_solve_batch", "kkt_factor_regularized", "kkt_set_delta_prev", "kkt_set_profile", "kkt_analyse_like", "kkt_factor_solve_host", "kkt_hsolve", "kkt_get_info",
                "kkt_inertia", "kkt_symbolic_info_get", "kkt_get_symbolic", "kkt_get_factor_panels", "kkt_get_profile", "kkt_get_solve_counters", "kkt_residual_noalloc",
                "kkt_get_solve_trace", "kkt_get_solve_item_order", "kkt_destroy", "kkt_analyse_4x4", "kkt_analyse_4x4_host", "kkt_get_4x4_pattern", "kkt_factor_4x4",
                "kkt_solve_4x4", "kkt_destroy_4x4"):
@@ -101,7 +103,7 @@ def _load():
 
 
 _lib = _load()
-EXPORTED = ("kkt_default_options", "kkt_analyse", "kkt_analyse_host", "kkt_factor", "kkt_solve", "kkt_solve_multi", "kkt_factor_batch", "kkt_solve_batch", "kkt_factor_regularized", "kkt_set_delta_prev", "kkt_factor_solve_host",
+EXPORTED = ("kkt_default_options", "kkt_analyse", "kkt_analyse_host", "kkt_factor", "kkt_solve", "kkt_solve_multi", "kkt_factor_batch", "kkt_solve_batch", "kkt_factor_regularized", "kkt_set_delta_prev", "kkt_set_profile", "kkt_analyse_like", "kkt_factor_solve_host",
             "kkt_hsolve", "kkt_get_info", "kkt_inertia", "kkt_symbolic_info_get", "kkt_get_symbolic",
             "kkt_get_factor_panels", "kkt_get_profile", "kkt_get_solve_counters", "kkt_residual_noalloc",
             "kkt_get_solve_trace", "kkt_get_solve_item_order", "kkt_destroy", "kkt_status_string", "kkt_analyse_4x4", "kkt_analyse_4x4_host", "kkt_4x4_inner",
@@ -377,6 +379,34 @@ class KKTSolver:
         self.nnz_j = int(np.asarray(J_rowptr)[-1]) if m else 0
         self.opt = kkt_default_options(**options)
         self.h = kkt_analyse(n, m, H_colptr, H_rowidx, J_rowptr, J_colidx, self.opt)
+
+    @classmethod
+    def host_only(cls, n, m, H_colptr, H_rowidx, J_rowptr, J_colidx, **options):
+        """The ordering, symbolic analysis and plan without device memory
+        (kkt_analyse_host): a source for like()."""
+        self = cls.__new__(cls)
+        self.n, self.m = int(n), int(m)
+        self.nnz_h = int(np.asarray(H_colptr)[-1])
+        self.nnz_j = int(np.asarray(J_rowptr)[-1]) if m else 0
+        self.opt = kkt_default_options(**options)
+        self.h = kkt_analyse_host(n, m, H_colptr, H_rowidx, J_rowptr, J_colidx, self.opt)
+        return self
+
+    @classmethod
+    def like(cls, other: "KKTSolver", **options):
+        """A solver for other's pattern with other options (e.g. the other
+        precision), reusing its ordering and symbolic analysis."""
+        self = cls.__new__(cls)
+        self.n, self.m, self.nnz_h, self.nnz_j = other.n, other.m, other.nnz_h, other.nnz_j
+        self.opt = kkt_default_options(**options)
+        h = C.c_void_p()
+        _check("kkt_analyse_like", _lib.kkt_analyse_like(other.h, C.byref(self.opt), C.byref(h)))
+        self.h = h
+        return self
+
+    def set_profile(self, on=True):
+        """Per-kernel timing on (kernel by kernel, events) or off (graph)."""
+        _check("kkt_set_profile", _lib.kkt_set_profile(self.h, int(bool(on))))
 
     def factor(self, H_vals, J_vals, delta, gamma=-1.0, stream=None, check=True):
         code = kkt_factor(self.h, H_vals, J_vals, delta, gamma, self.nnz_h, self.nnz_j, stream)

@@ -55,6 +55,8 @@ struct kkt_handle_s {
   kkt_options opt;
   Symbolic S;
   Plan P;
+  std::vector<int64_t> hHp, hJp;   // host copies of the pattern (H~ lower CSC, J CSR)
+  std::vector<int32_t> hHi, hJi;
   int device = 0;
   int grid = 0;
   int ctas = 2;   // solve-kernel CTAs per SM
@@ -267,8 +269,9 @@ kkt_status kkt_destroy(kkt_handle h) {
   return KKT_OK;
 }
 
-static kkt_status analyse_host(int64_t n, int64_t m, const int64_t* Hp, const int32_t* Hi, const int64_t* Jp,
-                               const int32_t* Ji, const kkt_options* opt, kkt_handle* out) {
+static kkt_status analyse_host_impl(int64_t n, int64_t m, const int64_t* Hp, const int32_t* Hi, const int64_t* Jp,
+                                    const int32_t* Ji, const kkt_options* opt, const Symbolic* reuse,
+                                    kkt_handle* out) {
   if (!out) return KKT_ERR_INVALID;
   *out = nullptr;
   if (n < 1 || m < 0 || !Hp || !Hi || (m > 0 && (!Jp || !Ji))) return KKT_ERR_INVALID;
@@ -296,7 +299,17 @@ static kkt_status analyse_host(int64_t n, int64_t m, const int64_t* Hp, const in
   RelaxParams rp;
   rp.small = o.relax_small; rp.num = o.relax_num; rp.den = o.relax_den; rp.wmax = o.relax_wmax;
   if (o.ordering < 0 || o.ordering > 2 || (o.ordering == 2 && o.nd_leaf < 1)) { delete h; return KKT_ERR_INVALID; }
-  if (analyse_pattern(n, m, Hp, Hi, Jp, Ji, rp, o.ordering, o.nd_leaf, h->S) != 0) { delete h; return KKT_ERR_INVALID; }
+  if (reuse) {
+    h->S = *reuse;
+  } else if (analyse_pattern(n, m, Hp, Hi, Jp, Ji, rp, o.ordering, o.nd_leaf, h->S) != 0) {
+    delete h;
+    return KKT_ERR_INVALID;
+  }
+  // host copies of the pattern: the device set-up and kkt_analyse_like read them
+  h->hHp.assign(Hp, Hp + n + 1);
+  h->hHi.assign(Hi, Hi + Hp[n]);
+  h->hJp.assign(Jp, Jp + m + 1);
+  h->hJi.assign(Ji, Ji + Jp[m]);
   // piece width and L entries per solve item: a head's first chunk covers
   // the next piece's columns, and two CTAs of the solve kernel fit on one SM
   // (about 107 KB (FP32) / 98 KB (FP64) of shared memory each)
@@ -316,6 +329,13 @@ static kkt_status analyse_host(int64_t n, int64_t m, const int64_t* Hp, const in
   return KKT_OK;
 }
 
+static kkt_status analyse_host(int64_t n, int64_t m, const int64_t* Hp, const int32_t* Hi, const int64_t* Jp,
+                               const int32_t* Ji, const kkt_options* opt, kkt_handle* out) {
+  return analyse_host_impl(n, m, Hp, Hi, Jp, Ji, opt, nullptr, out);
+}
+
+static kkt_status device_stage(kkt_handle h, kkt_handle* out);
+
 kkt_status kkt_analyse_host(int64_t n, int64_t m, const int64_t* Hp, const int32_t* Hi, const int64_t* Jp,
                             const int32_t* Ji, const kkt_options* opt, kkt_handle* out) {
   return analyse_host(n, m, Hp, Hi, Jp, Ji, opt, out);
@@ -327,9 +347,32 @@ kkt_status kkt_analyse(int64_t n, int64_t m, const int64_t* Hp, const int32_t* H
   if (s0) return s0;
   kkt_handle h = *out;
   *out = nullptr;
+  return device_stage(h, out);
+}
+
+kkt_status kkt_analyse_like(kkt_handle src, const kkt_options* opt, kkt_handle* out) {
+  if (!src || !out) return KKT_ERR_INVALID;
+  *out = nullptr;
+  kkt_options o;
+  if (opt) o = *opt; else kkt_default_options(&o);
+  const kkt_options& so = src->opt;
+  if (o.ordering != so.ordering || (o.ordering == 2 && o.nd_leaf != so.nd_leaf) || o.relax_small != so.relax_small ||
+      o.relax_num != so.relax_num || o.relax_den != so.relax_den || o.relax_wmax != so.relax_wmax)
+    return KKT_ERR_INVALID;
+  const int64_t n = src->S.n, m = src->S.m;
+  kkt_status s0 = analyse_host_impl(n, m, src->hHp.data(), src->hHi.data(), src->hJp.data(), src->hJi.data(), &o,
+                                    &src->S, out);
+  if (s0) return s0;
+  kkt_handle h = *out;
+  *out = nullptr;
+  return device_stage(h, out);
+}
+
+static kkt_status device_stage(kkt_handle h, kkt_handle* out) {
   const kkt_options& o = h->opt;
-  static const int64_t zero = 0;
-  if (m == 0) Jp = &zero;
+  const int64_t n = h->S.n, m = h->S.m;
+  const int64_t* Jp = h->hJp.data();
+  const int32_t* Ji = h->hJi.data();
   h->device = o.device;
   if (cudaSetDevice(h->device) != cudaSuccess) { cudaGetLastError(); delete h; return KKT_ERR_CUDA; }
   int coop = 0;
@@ -1192,6 +1235,7 @@ kkt_status kkt_symbolic_info_get(kkt_handle h, kkt_symbolic_info* o) {
   o->fwd_depth = h->P.fwd_depth; o->bwd_depth = h->P.bwd_depth;
   o->nsub = h->P.nsub; o->nitems = (int64_t)h->P.fwd_items.size();
   o->flops = h->S.flops;
+  o->tc_flops = h->P.tc_flops;
   o->device_bytes = (double)h->mem.bytes;
   return KKT_OK;
 }
@@ -1216,6 +1260,20 @@ kkt_status kkt_get_profile(kkt_handle h, double* ms, int64_t* launches, int32_t 
   if (reset) {
     for (int k = 0; k < KKT_K_COUNT; k++) { h->prof.ms[k] = 0; h->prof.n[k] = 0; }
   }
+  return KKT_OK;
+}
+
+kkt_status kkt_set_profile(kkt_handle h, int32_t on) {
+  if (!h) return KKT_ERR_INVALID;
+  if (!h->on_device) return KKT_ERR_STATE;
+  if (!on) {
+    h->profp = nullptr;
+    return KKT_OK;
+  }
+  CK(cudaSetDevice(h->device));
+  if (!h->prof.a) CK(cudaEventCreate(&h->prof.a));
+  if (!h->prof.b) CK(cudaEventCreate(&h->prof.b));
+  h->profp = &h->prof;
   return KKT_OK;
 }
 

@@ -200,6 +200,9 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
           for (int32_t cs = oe; cs < P.sw[s]; cs += 128)
             for (int32_t rs = cs; rs < P.snr[s]; rs += 128)
               P.it_syrk_tc.insert(P.it_syrk_tc.end(), {s, rs, cs, mi, oe - kTcPB, oe, 1, 0});
+          // lower trapezoid of rows [oe, nr) x columns [oe, w), K = kTcPB
+          const double cols = P.sw[s] - oe, top = P.snr[s] - oe;
+          P.tc_flops += 2.0 * kTcPB * (cols * top - cols * (cols - 1) / 2);
         }
         const int64_t c6 = (int64_t)P.it_syrk_tc.size() / 8 - o6;
         if (c6) P.launches.push_back({6, kb, o6, c6});
@@ -229,6 +232,8 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
       const int32_t mi = map_of(s);
       const int32_t w = P.sw[s];
       const int64_t nt = cdiv(P.snr[s] - w, 128);
+      const double rbd = P.snr[s] - w;
+      P.tc_flops += (double)w * rbd * (rbd + 1);   // U = -L21 L21^T, lower triangle
       for (int64_t ti = 0; ti < nt; ti++)
         for (int64_t tj = 0; tj <= ti; tj++)
           P.it_syrk_tc.insert(P.it_syrk_tc.end(),

@@ -77,6 +77,7 @@ struct Plan {
   std::vector<int32_t> it_syrk_tc;          // tensor-core update tiles, 8 ints each: (s, panel row of A,
                                             // panel row of B, tensor map), (K begin, K end, mode, 0)
   std::vector<int32_t> tc_front;            // fronts with a tensor map (index = map number)
+  double tc_flops = 0;                      // algorithmic flops of the tensor-core tiles per factorization
   std::vector<int32_t> it_block;            // (s, row tile, slot) per fused block step (kFItem ints each)
   std::vector<int32_t> it_syrk128;          // (s, ti, tj), 128 x 128 FP32 register-tiled SYRK
   std::vector<int32_t> it_dstore;           // (s, kb, slot): factored diagonal tile -> panel, per level

@@ -648,3 +648,37 @@ def test_solve_trace_records_every_item(precision):
             s2.solve_trace()
     finally:
         s2.close()
+
+
+def test_analyse_like_reuses_the_analysis_in_the_other_precision():
+    """kkt_analyse_like: an FP64 handle made from a mixed handle (and a mixed
+    one from a host-only analysis) has the same symbolic analysis and solves
+    the 50x40 workload to the oracle's solution; the profile toggle times
+    the factor kernels of a handle made without profiling."""
+    sys = W.make_config("grid2d_n2000")
+    _, _, odx, ody, _ = O.solve_system(sys)
+    ref = np.concatenate([odx, ody])
+    a = K.KKTSolver(sys.n, sys.m, sys.H_colptr, sys.H_rowidx, sys.J_rowptr, sys.J_colidx, precision="mixed")
+    b = K.KKTSolver.like(a, precision="fp64")
+    hs = K.KKTSolver.host_only(sys.n, sys.m, sys.H_colptr, sys.H_rowidx, sys.J_rowptr, sys.J_colidx)
+    c = K.KKTSolver.like(hs, precision="mixed")
+    ga, gb, gc = (K.kkt_get_symbolic(x.h) for x in (a, b, c))
+    for k in ga:
+        np.testing.assert_array_equal(ga[k], gb[k])
+        np.testing.assert_array_equal(ga[k], gc[k])
+    for x, tol in ((a, 1e-7), (b, 1e-9), (c, 1e-7)):
+        x.factor(cu(sys.H_vals), cu(sys.J_vals), sys.delta, sys.gamma)
+        dx, dy = x.solve(cu(sys.r_x), cu(sys.r_y))
+        assert rel(torch.cat([dx, dy]).cpu().numpy(), ref) <= tol
+    with pytest.raises(K.KKTError):
+        K.KKTSolver.like(a, precision="fp64", ordering=2)    # another ordering needs its own analysis
+    c.set_profile(True)
+    c.profile(reset=True)
+    c.factor(cu(sys.H_vals), cu(sys.J_vals), sys.delta, sys.gamma)
+    p = c.profile(reset=True)
+    assert p["assemble"][1] == 1 and p["tri_inv"][1] == 1
+    c.set_profile(False)
+    c.factor(cu(sys.H_vals), cu(sys.J_vals), sys.delta, sys.gamma)
+    assert c.profile(reset=True)["assemble"][1] == 0
+    for x in (a, b, c, hs):
+        x.close()
