@@ -358,24 +358,29 @@ def run_secondary(args, rank, world, dev, barrier):
 
 
 # ------------------------------------------------------------------ batching forms
-def run_batching(args, dev):
+def run_batching(args, dev, rank=0, world=1, group=None):
     """The batching workload (200 x 100 grid, n = 20000, m = 10000): nsys
     systems sharing one analysed pattern with per-system edge weights and
     barriers (independent seeds), factored and solved through the batched
     entry points; and one of them with 64 right-hand sides solved together
     (the triangular sweeps shared) against 64 separate solves. Mixed
-    precision (FP32 factor, FP64 CG and refinement)."""
+    precision (FP32 factor, FP64 CG and refinement). With several ranks the
+    systems are sharded by contiguous index (each rank its own block on its
+    own GPU) and the per-system statistics gathered on rank 0 over a CPU
+    group; the rate is all systems over the slowest rank's time."""
     import torch
     import paper_2110_03636_b300 as K
+    from paper_2110_03636_b300 import shard
     import workloads as W
     base = W.make_config("grid2d_n20k")
-    systems = [W.reweight(base, seed=(1, b)) for b in range(args.batch_systems)]
+    lo, hi = shard.partition(args.batch_systems, world)[rank]
+    systems = [W.reweight(base, seed=(1, b)) for b in range(lo, hi)]
     cu = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
     Hs = cu(np.stack([x.H_vals for x in systems]))
     Js = cu(np.stack([x.J_vals for x in systems]))
     rng = np.random.default_rng(11)
-    RX = cu(rng.standard_normal((args.batch_systems, base.n)))
-    RY = cu(rng.standard_normal((args.batch_systems, base.m)))
+    RX = cu(rng.standard_normal((args.batch_systems, base.n))[lo:hi])
+    RY = cu(rng.standard_normal((args.batch_systems, base.m))[lo:hi])
     s = K.KKTSolver(base.n, base.m, base.H_colptr, base.H_rowidx, base.J_rowptr, base.J_colidx,
                     precision="mixed", ordering=args.ordering)
     out = {"workload": "grid2d 200x100, n=20000, m=10000, per-system weights and barriers (seeds (1, b))",
@@ -395,11 +400,15 @@ def run_batching(args, dev):
         dx, dy, infos, sst, code2 = s.solve_batch(RX, RY)
         return st, sst, infos
     sec, (st, sst, infos) = timed(batch_step, 2)
-    out["batch"] = {"systems": args.batch_systems, "solves_per_s": round(args.batch_systems / sec, 2),
-                    "ms_per_system": round(1e3 * sec / args.batch_systems, 3),
-                    "failed": int((np.asarray(st) != 0).sum() + (np.asarray(sst) != 0).sum()),
-                    "rr_max": max(i.rr for i in infos),
-                    "form": "factor_batch + solve_batch on the shared analysis"}
+    sec = max_over_ranks(sec, dev)
+    stats = shard.gather_blocks({"status": np.asarray(st) + np.asarray(sst), "rr": np.array([i.rr for i in infos])},
+                                rank, world, group=group)
+    if rank == 0:
+        out["batch"] = {"systems": args.batch_systems, "solves_per_s": round(args.batch_systems / sec, 2),
+                        "ms_per_system": round(1e3 * sec * world / args.batch_systems, 3),
+                        "failed": int((stats["status"] != 0).sum()), "rr_max": float(stats["rr"].max()),
+                        "ranks": world, "form": "factor_batch + solve_batch on the shared analysis"
+                        + (", systems sharded by contiguous index over the ranks" if world > 1 else "")}
     s.factor(Hs[0], Js[0], base.delta, base.gamma)
     R64 = cu(rng.standard_normal((64, base.n)))
     Y64 = cu(rng.standard_normal((64, base.m)))
@@ -547,7 +556,8 @@ def main():
     if not args.no_secondary:
         line["secondary"] = run_secondary(args, rank, world, dev, barrier)
     if not args.no_batch:
-        line["batching"] = run_batching(args, dev)
+        group = D.new_group(backend="gloo") if world > 1 else None
+        line["batching"] = run_batching(args, dev, rank, world, group)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(si.flops, args.cpu_sample_seconds)
     if rank == 0:
