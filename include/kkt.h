@@ -105,6 +105,15 @@ typedef struct kkt_options {
                           passes (eps_32 kappa(H_gamma) > 1); 0 (default) = 2. ir_maxit
                           bounds the M applications after the first in both modes
                           (< 0: 10 for plain passes, 60 for GMRES) */
+  int32_t ruiz_iters;  /* symmetrized Ruiz scaling of K = [H~, J^T; J, 0] before the
+                          factorization (Sec. 4.1, so that gamma and delta are judged against
+                          the scaled system): 0 (default) = none, k in 1..100 = k iterations
+                          of D_i <- D_i / sqrt(max_j D_i |K_ij| D_j) from D = I. The handle
+                          then factors and solves D K D (delta, gamma act on it), scales the
+                          right-hand side by D and the solution back by D; kkt_info's RR and
+                          BE are those of the scaled system. kkt_solve_multi, kkt_hsolve,
+                          the batched and the 4x4 forms refuse a scaled handle
+                          (KKT_ERR_STATE; the 4x4 analysis: KKT_ERR_INVALID) */
 } kkt_options;
 
 /* Kernel kinds reported by kkt_get_profile. Kinds a plan does not launch
@@ -303,6 +312,10 @@ kkt_status kkt_get_factor_panels(kkt_handle h, double* panels);
  * event pair around each solve pass, at no cost to the pass). reset != 0
  * clears the counters after reading. */
 kkt_status kkt_get_profile(kkt_handle h, double* ms, int64_t* launches, int32_t reset);
+
+/* The Ruiz scaling D = diag(D_x, D_y) of the last factorization (host
+ * double[n + m]); KKT_ERR_STATE when the handle does not scale. */
+kkt_status kkt_get_scaling(kkt_handle h, double* D);
 
 /* Switches the per-kernel timing of kkt_get_profile on (1) or off (0) on an
  * existing handle, as opt.profile = 1 does at analysis: every launch is

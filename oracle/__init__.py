@@ -312,3 +312,47 @@ def recover4x4(p, dx):
     ds = Jd @ dx - p["r_yd"]
     dyd = p["D_s"] * ds - p["r_s"]
     return ds, dyd
+
+
+# --------------------------------------------------------------------------
+# Symmetrized Ruiz scaling (Sec. 4.1: the system is scaled before gamma and
+# delta_min are chosen; D. Ruiz, "A scaling algorithm to equilibrate both
+# rows and columns norms in matrices", RAL-TR-2001-034), numpy
+# --------------------------------------------------------------------------
+def ruiz_scaling(sys, iters):
+    """Diagonal D = diag(D_x, D_y) making the rows of D K D (K = [H~, J^T;
+    J, 0], symmetric) close to unit infinity norm: D = I, then ``iters``
+    times, with the row norms r_i = max_j (D_i |K_ij|) D_j of the current
+    scaled matrix (all rows from the same D), D_i <- D_i / sqrt(r_i) for
+    every row with r_i > 0. Returns (D_x, D_y)."""
+    n, m = sys.n, sys.m
+    Hp, Hi, Hv = sys.H_colptr, sys.H_rowidx, np.abs(sys.H_vals)
+    cols = np.repeat(np.arange(n), np.diff(Hp))
+    Jp, Jc, Jv = sys.J_rowptr, sys.J_colidx, np.abs(sys.J_vals)
+    jrow = np.repeat(np.arange(m), np.diff(Jp))
+    D = np.ones(n + m)
+    for _ in range(iters):
+        r = np.zeros(n + m)
+        # H~ entry (i, j) of the lower triangle lies in rows i and j
+        np.maximum.at(r, Hi, (D[Hi] * Hv) * D[cols])
+        np.maximum.at(r, cols, (D[cols] * Hv) * D[Hi])
+        # J entry (r, c) lies in row n + r and (as J^T) in row c
+        np.maximum.at(r, n + jrow, (D[n + jrow] * Jv) * D[Jc])
+        np.maximum.at(r, Jc, (D[Jc] * Jv) * D[n + jrow])
+        pos = r > 0
+        D = np.where(pos, D / np.sqrt(np.where(pos, r, 1.0)), D)
+    return D[:n].copy(), D[n:].copy()
+
+
+def scale_system(sys, Dx, Dy):
+    """The scaled system D K D x^ = D b as a new KKTSystem (values and
+    right-hand sides scaled; delta and gamma unchanged, so they act on the
+    scaled system). The solution of the original is x = D x^."""
+    s = sys.copy()
+    cols = np.repeat(np.arange(sys.n), np.diff(sys.H_colptr))
+    s.H_vals = (Dx[sys.H_rowidx] * sys.H_vals) * Dx[cols]
+    jrow = np.repeat(np.arange(sys.m), np.diff(sys.J_rowptr))
+    s.J_vals = (Dy[jrow] * sys.J_vals) * Dx[sys.J_colidx]
+    s.r_x = Dx * sys.r_x
+    s.r_y = Dy * sys.r_y
+    return s

@@ -37,7 +37,7 @@ class kkt_options(C.Structure):
                 ("solve_w", C.c_int32), ("device", C.c_int32), ("debug_stall_piece", C.c_int32),
                 ("spin_cycles", C.c_int64), ("profile", C.c_int32), ("nd_leaf", C.c_int32),
                 ("tensor_cores", C.c_int32), ("solve_ctas", C.c_int32), ("solve_ent", C.c_int32),
-                ("refine", C.c_int32)]
+                ("refine", C.c_int32), ("ruiz_iters", C.c_int32)]
 
 
 class kkt_info(C.Structure):
@@ -68,6 +68,7 @@ def _load():
     L.kkt_factor_regularized.argtypes = [P, P, P, D, D, D, P, P]
     L.kkt_set_delta_prev.argtypes = [P, D]
     L.kkt_set_profile.argtypes = [P, I32]
+    L.kkt_get_scaling.argtypes = [P, P]
     L.kkt_analyse_like.argtypes = [P, C.POINTER(kkt_options), C.POINTER(P)]
     L.kkt_factor_batch.argtypes = [P, I32, P, P, D, D, P, P]
     L.kkt_solve_batch.argtypes = [P, I32, P, P, P, P, P, P, P]
@@ -94,7 +95,7 @@ def _load():
     L.kkt_destroy_4x4.argtypes = [P]
     L.kkt_status_string.argtypes = [I32]
     L.kkt_status_string.restype = C.c_char_p
-    for nm in ("kkt_analyse", "kkt_analyse_host", "kkt_factor", "kkt_solve", "kkt_solve_multi", "kkt_factor_batch", "kkt_solve_batch", "kkt_factor_regularized", "kkt_set_delta_prev", "kkt_set_profile", "kkt_analyse_like", "kkt_factor_solve_host", "kkt_hsolve", "kkt_get_info",
+    for nm in ("kkt_analyse", "kkt_analyse_host", "kkt_factor", "kkt_solve", "kkt_solve_multi", "kkt_factor_batch", "kkt_solve_batch", "kkt_factor_regularized", "kkt_set_delta_prev", "kkt_set_profile", "kkt_get_scaling", "kkt_analyse_like", "kkt_factor_solve_host", "kkt_hsolve", "kkt_get_info",
                "kkt_inertia", "kkt_symbolic_info_get", "kkt_get_symbolic", "kkt_get_factor_panels", "kkt_get_profile", "kkt_get_solve_counters", "kkt_residual_noalloc",
                "kkt_get_solve_trace", "kkt_get_solve_item_order", "kkt_destroy", "kkt_analyse_4x4", "kkt_analyse_4x4_host", "kkt_get_4x4_pattern", "kkt_factor_4x4",
                "kkt_solve_4x4", "kkt_destroy_4x4"):
@@ -103,7 +104,7 @@ def _load():
 
 
 _lib = _load()
-EXPORTED = ("kkt_default_options", "kkt_analyse", "kkt_analyse_host", "kkt_factor", "kkt_solve", "kkt_solve_multi", "kkt_factor_batch", "kkt_solve_batch", "kkt_factor_regularized", "kkt_set_delta_prev", "kkt_set_profile", "kkt_analyse_like", "kkt_factor_solve_host",
+EXPORTED = ("kkt_default_options", "kkt_analyse", "kkt_analyse_host", "kkt_factor", "kkt_solve", "kkt_solve_multi", "kkt_factor_batch", "kkt_solve_batch", "kkt_factor_regularized", "kkt_set_delta_prev", "kkt_set_profile", "kkt_get_scaling", "kkt_analyse_like", "kkt_factor_solve_host",
             "kkt_hsolve", "kkt_get_info", "kkt_inertia", "kkt_symbolic_info_get", "kkt_get_symbolic",
             "kkt_get_factor_panels", "kkt_get_profile", "kkt_get_solve_counters", "kkt_residual_noalloc",
             "kkt_get_solve_trace", "kkt_get_solve_item_order", "kkt_destroy", "kkt_status_string", "kkt_analyse_4x4", "kkt_analyse_4x4_host", "kkt_4x4_inner",
@@ -403,6 +404,12 @@ class KKTSolver:
         _check("kkt_analyse_like", _lib.kkt_analyse_like(other.h, C.byref(self.opt), C.byref(h)))
         self.h = h
         return self
+
+    def scaling(self):
+        """The Ruiz scaling D (numpy float64[n + m]) of the last factorization."""
+        D = np.zeros(self.n + self.m)
+        _check("kkt_get_scaling", _lib.kkt_get_scaling(self.h, D.ctypes.data))
+        return D
 
     def set_profile(self, on=True):
         """Per-kernel timing on (kernel by kernel, events) or off (graph)."""

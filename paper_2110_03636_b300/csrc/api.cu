@@ -114,6 +114,10 @@ struct kkt_handle_s {
   cudaGraphExec_t fac_graph = nullptr; // the whole factorization as one CUDA graph
   cudaGraphExec_t reg_graph = nullptr; // Algorithm 1's delta_1 loop around it (conditional node)
   double delta_prev = 0;     // delta_1 accepted for the previous matrix of the sequence (Sec. 4.1)
+  // Ruiz scaling (opt.ruiz_iters > 0): D, its scratch, ones, and the lower CSC pattern of H~
+  double *d_D = nullptr, *d_Dtmp = nullptr, *d_ones = nullptr;
+  int64_t* d_Hp = nullptr;
+  int32_t* d_Hi = nullptr;
   // state
   bool on_device = false;   // false for a host-only (symbolic) handle
   bool factored = false;
@@ -231,6 +235,7 @@ void kkt_default_options(kkt_options* o) {
   o->profile = 0;
   o->nd_leaf = 64;
   o->tensor_cores = 1;
+  o->ruiz_iters = 0;
 }
 
 const char* kkt_status_string(kkt_status s) {
@@ -281,7 +286,7 @@ static kkt_status analyse_host_impl(int64_t n, int64_t m, const int64_t* Hp, con
   const kkt_options& o = h->opt;
   if ((o.solve_w != 0 && (o.solve_w < 32 || o.solve_w > 256)) || o.relax_den <= 0 || o.precision < 0 ||
       o.precision > 1 || o.solve_ctas < 0 || o.solve_ctas == 1 || o.solve_ctas > 4 || o.refine < 0 ||
-      o.refine > 2 ||
+      o.refine > 2 || o.ruiz_iters < 0 || o.ruiz_iters > 100 ||
       (o.solve_ent != 0 && (o.solve_ent < 2048 || o.solve_ent > 32768))) {
     delete h;
     return KKT_ERR_INVALID;
@@ -452,6 +457,13 @@ static kkt_status device_stage(kkt_handle h, kkt_handle* out) {
   h->counters = A.alloc<int>(4 * (size_t)P.npieces + 8);
   h->dst = A.alloc<DevStatus>(1);
   h->d_dg = A.alloc<double>(6);
+  if (o.ruiz_iters > 0) {
+    h->d_D = A.alloc<double>(n + m);
+    h->d_Dtmp = A.alloc<double>(n + m);
+    h->d_ones = A.upload(std::vector<double>(n + m, 1.0));
+    h->d_Hp = A.upload(h->hHp);
+    h->d_Hi = A.upload(h->hHi);
+  }
   h->d_instr = A.alloc<unsigned long long>(32);
   if (o.profile) h->d_trace = A.alloc<unsigned long long>(6 * P.fwd_items.size() + 6);
   if (A.failed) { kkt_destroy(h); return KKT_ERR_OOM; }
@@ -486,6 +498,21 @@ static kkt_status device_stage(kkt_handle h, kkt_handle* out) {
 }  // extern "C"
 
 // ------------------------------------------------------------------ drivers
+// Ruiz scaling of the values just copied into h->Hv / h->Jv (in place)
+static kkt_status apply_scaling(kkt_handle h, cudaStream_t st) {
+  if (h->opt.ruiz_iters <= 0) return KKT_OK;
+  const Plan& P = h->P;
+  RuizArgs a;
+  a.n = P.n; a.m = P.m;
+  a.Hs_ptr = h->Hs_ptr; a.Hs_col = h->Hs_col; a.Hs_vidx = h->Hs_vidx;
+  a.H_colptr = h->d_Hp; a.H_rowidx = h->d_Hi;
+  a.JT_ptr = h->JTo_ptr; a.JT_row = h->JTo_row; a.JT_vidx = h->JTo_vidx;
+  a.J_rowptr = h->J_rowptr; a.J_colidx = h->J_colidx;
+  a.Hv = h->Hv; a.Jv = h->Jv; a.ones = h->d_ones;
+  CK(launch_ruiz(a, h->opt.ruiz_iters, h->d_D, h->d_Dtmp, h->Hv, h->Jv, st));
+  return KKT_OK;
+}
+
 static kkt_status reset_status(kkt_handle h, cudaStream_t st) {
   std::memset(h->hst, 0, sizeof(DevStatus));
   h->hst->fail_col = INT_MAX;
@@ -978,7 +1005,7 @@ extern "C" {
 kkt_status kkt_factor_batch(kkt_handle h, int32_t nsys, const double* H_vals, const double* J_vals,
                             double delta, double gamma, int32_t* status, void* stream) {
   if (!h || nsys < 1 || !H_vals || (h->nnzJ > 0 && !J_vals)) return KKT_ERR_INVALID;
-  if (!h->on_device) return KKT_ERR_STATE;
+  if (!h->on_device || h->opt.ruiz_iters > 0) return KKT_ERR_STATE;
   CK(cudaSetDevice(h->device));
   cudaStream_t st = (cudaStream_t)stream;
   const size_t es = h->opt.precision == KKT_FP64 ? sizeof(double) : sizeof(float);
@@ -1027,7 +1054,7 @@ kkt_status kkt_factor_batch(kkt_handle h, int32_t nsys, const double* H_vals, co
 kkt_status kkt_solve_batch(kkt_handle h, int32_t nsys, const double* r_x, const double* r_y, double* dx,
                            double* dy, kkt_info* info, int32_t* status, void* stream) {
   if (!h || nsys < 1 || !r_x || !dx || (h->P.m > 0 && (!r_y || !dy))) return KKT_ERR_INVALID;
-  if (!h->on_device) return KKT_ERR_STATE;
+  if (!h->on_device || h->opt.ruiz_iters > 0) return KKT_ERR_STATE;
   if (nsys > (int32_t)h->bstatus.size()) return KKT_ERR_STATE;
   CK(cudaSetDevice(h->device));
   cudaStream_t st = (cudaStream_t)stream;
@@ -1062,7 +1089,7 @@ kkt_status kkt_solve_batch(kkt_handle h, int32_t nsys, const double* r_x, const 
 kkt_status kkt_solve_multi(kkt_handle h, int32_t nrhs, const double* r_x, const double* r_y, double* dx,
                            double* dy, kkt_info* info, void* stream) {
   if (!h || nrhs < 1 || !r_x || !dx || (h->P.m > 0 && (!r_y || !dy))) return KKT_ERR_INVALID;
-  if (!h->on_device) return KKT_ERR_STATE;
+  if (!h->on_device || h->opt.ruiz_iters > 0) return KKT_ERR_STATE;
   if (!h->factored) return KKT_ERR_STATE;
   CK(cudaSetDevice(h->device));
   cudaStream_t st = (cudaStream_t)stream;
@@ -1111,6 +1138,8 @@ kkt_status kkt_factor(kkt_handle h, const double* H_vals, const double* J_vals, 
   CK(cudaSetDevice(h->device));
   CK(cudaMemcpyAsync(h->Hv, H_vals, sizeof(double) * h->nnzH, cudaMemcpyDeviceToDevice, st));
   if (h->nnzJ) CK(cudaMemcpyAsync(h->Jv, J_vals, sizeof(double) * h->nnzJ, cudaMemcpyDeviceToDevice, st));
+  kkt_status sc = apply_scaling(h, st);
+  if (sc) return sc;
   return factor_common(h, delta, gamma, st);
 }
 
@@ -1127,6 +1156,10 @@ kkt_status kkt_factor_regularized(kkt_handle h, const double* H_vals, const doub
   CK(cudaSetDevice(h->device));
   CK(cudaMemcpyAsync(h->Hv, H_vals, sizeof(double) * h->nnzH, cudaMemcpyDeviceToDevice, st));
   if (h->nnzJ) CK(cudaMemcpyAsync(h->Jv, J_vals, sizeof(double) * h->nnzJ, cudaMemcpyDeviceToDevice, st));
+  {
+    kkt_status sc = apply_scaling(h, st);
+    if (sc) return sc;
+  }
   double d1 = 0.0;
   kkt_status s;
   if (h->profp) {
@@ -1175,7 +1208,15 @@ kkt_status kkt_solve(kkt_handle h, const double* r_x, const double* r_y, double*
   if (!h || !r_x || !dx || (h->P.m > 0 && (!r_y || !dy))) return KKT_ERR_INVALID;
   if (!h->on_device) return KKT_ERR_STATE;
   CK(cudaSetDevice(h->device));
-  return solve_common(h, r_x, r_y, dx, dy, (cudaStream_t)stream);
+  if (h->opt.ruiz_iters <= 0) return solve_common(h, r_x, r_y, dx, dy, (cudaStream_t)stream);
+  // scaled handle: solve D K D x^ = D b, then x = D x^
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = h->P.n, m = h->P.m;
+  CK(launch_scale_vec(n, m, h->d_D, r_x, r_y, h->stage_rx, h->stage_ry, st));
+  kkt_status s = solve_common(h, h->stage_rx, h->stage_ry, h->stage_dx, h->stage_dy, st);
+  CK(launch_scale_vec(n, m, h->d_D, h->stage_dx, h->stage_dy, dx, dy, st));
+  CK(cudaStreamSynchronize(st));
+  return s;
 }
 
 kkt_status kkt_factor_solve_host(kkt_handle h, const double* H_vals, const double* J_vals, double delta,
@@ -1190,9 +1231,14 @@ kkt_status kkt_factor_solve_host(kkt_handle h, const double* H_vals, const doubl
   if (h->nnzJ) CK(cudaMemcpyAsync(h->Jv, J_vals, sizeof(double) * h->nnzJ, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(h->stage_rx, r_x, sizeof(double) * n, cudaMemcpyHostToDevice, st));
   if (m) CK(cudaMemcpyAsync(h->stage_ry, r_y, sizeof(double) * m, cudaMemcpyHostToDevice, st));
-  kkt_status s = factor_common(h, delta, gamma, st);
+  kkt_status s = apply_scaling(h, st);
+  if (s) return s;
+  const bool scaled = h->opt.ruiz_iters > 0;
+  if (scaled) CK(launch_scale_vec(n, m, h->d_D, h->stage_rx, h->stage_ry, h->stage_rx, h->stage_ry, st));
+  s = factor_common(h, delta, gamma, st);
   if (s) return s;
   s = solve_common(h, h->stage_rx, h->stage_ry, h->stage_dx, h->stage_dy, st);
+  if (scaled) CK(launch_scale_vec(n, m, h->d_D, h->stage_dx, h->stage_dy, h->stage_dx, h->stage_dy, st));
   CK(cudaMemcpyAsync(dx, h->stage_dx, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
   if (m) CK(cudaMemcpyAsync(dy, h->stage_dy, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -1201,7 +1247,7 @@ kkt_status kkt_factor_solve_host(kkt_handle h, const double* H_vals, const doubl
 
 kkt_status kkt_hsolve(kkt_handle h, const double* b, double* x, void* stream) {
   if (!h || !b || !x) return KKT_ERR_INVALID;
-  if (!h->factored) return KKT_ERR_STATE;
+  if (!h->factored || h->opt.ruiz_iters > 0) return KKT_ERR_STATE;
   cudaStream_t st = (cudaStream_t)stream;
   CK(cudaSetDevice(h->device));
   kkt_status s = reset_status(h, st);
@@ -1260,6 +1306,14 @@ kkt_status kkt_get_profile(kkt_handle h, double* ms, int64_t* launches, int32_t 
   if (reset) {
     for (int k = 0; k < KKT_K_COUNT; k++) { h->prof.ms[k] = 0; h->prof.n[k] = 0; }
   }
+  return KKT_OK;
+}
+
+kkt_status kkt_get_scaling(kkt_handle h, double* D) {
+  if (!h || !D) return KKT_ERR_INVALID;
+  if (!h->on_device || h->opt.ruiz_iters <= 0) return KKT_ERR_STATE;
+  CK(cudaSetDevice(h->device));
+  CK(cudaMemcpy(D, h->d_D, sizeof(double) * (size_t)(h->P.n + h->P.m), cudaMemcpyDeviceToHost));
   return KKT_OK;
 }
 

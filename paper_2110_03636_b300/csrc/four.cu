@@ -263,6 +263,7 @@ kkt_status kkt_analyse_4x4(int64_t n_x, int64_t m_c, int64_t m_d, const int64_t*
                            const int32_t* H_rowidx, const int64_t* J_rowptr, const int32_t* J_colidx,
                            const int64_t* Jd_rowptr, const int32_t* Jd_colidx, const kkt_options* opt,
                            kkt_handle4* out) {
+  if (opt && opt->ruiz_iters != 0) return KKT_ERR_INVALID;   // the 4x4 form does not scale
   return analyse4(n_x, m_c, m_d, H_colptr, H_rowidx, J_rowptr, J_colidx, Jd_rowptr, Jd_colidx, opt, true, out);
 }
 

@@ -152,4 +152,18 @@ struct ResArgs {
 };
 cudaError_t launch_residual(const ResArgs& a, cudaStream_t st);
 
+// Symmetrized Ruiz scaling (scale.cu): the pattern of K = [H~, J^T; J, 0] in
+// original labels and the values it reads (and scales in place).
+struct RuizArgs {
+  int64_t n, m;
+  const int64_t *Hs_ptr, *H_colptr, *JT_ptr, *J_rowptr;
+  const int32_t *Hs_col, *Hs_vidx, *H_rowidx, *JT_row, *JT_vidx, *J_colidx;
+  const double *Hv, *Jv;
+  const double* ones;   // n + m ones (the initial D)
+};
+cudaError_t launch_ruiz(const RuizArgs& a, int iters, double* D, double* Dtmp, double* Hv, double* Jv,
+                        cudaStream_t st);
+cudaError_t launch_scale_vec(int64_t n, int64_t m, const double* D, const double* xx, const double* xy, double* yx,
+                             double* yy, cudaStream_t st);
+
 }  // namespace kkt

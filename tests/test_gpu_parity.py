@@ -682,3 +682,40 @@ def test_analyse_like_reuses_the_analysis_in_the_other_precision():
     assert c.profile(reset=True)["assemble"][1] == 0
     for x in (a, b, c, hs):
         x.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", ["grid2d_n2000", "tiny"])
+def test_ruiz_scaling_matches_oracle(name, precision):
+    """Symmetrized Ruiz scaling (Sec. 4.1) on the device: D equals the
+    oracle's bit for bit (products, maxima, square roots and divisions
+    only), and the solution of the scaled system, unscaled, matches the
+    oracle's scaled solve; the refused forms say so."""
+    if name == "tiny":
+        # a badly scaled system: S H~ S and R J S with S, R spread over 6 decades
+        sys = W.random_tiny_system(17, n_lo=60, n_hi=100, density=0.08)
+        rng = np.random.default_rng(1)
+        S, Rr = 10.0 ** rng.uniform(-3, 3, sys.n), 10.0 ** rng.uniform(-3, 3, sys.m)
+        cols = np.repeat(np.arange(sys.n), np.diff(sys.H_colptr))
+        sys.H_vals = S[sys.H_rowidx] * sys.H_vals * S[cols]
+        jrow = np.repeat(np.arange(sys.m), np.diff(sys.J_rowptr))
+        sys.J_vals = Rr[jrow] * sys.J_vals * S[sys.J_colidx]
+    else:
+        sys = W.make_config(name)
+    iters = 10
+    Dx, Dy = O.ruiz_scaling(sys, iters)
+    sc = O.scale_system(sys, Dx, Dy)
+    _, _, odx, ody, oinfo = O.solve_system(sc, ir_maxit=3)
+    if oinfo["status"] != 0:
+        pytest.skip("oracle: scaled H_gamma not SPD at this delta")
+    ref = np.concatenate([Dx * odx, Dy * ody])
+    s, code, dx, dy = gpu_solve(sys, precision, ruiz_iters=iters)
+    assert code == 0
+    np.testing.assert_array_equal(s.scaling(), np.concatenate([Dx, Dy]))
+    assert s.info.rr <= (1e-10 if precision == "fp64" else 1e-9)
+    assert rel(np.concatenate([dx, dy]), ref) <= (1e-9 if precision == "fp64" else 1e-6)
+    with pytest.raises(K.KKTError):
+        s.hsolve(cu(sys.r_x))
+    with pytest.raises(K.KKTError):
+        s.solve_multi(cu(np.stack([sys.r_x] * 2)), cu(np.stack([sys.r_y] * 2)))
+    s.close()
