@@ -114,6 +114,14 @@ typedef struct kkt_options {
                           BE are those of the scaled system. kkt_solve_multi, kkt_hsolve,
                           the batched and the 4x4 forms refuse a scaled handle
                           (KKT_ERR_STATE; the 4x4 analysis: KKT_ERR_INVALID) */
+  int32_t krylov;      /* Krylov method on the Schur complement S (Sec. 4, after eqs.
+                          Schur1-Schur2): 0 (default) = CG fused into the persistent solve
+                          kernel (Algorithm 1); 1 = CG preconditioned by
+                          M = (J J^T)^-1 J H_gamma J^T (J J^T)^-1, with J J^T factored by an
+                          inner FP64 handle (plain CG if J J^T is not positive definite);
+                          2 = MINRES. 1 and 2 need KKT_FP64, run the Krylov loop from the
+                          host with device vectors, no delta_2 restart, and are not used by
+                          kkt_solve_multi or the batched form (KKT_ERR_STATE) */
 } kkt_options;
 
 /* Kernel kinds reported by kkt_get_profile. Kinds a plan does not launch

@@ -356,3 +356,89 @@ def scale_system(sys, Dx, Dy):
     s.r_x = Dx * sys.r_x
     s.r_y = Dy * sys.r_y
     return s
+
+
+# --------------------------------------------------------------------------
+# Krylov variants on the Schur complement (Sec. 4, the discussion after eqs.
+# Schur1-Schur2: CG or MINRES on S y = J w - r_y, with or without the
+# multiplicative preconditioner M = (J J^T)^-1 J H_gamma J^T (J J^T)^-1),
+# numpy + the oracle's Cholesky for H_gamma^-1 + a sparse LU of J J^T
+# --------------------------------------------------------------------------
+def _csr(sys):
+    import scipy.sparse as sp
+    J = sp.csr_matrix((sys.J_vals, sys.J_colidx, sys.J_rowptr), shape=(sys.m, sys.n))
+    H = sp.csc_matrix((sys.H_vals, sys.H_rowidx, sys.H_colptr), shape=(sys.n, sys.n))
+    return J, (H + sp.tril(H, -1).T).tocsr()
+
+
+def schur_variant(fac: Factor, sys, method="pcg", rtol=1e-12, maxit=1000):
+    """Solves K_delta [dx; dy] = [r_x; r_y] through eq. Schur1 with
+    ``method`` = "pcg" (CG preconditioned by M, M applied as written: two
+    solves with J J^T around J H_gamma J^T) or "minres" (MINRES of Paige and
+    Saunders on S, unpreconditioned), stopping on ||b_S - S y|| <= rtol ||b_S||
+    as the recurrence reports it, then eq. Schur2 for dx. Returns
+    (dx, dy, iterations)."""
+    import scipy.sparse.linalg as spla
+    J, Hf = _csr(sys)
+    g, d = fac.gamma, fac.delta
+    hinv = fac.hsolve
+    rhx = sys.r_x + g * (J.T @ sys.r_y)
+    bS = J @ hinv(rhx) - sys.r_y
+    S = lambda p: J @ hinv(J.T @ p)
+    nb = np.linalg.norm(bS)
+    y = np.zeros(sys.m)
+    it = 0
+    if nb == 0:
+        pass
+    elif method == "pcg":
+        JJt = spla.splu((J @ J.T).tocsc())
+        Hg = lambda v: Hf @ v + d * v + g * (J.T @ (J @ v))
+        M = lambda r: JJt.solve(J @ Hg(J.T @ JJt.solve(r)))
+        r = bS.copy()
+        z = M(r)
+        p = z.copy()
+        rho = r @ z
+        while it < maxit:
+            q = S(p)
+            a = rho / (p @ q)
+            y += a * p
+            r -= a * q
+            it += 1
+            if np.linalg.norm(r) <= rtol * nb:
+                break
+            z = M(r)
+            rho2 = r @ z
+            p = z + (rho2 / rho) * p
+            rho = rho2
+    elif method == "minres":
+        # Lanczos on S with v_1 = b_S / ||b_S||, QR of the tridiagonal by Givens
+        # rotations (c, s), search directions w updated by the last two
+        v_old, v = np.zeros(sys.m), bS / nb
+        beta, eta = nb, nb
+        c_old = c = 1.0
+        s_old = s = 0.0
+        w_old2, w_old = np.zeros(sys.m), np.zeros(sys.m)
+        while it < maxit:
+            p = S(v)
+            alpha = v @ p
+            p = p - alpha * v - beta * v_old
+            beta_new = np.linalg.norm(p)
+            dlt = c * alpha - c_old * s * beta
+            r1 = np.hypot(dlt, beta_new)
+            r2 = s * alpha + c_old * c * beta
+            r3 = s_old * beta
+            c_new, s_new = dlt / r1, beta_new / r1
+            w = (v - r3 * w_old2 - r2 * w_old) / r1
+            y += c_new * eta * w
+            eta = -s_new * eta
+            it += 1
+            if abs(eta) <= rtol * nb or beta_new == 0:
+                break
+            v_old, v = v, p / beta_new
+            w_old2, w_old = w_old, w
+            c_old, c, s_old, s = c, c_new, s, s_new
+            beta = beta_new
+    else:
+        raise ValueError(method)
+    dx = hinv(rhx - J.T @ y)
+    return dx, y, it

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <climits>
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -116,6 +117,15 @@ struct kkt_handle_s {
   double delta_prev = 0;     // delta_1 accepted for the previous matrix of the sequence (Sec. 4.1)
   // Ruiz scaling (opt.ruiz_iters > 0): D, its scratch, ones, and the lower CSC pattern of H~
   double *d_D = nullptr, *d_Dtmp = nullptr, *d_ones = nullptr;
+  // Krylov variants on S (opt.krylov): the J J^T handle of the preconditioner,
+  // its value gather (pairs of J entries per lower entry), and workspace
+  kkt_handle jjt = nullptr;
+  int64_t* jjt_pp = nullptr;
+  int32_t *jjt_pa = nullptr, *jjt_pb = nullptr;
+  int64_t jjt_ne = 0;
+  double* jjt_vals = nullptr;
+  bool jjt_ok = false;
+  double *kv = nullptr, *kpart = nullptr, *kdots = nullptr;
   int64_t* d_Hp = nullptr;
   int32_t* d_Hi = nullptr;
   // state
@@ -236,6 +246,7 @@ void kkt_default_options(kkt_options* o) {
   o->nd_leaf = 64;
   o->tensor_cores = 1;
   o->ruiz_iters = 0;
+  o->krylov = 0;
 }
 
 const char* kkt_status_string(kkt_status s) {
@@ -264,6 +275,7 @@ kkt_status kkt_destroy(kkt_handle h) {
   if (h->h_dg) cudaFreeHost(h->h_dg);
   if (h->fac_graph) cudaGraphExecDestroy(h->fac_graph);
   if (h->reg_graph) cudaGraphExecDestroy(h->reg_graph);
+  if (h->jjt) kkt_destroy(h->jjt);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->prof.a) cudaEventDestroy(h->prof.a);
   if (h->prof.b) cudaEventDestroy(h->prof.b);
@@ -286,7 +298,8 @@ static kkt_status analyse_host_impl(int64_t n, int64_t m, const int64_t* Hp, con
   const kkt_options& o = h->opt;
   if ((o.solve_w != 0 && (o.solve_w < 32 || o.solve_w > 256)) || o.relax_den <= 0 || o.precision < 0 ||
       o.precision > 1 || o.solve_ctas < 0 || o.solve_ctas == 1 || o.solve_ctas > 4 || o.refine < 0 ||
-      o.refine > 2 || o.ruiz_iters < 0 || o.ruiz_iters > 100 ||
+      o.refine > 2 || o.ruiz_iters < 0 || o.ruiz_iters > 100 || o.krylov < 0 || o.krylov > 2 ||
+      (o.krylov != 0 && o.precision != KKT_FP64) ||
       (o.solve_ent != 0 && (o.solve_ent < 2048 || o.solve_ent > 32768))) {
     delete h;
     return KKT_ERR_INVALID;
@@ -466,6 +479,45 @@ static kkt_status device_stage(kkt_handle h, kkt_handle* out) {
   }
   h->d_instr = A.alloc<unsigned long long>(32);
   if (o.profile) h->d_trace = A.alloc<unsigned long long>(6 * P.fwd_items.size() + 6);
+  if (o.krylov == 1 && m > 0 && !A.failed) {
+    // lower pattern of J J^T (column r2, rows r1 >= r2 that share a column of
+    // J with r2) and, per entry, the pairs of J entries whose products sum to it
+    struct Tri { int32_t r2, r1, qa, qb; };
+    std::vector<Tri> tri;
+    for (int64_t c = 0; c < n; c++)
+      for (int64_t a1 = P.JTo_ptr[c]; a1 < P.JTo_ptr[c + 1]; a1++)
+        for (int64_t a2 = P.JTo_ptr[c]; a2 < P.JTo_ptr[c + 1]; a2++)
+          if (P.JTo_row[a1] >= P.JTo_row[a2]) tri.push_back({P.JTo_row[a2], P.JTo_row[a1], P.JTo_vidx[a1], P.JTo_vidx[a2]});
+    std::sort(tri.begin(), tri.end(), [](const Tri& x, const Tri& y) {
+      return x.r2 != y.r2 ? x.r2 < y.r2 : (x.r1 != y.r1 ? x.r1 < y.r1 : (x.qa != y.qa ? x.qa < y.qa : x.qb < y.qb));
+    });
+    std::vector<int64_t> cp(m + 1, 0), pp;
+    std::vector<int32_t> ri, pa, pb;
+    for (size_t t = 0; t < tri.size(); t++) {
+      if (t == 0 || tri[t].r2 != tri[t - 1].r2 || tri[t].r1 != tri[t - 1].r1) {
+        ri.push_back(tri[t].r1);
+        cp[tri[t].r2 + 1]++;
+        pp.push_back((int64_t)t);
+      }
+      pa.push_back(tri[t].qa);
+      pb.push_back(tri[t].qb);
+    }
+    pp.push_back((int64_t)tri.size());
+    for (int64_t r = 0; r < m; r++) cp[r + 1] += cp[r];
+    kkt_options so;
+    kkt_default_options(&so);
+    so.precision = KKT_FP64;
+    so.ordering = o.ordering;
+    so.nd_leaf = o.nd_leaf;
+    so.device = o.device;
+    const kkt_status sj = kkt_analyse(m, 0, cp.data(), ri.data(), nullptr, nullptr, &so, &h->jjt);
+    if (sj) { kkt_destroy(h); return sj; }
+    h->jjt_ne = (int64_t)ri.size();
+    h->jjt_pp = A.upload(pp);
+    h->jjt_pa = A.upload(pa);
+    h->jjt_pb = A.upload(pb);
+    h->jjt_vals = A.alloc<double>(ri.size());
+  }
   if (A.failed) { kkt_destroy(h); return KKT_ERR_OOM; }
   if (cudaMallocHost(&h->hst, sizeof(DevStatus)) != cudaSuccess) { cudaGetLastError(); h->hst = nullptr; kkt_destroy(h); return KKT_ERR_OOM; }
   if (cudaMallocHost(&h->h_dg, 6 * sizeof(double)) != cudaSuccess) { cudaGetLastError(); h->h_dg = nullptr; kkt_destroy(h); return KKT_ERR_OOM; }
@@ -584,6 +636,8 @@ static kkt_status factor_impl(kkt_handle h, cudaStream_t st) {
   return KKT_OK;
 }
 
+static kkt_status post_factor(kkt_handle h, cudaStream_t st);
+
 static kkt_status factor_common(kkt_handle h, double delta, double gamma, cudaStream_t st) {
   h->factored = false;
   h->inertia_ok = 0;
@@ -600,7 +654,7 @@ static kkt_status factor_common(kkt_handle h, double delta, double gamma, cudaSt
   if (h->hst->abort) return KKT_ERR_TIMEOUT;
   if (h->hst->fail_col != INT_MAX) return KKT_ERR_NOT_SPD;
   h->factored = true;
-  return KKT_OK;
+  return post_factor(h, st);
 }
 
 // Algorithm 1's regularization loop with the sequence rule of Sec. 4.1:
@@ -889,9 +943,217 @@ static kkt_status solve_fgmres(kkt_handle h, const double* rx, const double* ry,
   return finish(KKT_OK);
 }
 
+// ------------------------------------------------ Krylov variants on S
+// (opt.krylov = 1: CG preconditioned by M = (J J^T)^-1 J H_gamma J^T
+// (J J^T)^-1; 2: MINRES), FP64 handles. The loop runs on the host; every
+// vector lives on the device and every product is a device kernel: S p =
+// J H^-1 J^T p with H^-1 from the persistent solve kernel (one H^-1
+// application per launch), (J J^T)^-1 from the inner handle's.
+
+// J J^T values from the current J and its Cholesky on the inner handle; a
+// failure (J rank deficient) leaves the preconditioner off
+static kkt_status post_factor(kkt_handle h, cudaStream_t st) {
+  if (h->opt.krylov != 1 || !h->jjt) return KKT_OK;
+  h->jjt_ok = false;
+  CK(launch_jjt_values(h->jjt_ne, h->jjt_pp, h->jjt_pa, h->jjt_pb, h->Jv, h->jjt_vals, st));
+  const kkt_status s = kkt_factor(h->jjt, h->jjt_vals, nullptr, 0.0, 0.0, st);
+  if (s == KKT_OK) h->jjt_ok = true;
+  else if (s != KKT_ERR_NOT_SPD) return s;
+  return KKT_OK;
+}
+
+static kkt_status hinv(kkt_handle h, const double* b, double* x, cudaStream_t st) {
+  return solve_pass<double>(h, b, b, x, x, 0, 1, st);
+}
+
+// host copies of cnt inner products <x, V[:, i]> (V columns of length N, ld N)
+static kkt_status dots(kkt_handle h, const double* x, const double* V, int64_t N, int cnt, double* out,
+                       cudaStream_t st) {
+  CK(launch_multidot(x, V, N, N, cnt, h->kpart, h->kdots, st));
+  CK(cudaMemcpyAsync(out, h->kdots, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return KKT_OK;
+}
+
+// one solve of K_delta [x; y] = [bx; by] through eqs. Schur1/Schur2 with the
+// variant's Krylov method; ox, oy receive (accumulate = 0) or gain the result
+static kkt_status variant_pass(kkt_handle h, const double* bx, const double* by, double* ox, double* oy,
+                               int accumulate, int* iters, int* status, cudaStream_t st) {
+  const Plan& P = h->P;
+  const int64_t n = P.n, m = P.m;
+  const double g = h->gamma, dl = h->delta;
+  // workspace: n-vectors rhx, w, t1, t2, t3; m-vectors y, r, z (r and z adjacent), p, q, a, d,
+  // v_old, v, w2, w1, wk
+  double* rhx = h->kv;
+  double* w = rhx + n;
+  double* t1 = w + n;
+  double* t2 = t1 + n;
+  double* t3 = t2 + n;
+  double* y = t3 + n;
+  double* r = y + m;
+  double* z = r + m;
+  double* p = z + m;
+  double* q = p + m;
+  double* a = q + m;
+  double* d = a + m;
+  double* vo = d + m;
+  double* v = vo + m;
+  double* w2 = v + m;
+  double* w1 = w2 + m;
+  double* wk = w1 + m;
+  auto jt = [&](const double* yy, double alpha, double beta, double* out) {
+    return launch_jt_mult(n, h->JTo_ptr, h->JTo_row, h->JTo_vidx, h->Jv, yy, alpha, beta, out, st);
+  };
+  auto jm = [&](const double* xx, double alpha, double beta, double* out) {
+    return launch_j_mult(m, h->J_rowptr, h->J_colidx, h->Jv, xx, alpha, beta, out, st);
+  };
+  kkt_status s;
+  // r^_x = bx + gamma J^T by, w = H^-1 r^_x, b_S = J w - by (into r)
+  CK(launch_axpby(n, 1.0, bx, 0.0, rhx, st));
+  CK(jt(by, g, 1.0, rhx));
+  if ((s = hinv(h, rhx, w, st))) return s;
+  CK(launch_axpby(m, -1.0, by, 0.0, r, st));
+  CK(jm(w, 1.0, 1.0, r));
+  CK(cudaMemsetAsync(y, 0, sizeof(double) * m, st));
+  double dd[2];
+  if ((s = dots(h, r, r, m, 1, dd, st))) return s;
+  const double nb = std::sqrt(dd[0]);
+  const double tol = h->opt.cg_rtol * nb;
+  const int maxit = h->opt.cg_maxit;
+  int it = 0;
+  *status = 0;
+  // q = S p
+  auto sprod = [&](const double* pp, double* qq) -> kkt_status {
+    CK(jt(pp, 1.0, 0.0, t1));
+    kkt_status e = hinv(h, t1, t2, st);
+    if (e) return e;
+    CK(jm(t2, 1.0, 0.0, qq));
+    return KKT_OK;
+  };
+  // zz = M rr = (J J^T)^-1 J H_gamma J^T (J J^T)^-1 rr
+  auto mprec = [&](const double* rr, double* zz) -> kkt_status {
+    kkt_status e = kkt_hsolve(h->jjt, rr, a, st);
+    if (e) return e;
+    CK(jt(a, 1.0, 0.0, t1));
+    CK(launch_hsym_mult(n, h->Hs_ptr, h->Hs_col, h->Hs_vidx, h->Hv, t1, dl, t3, st));
+    CK(jm(t1, 1.0, 0.0, d));
+    CK(jt(d, g, 1.0, t3));
+    CK(jm(t3, 1.0, 0.0, d));
+    return kkt_hsolve(h->jjt, d, zz, st);
+  };
+  if (nb > 0 && h->opt.krylov == 1) {
+    const bool pre = h->jjt_ok;
+    if (pre) { if ((s = mprec(r, z))) return s; }
+    else CK(launch_axpby(m, 1.0, r, 0.0, z, st));
+    CK(launch_axpby(m, 1.0, z, 0.0, p, st));
+    if ((s = dots(h, r, z, m, 1, dd, st))) return s;
+    double rho = dd[0];
+    for (;;) {
+      if (it >= maxit) { *status = 4; break; }
+      if ((s = sprod(p, q))) return s;
+      if ((s = dots(h, p, q, m, 1, dd, st))) return s;
+      if (!(dd[0] > 0)) { *status = 3; break; }
+      const double al = rho / dd[0];
+      CK(launch_axpby(m, al, p, 1.0, y, st));
+      CK(launch_axpby(m, -al, q, 1.0, r, st));
+      it++;
+      if (pre) { if ((s = mprec(r, z))) return s; }
+      else CK(launch_axpby(m, 1.0, r, 0.0, z, st));
+      if ((s = dots(h, r, r, m, 2, dd, st))) return s;   // r.r and r.z (z follows r)
+      if (std::sqrt(dd[0]) <= tol) break;
+      const double be = dd[1] / rho;
+      rho = dd[1];
+      CK(launch_axpby(m, 1.0, z, be, p, st));
+    }
+  } else if (nb > 0) {
+    // MINRES: Lanczos on S from b_S / ||b_S||, Givens QR of the tridiagonal
+    CK(cudaMemsetAsync(vo, 0, sizeof(double) * m, st));
+    CK(cudaMemsetAsync(w2, 0, sizeof(double) * m, st));
+    CK(cudaMemsetAsync(w1, 0, sizeof(double) * m, st));
+    CK(launch_axpby(m, 1.0 / nb, r, 0.0, v, st));
+    double beta = nb, eta = nb, c_old = 1.0, c = 1.0, s_old = 0.0, sn = 0.0;
+    for (;;) {
+      if (it >= maxit) { *status = 4; break; }
+      if ((s = sprod(v, p))) return s;
+      if ((s = dots(h, v, p, m, 1, dd, st))) return s;
+      const double al = dd[0];
+      CK(launch_axpby(m, -al, v, 1.0, p, st));
+      CK(launch_axpby(m, -beta, vo, 1.0, p, st));
+      if ((s = dots(h, p, p, m, 1, dd, st))) return s;
+      const double bn = std::sqrt(dd[0]);
+      const double dlt = c * al - c_old * sn * beta;
+      const double r1 = std::hypot(dlt, bn);
+      const double r2 = sn * al + c_old * c * beta;
+      const double r3 = s_old * beta;
+      if (!(r1 > 0)) { *status = 3; break; }
+      const double cn = dlt / r1, snn = bn / r1;
+      // wk = (v - r3 w2 - r2 w1) / r1
+      CK(launch_axpby(m, 1.0 / r1, v, 0.0, wk, st));
+      CK(launch_axpby(m, -r3 / r1, w2, 1.0, wk, st));
+      CK(launch_axpby(m, -r2 / r1, w1, 1.0, wk, st));
+      CK(launch_axpby(m, cn * eta, wk, 1.0, y, st));
+      eta = -snn * eta;
+      it++;
+      if (std::fabs(eta) <= tol || bn == 0.0) break;
+      std::swap(vo, v);                                   // v_old <- v
+      CK(launch_axpby(m, 1.0 / bn, p, 0.0, v, st));       // v <- p / beta_new
+      std::swap(w2, w1);                                  // w2 <- w1
+      std::swap(w1, wk);                                  // w1 <- wk
+      c_old = c; c = cn; s_old = sn; sn = snn;
+      beta = bn;
+    }
+  }
+  *iters = it;
+  // x = H^-1 (r^_x - J^T y)
+  CK(launch_axpby(n, 1.0, rhx, 0.0, t3, st));
+  CK(jt(y, -1.0, 1.0, t3));
+  if ((s = hinv(h, t3, t1, st))) return s;
+  CK(launch_axpby(n, 1.0, t1, accumulate ? 1.0 : 0.0, ox, st));
+  CK(launch_axpby(m, 1.0, y, accumulate ? 1.0 : 0.0, oy, st));
+  return KKT_OK;
+}
+
+static kkt_status solve_variant(kkt_handle h, const double* rx, const double* ry, double* dx, double* dy,
+                                cudaStream_t st) {
+  const int64_t n = h->P.n, m = h->P.m;
+  h->inertia_ok = 0;
+  std::memset(&h->info, 0, sizeof(h->info));
+  if (!h->kv) {
+    h->kv = h->mem.alloc<double>(5 * (size_t)n + 12 * (size_t)std::max<int64_t>(m, 1));
+    h->kpart = h->mem.alloc<double>(296 * (size_t)kMaxKrylov);
+    h->kdots = h->mem.alloc<double>(kMaxKrylov);
+    if (h->mem.failed) return KKT_ERR_OOM;
+  }
+  kkt_status s = reset_status(h, st);
+  if (s) return s;
+  int total = 0;
+  for (int pass = 0;; pass++) {
+    const double* bx = pass == 0 ? rx : h->res_x;
+    const double* by = pass == 0 ? ry : h->res_y;
+    int it = 0, cst = 0;
+    if ((s = variant_pass(h, bx, by, dx, dy, pass > 0, &it, &cst, st))) return s;
+    total += it;
+    if ((s = residual(h, rx, ry, dx, dy, st))) return s;
+    if ((s = read_status(h, st))) return s;
+    const DevStatus& d = *h->hst;
+    h->info.cg_iters = total;
+    h->info.ir_steps = pass;
+    h->info.cg_status = cst;
+    h->info.rr = d.rr;
+    h->info.be = d.be;
+    if (d.abort) return KKT_ERR_TIMEOUT;
+    if (cst == 3) return KKT_ERR_CG_BREAKDOWN;
+    if (cst == 4) return KKT_ERR_CG_MAXIT;
+    if (!(d.rr > h->opt.ir_rtol) || pass >= h->opt.ir_maxit) break;
+  }
+  h->inertia_ok = 1;
+  return KKT_OK;
+}
+
 static kkt_status solve_common(kkt_handle h, const double* rx, const double* ry, double* dx, double* dy,
                                cudaStream_t st) {
   if (!h->factored) return KKT_ERR_STATE;
+  if (h->opt.krylov != 0) return solve_variant(h, rx, ry, dx, dy, st);
   if (h->opt.precision == KKT_MIXED && h->opt.refine == 2) {
     h->inertia_ok = 0;
     std::memset(&h->info, 0, sizeof(h->info));
@@ -1005,7 +1267,7 @@ extern "C" {
 kkt_status kkt_factor_batch(kkt_handle h, int32_t nsys, const double* H_vals, const double* J_vals,
                             double delta, double gamma, int32_t* status, void* stream) {
   if (!h || nsys < 1 || !H_vals || (h->nnzJ > 0 && !J_vals)) return KKT_ERR_INVALID;
-  if (!h->on_device || h->opt.ruiz_iters > 0) return KKT_ERR_STATE;
+  if (!h->on_device || h->opt.ruiz_iters > 0 || h->opt.krylov != 0) return KKT_ERR_STATE;
   CK(cudaSetDevice(h->device));
   cudaStream_t st = (cudaStream_t)stream;
   const size_t es = h->opt.precision == KKT_FP64 ? sizeof(double) : sizeof(float);
@@ -1054,7 +1316,7 @@ kkt_status kkt_factor_batch(kkt_handle h, int32_t nsys, const double* H_vals, co
 kkt_status kkt_solve_batch(kkt_handle h, int32_t nsys, const double* r_x, const double* r_y, double* dx,
                            double* dy, kkt_info* info, int32_t* status, void* stream) {
   if (!h || nsys < 1 || !r_x || !dx || (h->P.m > 0 && (!r_y || !dy))) return KKT_ERR_INVALID;
-  if (!h->on_device || h->opt.ruiz_iters > 0) return KKT_ERR_STATE;
+  if (!h->on_device || h->opt.ruiz_iters > 0 || h->opt.krylov != 0) return KKT_ERR_STATE;
   if (nsys > (int32_t)h->bstatus.size()) return KKT_ERR_STATE;
   CK(cudaSetDevice(h->device));
   cudaStream_t st = (cudaStream_t)stream;
@@ -1089,7 +1351,7 @@ kkt_status kkt_solve_batch(kkt_handle h, int32_t nsys, const double* r_x, const 
 kkt_status kkt_solve_multi(kkt_handle h, int32_t nrhs, const double* r_x, const double* r_y, double* dx,
                            double* dy, kkt_info* info, void* stream) {
   if (!h || nrhs < 1 || !r_x || !dx || (h->P.m > 0 && (!r_y || !dy))) return KKT_ERR_INVALID;
-  if (!h->on_device || h->opt.ruiz_iters > 0) return KKT_ERR_STATE;
+  if (!h->on_device || h->opt.ruiz_iters > 0 || h->opt.krylov != 0) return KKT_ERR_STATE;
   if (!h->factored) return KKT_ERR_STATE;
   CK(cudaSetDevice(h->device));
   cudaStream_t st = (cudaStream_t)stream;
@@ -1190,7 +1452,7 @@ kkt_status kkt_factor_regularized(kkt_handle h, const double* H_vals, const doub
     else if (h->hst->fail_col != INT_MAX) s = KKT_ERR_NOT_SPD;
     else {
       h->factored = true;
-      s = KKT_OK;
+      s = post_factor(h, st);
     }
   }
   if (s == KKT_OK) h->delta_prev = d1;

@@ -126,6 +126,16 @@ cudaError_t launch_multidot(const double* w, const double* V, int64_t ld, int64_
 cudaError_t launch_lincomb(double* y, double alpha, const double* V, int64_t ld, int64_t N, int cnt, const double* c,
                            cudaStream_t st);
 constexpr int kRedStride = 2 * kMaxRhs;   // doubles per CTA in the reduction buffer
+// FP64 products of the Krylov variants on S (krylov.cu)
+cudaError_t launch_jt_mult(int64_t n, const int64_t* tp, const int32_t* trow, const int32_t* tv, const double* Jv,
+                           const double* y, double alpha, double beta, double* out, cudaStream_t st);
+cudaError_t launch_j_mult(int64_t m, const int64_t* jp, const int32_t* jc, const double* Jv, const double* x,
+                          double alpha, double beta, double* out, cudaStream_t st);
+cudaError_t launch_hsym_mult(int64_t n, const int64_t* hp, const int32_t* hc, const int32_t* hv, const double* Hv,
+                             const double* x, double delta, double* out, cudaStream_t st);
+cudaError_t launch_axpby(int64_t N, double a, const double* x, double b, double* y, cudaStream_t st);
+cudaError_t launch_jjt_values(int64_t ne, const int64_t* pp, const int32_t* pa, const int32_t* pb, const double* Jv,
+                              double* out, cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_solve(const SolveArgs<T>& a, int grid, int ctas, cudaStream_t st);

@@ -86,4 +86,78 @@ cudaError_t launch_lincomb(double* y, double alpha, const double* V, int64_t ld,
   return cudaGetLastError();
 }
 
+// ------------------------------------------------ Krylov variants on S (FP64)
+// out = beta * out + alpha * J^T y   (J^T by column, original labels; no atomics)
+__global__ void k_jt_mult(int64_t n, const int64_t* __restrict__ tp, const int32_t* __restrict__ trow,
+                          const int32_t* __restrict__ tv, const double* __restrict__ Jv, const double* __restrict__ y,
+                          double alpha, double beta, double* __restrict__ out) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int64_t q = tp[c]; q < tp[c + 1]; q++) s += Jv[tv[q]] * y[trow[q]];
+    out[c] = (beta == 0.0 ? 0.0 : beta * out[c]) + alpha * s;
+  }
+}
+// out = beta * out + alpha * J x
+__global__ void k_j_mult(int64_t m, const int64_t* __restrict__ jp, const int32_t* __restrict__ jc,
+                         const double* __restrict__ Jv, const double* __restrict__ x, double alpha, double beta,
+                         double* __restrict__ out) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < m; r += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int64_t q = jp[r]; q < jp[r + 1]; q++) s += Jv[q] * x[jc[q]];
+    out[r] = (beta == 0.0 ? 0.0 : beta * out[r]) + alpha * s;
+  }
+}
+// out = H~ x + delta x (H~ from its full symmetric pattern, original labels)
+__global__ void k_hsym_mult(int64_t n, const int64_t* __restrict__ hp, const int32_t* __restrict__ hc,
+                            const int32_t* __restrict__ hv, const double* __restrict__ Hv, const double* __restrict__ x,
+                            double delta, double* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double s = delta * x[i];
+    for (int64_t q = hp[i]; q < hp[i + 1]; q++) s += Hv[hv[q]] * x[hc[q]];
+    out[i] = s;
+  }
+}
+// y = a * x + b * y
+__global__ void k_axpby(int64_t N, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
+    y[k] = a * x[k] + (b == 0.0 ? 0.0 : b * y[k]);
+}
+// lower values of J J^T: entry e = sum of J[qa] J[qb] over its pairs
+__global__ void k_jjt_values(int64_t ne, const int64_t* __restrict__ pp, const int32_t* __restrict__ pa,
+                             const int32_t* __restrict__ pb, const double* __restrict__ Jv, double* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int64_t q = pp[e]; q < pp[e + 1]; q++) s += Jv[pa[q]] * Jv[pb[q]];
+    out[e] = s;
+  }
+}
+
+cudaError_t launch_jt_mult(int64_t n, const int64_t* tp, const int32_t* trow, const int32_t* tv, const double* Jv,
+                           const double* y, double alpha, double beta, double* out, cudaStream_t st) {
+  k_jt_mult<<<krylov_grid(n), kKrylovThreads, 0, st>>>(n, tp, trow, tv, Jv, y, alpha, beta, out);
+  return cudaGetLastError();
+}
+cudaError_t launch_j_mult(int64_t m, const int64_t* jp, const int32_t* jc, const double* Jv, const double* x,
+                          double alpha, double beta, double* out, cudaStream_t st) {
+  if (m == 0) return cudaSuccess;
+  k_j_mult<<<krylov_grid(m), kKrylovThreads, 0, st>>>(m, jp, jc, Jv, x, alpha, beta, out);
+  return cudaGetLastError();
+}
+cudaError_t launch_hsym_mult(int64_t n, const int64_t* hp, const int32_t* hc, const int32_t* hv, const double* Hv,
+                             const double* x, double delta, double* out, cudaStream_t st) {
+  k_hsym_mult<<<krylov_grid(n), kKrylovThreads, 0, st>>>(n, hp, hc, hv, Hv, x, delta, out);
+  return cudaGetLastError();
+}
+cudaError_t launch_axpby(int64_t N, double a, const double* x, double b, double* y, cudaStream_t st) {
+  if (N == 0) return cudaSuccess;
+  k_axpby<<<krylov_grid(N), kKrylovThreads, 0, st>>>(N, a, x, b, y);
+  return cudaGetLastError();
+}
+cudaError_t launch_jjt_values(int64_t ne, const int64_t* pp, const int32_t* pa, const int32_t* pb, const double* Jv,
+                              double* out, cudaStream_t st) {
+  if (ne == 0) return cudaSuccess;
+  k_jjt_values<<<krylov_grid(ne), kKrylovThreads, 0, st>>>(ne, pp, pa, pb, Jv, out);
+  return cudaGetLastError();
+}
+
 }  // namespace kkt

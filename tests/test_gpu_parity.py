@@ -719,3 +719,30 @@ def test_ruiz_scaling_matches_oracle(name, precision):
     with pytest.raises(K.KKTError):
         s.solve_multi(cu(np.stack([sys.r_x] * 2)), cu(np.stack([sys.r_y] * 2)))
     s.close()
+
+
+@pytest.mark.parametrize("method,code", [("pcg", 1), ("minres", 2)])
+@pytest.mark.parametrize("name", ["grid2d_n2000", "tiny"])
+def test_schur_krylov_variants_match_oracle(name, method, code):
+    """Sec. 4's variants on the device (FP64): CG preconditioned by
+    M = (J J^T)^-1 J H_gamma J^T (J J^T)^-1 and MINRES on S, against the
+    oracle's restatement: same solution to 1e-9, iteration counts within 1,
+    RR <= 1e-10 (one refinement pass at most)."""
+    sys = W.make_config(name) if name != "tiny" else W.random_tiny_system(23, n_lo=60, n_hi=100, density=0.08)
+    sym = O.Symbolic(sys.n, sys.m, sys.H_colptr, sys.H_rowidx, sys.J_rowptr, sys.J_colidx)
+    fac = O.Factor(sym, sys.H_vals, sys.J_vals, sys.delta, sys.gamma)
+    odx, ody, oit = O.schur_variant(fac, sys, method)
+    s, c, dx, dy = gpu_solve(sys, "fp64", krylov=code)
+    assert c == 0
+    assert rel(np.concatenate([dx, dy]), np.concatenate([odx, ody])) <= 1e-9
+    assert s.info.rr <= 1e-10
+    assert abs(s.info.cg_iters - oit) <= 1 + s.info.ir_steps * (oit + 1)
+    if s.info.ir_steps == 0:
+        assert abs(s.info.cg_iters - oit) <= 1
+    s.close()
+
+
+def test_schur_krylov_variants_need_fp64():
+    sys = W.make_config("grid2d_n2000")
+    with pytest.raises(K.KKTError):
+        K.KKTSolver(sys.n, sys.m, sys.H_colptr, sys.H_rowidx, sys.J_rowptr, sys.J_colidx, precision="mixed", krylov=1)

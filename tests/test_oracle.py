@@ -678,3 +678,52 @@ def test_ruiz_scaled_solve_recovers_the_original_solution(seed):
     got = np.concatenate([Dx * dxh, Dy * dyh])
     ref = np.linalg.solve(dense_K(sys, 0.0), np.concatenate([sys.r_x, sys.r_y]))
     assert np.linalg.norm(got - ref) <= 1e-8 * np.linalg.norm(ref)
+
+
+# ----------------------------------------------------------------- Krylov variants (Sec. 4)
+@pytest.mark.parametrize("method", ["pcg", "minres"])
+@pytest.mark.parametrize("seed", range(6))
+def test_schur_variants_match_dense_lu(method, seed):
+    """PCG with M = (J J^T)^-1 J H_gamma J^T (J J^T)^-1 and MINRES on eq.
+    Schur1 reach the dense LU solution of K_delta."""
+    sys = W.random_tiny_system(seed + 1200, n_lo=20, n_hi=90, density=0.08)
+    sym = sym_of(sys)
+    fac = O.Factor(sym, sys.H_vals, sys.J_vals, sys.delta, sys.gamma)
+    assert fac.ok
+    dx, dy, it = O.schur_variant(fac, sys, method)
+    ref = np.linalg.solve(dense_K(sys), np.concatenate([sys.r_x, sys.r_y]))
+    assert np.linalg.norm(np.concatenate([dx, dy]) - ref) <= 1e-9 * np.linalg.norm(ref)
+    assert 1 <= it <= sys.m + 2
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_pcg_with_square_j_converges_in_one_step(seed):
+    """With J square (m = n) the preconditioner is exactly S^-1 (Sec. 4:
+    M gives the exact solution when J is square), so PCG stops after one
+    product."""
+    rng = np.random.default_rng(seed)
+    n = 15
+    A = rng.standard_normal((n, n))
+    H = A @ A.T + n * np.eye(n)
+    J = np.eye(n) + 0.3 * rng.standard_normal((n, n))
+    sys = make_sys(H, J, rng.standard_normal(n), rng.standard_normal(n), gamma=10.0)
+    fac = O.Factor(sym_of(sys), sys.H_vals, sys.J_vals, sys.delta, sys.gamma)
+    dx, dy, it = O.schur_variant(fac, sys, "pcg")
+    assert it == 1
+    ref = np.linalg.solve(dense_K(sys), np.concatenate([sys.r_x, sys.r_y]))
+    assert np.linalg.norm(np.concatenate([dx, dy]) - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("alpha,gamma", [(1.0, 1e2), (3.0, 1e4)])
+def test_minres_on_identity_schur_complement_takes_one_step(alpha, gamma):
+    """H~ = alpha I, J = [I 0]: S = I / (alpha + gamma), a multiple of the
+    identity, so the first Lanczos step spans the solution."""
+    n, m = 12, 5
+    rng = np.random.default_rng(9)
+    J = np.zeros((m, n))
+    J[np.arange(m), np.arange(m)] = 1.0
+    sys = make_sys(alpha * np.eye(n), J, rng.standard_normal(n), rng.standard_normal(m), gamma=gamma)
+    fac = O.Factor(sym_of(sys), sys.H_vals, sys.J_vals, sys.delta, sys.gamma)
+    dx, dy, it = O.schur_variant(fac, sys, "minres")
+    assert it == 1
+    np.testing.assert_allclose(dy, sys.r_x[:m] - alpha * sys.r_y, rtol=1e-11, atol=1e-11)
