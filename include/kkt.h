@@ -122,6 +122,10 @@ typedef struct kkt_options {
                           2 = MINRES. 1 and 2 need KKT_FP64, run the Krylov loop from the
                           host with device vectors, no delta_2 restart, and are not used by
                           kkt_solve_multi or the batched form (KKT_ERR_STATE) */
+  int32_t solve_sms;   /* 0 (default): the persistent solve kernel's grid covers every SM;
+                          k >= 1: at most k SMs' worth of its CTAs, so that several handles'
+                          solves (one per stream, e.g. the request server's slots) can be
+                          resident at once */
 } kkt_options;
 
 /* Kernel kinds reported by kkt_get_profile. Kinds a plan does not launch
@@ -414,6 +418,64 @@ kkt_status kkt_residual_noalloc(int64_t n, int64_t m, const int64_t* H_colptr, c
                                 double* norms, void* stream);
 
 const char* kkt_status_string(kkt_status s);
+
+/* ---------------------------------------------------------------------------
+ * Request server: continuous batching of KKT solves over resident patterns.
+ * The paper's method is a sequence of interior iterations on one sparsity
+ * pattern (Sec. 2: analysis once, then value refactorizations and solves);
+ * the server holds several patterns' analyses and, per pattern, "slots" --
+ * handles with their factor storage and workspace resident on the device --
+ * and runs the requests that arrive (one value refactorization + solve each)
+ * as slots and device memory free up. Admission is by an HBM budget: a
+ * request starts as soon as its pattern has an idle slot, or a new slot fits
+ * the budget; the pending list is scanned in arrival order and a request
+ * that cannot start does not block later ones of other patterns. Up to
+ * max_inflight requests run at once, each on its slot's own CUDA stream and
+ * host worker thread, so their kernels overlap on the device. Results do not
+ * depend on what else runs (each slot is a separate handle).
+ * ------------------------------------------------------------------------ */
+typedef struct kkt_server_s* kkt_server;
+
+typedef struct kkt_request_info {
+  int32_t status;      /* kkt_status of the factor + solve */
+  int32_t pattern, slot;
+  int32_t cg_iters, ir_steps, pad;
+  double rr, be;       /* as kkt_info */
+  double t_submit, t_start, t_end;  /* seconds on the server's clock (steady, from its creation) */
+} kkt_request_info;
+
+typedef struct kkt_server_stats {
+  int64_t submitted, completed, failed;
+  int64_t bytes_used, bytes_peak, budget;  /* device bytes of the slots (estimated before a
+                                              slot's first solve allocates its refinement
+                                              workspace, exact after) */
+  int32_t patterns, slots, inflight, peak_inflight, waiting, pad;
+} kkt_server_stats;
+
+/* budget_bytes: device memory the slots may hold (<= 0: 90 % of the free
+ * memory at creation); max_inflight: requests run at once (>= 1); opt: the
+ * options of every slot (NULL: defaults), opt->device the GPU. */
+kkt_status kkt_server_create(int64_t budget_bytes, int32_t max_inflight, const kkt_options* opt,
+                             kkt_server* out);
+/* Analyses a pattern (host, as kkt_analyse_host) and creates its first
+ * slot; *pattern_id receives its index. KKT_ERR_OOM when that slot does not
+ * fit the budget. Patterns as for kkt_analyse (host arrays). */
+kkt_status kkt_server_add_pattern(kkt_server s, int64_t n, int64_t m, const int64_t* H_colptr,
+                                  const int32_t* H_rowidx, const int64_t* J_rowptr, const int32_t* J_colidx,
+                                  int32_t* pattern_id);
+/* Queues one request: factor H_vals/J_vals (delta, gamma) on a slot of the
+ * pattern, then solve r_x, r_y into dx, dy. All six are DEVICE arrays of the
+ * pattern's sizes that must stay valid (inputs unchanged) until the request
+ * completes. Returns at once with *request_id. */
+kkt_status kkt_server_submit(kkt_server s, int32_t pattern_id, const double* H_vals, const double* J_vals,
+                             double delta, double gamma, const double* r_x, const double* r_y, double* dx,
+                             double* dy, int64_t* request_id);
+/* Blocks until the request completes and returns its record (once per id;
+ * the id is then forgotten). The request's own status is in info->status. */
+kkt_status kkt_server_wait(kkt_server s, int64_t request_id, kkt_request_info* info);
+kkt_status kkt_server_get_stats(kkt_server s, kkt_server_stats* out);
+/* Waits for every queued request, then releases all slots and patterns. */
+kkt_status kkt_server_destroy(kkt_server s);
 
 /* ------------------------------------------------------------------------
  * The 4x4 form (Sec. 3, eq. linsys4x4):

@@ -38,7 +38,7 @@ class kkt_options(C.Structure):
                 ("spin_cycles", C.c_int64), ("profile", C.c_int32), ("nd_leaf", C.c_int32),
                 ("tensor_cores", C.c_int32), ("solve_ctas", C.c_int32), ("solve_ent", C.c_int32),
                 ("refine", C.c_int32), ("ruiz_iters", C.c_int32),
-                ("krylov", C.c_int32)]
+                ("krylov", C.c_int32), ("solve_sms", C.c_int32)]
 
 
 class kkt_info(C.Structure):
@@ -52,6 +52,19 @@ class kkt_symbolic_info(C.Structure):
                 ("npieces", C.c_int64), ("nchunks", C.c_int64), ("nlevels", C.c_int32), ("pad", C.c_int32),
                 ("flops", C.c_double), ("device_bytes", C.c_double), ("fwd_depth", C.c_int64),
                 ("bwd_depth", C.c_int64), ("nsub", C.c_int64), ("nitems", C.c_int64), ("tc_flops", C.c_double)]
+
+
+class kkt_request_info(C.Structure):
+    _fields_ = [("status", C.c_int32), ("pattern", C.c_int32), ("slot", C.c_int32), ("cg_iters", C.c_int32),
+                ("ir_steps", C.c_int32), ("pad", C.c_int32), ("rr", C.c_double), ("be", C.c_double),
+                ("t_submit", C.c_double), ("t_start", C.c_double), ("t_end", C.c_double)]
+
+
+class kkt_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
+                ("bytes_used", C.c_int64), ("bytes_peak", C.c_int64), ("budget", C.c_int64),
+                ("patterns", C.c_int32), ("slots", C.c_int32), ("inflight", C.c_int32),
+                ("peak_inflight", C.c_int32), ("waiting", C.c_int32), ("pad", C.c_int32)]
 
 
 def _load():
@@ -69,6 +82,15 @@ def _load():
     L.kkt_factor_regularized.argtypes = [P, P, P, D, D, D, P, P]
     L.kkt_set_delta_prev.argtypes = [P, D]
     L.kkt_set_profile.argtypes = [P, I32]
+    L.kkt_server_create.argtypes = [I64, I32, C.POINTER(kkt_options), C.POINTER(P)]
+    L.kkt_server_add_pattern.argtypes = [P, I64, I64, P, P, P, P, C.POINTER(I32)]
+    L.kkt_server_submit.argtypes = [P, I32, P, P, D, D, P, P, P, P, C.POINTER(I64)]
+    L.kkt_server_wait.argtypes = [P, I64, C.POINTER(kkt_request_info)]
+    L.kkt_server_get_stats.argtypes = [P, C.POINTER(kkt_server_stats)]
+    L.kkt_server_destroy.argtypes = [P]
+    for nm in ("kkt_server_create", "kkt_server_add_pattern", "kkt_server_submit", "kkt_server_wait",
+               "kkt_server_get_stats", "kkt_server_destroy"):
+        getattr(L, nm).restype = I32
     L.kkt_get_scaling.argtypes = [P, P]
     L.kkt_analyse_like.argtypes = [P, C.POINTER(kkt_options), C.POINTER(P)]
     L.kkt_factor_batch.argtypes = [P, I32, P, P, D, D, P, P]
@@ -105,7 +127,8 @@ def _load():
 
 
 _lib = _load()
-EXPORTED = ("kkt_default_options", "kkt_analyse", "kkt_analyse_host", "kkt_factor", "kkt_solve", "kkt_solve_multi", "kkt_factor_batch", "kkt_solve_batch", "kkt_factor_regularized", "kkt_set_delta_prev", "kkt_set_profile", "kkt_get_scaling", "kkt_analyse_like", "kkt_factor_solve_host",
+EXPORTED = ("kkt_default_options", "kkt_analyse", "kkt_analyse_host", "kkt_factor", "kkt_solve", "kkt_solve_multi", "kkt_factor_batch", "kkt_solve_batch", "kkt_factor_regularized", "kkt_set_delta_prev", "kkt_set_profile", "kkt_get_scaling", "kkt_analyse_like", "kkt_server_create", "kkt_server_add_pattern",
+            "kkt_server_submit", "kkt_server_wait", "kkt_server_get_stats", "kkt_server_destroy", "kkt_factor_solve_host",
             "kkt_hsolve", "kkt_get_info", "kkt_inertia", "kkt_symbolic_info_get", "kkt_get_symbolic",
             "kkt_get_factor_panels", "kkt_get_profile", "kkt_get_solve_counters", "kkt_residual_noalloc",
             "kkt_get_solve_trace", "kkt_get_solve_item_order", "kkt_destroy", "kkt_status_string", "kkt_analyse_4x4", "kkt_analyse_4x4_host", "kkt_4x4_inner",
@@ -597,4 +620,67 @@ class KKTSolver4x4:
         try:
             self.close()
         except Exception:
+            pass
+
+
+class KKTServer:
+    """Continuous-batching request server over resident patterns (the
+    library's kkt_server_*): add patterns, submit value refactorizations +
+    solves with device tensors, wait for their records.
+
+    >>> srv = KKTServer(budget_bytes=0, max_inflight=4, precision="mixed", ordering="nd")
+    >>> pid = srv.add_pattern(n, m, H_colptr, H_rowidx, J_rowptr, J_colidx)
+    >>> rid = srv.submit(pid, H_vals, J_vals, delta, gamma, r_x, r_y, dx, dy)
+    >>> info = srv.wait(rid)
+    """
+
+    def __init__(self, budget_bytes=0, max_inflight=4, **options):
+        self.opt = kkt_default_options(**options)
+        h = C.c_void_p()
+        _check("kkt_server_create", _lib.kkt_server_create(int(budget_bytes), int(max_inflight), C.byref(self.opt),
+                                                           C.byref(h)))
+        self.h = h
+        self._sizes = []
+        self._keep = {}
+
+    def add_pattern(self, n, m, H_colptr, H_rowidx, J_rowptr, J_colidx):
+        keep = [_np(H_colptr, np.int64), _np(H_rowidx, np.int32), _np(J_rowptr, np.int64), _np(J_colidx, np.int32)]
+        pid = C.c_int32(0)
+        _check("kkt_server_add_pattern", _lib.kkt_server_add_pattern(self.h, int(n), int(m), keep[0][1], keep[1][1],
+                                                                     keep[2][1], keep[3][1], C.byref(pid)))
+        self._sizes.append((int(n), int(m), int(np.asarray(H_colptr)[-1]), int(np.asarray(J_rowptr)[-1]) if m else 0))
+        return pid.value
+
+    def submit(self, pattern, H_vals, J_vals, delta, gamma, r_x, r_y, dx, dy):
+        """All tensors on the device; they must stay alive and unchanged until
+        wait() returns for this request (the server keeps references)."""
+        n, m, nh, nj = self._sizes[pattern]
+        rid = C.c_int64(0)
+        _check("kkt_server_submit", _lib.kkt_server_submit(
+            self.h, int(pattern), _dev(H_vals, nh), _dev(J_vals, nj), float(delta), float(gamma), _dev(r_x, n),
+            _dev(r_y, m), _dev(dx, n), _dev(dy, m), C.byref(rid)))
+        self._keep[rid.value] = (H_vals, J_vals, r_x, r_y, dx, dy)
+        return rid.value
+
+    def wait(self, rid):
+        info = kkt_request_info()
+        _check("kkt_server_wait", _lib.kkt_server_wait(self.h, int(rid), C.byref(info)))
+        self._keep.pop(rid, None)
+        return info
+
+    def stats(self):
+        st = kkt_server_stats()
+        _check("kkt_server_get_stats", _lib.kkt_server_get_stats(self.h, C.byref(st)))
+        return st
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.kkt_server_destroy(self.h)
+            self.h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
             pass

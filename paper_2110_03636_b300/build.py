@@ -9,7 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libkkt.so")
-SOURCES = ["symbolic.cpp", "plan.cpp", "factor.cu", "solve.cu", "api.cu", "noalloc.cu", "four.cu", "krylov.cu", "tc_update.cu", "scale.cu"]
+SOURCES = ["symbolic.cpp", "plan.cpp", "factor.cu", "solve.cu", "api.cu", "noalloc.cu", "four.cu", "krylov.cu", "tc_update.cu", "scale.cu", "serve.cpp"]
 HEADERS = ["symbolic.hpp", "plan.hpp", "common.cuh", "kernels.cuh"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",

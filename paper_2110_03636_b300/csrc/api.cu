@@ -247,6 +247,7 @@ void kkt_default_options(kkt_options* o) {
   o->tensor_cores = 1;
   o->ruiz_iters = 0;
   o->krylov = 0;
+  o->solve_sms = 0;
 }
 
 const char* kkt_status_string(kkt_status s) {
@@ -298,7 +299,7 @@ static kkt_status analyse_host_impl(int64_t n, int64_t m, const int64_t* Hp, con
   const kkt_options& o = h->opt;
   if ((o.solve_w != 0 && (o.solve_w < 32 || o.solve_w > 256)) || o.relax_den <= 0 || o.precision < 0 ||
       o.precision > 1 || o.solve_ctas < 0 || o.solve_ctas == 1 || o.solve_ctas > 4 || o.refine < 0 ||
-      o.refine > 2 || o.ruiz_iters < 0 || o.ruiz_iters > 100 || o.krylov < 0 || o.krylov > 2 ||
+      o.refine > 2 || o.ruiz_iters < 0 || o.ruiz_iters > 100 || o.krylov < 0 || o.krylov > 2 || o.solve_sms < 0 ||
       (o.krylov != 0 && o.precision != KKT_FP64) ||
       (o.solve_ent != 0 && (o.solve_ent < 2048 || o.solve_ent > 32768))) {
     delete h;
@@ -401,6 +402,7 @@ static kkt_status device_stage(kkt_handle h, kkt_handle* out) {
   h->grid = f64 ? solve_grid_size<double>(h->device, h->P.solve_w, h->P.ent, h->P.ent0, h->P.max_rows, h->ctas)
                 : solve_grid_size<float>(h->device, h->P.solve_w, h->P.ent, h->P.ent0, h->P.max_rows, h->ctas);
   if (h->grid <= 0) { delete h; return KKT_ERR_INVALID; }
+  if (o.solve_sms > 0) h->grid = std::min(h->grid, h->ctas * o.solve_sms);
   const Plan& P = h->P;
   DevArena& A = h->mem;
   auto as_int4 = [&](const std::vector<int32_t>& v) {
