@@ -432,6 +432,81 @@ def run_batching(args, dev, rank=0, world=1, group=None):
     return out
 
 
+# ------------------------------------------------------------------ serving form
+def run_serving(args, dev):
+    """The serving workload: 4 resident patterns (2-D grids 100^2 .. 800^2,
+    n = 1e4 .. 6.4e5, m = n/2, gamma = 1e6), requests = value updates of a
+    random pattern (barrier rescaled by 10^U(-1,1), new right-hand sides),
+    through the continuous-batching request server (HBM-budget admission,
+    4 requests in flight on their own streams). First the saturated rate (all
+    requests queued at once), then Poisson arrivals at 0.5 / 0.8 / 0.95 of it:
+    latency p50 / p99 (submission to completion) and served solves/s."""
+    import torch
+    import paper_2110_03636_b300 as K
+    import workloads as W
+    cu = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
+    sides = (100, 200, 400, 800)
+    nval = 3
+    srv = K.KKTServer(0, max_inflight=4, precision="mixed", ordering=args.ordering, solve_sms=37)
+    t0 = time.time()
+    vals, pids = [], []
+    for side in sides:
+        x = W.serving_pattern(side)
+        pids.append(srv.add_pattern(x.n, x.m, x.H_colptr, x.H_rowidx, x.J_rowptr, x.J_colidx))
+        vs = []
+        for t in range(nval):
+            x = W.rescale_barrier(x, seed=(side, t))
+            vs.append((cu(x.H_vals), cu(x.J_vals), x.delta, x.gamma, cu(x.r_x), cu(x.r_y),
+                       torch.empty(x.n, dtype=torch.float64, device=dev),
+                       torch.empty(x.m, dtype=torch.float64, device=dev)))
+        vals.append(vs)
+    t_setup = time.time() - t0
+    rng = np.random.default_rng(5)
+
+    def submit(k, p):
+        H, J, d, g, rx, ry, dx, dy = vals[p][k % nval]
+        # each in-flight request writes its own outputs: a fresh pair per request
+        return srv.submit(pids[p], H, J, d, g, rx, ry, torch.empty_like(dx), torch.empty_like(dy))
+
+    for p in range(len(sides)):                 # warm every pattern's first slot
+        srv.wait(submit(0, p))
+
+    def run(count, rate):
+        pats = rng.integers(0, len(sides), count)
+        gaps = rng.exponential(1.0 / rate, count) if rate else np.zeros(count)
+        ids = []
+        start = time.perf_counter()
+        due = start
+        for k in range(count):
+            due += gaps[k]
+            wait = due - time.perf_counter()
+            if wait > 0:
+                time.sleep(wait)
+            ids.append(submit(k, int(pats[k])))
+        infos = [srv.wait(r) for r in ids]
+        t_first = min(i.t_submit for i in infos)
+        t_last = max(i.t_end for i in infos)
+        lat = np.array([1e3 * (i.t_end - i.t_submit) for i in infos])
+        return {"requests": count, "solves_per_s": round(count / (t_last - t_first), 2),
+                "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 2),
+                               "p99": round(float(np.percentile(lat, 99)), 2)},
+                "rr_max": max(i.rr for i in infos), "failed": int(sum(i.status != 0 for i in infos))}
+
+    sat = run(args.serve_requests, None)
+    out = {"workload": "4 patterns: 2-D grids 100^2, 200^2, 400^2, 800^2 (n = 1e4 .. 6.4e5), m = n/2, gamma = 1e6; "
+                       "each request one value refactorization + solve (mixed)",
+           "server": "continuous batching, 4 in flight, HBM-budget admission (90 % of free memory)",
+           "setup_s": round(t_setup, 1), "saturated": sat}
+    lam = sat["solves_per_s"]
+    for f in (0.5, 0.8, 0.95):
+        out[f"poisson_{f}"] = dict(run(args.serve_requests, f * lam), arrival_rate=round(f * lam, 2))
+    st = srv.stats()
+    out["slots"], out["peak_inflight"] = st.slots, st.peak_inflight
+    out["device_gb_peak"] = round(st.bytes_peak / 1e9, 2)
+    srv.close()
+    return out
+
+
 # ------------------------------------------------------------------ oracle (CPU) samples
 def oracle_sample_setup(workload_flops):
     """The oracle's bounded sample: the headline workload's generator recipe
@@ -519,6 +594,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched / multi-RHS measurements")
     ap.add_argument("--batch-systems", type=int, default=256)
     ap.add_argument("--no-autotune", action="store_true", help="batching block with the default plan parameters")
+    ap.add_argument("--no-serving", action="store_true", help="skip the request-server block")
+    ap.add_argument("--serve-requests", type=int, default=300, help="requests per serving rate point")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -570,6 +647,8 @@ def main():
     if not args.no_batch:
         group = D.new_group(backend="gloo") if world > 1 else None
         line["batching"] = run_batching(args, dev, rank, world, group)
+    if not args.no_serving:
+        line["serving"] = run_serving(args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(si.flops, args.cpu_sample_seconds)
     if rank == 0:
