@@ -418,7 +418,9 @@ def run_batching(args, dev, rank=0, world=1, group=None):
         out["batch"] = {"systems": args.batch_systems, "solves_per_s": round(args.batch_systems / sec, 2),
                         "ms_per_system": round(1e3 * sec * world / args.batch_systems, 3),
                         "failed": int((stats["status"] != 0).sum()), "rr_max": float(stats["rr"].max()),
-                        "ranks": world, "form": "factor_batch + solve_batch on the shared analysis"
+                        "ranks": world, "form": ("factor_batch: one graph replay factors every system (system = "
+                                                 "blockIdx.y of each launch); solve_batch: 4 concurrent solves "
+                                                 "reading the systems' factors in place")
                         + (", systems sharded by contiguous index over the ranks" if world > 1 else "")}
     s.factor(Hs[0], Js[0], base.delta, base.gamma)
     R64 = cu(rng.standard_normal((64, base.n)))

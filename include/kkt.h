@@ -265,16 +265,23 @@ kkt_status kkt_solve_multi(kkt_handle h, int32_t nrhs, const double* r_x, const 
  *   H_vals  device double[nsys * nnz(H~)], system after system
  *   J_vals  device double[nsys * nnz(J)]
  *   status  host int32[nsys] (may be NULL): KKT_OK or KKT_ERR_NOT_SPD per system
- * Each system is factored by the handle's own factorization and kept in a
- * per-system slot (the handle allocates nsys slots of panels, inverses and
- * values; a larger nsys later reallocates them). Returns KKT_ERR_NOT_SPD if
- * any system failed (the others are usable), else the first other error.
- * The single-system factor is not kept: kkt_solve needs a new kkt_factor. */
+ * All systems are factored by one CUDA graph replay: every launch of the
+ * factorization covers every system (the system is the launch's second grid
+ * coordinate), into per-system slots of panels, inverses and update
+ * matrices that the handle allocates (nsys <= 65535; a larger nsys later
+ * reallocates them). Returns KKT_ERR_NOT_SPD if any system failed (the
+ * others are usable), else the first other error. The single-system factor
+ * is not changed: kkt_solve still solves with the last kkt_factor. */
 kkt_status kkt_factor_batch(kkt_handle h, int32_t nsys, const double* H_vals, const double* J_vals,
                             double delta, double gamma, int32_t* status, void* stream);
 
 /* Solves system b of the last kkt_factor_batch with right-hand side
  * r_x + b n, r_y + b m (device) into dx + b n, dy + b m, for b < nsys.
+ * Up to four systems are solved at once, each by a helper handle made from
+ * this analysis (own stream, host thread and workspace; its solve kernel on a
+ * quarter of the SMs) that reads the system's factor in its batch slot; the
+ * helpers are created by the first call. The call waits for `stream` first
+ * and returns when every solve is done.
  *   info    host kkt_info[nsys] (may be NULL)
  *   status  host int32[nsys] (may be NULL): per-system status (a system whose
  *           factorization failed reports KKT_ERR_NOT_SPD and is skipped)

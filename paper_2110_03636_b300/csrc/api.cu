@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -51,6 +52,9 @@ struct DevArena {
 };
 
 }  // namespace
+
+// concurrent solver handles of the batched form (kkt_solve_batch)
+constexpr int kBatchSolvers = 4;
 
 struct kkt_handle_s {
   kkt_options opt;
@@ -114,6 +118,27 @@ struct kkt_handle_s {
   cudaStream_t cap_stream = nullptr;   // private stream used to capture the factor graph
   cudaGraphExec_t fac_graph = nullptr; // the whole factorization as one CUDA graph
   cudaGraphExec_t reg_graph = nullptr; // Algorithm 1's delta_1 loop around it (conditional node)
+  // what the solve reads: the single factor, or one system of the batch
+  struct SolveView {
+    void *L = nullptr, *Linv = nullptr;
+    double *Hv = nullptr, *Jv = nullptr;
+    uint8_t* tmaps = nullptr;
+    int32_t tz = 0;   // the system's coordinate in the tensor maps' third dimension
+  } sv;
+  // batched form: nsys slots of panels, inverses, update matrices, diagonal
+  // tile scratch, values and status; 3-D tensor maps over them; one graph
+  void *bU = nullptr, *bDsc = nullptr;
+  DevStatus* bst = nullptr;
+  DevStatus* hbst = nullptr;   // pinned
+  uint8_t *btc_maps = nullptr, *bs_maps = nullptr;
+  cudaGraphExec_t bgraph = nullptr;
+  int32_t bgraph_nb = 0;
+  double bdelta = 0, bgamma = 0;   // the shift and gamma the batch was factored with
+  // concurrent solves of a batch: helper handles made from this analysis
+  // (own workspace and stream, a share of the SMs for the solve kernel) that
+  // read each system's factor from the batch slots
+  std::vector<kkt_handle> helpers;
+  std::vector<cudaStream_t> hstreams;
   double delta_prev = 0;     // delta_1 accepted for the previous matrix of the sequence (Sec. 4.1)
   // Ruiz scaling (opt.ruiz_iters > 0): D, its scratch, ones, and the lower CSC pattern of H~
   double *d_D = nullptr, *d_Dtmp = nullptr, *d_ones = nullptr;
@@ -145,7 +170,7 @@ struct kkt_handle_s {
 // the piece's pw columns of its supernode panel (ld rows each, rows past
 // the panel read as zeros), box = pc_box rows x pw columns. The encoder is
 // the driver's, fetched through the runtime (no link against libcuda).
-static bool build_tensor_maps(const Plan& P, void* L, size_t es, std::vector<uint8_t>& out) {
+static bool build_tensor_maps(const Plan& P, void* L, size_t es, int depth, std::vector<uint8_t>& out) {
   static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
   out.assign((size_t)P.npieces * 128, 0);
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
@@ -164,13 +189,14 @@ static bool build_tensor_maps(const Plan& P, void* L, size_t es, std::vector<uin
     if (P.pc_box[p] <= 0) continue;
     const int32_t pw = P.pc_w[p], ld = P.pc_ld[p], box = P.pc_box[p];
     if (box > 256 || pw > 256 || (box * es) % 16 || ((size_t)ld * es) % 16 || (P.pc_colbase[p] * es) % 16) return false;
-    const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)pw};
-    const cuuint64_t strides[1] = {(cuuint64_t)ld * es};
-    const cuuint32_t boxd[2] = {(cuuint32_t)box, (cuuint32_t)pw};
-    const cuuint32_t estr[2] = {1, 1};
+    // third dimension: the systems of a batch (panel sets panel_total apart)
+    const cuuint64_t dims[3] = {(cuuint64_t)ld, (cuuint64_t)pw, (cuuint64_t)depth};
+    const cuuint64_t strides[2] = {(cuuint64_t)ld * es, (cuuint64_t)P.panel_total * es};
+    const cuuint32_t boxd[3] = {(cuuint32_t)box, (cuuint32_t)pw, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
     CUtensorMap* m = (CUtensorMap*)(out.data() + (size_t)p * 128);
     void* g = (char*)L + (size_t)P.pc_colbase[p] * es;
-    if (encode(m, es == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, g, dims, strides,
+    if (encode(m, es == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, g, dims, strides,
                boxd, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return false;
@@ -181,7 +207,7 @@ static bool build_tensor_maps(const Plan& P, void* L, size_t es, std::vector<uin
 // Tensor maps of the fronts whose updates run on the tensor cores: the
 // whole FP32 panel (ld rows x w columns; rows past ld and columns past w
 // read as zeros), boxes of kTcBoxRows rows x 32 columns.
-static bool build_tc_maps(const Plan& P, void* L, std::vector<uint8_t>& out) {
+static bool build_tc_maps(const Plan& P, void* L, int depth, std::vector<uint8_t>& out) {
   out.assign(P.tc_front.size() * 128, 0);
   if (P.tc_front.empty()) return true;
   void* fn = nullptr;
@@ -196,13 +222,14 @@ static bool build_tc_maps(const Plan& P, void* L, std::vector<uint8_t>& out) {
     const int32_t s = P.tc_front[k];
     const int32_t ld = P.sld[s], w = P.sw[s];
     if (ld < kTcBoxRows || w < kTcMinWidth || (ld * 4) % 16 || (P.poff[s] * 4) % 16) return false;
-    const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)w};
-    const cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
-    const cuuint32_t boxd[2] = {(cuuint32_t)kTcBoxRows, 32};
-    const cuuint32_t estr[2] = {1, 1};
+    // third dimension: the systems of a batch (panel sets panel_total apart)
+    const cuuint64_t dims[3] = {(cuuint64_t)ld, (cuuint64_t)w, (cuuint64_t)depth};
+    const cuuint64_t strides[2] = {(cuuint64_t)ld * 4, (cuuint64_t)P.panel_total * 4};
+    const cuuint32_t boxd[3] = {(cuuint32_t)kTcBoxRows, 32, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
     CUtensorMap* m = (CUtensorMap*)(out.data() + k * 128);
     void* g = (char*)L + (size_t)P.poff[s] * 4;
-    if (encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, g, dims, strides, boxd, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+    if (encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, g, dims, strides, boxd, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return false;
@@ -277,6 +304,11 @@ kkt_status kkt_destroy(kkt_handle h) {
   if (h->fac_graph) cudaGraphExecDestroy(h->fac_graph);
   if (h->reg_graph) cudaGraphExecDestroy(h->reg_graph);
   if (h->jjt) kkt_destroy(h->jjt);
+  if (h->bgraph) cudaGraphExecDestroy(h->bgraph);
+  if (h->bU) { cudaFree(h->bU); cudaFree(h->bDsc); cudaFree(h->bst); cudaFree(h->btc_maps); cudaFree(h->bs_maps); }
+  if (h->hbst) cudaFreeHost(h->hbst);
+  for (kkt_handle x : h->helpers) kkt_destroy(x);
+  for (cudaStream_t x : h->hstreams) cudaStreamDestroy(x);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->prof.a) cudaEventDestroy(h->prof.a);
   if (h->prof.b) cudaEventDestroy(h->prof.b);
@@ -452,10 +484,11 @@ static kkt_status device_stage(kkt_handle h, kkt_handle* out) {
   {
     std::vector<uint8_t> maps;
     if (!A.failed) {
-      if (!build_tensor_maps(P, h->L, es, maps)) { kkt_destroy(h); return KKT_ERR_CUDA; }
+      if (!build_tensor_maps(P, h->L, es, 1, maps)) { kkt_destroy(h); return KKT_ERR_CUDA; }
       h->tmaps = A.upload(maps);
+      h->sv.L = h->L; h->sv.Linv = h->Linv; h->sv.Hv = h->Hv; h->sv.Jv = h->Jv; h->sv.tmaps = h->tmaps; h->sv.tz = 0;
       if (!f64) {
-        if (!build_tc_maps(P, h->L, maps)) { kkt_destroy(h); return KKT_ERR_CUDA; }
+        if (!build_tc_maps(P, h->L, 1, maps)) { kkt_destroy(h); return KKT_ERR_CUDA; }
         h->tc_maps = A.upload(maps);
       }
     }
@@ -581,29 +614,41 @@ static kkt_status read_status(kkt_handle h, cudaStream_t st) {
 }
 
 template <typename T>
-static cudaError_t factor_launches(kkt_handle h, cudaStream_t st, Prof* prof) {
+static cudaError_t factor_launches(kkt_handle h, cudaStream_t st, Prof* prof, int nb = 0) {
+  // nb > 0: the batched form, nb systems in the batch slots (system b =
+  // blockIdx.y of every launch); nb = 0: the single factor
   FacArgs<T> a;
   a.sfirst = h->sfirst; a.sw = h->sw; a.snr = h->snr; a.sld = h->sld; a.sparent = h->sparent; a.rel = h->rel;
   a.srow = h->srow; a.poff = h->poff; a.uoff = h->uoff;
   a.Hv = h->Hv; a.Jv = h->Jv;
   a.L = (T*)h->L; a.U = (T*)h->U; a.Dsc = (T*)h->Dsc; a.st = h->dst;
+  if (nb > 0) {
+    a.Hv = h->bHv; a.Jv = h->bJv;
+    a.L = (T*)h->bL; a.U = (T*)h->bU; a.Dsc = (T*)h->bDsc; a.st = h->bst;
+    a.bsL = h->P.panel_total; a.bsU = h->P.u_total; a.bsD = h->P.dsc_total;
+    a.bsH = h->nnzH; a.bsJ = h->nnzJ;
+  }
   FacLists fl;
   fl.it_potrf = h->it_potrf; fl.it_trsm = h->it_trsm; fl.it_pupd = h->it_pupd;
   fl.it_syrk = h->it_syrk; fl.it_eadd = h->it_eadd; fl.it_syrk_tc = h->it_syrk_tc;
-  fl.tc_maps = h->tc_maps;
+  fl.tc_maps = nb > 0 ? h->btc_maps : h->tc_maps;
   fl.it_block = h->it_block; fl.it_syrk128 = h->it_syrk128; fl.it_dstore = h->it_dstore;
   fl.slot_pos = h->slot_pos; fl.src_ptr = h->src_ptr; fl.srcA = h->srcA; fl.srcB = h->srcB;
   fl.nslot = (int64_t)h->P.slot_pos.size();
   fl.panel_total = h->P.panel_total; fl.u_total = h->P.u_total;
   fl.launches = &h->P.launches;
-  cudaError_t e = launch_factor<T>(a, fl, h->d_dg, st, prof);
+  cudaError_t e = launch_factor<T>(a, fl, h->d_dg, st, prof, nb > 0 ? nb : 1);
   if (e) return e;
   InvArgs<T> ia;
   ia.pc_w = h->pc_w; ia.pc_ld = h->pc_ld; ia.pc_c = h->pc_c;
   ia.pc_colbase = h->pc_colbase; ia.pc_inv = h->pc_inv;
   ia.L = (const T*)h->L; ia.Linv = (T*)h->Linv;
+  if (nb > 0) {
+    ia.L = (const T*)h->bL; ia.Linv = (T*)h->bLinv;
+    ia.bsL = h->P.panel_total; ia.bsI = h->P.inv_total;
+  }
   if ((e = prof_begin(prof, st))) return e;
-  if ((e = launch_tri_inv<T>(ia, h->P.npieces, h->P.solve_w, st))) return e;
+  if ((e = launch_tri_inv<T>(ia, h->P.npieces, h->P.solve_w, st, nb > 0 ? nb : 1))) return e;
   return prof_end(prof, KKT_K_TRI_INV, st);
 }
 
@@ -727,7 +772,7 @@ static SolveArgs<T> solve_args(kkt_handle h) {
   a.sn_rows = h->sn_rows;
   a.pc_inv = h->pc_inv; a.hd_tgt = h->hd_tgt;
   a.sw = P.solve_w; a.ent = P.ent; a.ent0 = P.ent0; a.max_rows = P.max_rows;
-  a.Linv = (const T*)h->Linv;
+  a.Linv = (const T*)h->sv.Linv;
   a.ch_tgt = h->ch_tgt;
   a.fwd_items = h->fwd_items; a.bwd_items = h->bwd_items;
   a.nitems = (int64_t)P.fwd_items.size();
@@ -735,10 +780,10 @@ static SolveArgs<T> solve_args(kkt_handle h) {
   a.st_first = h->st_first; a.st_last = h->st_last; a.st_clo = h->st_clo; a.st_chi = h->st_chi;
   a.st_tgt = h->st_tgt; a.st_tptr = h->st_tptr; a.sn_piece = h->sn_piece;
   a.st_lptr = h->st_lptr; a.st_lev = h->st_lev; a.st_sn = h->st_sn;
-  a.cdesc = h->cdesc; a.hdesc = h->hdesc; a.tmaps = h->tmaps;
+  a.cdesc = h->cdesc; a.hdesc = h->hdesc; a.tmaps = h->sv.tmaps; a.tz = h->sv.tz;
   a.sfirst = h->sfirst; a.sw_ = h->sw; a.snr = h->snr; a.sld = h->sld; a.srow = h->srow; a.poff = h->poff;
-  a.L = (const T*)h->L;
-  a.J_rowptr = h->J_rowptr; a.Jcol_perm = h->Jcol_perm; a.Jv = h->Jv;
+  a.L = (const T*)h->sv.L;
+  a.J_rowptr = h->J_rowptr; a.Jcol_perm = h->Jcol_perm; a.Jv = h->sv.Jv;
   a.JT_ptr = h->JT_ptr; a.JT_row = h->JT_row; a.JT_vidx = h->JT_vidx;
   a.perm = h->perm;
   a.gamma = h->gamma; a.delta2 = h->opt.delta2; a.rtol = h->opt.cg_rtol; a.maxit = h->opt.cg_maxit;
@@ -788,7 +833,7 @@ static kkt_status residual(kkt_handle h, const double* bx, const double* by, con
   r.Hs_ptr = h->Hs_ptr; r.Hs_col = h->Hs_col; r.Hs_vidx = h->Hs_vidx;
   r.J_rowptr = h->J_rowptr; r.J_colidx = h->J_colidx;
   r.JT_ptr = h->JTo_ptr; r.JT_row = h->JTo_row; r.JT_vidx = h->JTo_vidx;
-  r.Hv = h->Hv; r.Jv = h->Jv; r.delta = h->delta;
+  r.Hv = h->sv.Hv; r.Jv = h->sv.Jv; r.delta = h->delta;
   r.bx = bx; r.by = by; r.x = x; r.y = y;
   r.res_x = res_x ? res_x : h->res_x; r.res_y = res_y ? res_y : h->res_y;
   r.red = h->red; r.st = h->dst;
@@ -1266,52 +1311,131 @@ extern "C" {
 // another with the handle's factorization (its captured graph) and kept in
 // per-system slots; each solve copies its system's factor back into the
 // working buffers (a few microseconds of device copies) and runs the solve.
+}  // extern "C"
+
+// Restores the solve view of the single factor when a batched solve returns.
+struct Handle_sv_saver {
+  kkt_handle h;
+  explicit Handle_sv_saver(kkt_handle hh) : h(hh) {}
+  ~Handle_sv_saver() {
+    h->sv.L = h->L; h->sv.Linv = h->Linv; h->sv.Hv = h->Hv; h->sv.Jv = h->Jv;
+    h->sv.tmaps = h->tmaps; h->sv.tz = 0;
+  }
+};
+
+// Batch slots for nsys systems: panels, inverses, update matrices, diagonal
+// tile scratch and values, system after system, a status per system, and the
+// tensor maps over them (third coordinate = system).
+static kkt_status batch_reserve(kkt_handle h, int32_t nsys) {
+  if (nsys <= h->batch_cap) return KKT_OK;
+  const Plan& P = h->P;
+  const bool f64 = h->opt.precision == KKT_FP64;
+  const size_t es = f64 ? sizeof(double) : sizeof(float);
+  void* old[] = {h->bL, h->bLinv, h->bHv, h->bJv, h->bU, h->bDsc, h->bst, h->btc_maps, h->bs_maps};
+  for (void* p : old) cudaFree(p);
+  if (h->hbst) cudaFreeHost(h->hbst);
+  if (h->bgraph) cudaGraphExecDestroy(h->bgraph);
+  h->bL = h->bLinv = h->bU = h->bDsc = nullptr;
+  h->bHv = h->bJv = nullptr;
+  h->bst = h->hbst = nullptr;
+  h->btc_maps = h->bs_maps = nullptr;
+  h->bgraph = nullptr;
+  h->bgraph_nb = 0;
+  h->batch_cap = 0;
+  auto al = [&](void** p, size_t bytes) { return cudaMalloc(p, std::max<size_t>(bytes, 16)) == cudaSuccess; };
+  bool ok = al(&h->bL, es * (size_t)P.panel_total * nsys) && al(&h->bLinv, es * (size_t)P.inv_total * nsys) &&
+            al((void**)&h->bHv, sizeof(double) * (size_t)h->nnzH * nsys) &&
+            al((void**)&h->bJv, sizeof(double) * (size_t)h->nnzJ * nsys) &&
+            al(&h->bU, es * (size_t)P.u_total * nsys) && al(&h->bDsc, es * (size_t)P.dsc_total * nsys) &&
+            al((void**)&h->bst, sizeof(DevStatus) * nsys) &&
+            cudaMallocHost((void**)&h->hbst, sizeof(DevStatus) * nsys) == cudaSuccess;
+  if (!ok) { cudaGetLastError(); return KKT_ERR_OOM; }
+  std::vector<uint8_t> maps;
+  if (!build_tensor_maps(P, h->bL, es, nsys, maps)) return KKT_ERR_CUDA;
+  if (!maps.empty()) {
+    if (!al((void**)&h->bs_maps, maps.size())) { cudaGetLastError(); return KKT_ERR_OOM; }
+    CK(cudaMemcpy(h->bs_maps, maps.data(), maps.size(), cudaMemcpyHostToDevice));
+  }
+  if (!f64) {
+    if (!build_tc_maps(P, h->bL, nsys, maps)) return KKT_ERR_CUDA;
+    if (!maps.empty()) {
+      if (!al((void**)&h->btc_maps, maps.size())) { cudaGetLastError(); return KKT_ERR_OOM; }
+      CK(cudaMemcpy(h->btc_maps, maps.data(), maps.size(), cudaMemcpyHostToDevice));
+    }
+  }
+  h->batch_cap = nsys;
+  return KKT_OK;
+}
+
+// One graph for the whole batch: every factor launch covers all nsys systems
+// (system b = blockIdx.y), so the level-by-level launch sequence is paid once.
+template <typename T>
+static kkt_status batch_graph(kkt_handle h, int32_t nsys) {
+  if (h->bgraph && h->bgraph_nb == nsys) return KKT_OK;
+  if (h->bgraph) cudaGraphExecDestroy(h->bgraph);
+  h->bgraph = nullptr;
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = factor_launches<T>(h, h->cap_stream, nullptr, nsys);
+  cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &g);
+  if (e || e2) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return KKT_ERR_CUDA;
+  }
+  e = cudaGraphInstantiate(&h->bgraph, g, 0);
+  cudaGraphDestroy(g);
+  if (e) { h->bgraph = nullptr; return cuda_status(e); }
+  h->bgraph_nb = nsys;
+  return KKT_OK;
+}
+
+extern "C" {
+
 kkt_status kkt_factor_batch(kkt_handle h, int32_t nsys, const double* H_vals, const double* J_vals,
                             double delta, double gamma, int32_t* status, void* stream) {
-  if (!h || nsys < 1 || !H_vals || (h->nnzJ > 0 && !J_vals)) return KKT_ERR_INVALID;
+  if (!h || nsys < 1 || nsys > 65535 || !H_vals || (h->nnzJ > 0 && !J_vals)) return KKT_ERR_INVALID;
   if (!h->on_device || h->opt.ruiz_iters > 0 || h->opt.krylov != 0) return KKT_ERR_STATE;
+  if (!(delta >= 0.0) || !std::isfinite(delta)) return KKT_ERR_INVALID;
+  if (gamma < 0) gamma = h->opt.gamma;
+  if (!std::isfinite(gamma)) return KKT_ERR_INVALID;
   CK(cudaSetDevice(h->device));
   cudaStream_t st = (cudaStream_t)stream;
-  const size_t es = h->opt.precision == KKT_FP64 ? sizeof(double) : sizeof(float);
-  const size_t pb = es * (size_t)h->P.panel_total, ib = es * (size_t)h->P.inv_total;
-  if (nsys > h->batch_cap) {
-    if (h->bL) { cudaFree(h->bL); cudaFree(h->bLinv); cudaFree(h->bHv); cudaFree(h->bJv); }
-    h->bL = h->bLinv = nullptr; h->bHv = h->bJv = nullptr; h->batch_cap = 0;
-    if (cudaMalloc(&h->bL, pb * nsys) || cudaMalloc(&h->bLinv, std::max<size_t>(ib, 16) * nsys) ||
-        cudaMalloc((void**)&h->bHv, sizeof(double) * std::max<int64_t>(h->nnzH, 1) * nsys) ||
-        cudaMalloc((void**)&h->bJv, sizeof(double) * std::max<int64_t>(h->nnzJ, 1) * nsys)) {
-      cudaGetLastError();
-      return KKT_ERR_OOM;
-    }
-    h->batch_cap = nsys;
-  }
+  kkt_status s = batch_reserve(h, nsys);
+  if (s) return s;
   h->bstatus.assign((size_t)nsys, KKT_ERR_STATE);
+  CK(cudaMemcpyAsync(h->bHv, H_vals, sizeof(double) * h->nnzH * nsys, cudaMemcpyDeviceToDevice, st));
+  if (h->nnzJ) CK(cudaMemcpyAsync(h->bJv, J_vals, sizeof(double) * h->nnzJ * nsys, cudaMemcpyDeviceToDevice, st));
+  for (int b = 0; b < nsys; b++) {
+    std::memset(&h->hbst[b], 0, sizeof(DevStatus));
+    h->hbst[b].fail_col = INT_MAX;
+  }
+  CK(cudaMemcpyAsync(h->bst, h->hbst, sizeof(DevStatus) * nsys, cudaMemcpyHostToDevice, st));
+  h->h_dg[0] = delta;
+  h->h_dg[1] = gamma;
+  CK(cudaMemcpyAsync(h->d_dg, h->h_dg, 2 * sizeof(double), cudaMemcpyHostToDevice, st));
+  if (h->profp) {
+    CK(h->opt.precision == KKT_FP64 ? factor_launches<double>(h, st, h->profp, nsys)
+                                    : factor_launches<float>(h, st, h->profp, nsys));
+  } else {
+    s = h->opt.precision == KKT_FP64 ? batch_graph<double>(h, nsys) : batch_graph<float>(h, nsys);
+    if (s) return s;
+    CK(cudaGraphLaunch(h->bgraph, st));
+  }
+  CK(cudaMemcpyAsync(h->hbst, h->bst, sizeof(DevStatus) * nsys, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
   kkt_status worst = KKT_OK;
   for (int b = 0; b < nsys; b++) {
-    CK(cudaMemcpyAsync(h->Hv, H_vals + (int64_t)b * h->nnzH, sizeof(double) * h->nnzH, cudaMemcpyDeviceToDevice,
-                       st));
-    if (h->nnzJ)
-      CK(cudaMemcpyAsync(h->Jv, J_vals + (int64_t)b * h->nnzJ, sizeof(double) * h->nnzJ,
-                         cudaMemcpyDeviceToDevice, st));
-    const kkt_status s = factor_common(h, delta, gamma, st);
-    h->bstatus[b] = s;
-    if (status) status[b] = s;
-    if (s == KKT_OK) {
-      CK(cudaMemcpyAsync((char*)h->bL + pb * b, h->L, pb, cudaMemcpyDeviceToDevice, st));
-      if (ib) CK(cudaMemcpyAsync((char*)h->bLinv + ib * b, h->Linv, ib, cudaMemcpyDeviceToDevice, st));
-      CK(cudaMemcpyAsync(h->bHv + (int64_t)b * h->nnzH, h->Hv, sizeof(double) * h->nnzH, cudaMemcpyDeviceToDevice,
-                         st));
-      if (h->nnzJ)
-        CK(cudaMemcpyAsync(h->bJv + (int64_t)b * h->nnzJ, h->Jv, sizeof(double) * h->nnzJ,
-                           cudaMemcpyDeviceToDevice, st));
-    } else if (s != KKT_ERR_NOT_SPD) {
-      return s;
-    } else {
-      worst = KKT_ERR_NOT_SPD;
-    }
+    const kkt_status sb = h->hbst[b].abort ? KKT_ERR_TIMEOUT
+                                           : (h->hbst[b].fail_col != INT_MAX ? KKT_ERR_NOT_SPD : KKT_OK);
+    h->bstatus[b] = sb;
+    if (status) status[b] = sb;
+    if (sb == KKT_ERR_TIMEOUT) worst = KKT_ERR_TIMEOUT;
+    else if (sb == KKT_ERR_NOT_SPD && worst == KKT_OK) worst = KKT_ERR_NOT_SPD;
   }
-  CK(cudaStreamSynchronize(st));
-  h->factored = false;   // the working buffers hold a slot's copy only during kkt_solve_batch
+  h->factored = false;   // kkt_solve needs a kkt_factor; the batch is solved with kkt_solve_batch
+  h->bdelta = delta;
+  h->bgamma = gamma;
   return worst;
 }
 
@@ -1324,26 +1448,61 @@ kkt_status kkt_solve_batch(kkt_handle h, int32_t nsys, const double* r_x, const 
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t n = h->P.n, m = h->P.m;
   const size_t es = h->opt.precision == KKT_FP64 ? sizeof(double) : sizeof(float);
-  const size_t pb = es * (size_t)h->P.panel_total, ib = es * (size_t)h->P.inv_total;
+  // helpers: kBatchSolvers concurrent solves, each solve kernel on its share of the SMs
+  const int K = std::min<int>(kBatchSolvers, nsys);
+  while ((int)h->helpers.size() < K) {
+    kkt_options o = h->opt;
+    o.solve_sms = std::max(1, 148 / kBatchSolvers);
+    o.profile = 0;
+    kkt_handle x = nullptr;
+    kkt_status s = kkt_analyse_like(h, &o, &x);
+    if (s) return s;
+    cudaStream_t xs = nullptr;
+    if (cudaStreamCreateWithFlags(&xs, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      kkt_destroy(x);
+      return KKT_ERR_CUDA;
+    }
+    h->helpers.push_back(x);
+    h->hstreams.push_back(xs);
+  }
+  CK(cudaStreamSynchronize(st));   // the right-hand sides are written in the caller's stream order
+  std::vector<kkt_status> res((size_t)nsys, KKT_OK);
+  std::vector<kkt_info> inf((size_t)nsys);
+  auto run = [&](int k) {
+    kkt_handle x = h->helpers[k];
+    cudaSetDevice(h->device);
+    x->delta = h->bdelta;
+    x->gamma = h->bgamma;
+    for (int b = k; b < nsys; b += K) {
+      kkt_status s = (kkt_status)h->bstatus[b];
+      std::memset(&inf[b], 0, sizeof(kkt_info));
+      if (s == KKT_OK) {
+        // solve system b where the batch factored it: no copies
+        x->sv.L = (char*)h->bL + es * (size_t)h->P.panel_total * b;
+        x->sv.Linv = (char*)h->bLinv + es * (size_t)h->P.inv_total * b;
+        x->sv.Hv = h->bHv + (int64_t)b * h->nnzH;
+        x->sv.Jv = h->bJv + (int64_t)b * h->nnzJ;
+        x->sv.tmaps = h->bs_maps;
+        x->sv.tz = b;
+        x->factored = true;
+        s = solve_common(x, r_x + b * n, r_y + b * m, dx + b * n, dy + b * m, h->hstreams[k]);
+        x->factored = false;
+        inf[b] = x->info;
+      }
+      res[b] = s;
+    }
+    { const Handle_sv_saver restore(x); }
+  };
+  std::vector<std::thread> th;
+  for (int k = 1; k < K; k++) th.emplace_back(run, k);
+  run(0);
+  for (std::thread& t : th) t.join();
   kkt_status worst = KKT_OK;
   for (int b = 0; b < nsys; b++) {
-    kkt_status s = (kkt_status)h->bstatus[b];
-    if (s == KKT_OK) {
-      CK(cudaMemcpyAsync(h->L, (char*)h->bL + pb * b, pb, cudaMemcpyDeviceToDevice, st));
-      if (ib) CK(cudaMemcpyAsync(h->Linv, (char*)h->bLinv + ib * b, ib, cudaMemcpyDeviceToDevice, st));
-      CK(cudaMemcpyAsync(h->Hv, h->bHv + (int64_t)b * h->nnzH, sizeof(double) * h->nnzH, cudaMemcpyDeviceToDevice,
-                         st));
-      if (h->nnzJ)
-        CK(cudaMemcpyAsync(h->Jv, h->bJv + (int64_t)b * h->nnzJ, sizeof(double) * h->nnzJ,
-                           cudaMemcpyDeviceToDevice, st));
-      h->factored = true;
-      s = solve_common(h, r_x + b * n, r_y + b * m, dx + b * n, dy + b * m, st);
-      h->factored = false;
-      if (info) info[b] = h->info;
-    } else if (info) {
-      std::memset(&info[b], 0, sizeof(kkt_info));
-    }
-    if (status) status[b] = s;
+    if (info) info[b] = inf[b];
+    if (status) status[b] = res[b];
+    const kkt_status s = res[b];
     if (s == KKT_ERR_CUDA || s == KKT_ERR_TIMEOUT || s == KKT_ERR_OOM) return s;
     if (s != KKT_OK && worst == KKT_OK) worst = s;
   }

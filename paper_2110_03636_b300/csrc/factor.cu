@@ -26,8 +26,12 @@ template <typename T>
 __global__ void k_assemble(int64_t nslot, const int64_t* __restrict__ slot_pos,
                            const int64_t* __restrict__ src_ptr, const int32_t* __restrict__ srcA,
                            const int32_t* __restrict__ srcB, const double* __restrict__ Hv,
-                           const double* __restrict__ Jv, const double* __restrict__ dg, T* __restrict__ L) {
+                           const double* __restrict__ Jv, const double* __restrict__ dg, T* __restrict__ L,
+                           int64_t bsH, int64_t bsJ, int64_t bsL) {
   const double delta = dg[0], gamma = dg[1];   // device scalars: a captured graph replays with new values
+  Hv += blockIdx.y * bsH;                       // system blockIdx.y of a batched launch
+  Jv += blockIdx.y * bsJ;
+  L += blockIdx.y * bsL;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nslot; t += (int64_t)gridDim.x * blockDim.x) {
     double v = 0.0;
     for (int64_t q = src_ptr[t]; q < src_ptr[t + 1]; q++) {
@@ -44,6 +48,7 @@ __global__ void k_assemble(int64_t nslot, const int64_t* __restrict__ slot_pos,
 // pivot <= 0 or non-finite records the column in DevStatus::fail_col.
 template <typename T>
 __global__ void __launch_bounds__(256) k_potrf(const int4* __restrict__ items, int kb, FacArgs<T> a) {
+  batch_view(a);
   __shared__ T D[kPB][kPB + 1];
   const int s = items[blockIdx.x].x;
   const int w = a.sw[s], nr = a.snr[s], ld = a.sld[s];
@@ -86,6 +91,7 @@ __global__ void __launch_bounds__(256) k_potrf(const int4* __restrict__ items, i
 // factored tile (read from the panel); items (s, row tile of kTR rows).
 template <typename T>
 __global__ void __launch_bounds__(kTR) k_trsm(const int4* __restrict__ items, int kb, FacArgs<T> a) {
+  batch_view(a);
   __shared__ T D[kPB][kPB + 1];
   const int4 it = items[blockIdx.x];
   const int s = it.x, t = it.y;
@@ -169,6 +175,7 @@ static_assert(kFItem == 3 * 4, "block-step and update items are three int4");
 
 template <typename T>
 __global__ void __launch_bounds__(kTR) k_block(const int4* __restrict__ items, int kb, FacArgs<T> a) {
+  batch_view(a);
   __shared__ T D[kPB][kPB + 1];
   __shared__ T Dinv[kPB];   // reciprocals of the factored tile's diagonal
   const int4 it = items[3 * blockIdx.x], fm = items[3 * blockIdx.x + 1], fo = items[3 * blockIdx.x + 2];
@@ -218,6 +225,7 @@ __global__ void __launch_bounds__(kTR) k_block(const int4* __restrict__ items, i
 // The level's factored diagonal tiles from the scratch into the panels.
 template <typename T>
 __global__ void __launch_bounds__(256) k_dstore(const int4* __restrict__ items, FacArgs<T> a) {
+  batch_view(a);
   const int4 it = items[blockIdx.x];
   const int s = it.x, c0 = it.y * kPB;
   const int w = a.sw[s], ld = a.sld[s];
@@ -236,6 +244,7 @@ __global__ void __launch_bounds__(256) k_dstore(const int4* __restrict__ items, 
 // items (s, row tile of kUR rows, column tile of kPB columns).
 template <typename T>
 __global__ void __launch_bounds__(256) k_panel_update(const int4* __restrict__ items, int kb, FacArgs<T> a) {
+  batch_view(a);
   __shared__ T As[kUR][kPB + 1];
   __shared__ T Bs[kPB][kPB + 1];
   const int4 it = items[3 * blockIdx.x], fm = items[3 * blockIdx.x + 1], fo = items[3 * blockIdx.x + 2];
@@ -280,6 +289,7 @@ __global__ void __launch_bounds__(256) k_panel_update(const int4* __restrict__ i
 // U_s = -L21 L21^T on 64 x 64 tiles (ti >= tj), k = panel width.
 template <typename T>
 __global__ void __launch_bounds__(256) k_syrk(const int4* __restrict__ items, FacArgs<T> a) {
+  batch_view(a);
   constexpr int KC = 16;
   __shared__ T As[KC][kST + 1];
   __shared__ T Bs[KC][kST + 1];
@@ -334,6 +344,7 @@ __global__ void __launch_bounds__(256) k_syrk(const int4* __restrict__ items, Fa
 // columns ty*4 + {0..3, 64..67}, tx = tid % 16, ty = tid / 16), K staged 16
 // columns at a time through two shared-memory buffers.
 __global__ void __launch_bounds__(256) k_syrk128(const int4* __restrict__ items, FacArgs<float> a) {
+  batch_view(a);
   constexpr int KC = 16, TS = 128;
   __shared__ __align__(16) float As[2][KC][TS];
   __shared__ __align__(16) float Bs[2][KC][TS];
@@ -413,6 +424,7 @@ __global__ void __launch_bounds__(256) k_syrk128(const int4* __restrict__ items,
 // is one of its columns, else its update matrix.
 template <typename T>
 __global__ void __launch_bounds__(256) k_extend_add(const int4* __restrict__ items, FacArgs<T> a) {
+  batch_view(a);
   const int4 it = items[blockIdx.x];
   const int s = it.x, j0 = it.y, j1 = it.z;   // child columns [j0, min(j0 + kEC, j1))
   const int p = a.sparent[s];
@@ -461,21 +473,21 @@ __global__ void __launch_bounds__(256) k_extend_add(const int4* __restrict__ ite
 }
 
 
-static cudaError_t launch_syrk128(const int4* items, int64_t cnt, const FacArgs<float>& a, cudaStream_t st) {
-  k_syrk128<<<(unsigned)cnt, 256, 0, st>>>(items, a);
+static cudaError_t launch_syrk128(const int4* items, int64_t cnt, const FacArgs<float>& a, cudaStream_t st, int nb) {
+  k_syrk128<<<dim3((unsigned)cnt, (unsigned)nb), 256, 0, st>>>(items, a);
   return cudaGetLastError();
 }
 template <typename T>
-static cudaError_t launch_syrk128(const int4*, int64_t, const FacArgs<T>&, cudaStream_t) {
+static cudaError_t launch_syrk128(const int4*, int64_t, const FacArgs<T>&, cudaStream_t, int) {
   return cudaErrorNotSupported;   // FP64 fronts keep the 64 x 64 tiles
 }
 
 static cudaError_t launch_syrk_tc(const int4* items, int64_t cnt, const uint8_t* maps, const FacArgs<float>& a,
-                                  cudaStream_t st) {
-  return launch_tc_update(items, cnt, maps, a, st);
+                                  cudaStream_t st, int nb) {
+  return launch_tc_update(items, cnt, maps, a, st, nb);
 }
 template <typename T>
-static cudaError_t launch_syrk_tc(const int4*, int64_t, const uint8_t*, const FacArgs<T>&, cudaStream_t) {
+static cudaError_t launch_syrk_tc(const int4*, int64_t, const uint8_t*, const FacArgs<T>&, cudaStream_t, int) {
   return cudaErrorNotSupported;   // the tensor-core updates are the FP32 factor's
 }
 
@@ -489,6 +501,8 @@ template <typename T>
 __global__ void __launch_bounds__(128) k_tri_inv(InvArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* Ts = (T*)smem_raw;
+  a.L += blockIdx.y * a.bsL;
+  a.Linv += blockIdx.y * a.bsI;
   const int p = blockIdx.x;
   const int pw = a.pc_w[p], ld = a.pc_ld[p], c = a.pc_c[p];
   const T* L = a.L + a.pc_colbase[p] + c;      // (row c, col c) of the supernode panel
@@ -513,15 +527,16 @@ __global__ void __launch_bounds__(128) k_tri_inv(InvArgs<T> a) {
 }
 
 template <typename T>
-cudaError_t launch_tri_inv(const InvArgs<T>& a, int64_t npieces, int max_pw, cudaStream_t st) {
+cudaError_t launch_tri_inv(const InvArgs<T>& a, int64_t npieces, int max_pw, cudaStream_t st, int nb) {
   const size_t smem = sizeof(T) * (size_t)max_pw * max_pw;
   cudaError_t e = cudaFuncSetAttribute(k_tri_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e) return e;
-  k_tri_inv<T><<<(unsigned)npieces, 128, smem, st>>>(a);
+  if (npieces <= 0) return cudaSuccess;
+  k_tri_inv<T><<<dim3((unsigned)npieces, (unsigned)nb), 128, smem, st>>>(a);
   return cudaGetLastError();
 }
-template cudaError_t launch_tri_inv<double>(const InvArgs<double>&, int64_t, int, cudaStream_t);
-template cudaError_t launch_tri_inv<float>(const InvArgs<float>&, int64_t, int, cudaStream_t);
+template cudaError_t launch_tri_inv<double>(const InvArgs<double>&, int64_t, int, cudaStream_t, int);
+template cudaError_t launch_tri_inv<float>(const InvArgs<float>&, int64_t, int, cudaStream_t, int);
 
 cudaError_t prof_begin(Prof* pr, cudaStream_t st) {
   if (!pr) return cudaSuccess;
@@ -542,36 +557,40 @@ cudaError_t prof_end(Prof* pr, int kind, cudaStream_t st) {
 
 template <typename T>
 cudaError_t launch_factor(const FacArgs<T>& a, const FacLists& fl, const double* dg, cudaStream_t st,
-                          Prof* prof) {
+                          Prof* prof, int nb) {
   cudaError_t e;
-  if ((e = cudaMemsetAsync(a.L, 0, sizeof(T) * (size_t)fl.panel_total, st))) return e;
+  // nb systems: the panels of system b start at a.L + b * a.bsL (contiguous
+  // when bsL = panel_total, as the batched form lays them out)
+  if ((e = cudaMemsetAsync(a.L, 0, sizeof(T) * (size_t)fl.panel_total * nb, st))) return e;
+  const unsigned y = (unsigned)nb;
   {
     const int threads = 256;
     int64_t blocks = (fl.nslot + threads - 1) / threads;
     if (blocks > 148 * 64) blocks = 148 * 64;
     if (blocks < 1) blocks = 1;
     if ((e = prof_begin(prof, st))) return e;
-    k_assemble<T><<<(unsigned)blocks, threads, 0, st>>>(fl.nslot, fl.slot_pos, fl.src_ptr, fl.srcA, fl.srcB,
-                                                         a.Hv, a.Jv, dg, a.L);
+    k_assemble<T><<<dim3((unsigned)blocks, y), threads, 0, st>>>(fl.nslot, fl.slot_pos, fl.src_ptr, fl.srcA, fl.srcB,
+                                                                  a.Hv, a.Jv, dg, a.L, a.bsH, a.bsJ, a.bsL);
     if ((e = prof_end(prof, 0, st))) return e;
   }
   for (const Launch& L : *fl.launches) {
     if (L.cnt <= 0) continue;
     if ((e = prof_begin(prof, st))) return e;
+    const dim3 g((unsigned)L.cnt, y);
     switch (L.kind) {
-      case 0: k_potrf<T><<<(unsigned)L.cnt, 256, 0, st>>>(fl.it_potrf + L.off, L.kb, a); break;
-      case 1: k_trsm<T><<<(unsigned)L.cnt, kTR, 0, st>>>(fl.it_trsm + L.off, L.kb, a); break;
-      case 2: k_panel_update<T><<<(unsigned)L.cnt, 256, 0, st>>>(fl.it_pupd + 3 * L.off, L.kb, a); break;
-      case 3: k_syrk<T><<<(unsigned)L.cnt, 256, 0, st>>>(fl.it_syrk + L.off, a); break;
-      case 4: k_extend_add<T><<<(unsigned)L.cnt, 256, 0, st>>>(fl.it_eadd + L.off, a); break;
+      case 0: k_potrf<T><<<g, 256, 0, st>>>(fl.it_potrf + L.off, L.kb, a); break;
+      case 1: k_trsm<T><<<g, kTR, 0, st>>>(fl.it_trsm + L.off, L.kb, a); break;
+      case 2: k_panel_update<T><<<g, 256, 0, st>>>(fl.it_pupd + 3 * L.off, L.kb, a); break;
+      case 3: k_syrk<T><<<g, 256, 0, st>>>(fl.it_syrk + L.off, a); break;
+      case 4: k_extend_add<T><<<g, 256, 0, st>>>(fl.it_eadd + L.off, a); break;
       case 6:
-        if ((e = launch_syrk_tc(fl.it_syrk_tc + 2 * L.off, L.cnt, fl.tc_maps, a, st))) return e;
+        if ((e = launch_syrk_tc(fl.it_syrk_tc + 2 * L.off, L.cnt, fl.tc_maps, a, st, nb))) return e;
         break;
-      case 7: k_block<T><<<(unsigned)L.cnt, kTR, 0, st>>>(fl.it_block + 3 * L.off, L.kb, a); break;
+      case 7: k_block<T><<<g, kTR, 0, st>>>(fl.it_block + 3 * L.off, L.kb, a); break;
       case 8:
-        if ((e = launch_syrk128(fl.it_syrk128 + L.off, L.cnt, a, st))) return e;
+        if ((e = launch_syrk128(fl.it_syrk128 + L.off, L.cnt, a, st, nb))) return e;
         break;
-      case 9: k_dstore<T><<<(unsigned)L.cnt, 256, 0, st>>>(fl.it_dstore + L.off, a); break;
+      case 9: k_dstore<T><<<g, 256, 0, st>>>(fl.it_dstore + L.off, a); break;
     }
     // kinds 0..5 -> profile slots 1..6; 8 (128-tile SYRK) shares the SYRK slot
     const int slot = L.kind == 6 ? KKT_K_SYRK_TC_PROF
@@ -582,8 +601,8 @@ cudaError_t launch_factor(const FacArgs<T>& a, const FacLists& fl, const double*
 }
 
 template cudaError_t launch_factor<double>(const FacArgs<double>&, const FacLists&, const double*, cudaStream_t,
-                                           Prof*);
+                                           Prof*, int);
 template cudaError_t launch_factor<float>(const FacArgs<float>&, const FacLists&, const double*, cudaStream_t,
-                                          Prof*);
+                                          Prof*, int);
 
 }  // namespace kkt

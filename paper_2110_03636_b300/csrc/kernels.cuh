@@ -19,7 +19,24 @@ struct FacArgs {
   T* U;
   T* Dsc;    // factored diagonal tiles of the current level's block steps (kPB x kPB each)
   DevStatus* st;
+  // batched form: system b = blockIdx.y works on these pointers advanced by
+  // b times the strides (elements; DevStatus entries for st); 0 for one system
+  int64_t bsL = 0, bsU = 0, bsD = 0, bsH = 0, bsJ = 0;
 };
+
+// The view of system blockIdx.y of a batched launch (identity for one system).
+template <typename T>
+__device__ __forceinline__ void batch_view(FacArgs<T>& a) {
+  const int64_t b = blockIdx.y;
+  if (b) {
+    a.L += b * a.bsL;
+    a.U += b * a.bsU;
+    a.Dsc += b * a.bsD;
+    a.Hv += b * a.bsH;
+    a.Jv += b * a.bsJ;
+    a.st += b;
+  }
+}
 
 // Optional per-launch timing (profile mode): events around each launch,
 // elapsed time accumulated per kernel kind.
@@ -48,17 +65,18 @@ struct InvArgs {
   const int64_t *pc_colbase, *pc_inv;
   const T* L;
   T* Linv;
+  int64_t bsL = 0, bsI = 0;   // batch strides (system blockIdx.y)
 };
 template <typename T>
-cudaError_t launch_tri_inv(const InvArgs<T>& a, int64_t npieces, int max_pw, cudaStream_t st);
+cudaError_t launch_tri_inv(const InvArgs<T>& a, int64_t npieces, int max_pw, cudaStream_t st, int nb = 1);
 
 // Tensor-core update tiles (tc_update.cu): items of 8 ints (Plan::it_syrk_tc).
 cudaError_t launch_tc_update(const int4* items, int64_t cnt, const uint8_t* maps, const FacArgs<float>& a,
-                             cudaStream_t st);
+                             cudaStream_t st, int nb = 1);
 
 template <typename T>
 cudaError_t launch_factor(const FacArgs<T>& a, const FacLists& fl, const double* dg, cudaStream_t st,
-                          Prof* prof = nullptr);
+                          Prof* prof = nullptr, int nb = 1);
 
 // Persistent CG on the Schur complement (plus the two direct solves).
 template <typename T>
@@ -78,6 +96,7 @@ struct SolveArgs {
   const ChunkDesc* cdesc;
   const HeadDesc* hdesc;
   const uint8_t* tmaps;     // one 128-byte tensor map per piece (TMA pieces only)
+  int32_t tz;               // the system's coordinate in the maps' third dimension (batched form)
   const int32_t *sfirst, *sw_, *snr, *sld;
   const int64_t *srow, *poff;
   const T* L;

@@ -273,13 +273,13 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                : "memory");
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-// 2-D tiled TMA load of the box at (x = row, y = column) of a tensor map held
-// in global memory; x * element size is a multiple of 16 bytes
-__device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int x, int y, unsigned long long* m) {
+// 3-D tiled TMA load of the box at (x = row, y = column, z = system of a batch)
+// of a tensor map held in global memory; x * element size is a multiple of 16 bytes
+__device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int x, int y, int z, unsigned long long* m) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
           saddr(dst)),
-      "l"(tmap), "r"(x), "r"(y), "r"(saddr(m))
+      "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(saddr(m))
       : "memory");
 }
 
@@ -323,7 +323,7 @@ __device__ int stage_tile(const SolveArgs<T>& a, int p, int64_t colbase, int ld,
   const int A0 = R0 & ~3;
   if (tma) {
     bytes_out = (uint32_t)cs * (uint32_t)pw * (uint32_t)sizeof(T);
-    if (issue && threadIdx.x == 0) tma_load_2d(tile, a.tmaps + (int64_t)p * 128, A0, 0, mbar);
+    if (issue && threadIdx.x == 0) tma_load_3d(tile, a.tmaps + (int64_t)p * 128, A0, 0, a.tz, mbar);
   } else {
     const int E = (R0 + nrows + 3) & ~3;
     const uint32_t bytes = (uint32_t)(E - A0) * (uint32_t)sizeof(T);

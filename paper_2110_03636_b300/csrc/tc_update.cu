@@ -38,6 +38,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.cuh"
 #include "plan.hpp"
@@ -106,11 +108,12 @@ __device__ __forceinline__ void bar_drain(unsigned long long* b, uint32_t parity
   }
 }
 
-__device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int x, int y, unsigned long long* b) {
+// 3-D tiled TMA load: (x = panel row, y = panel column, z = system of a batch)
+__device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int x, int y, int z, unsigned long long* b) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
           saddr(dst)),
-      "l"(tmap), "r"(x), "r"(y), "r"(saddr(b))
+      "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(saddr(b))
       : "memory");
 }
 
@@ -150,6 +153,7 @@ __device__ __forceinline__ void mma_commit(unsigned long long* b) {
 __global__ void __launch_bounds__(tcu::kThreads, 1)
     k_tc_update(const int4* __restrict__ items, int64_t nitems, const uint8_t* __restrict__ maps, FacArgs<float> a) {
   using namespace tcu;
+  batch_view(a);                                         // system blockIdx.y of a batched launch
   extern __shared__ __align__(1024) unsigned char sm[];
   unsigned char* raw = sm;                               // [kRaw][A, B][RAW]
   unsigned char* opb = sm + kRaw * 2 * RAW;              // [kOp][A hi, A lo, B hi, B lo][OPT]
@@ -202,8 +206,8 @@ __global__ void __launch_bounds__(tcu::kThreads, 1)
           if (!(ok = bar_wait(&bar[B_RAW_EMPTY + slot], (round & 1) ^ 1, abrt, a.st))) break;
           unsigned char* dst = raw + slot * 2 * RAW;
           bar_expect_tx(&bar[B_RAW_FULL + slot], diag ? RAW : 2 * RAW);
-          tma_load_2d(dst, mp, xa, i1.x + c * KC, &bar[B_RAW_FULL + slot]);
-          if (!diag) tma_load_2d(dst + RAW, mp, xb, i1.x + c * KC, &bar[B_RAW_FULL + slot]);
+          tma_load_3d(dst, mp, xa, i1.x + c * KC, (int)blockIdx.y, &bar[B_RAW_FULL + slot]);
+          if (!diag) tma_load_3d(dst + RAW, mp, xb, i1.x + c * KC, (int)blockIdx.y, &bar[B_RAW_FULL + slot]);
           rc++;
         }
       }
@@ -405,15 +409,18 @@ __global__ void __launch_bounds__(tcu::kThreads, 1)
 }
 
 cudaError_t launch_tc_update(const int4* items, int64_t cnt, const uint8_t* maps, const FacArgs<float>& a,
-                             cudaStream_t st) {
+                             cudaStream_t st, int nb) {
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_tc_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tcu::kSmem);
     if (e) return e;
     attr = true;
   }
-  const int64_t grid = cnt < kTcGrid ? cnt : kTcGrid;
-  k_tc_update<<<(unsigned)grid, tcu::kThreads, tcu::kSmem, st>>>(items, cnt, maps, a);
+  // one CTA per SM in all: nb systems share the SMs (each system's tiles go
+  // round-robin over its gridDim.x CTAs)
+  const int64_t per = std::max<int64_t>(1, kTcGrid / nb);
+  const int64_t grid = cnt < per ? cnt : per;
+  k_tc_update<<<dim3((unsigned)grid, (unsigned)nb), tcu::kThreads, tcu::kSmem, st>>>(items, cnt, maps, a);
   return cudaGetLastError();
 }
 
