@@ -280,8 +280,10 @@ kkt_status kkt_factor_batch(kkt_handle h, int32_t nsys, const double* H_vals, co
  * Up to four systems are solved at once, each by a helper handle made from
  * this analysis (own stream, host thread and workspace; its solve kernel on a
  * quarter of the SMs) that reads the system's factor in its batch slot; the
- * helpers are created by the first call. The call waits for `stream` first
- * and returns when every solve is done.
+ * helpers are created by the first call. A system whose solve met
+ * KKT_ERR_TIMEOUT while the others ran (the persistent solve kernel needs
+ * all its CTAs resident at once) is solved again alone afterwards. The call
+ * waits for `stream` first and returns when every solve is done.
  *   info    host kkt_info[nsys] (may be NULL)
  *   status  host int32[nsys] (may be NULL): per-system status (a system whose
  *           factorization failed reports KKT_ERR_NOT_SPD and is skipped)
@@ -439,14 +441,20 @@ const char* kkt_status_string(kkt_status s);
  * that cannot start does not block later ones of other patterns. Up to
  * max_inflight requests run at once, each on its slot's own CUDA stream and
  * host worker thread, so their kernels overlap on the device. Results do not
- * depend on what else runs (each slot is a separate handle).
+ * depend on what else runs (each slot is a separate handle). The persistent
+ * solve kernel needs all of its CTAs resident at once (give the server's
+ * options a solve_sms of about 148 / max_inflight); should one of its bounded
+ * waits run out while other requests' kernels hold the device, the request
+ * is run again with nothing else in flight (kkt_request_info.retried).
  * ------------------------------------------------------------------------ */
 typedef struct kkt_server_s* kkt_server;
 
 typedef struct kkt_request_info {
   int32_t status;      /* kkt_status of the factor + solve */
   int32_t pattern, slot;
-  int32_t cg_iters, ir_steps, pad;
+  int32_t cg_iters, ir_steps;
+  int32_t retried;     /* 1 if a bounded wait ran out while other requests were on the
+                          device and the request was run again alone */
   double rr, be;       /* as kkt_info */
   double t_submit, t_start, t_end;  /* seconds on the server's clock (steady, from its creation) */
 } kkt_request_info;

@@ -56,7 +56,7 @@ class kkt_symbolic_info(C.Structure):
 
 class kkt_request_info(C.Structure):
     _fields_ = [("status", C.c_int32), ("pattern", C.c_int32), ("slot", C.c_int32), ("cg_iters", C.c_int32),
-                ("ir_steps", C.c_int32), ("pad", C.c_int32), ("rr", C.c_double), ("be", C.c_double),
+                ("ir_steps", C.c_int32), ("retried", C.c_int32), ("rr", C.c_double), ("be", C.c_double),
                 ("t_submit", C.c_double), ("t_start", C.c_double), ("t_end", C.c_double)]
 
 

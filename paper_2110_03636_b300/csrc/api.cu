@@ -106,7 +106,8 @@ struct kkt_handle_s {
   // FGMRES refinement workspace (first use): basis V (N x (kRestart + 1)),
   // preconditioned directions Z (N x kRestart), N = n + m
   double *fV = nullptr, *fZ = nullptr, *fw = nullptr, *fr = nullptr, *fzero = nullptr, *fpart = nullptr,
-         *fdots = nullptr, *fcoef = nullptr;
+         *fdots = nullptr, *fcoef = nullptr, *fgs = nullptr;
+  double* hflag = nullptr;   // pinned: the FGMRES stop flag
   bool multi = false;
   void *mv;
   double *mrhx, *mp, *mr, *my, *mq, *mbS, *mres_x, *mres_y, *mwv, *mxa;
@@ -307,6 +308,7 @@ kkt_status kkt_destroy(kkt_handle h) {
   if (h->bgraph) cudaGraphExecDestroy(h->bgraph);
   if (h->bU) { cudaFree(h->bU); cudaFree(h->bDsc); cudaFree(h->bst); cudaFree(h->btc_maps); cudaFree(h->bs_maps); }
   if (h->hbst) cudaFreeHost(h->hbst);
+  if (h->hflag) cudaFreeHost(h->hflag);
   for (kkt_handle x : h->helpers) kkt_destroy(x);
   for (cudaStream_t x : h->hstreams) cudaStreamDestroy(x);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -557,7 +559,9 @@ static kkt_status device_stage(kkt_handle h, kkt_handle* out) {
   if (cudaMallocHost(&h->hst, sizeof(DevStatus)) != cudaSuccess) { cudaGetLastError(); h->hst = nullptr; kkt_destroy(h); return KKT_ERR_OOM; }
   if (cudaMallocHost(&h->h_dg, 6 * sizeof(double)) != cudaSuccess) { cudaGetLastError(); h->h_dg = nullptr; kkt_destroy(h); return KKT_ERR_OOM; }
   if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) { cudaGetLastError(); h->cap_stream = nullptr; kkt_destroy(h); return KKT_ERR_CUDA; }
-  if (cudaDeviceSynchronize() != cudaSuccess) { cudaGetLastError(); kkt_destroy(h); return KKT_ERR_CUDA; }
+  // (no device-wide synchronisation here: other threads may be capturing a
+  // graph or running solves on their own streams; the uploads above are
+  // synchronous copies)
   if (cudaEventCreate(&h->cg_a) != cudaSuccess || cudaEventCreate(&h->cg_b) != cudaSuccess) {
     cudaGetLastError();
     kkt_destroy(h);
@@ -861,7 +865,13 @@ static kkt_status solve_fgmres(kkt_handle h, const double* rx, const double* ry,
     h->fw = A.alloc<double>(N); h->fr = A.alloc<double>(N); h->fzero = A.alloc<double>(N);
     h->fpart = A.alloc<double>((size_t)296 * kMaxKrylov);
     h->fdots = A.alloc<double>(kMaxKrylov); h->fcoef = A.alloc<double>(kMaxKrylov);
+    h->fgs = A.alloc<double>((size_t)(kRestart + 1) * kRestart + 2 * kRestart + 2 * (kRestart + 1) + 1);
     if (A.failed) { h->fV = nullptr; return KKT_ERR_OOM; }
+    if (!h->hflag && cudaMallocHost((void**)&h->hflag, sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      h->fV = nullptr;
+      return KKT_ERR_OOM;
+    }
     CK(cudaMemsetAsync(h->fzero, 0, sizeof(double) * N, st));
   }
   kkt_status s = reset_status(h, st);
@@ -889,16 +899,6 @@ static kkt_status solve_fgmres(kkt_handle h, const double* rx, const double* ry,
     CK(cudaMemcpyAsync(h->dst, h->hst, sizeof(DevStatus), cudaMemcpyHostToDevice, st));
     return KKT_OK;
   };
-  auto dots = [&](const double* w, int cnt, double* out) -> kkt_status {
-    CK(launch_multidot(w, h->fV, N, N, cnt, h->fpart, h->fdots, st));
-    CK(cudaMemcpyAsync(out, h->fdots, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    return KKT_OK;
-  };
-  auto coefs = [&](const double* c, int cnt) -> kkt_status {   // pageable copy: the host buffer is reusable at once
-    CK(cudaMemcpy(h->fcoef, c, sizeof(double) * cnt, cudaMemcpyHostToDevice));
-    return KKT_OK;
-  };
   auto true_residual = [&](double& rr, double& rnorm, double& bnorm) -> kkt_status {
     kkt_status e = residual(h, rx, ry, dx, dy, st, h->fr, h->fr + n);
     if (e) return e;
@@ -919,14 +919,18 @@ static kkt_status solve_fgmres(kkt_handle h, const double* rx, const double* ry,
   if ((s = apply_M(rx, ry, dx, dy))) return finish(s);
   double rr, rnorm, bnorm;
   if ((s = true_residual(rr, rnorm, bnorm))) return finish(s);
-  double H[kRestart + 1][kRestart], cs[kRestart], sn[kRestart], g[kRestart + 1], hc[kMaxKrylov], d2[kMaxKrylov];
+  // Gram-Schmidt coefficients, the Hessenberg column, the rotations and the
+  // stop test stay on the device (k_fgmres_coef); the host reads one flag
+  // per step, and the preconditioner's status once per application
+  const int R = kRestart;
+  const double tol = 0.5 * h->opt.ir_rtol * bnorm;
+  auto dots_dev = [&](const double* w, const double* V, int cnt) -> cudaError_t {
+    return launch_multidot(w, V, N, N, cnt, h->fpart, h->fdots, st);
+  };
   while (rr > h->opt.ir_rtol && applications - 1 < h->opt.ir_maxit) {
-    // V0 = r / ||r||
-    double c0 = 1.0 / rnorm;
-    if ((s = coefs(&c0, 1))) return finish(s);
+    // V0 = r / ||r|| (||r|| from the residual's status on the device)
+    CK(launch_fgmres_coef(4, 0, R, h->fdots, h->dst, tol, h->fgs, h->fcoef, st));
     CK(launch_lincomb(h->fV, 0.0, h->fr, N, N, 1, h->fcoef, st));
-    for (int i = 0; i <= kRestart; i++) g[i] = 0.0;
-    g[0] = rnorm;
     int k = 0;
     for (; k < kRestart && applications - 1 < h->opt.ir_maxit; k++) {
       double* Vk = h->fV + (size_t)k * N;
@@ -935,52 +939,24 @@ static kkt_status solve_fgmres(kkt_handle h, const double* rx, const double* ry,
       // w = -K Z_k (the residual kernel with a zero right-hand side)
       if ((s = residual(h, h->fzero, h->fzero, Zk, Zk + n, st, h->fw, h->fw + n))) return finish(s);
       // u = K Z_k = -w; h_i = (u, V_i) = -(w, V_i); w <- w - sum (w, V_i) V_i (twice)
-      if ((s = dots(h->fw, k + 1, hc))) return finish(s);
-      for (int i = 0; i <= k; i++) d2[i] = -hc[i];
-      if ((s = coefs(d2, k + 1))) return finish(s);
+      CK(dots_dev(h->fw, h->fV, k + 1));
+      CK(launch_fgmres_coef(0, k, R, h->fdots, h->dst, tol, h->fgs, h->fcoef, st));
       CK(launch_lincomb(h->fw, 1.0, h->fV, N, N, k + 1, h->fcoef, st));
-      double hc2[kMaxKrylov];
-      if ((s = dots(h->fw, k + 1, hc2))) return finish(s);
-      for (int i = 0; i <= k; i++) { d2[i] = -hc2[i]; hc[i] += hc2[i]; }
-      if ((s = coefs(d2, k + 1))) return finish(s);
+      CK(dots_dev(h->fw, h->fV, k + 1));
+      CK(launch_fgmres_coef(1, k, R, h->fdots, h->dst, tol, h->fgs, h->fcoef, st));
       CK(launch_lincomb(h->fw, 1.0, h->fV, N, N, k + 1, h->fcoef, st));
-      CK(launch_multidot(h->fw, h->fw, N, N, 1, h->fpart, h->fdots, st));
-      double ww;
-      CK(cudaMemcpyAsync(&ww, h->fdots, sizeof(double), cudaMemcpyDeviceToHost, st));
+      CK(dots_dev(h->fw, h->fw, 1));
+      // column k of H, rotations, g; coef[0] = -1/||w||: V_{k+1} = u / ||u|| = -w / ||w||
+      CK(launch_fgmres_coef(2, k, R, h->fdots, h->dst, tol, h->fgs, h->fcoef, st));
+      CK(launch_lincomb(h->fV + (size_t)(k + 1) * N, 0.0, h->fw, N, N, 1, h->fcoef, st));
+      CK(cudaMemcpyAsync(h->hflag, h->fgs + (R + 1) * R + 2 * R + 2 * (R + 1), sizeof(double),
+                         cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
-      const double hn = std::sqrt(std::max(ww, 0.0));
-      for (int i = 0; i <= k; i++) H[i][k] = -hc[i];
-      H[k + 1][k] = hn;
-      // V_{k+1} = u / ||u|| = -w / hn
-      if (hn > 0) {
-        double c1 = -1.0 / hn;
-        if ((s = coefs(&c1, 1))) return finish(s);
-        CK(launch_lincomb(h->fV + (size_t)(k + 1) * N, 0.0, h->fw, N, N, 1, h->fcoef, st));
-      }
-      // Givens rotations
-      for (int i = 0; i < k; i++) {
-        const double t = cs[i] * H[i][k] + sn[i] * H[i + 1][k];
-        H[i + 1][k] = -sn[i] * H[i][k] + cs[i] * H[i + 1][k];
-        H[i][k] = t;
-      }
-      const double den = std::hypot(H[k][k], H[k + 1][k]);
-      cs[k] = den > 0 ? H[k][k] / den : 1.0;
-      sn[k] = den > 0 ? H[k + 1][k] / den : 0.0;
-      H[k][k] = den;
-      H[k + 1][k] = 0.0;
-      g[k + 1] = -sn[k] * g[k];
-      g[k] = cs[k] * g[k];
-      if (std::fabs(g[k + 1]) <= 0.5 * h->opt.ir_rtol * bnorm || hn == 0.0) { k++; break; }
+      if (*h->hflag != 0.0) { k++; break; }
     }
     // y = H^-1 g (upper triangular k x k); x += Z y
-    double y[kRestart];
-    for (int i = k - 1; i >= 0; i--) {
-      double t = g[i];
-      for (int j = i + 1; j < k; j++) t -= H[i][j] * y[j];
-      y[i] = H[i][i] != 0.0 ? t / H[i][i] : 0.0;
-    }
     if (k > 0) {
-      if ((s = coefs(y, k))) return finish(s);
+      CK(launch_fgmres_coef(3, k, R, h->fdots, h->dst, tol, h->fgs, h->fcoef, st));
       CK(launch_lincomb(dx, 1.0, h->fZ, N, n, k, h->fcoef, st));
       if (m) CK(launch_lincomb(dy, 1.0, h->fZ + n, N, m, k, h->fcoef, st));
     }
@@ -1498,6 +1474,26 @@ kkt_status kkt_solve_batch(kkt_handle h, int32_t nsys, const double* r_x, const 
   for (int k = 1; k < K; k++) th.emplace_back(run, k);
   run(0);
   for (std::thread& t : th) t.join();
+  // a bounded wait that ran out while other solves were resident: solve
+  // that system again alone (the persistent solve kernel's grid barriers need
+  // all of its CTAs on the device at once)
+  for (int b = 0; b < nsys; b++) {
+    if (res[b] != KKT_ERR_TIMEOUT) continue;
+    kkt_handle x = h->helpers[0];
+    x->delta = h->bdelta;
+    x->gamma = h->bgamma;
+    x->sv.L = (char*)h->bL + es * (size_t)h->P.panel_total * b;
+    x->sv.Linv = (char*)h->bLinv + es * (size_t)h->P.inv_total * b;
+    x->sv.Hv = h->bHv + (int64_t)b * h->nnzH;
+    x->sv.Jv = h->bJv + (int64_t)b * h->nnzJ;
+    x->sv.tmaps = h->bs_maps;
+    x->sv.tz = b;
+    x->factored = true;
+    res[b] = solve_common(x, r_x + b * n, r_y + b * m, dx + b * n, dy + b * m, h->hstreams[0]);
+    x->factored = false;
+    inf[b] = x->info;
+    const Handle_sv_saver restore(x);
+  }
   kkt_status worst = KKT_OK;
   for (int b = 0; b < nsys; b++) {
     if (info) info[b] = inf[b];

@@ -145,6 +145,10 @@ cudaError_t launch_multidot(const double* w, const double* V, int64_t ld, int64_
 cudaError_t launch_lincomb(double* y, double alpha, const double* V, int64_t ld, int64_t N, int cnt, const double* c,
                            cudaStream_t st);
 constexpr int kRedStride = 2 * kMaxRhs;   // doubles per CTA in the reduction buffer
+// FGMRES coefficients, rotations and stop test on the device (krylov.cu);
+// gs holds (R+1)R + 2R + 2(R+1) + 1 doubles
+cudaError_t launch_fgmres_coef(int mode, int k, int R, const double* dots, const DevStatus* st, double tol, double* gs,
+                               double* coef, cudaStream_t s);
 // FP64 products of the Krylov variants on S (krylov.cu)
 cudaError_t launch_jt_mult(int64_t n, const int64_t* tp, const int32_t* trow, const int32_t* tv, const double* Jv,
                            const double* y, double alpha, double beta, double* out, cudaStream_t st);

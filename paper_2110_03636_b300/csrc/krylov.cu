@@ -132,6 +132,69 @@ __global__ void k_jjt_values(int64_t ne, const int64_t* __restrict__ pp, const i
   }
 }
 
+// ------------------------------------------------ FGMRES coefficients on the device
+// State (doubles): H[(R+1) x R] row-major with row stride R, cs[R], sn[R],
+// g[R+1], hcol[R+1], then flag (1.0 when the cycle may stop). One thread.
+//   mode 0: hcol = dots;            coef = -dots       (first Gram-Schmidt pass)
+//   mode 1: hcol += dots;           coef = -dots       (reorthogonalisation)
+//   mode 2: hn = sqrt(max(dots[0], 0)); column k of H = -hcol, H[k+1][k] = hn;
+//           previous rotations, new rotation, g update; coef[0] = -1/hn (0 if
+//           hn = 0); flag = |g[k+1]| <= tol or hn = 0
+//   mode 3: coef = the solution y of the k x k upper triangle H y = g
+//   mode 4: start of a cycle: g = (rnorm, 0, ...), coef[0] = 1/rnorm, flag = 0
+__global__ void k_fgmres_coef(int mode, int k, int R, const double* __restrict__ dots, const DevStatus* st,
+                              double tol, double* __restrict__ gs, double* __restrict__ coef) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double* H = gs;
+  double* cs = H + (R + 1) * R;
+  double* sn = cs + R;
+  double* g = sn + R;
+  double* hcol = g + R + 1;
+  double* flag = hcol + R + 1;
+  if (mode == 0 || mode == 1) {
+    for (int i = 0; i <= k; i++) {
+      hcol[i] = mode == 0 ? dots[i] : hcol[i] + dots[i];
+      coef[i] = -dots[i];
+    }
+  } else if (mode == 2) {
+    const double hn = sqrt(fmax(dots[0], 0.0));
+    for (int i = 0; i <= k; i++) H[i * R + k] = -hcol[i];
+    H[(k + 1) * R + k] = hn;
+    for (int i = 0; i < k; i++) {
+      const double t = cs[i] * H[i * R + k] + sn[i] * H[(i + 1) * R + k];
+      H[(i + 1) * R + k] = -sn[i] * H[i * R + k] + cs[i] * H[(i + 1) * R + k];
+      H[i * R + k] = t;
+    }
+    const double den = hypot(H[k * R + k], H[(k + 1) * R + k]);
+    cs[k] = den > 0 ? H[k * R + k] / den : 1.0;
+    sn[k] = den > 0 ? H[(k + 1) * R + k] / den : 0.0;
+    H[k * R + k] = den;
+    H[(k + 1) * R + k] = 0.0;
+    g[k + 1] = -sn[k] * g[k];
+    g[k] = cs[k] * g[k];
+    coef[0] = hn > 0 ? -1.0 / hn : 0.0;
+    *flag = (fabs(g[k + 1]) <= tol || hn == 0.0) ? 1.0 : 0.0;
+  } else if (mode == 3) {
+    for (int i = k - 1; i >= 0; i--) {
+      double t = g[i];
+      for (int j = i + 1; j < k; j++) t -= H[i * R + j] * coef[j];
+      coef[i] = H[i * R + i] != 0.0 ? t / H[i * R + i] : 0.0;
+    }
+  } else {
+    const double rn = st->res_norm;
+    for (int i = 0; i <= R; i++) g[i] = 0.0;
+    g[0] = rn;
+    coef[0] = rn > 0 ? 1.0 / rn : 0.0;
+    *flag = 0.0;
+  }
+}
+
+cudaError_t launch_fgmres_coef(int mode, int k, int R, const double* dots, const DevStatus* st, double tol, double* gs,
+                               double* coef, cudaStream_t s) {
+  k_fgmres_coef<<<1, 32, 0, s>>>(mode, k, R, dots, st, tol, gs, coef);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_jt_mult(int64_t n, const int64_t* tp, const int32_t* trow, const int32_t* tv, const double* Jv,
                            const double* y, double alpha, double beta, double* out, cudaStream_t st) {
   k_jt_mult<<<krylov_grid(n), kKrylovThreads, 0, st>>>(n, tp, trow, tv, Jv, y, alpha, beta, out);

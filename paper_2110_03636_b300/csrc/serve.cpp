@@ -17,6 +17,7 @@
 #include <cstring>
 #include <deque>
 #include <mutex>
+#include <shared_mutex>
 #include <new>
 #include <thread>
 #include <unordered_map>
@@ -65,6 +66,7 @@ struct kkt_server_s {
   std::deque<Req*> pending;
   std::unordered_map<int64_t, Req*> reqs;
   std::mutex mu;
+  std::shared_mutex exclusive;   // held shared while a request runs, exclusively by a retry
   std::condition_variable cv_work, cv_done;
   std::vector<std::thread> workers;
   bool stop = false;
@@ -146,8 +148,20 @@ void worker(kkt_server s) {
     if (create) st = make_slot(s, p, &sl);
     r->info.t_start = s->now();
     if (st == KKT_OK) {
-      st = kkt_factor(sl->h, r->H, r->J, r->delta, r->gamma, sl->st);
-      if (st == KKT_OK) st = kkt_solve(sl->h, r->rx, r->ry, r->dx, r->dy, sl->st);
+      {
+        std::shared_lock<std::shared_mutex> run_lk(s->exclusive);
+        st = kkt_factor(sl->h, r->H, r->J, r->delta, r->gamma, sl->st);
+        if (st == KKT_OK) st = kkt_solve(sl->h, r->rx, r->ry, r->dx, r->dy, sl->st);
+      }
+      if (st == KKT_ERR_TIMEOUT) {
+        // a bounded wait ran out while other requests' kernels were resident
+        // (the persistent solve kernel needs all its CTAs on the device at
+        // once): run the request again with nothing else in flight
+        std::unique_lock<std::shared_mutex> alone(s->exclusive);
+        st = kkt_factor(sl->h, r->H, r->J, r->delta, r->gamma, sl->st);
+        if (st == KKT_OK) st = kkt_solve(sl->h, r->rx, r->ry, r->dx, r->dy, sl->st);
+        r->info.retried = 1;
+      }
       kkt_info inf{};
       kkt_get_info(sl->h, &inf);
       r->info.cg_iters = inf.cg_iters;
