@@ -13,6 +13,9 @@
 #include "symbolic.hpp"
 
 #include <algorithm>
+#include <thread>
+#include <mutex>
+#include <condition_variable>
 #include <cstdlib>
 #include <set>
 #include <tuple>
@@ -220,25 +223,37 @@ struct Nd {
   const std::vector<int64_t>& gp;
   const std::vector<int32_t>& gi;
   int32_t leaf;
-  std::vector<int32_t> member;   // stamp: vertex belongs to the current set
-  std::vector<int32_t> seen;     // stamp: visited by the current BFS
-  std::vector<int32_t> level;
-  int32_t stamp = 0;
-  Nd(const std::vector<int64_t>& p, const std::vector<int32_t>& i, int32_t l)
-      : gp(p), gi(i), leaf(l), member(p.size() - 1, 0), seen(p.size() - 1, 0), level(p.size() - 1, -1) {}
+  Nd(const std::vector<int64_t>& p, const std::vector<int32_t>& i, int32_t l) : gp(p), gi(i), leaf(l) {}
+
+  // Per-thread scratch: stamps mark membership of the current set and BFS
+  // visits (each thread counts its own stamps, so tasks on different threads
+  // never see each other's marks as their own).
+  struct Scratch {
+    std::vector<int32_t> member, seen;
+    int32_t stamp = 0;
+    std::vector<std::vector<int32_t>> L, L2;
+    explicit Scratch(size_t n) : member(n, 0), seen(n, 0) {}
+  };
+  // A subproblem and where its vertices go in the order: kind 0 = a set to
+  // split into components, 2 = one connected component.
+  struct Task {
+    int kind;
+    int64_t off;
+    std::vector<int32_t> v;
+  };
 
   // BFS level structure of the member set (stamp mst) from r
-  void levels_from(int32_t r, int32_t mst, std::vector<std::vector<int32_t>>& L) {
+  void levels_from(Scratch& w, int32_t r, int32_t mst, std::vector<std::vector<int32_t>>& L) {
     L.clear();
-    const int32_t st = ++stamp;
+    const int32_t st = ++w.stamp;
     L.push_back({r});
-    seen[r] = st;
+    w.seen[r] = st;
     for (size_t d = 0; d < L.size(); d++) {
       std::vector<int32_t> nxt;
       for (int32_t v : L[d])
         for (int64_t q = gp[v]; q < gp[v + 1]; q++) {
           const int32_t u = gi[q];
-          if (member[u] == mst && seen[u] != st) { seen[u] = st; nxt.push_back(u); }
+          if (w.member[u] == mst && w.seen[u] != st) { w.seen[u] = st; nxt.push_back(u); }
         }
       if (nxt.empty()) break;
       std::sort(nxt.begin(), nxt.end());
@@ -246,92 +261,135 @@ struct Nd {
     }
   }
 
+  // One task: writes the vertices it places into order[] and appends the
+  // subtasks it creates to out (each with its final offset).
+  void process(Task& t, Scratch& w, std::vector<int32_t>& order, std::vector<Task>& out) {
+    if (t.kind == 0) {
+      std::sort(t.v.begin(), t.v.end());
+      const int32_t mst = ++w.stamp;
+      for (int32_t v : t.v) w.member[v] = mst;
+      const int32_t vst = ++w.stamp;
+      int64_t off = t.off;
+      for (int32_t s0 : t.v) {
+        if (w.seen[s0] == vst) continue;
+        std::vector<int32_t> c{s0};
+        w.seen[s0] = vst;
+        for (size_t h = 0; h < c.size(); h++)
+          for (int64_t q = gp[c[h]]; q < gp[c[h] + 1]; q++) {
+            const int32_t u = gi[q];
+            if (w.member[u] == mst && w.seen[u] != vst) { w.seen[u] = vst; c.push_back(u); }
+          }
+        std::sort(c.begin(), c.end());
+        const int64_t sz = (int64_t)c.size();
+        out.push_back({2, off, std::move(c)});
+        off += sz;
+      }
+      return;
+    }
+    std::vector<int32_t>& C = t.v;
+    auto emit = [&](const std::vector<int32_t>& v, int64_t off) { std::copy(v.begin(), v.end(), order.begin() + off); };
+    if ((int64_t)C.size() <= leaf) { emit(C, t.off); return; }
+    const int32_t mst = ++w.stamp;
+    for (int32_t v : C) w.member[v] = mst;
+    auto deg_in = [&](int32_t v) {
+      int64_t d = 0;
+      for (int64_t q = gp[v]; q < gp[v + 1]; q++) d += w.member[gi[q]] == mst;
+      return d;
+    };
+    std::vector<std::vector<int32_t>>& L = w.L;
+    std::vector<std::vector<int32_t>>& L2 = w.L2;
+    levels_from(w, C[0], mst, L);
+    for (;;) {
+      int32_t x = -1;
+      int64_t bd = 0;
+      for (int32_t v : L.back()) {
+        const int64_t d = deg_in(v);
+        if (x < 0 || d < bd || (d == bd && v < x)) { x = v; bd = d; }
+      }
+      levels_from(w, x, mst, L2);
+      if (L2.size() > L.size()) std::swap(L, L2);
+      else break;
+    }
+    const int64_t h = (int64_t)L.size() - 1;
+    if (h < 2) { emit(C, t.off); return; }
+    const int64_t lo = std::max<int64_t>(1, h / 3);
+    const int64_t hi = std::min<int64_t>(h - 1, std::max<int64_t>(1, (2 * h + 2) / 3));
+    const int64_t mid = (h + 1) / 2;
+    int64_t k = lo;
+    for (int64_t q = lo + 1; q <= hi; q++) {
+      const auto key = std::make_tuple(L[q].size(), std::llabs(q - mid), q);
+      const auto best = std::make_tuple(L[k].size(), std::llabs(k - mid), k);
+      if (key < best) k = q;
+    }
+    const int32_t nst = ++w.stamp;            // marks level k+1
+    for (int32_t v : L[k + 1]) w.seen[v] = nst;
+    std::vector<int32_t> S, P1, P2;
+    for (int64_t d = 0; d < k; d++) P1.insert(P1.end(), L[d].begin(), L[d].end());
+    for (int32_t v : L[k]) {
+      bool sep = false;
+      for (int64_t q = gp[v]; q < gp[v + 1] && !sep; q++) sep = w.seen[gi[q]] == nst;
+      (sep ? S : P1).push_back(v);
+    }
+    for (int64_t d = k + 1; d <= h; d++) P2.insert(P2.end(), L[d].begin(), L[d].end());
+    // order = part before, part after, separator
+    const int64_t n1 = (int64_t)P1.size(), n2 = (int64_t)P2.size();
+    emit(S, t.off + n1 + n2);
+    out.push_back({0, t.off, std::move(P1)});
+    out.push_back({0, t.off + n1, std::move(P2)});
+  }
+
+  // Subproblems are independent and each knows its place in the order, so
+  // they run on a pool of threads (a subproblem below kLocal vertices is
+  // finished by the thread that made it); the order does not depend on the
+  // schedule.
   void run(std::vector<int32_t>& order) {
     const int32_t n = (int32_t)gp.size() - 1;
-    order.clear();
-    order.reserve(n);
-    struct Task { int kind; std::vector<int32_t> v; };   // 0 set, 1 emit, 2 connected component
-    std::vector<Task> stack;
+    order.assign(n, -1);
+    constexpr int64_t kLocal = 4096;
+    unsigned nt = std::thread::hardware_concurrency();
+    nt = std::max(1u, std::min(nt, 32u));
+    if (n < 4 * kLocal) nt = 1;
+    std::vector<Task> queue;
     std::vector<int32_t> all(n);
     for (int32_t i = 0; i < n; i++) all[i] = i;
-    stack.push_back({0, std::move(all)});
-    std::vector<std::vector<int32_t>> L, L2;
-    while (!stack.empty()) {
-      Task t = std::move(stack.back());
-      stack.pop_back();
-      if (t.kind == 1) {
-        order.insert(order.end(), t.v.begin(), t.v.end());
-        continue;
-      }
-      if (t.kind == 0) {
-        std::sort(t.v.begin(), t.v.end());
-        const int32_t mst = ++stamp;
-        for (int32_t v : t.v) member[v] = mst;
-        const int32_t vst = ++stamp;
-        std::vector<std::vector<int32_t>> comps;
-        for (int32_t s0 : t.v) {
-          if (seen[s0] == vst) continue;
-          std::vector<int32_t> c{s0};
-          seen[s0] = vst;
-          for (size_t h = 0; h < c.size(); h++)
-            for (int64_t q = gp[c[h]]; q < gp[c[h] + 1]; q++) {
-              const int32_t u = gi[q];
-              if (member[u] == mst && seen[u] != vst) { seen[u] = vst; c.push_back(u); }
-            }
-          std::sort(c.begin(), c.end());
-          comps.push_back(std::move(c));
-        }
-        for (size_t k = comps.size(); k-- > 0;) stack.push_back({2, std::move(comps[k])});
-        continue;
-      }
-      std::vector<int32_t>& C = t.v;
-      if ((int64_t)C.size() <= leaf) { stack.push_back({1, std::move(C)}); continue; }
-      const int32_t mst = ++stamp;
-      for (int32_t v : C) member[v] = mst;
-      auto deg_in = [&](int32_t v) {
-        int64_t d = 0;
-        for (int64_t q = gp[v]; q < gp[v + 1]; q++) d += member[gi[q]] == mst;
-        return d;
-      };
-      levels_from(C[0], mst, L);
+    queue.push_back({0, 0, std::move(all)});
+    std::mutex mu;
+    std::condition_variable cv;
+    int busy = 0;
+    auto worker = [&]() {
+      Scratch w((size_t)n);
+      std::vector<Task> out, local;
+      std::unique_lock<std::mutex> lk(mu);
       for (;;) {
-        int32_t x = -1;
-        int64_t bd = 0;
-        for (int32_t v : L.back()) {
-          const int64_t d = deg_in(v);
-          if (x < 0 || d < bd || (d == bd && v < x)) { x = v; bd = d; }
+        cv.wait(lk, [&] { return !queue.empty() || busy == 0; });
+        if (queue.empty()) return;   // busy == 0 and nothing queued: done
+        Task t = std::move(queue.back());
+        queue.pop_back();
+        busy++;
+        lk.unlock();
+        local.clear();
+        local.push_back(std::move(t));
+        std::vector<Task> share;
+        while (!local.empty()) {
+          Task u = std::move(local.back());
+          local.pop_back();
+          out.clear();
+          process(u, w, order, out);
+          for (Task& o : out) ((int64_t)o.v.size() >= kLocal && nt > 1 ? share : local).push_back(std::move(o));
         }
-        levels_from(x, mst, L2);
-        if (L2.size() > L.size()) std::swap(L, L2);
-        else break;
+        lk.lock();
+        for (Task& o : share) queue.push_back(std::move(o));
+        busy--;
+        cv.notify_all();
       }
-      const int64_t h = (int64_t)L.size() - 1;
-      if (h < 2) { stack.push_back({1, std::move(C)}); continue; }
-      const int64_t lo = std::max<int64_t>(1, h / 3);
-      const int64_t hi = std::min<int64_t>(h - 1, std::max<int64_t>(1, (2 * h + 2) / 3));
-      const int64_t mid = (h + 1) / 2;
-      int64_t k = lo;
-      for (int64_t q = lo + 1; q <= hi; q++) {
-        const auto key = std::make_tuple(L[q].size(), std::llabs(q - mid), q);
-        const auto best = std::make_tuple(L[k].size(), std::llabs(k - mid), k);
-        if (key < best) k = q;
-      }
-      const int32_t nst = ++stamp;            // marks level k+1
-      for (int32_t v : L[k + 1]) seen[v] = nst;
-      std::vector<int32_t> S, P1, P2;
-      for (int64_t d = 0; d < k; d++) P1.insert(P1.end(), L[d].begin(), L[d].end());
-      for (int32_t v : L[k]) {
-        bool sep = false;
-        for (int64_t q = gp[v]; q < gp[v + 1] && !sep; q++) sep = seen[gi[q]] == nst;
-        (sep ? S : P1).push_back(v);
-      }
-      for (int64_t d = k + 1; d <= h; d++) P2.insert(P2.end(), L[d].begin(), L[d].end());
-      stack.push_back({1, std::move(S)});
-      stack.push_back({0, std::move(P2)});
-      stack.push_back({0, std::move(P1)});
-    }
+    };
+    std::vector<std::thread> th;
+    for (unsigned k = 1; k < nt; k++) th.emplace_back(worker);
+    worker();
+    for (std::thread& x : th) x.join();
   }
 };
+
 
 // --------------------------------------------------------------- etree
 // Liu's algorithm on P A P^T given in the graph's labels and a permutation.
