@@ -242,6 +242,12 @@ __global__ void __launch_bounds__(tcu::kThreads, 1)
           const float* src = ra + (half ? BOXR * KC : 0) + (half ? sb : sa) + i;
           unsigned char* hi = o + (half ? 2 : 0) * OPT;
           unsigned char* lo = hi + OPT;
+          // all 32 loads of the row first: the stores below go to other
+          // shared-memory tiles, but the compiler cannot tell, so loads
+          // interleaved with them would each wait out their latency
+          float xv[KC];
+#pragma unroll
+          for (int k = 0; k < KC; k++) xv[k] = src[k * BOXR];
 #pragma unroll
           for (int q = 0; q < KC / 4; q++) {
             float4 h, l;
@@ -249,7 +255,7 @@ __global__ void __launch_bounds__(tcu::kThreads, 1)
             float* lp = &l.x;
 #pragma unroll
             for (int r = 0; r < 4; r++) {
-              const float x = src[(4 * q + r) * BOXR];
+              const float x = xv[4 * q + r];
               const float xh = tf32_rna(x);
               hp[r] = xh;
               lp[r] = tf32_rna(x - xh);
