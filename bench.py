@@ -252,7 +252,7 @@ def run_ours(args, rank, world):
     s.set_profile(False)
     per_step = {k: v[0] / prof_steps for k, v in prof.items() if v[1]}
     launches_per_step = sum(v[1] for v in prof.values()) / prof_steps
-    fac_kinds = ("assemble", "potrf", "trsm", "panel_update", "syrk", "extend_add", "zero_u", "tri_inv", "syrk_tc",
+    fac_kinds = ("assemble", "potrf", "trsm", "panel_update", "syrk", "extend_add", "tc_split", "tri_inv", "syrk_tc",
                  "block")
     fac_ms = sum(per_step.get(k, 0.0) for k in fac_kinds)
     tc_ms = per_step.get("syrk_tc", 0.0)

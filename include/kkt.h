@@ -130,11 +130,12 @@ typedef struct kkt_options {
 
 /* Kernel kinds reported by kkt_get_profile. Kinds a plan does not launch
  * stay zero: KKT_MIXED factors with KKT_K_BLOCK (fused POTRF + TRSM) instead
- * of KKT_K_POTRF and KKT_K_TRSM; no plan clears update matrices any more
- * (KKT_K_ZERO_U): the SYRK stores them. */
+ * of KKT_K_POTRF and KKT_K_TRSM; KKT_K_TC_SPLIT (the TF32 hi/lo split of the
+ * operands of each tensor-core launch) and KKT_K_SYRK_TC (the tensor-core
+ * tiles) run only in KKT_MIXED with tensor_cores = 1. */
 enum {
   KKT_K_ASSEMBLE = 0, KKT_K_POTRF = 1, KKT_K_TRSM = 2, KKT_K_PANEL_UPDATE = 3, KKT_K_SYRK = 4,
-  KKT_K_EXTEND_ADD = 5, KKT_K_ZERO_U = 6, KKT_K_CG = 7, KKT_K_RESIDUAL = 8, KKT_K_TRI_INV = 9,
+  KKT_K_EXTEND_ADD = 5, KKT_K_TC_SPLIT = 6, KKT_K_CG = 7, KKT_K_RESIDUAL = 8, KKT_K_TRI_INV = 9,
   KKT_K_SYRK_TC = 10, KKT_K_BLOCK = 11, KKT_K_COUNT = 12
 };
 

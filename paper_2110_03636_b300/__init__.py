@@ -133,7 +133,7 @@ EXPORTED = ("kkt_default_options", "kkt_analyse", "kkt_analyse_host", "kkt_facto
             "kkt_get_factor_panels", "kkt_get_profile", "kkt_get_solve_counters", "kkt_residual_noalloc",
             "kkt_get_solve_trace", "kkt_get_solve_item_order", "kkt_destroy", "kkt_status_string", "kkt_analyse_4x4", "kkt_analyse_4x4_host", "kkt_4x4_inner",
             "kkt_get_4x4_pattern", "kkt_factor_4x4", "kkt_solve_4x4", "kkt_destroy_4x4")
-KERNEL_KINDS = ("assemble", "potrf", "trsm", "panel_update", "syrk", "extend_add", "zero_u", "cg_persistent",
+KERNEL_KINDS = ("assemble", "potrf", "trsm", "panel_update", "syrk", "extend_add", "tc_split", "cg_persistent",
                 "residual", "tri_inv", "syrk_tc", "block")
 
 

@@ -70,8 +70,10 @@ struct kkt_handle_s {
   // pattern / plan on the device
   int32_t *sfirst, *sw, *snr, *sld, *sparent, *rel, *sn_rows, *perm;
   int64_t *srow, *poff, *uoff;
-  int4 *it_potrf, *it_trsm, *it_pupd, *it_syrk, *it_eadd, *it_syrk_tc, *it_block, *it_syrk128, *it_dstore;
+  int4 *it_potrf, *it_trsm, *it_pupd, *it_syrk, *it_eadd, *it_syrk_tc, *it_block, *it_syrk128, *it_dstore,
+      *it_tc_split;
   void* Dsc;
+  float* Wtc = nullptr;         // split operand tiles of one tensor-core launch (FP32 factor)
   int64_t *slot_pos, *src_ptr;
   int32_t *srcA, *srcB;
   int32_t *Jcol_perm, *JT_row, *JT_vidx, *Hs_col, *Hs_vidx, *JTo_row, *JTo_vidx, *J_colidx;
@@ -85,7 +87,6 @@ struct kkt_handle_s {
   ChunkDesc* cdesc;
   HeadDesc* hdesc;
   uint8_t* tmaps;
-  uint8_t* tc_maps = nullptr;   // tensor maps of the tensor-core fronts' panels (FP32)
   // values and workspace
   double *Hv, *Jv;
   void *L, *U, *v, *Linv;
@@ -129,9 +130,10 @@ struct kkt_handle_s {
   // batched form: nsys slots of panels, inverses, update matrices, diagonal
   // tile scratch, values and status; 3-D tensor maps over them; one graph
   void *bU = nullptr, *bDsc = nullptr;
+  float* bWtc = nullptr;
   DevStatus* bst = nullptr;
   DevStatus* hbst = nullptr;   // pinned
-  uint8_t *btc_maps = nullptr, *bs_maps = nullptr;
+  uint8_t* bs_maps = nullptr;
   cudaGraphExec_t bgraph = nullptr;
   int32_t bgraph_nb = 0;
   double bdelta = 0, bgamma = 0;   // the shift and gamma the batch was factored with
@@ -205,39 +207,6 @@ static bool build_tensor_maps(const Plan& P, void* L, size_t es, int depth, std:
   return true;
 }
 
-// Tensor maps of the fronts whose updates run on the tensor cores: the
-// whole FP32 panel (ld rows x w columns; rows past ld and columns past w
-// read as zeros), boxes of kTcBoxRows rows x 32 columns.
-static bool build_tc_maps(const Plan& P, void* L, int depth, std::vector<uint8_t>& out) {
-  out.assign(P.tc_front.size() * 128, 0);
-  if (P.tc_front.empty()) return true;
-  void* fn = nullptr;
-  cudaDriverEntryPointQueryResult q;
-  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-      q != cudaDriverEntryPointSuccess || !fn) {
-    cudaGetLastError();
-    return false;
-  }
-  PFN_cuTensorMapEncodeTiled_v12000 encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
-  for (size_t k = 0; k < P.tc_front.size(); k++) {
-    const int32_t s = P.tc_front[k];
-    const int32_t ld = P.sld[s], w = P.sw[s];
-    if (ld < kTcBoxRows || w < kTcMinWidth || (ld * 4) % 16 || (P.poff[s] * 4) % 16) return false;
-    // third dimension: the systems of a batch (panel sets panel_total apart)
-    const cuuint64_t dims[3] = {(cuuint64_t)ld, (cuuint64_t)w, (cuuint64_t)depth};
-    const cuuint64_t strides[2] = {(cuuint64_t)ld * 4, (cuuint64_t)P.panel_total * 4};
-    const cuuint32_t boxd[3] = {(cuuint32_t)kTcBoxRows, 32, 1};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    CUtensorMap* m = (CUtensorMap*)(out.data() + k * 128);
-    void* g = (char*)L + (size_t)P.poff[s] * 4;
-    if (encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, g, dims, strides, boxd, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-      return false;
-  }
-  return true;
-}
-
 static kkt_status cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return KKT_OK;
   cudaGetLastError();
@@ -306,7 +275,7 @@ kkt_status kkt_destroy(kkt_handle h) {
   if (h->reg_graph) cudaGraphExecDestroy(h->reg_graph);
   if (h->jjt) kkt_destroy(h->jjt);
   if (h->bgraph) cudaGraphExecDestroy(h->bgraph);
-  if (h->bU) { cudaFree(h->bU); cudaFree(h->bDsc); cudaFree(h->bst); cudaFree(h->btc_maps); cudaFree(h->bs_maps); }
+  if (h->bU) { cudaFree(h->bU); cudaFree(h->bDsc); cudaFree(h->bst); cudaFree(h->bs_maps); cudaFree(h->bWtc); }
   if (h->hbst) cudaFreeHost(h->hbst);
   if (h->hflag) cudaFreeHost(h->hflag);
   for (kkt_handle x : h->helpers) kkt_destroy(x);
@@ -452,6 +421,7 @@ static kkt_status device_stage(kkt_handle h, kkt_handle* out) {
   h->it_trsm = as_int4(P.it_trsm); h->it_pupd = as_int4(P.it_pupd);
   h->it_syrk = as_int4(P.it_syrk); h->it_eadd = as_int4(P.it_eadd); h->it_syrk_tc = as_int4(P.it_syrk_tc);
   h->it_block = as_int4(P.it_block); h->it_syrk128 = as_int4(P.it_syrk128); h->it_dstore = as_int4(P.it_dstore);
+  h->it_tc_split = as_int4(P.it_tc_split);
   h->slot_pos = A.upload(P.slot_pos); h->src_ptr = A.upload(P.src_ptr);
   h->srcA = A.upload(P.srcA); h->srcB = A.upload(P.srcB);
   h->Jcol_perm = A.upload(P.Jcol_perm); h->JT_ptr = A.upload(P.JT_ptr);
@@ -481,6 +451,7 @@ static kkt_status device_stage(kkt_handle h, kkt_handle* out) {
   h->L = A.alloc<char>(es * (size_t)P.panel_total);
   h->U = A.alloc<char>(es * (size_t)P.u_total);
   h->Dsc = A.alloc<char>(es * (size_t)P.dsc_total);
+  if (!f64 && P.tc_ws_tiles > 0) h->Wtc = A.alloc<float>((size_t)P.tc_ws_tiles * kTcTileFloats);
   h->v = A.alloc<char>(es * (size_t)n);
   h->Linv = A.alloc<char>(es * (size_t)P.inv_total);
   {
@@ -489,10 +460,6 @@ static kkt_status device_stage(kkt_handle h, kkt_handle* out) {
       if (!build_tensor_maps(P, h->L, es, 1, maps)) { kkt_destroy(h); return KKT_ERR_CUDA; }
       h->tmaps = A.upload(maps);
       h->sv.L = h->L; h->sv.Linv = h->Linv; h->sv.Hv = h->Hv; h->sv.Jv = h->Jv; h->sv.tmaps = h->tmaps; h->sv.tz = 0;
-      if (!f64) {
-        if (!build_tc_maps(P, h->L, 1, maps)) { kkt_destroy(h); return KKT_ERR_CUDA; }
-        h->tc_maps = A.upload(maps);
-      }
     }
   }
   h->rhx = A.alloc<double>(n);
@@ -625,18 +592,19 @@ static cudaError_t factor_launches(kkt_handle h, cudaStream_t st, Prof* prof, in
   a.sfirst = h->sfirst; a.sw = h->sw; a.snr = h->snr; a.sld = h->sld; a.sparent = h->sparent; a.rel = h->rel;
   a.srow = h->srow; a.poff = h->poff; a.uoff = h->uoff;
   a.Hv = h->Hv; a.Jv = h->Jv;
-  a.L = (T*)h->L; a.U = (T*)h->U; a.Dsc = (T*)h->Dsc; a.st = h->dst;
+  a.L = (T*)h->L; a.U = (T*)h->U; a.Dsc = (T*)h->Dsc; a.st = h->dst; a.W = h->Wtc;
   if (nb > 0) {
     a.Hv = h->bHv; a.Jv = h->bJv;
-    a.L = (T*)h->bL; a.U = (T*)h->bU; a.Dsc = (T*)h->bDsc; a.st = h->bst;
+    a.L = (T*)h->bL; a.U = (T*)h->bU; a.Dsc = (T*)h->bDsc; a.st = h->bst; a.W = h->bWtc;
     a.bsL = h->P.panel_total; a.bsU = h->P.u_total; a.bsD = h->P.dsc_total;
+    a.bsW = h->P.tc_ws_tiles * kTcTileFloats;
     a.bsH = h->nnzH; a.bsJ = h->nnzJ;
   }
   FacLists fl;
   fl.it_potrf = h->it_potrf; fl.it_trsm = h->it_trsm; fl.it_pupd = h->it_pupd;
   fl.it_syrk = h->it_syrk; fl.it_eadd = h->it_eadd; fl.it_syrk_tc = h->it_syrk_tc;
-  fl.tc_maps = nb > 0 ? h->btc_maps : h->tc_maps;
   fl.it_block = h->it_block; fl.it_syrk128 = h->it_syrk128; fl.it_dstore = h->it_dstore;
+  fl.it_tc_split = h->it_tc_split;
   fl.slot_pos = h->slot_pos; fl.src_ptr = h->src_ptr; fl.srcA = h->srcA; fl.srcB = h->srcB;
   fl.nslot = (int64_t)h->P.slot_pos.size();
   fl.panel_total = h->P.panel_total; fl.u_total = h->P.u_total;
@@ -1307,14 +1275,15 @@ static kkt_status batch_reserve(kkt_handle h, int32_t nsys) {
   const Plan& P = h->P;
   const bool f64 = h->opt.precision == KKT_FP64;
   const size_t es = f64 ? sizeof(double) : sizeof(float);
-  void* old[] = {h->bL, h->bLinv, h->bHv, h->bJv, h->bU, h->bDsc, h->bst, h->btc_maps, h->bs_maps};
+  void* old[] = {h->bL, h->bLinv, h->bHv, h->bJv, h->bU, h->bDsc, h->bst, h->bs_maps, h->bWtc};
   for (void* p : old) cudaFree(p);
   if (h->hbst) cudaFreeHost(h->hbst);
   if (h->bgraph) cudaGraphExecDestroy(h->bgraph);
   h->bL = h->bLinv = h->bU = h->bDsc = nullptr;
   h->bHv = h->bJv = nullptr;
   h->bst = h->hbst = nullptr;
-  h->btc_maps = h->bs_maps = nullptr;
+  h->bs_maps = nullptr;
+  h->bWtc = nullptr;
   h->bgraph = nullptr;
   h->bgraph_nb = 0;
   h->batch_cap = 0;
@@ -1324,6 +1293,8 @@ static kkt_status batch_reserve(kkt_handle h, int32_t nsys) {
             al((void**)&h->bJv, sizeof(double) * (size_t)h->nnzJ * nsys) &&
             al(&h->bU, es * (size_t)P.u_total * nsys) && al(&h->bDsc, es * (size_t)P.dsc_total * nsys) &&
             al((void**)&h->bst, sizeof(DevStatus) * nsys) &&
+            (f64 || P.tc_ws_tiles == 0 ||
+             al((void**)&h->bWtc, sizeof(float) * (size_t)P.tc_ws_tiles * kTcTileFloats * nsys)) &&
             cudaMallocHost((void**)&h->hbst, sizeof(DevStatus) * nsys) == cudaSuccess;
   if (!ok) { cudaGetLastError(); return KKT_ERR_OOM; }
   std::vector<uint8_t> maps;
@@ -1331,13 +1302,6 @@ static kkt_status batch_reserve(kkt_handle h, int32_t nsys) {
   if (!maps.empty()) {
     if (!al((void**)&h->bs_maps, maps.size())) { cudaGetLastError(); return KKT_ERR_OOM; }
     CK(cudaMemcpy(h->bs_maps, maps.data(), maps.size(), cudaMemcpyHostToDevice));
-  }
-  if (!f64) {
-    if (!build_tc_maps(P, h->bL, nsys, maps)) return KKT_ERR_CUDA;
-    if (!maps.empty()) {
-      if (!al((void**)&h->btc_maps, maps.size())) { cudaGetLastError(); return KKT_ERR_OOM; }
-      CK(cudaMemcpy(h->btc_maps, maps.data(), maps.size(), cudaMemcpyHostToDevice));
-    }
   }
   h->batch_cap = nsys;
   return KKT_OK;

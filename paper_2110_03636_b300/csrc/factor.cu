@@ -482,12 +482,18 @@ static cudaError_t launch_syrk128(const int4*, int64_t, const FacArgs<T>&, cudaS
   return cudaErrorNotSupported;   // FP64 fronts keep the 64 x 64 tiles
 }
 
-static cudaError_t launch_syrk_tc(const int4* items, int64_t cnt, const uint8_t* maps, const FacArgs<float>& a,
-                                  cudaStream_t st, int nb) {
-  return launch_tc_update(items, cnt, maps, a, st, nb);
+static cudaError_t launch_split_tc(const int4* items, int64_t cnt, const FacArgs<float>& a, cudaStream_t st, int nb) {
+  return launch_tc_split(items, cnt, a, st, nb);
 }
 template <typename T>
-static cudaError_t launch_syrk_tc(const int4*, int64_t, const uint8_t*, const FacArgs<T>&, cudaStream_t, int) {
+static cudaError_t launch_split_tc(const int4*, int64_t, const FacArgs<T>&, cudaStream_t, int) {
+  return cudaErrorNotSupported;   // the FP64 factor has no tensor-core path
+}
+static cudaError_t launch_syrk_tc(const int4* items, int64_t cnt, const FacArgs<float>& a, cudaStream_t st, int nb) {
+  return launch_tc_update(items, cnt, a, st, nb);
+}
+template <typename T>
+static cudaError_t launch_syrk_tc(const int4*, int64_t, const FacArgs<T>&, cudaStream_t, int) {
   return cudaErrorNotSupported;   // the tensor-core updates are the FP32 factor's
 }
 
@@ -584,17 +590,22 @@ cudaError_t launch_factor(const FacArgs<T>& a, const FacLists& fl, const double*
       case 3: k_syrk<T><<<g, 256, 0, st>>>(fl.it_syrk + L.off, a); break;
       case 4: k_extend_add<T><<<g, 256, 0, st>>>(fl.it_eadd + L.off, a); break;
       case 6:
-        if ((e = launch_syrk_tc(fl.it_syrk_tc + 2 * L.off, L.cnt, fl.tc_maps, a, st, nb))) return e;
+        if ((e = launch_syrk_tc(fl.it_syrk_tc + (kTcItem / 4) * L.off, L.cnt, a, st, nb))) return e;
         break;
       case 7: k_block<T><<<g, kTR, 0, st>>>(fl.it_block + 3 * L.off, L.kb, a); break;
       case 8:
         if ((e = launch_syrk128(fl.it_syrk128 + L.off, L.cnt, a, st, nb))) return e;
         break;
       case 9: k_dstore<T><<<g, 256, 0, st>>>(fl.it_dstore + L.off, a); break;
+      case 10:
+        if ((e = launch_split_tc(fl.it_tc_split + (kTcItem / 4) * L.off, L.cnt, a, st, nb))) return e;
+        break;
     }
-    // kinds 0..5 -> profile slots 1..6; 8 (128-tile SYRK) shares the SYRK slot
-    const int slot = L.kind == 6 ? KKT_K_SYRK_TC_PROF
-                                 : ((L.kind == 7 || L.kind == 9) ? KKT_K_BLOCK_PROF : (L.kind == 8 ? 4 : 1 + L.kind));
+    // kinds 0..4 -> profile slots 1..5; 8 (128-tile SYRK) shares the SYRK
+    // slot, 7 and 9 the block slot; 10 (operand split) has slot 6
+    const int slot = L.kind == 6    ? KKT_K_SYRK_TC_PROF
+                     : L.kind == 10 ? KKT_K_TC_SPLIT_PROF
+                                    : ((L.kind == 7 || L.kind == 9) ? KKT_K_BLOCK_PROF : (L.kind == 8 ? 4 : 1 + L.kind));
     if ((e = prof_end(prof, slot, st))) return e;
   }
   return cudaGetLastError();

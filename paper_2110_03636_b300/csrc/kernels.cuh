@@ -19,9 +19,10 @@ struct FacArgs {
   T* U;
   T* Dsc;    // factored diagonal tiles of the current level's block steps (kPB x kPB each)
   DevStatus* st;
+  float* W = nullptr;   // split operand tiles of the current tensor-core launch (FP32 factor)
   // batched form: system b = blockIdx.y works on these pointers advanced by
   // b times the strides (elements; DevStatus entries for st); 0 for one system
-  int64_t bsL = 0, bsU = 0, bsD = 0, bsH = 0, bsJ = 0;
+  int64_t bsL = 0, bsU = 0, bsD = 0, bsH = 0, bsJ = 0, bsW = 0;
 };
 
 // The view of system blockIdx.y of a batched launch (identity for one system).
@@ -34,12 +35,14 @@ __device__ __forceinline__ void batch_view(FacArgs<T>& a) {
     a.Dsc += b * a.bsD;
     a.Hv += b * a.bsH;
     a.Jv += b * a.bsJ;
+    if (a.W) a.W += b * a.bsW;
     a.st += b;
   }
 }
 
 // Optional per-launch timing (profile mode): events around each launch,
 // elapsed time accumulated per kernel kind.
+constexpr int KKT_K_TC_SPLIT_PROF = 6;   // profile slot of the tensor-core operand split
 constexpr int KKT_K_SYRK_TC_PROF = 10;   // profile slot of the tensor-core SYRK
 constexpr int KKT_K_BLOCK_PROF = 11;     // profile slot of the fused block step
 struct Prof {
@@ -51,8 +54,8 @@ cudaError_t prof_begin(Prof* pr, cudaStream_t st);
 cudaError_t prof_end(Prof* pr, int kind, cudaStream_t st);
 
 struct FacLists {
-  const int4 *it_potrf, *it_trsm, *it_pupd, *it_syrk, *it_eadd, *it_syrk_tc, *it_block, *it_syrk128, *it_dstore;
-  const uint8_t* tc_maps;   // one 128-byte tensor map per tensor-core front (Plan::tc_front)
+  const int4 *it_potrf, *it_trsm, *it_pupd, *it_syrk, *it_eadd, *it_syrk_tc, *it_block, *it_syrk128, *it_dstore,
+      *it_tc_split;
   const int64_t *slot_pos, *src_ptr;
   const int32_t *srcA, *srcB;
   int64_t nslot, panel_total, u_total;
@@ -70,9 +73,11 @@ struct InvArgs {
 template <typename T>
 cudaError_t launch_tri_inv(const InvArgs<T>& a, int64_t npieces, int max_pw, cudaStream_t st, int nb = 1);
 
-// Tensor-core update tiles (tc_update.cu): items of 8 ints (Plan::it_syrk_tc).
-cudaError_t launch_tc_update(const int4* items, int64_t cnt, const uint8_t* maps, const FacArgs<float>& a,
-                             cudaStream_t st, int nb = 1);
+// Tensor-core update tiles (tc_update.cu): items of kTcItem ints
+// (Plan::it_syrk_tc), operands split beforehand by launch_tc_split
+// (Plan::it_tc_split) into a.W.
+cudaError_t launch_tc_split(const int4* items, int64_t cnt, const FacArgs<float>& a, cudaStream_t st, int nb = 1);
+cudaError_t launch_tc_update(const int4* items, int64_t cnt, const FacArgs<float>& a, cudaStream_t st, int nb = 1);
 
 template <typename T>
 cudaError_t launch_factor(const FacArgs<T>& a, const FacLists& fl, const double* dg, cudaStream_t st,

@@ -97,14 +97,46 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
   // block-step and in-panel-update items carry their front's width, rows,
   // leading dimension, first column and panel offset, so their kernels reach
   // the panel after one load instead of two dependent ones
-  // tensor-core fronts: a tensor map per front (index in P.tc_front)
-  std::vector<int32_t> map_idx(ns, -1);
-  auto map_of = [&](int32_t sn) {
-    if (map_idx[sn] < 0) {
-      map_idx[sn] = (int32_t)P.tc_front.size();
-      P.tc_front.push_back(sn);
+  // Tensor-core launches. tc_region: the split items of rows [r0, rows) x K
+  // [klo, khi) of front sn, as operand tiles from ws on (row block by row
+  // block, nch chunks each); returns the region's first tile. tc_item: the
+  // tile C = A B^T of panel rows ra and rb of that region.
+  int64_t ws = 0;
+  auto lo32 = [](int64_t v) { return (int32_t)(uint32_t)(v & 0xffffffff); };
+  auto hi32 = [](int64_t v) { return (int32_t)(v >> 32); };
+  auto tc_region = [&](int32_t sn, int32_t r0, int32_t klo, int32_t khi) {
+    const int64_t nrb = cdiv(P.snr[sn] - r0, 128), nch = cdiv(khi - klo, 32), base = ws;
+    const int64_t po = P.poff[sn];
+    for (int64_t rbi = 0; rbi < nrb; rbi++)
+      for (int64_t c0 = 0; c0 < nch; c0 += kTcSplitChunks) {
+        const int64_t dst = base + rbi * nch + c0;
+        P.it_tc_split.insert(P.it_tc_split.end(),
+                             {P.sld[sn], P.snr[sn], r0 + (int32_t)rbi * 128, klo, khi, (int32_t)c0,
+                              (int32_t)std::min(nch, c0 + kTcSplitChunks), 0, lo32(po), hi32(po), lo32(dst),
+                              hi32(dst), 0, 0, 0, 0});
+      }
+    ws += nrb * nch;
+    return base;
+  };
+  auto tc_item = [&](int32_t sn, int32_t ra, int32_t rb, int32_t r0, int64_t base, int32_t klo, int32_t khi,
+                     int32_t mode) {
+    const int64_t nch = cdiv(khi - klo, 32);
+    const int64_t ta = base + (ra - r0) / 128 * nch, tb = base + (rb - r0) / 128 * nch;
+    const int64_t out = mode ? P.poff[sn] : P.uoff[sn];
+    P.it_syrk_tc.insert(P.it_syrk_tc.end(), {lo32(ta), hi32(ta), lo32(tb), hi32(tb), (int32_t)nch, mode, ra, rb,
+                                             P.sld[sn], P.snr[sn], P.sw[sn], 0, lo32(out), hi32(out), 0, 0});
+  };
+  // the split launch (kind 10) and the tile launch (kind 6) of the items
+  // added since (o10, o6)
+  auto tc_launch = [&](int32_t kb, int64_t o10, int64_t o6) {
+    const int64_t c10 = (int64_t)P.it_tc_split.size() / kTcItem - o10;
+    const int64_t c6 = (int64_t)P.it_syrk_tc.size() / kTcItem - o6;
+    if (c6) {
+      P.launches.push_back({10, kb, o10, c10});
+      P.launches.push_back({6, kb, o6, c6});
     }
-    return map_idx[sn];
+    P.tc_ws_tiles = std::max(P.tc_ws_tiles, ws);
+    ws = 0;
   };
   // fronts at least kTcPanelMinWidth wide take the in-panel update beyond
   // each outer block on the tensor cores (narrower fronts give launches too
@@ -192,27 +224,25 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
       // end of an outer block: the columns beyond it -= L[rows, block] L[cols, block]^T,
       // K = the block's kTcPB columns, on the tensor cores (mode 1)
       if ((kb + 1) * kPB % kTcPB == 0) {
-        const int64_t o6 = (int64_t)P.it_syrk_tc.size() / 8;
+        const int64_t o6 = (int64_t)P.it_syrk_tc.size() / kTcItem, o10 = (int64_t)P.it_tc_split.size() / kTcItem;
         const int32_t oe = (kb + 1) * kPB;          // first column after the outer block
         for (int32_t s : F) {
           if (!tc_panel(s) || oe >= P.sw[s]) continue;
-          const int32_t mi = map_of(s);
+          const int64_t base = tc_region(s, oe, oe - kTcPB, oe);
           for (int32_t cs = oe; cs < P.sw[s]; cs += 128)
-            for (int32_t rs = cs; rs < P.snr[s]; rs += 128)
-              P.it_syrk_tc.insert(P.it_syrk_tc.end(), {s, rs, cs, mi, oe - kTcPB, oe, 1, 0});
+            for (int32_t rs = cs; rs < P.snr[s]; rs += 128) tc_item(s, rs, cs, oe, base, oe - kTcPB, oe, 1);
           // lower trapezoid of rows [oe, nr) x columns [oe, w), K = kTcPB
           const double cols = P.sw[s] - oe, top = P.snr[s] - oe;
           P.tc_flops += 2.0 * kTcPB * (cols * top - cols * (cols - 1) / 2);
         }
-        const int64_t c6 = (int64_t)P.it_syrk_tc.size() / 8 - o6;
-        if (c6) P.launches.push_back({6, kb, o6, c6});
+        tc_launch(kb, o10, o6);
       }
     }
     P.dsc_total = std::max(P.dsc_total, (int64_t)slot * kPB * kPB);
     const int64_t cd = (int64_t)P.it_dstore.size() / 4 - od;
     if (cd) P.launches.push_back({9, 0, od, cd});
-    const int64_t o2 = (int64_t)P.it_syrk.size() / 4, o6 = (int64_t)P.it_syrk_tc.size() / 8,
-                  o8 = (int64_t)P.it_syrk128.size() / 4;
+    const int64_t o2 = (int64_t)P.it_syrk.size() / 4, o6 = (int64_t)P.it_syrk_tc.size() / kTcItem,
+                  o8 = (int64_t)P.it_syrk128.size() / 4, o10 = (int64_t)P.it_tc_split.size() / kTcItem;
     // tensor-core tiles of the level's fronts, widest (longest K) first, so
     // the persistent kernel's round-robin hands every CTA a similar share
     std::vector<int32_t> tcf;
@@ -229,19 +259,17 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
     }
     std::stable_sort(tcf.begin(), tcf.end(), [&](int32_t x, int32_t y) { return P.sw[x] > P.sw[y]; });
     for (int32_t s : tcf) {
-      const int32_t mi = map_of(s);
       const int32_t w = P.sw[s];
       const int64_t nt = cdiv(P.snr[s] - w, 128);
       const double rbd = P.snr[s] - w;
       P.tc_flops += (double)w * rbd * (rbd + 1);   // U = -L21 L21^T, lower triangle
+      const int64_t base = tc_region(s, w, 0, w);
       for (int64_t ti = 0; ti < nt; ti++)
         for (int64_t tj = 0; tj <= ti; tj++)
-          P.it_syrk_tc.insert(P.it_syrk_tc.end(),
-                              {s, w + (int32_t)ti * 128, w + (int32_t)tj * 128, mi, 0, w, 0, 0});
+          tc_item(s, w + (int32_t)ti * 128, w + (int32_t)tj * 128, w, base, 0, w, 0);
     }
-    const int64_t c2 = (int64_t)P.it_syrk.size() / 4 - o2, c6 = (int64_t)P.it_syrk_tc.size() / 8 - o6,
-                  c8 = (int64_t)P.it_syrk128.size() / 4 - o8;
-    if (c6) P.launches.push_back({6, 0, o6, c6});
+    const int64_t c2 = (int64_t)P.it_syrk.size() / 4 - o2, c8 = (int64_t)P.it_syrk128.size() / 4 - o8;
+    tc_launch(0, o10, o6);
     if (c8) P.launches.push_back({8, 0, o8, c8});
     if (c2) P.launches.push_back({3, 0, o2, c2});
     const int64_t o4 = (int64_t)P.it_eadd.size() / 4;

@@ -51,7 +51,9 @@ constexpr int kFItem = 12;
 
 struct Launch {              // one batched kernel launch of the factorization
   int32_t kind;              // 0 potrf (diagonal tile), 1 trsm, 2 in-panel update, 3 syrk,
-                             // 4 extend-add, 5 zero update matrices, 6 tensor-core syrk
+                             // 4 extend-add, 6 tensor-core tiles, 7 fused block step,
+                             // 8 128 x 128 FP32 syrk, 9 diagonal-tile store,
+                             // 10 operand split of the next tensor-core launch
   int32_t kb;                // column block (kinds 0-2)
   int64_t off, cnt;          // range in the item array of that kind
 };
@@ -74,9 +76,15 @@ struct Plan {
   std::vector<int32_t> it_trsm;             // (s, row tile) pairs
   std::vector<int32_t> it_pupd;             // (s, row tile, col tile) triples (kFItem ints each)
   std::vector<int32_t> it_syrk;             // (s, ti, tj) triples, 64 x 64 tiles
-  std::vector<int32_t> it_syrk_tc;          // tensor-core update tiles, 8 ints each: (s, panel row of A,
-                                            // panel row of B, tensor map), (K begin, K end, mode, 0)
-  std::vector<int32_t> tc_front;            // fronts with a tensor map (index = map number)
+  std::vector<int32_t> it_syrk_tc;          // tensor-core update tiles, kTcItem ints each: (A operand tile
+                                            // lo, hi, B operand tile lo, hi), (chunks, mode, panel row of
+                                            // A, panel row of B), (ld, rows, width, 0), (output offset
+                                            // lo, hi, 0, 0)
+  std::vector<int32_t> it_tc_split;         // operand splits before each tensor-core launch, kTcItem
+                                            // ints each: (ld, rows, first row, K begin), (K end, first
+                                            // chunk, end chunk, 0), (panel offset lo, hi, first operand
+                                            // tile lo, hi), 0 x 4
+  int64_t tc_ws_tiles = 0;                  // operand tiles of the largest tensor-core launch
   double tc_flops = 0;                      // algorithmic flops of the tensor-core tiles per factorization
   std::vector<int32_t> it_block;            // (s, row tile, slot) per fused block step (kFItem ints each)
   std::vector<int32_t> it_syrk128;          // (s, ti, tj), 128 x 128 FP32 register-tiled SYRK
@@ -149,14 +157,19 @@ inline int64_t packed_inv_size(int64_t pw) {
 }
 
 // tc_syrk: fronts with rb >= kTcMinRows and at least kTcMinWidth columns get
-// 128 x 128 tensor-core SYRK tiles; their panels are read through tensor maps
-// with boxes of kTcBoxRows rows x 32 columns; the persistent kernel runs at
-// most kTcGrid CTAs (one per SM)
+// 128 x 128 tensor-core SYRK tiles; the persistent kernel runs at most
+// kTcGrid CTAs (one per SM). Before each tensor-core launch a split launch
+// writes the launch's operands, rows [r0, rows) x K [K begin, K end) of each
+// front, as operand tiles (kTcTileFloats floats each, in the layout the MMA
+// reads) into a workspace of tc_ws_tiles tiles; a tile item names its A and
+// B operand tiles and carries its front's geometry (kTcItem ints)
 constexpr int kTcMinRows = 128;
 constexpr int kTcPB = 128;        // outer column block of the tensor-core in-panel update
 constexpr int kTcPanelMinWidth = 1024;   // narrowest front that takes it
 constexpr int kTcMinWidth = 32;
-constexpr int kTcBoxRows = 132;
+constexpr int kTcItem = 16;
+constexpr int kTcTileFloats = 2 * 128 * 32;   // one operand tile: TF32 hi and lo parts of 128 rows x 32 K
+constexpr int kTcSplitChunks = 16;            // chunks of one row block per split item
 constexpr int kTcGrid = 148;
 // f32 (FP32 factor): fronts with rb >= kBigRows get 128 x 128 register-tiled SYRK
 // tiles, and each block step fuses POTRF into the TRSM launch

@@ -13,24 +13,32 @@
 // "Recovering single precision accuracy from Tensor Cores while surpassing
 // the FP32 theoretical peak performance" (2022). The tensor core accumulates
 // in FP32 without rounding to nearest, so its accumulator in tensor memory
-// only ever holds kGroup K chunks: the epilogue warps drain it into FP32
-// registers after each group and sum the groups with round-to-nearest adds,
-// so the accumulation error grows with the number of groups the way an FMA
-// loop's does, not with K.
+// only ever holds kGroup K chunks: the epilogue warps drain it after each
+// group and sum the groups with round-to-nearest FP32 adds, so the
+// accumulation error grows with the number of groups the way an FMA loop's
+// does, not with K.
 //
-// Pipeline (one CTA per SM, persistent over the launch's tiles):
-//   warp 8      TMA producer: 2-D boxes of 132 rows x 32 columns of the
-//               panel (the row start rounded down to a multiple of 4, as the
-//               16-byte rule for the innermost TMA coordinate requires) into
-//               a ring of kRaw stages;
-//   warps 4-7   converters: raw FP32 -> hi/lo TF32 tiles in the K-major
-//               core-matrix layout the MMA reads (8 rows x 16 bytes per core
-//               matrix, no swizzle), ring of kOp stages;
-//   warp 9      MMA issuer (one thread) and tensor-memory owner: 3 MMAs per
-//               8-wide K step into one of two 128 x 128 FP32 accumulators;
-//   warps 0-3   drain + epilogue: tcgen05.ld of the accumulator (warp w
-//               reads lanes 32w..32w+31 = tile rows), FP32 sums in
-//               registers, stores of the finished tile.
+// Two launches per tensor-core step:
+//   k_tc_split   splits the step's operands once: each 128-row block x 32-K
+//                chunk of a front's rows becomes one operand tile (hi then lo,
+//                16 KB each) in the K-major core-matrix layout the MMA reads
+//                (8 rows x 16 bytes per core matrix, no swizzle), in a global
+//                workspace. HBM-bound: 4 bytes read, 8 written per value.
+//   k_tc_update  one CTA per SM, persistent over the step's tiles:
+//     warp 4     copies the A and B operand tiles of each K chunk into a ring
+//                of kOp shared-memory stages (cp.async.bulk, mbarrier
+//                transaction counts);
+//     warp 5     MMA issuer (one thread) and tensor-memory owner: 3 MMAs per
+//                8-wide K step into one of two 128 x 128 FP32 accumulators;
+//     warps 0-3  drain + epilogue: tcgen05.ld of the accumulator (warp w
+//                reads lanes 32w..32w+31 = tile rows), round-to-nearest adds
+//                into the tile's running sums in tensor memory, and stores of
+//                the finished tile.
+// Splitting in the tile kernel itself would read every raw value from and
+// write its two parts to shared memory once per tile that uses it, and
+// shared-memory bandwidth (the bulk copies' writes and the MMAs' operand
+// reads) is what bounds the tile kernel; split once, an operand is only
+// copied in and read by the MMAs.
 // Every wait is bounded; a wait that runs out sets DevStatus::abort, every
 // role leaves its loop, copies and MMAs in flight are waited for (bounded)
 // and the tensor memory is released before the CTA exits.
@@ -47,21 +55,20 @@
 namespace kkt {
 namespace tcu {
 
-constexpr int KC = 32;                        // K per chunk (one TMA box)
-constexpr int BOXR = kTcBoxRows;              // rows per TMA box: 128 + up to 3 of start alignment
-constexpr uint32_t RAW = BOXR * KC * 4;       // bytes of one raw box (16896)
-constexpr uint32_t OPT = 128 * KC * 4;        // bytes of one split operand tile (16384)
-constexpr int kRaw = 2, kOp = 2;              // ring depths
+constexpr int KC = 32;                        // K per chunk
+constexpr uint32_t OPT = 128 * KC * 4;        // bytes of one split part (hi or lo) of an operand tile
+constexpr uint32_t TILE = 2 * OPT;            // bytes of an operand tile: hi, then lo
+static_assert(TILE == kTcTileFloats * 4, "operand tile size");
+constexpr int kOp = 3;                        // ring depth (stages of A and B operand tiles)
 constexpr int kGroup = 2;                     // K chunks accumulated in tensor memory per drain
 constexpr uint32_t LBO = 128;                 // bytes between core matrices along K
 constexpr uint32_t SBO = (KC / 4) * 128;      // bytes between 8-row groups
-constexpr int kThreads = 320;
-constexpr uint32_t kSmem = kRaw * 2 * RAW + kOp * 4 * OPT + 1024;   // + barriers, slack
+constexpr int kThreads = 192;
+constexpr uint32_t kSmem = kOp * 2 * TILE + 1024;   // + barriers, slack
 
 // barrier indices
-constexpr int B_RAW_FULL = 0, B_RAW_EMPTY = kRaw, B_OP_FULL = 2 * kRaw, B_OP_EMPTY = 2 * kRaw + kOp,
-              B_ACC_FULL = 2 * kRaw + 2 * kOp, B_ACC_EMPTY = B_ACC_FULL + 2, B_DONE = B_ACC_EMPTY + 2,
-              kBars = B_DONE + 1;
+constexpr int B_OP_FULL = 0, B_OP_EMPTY = kOp, B_ACC_FULL = 2 * kOp, B_ACC_EMPTY = B_ACC_FULL + 2,
+              B_DONE = B_ACC_EMPTY + 2, kBars = B_DONE + 1;
 static_assert(kBars * 8 <= 1024, "barriers fit the reserved shared memory");
 
 __device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -71,9 +78,6 @@ __device__ __forceinline__ void bar_init(unsigned long long* b, uint32_t count) 
 }
 __device__ __forceinline__ void bar_arrive(unsigned long long* b) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(b)) : "memory");
-}
-__device__ __forceinline__ void bar_expect_tx(unsigned long long* b, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(b)), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ bool bar_test(unsigned long long* b, uint32_t parity) {
   uint32_t ok;
@@ -108,20 +112,37 @@ __device__ __forceinline__ void bar_drain(unsigned long long* b, uint32_t parity
   }
 }
 
-// 3-D tiled TMA load: (x = panel row, y = panel column, z = system of a batch)
-__device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int x, int y, int z, unsigned long long* b) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
-          saddr(dst)),
-      "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(saddr(b))
-      : "memory");
-}
-
 __device__ __forceinline__ float tf32_rna(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
   return __uint_as_float(r);
 }
+
+// One panel row's KC values of a K chunk (column-major panel: consecutive
+// lanes read consecutive rows, so each of the KC loads is one coalesced
+// 128-byte line per warp); the nv valid columns, zeros beyond.
+__device__ __forceinline__ void ld_row(float (&v)[KC], const float* p, int64_t ld, int nv) {
+#pragma unroll
+  for (int k = 0; k < KC; k++) v[k] = k < nv ? __ldg(p + k * ld) : 0.f;
+}
+
+__device__ __forceinline__ int64_t i64_of(int lo, int hi) { return (int64_t)(uint32_t)lo | ((int64_t)hi << 32); }
+
+// bulk copy global -> shared (16-byte aligned, size a multiple of 16),
+// completion counted on the mbarrier's transaction count
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, unsigned long long* b) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   saddr(dst)),
+               "l"(src), "r"(bytes), "r"(saddr(b))
+               : "memory");
+}
+__device__ __forceinline__ void bar_expect_tx(unsigned long long* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(b)), "r"(bytes) : "memory");
+}
+
+// split one row's KC values into TF32 hi/lo parts and store them at row i of
+// the hi and lo operand tiles (K-major core-matrix layout)
+__device__ __forceinline__ void split_store(const float (&xv)[KC], unsigned char* hi, unsigned char* lo, int i);
 
 // shared-memory matrix descriptor: K-major, no swizzle, core matrices of 8
 // rows x 16 bytes, LBO between core matrices along K, SBO between 8-row groups
@@ -135,10 +156,50 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
 __device__ __forceinline__ uint32_t koff(int i, int k) {
   return (uint32_t)((i >> 3) * SBO + (k >> 2) * LBO + (i & 7) * 16 + (k & 3) * 4);
 }
+__device__ __forceinline__ void split_store(const float (&xv)[KC], unsigned char* hi, unsigned char* lo, int i) {
+#pragma unroll
+  for (int q = 0; q < KC / 4; q++) {
+    float4 h, l;
+    float* hp = &h.x;
+    float* lp = &l.x;
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+      const float x = xv[4 * q + r];
+      const float xh = tf32_rna(x);
+      hp[r] = xh;
+      lp[r] = tf32_rna(x - xh);
+    }
+    const uint32_t off = koff(i, 4 * q);
+    *(float4*)(hi + off) = h;
+    *(float4*)(lo + off) = l;
+  }
+}
 __device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+// 32 consecutive tensor-memory columns of this warp's 32 lanes (one
+// register per column per thread)
+__device__ __forceinline__ void tmem_ld32(uint32_t (&r)[32], uint32_t ta) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(ta));
+}
+__device__ __forceinline__ void tmem_st32(uint32_t ta, const uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(ta),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]),
+      "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]),
+      "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+      : "memory");
 }
 __device__ __forceinline__ void mma_commit(unsigned long long* b) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(b))
@@ -147,17 +208,44 @@ __device__ __forceinline__ void mma_commit(unsigned long long* b) {
 
 }  // namespace tcu
 
-// Item of a tensor-core update launch (two int4): (s, row of A, row of B,
-// tensor map), (first K column, end K column, mode, 0). Rows are panel rows
-// of front s; A = B for a diagonal tile.
+// Split item (kTcItem ints = four int4): (ld, rows of the front, first row
+// of the row block, K begin), (K end, first chunk, end chunk, 0), (panel
+// offset lo, hi, first operand tile lo, hi). One CTA of 128 threads per item;
+// thread i splits row i of the block, chunk by chunk, into operand tiles
+// first tile + 0, 1, ... (rows past the front and columns past K end are
+// zeros).
+__global__ void __launch_bounds__(128) k_tc_split(const int4* __restrict__ items, FacArgs<float> a) {
+  using namespace tcu;
+  batch_view(a);
+  const int4* q = items + (kTcItem / 4) * (int64_t)blockIdx.x;
+  const int4 q0 = q[0], q1 = q[1], q2 = q[2];
+  const int i = threadIdx.x;
+  const int64_t ld = q0.x;
+  const int nr = q0.y, row = q0.z + i, klo = q0.w, khi = q1.x, c0 = q1.y, c1 = q1.z;
+  const float* P = a.L + i64_of(q2.x, q2.y) + row;
+  unsigned char* dst = (unsigned char*)(a.W + i64_of(q2.z, q2.w) * kTcTileFloats);
+  for (int c = c0; c < c1; c++) {
+    const int k0 = klo + c * KC;
+    const int nv = row < nr ? min(KC, khi - k0) : 0;
+    float v[KC];
+    ld_row(v, nv > 0 ? P + (int64_t)k0 * ld : P, ld, nv);
+    unsigned char* o = dst + (size_t)(c - c0) * TILE;
+    split_store(v, o, o + OPT, i);
+  }
+}
+
+// Tile item (kTcItem ints): (A operand tile lo, hi, B operand tile lo, hi),
+// (chunks, mode, panel row of A, panel row of B), (ld, rows, width, 0),
+// (output offset lo, hi, 0, 0): chunk c of A is operand tile A + c; the
+// output is U_s (mode 0, offset uoff[s]) or the panel (mode 1, poff[s]). A = B
+// (the same operand tiles) for a diagonal tile.
 __global__ void __launch_bounds__(tcu::kThreads, 1)
-    k_tc_update(const int4* __restrict__ items, int64_t nitems, const uint8_t* __restrict__ maps, FacArgs<float> a) {
+    k_tc_update(const int4* __restrict__ items, int64_t nitems, FacArgs<float> a) {
   using namespace tcu;
   batch_view(a);                                         // system blockIdx.y of a batched launch
   extern __shared__ __align__(1024) unsigned char sm[];
-  unsigned char* raw = sm;                               // [kRaw][A, B][RAW]
-  unsigned char* opb = sm + kRaw * 2 * RAW;              // [kOp][A hi, A lo, B hi, B lo][OPT]
-  unsigned long long* bar = (unsigned long long*)(opb + kOp * 4 * OPT);
+  unsigned char* opb = sm;                               // [kOp][A tile, B tile][TILE]
+  unsigned long long* bar = (unsigned long long*)(opb + kOp * 2 * TILE);
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   volatile int* abrt = &abort_flag;
@@ -165,12 +253,8 @@ __global__ void __launch_bounds__(tcu::kThreads, 1)
 
   if (tid == 0) {
     abort_flag = 0;
-    for (int q = 0; q < kRaw; q++) {
-      bar_init(&bar[B_RAW_FULL + q], 1);
-      bar_init(&bar[B_RAW_EMPTY + q], 4);
-    }
     for (int q = 0; q < kOp; q++) {
-      bar_init(&bar[B_OP_FULL + q], 4);
+      bar_init(&bar[B_OP_FULL + q], 1);
       bar_init(&bar[B_OP_EMPTY + q], 1);
     }
     for (int q = 0; q < 2; q++) {
@@ -180,9 +264,9 @@ __global__ void __launch_bounds__(tcu::kThreads, 1)
     bar_init(&bar[B_DONE], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 9) {
-    // two 128-column FP32 accumulators
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(saddr(&tmem_base)));
+  if (warp == 5) {
+    // two 128-column FP32 accumulators and the tile's 128 running sums
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(saddr(&tmem_base)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -190,91 +274,32 @@ __global__ void __launch_bounds__(tcu::kThreads, 1)
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
 
-  if (warp == 8) {
-    // ------------------------------------------------ TMA producer
+  if (warp == 4) {
+    // ------------------------------------------------ operand copies
     if (lane == 0) {
       uint32_t rc = 0;
       bool ok = true;
       for (int64_t t = blockIdx.x; t < nitems && ok; t += gridDim.x) {
-        const int4 i0 = items[2 * t], i1 = items[2 * t + 1];
-        const void* mp = maps + (size_t)i0.w * 128;
-        const bool diag = i0.y == i0.z;
-        const int xa = i0.y & ~3, xb = i0.z & ~3;
-        const int nk = (i1.y - i1.x + KC - 1) / KC;
-        for (int c = 0; c < nk; c++) {
-          const uint32_t slot = rc % kRaw, round = rc / kRaw;
-          if (!(ok = bar_wait(&bar[B_RAW_EMPTY + slot], (round & 1) ^ 1, abrt, a.st))) break;
-          unsigned char* dst = raw + slot * 2 * RAW;
-          bar_expect_tx(&bar[B_RAW_FULL + slot], diag ? RAW : 2 * RAW);
-          tma_load_3d(dst, mp, xa, i1.x + c * KC, (int)blockIdx.y, &bar[B_RAW_FULL + slot]);
-          if (!diag) tma_load_3d(dst + RAW, mp, xb, i1.x + c * KC, (int)blockIdx.y, &bar[B_RAW_FULL + slot]);
+        const int4 q0 = items[(kTcItem / 4) * t], q1 = items[(kTcItem / 4) * t + 1];
+        const int64_t ta = i64_of(q0.x, q0.y), tb = i64_of(q0.z, q0.w);
+        const bool diag = ta == tb;
+        for (int c = 0; c < q1.x; c++) {
+          const uint32_t slot = rc % kOp, round = rc / kOp;
+          if (!(ok = bar_wait(&bar[B_OP_EMPTY + slot], (round & 1) ^ 1, abrt, a.st))) break;
+          unsigned char* dst = opb + slot * 2 * TILE;
+          bar_expect_tx(&bar[B_OP_FULL + slot], diag ? TILE : 2 * TILE);
+          bulk_load(dst, a.W + (ta + c) * kTcTileFloats, TILE, &bar[B_OP_FULL + slot]);
+          if (!diag) bulk_load(dst + TILE, a.W + (tb + c) * kTcTileFloats, TILE, &bar[B_OP_FULL + slot]);
           rc++;
         }
       }
       if (!ok) {
         // let the copies already issued land before the CTA exits
-        for (uint32_t q = rc > (uint32_t)kRaw ? rc - kRaw : 0; q < rc; q++)
-          bar_drain(&bar[B_RAW_FULL + q % kRaw], (q / kRaw) & 1);
+        for (uint32_t q = rc > (uint32_t)kOp ? rc - kOp : 0; q < rc; q++)
+          bar_drain(&bar[B_OP_FULL + q % kOp], (q / kOp) & 1);
       }
     }
-  } else if (warp >= 4 && warp < 8) {
-    // ------------------------------------------------ converters
-    const int i = tid - 128;                 // tile row
-    uint32_t rc = 0;
-    bool ok = true;
-    for (int64_t t = blockIdx.x; t < nitems && ok; t += gridDim.x) {
-      const int4 i0 = items[2 * t], i1 = items[2 * t + 1];
-      const bool diag = i0.y == i0.z;
-      const int sa = i0.y & 3, sb = i0.z & 3;
-      const int nk = (i1.y - i1.x + KC - 1) / KC;
-      for (int c = 0; c < nk; c++) {
-        const uint32_t rs = rc % kRaw, rr = rc / kRaw, os = rc % kOp, orr = rc / kOp;
-        bool w = true;
-        if (lane == 0)
-          w = bar_wait(&bar[B_RAW_FULL + rs], rr & 1, abrt, a.st) &&
-              bar_wait(&bar[B_OP_EMPTY + os], (orr & 1) ^ 1, abrt, a.st);
-        if (!(ok = __shfl_sync(0xffffffffu, w, 0))) break;
-        const float* ra = (const float*)(raw + rs * 2 * RAW);
-        unsigned char* o = opb + os * 4 * OPT;
-#pragma unroll
-        for (int half = 0; half < 2; half++) {
-          if (half == 1 && diag) break;
-          const float* src = ra + (half ? BOXR * KC : 0) + (half ? sb : sa) + i;
-          unsigned char* hi = o + (half ? 2 : 0) * OPT;
-          unsigned char* lo = hi + OPT;
-          // all 32 loads of the row first: the stores below go to other
-          // shared-memory tiles, but the compiler cannot tell, so loads
-          // interleaved with them would each wait out their latency
-          float xv[KC];
-#pragma unroll
-          for (int k = 0; k < KC; k++) xv[k] = src[k * BOXR];
-#pragma unroll
-          for (int q = 0; q < KC / 4; q++) {
-            float4 h, l;
-            float* hp = &h.x;
-            float* lp = &l.x;
-#pragma unroll
-            for (int r = 0; r < 4; r++) {
-              const float x = xv[4 * q + r];
-              const float xh = tf32_rna(x);
-              hp[r] = xh;
-              lp[r] = tf32_rna(x - xh);
-            }
-            const uint32_t off = koff(i, 4 * q);
-            *(float4*)(hi + off) = h;
-            *(float4*)(lo + off) = l;
-          }
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncwarp();
-        if (lane == 0) {
-          bar_arrive(&bar[B_RAW_EMPTY + rs]);
-          bar_arrive(&bar[B_OP_FULL + os]);
-        }
-        rc++;
-      }
-    }
-  } else if (warp == 9) {
+  } else if (warp == 5) {
     // ------------------------------------------------ MMA issuer
     if (lane == 0) {
       // D = F32, A = B = TF32, both K-major, N = 128, M = 128
@@ -282,9 +307,9 @@ __global__ void __launch_bounds__(tcu::kThreads, 1)
       uint32_t oc = 0, gc = 0;
       bool ok = true, issued = false;
       for (int64_t t = blockIdx.x; t < nitems && ok; t += gridDim.x) {
-        const int4 i0 = items[2 * t], i1 = items[2 * t + 1];
-        const bool diag = i0.y == i0.z;
-        const int nk = (i1.y - i1.x + KC - 1) / KC;
+        const int4 q0 = items[(kTcItem / 4) * t], q1 = items[(kTcItem / 4) * t + 1];
+        const bool diag = q0.x == q0.z && q0.y == q0.w;
+        const int nk = q1.x;
         for (int g0 = 0; g0 < nk && ok; g0 += kGroup) {
           const uint32_t b = gc & 1;
           if (!(ok = bar_wait(&bar[B_ACC_EMPTY + b], ((gc >> 1) & 1) ^ 1, abrt, a.st))) break;
@@ -295,8 +320,8 @@ __global__ void __launch_bounds__(tcu::kThreads, 1)
             const uint32_t os = oc % kOp, orr = oc / kOp;
             if (!(ok = bar_wait(&bar[B_OP_FULL + os], orr & 1, abrt, a.st))) break;
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t base = saddr(opb + os * 4 * OPT);
-            const uint32_t ah = base, al = base + OPT, bh = diag ? ah : base + 2 * OPT, bl = diag ? al : base + 3 * OPT;
+            const uint32_t base = saddr(opb + os * 2 * TILE);
+            const uint32_t ah = base, al = base + OPT, bh = diag ? ah : base + TILE, bl = diag ? al : base + TILE + OPT;
 #pragma unroll
             for (int kk = 0; kk < KC / 8; kk++) {
               const uint32_t ko = kk * 2 * LBO;
@@ -321,87 +346,89 @@ __global__ void __launch_bounds__(tcu::kThreads, 1)
     }
   } else {
     // ------------------------------------------------ drain + epilogue (warps 0-3)
+    // The tile's running sums live in tensor memory (columns 256..383): each
+    // drained group is added to them with round-to-nearest FP32 adds, 32
+    // columns at a time, so a thread holds 64 values, not the row's 128 sums.
     const int i = 32 * warp + lane;          // tile row = tensor-memory lane
+    const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
+    const uint32_t run = tmem + lane_off + 256;
     uint32_t gc = 0;
     bool ok = true;
     for (int64_t t = blockIdx.x; t < nitems && ok; t += gridDim.x) {
-      const int4 i0 = items[2 * t], i1 = items[2 * t + 1];
-      const int nk = (i1.y - i1.x + KC - 1) / KC;
-      if (i1.z != 0) {
+      const int4* q = items + (kTcItem / 4) * t;
+      const int4 q1 = q[1], q2 = q[2], q3 = q[3];
+      const int nk = q1.x, mode = q1.y, ra = q1.z, rb = q1.w;
+      const int ld = q2.x, nr = q2.y, w = q2.z;
+      const int64_t out = i64_of(q3.x, q3.y);
+      if (mode != 0) {
         // in-panel tile: pull this row's 128 outputs into L2 while the MMAs
         // run, so the read-modify-write below waits on L2, not on HBM
-        const int s = i0.x;
-        const int ld = a.sld[s], nr = a.snr[s], w = a.sw[s];
-        const int row = i0.y + i;
-        const float* P = a.L + a.poff[s] + row;
+        const int row = ra + i;
+        const float* P = a.L + out + row;
         if (row < nr)
-          for (int j = 0; j < 128 && i0.z + j < w; j++)
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(P + (int64_t)(i0.z + j) * ld));
+          for (int j = 0; j < 128 && rb + j < w; j++)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(P + (int64_t)(rb + j) * ld));
       }
-      float acc[128];
-#pragma unroll
-      for (int j = 0; j < 128; j++) acc[j] = 0.f;
       for (int g0 = 0; g0 < nk; g0 += kGroup) {
         const uint32_t b = gc & 1;
-        bool w = true;
-        if (lane == 0) w = bar_wait(&bar[B_ACC_FULL + b], (gc >> 1) & 1, abrt, a.st);
-        if (!(ok = __shfl_sync(0xffffffffu, w, 0))) break;
+        bool got = true;
+        if (lane == 0) got = bar_wait(&bar[B_ACC_FULL + b], (gc >> 1) & 1, abrt, a.st);
+        if (!(ok = __shfl_sync(0xffffffffu, got, 0))) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + b * 128;
-#pragma unroll
+        const uint32_t ta = tmem + lane_off + b * 128;
+#pragma unroll 1
         for (int c4 = 0; c4 < 4; c4++) {
-          uint32_t r[32];
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-              "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-                "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-                "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-              : "r"(ta + (uint32_t)(c4 * 32)));
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          uint32_t r[32], s[32];
+          tmem_ld32(r, ta + (uint32_t)(c4 * 32));
+          if (g0 > 0) {
+            tmem_ld32(s, run + (uint32_t)(c4 * 32));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-          for (int j = 0; j < 32; j++) acc[c4 * 32 + j] += __uint_as_float(r[j]);
+            for (int j = 0; j < 32; j++) r[j] = __float_as_uint(__uint_as_float(s[j]) + __uint_as_float(r[j]));
+          } else {
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          }
+          tmem_st32(run + (uint32_t)(c4 * 32), r);
         }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncwarp();
         if (lane == 0) bar_arrive(&bar[B_ACC_EMPTY + b]);
         gc++;
       }
       if (!ok) break;
-      // store the finished tile
-      const int s = i0.x;
-      const int w = a.sw[s], nr = a.snr[s];
-      if (i1.z == 0) {
-        const int rb = nr - w;
-        const int gi = i0.y - w + i, gj0 = i0.z - w;
-        float* U = a.U + a.uoff[s];
-        if (gi < rb) {
+      // store the finished tile, 32 columns at a time
+#pragma unroll 1
+      for (int c4 = 0; c4 < 4; c4++) {
+        uint32_t r[32];
+        tmem_ld32(r, run + (uint32_t)(c4 * 32));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (mode == 0) {
+          const int rbk = nr - w;
+          const int gi = ra - w + i, gj0 = rb - w + c4 * 32;
+          float* U = a.U + out;
+          if (gi < rbk) {
 #pragma unroll
-          for (int j = 0; j < 128; j++) {
-            const int gj = gj0 + j;
-            if (gj < rb && gi >= gj) U[(int64_t)gi + (int64_t)gj * rb] = -acc[j];
+            for (int j = 0; j < 32; j++) {
+              const int gj = gj0 + j;
+              if (gj < rbk && gi >= gj) U[(int64_t)gi + (int64_t)gj * rbk] = -__uint_as_float(r[j]);
+            }
           }
-        }
-      } else {
-        // read-modify-write in batches of 32 independent loads
-        const int ld = a.sld[s];
-        const int row = i0.y + i, col0 = i0.z;
-        float* __restrict__ P = a.L + a.poff[s] + row;
-        if (row < nr) {
-#pragma unroll
-          for (int c4 = 0; c4 < 4; c4++) {
+        } else {
+          // read-modify-write: 32 independent loads, then the stores
+          const int row = ra + i, col0 = rb + c4 * 32;
+          float* __restrict__ P = a.L + out + row;
+          if (row < nr) {
             float v[32];
 #pragma unroll
             for (int j = 0; j < 32; j++) {
-              const int col = col0 + c4 * 32 + j;
+              const int col = col0 + j;
               v[j] = (col < w && row >= col) ? P[(int64_t)col * ld] : 0.f;
             }
 #pragma unroll
             for (int j = 0; j < 32; j++) {
-              const int col = col0 + c4 * 32 + j;
-              if (col < w && row >= col) P[(int64_t)col * ld] = v[j] - acc[c4 * 32 + j];
+              const int col = col0 + j;
+              if (col < w && row >= col) P[(int64_t)col * ld] = v[j] - __uint_as_float(r[j]);
             }
           }
         }
@@ -411,11 +438,16 @@ __global__ void __launch_bounds__(tcu::kThreads, 1)
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
-  if (warp == 9) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
+  if (warp == 5) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
 }
 
-cudaError_t launch_tc_update(const int4* items, int64_t cnt, const uint8_t* maps, const FacArgs<float>& a,
-                             cudaStream_t st, int nb) {
+cudaError_t launch_tc_split(const int4* items, int64_t cnt, const FacArgs<float>& a, cudaStream_t st, int nb) {
+  if (cnt <= 0) return cudaSuccess;
+  k_tc_split<<<dim3((unsigned)cnt, (unsigned)nb), 128, 0, st>>>(items, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_update(const int4* items, int64_t cnt, const FacArgs<float>& a, cudaStream_t st, int nb) {
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_tc_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tcu::kSmem);
@@ -426,7 +458,7 @@ cudaError_t launch_tc_update(const int4* items, int64_t cnt, const uint8_t* maps
   // round-robin over its gridDim.x CTAs)
   const int64_t per = std::max<int64_t>(1, kTcGrid / nb);
   const int64_t grid = cnt < per ? cnt : per;
-  k_tc_update<<<dim3((unsigned)grid, (unsigned)nb), tcu::kThreads, tcu::kSmem, st>>>(items, cnt, maps, a);
+  k_tc_update<<<dim3((unsigned)grid, (unsigned)nb), tcu::kThreads, tcu::kSmem, st>>>(items, cnt, a);
   return cudaGetLastError();
 }
 
