@@ -89,11 +89,12 @@ typedef struct kkt_options {
   int32_t nd_leaf;     /* nested dissection stops at components of at most this many
                           vertices (ordered naturally); default 64 */
   int32_t tensor_cores;/* KKT_MIXED: 1 (default) = fronts with >= 128 update rows and >= 32
-                          columns take their update-matrix product (SYRK) on the tcgen05
-                          tensor cores: operands split into two TF32 parts, three partial
-                          products, FP32 accumulation in tensor memory drained into FP32
-                          registers every 64 K and summed there with round-to-nearest;
-                          0 = FP32 FMA units only */
+                          columns take their update-matrix product (SYRK), and fronts at
+                          least tc_panel_min columns wide the in-panel update beyond each
+                          128-column outer block, on the tcgen05 tensor cores: operands
+                          split once per step into two TF32 parts, three partial products,
+                          FP32 accumulation in tensor memory drained every 64 K and summed
+                          with round-to-nearest adds; 0 = FP32 FMA units only */
   int32_t solve_ctas;  /* resident solve-kernel CTAs per SM, 2..4 (0 = 2); the grid is this
                           many per SM or fewer if shared memory does not allow it */
   int32_t solve_ent;   /* L entries staged per triangular-solve work item, 2048..32768
@@ -126,6 +127,10 @@ typedef struct kkt_options {
                           k >= 1: at most k SMs' worth of its CTAs, so that several handles'
                           solves (one per stream, e.g. the request server's slots) can be
                           resident at once */
+  int32_t tc_panel_min;/* narrowest front (columns) whose in-panel updates beyond each
+                          128-column outer block run on the tensor cores (tensor_cores = 1):
+                          0 = default 1024, else >= 128; narrower fronts keep them on the
+                          FMA units (each such step is a launch of its own) */
 } kkt_options;
 
 /* Kernel kinds reported by kkt_get_profile. Kinds a plan does not launch

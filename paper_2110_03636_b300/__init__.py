@@ -38,7 +38,7 @@ class kkt_options(C.Structure):
                 ("spin_cycles", C.c_int64), ("profile", C.c_int32), ("nd_leaf", C.c_int32),
                 ("tensor_cores", C.c_int32), ("solve_ctas", C.c_int32), ("solve_ent", C.c_int32),
                 ("refine", C.c_int32), ("ruiz_iters", C.c_int32),
-                ("krylov", C.c_int32), ("solve_sms", C.c_int32)]
+                ("krylov", C.c_int32), ("solve_sms", C.c_int32), ("tc_panel_min", C.c_int32)]
 
 
 class kkt_info(C.Structure):

@@ -245,6 +245,7 @@ void kkt_default_options(kkt_options* o) {
   o->ruiz_iters = 0;
   o->krylov = 0;
   o->solve_sms = 0;
+  o->tc_panel_min = 0;
 }
 
 const char* kkt_status_string(kkt_status s) {
@@ -303,6 +304,7 @@ static kkt_status analyse_host_impl(int64_t n, int64_t m, const int64_t* Hp, con
   if ((o.solve_w != 0 && (o.solve_w < 32 || o.solve_w > 256)) || o.relax_den <= 0 || o.precision < 0 ||
       o.precision > 1 || o.solve_ctas < 0 || o.solve_ctas == 1 || o.solve_ctas > 4 || o.refine < 0 ||
       o.refine > 2 || o.ruiz_iters < 0 || o.ruiz_iters > 100 || o.krylov < 0 || o.krylov > 2 || o.solve_sms < 0 ||
+      (o.tc_panel_min != 0 && o.tc_panel_min < 128) ||
       (o.krylov != 0 && o.precision != KKT_FP64) ||
       (o.solve_ent != 0 && (o.solve_ent < 2048 || o.solve_ent > 32768))) {
     delete h;
@@ -340,7 +342,8 @@ static kkt_status analyse_host_impl(int64_t n, int64_t m, const int64_t* Hp, con
   const int ent = o.solve_ent > 0 ? o.solve_ent : (f64o ? 8192 : 16384);
   // the triangle inversion holds a piece's sw x sw triangle in shared memory
   if ((size_t)sw * sw * (f64o ? 8 : 4) > (size_t)200 * 1024) { delete h; return KKT_ERR_INVALID; }
-  if (build_plan(h->S, Hp, Hi, Jp, Ji, sw, ent, ent, !f64o && o.tensor_cores, !f64o, h->P) != 0) {
+  if (build_plan(h->S, Hp, Hi, Jp, Ji, sw, ent, ent, !f64o && o.tensor_cores, !f64o,
+                 o.tc_panel_min ? o.tc_panel_min : kTcPanelMinWidth, h->P) != 0) {
     delete h;
     return KKT_ERR_INVALID;
   }

@@ -9,7 +9,8 @@ namespace kkt {
 static inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const int64_t* Jp,
-               const int32_t* Ji, int32_t solve_w, int32_t ent, int32_t ent0, bool tc_syrk, bool f32, Plan& P) {
+               const int32_t* Ji, int32_t solve_w, int32_t ent, int32_t ent0, bool tc_syrk, bool f32,
+               int32_t tc_panel_min, Plan& P) {
   P = Plan();
   const int64_t n = S.n, m = S.m, ns = S.ns;
   P.n = n; P.m = m; P.ns = ns;
@@ -141,7 +142,7 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
   // fronts at least kTcPanelMinWidth wide take the in-panel update beyond
   // each outer block on the tensor cores (narrower fronts give launches too
   // small to pay for the persistent kernel's start)
-  auto tc_panel = [&](int32_t sn) { return tc_syrk && P.sw[sn] >= kTcPanelMinWidth; };
+  auto tc_panel = [&](int32_t sn) { return tc_syrk && P.sw[sn] >= tc_panel_min; };
   auto push_fitem = [&](std::vector<int32_t>& v, int32_t sn, int32_t x, int32_t y) {
     const int64_t po = P.poff[sn];
     v.insert(v.end(), {sn, x, y, 0, P.sw[sn], P.snr[sn], P.sld[sn], P.sfirst[sn],

@@ -165,7 +165,7 @@ inline int64_t packed_inv_size(int64_t pw) {
 // B operand tiles and carries its front's geometry (kTcItem ints)
 constexpr int kTcMinRows = 128;
 constexpr int kTcPB = 128;        // outer column block of the tensor-core in-panel update
-constexpr int kTcPanelMinWidth = 1024;   // narrowest front that takes it
+constexpr int kTcPanelMinWidth = 1024;   // narrowest front that takes it (default of opt.tc_panel_min)
 constexpr int kTcMinWidth = 32;
 constexpr int kTcItem = 16;
 constexpr int kTcTileFloats = 2 * 128 * 32;   // one operand tile: TF32 hi and lo parts of 128 rows x 32 K
@@ -175,6 +175,7 @@ constexpr int kTcGrid = 148;
 // tiles, and each block step fuses POTRF into the TRSM launch
 constexpr int kBigRows = 128;
 int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const int64_t* Jp,
-               const int32_t* Ji, int32_t solve_w, int32_t ent, int32_t ent0, bool tc_syrk, bool f32, Plan& P);
+               const int32_t* Ji, int32_t solve_w, int32_t ent, int32_t ent0, bool tc_syrk, bool f32,
+               int32_t tc_panel_min, Plan& P);
 
 }  // namespace kkt
