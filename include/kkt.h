@@ -129,8 +129,8 @@ typedef struct kkt_options {
                           resident at once */
   int32_t tc_panel_min;/* narrowest front (columns) whose in-panel updates beyond each
                           128-column outer block run on the tensor cores (tensor_cores = 1):
-                          0 = default 1024, else >= 128; narrower fronts keep them on the
-                          FMA units (each such step is a launch of its own) */
+                          0 = default 128 (every front), else >= 128; narrower fronts keep
+                          them on the FMA units */
 } kkt_options;
 
 /* Kernel kinds reported by kkt_get_profile. Kinds a plan does not launch

@@ -1,7 +1,8 @@
 """Autotuner for the per-pattern plan parameters: supernode relaxation
 (relax_small, relax_num/relax_den, relax_wmax), the triangular-solve tile
-shape (solve_w columns per piece, solve_ent L entries per work item) and the
-tensor-core switch. The analysis is exact for every parameter set (the
+shape (solve_w columns per piece, solve_ent L entries per work item), the
+tensor-core switch and the narrowest front whose in-panel updates take the
+tensor cores. The analysis is exact for every parameter set (the
 supernode partition only changes which explicit zeros are stored, never the
 factor), so the tuner may pick any of them; it keeps the fastest one whose
 solves meet the residual target.
@@ -31,6 +32,7 @@ SPACE = {
     "solve_w": (128, 64, 192),
     "solve_ent": (16384, 8192, 32768),
     "tensor_cores": (1, 0),
+    "tc_panel_min": (128, 512, 1024),
 }
 DEFAULT = {k: v[0] for k, v in SPACE.items()}
 

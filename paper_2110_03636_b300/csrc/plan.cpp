@@ -139,9 +139,9 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
     P.tc_ws_tiles = std::max(P.tc_ws_tiles, ws);
     ws = 0;
   };
-  // fronts at least kTcPanelMinWidth wide take the in-panel update beyond
-  // each outer block on the tensor cores (narrower fronts give launches too
-  // small to pay for the persistent kernel's start)
+  // fronts at least tc_panel_min wide take the in-panel update beyond each
+  // outer block on the tensor cores (the default, 128, is every front that
+  // has columns beyond its first outer block)
   auto tc_panel = [&](int32_t sn) { return tc_syrk && P.sw[sn] >= tc_panel_min; };
   auto push_fitem = [&](std::vector<int32_t>& v, int32_t sn, int32_t x, int32_t y) {
     const int64_t po = P.poff[sn];

@@ -165,7 +165,7 @@ inline int64_t packed_inv_size(int64_t pw) {
 // B operand tiles and carries its front's geometry (kTcItem ints)
 constexpr int kTcMinRows = 128;
 constexpr int kTcPB = 128;        // outer column block of the tensor-core in-panel update
-constexpr int kTcPanelMinWidth = 1024;   // narrowest front that takes it (default of opt.tc_panel_min)
+constexpr int kTcPanelMinWidth = 128;    // narrowest front that takes it (default of opt.tc_panel_min)
 constexpr int kTcMinWidth = 32;
 constexpr int kTcItem = 16;
 constexpr int kTcTileFloats = 2 * 128 * 32;   // one operand tile: TF32 hi and lo parts of 128 rows x 32 K
