@@ -106,7 +106,7 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
   auto lo32 = [](int64_t v) { return (int32_t)(uint32_t)(v & 0xffffffff); };
   auto hi32 = [](int64_t v) { return (int32_t)(v >> 32); };
   auto tc_region = [&](int32_t sn, int32_t r0, int32_t klo, int32_t khi) {
-    const int64_t nrb = cdiv(P.snr[sn] - r0, 128), nch = cdiv(khi - klo, 32), base = ws;
+    const int64_t nrb = cdiv(P.snr[sn] - r0, 128), nch = cdiv(khi - klo, kTcK), base = ws;
     const int64_t po = P.poff[sn];
     for (int64_t rbi = 0; rbi < nrb; rbi++)
       for (int64_t c0 = 0; c0 < nch; c0 += kTcSplitChunks) {
@@ -119,13 +119,16 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
     ws += nrb * nch;
     return base;
   };
+  // tc_item: the 128 x 256 tile of rows ra.. and the columns of row blocks
+  // rb.. and rb + 128.. of that region (the second only if the front has it)
   auto tc_item = [&](int32_t sn, int32_t ra, int32_t rb, int32_t r0, int64_t base, int32_t klo, int32_t khi,
                      int32_t mode) {
-    const int64_t nch = cdiv(khi - klo, 32);
+    const int64_t nch = cdiv(khi - klo, kTcK);
     const int64_t ta = base + (ra - r0) / 128 * nch, tb = base + (rb - r0) / 128 * nch;
     const int64_t out = mode ? P.poff[sn] : P.uoff[sn];
+    const int32_t two = rb + 128 < P.snr[sn] ? 1 : 0;
     P.it_syrk_tc.insert(P.it_syrk_tc.end(), {lo32(ta), hi32(ta), lo32(tb), hi32(tb), (int32_t)nch, mode, ra, rb,
-                                             P.sld[sn], P.snr[sn], P.sw[sn], 0, lo32(out), hi32(out), 0, 0});
+                                             P.sld[sn], P.snr[sn], P.sw[sn], two, lo32(out), hi32(out), 0, 0});
   };
   // the split launch (kind 10) and the tile launch (kind 6) of the items
   // added since (o10, o6)
@@ -230,7 +233,7 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
         for (int32_t s : F) {
           if (!tc_panel(s) || oe >= P.sw[s]) continue;
           const int64_t base = tc_region(s, oe, oe - kTcPB, oe);
-          for (int32_t cs = oe; cs < P.sw[s]; cs += 128)
+          for (int32_t cs = oe; cs < P.sw[s]; cs += 256)
             for (int32_t rs = cs; rs < P.snr[s]; rs += 128) tc_item(s, rs, cs, oe, base, oe - kTcPB, oe, 1);
           // lower trapezoid of rows [oe, nr) x columns [oe, w), K = kTcPB
           const double cols = P.sw[s] - oe, top = P.snr[s] - oe;
@@ -266,7 +269,7 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
       P.tc_flops += (double)w * rbd * (rbd + 1);   // U = -L21 L21^T, lower triangle
       const int64_t base = tc_region(s, w, 0, w);
       for (int64_t ti = 0; ti < nt; ti++)
-        for (int64_t tj = 0; tj <= ti; tj++)
+        for (int64_t tj = 0; tj <= ti; tj += 2)
           tc_item(s, w + (int32_t)ti * 128, w + (int32_t)tj * 128, w, base, 0, w, 0);
     }
     const int64_t c2 = (int64_t)P.it_syrk.size() / 4 - o2, c8 = (int64_t)P.it_syrk128.size() / 4 - o8;

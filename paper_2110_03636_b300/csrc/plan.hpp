@@ -76,10 +76,10 @@ struct Plan {
   std::vector<int32_t> it_trsm;             // (s, row tile) pairs
   std::vector<int32_t> it_pupd;             // (s, row tile, col tile) triples (kFItem ints each)
   std::vector<int32_t> it_syrk;             // (s, ti, tj) triples, 64 x 64 tiles
-  std::vector<int32_t> it_syrk_tc;          // tensor-core update tiles, kTcItem ints each: (A operand tile
-                                            // lo, hi, B operand tile lo, hi), (chunks, mode, panel row of
-                                            // A, panel row of B), (ld, rows, width, 0), (output offset
-                                            // lo, hi, 0, 0)
+  std::vector<int32_t> it_syrk_tc;          // tensor-core update tiles (128 rows x 256 columns), kTcItem
+                                            // ints each: (A operand tile lo, hi, B operand tile lo, hi),
+                                            // (chunks, mode, panel row of A, panel row of B), (ld, rows,
+                                            // width, B has a second row block), (output offset lo, hi, 0, 0)
   std::vector<int32_t> it_tc_split;         // operand splits before each tensor-core launch, kTcItem
                                             // ints each: (ld, rows, first row, K begin), (K end, first
                                             // chunk, end chunk, 0), (panel offset lo, hi, first operand
@@ -168,8 +168,9 @@ constexpr int kTcPB = 128;        // outer column block of the tensor-core in-pa
 constexpr int kTcPanelMinWidth = 128;    // narrowest front that takes it (default of opt.tc_panel_min)
 constexpr int kTcMinWidth = 32;
 constexpr int kTcItem = 16;
-constexpr int kTcTileFloats = 2 * 128 * 32;   // one operand tile: TF32 hi and lo parts of 128 rows x 32 K
-constexpr int kTcSplitChunks = 16;            // chunks of one row block per split item
+constexpr int kTcK = 16;                      // K columns of one operand tile
+constexpr int kTcTileFloats = 2 * 128 * kTcK; // one operand tile: TF32 hi and lo parts of 128 rows x kTcK
+constexpr int kTcSplitChunks = 32;            // operand tiles of one row block per split item
 constexpr int kTcGrid = 148;
 // f32 (FP32 factor): fronts with rb >= kBigRows get 128 x 128 register-tiled SYRK
 // tiles, and each block step fuses POTRF into the TRSM launch

@@ -55,16 +55,20 @@
 namespace kkt {
 namespace tcu {
 
-constexpr int KC = 32;                        // K per chunk
-constexpr uint32_t OPT = 128 * KC * 4;        // bytes of one split part (hi or lo) of an operand tile
+constexpr int KC = 16;                        // K per chunk (one operand tile)
+constexpr uint32_t OPT = 128 * KC * 4;        // bytes of one split part (hi or lo) of an operand tile (8 KB)
 constexpr uint32_t TILE = 2 * OPT;            // bytes of an operand tile: hi, then lo
 static_assert(TILE == kTcTileFloats * 4, "operand tile size");
-constexpr int kOp = 3;                        // ring depth (stages of A and B operand tiles)
-constexpr int kGroup = 2;                     // K chunks accumulated in tensor memory per drain
+// A stage holds one K chunk of a 128 x 256 output tile: A's operand tile,
+// then B's hi parts of its two 128-row blocks (256 rows, contiguous in the
+// core-matrix layout), then their lo parts.
+constexpr uint32_t STAGE = TILE + 2 * TILE;   // 48 KB
+constexpr int kOp = 4;                        // ring depth
+constexpr int kGroup = 4;                     // K chunks accumulated in tensor memory per drain (64 K)
 constexpr uint32_t LBO = 128;                 // bytes between core matrices along K
 constexpr uint32_t SBO = (KC / 4) * 128;      // bytes between 8-row groups
-constexpr int kThreads = 192;
-constexpr uint32_t kSmem = kOp * 2 * TILE + 1024;   // + barriers, slack
+constexpr int kThreads = 320;
+constexpr uint32_t kSmem = kOp * STAGE + 1024;   // + barriers, slack
 
 // barrier indices
 constexpr int B_OP_FULL = 0, B_OP_EMPTY = kOp, B_ACC_FULL = 2 * kOp, B_ACC_EMPTY = B_ACC_FULL + 2,
@@ -235,17 +239,20 @@ __global__ void __launch_bounds__(128) k_tc_split(const int4* __restrict__ items
 }
 
 // Tile item (kTcItem ints): (A operand tile lo, hi, B operand tile lo, hi),
-// (chunks, mode, panel row of A, panel row of B), (ld, rows, width, 0),
-// (output offset lo, hi, 0, 0): chunk c of A is operand tile A + c; the
-// output is U_s (mode 0, offset uoff[s]) or the panel (mode 1, poff[s]). A = B
-// (the same operand tiles) for a diagonal tile.
+// (chunks, mode, panel row of A, panel row of B), (ld, rows, width, B has a
+// second row block), (output offset lo, hi, 0, 0). The tile is 128 rows
+// (A's block) x 256 columns (B's block and the next one, whose operand tiles
+// follow B's after `chunks` tiles); chunk c of A is operand tile A + c. The
+// output is U_s (mode 0, offset uoff[s]) or the panel (mode 1, poff[s]);
+// columns past the front (a missing second block) are computed from whatever
+// the stage holds there and never stored.
 __global__ void __launch_bounds__(tcu::kThreads, 1)
     k_tc_update(const int4* __restrict__ items, int64_t nitems, FacArgs<float> a) {
   using namespace tcu;
   batch_view(a);                                         // system blockIdx.y of a batched launch
   extern __shared__ __align__(1024) unsigned char sm[];
-  unsigned char* opb = sm;                               // [kOp][A tile, B tile][TILE]
-  unsigned long long* bar = (unsigned long long*)(opb + kOp * 2 * TILE);
+  unsigned char* opb = sm;                               // [kOp][STAGE]
+  unsigned long long* bar = (unsigned long long*)(opb + kOp * STAGE);
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   volatile int* abrt = &abort_flag;
@@ -259,13 +266,13 @@ __global__ void __launch_bounds__(tcu::kThreads, 1)
     }
     for (int q = 0; q < 2; q++) {
       bar_init(&bar[B_ACC_FULL + q], 1);
-      bar_init(&bar[B_ACC_EMPTY + q], 4);
+      bar_init(&bar[B_ACC_EMPTY + q], 8);
     }
     bar_init(&bar[B_DONE], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 5) {
-    // two 128-column FP32 accumulators and the tile's 128 running sums
+  if (warp == 9) {
+    // two 256-column FP32 accumulators
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(saddr(&tmem_base)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
@@ -274,22 +281,32 @@ __global__ void __launch_bounds__(tcu::kThreads, 1)
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
 
-  if (warp == 4) {
+  if (warp == 8) {
     // ------------------------------------------------ operand copies
     if (lane == 0) {
       uint32_t rc = 0;
       bool ok = true;
       for (int64_t t = blockIdx.x; t < nitems && ok; t += gridDim.x) {
-        const int4 q0 = items[(kTcItem / 4) * t], q1 = items[(kTcItem / 4) * t + 1];
+        const int4* q = items + (kTcItem / 4) * t;
+        const int4 q0 = q[0], q1 = q[1], q2 = q[2];
         const int64_t ta = i64_of(q0.x, q0.y), tb = i64_of(q0.z, q0.w);
-        const bool diag = ta == tb;
-        for (int c = 0; c < q1.x; c++) {
+        const int nk = q1.x;
+        const bool two = q2.w != 0;
+        for (int c = 0; c < nk; c++) {
           const uint32_t slot = rc % kOp, round = rc / kOp;
           if (!(ok = bar_wait(&bar[B_OP_EMPTY + slot], (round & 1) ^ 1, abrt, a.st))) break;
-          unsigned char* dst = opb + slot * 2 * TILE;
-          bar_expect_tx(&bar[B_OP_FULL + slot], diag ? TILE : 2 * TILE);
-          bulk_load(dst, a.W + (ta + c) * kTcTileFloats, TILE, &bar[B_OP_FULL + slot]);
-          if (!diag) bulk_load(dst + TILE, a.W + (tb + c) * kTcTileFloats, TILE, &bar[B_OP_FULL + slot]);
+          unsigned char* dst = opb + slot * STAGE;
+          const float* pa = a.W + (ta + c) * kTcTileFloats;
+          const float* pb = a.W + (tb + c) * kTcTileFloats;
+          const float* pb2 = a.W + (tb + nk + c) * kTcTileFloats;
+          bar_expect_tx(&bar[B_OP_FULL + slot], two ? STAGE : STAGE - TILE);
+          bulk_load(dst, pa, TILE, &bar[B_OP_FULL + slot]);                       // A hi, lo
+          bulk_load(dst + TILE, pb, OPT, &bar[B_OP_FULL + slot]);                 // B rows 0..127 hi
+          bulk_load(dst + 2 * TILE, pb + OPT / 4, OPT, &bar[B_OP_FULL + slot]);   // B rows 0..127 lo
+          if (two) {
+            bulk_load(dst + TILE + OPT, pb2, OPT, &bar[B_OP_FULL + slot]);        // B rows 128..255 hi
+            bulk_load(dst + 2 * TILE + OPT, pb2 + OPT / 4, OPT, &bar[B_OP_FULL + slot]);   // lo
+          }
           rc++;
         }
       }
@@ -299,29 +316,27 @@ __global__ void __launch_bounds__(tcu::kThreads, 1)
           bar_drain(&bar[B_OP_FULL + q % kOp], (q / kOp) & 1);
       }
     }
-  } else if (warp == 5) {
+  } else if (warp == 9) {
     // ------------------------------------------------ MMA issuer
     if (lane == 0) {
-      // D = F32, A = B = TF32, both K-major, N = 128, M = 128
-      const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | (16u << 17) | (8u << 24);
+      // D = F32, A = B = TF32, both K-major, N = 256, M = 128
+      const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | (32u << 17) | (8u << 24);
       uint32_t oc = 0, gc = 0;
       bool ok = true, issued = false;
       for (int64_t t = blockIdx.x; t < nitems && ok; t += gridDim.x) {
-        const int4 q0 = items[(kTcItem / 4) * t], q1 = items[(kTcItem / 4) * t + 1];
-        const bool diag = q0.x == q0.z && q0.y == q0.w;
-        const int nk = q1.x;
+        const int nk = items[(kTcItem / 4) * t + 1].x;
         for (int g0 = 0; g0 < nk && ok; g0 += kGroup) {
           const uint32_t b = gc & 1;
           if (!(ok = bar_wait(&bar[B_ACC_EMPTY + b], ((gc >> 1) & 1) ^ 1, abrt, a.st))) break;
           asm volatile("tcgen05.fence::after_thread_sync;");
-          const uint32_t d = tmem + b * 128;
+          const uint32_t d = tmem + b * 256;
           const int g1 = min(nk, g0 + kGroup);
           for (int c = g0; c < g1; c++) {
             const uint32_t os = oc % kOp, orr = oc / kOp;
             if (!(ok = bar_wait(&bar[B_OP_FULL + os], orr & 1, abrt, a.st))) break;
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t base = saddr(opb + os * 2 * TILE);
-            const uint32_t ah = base, al = base + OPT, bh = diag ? ah : base + TILE, bl = diag ? al : base + TILE + OPT;
+            const uint32_t base = saddr(opb + os * STAGE);
+            const uint32_t ah = base, al = base + OPT, bh = base + TILE, bl = base + 2 * TILE;
 #pragma unroll
             for (int kk = 0; kk < KC / 8; kk++) {
               const uint32_t ko = kk * 2 * LBO;
@@ -345,19 +360,19 @@ __global__ void __launch_bounds__(tcu::kThreads, 1)
       }
     }
   } else {
-    // ------------------------------------------------ drain + epilogue (warps 0-3)
-    // The tile's running sums live in tensor memory (columns 256..383): each
-    // drained group is added to them with round-to-nearest FP32 adds, 32
-    // columns at a time, so a thread holds 64 values, not the row's 128 sums.
-    const int i = 32 * warp + lane;          // tile row = tensor-memory lane
-    const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
-    const uint32_t run = tmem + lane_off + 256;
+    // ------------------------------------------------ drain + epilogue (warps 0-7)
+    // warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (tile rows) and
+    // columns 128 (w / 4) .. + 127 of the 256; the tile's running sums stay
+    // in its registers, one per column, added with round-to-nearest
+    const int quad = warp & 3, half = warp >> 2;
+    const int i = 32 * quad + lane;          // tile row = tensor-memory lane
+    const uint32_t lane_off = (uint32_t)(32 * quad) << 16;
     uint32_t gc = 0;
     bool ok = true;
     for (int64_t t = blockIdx.x; t < nitems && ok; t += gridDim.x) {
       const int4* q = items + (kTcItem / 4) * t;
       const int4 q1 = q[1], q2 = q[2], q3 = q[3];
-      const int nk = q1.x, mode = q1.y, ra = q1.z, rb = q1.w;
+      const int nk = q1.x, mode = q1.y, ra = q1.z, cb = q1.w + 128 * half;
       const int ld = q2.x, nr = q2.y, w = q2.z;
       const int64_t out = i64_of(q3.x, q3.y);
       if (mode != 0) {
@@ -366,69 +381,62 @@ __global__ void __launch_bounds__(tcu::kThreads, 1)
         const int row = ra + i;
         const float* P = a.L + out + row;
         if (row < nr)
-          for (int j = 0; j < 128 && rb + j < w; j++)
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(P + (int64_t)(rb + j) * ld));
+          for (int j = 0; j < 128 && cb + j < w; j++)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(P + (int64_t)(cb + j) * ld));
       }
+      float acc[128];
+#pragma unroll
+      for (int j = 0; j < 128; j++) acc[j] = 0.f;
       for (int g0 = 0; g0 < nk; g0 += kGroup) {
         const uint32_t b = gc & 1;
         bool got = true;
         if (lane == 0) got = bar_wait(&bar[B_ACC_FULL + b], (gc >> 1) & 1, abrt, a.st);
         if (!(ok = __shfl_sync(0xffffffffu, got, 0))) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t ta = tmem + lane_off + b * 128;
-#pragma unroll 1
-        for (int c4 = 0; c4 < 4; c4++) {
-          uint32_t r[32], s[32];
-          tmem_ld32(r, ta + (uint32_t)(c4 * 32));
-          if (g0 > 0) {
-            tmem_ld32(s, run + (uint32_t)(c4 * 32));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const uint32_t ta = tmem + lane_off + b * 256 + half * 128;
 #pragma unroll
-            for (int j = 0; j < 32; j++) r[j] = __float_as_uint(__uint_as_float(s[j]) + __uint_as_float(r[j]));
-          } else {
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-          }
-          tmem_st32(run + (uint32_t)(c4 * 32), r);
+        for (int c4 = 0; c4 < 4; c4++) {
+          uint32_t r[32];
+          tmem_ld32(r, ta + (uint32_t)(c4 * 32));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int j = 0; j < 32; j++) acc[c4 * 32 + j] += __uint_as_float(r[j]);
         }
-        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncwarp();
         if (lane == 0) bar_arrive(&bar[B_ACC_EMPTY + b]);
         gc++;
       }
       if (!ok) break;
-      // store the finished tile, 32 columns at a time
-#pragma unroll 1
-      for (int c4 = 0; c4 < 4; c4++) {
-        uint32_t r[32];
-        tmem_ld32(r, run + (uint32_t)(c4 * 32));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (mode == 0) {
-          const int rbk = nr - w;
-          const int gi = ra - w + i, gj0 = rb - w + c4 * 32;
-          float* U = a.U + out;
-          if (gi < rbk) {
+      // store the finished tile
+      if (mode == 0) {
+        const int rbk = nr - w;
+        const int gi = ra - w + i, gj0 = cb - w;
+        float* U = a.U + out;
+        if (gi < rbk) {
 #pragma unroll
-            for (int j = 0; j < 32; j++) {
-              const int gj = gj0 + j;
-              if (gj < rbk && gi >= gj) U[(int64_t)gi + (int64_t)gj * rbk] = -__uint_as_float(r[j]);
-            }
+          for (int j = 0; j < 128; j++) {
+            const int gj = gj0 + j;
+            if (gj < rbk && gi >= gj) U[(int64_t)gi + (int64_t)gj * rbk] = -acc[j];
           }
-        } else {
-          // read-modify-write: 32 independent loads, then the stores
-          const int row = ra + i, col0 = rb + c4 * 32;
-          float* __restrict__ P = a.L + out + row;
-          if (row < nr) {
+        }
+      } else {
+        // read-modify-write in batches of 32 independent loads
+        const int row = ra + i;
+        float* __restrict__ P = a.L + out + row;
+        if (row < nr) {
+#pragma unroll
+          for (int c4 = 0; c4 < 4; c4++) {
             float v[32];
 #pragma unroll
             for (int j = 0; j < 32; j++) {
-              const int col = col0 + j;
+              const int col = cb + c4 * 32 + j;
               v[j] = (col < w && row >= col) ? P[(int64_t)col * ld] : 0.f;
             }
 #pragma unroll
             for (int j = 0; j < 32; j++) {
-              const int col = col0 + j;
-              if (col < w && row >= col) P[(int64_t)col * ld] = v[j] - __uint_as_float(r[j]);
+              const int col = cb + c4 * 32 + j;
+              if (col < w && row >= col) P[(int64_t)col * ld] = v[j] - acc[c4 * 32 + j];
             }
           }
         }
@@ -438,7 +446,7 @@ __global__ void __launch_bounds__(tcu::kThreads, 1)
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
-  if (warp == 5) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+  if (warp == 9) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
 }
 
 cudaError_t launch_tc_split(const int4* items, int64_t cnt, const FacArgs<float>& a, cudaStream_t st, int nb) {
