@@ -19,26 +19,31 @@
 // does, not with K.
 //
 // Two launches per tensor-core step:
-//   k_tc_split   splits the step's operands once: each 128-row block x 32-K
+//   k_tc_split   splits the step's operands once: each 128-row block x 16-K
 //                chunk of a front's rows becomes one operand tile (hi then lo,
-//                16 KB each) in the K-major core-matrix layout the MMA reads
+//                8 KB each) in the K-major core-matrix layout the MMA reads
 //                (8 rows x 16 bytes per core matrix, no swizzle), in a global
 //                workspace. HBM-bound: 4 bytes read, 8 written per value.
-//   k_tc_update  one CTA per SM, persistent over the step's tiles:
-//     warp 4     copies the A and B operand tiles of each K chunk into a ring
-//                of kOp shared-memory stages (cp.async.bulk, mbarrier
-//                transaction counts);
-//     warp 5     MMA issuer (one thread) and tensor-memory owner: 3 MMAs per
-//                8-wide K step into one of two 128 x 128 FP32 accumulators;
-//     warps 0-3  drain + epilogue: tcgen05.ld of the accumulator (warp w
-//                reads lanes 32w..32w+31 = tile rows), round-to-nearest adds
-//                into the tile's running sums in tensor memory, and stores of
-//                the finished tile.
+//   k_tc_update  one CTA per SM, persistent over the step's tiles, each 128
+//                rows x 256 columns (A one row block, B two):
+//     warp 8     copies A's operand tile and B's two into a ring of kOp
+//                shared-memory stages (cp.async.bulk, mbarrier transaction
+//                counts), B's two hi parts adjacent (256 rows) and then its
+//                two lo parts;
+//     warp 9     MMA issuer (one thread) and tensor-memory owner: 3 MMAs
+//                (M = 128, N = 256, K = 8) per 8-wide K step into one of two
+//                256-column FP32 accumulators;
+//     warps 0-7  drain + epilogue: warp w reads lanes 32 (w % 4) .. + 31
+//                (tile rows) and columns 128 (w / 4) .. + 127 with
+//                tcgen05.ld, adds them into the tile's running sums in its
+//                registers with round-to-nearest, and stores the finished
+//                tile.
 // Splitting in the tile kernel itself would read every raw value from and
 // write its two parts to shared memory once per tile that uses it, and
 // shared-memory bandwidth (the bulk copies' writes and the MMAs' operand
 // reads) is what bounds the tile kernel; split once, an operand is only
-// copied in and read by the MMAs.
+// copied in and read by the MMAs, and N = 256 reads A once per 256 output
+// columns instead of 128.
 // Every wait is bounded; a wait that runs out sets DevStatus::abort, every
 // role leaves its loop, copies and MMAs in flight are waited for (bounded)
 // and the tensor memory is released before the CTA exits.
