@@ -95,10 +95,14 @@ typedef struct kkt_options {
                           split once per step into two TF32 parts, three partial products,
                           FP32 accumulation in tensor memory drained every 64 K and summed
                           with round-to-nearest adds; 0 = FP32 FMA units only */
-  int32_t solve_ctas;  /* resident solve-kernel CTAs per SM, 2..4 (0 = 2); the grid is this
-                          many per SM or fewer if shared memory does not allow it */
-  int32_t solve_ent;   /* L entries staged per triangular-solve work item, 2048..32768
-                          (0 = 16384 for KKT_MIXED, 8192 for KKT_FP64) */
+  int32_t solve_ctas;  /* resident solve-kernel CTAs per SM, 2..4 (0 = 3 for KKT_MIXED, 2 for
+                          KKT_FP64); the grid is this many per SM or fewer if shared memory
+                          does not allow it (kkt_solve_multi runs two per SM) */
+  int32_t solve_ent;   /* L entries staged per triangular-solve chunk item, 2048..32768
+                          (0 = 16000 for KKT_MIXED, 8192 for KKT_FP64). KKT_MIXED stages a
+                          head's first chunk and a subtree's panels in min(solve_ent, 7680)
+                          entries and puts chunk tiles where the heads' inverses go, so that
+                          three solve CTAs fit on an SM */
   int32_t refine;      /* KKT_MIXED refinement on K_delta: 1 = plain passes x += M r;
                           2 = flexible GMRES (restart 20) preconditioned by the mixed
                           solve M: one M application per iteration, like a pass, and it

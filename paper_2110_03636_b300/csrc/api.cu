@@ -65,6 +65,7 @@ struct kkt_handle_s {
   int device = 0;
   int grid = 0;
   int ctas = 2;   // solve-kernel CTAs per SM
+  int grid2 = 0;  // the solve grid without the overlapped layout (several right-hand sides)
   int64_t nnzH = 0, nnzJ = 0;
   DevArena mem;
   // pattern / plan on the device
@@ -334,15 +335,19 @@ static kkt_status analyse_host_impl(int64_t n, int64_t m, const int64_t* Hp, con
   h->hHi.assign(Hi, Hi + Hp[n]);
   h->hJp.assign(Jp, Jp + m + 1);
   h->hJi.assign(Ji, Ji + Jp[m]);
-  // piece width and L entries per solve item: a head's first chunk covers
-  // the next piece's columns, and two CTAs of the solve kernel fit on one SM
-  // (about 107 KB (FP32) / 98 KB (FP64) of shared memory each)
+  // piece width and L entries per solve item. FP64: chunks, heads' chunk 0
+  // and subtrees of 8192 entries, two solve CTAs per SM (about 98 KB of
+  // shared memory each). FP32: chunk tiles of 16000 entries share their
+  // region with the heads' inverses (ent0 = subtree entries = 7680), about
+  // 73 KB per CTA, three per SM.
   const bool f64o = o.precision == KKT_FP64;
   const int sw = o.solve_w > 0 ? o.solve_w : (f64o ? 64 : 128);
-  const int ent = o.solve_ent > 0 ? o.solve_ent : (f64o ? 8192 : 16384);
+  const int ent = o.solve_ent > 0 ? o.solve_ent : (f64o ? 8192 : 16000);
+  const int ov = f64o ? 0 : 1;
+  const int ent0 = ov ? std::min(ent, 7680) : ent;
   // the triangle inversion holds a piece's sw x sw triangle in shared memory
   if ((size_t)sw * sw * (f64o ? 8 : 4) > (size_t)200 * 1024) { delete h; return KKT_ERR_INVALID; }
-  if (build_plan(h->S, Hp, Hi, Jp, Ji, sw, ent, ent, !f64o && o.tensor_cores, !f64o,
+  if (build_plan(h->S, Hp, Hi, Jp, Ji, sw, ent, ent0, ent0, ov, !f64o && o.tensor_cores, !f64o,
                  o.tc_panel_min ? o.tc_panel_min : kTcPanelMinWidth, h->P) != 0) {
     delete h;
     return KKT_ERR_INVALID;
@@ -404,11 +409,19 @@ static kkt_status device_stage(kkt_handle h, kkt_handle* out) {
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device);
   if (!coop) { delete h; return KKT_ERR_CUDA; }
   const bool f64 = o.precision == KKT_FP64;
-  h->ctas = o.solve_ctas > 0 ? o.solve_ctas : 2;
-  h->grid = f64 ? solve_grid_size<double>(h->device, h->P.solve_w, h->P.ent, h->P.ent0, h->P.max_rows, h->ctas)
-                : solve_grid_size<float>(h->device, h->P.solve_w, h->P.ent, h->P.ent0, h->P.max_rows, h->ctas);
-  if (h->grid <= 0) { delete h; return KKT_ERR_INVALID; }
-  if (o.solve_sms > 0) h->grid = std::min(h->grid, h->ctas * o.solve_sms);
+  const Plan& Pl = h->P;
+  h->ctas = o.solve_ctas > 0 ? o.solve_ctas : (Pl.solve_ov ? 3 : 2);
+  h->grid = f64 ? solve_grid_size<double>(h->device, Pl.solve_w, Pl.ent, Pl.ent0, Pl.esub, Pl.max_rows, Pl.solve_ov,
+                                          h->ctas)
+                : solve_grid_size<float>(h->device, Pl.solve_w, Pl.ent, Pl.ent0, Pl.esub, Pl.max_rows, Pl.solve_ov,
+                                         h->ctas);
+  h->grid2 = !Pl.solve_ov ? h->grid
+                          : solve_grid_size<float>(h->device, Pl.solve_w, Pl.ent, Pl.ent0, Pl.esub, Pl.max_rows, 0, 2);
+  if (h->grid <= 0 || h->grid2 <= 0) { delete h; return KKT_ERR_INVALID; }
+  if (o.solve_sms > 0) {
+    h->grid = std::min(h->grid, h->ctas * o.solve_sms);
+    h->grid2 = std::min(h->grid2, 2 * o.solve_sms);
+  }
   const Plan& P = h->P;
   DevArena& A = h->mem;
   auto as_int4 = [&](const std::vector<int32_t>& v) {
@@ -747,6 +760,7 @@ static SolveArgs<T> solve_args(kkt_handle h) {
   a.sn_rows = h->sn_rows;
   a.pc_inv = h->pc_inv; a.hd_tgt = h->hd_tgt;
   a.sw = P.solve_w; a.ent = P.ent; a.ent0 = P.ent0; a.max_rows = P.max_rows;
+  a.esub = P.esub; a.ov = P.solve_ov;
   a.Linv = (const T*)h->sv.Linv;
   a.ch_tgt = h->ch_tgt;
   a.fwd_items = h->fwd_items; a.bwd_items = h->bwd_items;
@@ -789,13 +803,21 @@ static kkt_status solve_pass(kkt_handle h, const double* bx, const double* by, d
     a.p = h->mp; a.r = h->mr; a.y = h->my; a.q = h->mq; a.bS = h->mbS;
     a.wv = h->mwv; a.xa = h->mxa;
   }
+  // several right-hand sides use region A as scratch in their chunks: the
+  // layout without overlap, two CTAs per SM
+  int grid = h->grid, ctas = h->ctas;
+  if (nrhs > 1 && a.ov) {
+    a.ov = 0;
+    grid = h->grid2;
+    ctas = 2;
+  }
   if (h->profp) {
     CK(prof_begin(h->profp, st));
-    CK(launch_solve<T>(a, h->grid, h->ctas, st));
+    CK(launch_solve<T>(a, grid, ctas, st));
     CK(prof_end(h->profp, KKT_K_CG, st));
   } else {
     CK(cudaEventRecord(h->cg_a, st));
-    CK(launch_solve<T>(a, h->grid, h->ctas, st));
+    CK(launch_solve<T>(a, grid, ctas, st));
     CK(cudaEventRecord(h->cg_b, st));
   }
   return KKT_OK;

@@ -94,6 +94,8 @@ struct SolveArgs {
   const int32_t *fwd_items, *bwd_items;
   int64_t nitems, npieces;
   int32_t sw, ent, ent0, max_rows;  // piece width, L entries per chunk / head chunk 0, max chunk rows
+  int32_t esub;             // panel entries of a subtree item
+  int32_t ov;               // 1: chunk tiles overlap the inverse region (one right-hand side only)
   // small subtrees solved whole by one CTA
   const int32_t *st_first, *st_last, *st_clo, *st_chi, *st_tgt, *sn_piece;
   const int64_t* st_tptr;
@@ -168,8 +170,8 @@ cudaError_t launch_jjt_values(int64_t ne, const int64_t* pp, const int32_t* pa, 
 template <typename T>
 cudaError_t launch_solve(const SolveArgs<T>& a, int grid, int ctas, cudaStream_t st);
 template <typename T>
-int solve_grid_size(int device, int sw, int ent, int ent0, int max_rows, int ctas);
-size_t solve_smem_bytes(size_t elem, int sw, int ent, int ent0, int max_rows);
+int solve_grid_size(int device, int sw, int ent, int ent0, int esub, int max_rows, int ov, int ctas);
+size_t solve_smem_bytes(size_t elem, int sw, int ent, int ent0, int esub, int max_rows, int ov);
 
 // FP64 residual of K_delta = [H~ + delta I, J^T; J, 0] (original labels):
 // res = b - K x, and norms into DevStatus (rr, be, ...).

@@ -9,8 +9,8 @@ namespace kkt {
 static inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const int64_t* Jp,
-               const int32_t* Ji, int32_t solve_w, int32_t ent, int32_t ent0, bool tc_syrk, bool f32,
-               int32_t tc_panel_min, Plan& P) {
+               const int32_t* Ji, int32_t solve_w, int32_t ent, int32_t ent0, int32_t esub, int32_t ov,
+               bool tc_syrk, bool f32, int32_t tc_panel_min, Plan& P) {
   P = Plan();
   const int64_t n = S.n, m = S.m, ns = S.ns;
   P.n = n; P.m = m; P.ns = ns;
@@ -363,10 +363,10 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
   // entries; supernode indices are a postorder, so a subtree is the index
   // range [root - size + 1, root].
   // The solve kernel stages a subtree's panels (stored entries, ld
-  // included) into its row-tile region of ent entries and the inverses of
+  // included) into its row-tile region of esub entries and the inverses of
   // its triangles into the inverse region of one solve_w-wide piece (their
   // sum over <= solve_w columns never exceeds that piece's).
-  const int64_t kSubCols = std::min<int64_t>(128, solve_w), kSubEntries = ent;
+  const int64_t kSubCols = std::min<int64_t>(128, solve_w), kSubEntries = esub;
   std::vector<int64_t> sub_cols(ns, 0), sub_ent(ns, 0), sub_size(ns, 1);
   for (int64_t s = 0; s < ns; s++) {
     sub_cols[s] += P.sw[s];
@@ -432,6 +432,8 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
   P.solve_w = solve_w;
   P.ent = ent;
   P.ent0 = ent0;
+  P.esub = esub;
+  P.solve_ov = ov;
   // rows of an item holding at most e entries of a pw-wide piece: a multiple
   // of 4 (so the staged column segments stay 16-byte aligned) in [4, max_rows]
   auto rows_for = [&](int32_t e, int32_t pw) {
@@ -468,7 +470,7 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
     const int32_t s0 = P.st_first[t], s1 = P.st_last[t];
     const int64_t pe = P.poff[s1] + (int64_t)P.sw[s1] * P.sld[s1] - P.poff[s0];
     const int64_t ie = P.pc_inv[P.sn_piece[s1] + 1] - P.pc_inv[P.sn_piece[s0]];
-    if (pe > ent || ie > packed_inv_size(solve_w) || P.sn_piece[s1] - P.sn_piece[s0] != s1 - s0) return 2;
+    if (pe > esub || ie > packed_inv_size(solve_w) || P.sn_piece[s1] - P.sn_piece[s0] != s1 - s0) return 2;
   }
   P.pc_nchunk.resize(P.npieces);
   P.pc_rc0.resize(P.npieces);
@@ -495,7 +497,10 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
     const bool tma = pw >= kTmaMinWidth;
     const int32_t rc0 = tma ? std::min(rows_for(ent0, pw), kTmaRows) : rows_for(ent0, pw);
     const int32_t rc = tma ? std::min(rows_for(ent, pw), kTmaRows) : rows_for(ent, pw);
-    P.pc_box[p] = tma ? std::max(rc0, rc) + 4 : 0;
+    // one box height per piece (its tensor map): with the overlapped layout
+    // it fits a chunk (heads then stage chunk 0 column by column, into the
+    // smaller region B); otherwise both
+    P.pc_box[p] = tma ? (ov ? rc : std::max(rc0, rc)) + 4 : 0;
     const int32_t r0n = std::min(below, rc0);
     P.pc_rc0[p] = r0n;
     P.hd_tptr.push_back((int64_t)P.hd_tgt.size());
@@ -535,7 +540,7 @@ int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const in
     HeadDesc& d = P.hdesc[p];
     d.pw = P.pc_w[p]; d.f = P.pc_first[p]; d.rn = P.pc_rc0[p]; d.need = 0;   // need: set below
     d.c = P.pc_c[p]; d.ld = P.pc_ld[p]; d.nch = P.pc_nchunk[p];
-    d.tma = P.pc_box[p] > 0 ? 1 : 0; d.pad = 0;
+    d.tma = P.pc_box[p] > 0 && !ov ? 1 : 0; d.pad = 0;
     d.cs = d.tma ? P.pc_box[p] : ((d.rn + 3) & ~3) + 8;
     d.colbase = P.pc_colbase[p]; d.rowbase = P.pc_row[p];
     d.inv0 = P.pc_inv[p]; d.inv1 = P.pc_inv[p + 1];

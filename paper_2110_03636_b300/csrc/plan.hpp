@@ -111,6 +111,8 @@ struct Plan {
   // 0"); the remaining rows form separate chunks of at most rc rows.
   int32_t solve_w = 128;
   int32_t ent = 16384, ent0 = 8192;         // L entries per chunk item / per head's chunk 0
+  int32_t esub = 16384;                     // panel entries per subtree item
+  int32_t solve_ov = 0;                     // chunk tiles overlap the inverse region (see solve.cu)
   int32_t max_rows = 1024;                  // rows of any chunk (gathered-vector limit)
   int64_t npieces = 0, nchunks = 0;
   std::vector<int32_t> pc_first, pc_w, pc_nr, pc_ld; // piece: first column, width, rows from its first row, ld
@@ -176,7 +178,7 @@ constexpr int kTcGrid = 148;
 // tiles, and each block step fuses POTRF into the TRSM launch
 constexpr int kBigRows = 128;
 int build_plan(const Symbolic& S, const int64_t* Hp, const int32_t* Hi, const int64_t* Jp,
-               const int32_t* Ji, int32_t solve_w, int32_t ent, int32_t ent0, bool tc_syrk, bool f32,
-               int32_t tc_panel_min, Plan& P);
+               const int32_t* Ji, int32_t solve_w, int32_t ent, int32_t ent0, int32_t esub, int32_t ov,
+               bool tc_syrk, bool f32, int32_t tc_panel_min, Plan& P);
 
 }  // namespace kkt

@@ -56,8 +56,9 @@ struct SolveSmemHdr {
 
 template <typename T>
 struct Tiles {
-  T* A;     // packed inverse of a piece triangle, or a chunk tile
-  T* B;     // chunk-0 tile of a head
+  T* A;     // packed inverse of a piece triangle (heads, subtrees)
+  T* B;     // chunk-0 tile of a head, a subtree's panels
+  T* C;     // a chunk's tile
   T* vec;   // sw
   T* vec2;  // sw
   T* aux;   // max_rows + kSolveThreads
@@ -68,15 +69,40 @@ __host__ __device__ static size_t packed_inv(size_t pw) {
   for (size_t k = 0; k < pw; k++) t += (pw - k + 3) & ~(size_t)3;
   return t;
 }
-// Shared memory: region A holds a head's packed inverse, region B the row
-// tile of a head's chunk 0 or of a chunk (both at most ent0 = ent entries).
+// Shared memory: region A holds a head's or a subtree's packed inverses,
+// region B the row tile of a head's chunk 0 (ent0 entries) or a subtree's
+// panels (esub), C a chunk's row tile (ent), each + 8 entries per column of
+// start alignment. Without overlap (ov = 0) C is B. With it (ov = 1) C
+// starts where A does: a chunk of one right-hand side never uses A, and the
+// region is then max(C, A + B) instead of A + max(B, C) (three solve CTAs
+// per SM fit where two did). Every region starts on 128 bytes (TMA boxes).
 __host__ __device__ static size_t tileA(int sw, int /*ent*/) { return packed_inv((size_t)sw); }
+__host__ __device__ static size_t round128(size_t elem, size_t x) {
+  const size_t q = 128 / elem;
+  return (x + q - 1) / q * q;
+}
+struct SolveLayout {
+  size_t b_off, c_off, vec_off;   // element offsets from the aligned base (A at 0)
+};
+__host__ __device__ static SolveLayout solve_layout(size_t elem, int sw, int ent, int ent0, int esub, int ov) {
+  SolveLayout l;
+  const size_t a = round128(elem, tileA(sw, ent));
+  const size_t b = (size_t)max(ent0, esub) + 8 * (size_t)sw;
+  const size_t c = (size_t)ent + 8 * (size_t)sw;
+  l.b_off = a;
+  if (ov) {
+    l.c_off = 0;
+    l.vec_off = max(round128(elem, c), a + b);
+  } else {
+    l.c_off = a;
+    l.vec_off = a + max(b, c);
+  }
+  return l;
+}
 
-size_t solve_smem_bytes(size_t elem, int sw, int ent, int ent0, int max_rows) {
-  const size_t a = tileA(sw, ent);
-  const size_t e = (size_t)(ent > ent0 ? ent : ent0);
-  const size_t b = e + 8 * (size_t)sw;
-  return elem * (a + b + 2 * (size_t)sw + (size_t)max_rows + kSolveThreads) + 256;   // + alignment of A and B
+size_t solve_smem_bytes(size_t elem, int sw, int ent, int ent0, int esub, int max_rows, int ov) {
+  const SolveLayout l = solve_layout(elem, sw, ent, ent0, esub, ov);
+  return elem * (l.vec_off + 2 * (size_t)sw + (size_t)max_rows + kSolveThreads) + 128;   // + base alignment
 }
 
 // Offset of column k in a packed pw-wide inverse: sum over j < k of
@@ -490,10 +516,10 @@ __device__ bool fwd_chunk(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>
   if (tid < 32) {
     uint32_t b = 0;
     if (tid == 0) fence_proxy_async();
-    stage_tile(a, p, d.colbase, d.ld, d.c, pw, d.r0, nr, d.cs, d.tma, t.B, b, &h.mbar, false);
+    stage_tile(a, p, d.colbase, d.ld, d.c, pw, d.r0, nr, d.cs, d.tma, t.C, b, &h.mbar, false);
     if (tid == 0) mbar_expect_tx(&h.mbar, b);
     __syncwarp();
-    stage_tile(a, p, d.colbase, d.ld, d.c, pw, d.r0, nr, d.cs, d.tma, t.B, b, &h.mbar, true);
+    stage_tile(a, p, d.colbase, d.ld, d.c, pw, d.r0, nr, d.cs, d.tma, t.C, b, &h.mbar, true);
     mark(a, h, 3);
     if (tid == 0) {
       const long long t0 = clock64();
@@ -505,7 +531,7 @@ __device__ bool fwd_chunk(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>
   __syncthreads();
   const bool dep = h.flag != 0;
   const int R = a.nrhs;
-  if (R > 1 && R * pw <= a.max_rows + kSolveThreads && (size_t)R * blockDim.x <= packed_inv((size_t)a.sw)) {
+  if (R > 1 && !a.ov && R * pw <= a.max_rows + kSolveThreads && (size_t)R * blockDim.x <= packed_inv((size_t)a.sw)) {
     // all right-hand sides' piece vectors at once (into the gathered-vector
     // region; chunks leave the inverse region free for the partial sums)
     T* X = t.aux;
@@ -514,7 +540,7 @@ __device__ bool fwd_chunk(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>
         X[idx] = ldcg(&a.v[(int64_t)(idx / pw) * a.n + f + idx % pw]);
     if (!mbar_wait(a, h) || !dep) return false;
     const int d0 = (d.c + d.r0) & 3;
-    rows_matvec_multi(t.B, d.cs, d0, nr, pw, X, R, t.A, [&](int i, int j, T o) {
+    rows_matvec_multi(t.C, d.cs, d0, nr, pw, X, R, t.A, [&](int i, int j, T o) {
       atomicAdd(&a.v[(int64_t)j * a.n + (nr <= (int)blockDim.x ? myrow : rows[i])], -o);
     });
     __syncthreads();
@@ -532,7 +558,7 @@ __device__ bool fwd_chunk(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>
       for (int k = tid; k < pw; k += blockDim.x) t.vec[k] = ldcg(&vj[f + k]);
       __syncthreads();
     }
-    rows_matvec(t.B, d.cs, d0, nr, pw, t.vec, t.aux, [&](int i, int u, T o) {
+    rows_matvec(t.C, d.cs, d0, nr, pw, t.vec, t.aux, [&](int i, int u, T o) {
       atomicAdd(&vj[u >= 0 ? myrows[u] : rows[i]], -o);
     });
     __syncthreads();
@@ -554,10 +580,10 @@ __device__ bool bwd_chunk(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>
   if (tid < 32) {
     uint32_t b = 0;
     if (tid == 0) fence_proxy_async();
-    stage_tile(a, p, d.colbase, d.ld, d.c, pw, d.r0, nr, d.cs, d.tma, t.B, b, &h.mbar, false);
+    stage_tile(a, p, d.colbase, d.ld, d.c, pw, d.r0, nr, d.cs, d.tma, t.C, b, &h.mbar, false);
     if (tid == 0) mbar_expect_tx(&h.mbar, b);
     __syncwarp();
-    stage_tile(a, p, d.colbase, d.ld, d.c, pw, d.r0, nr, d.cs, d.tma, t.B, b, &h.mbar, true);
+    stage_tile(a, p, d.colbase, d.ld, d.c, pw, d.r0, nr, d.cs, d.tma, t.C, b, &h.mbar, true);
     const long long t0 = clock64();
     const bool ok = warp_wait_all(a.bwd_done, a.ch_tgt, d.tp0, d.tp1, e, a.st, a.spin);
     if (tid == 0) {
@@ -578,7 +604,7 @@ __device__ bool bwd_chunk(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>
   const int d0 = (d.c + d.r0) & 3;
   const int cs = d.cs;
   const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  if (R > 1 && (size_t)R * nr <= packed_inv((size_t)a.sw)) {
+  if (R > 1 && !a.ov && (size_t)R * nr <= packed_inv((size_t)a.sw)) {
     // every right-hand side's values at the chunk rows at once (inverse region)
     T* Gx = t.A;
     if (dep)
@@ -592,7 +618,7 @@ __device__ bool bwd_chunk(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>
 #pragma unroll
       for (int j = 0; j < kMaxRhs; j++) acc[j] = T(0);
       for (int i = lane; i < nr; i += 32) {
-        const T tv = t.B[k * cs + d0 + i];
+        const T tv = t.C[k * cs + d0 + i];
 #pragma unroll
         for (int j = 0; j < kMaxRhs; j++)
           if (j < R) acc[j] += tv * Gx[j * nr + i];
@@ -627,7 +653,7 @@ __device__ bool bwd_chunk(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>
         const T xv = t.aux[i];
 #pragma unroll
         for (int q = 0; q < 8; q++)
-          if (k0 + q < pw) acc[q] += t.B[(k0 + q) * cs + d0 + i] * xv;
+          if (k0 + q < pw) acc[q] += t.C[(k0 + q) * cs + d0 + i] * xv;
       }
       const T sum = warp_sum8(acc);
       const int k = k0 + (lane >> 2);
@@ -1107,14 +1133,15 @@ __global__ void __launch_bounds__(kSolveThreads, MB) k_cg(SolveArgs<T> a) {
   extern __shared__ __align__(16) unsigned char dsm[];
   Tiles<T> tl;
   {
-    // region A at a 128-byte aligned shared address, region B (TMA boxes) too
+    // every region at a 128-byte aligned shared address (TMA boxes)
     const uint32_t sa = saddr(dsm);
-    unsigned char* pa = dsm + ((128u - (sa & 127u)) & 127u);
-    tl.A = (T*)pa;
-    const size_t abytes = (tileA(a.sw, a.ent) * sizeof(T) + 127) & ~(size_t)127;
-    tl.B = (T*)(pa + abytes);
+    T* base = (T*)(dsm + ((128u - (sa & 127u)) & 127u));
+    const SolveLayout l = solve_layout(sizeof(T), a.sw, a.ent, a.ent0, a.esub, a.ov);
+    tl.A = base;
+    tl.B = base + l.b_off;
+    tl.C = base + l.c_off;
+    tl.vec = base + l.vec_off;
   }
-  tl.vec = tl.B + (size_t)(a.ent > a.ent0 ? a.ent : a.ent0) + 8 * (size_t)a.sw;
   tl.vec2 = tl.vec + a.sw;
   tl.aux = tl.vec2 + a.sw;
   if (threadIdx.x == 0) {
@@ -1375,11 +1402,11 @@ static CgKernel<T> cg_kernel(int ctas) {
 }
 
 template <typename T>
-int solve_grid_size(int device, int sw, int ent, int ent0, int max_rows, int ctas) {
+int solve_grid_size(int device, int sw, int ent, int ent0, int esub, int max_rows, int ov, int ctas) {
   int sms = 0, per = 0, maxsm = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
-  const size_t smem = solve_smem_bytes(sizeof(T), sw, ent, ent0, max_rows);
+  const size_t smem = solve_smem_bytes(sizeof(T), sw, ent, ent0, esub, max_rows, ov);
   if (smem > (size_t)maxsm) return 0;
   auto k = cg_kernel<T>(ctas);
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
@@ -1395,13 +1422,13 @@ template <typename T>
 cudaError_t launch_solve(const SolveArgs<T>& a, int grid, int ctas, cudaStream_t st) {
   SolveArgs<T> args = a;
   void* params[] = {&args};
-  const size_t smem = solve_smem_bytes(sizeof(T), a.sw, a.ent, a.ent0, a.max_rows);
+  const size_t smem = solve_smem_bytes(sizeof(T), a.sw, a.ent, a.ent0, a.esub, a.max_rows, a.ov);
   return cudaLaunchCooperativeKernel((const void*)cg_kernel<T>(ctas), dim3(grid), dim3(kSolveThreads), params, smem,
                                      st);
 }
 
-template int solve_grid_size<double>(int, int, int, int, int, int);
-template int solve_grid_size<float>(int, int, int, int, int, int);
+template int solve_grid_size<double>(int, int, int, int, int, int, int, int);
+template int solve_grid_size<float>(int, int, int, int, int, int, int, int);
 template cudaError_t launch_solve<double>(const SolveArgs<double>&, int, int, cudaStream_t);
 template cudaError_t launch_solve<float>(const SolveArgs<float>&, int, int, cudaStream_t);
 

@@ -25,7 +25,7 @@ def _fake(best, slow_rr=()):
 
 
 def test_search_finds_the_coordinate_optimum_and_evaluates_each_set_once():
-    best = {"relax_small": 32, "relax_frac": (1, 20), "relax_wmax": 256, "solve_w": 64, "solve_ent": 32768,
+    best = {"relax_small": 32, "relax_frac": (1, 20), "relax_wmax": 256, "solve_w": 64, "solve_ent": 8192,
             "tensor_cores": 1, "tc_panel_min": 512}
     obj, calls = _fake(best)
     got, t, evals = AT.coordinate_search(obj)
@@ -36,7 +36,7 @@ def test_search_finds_the_coordinate_optimum_and_evaluates_each_set_once():
 
 
 def test_search_skips_sets_that_miss_the_residual_target():
-    best = {"relax_small": 8, "relax_frac": (1, 10), "relax_wmax": 256, "solve_w": 128, "solve_ent": 16384,
+    best = {"relax_small": 8, "relax_frac": (1, 10), "relax_wmax": 256, "solve_w": 128, "solve_ent": 12288,
             "tensor_cores": 0, "tc_panel_min": 128}
     obj, _ = _fake(best, slow_rr=[("tensor_cores", 0)])     # the faster setting is not accurate enough
     got, _, evals = AT.coordinate_search(obj)
