@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 namespace kkt {
 
 // Device status block written by kernels, read by the host after a call.
@@ -77,6 +79,21 @@ __device__ __forceinline__ bool warp_wait_all(const int* flags, const int32_t* t
     }
   }
   return __all_sync(0xffffffffu, ok);
+}
+
+// Raises kernel k's dynamic shared-memory limit to at least `bytes` and never
+// lowers it: handles with different plans launch the same kernels with
+// different sizes (also from several threads, and from graphs captured
+// earlier), and every launch needs the limit at or above its own size.
+template <typename K>
+inline cudaError_t raise_smem_limit(K k, size_t bytes) {
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lk(mu);
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, (const void*)k);
+  if (e) return e;
+  if ((size_t)fa.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+  return cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 }  // namespace kkt

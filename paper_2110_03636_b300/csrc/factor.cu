@@ -535,7 +535,7 @@ __global__ void __launch_bounds__(128) k_tri_inv(InvArgs<T> a) {
 template <typename T>
 cudaError_t launch_tri_inv(const InvArgs<T>& a, int64_t npieces, int max_pw, cudaStream_t st, int nb) {
   const size_t smem = sizeof(T) * (size_t)max_pw * max_pw;
-  cudaError_t e = cudaFuncSetAttribute(k_tri_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = raise_smem_limit(k_tri_inv<T>, smem);
   if (e) return e;
   if (npieces <= 0) return cudaSuccess;
   k_tri_inv<T><<<dim3((unsigned)npieces, (unsigned)nb), 128, smem, st>>>(a);

@@ -1409,7 +1409,7 @@ int solve_grid_size(int device, int sw, int ent, int ent0, int esub, int max_row
   const size_t smem = solve_smem_bytes(sizeof(T), sw, ent, ent0, esub, max_rows, ov);
   if (smem > (size_t)maxsm) return 0;
   auto k = cg_kernel<T>(ctas);
-  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+  if (raise_smem_limit(k, smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }

@@ -782,3 +782,29 @@ def test_batched_factor_on_tensor_core_fronts_matches_oracle():
     ddx, ddy = s.solve(cu(x.r_x), cu(x.r_y))
     assert rel(torch.cat([ddx, ddy]).cpu().numpy(), np.concatenate([dx[1].cpu().numpy(), dy[1].cpu().numpy()])) <= 1e-6
     s.close()
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_handle_still_solves_after_handles_with_smaller_solve_layouts(precision):
+    """Handles with different plans launch the same solve and triangle-inverse
+    kernels with different shared-memory sizes: a handle made, used and
+    destroyed later with a smaller layout (narrower pieces, fewer entries per
+    item) must leave the first one able to factor and solve to the oracle's
+    solution."""
+    sys = W.make_config("grid2d_n2000")
+    _, _, odx, ody, _ = O.solve_system(sys, ordering="nd")
+    ref = np.concatenate([odx, ody])
+    s = K.KKTSolver(sys.n, sys.m, sys.H_colptr, sys.H_rowidx, sys.J_rowptr, sys.J_colidx, precision=precision,
+                    ordering="nd")
+    for rep in range(2):
+        if rep:
+            t = K.KKTSolver.like(s, precision=precision, ordering="nd", solve_w=32, solve_ent=2048)
+            t.factor(cu(sys.H_vals), cu(sys.J_vals), sys.delta, sys.gamma)
+            dx, dy = t.solve(cu(sys.r_x), cu(sys.r_y))
+            assert rel(torch.cat([dx, dy]).cpu().numpy(), ref) <= 1e-6
+            t.close()
+        s.factor(cu(sys.H_vals), cu(sys.J_vals), sys.delta, sys.gamma)
+        dx, dy = s.solve(cu(sys.r_x), cu(sys.r_y))
+        assert s.info.cg_iters > 0 and s.info.rr <= 1e-9
+        assert rel(torch.cat([dx, dy]).cpu().numpy(), ref) <= 1e-6
+    s.close()
