@@ -59,7 +59,10 @@ typedef struct kkt_options {
   double delta2;       /* delta_2 of the CG restart on S + delta_2 I (Algorithm 1: 1e-9) */
   double cg_rtol;      /* CG stop: ||r|| <= cg_rtol ||b_S||; <= 0 selects by precision:
                           1e-12 for KKT_FP64 (Sec. 5.1), 3e-3 per refinement pass for
-                          KKT_MIXED (the FP32 factor bounds what one pass can reach) */
+                          KKT_MIXED (the FP32 factor bounds what one pass can reach). With
+                          the flexible-GMRES refinement (refine = 2) this is the tightest
+                          per-pass tolerance: each pass after an FGMRES step uses
+                          min(0.5, max(cg_rtol, 2 x that step's residual contraction)) */
   int32_t cg_maxit;    /* CG product limit (1000) */
   int32_t ir_maxit;    /* refinement passes on K_delta after the first solve; < 0 selects
                           by precision: 3 (KKT_FP64), 10 (KKT_MIXED) */
@@ -95,14 +98,16 @@ typedef struct kkt_options {
                           split once per step into two TF32 parts, three partial products,
                           FP32 accumulation in tensor memory drained every 64 K and summed
                           with round-to-nearest adds; 0 = FP32 FMA units only */
-  int32_t solve_ctas;  /* resident solve-kernel CTAs per SM, 2..4 (0 = 3 for KKT_MIXED, 2 for
-                          KKT_FP64); the grid is this many per SM or fewer if shared memory
-                          does not allow it (kkt_solve_multi runs two per SM) */
+  int32_t solve_ctas;  /* resident solve-kernel CTAs per SM, 2..4 (0 = 3 for KKT_MIXED factors
+                          of at least 1e8 panel entries, else 2); the grid is this many per
+                          SM or fewer if shared memory does not allow it (kkt_solve_multi
+                          runs two per SM) */
   int32_t solve_ent;   /* L entries staged per triangular-solve chunk item, 2048..32768
-                          (0 = 16000 for KKT_MIXED, 8192 for KKT_FP64). KKT_MIXED stages a
-                          head's first chunk and a subtree's panels in min(solve_ent, 7680)
-                          entries and puts chunk tiles where the heads' inverses go, so that
-                          three solve CTAs fit on an SM */
+                          (0 = 8192 for KKT_FP64; KKT_MIXED: 16000 for factors of at least
+                          1e8 panel entries, else 16384). Those large KKT_MIXED factors
+                          stage a head's first chunk and a subtree's panels in
+                          min(solve_ent, 7680) entries and put chunk tiles where the heads'
+                          inverses go, so that three solve CTAs fit on an SM */
   int32_t refine;      /* KKT_MIXED refinement on K_delta: 1 = plain passes x += M r;
                           2 = flexible GMRES (restart 20) preconditioned by the mixed
                           solve M: one M application per iteration, like a pass, and it

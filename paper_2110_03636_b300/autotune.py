@@ -30,7 +30,7 @@ SPACE = {
     "relax_frac": ((1, 10), (1, 20), (1, 5)),
     "relax_wmax": (256, 128, 512),
     "solve_w": (128, 64, 192),
-    "solve_ent": (16000, 8192, 12288),
+    "solve_ent": (0, 8192, 12288),          # 0: the library's size-dependent default
     "tensor_cores": (1, 0),
     "tc_panel_min": (128, 512, 1024),
 }

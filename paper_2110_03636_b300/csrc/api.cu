@@ -109,7 +109,7 @@ struct kkt_handle_s {
   // preconditioned directions Z (N x kRestart), N = n + m
   double *fV = nullptr, *fZ = nullptr, *fw = nullptr, *fr = nullptr, *fzero = nullptr, *fpart = nullptr,
          *fdots = nullptr, *fcoef = nullptr, *fgs = nullptr;
-  double* hflag = nullptr;   // pinned: the FGMRES stop flag
+  double* hflag = nullptr;   // pinned: the FGMRES stop flag and the step's residual contraction
   bool multi = false;
   void *mv;
   double *mrhx, *mp, *mr, *my, *mq, *mbS, *mres_x, *mres_y, *mwv, *mxa;
@@ -337,18 +337,27 @@ static kkt_status analyse_host_impl(int64_t n, int64_t m, const int64_t* Hp, con
   h->hJi.assign(Ji, Ji + Jp[m]);
   // piece width and L entries per solve item. FP64: chunks, heads' chunk 0
   // and subtrees of 8192 entries, two solve CTAs per SM (about 98 KB of
-  // shared memory each). FP32: chunk tiles of 16000 entries share their
-  // region with the heads' inverses (ent0 = subtree entries = 7680), about
-  // 73 KB per CTA, three per SM.
+  // shared memory each). FP32 factors of at least kSolveOverlapMin panel
+  // entries: chunk tiles of 16000 entries share their region with the heads'
+  // inverses (ent0 = subtree entries = 7680), about 73 KB per CTA, three per
+  // SM (measured: 100^3, 1.2e10 entries, 15 % faster solves; 500 x 500,
+  // 3.2e8, unchanged); smaller FP32 factors keep 16384 entries for all items
+  // and two CTAs per SM (a 200 x 100 grid, 8e6 entries, was 5 % slower with
+  // the smaller head and subtree items).
+  constexpr int64_t kSolveOverlapMin = 100000000;
   const bool f64o = o.precision == KKT_FP64;
   const int sw = o.solve_w > 0 ? o.solve_w : (f64o ? 64 : 128);
-  const int ent = o.solve_ent > 0 ? o.solve_ent : (f64o ? 8192 : 16000);
-  const int ov = f64o ? 0 : 1;
-  const int ent0 = ov ? std::min(ent, 7680) : ent;
   // the triangle inversion holds a piece's sw x sw triangle in shared memory
   if ((size_t)sw * sw * (f64o ? 8 : 4) > (size_t)200 * 1024) { delete h; return KKT_ERR_INVALID; }
-  if (build_plan(h->S, Hp, Hi, Jp, Ji, sw, ent, ent0, ent0, ov, !f64o && o.tensor_cores, !f64o,
-                 o.tc_panel_min ? o.tc_panel_min : kTcPanelMinWidth, h->P) != 0) {
+  auto plan = [&](int ov) {
+    const int ent = o.solve_ent > 0 ? o.solve_ent : (f64o ? 8192 : (ov ? 16000 : 16384));
+    const int ent0 = ov ? std::min(ent, 7680) : ent;
+    return build_plan(h->S, Hp, Hi, Jp, Ji, sw, ent, ent0, ent0, ov, !f64o && o.tensor_cores, !f64o,
+                      o.tc_panel_min ? o.tc_panel_min : kTcPanelMinWidth, h->P);
+  };
+  int pr = plan(f64o ? 0 : 1);
+  if (pr == 0 && h->P.solve_ov && h->P.panel_total < kSolveOverlapMin) pr = plan(0);
+  if (pr != 0) {
     delete h;
     return KKT_ERR_INVALID;
   }
@@ -793,9 +802,10 @@ static SolveArgs<T> solve_args(kkt_handle h) {
 
 template <typename T>
 static kkt_status solve_pass(kkt_handle h, const double* bx, const double* by, double* ox, double* oy,
-                             int accumulate, int mode, cudaStream_t st, int nrhs = 1) {
+                             int accumulate, int mode, cudaStream_t st, int nrhs = 1, double rtol = 0.0) {
   CK(cudaMemsetAsync(h->counters, 0, sizeof(int) * (4 * (size_t)h->P.npieces + 8), st));
   SolveArgs<T> a = solve_args<T>(h);
+  if (rtol > 0) a.rtol = rtol;
   a.bx = bx; a.by = by; a.ox = ox; a.oy = oy; a.accumulate = accumulate; a.mode = mode;
   if (nrhs > 1) {
     a.nrhs = nrhs;
@@ -846,6 +856,8 @@ static kkt_status residual(kkt_handle h, const double* bx, const double* by, con
 // one reorthogonalisation; the small Hessenberg problem by Givens rotations
 // on the host. The mixed form's default refinement (opt.refine = 2).
 constexpr int kRestart = 20;
+constexpr double kInnerRtolMax = 0.5;   // loosest inner CG tolerance of a refinement pass
+constexpr double kInnerRtolScale = 2.0; // inner tolerance per unit of the last step's contraction
 static_assert(kRestart + 1 <= kMaxKrylov, "basis size");
 
 static kkt_status solve_fgmres(kkt_handle h, const double* rx, const double* ry, double* dx, double* dy,
@@ -858,9 +870,9 @@ static kkt_status solve_fgmres(kkt_handle h, const double* rx, const double* ry,
     h->fw = A.alloc<double>(N); h->fr = A.alloc<double>(N); h->fzero = A.alloc<double>(N);
     h->fpart = A.alloc<double>((size_t)296 * kMaxKrylov);
     h->fdots = A.alloc<double>(kMaxKrylov); h->fcoef = A.alloc<double>(kMaxKrylov);
-    h->fgs = A.alloc<double>((size_t)(kRestart + 1) * kRestart + 2 * kRestart + 2 * (kRestart + 1) + 1);
+    h->fgs = A.alloc<double>((size_t)(kRestart + 1) * kRestart + 2 * kRestart + 2 * (kRestart + 1) + 2);
     if (A.failed) { h->fV = nullptr; return KKT_ERR_OOM; }
-    if (!h->hflag && cudaMallocHost((void**)&h->hflag, sizeof(double)) != cudaSuccess) {
+    if (!h->hflag && cudaMallocHost((void**)&h->hflag, 2 * sizeof(double)) != cudaSuccess) {
       cudaGetLastError();
       h->fV = nullptr;
       return KKT_ERR_OOM;
@@ -870,8 +882,14 @@ static kkt_status solve_fgmres(kkt_handle h, const double* rx, const double* ry,
   kkt_status s = reset_status(h, st);
   if (s) return s;
   int total_it = 0, brk = 0, applications = 0;
+  // The preconditioner's inner CG tolerance follows the outer iteration: an
+  // application never needs to be more accurate than the contraction the
+  // last FGMRES step achieved (where that is poor, a pass of one S product
+  // serves as well as a converged one; where it is strong, passes stay
+  // tight).
+  double inner_rtol = h->opt.cg_rtol;
   auto apply_M = [&](const double* bx, const double* by, double* ox, double* oy) -> kkt_status {
-    kkt_status e = solve_pass<float>(h, bx, by, ox, oy, 0, 0, st);
+    kkt_status e = solve_pass<float>(h, bx, by, ox, oy, 0, 0, st, 1, inner_rtol);
     if (e) return e;
     if ((e = read_status(h, st))) return e;
     if (!h->profp) {
@@ -942,10 +960,11 @@ static kkt_status solve_fgmres(kkt_handle h, const double* rx, const double* ry,
       // column k of H, rotations, g; coef[0] = -1/||w||: V_{k+1} = u / ||u|| = -w / ||w||
       CK(launch_fgmres_coef(2, k, R, h->fdots, h->dst, tol, h->fgs, h->fcoef, st));
       CK(launch_lincomb(h->fV + (size_t)(k + 1) * N, 0.0, h->fw, N, N, 1, h->fcoef, st));
-      CK(cudaMemcpyAsync(h->hflag, h->fgs + (R + 1) * R + 2 * R + 2 * (R + 1), sizeof(double),
+      CK(cudaMemcpyAsync(h->hflag, h->fgs + (R + 1) * R + 2 * R + 2 * (R + 1), 2 * sizeof(double),
                          cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
-      if (*h->hflag != 0.0) { k++; break; }
+      inner_rtol = std::min(kInnerRtolMax, std::max(h->opt.cg_rtol, kInnerRtolScale * h->hflag[1]));
+      if (h->hflag[0] != 0.0) { k++; break; }
     }
     // y = H^-1 g (upper triangular k x k); x += Z y
     if (k > 0) {

@@ -174,6 +174,7 @@ __global__ void k_fgmres_coef(int mode, int k, int R, const double* __restrict__
     g[k] = cs[k] * g[k];
     coef[0] = hn > 0 ? -1.0 / hn : 0.0;
     *flag = (fabs(g[k + 1]) <= tol || hn == 0.0) ? 1.0 : 0.0;
+    flag[1] = fabs(sn[k]);   // this step's residual contraction |g[k+1]| / |g[k]|
   } else if (mode == 3) {
     for (int i = k - 1; i >= 0; i--) {
       double t = g[i];
