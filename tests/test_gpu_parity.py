@@ -808,3 +808,29 @@ def test_handle_still_solves_after_handles_with_smaller_solve_layouts(precision)
         assert s.info.cg_iters > 0 and s.info.rr <= 1e-9
         assert rel(torch.cat([dx, dy]).cpu().numpy(), ref) <= 1e-6
     s.close()
+
+
+def test_multi_rhs_on_a_large_mixed_plan_equals_single_solves():
+    """Mixed factors of at least 1e8 panel entries solve one right-hand side
+    with chunk tiles over the inverse region (three solve CTAs per SM); the
+    several-right-hand-side launches switch to the separate layout. On the
+    500 x 500 workload (3.2e8 panel entries) four right-hand sides solved
+    together equal their single solves to the refinement's tolerance and
+    reach the RR target."""
+    sys = W.make_config("grid2d_n250k")
+    s = K.KKTSolver(sys.n, sys.m, sys.H_colptr, sys.H_rowidx, sys.J_rowptr, sys.J_colidx, precision="mixed",
+                    ordering="nd")
+    assert s.symbolic_info.panel_entries >= 10 ** 8
+    rng = np.random.default_rng(11)
+    RX = rng.standard_normal((4, sys.n))
+    RY = rng.standard_normal((4, sys.m))
+    s.factor(cu(sys.H_vals), cu(sys.J_vals), sys.delta, sys.gamma)
+    dx, dy, infos = s.solve_multi(cu(RX), cu(RY))
+    for j in range(4):
+        assert infos[j].rr <= 1e-8
+        sx, sy = s.solve(cu(RX[j]), cu(RY[j]))
+        assert s.info.rr <= 1e-8
+        a = torch.cat([dx[j], dy[j]]).cpu().numpy()
+        b = torch.cat([sx, sy]).cpu().numpy()
+        assert rel(a, b) <= 1e-6
+    s.close()
