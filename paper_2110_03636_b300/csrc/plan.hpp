@@ -159,7 +159,7 @@ inline int64_t packed_inv_size(int64_t pw) {
 }
 
 // tc_syrk: fronts with rb >= kTcMinRows and at least kTcMinWidth columns get
-// 128 x 128 tensor-core SYRK tiles; the persistent kernel runs at most
+// 128 x 256 tensor-core SYRK tiles; the persistent kernel runs at most
 // kTcGrid CTAs (one per SM). Before each tensor-core launch a split launch
 // writes the launch's operands, rows [r0, rows) x K [K begin, K end) of each
 // front, as operand tiles (kTcTileFloats floats each, in the layout the MMA

@@ -750,7 +750,7 @@ def test_schur_krylov_variants_need_fp64():
 
 def test_batched_factor_on_tensor_core_fronts_matches_oracle():
     """The batched form's one-graph factorization (system b = blockIdx.y of
-    every launch, 3-D tensor maps over the systems' panels) on fronts that
+    every launch, one tensor-core operand workspace per system) on fronts that
     take the tensor-core SYRK and in-panel updates: each system's solution
     equals the oracle's, read from its own batch slot with no copies; the
     single-system path of the same handle still works afterwards."""
