@@ -42,7 +42,7 @@ constexpr int kSolveThreads = 256;
 struct SolveSmemHdr {
   unsigned long long mbar;   // completion of the bulk copies of the current item
   unsigned phase;
-  int item;
+  int item, code;   // the CTA's current ticket and its item code
   int flag;
   // cycle counters of thread 0 (kept when a.instr != nullptr): dispatch,
   // dependency waits, bulk-copy waits, whole items, grid barriers, items
@@ -1052,13 +1052,19 @@ __device__ bool sweep(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>& t,
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(&a.disp[(seq + 1) % 3], 0);
   const int32_t* items = FWD ? a.fwd_items : a.bwd_items;
   for (;;) {
+    // warp 1 takes the next ticket and reads its item code while warp 0 may
+    // still be publishing the previous item (a fence and the arrival
+    // atomics): the two round trips overlap instead of adding up
     long long td = 0;
-    if (threadIdx.x == 0) {
-      td = clock64();
-      h.item = atomicAdd(&a.disp[seq % 3], 1);
+    if (threadIdx.x == 0) td = clock64();
+    if (threadIdx.x == 32) {
+      const int t = atomicAdd(&a.disp[seq % 3], 1);
+      h.item = t;
+      h.code = t < a.nitems ? items[t] : 0;
     }
     __syncthreads();
     const int it = h.item;
+    const int code = h.code;
     __syncthreads();
     unsigned long long tg0 = 0;
     if (threadIdx.x == 0) {
@@ -1068,7 +1074,6 @@ __device__ bool sweep(const SolveArgs<T>& a, SolveSmemHdr& h, const Tiles<T>& t,
       if (a.trace) tg0 = globaltimer();
     }
     if (it >= a.nitems) return true;
-    const int code = items[it];
     const int kind = code < -(int)a.npieces ? 0 : (code < 0 ? 1 : 2);
     bool ok;
     if (code < -(int)a.npieces) {
