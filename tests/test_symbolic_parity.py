@@ -227,3 +227,19 @@ def test_4x4_invalid_jd_rejected():
             K.kkt_analyse_4x4(p["n_x"], p["m_c"], p["m_d"], p["H_colptr"], p["H_rowidx"], p["J_rowptr"],
                               p["J_colidx"], p["Jd_rowptr"], Jc, host=True)
         assert e.value.code == 1
+
+
+@pytest.mark.parametrize("wa,wc", [(300, 300), (700, 260)])
+def test_dense_front_probe_system(wa, wc):
+    """The profiling probe's dense-front system (workloads.probe): natural
+    order gives exactly three fronts, A (wa columns, wc rows below), B (100
+    columns, wc below) and the root C (wc columns), with the library's
+    analysis bit-exact against the oracle's."""
+    from workloads.probe import dense_fronts
+    sys = dense_fronts(wa, wc)
+    assert_same(sys, ordering=1)
+    g, _ = lib_symbolic(sys, ordering=1)
+    w = np.diff(g["sn_start"])
+    nr = np.diff(g["sn_rowptr"])
+    np.testing.assert_array_equal(w, [wa, 100, wc])
+    np.testing.assert_array_equal(nr - w, [wc, wc, 0])
