@@ -834,3 +834,28 @@ def test_multi_rhs_on_a_large_mixed_plan_equals_single_solves():
         b = torch.cat([sx, sy]).cpu().numpy()
         assert rel(a, b) <= 1e-6
     s.close()
+
+
+def test_batched_form_on_a_large_mixed_plan_equals_single_solves():
+    """The batched form on a plan that uses the overlapped solve layout (the
+    500 x 500 workload, 3.2e8 panel entries, tensor-core fronts): two systems
+    factored in one graph and solved on the helper handles equal the same
+    systems factored and solved one at a time, and reach the RR target."""
+    base = W.make_config("grid2d_n250k")
+    systems = [base, W.rescale_barrier(base, seed=(3, 1))]
+    s = K.KKTSolver(base.n, base.m, base.H_colptr, base.H_rowidx, base.J_rowptr, base.J_colidx, precision="mixed",
+                    ordering="nd")
+    assert s.symbolic_info.panel_entries >= 10 ** 8
+    code, st = s.factor_batch(cu(np.stack([x.H_vals for x in systems])), cu(np.stack([x.J_vals for x in systems])),
+                              base.delta, base.gamma)
+    assert code == 0 and list(st) == [0, 0]
+    dx, dy, infos, sst, code = s.solve_batch(cu(np.stack([x.r_x for x in systems])),
+                                             cu(np.stack([x.r_y for x in systems])))
+    assert code == 0 and list(sst) == [0, 0]
+    for b, x in enumerate(systems):
+        assert infos[b].rr <= 1e-8
+        s.factor(cu(x.H_vals), cu(x.J_vals), x.delta, x.gamma)
+        sx, sy = s.solve(cu(x.r_x), cu(x.r_y))
+        a = np.concatenate([dx[b].cpu().numpy(), dy[b].cpu().numpy()])
+        assert rel(a, torch.cat([sx, sy]).cpu().numpy()) <= 1e-6
+    s.close()
